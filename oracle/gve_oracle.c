@@ -1,0 +1,1098 @@
+/*
+ * gve_oracle.c -- plain FP64 CPU oracle for fixed-budget Gaussian volume
+ * encoding (arxiv 2608.14112).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this file's library.  It shares
+ * no code, header, table or constant generator with the CUDA path; it is
+ * written to be read against the paper, not to be fast.
+ *
+ * What each part follows:
+ *   - Primitive parameterisation: Sec. III-C, Eq. 2 (position, log-scales,
+ *     normalised quaternion, scalar attribute a, weight w = sigmoid(logit)).
+ *   - Field: Sec. III-C, Eq. 3, normalised Gaussian kernel regression with
+ *     density floor rho0 and truncation at squared Mahalanobis distance k^2.
+ *   - Loss: full-grid mean squared error (Sec. III-E, Eq. 6 value term as a
+ *     mean over voxel centres; optional occupancy mask 1[V > thr]).
+ *   - PSNR: 10 log10(1/MSE) (Sec. IV-C).
+ *   - Gradient: hand-derived chain rule through Eq. 3 and Eq. 2 (the paper's
+ *     closed-form-gradient engine, Sec. V-D).
+ *   - Adam with bias correction (Sec. III-E, Kingma and Ba).
+ *   - Allocation: Sec. III-E (Structure-Aware Fixed-Budget Allocation) and
+ *     Table I stages S1a..S1e; Eq. 4 jitter.
+ *   - Budget limit: Sec. V-B (seed limit).
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - Truncation decision.  Whether a (voxel, Gaussian) pair is kept decides
+ *     an integer (membership), so it is taken in float32, the paper's
+ *     precision: float32 coefficients of -0.5*log2(e)*C are obtained by
+ *     rounding an FP64 computation done in a fixed operation order, and the
+ *     exponent t is evaluated by a fixed chain of float32 fused multiply-adds;
+ *     the pair is kept iff t > T, T = fp32(-0.5*log2(e)*k^2).  The VALUE of
+ *     every kept pair is then evaluated in FP64 from the FP64 parameters.
+ *   - w = sigmoid(w_logit); the scalar a is a raw parameter.
+ *   - Quaternion order (w,x,y,z), normalised in every forward pass.
+ *   - Voxel (i,j,k) has its centre at (i,j,k); x is the fastest axis.
+ *   - Gradient stencil: central differences, one-sided at the borders.
+ *   - Occupancy V > 0.02 decided in float32; detail eligibility adds g > 0.
+ *   - Detail/coverage counts Nd = floor(0.55 N + 1/2), Nc = N - Nd.
+ *   - Weighted draw without replacement: Efraimidis-Spirakis keys
+ *     -ln(u)/g with u from Philox4x32-10 (Salmon et al. 2011); the Nd smallest
+ *     keys win, ties broken by voxel index.  The coverage draw keeps the Nc
+ *     smallest raw 64-bit Philox words among occupied voxels.
+ *   - Jitter u_k = (x_k >> 8) * 2^-24 - 1/2 from Philox (Eq. 4).
+ *   - Group spacing: lower median, over an evenly strided subsample of at most
+ *     4096 seeds of the group, of the mean distance to the 3 nearest seeds of
+ *     the same group; sigma_g = h_g / 2.
+ *   - Tangent elongation s_t = sigma_g * clamp(1 + g(c)/gbar, 1, 3), gbar the
+ *     lower median of g over occupied voxels; s_perp = sigma_g; all scales
+ *     clamped to [0.3, max(nx,ny,nz)/16].
+ *   - 7^3 structure-tensor window clipped at the borders; cyclic Jacobi.
+ *   - Initial a = trilinear V at mu (edge clamped); w = 0.1.
+ *
+ * Everything here is FP64 unless a comment says float32.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* -0.5 * log2(e): the factor that turns a squared Mahalanobis distance into a
+ * base-2 exponent.  Used only for the float32 truncation decision. */
+#define OR_NEG_HALF_LOG2E (-0.72134752044448170367996234050095)
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its definition.   */
+/* ------------------------------------------------------------------------ */
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo)
+{
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(0xD2511F53u, c0, &hi0, &lo0);
+        mulhilo32(0xCD9E8D57u, c2, &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Counter layout used by the allocator: (lo32(index), hi32(index), stream,
+ * 'GVE1'), key = (lo32(seed), hi32(seed)). */
+#define OR_CTR_TAG 0x47564531u
+static void or_draw(uint64_t index, uint32_t stream, uint64_t seed, uint32_t out[4])
+{
+    uint32_t ctr[4] = {(uint32_t)index, (uint32_t)(index >> 32), stream, OR_CTR_TAG};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Primitive activation, Eq. 2: mu, s = exp(log s), q/|q|, R(q), w, a.       */
+/* Record layout: [mux muy muz ls0 ls1 ls2 qw qx qy qz a w_logit].           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double mu[3], s[3], q[4], nq;   /* q normalised, nq = |q_raw| */
+    double R[3][3];                 /* rotation of the normalised quaternion */
+    double C[3][3];                 /* inverse covariance R diag(s^-2) R^T */
+    double w, a;
+    int valid;
+} act_t;
+
+static void rot_from_quat(double w, double x, double y, double z, double R[3][3])
+{
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static int all_finite(const double* p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(p[i])) return 0;
+    return 1;
+}
+
+static void activate(const double* p, act_t* A)
+{
+    memset(A, 0, sizeof(*A));
+    if (!all_finite(p, 12)) return;
+    for (int j = 0; j < 3; ++j) { A->mu[j] = p[j]; A->s[j] = exp(p[3 + j]); }
+    double qw = p[6], qx = p[7], qy = p[8], qz = p[9];
+    double nq = sqrt(((qw * qw + qx * qx) + qy * qy) + qz * qz);
+    if (!(nq > 0.0) || !isfinite(nq)) return;
+    for (int j = 0; j < 3; ++j)
+        if (!(A->s[j] > 0.0) || !isfinite(A->s[j])) return;
+    A->nq = nq;
+    A->q[0] = qw / nq; A->q[1] = qx / nq; A->q[2] = qy / nq; A->q[3] = qz / nq;
+    rot_from_quat(A->q[0], A->q[1], A->q[2], A->q[3], A->R);
+    double inv[3];
+    for (int j = 0; j < 3; ++j) inv[j] = 1.0 / (A->s[j] * A->s[j]);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            A->C[a][b] = ((A->R[a][0] * A->R[b][0]) * inv[0] + (A->R[a][1] * A->R[b][1]) * inv[1])
+                       + (A->R[a][2] * A->R[b][2]) * inv[2];
+    A->a = p[10];
+    A->w = 1.0 / (1.0 + exp(-p[11]));
+    A->valid = 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* float32 truncation decision (reading of "squared Mahalanobis distance     */
+/* below k^2", Sec. III-C).                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    float mu[3];
+    float qxx, qyy, qzz, qxy2, qxz2, qyz2;
+    int valid;
+} pred_t;
+
+/* Coefficients from the float32 parameter record; FP64 in a fixed order,
+ * then rounded once to float32. */
+static void pred_coeffs(const float* p32, pred_t* P)
+{
+    double p[12];
+    for (int i = 0; i < 12; ++i) p[i] = (double)p32[i];
+    act_t A;
+    activate(p, &A);
+    P->valid = A.valid;
+    for (int j = 0; j < 3; ++j) P->mu[j] = p32[j];
+    if (!A.valid) return;
+    double Q00 = A.C[0][0] * OR_NEG_HALF_LOG2E, Q11 = A.C[1][1] * OR_NEG_HALF_LOG2E;
+    double Q22 = A.C[2][2] * OR_NEG_HALF_LOG2E, Q01 = A.C[0][1] * OR_NEG_HALF_LOG2E;
+    double Q02 = A.C[0][2] * OR_NEG_HALF_LOG2E, Q12 = A.C[1][2] * OR_NEG_HALF_LOG2E;
+    P->qxx = (float)Q00; P->qyy = (float)Q11; P->qzz = (float)Q22;
+    P->qxy2 = (float)(2.0 * Q01); P->qxz2 = (float)(2.0 * Q02); P->qyz2 = (float)(2.0 * Q12);
+}
+
+static float pred_threshold(float k)
+{
+    double k2 = (double)k * (double)k;
+    return (float)(k2 * OR_NEG_HALF_LOG2E);
+}
+
+/* Exponent t of the kept-pair test, by a fixed float32 chain. */
+static float pred_t_of(const pred_t* P, int x, int y, int z)
+{
+    float dx = (float)x - P->mu[0];
+    float dy = (float)y - P->mu[1];
+    float dz = (float)z - P->mu[2];
+    float e = P->qxz2 * dz;
+    float b = fmaf(P->qxy2, dy, e);
+    float f = P->qyz2 * dz;
+    float g = fmaf(P->qyy, dy, f);
+    float hh = P->qzz * dz;
+    float dzh = dz * hh;
+    float c = fmaf(dy, g, dzh);
+    float u = fmaf(P->qxx, dx, b);
+    return fmaf(dx, u, c);
+}
+
+float or_pred_t(const float* p32, int x, int y, int z)
+{
+    pred_t P;
+    pred_coeffs(p32, &P);
+    if (!P.valid) return -INFINITY;
+    return pred_t_of(&P, x, y, z);
+}
+
+float or_pred_threshold(float k) { return pred_threshold(k); }
+
+/* ------------------------------------------------------------------------ */
+/* Enumeration box used by the oracle itself: a generous superset of every   */
+/* voxel the float32 decision can keep (k*1.01 + 1/2 standard deviations).    */
+/* ------------------------------------------------------------------------ */
+static int enum_box(const act_t* A, double k, int truncated, const int dims[3], int lo[3], int hi[3])
+{
+    if (!A->valid) return 0;
+    for (int j = 0; j < 3; ++j) {
+        if (!truncated) { lo[j] = 0; hi[j] = dims[j] - 1; continue; }
+        double var = 0.0;
+        for (int m = 0; m < 3; ++m) var += A->R[j][m] * A->R[j][m] * A->s[m] * A->s[m];
+        double r = (k * 1.01) * sqrt(var) + 0.5;
+        double l = ceil(A->mu[j] - r), h = floor(A->mu[j] + r);
+        if (!(l <= h)) return 0;
+        if (l < 0) l = 0;
+        if (h > dims[j] - 1) h = dims[j] - 1;
+        if (l > h) return 0;
+        lo[j] = (int)l; hi[j] = (int)h;
+    }
+    return 1;
+}
+
+/* Mahalanobis distance squared at voxel centre p, FP64. */
+static double maha2(const act_t* A, double px, double py, double pz)
+{
+    double d[3] = {px - A->mu[0], py - A->mu[1], pz - A->mu[2]};
+    double m = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) m += d[a] * A->C[a][b] * d[b];
+    return m;
+}
+
+typedef struct {
+    act_t A;
+    pred_t P;
+    int lo[3], hi[3];
+    int has_box;
+} gctx_t;
+
+static gctx_t* prepare(const double* prm, const double* pred_prm, int64_t n, double k, int truncated,
+                       const int dims[3])
+{
+    gctx_t* G = (gctx_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(gctx_t));
+    if (!G) return NULL;
+    for (int64_t i = 0; i < n; ++i) {
+        activate(prm + 12 * i, &G[i].A);
+        const double* pp = pred_prm ? pred_prm + 12 * i : prm + 12 * i;
+        float p32[12];
+        for (int j = 0; j < 12; ++j) p32[j] = (float)pp[j];
+        pred_coeffs(p32, &G[i].P);
+        if (pred_prm) {
+            /* the box follows the parameters that decide membership */
+            act_t Ap;
+            activate(pp, &Ap);
+            G[i].has_box = G[i].A.valid && enum_box(&Ap, k, truncated, dims, G[i].lo, G[i].hi);
+        } else {
+            G[i].has_box = enum_box(&G[i].A, k, truncated, dims, G[i].lo, G[i].hi);
+        }
+        if (!G[i].P.valid) G[i].has_box = 0;
+    }
+    return G;
+}
+
+static int kept(const gctx_t* g, float T, int truncated, int x, int y, int z)
+{
+    if (!truncated) return 1;
+    return pred_t_of(&g->P, x, y, z) > T;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 3 over a region [r0, r0+rs) of the grid.  num/den/vt have the         */
+/* region's size, x fastest.  truncated = 0 evaluates every voxel for every  */
+/* Gaussian (the dense sum).  normalized = 0 returns num (plain sum).        */
+/* pred_prm (optional) decides membership instead of prm (frozen mask).      */
+/* ------------------------------------------------------------------------ */
+int or_eval_region(const double* prm, const double* pred_prm, int64_t n, const int dims[3],
+                   const int r0[3], const int rs[3], float k, double rho0, int normalized,
+                   int truncated, double* num, double* den, double* vt)
+{
+    gctx_t* G = prepare(prm, pred_prm, n, (double)k, truncated, dims);
+    if (!G) return 1;
+    float T = pred_threshold(k);
+    /* Gaussians whose box meets the region, in ascending index order */
+    int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t nids = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!G[i].has_box) continue;
+        int ok = 1;
+        for (int j = 0; j < 3; ++j)
+            if (G[i].hi[j] < r0[j] || G[i].lo[j] > r0[j] + rs[j] - 1) ok = 0;
+        if (ok) ids[nids++] = i;
+    }
+    int64_t plane = (int64_t)rs[0] * rs[1];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int zz = 0; zz < rs[2]; ++zz) {
+        int z = r0[2] + zz;
+        double* nm = num + plane * zz;
+        double* dn = den + plane * zz;
+        for (int64_t v = 0; v < plane; ++v) { nm[v] = 0.0; dn[v] = 0.0; }
+        for (int64_t t = 0; t < nids; ++t) {
+            const gctx_t* g = &G[ids[t]];
+            if (z < g->lo[2] || z > g->hi[2]) continue;
+            int y0 = g->lo[1] > r0[1] ? g->lo[1] : r0[1];
+            int y1 = g->hi[1] < r0[1] + rs[1] - 1 ? g->hi[1] : r0[1] + rs[1] - 1;
+            int x0 = g->lo[0] > r0[0] ? g->lo[0] : r0[0];
+            int x1 = g->hi[0] < r0[0] + rs[0] - 1 ? g->hi[0] : r0[0] + rs[0] - 1;
+            for (int y = y0; y <= y1; ++y)
+                for (int x = x0; x <= x1; ++x) {
+                    if (!kept(g, T, truncated, x, y, z)) continue;
+                    double Gv = exp(-0.5 * maha2(&g->A, x, y, z));
+                    int64_t v = (int64_t)(y - r0[1]) * rs[0] + (x - r0[0]);
+                    nm[v] += g->A.w * g->A.a * Gv;
+                    dn[v] += g->A.w * Gv;
+                }
+        }
+        if (vt) {
+            double* o = vt + plane * zz;
+            for (int64_t v = 0; v < plane; ++v) {
+                if (!normalized) o[v] = nm[v];
+                else o[v] = nm[v] / (dn[v] > rho0 ? dn[v] : rho0);
+            }
+        }
+    }
+    free(ids);
+    free(G);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Loss (mean squared error over all M voxel centres, optional occupancy     */
+/* mask) and its analytic gradient with respect to the raw 12-float record. */
+/* grad may be NULL.  sse_out receives the unmasked sum of squared errors   */
+/* (for PSNR = 10 log10(M / sse)).                                          */
+/* ------------------------------------------------------------------------ */
+static void chain_rule(const act_t* A, const double* raw, double Ag, double Bg, const double S1[3],
+                       const double S2[3][3], double* out)
+{
+    /* dL/da, dL/dw, dL/dw_logit (Eq. 2 sigmoid) */
+    double w = A->w, a = A->a;
+    out[10] = w * Ag;
+    double dw = a * Ag + Bg;
+    out[11] = dw * w * (1.0 - w);
+    /* dL/dmu = -2 C S1 */
+    for (int i = 0; i < 3; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < 3; ++j) t += A->C[i][j] * S1[j];
+        out[i] = -2.0 * t;
+    }
+    /* C = R D R^T, D = diag(s^-2); dL/dC = S2 (symmetric) */
+    double D[3];
+    for (int j = 0; j < 3; ++j) D[j] = 1.0 / (A->s[j] * A->s[j]);
+    /* dL/dD_jj = (R^T S2 R)_jj ; dD_jj/dlog s_j = -2 D_jj */
+    for (int j = 0; j < 3; ++j) {
+        double t = 0.0;
+        for (int a2 = 0; a2 < 3; ++a2)
+            for (int b = 0; b < 3; ++b) t += A->R[a2][j] * S2[a2][b] * A->R[b][j];
+        out[3 + j] = -2.0 * D[j] * t;
+    }
+    /* dL/dR = 2 S2 R D */
+    double gR[3][3];
+    for (int a2 = 0; a2 < 3; ++a2)
+        for (int j = 0; j < 3; ++j) {
+            double t = 0.0;
+            for (int b = 0; b < 3; ++b) t += S2[a2][b] * A->R[b][j];
+            gR[a2][j] = 2.0 * t * D[j];
+        }
+    /* dR/dq_hat for R(q) written out entry by entry */
+    double qw = A->q[0], qx = A->q[1], qy = A->q[2], qz = A->q[3];
+    double gw = 0, gx = 0, gy = 0, gz = 0;
+    /* R00 = 1-2y^2-2z^2 */
+    gy += gR[0][0] * (-4.0 * qy); gz += gR[0][0] * (-4.0 * qz);
+    /* R01 = 2xy - 2wz */
+    gw += gR[0][1] * (-2.0 * qz); gx += gR[0][1] * (2.0 * qy); gy += gR[0][1] * (2.0 * qx); gz += gR[0][1] * (-2.0 * qw);
+    /* R02 = 2xz + 2wy */
+    gw += gR[0][2] * (2.0 * qy); gx += gR[0][2] * (2.0 * qz); gy += gR[0][2] * (2.0 * qw); gz += gR[0][2] * (2.0 * qx);
+    /* R10 = 2xy + 2wz */
+    gw += gR[1][0] * (2.0 * qz); gx += gR[1][0] * (2.0 * qy); gy += gR[1][0] * (2.0 * qx); gz += gR[1][0] * (2.0 * qw);
+    /* R11 = 1-2x^2-2z^2 */
+    gx += gR[1][1] * (-4.0 * qx); gz += gR[1][1] * (-4.0 * qz);
+    /* R12 = 2yz - 2wx */
+    gw += gR[1][2] * (-2.0 * qx); gx += gR[1][2] * (-2.0 * qw); gy += gR[1][2] * (2.0 * qz); gz += gR[1][2] * (2.0 * qy);
+    /* R20 = 2xz - 2wy */
+    gw += gR[2][0] * (-2.0 * qy); gx += gR[2][0] * (2.0 * qz); gy += gR[2][0] * (-2.0 * qw); gz += gR[2][0] * (2.0 * qx);
+    /* R21 = 2yz + 2wx */
+    gw += gR[2][1] * (2.0 * qx); gx += gR[2][1] * (2.0 * qw); gy += gR[2][1] * (2.0 * qz); gz += gR[2][1] * (2.0 * qy);
+    /* R22 = 1-2x^2-2y^2 */
+    gx += gR[2][2] * (-4.0 * qx); gy += gR[2][2] * (-4.0 * qy);
+    /* through q_hat = q / |q| */
+    double dot = gw * qw + gx * qx + gy * qy + gz * qz;
+    out[6] = (gw - qw * dot) / A->nq;
+    out[7] = (gx - qx * dot) / A->nq;
+    out[8] = (gy - qy * dot) / A->nq;
+    out[9] = (gz - qz * dot) / A->nq;
+    (void)raw;
+}
+
+double or_loss_grad(const double* prm, const double* pred_prm, int64_t n, const float* field,
+                    const int dims[3], float k, double rho0, int normalized, int truncated,
+                    double mask_thresh, double* grad, double* sse_out)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2];
+    int r0[3] = {0, 0, 0};
+    double* num = (double*)malloc(sizeof(double) * (size_t)M);
+    double* den = (double*)malloc(sizeof(double) * (size_t)M);
+    double* vt = (double*)malloc(sizeof(double) * (size_t)M);
+    double* gn = grad ? (double*)malloc(sizeof(double) * (size_t)M) : NULL;
+    double* gd = grad ? (double*)malloc(sizeof(double) * (size_t)M) : NULL;
+    if (!num || !den || !vt || (grad && (!gn || !gd))) return NAN;
+    or_eval_region(prm, pred_prm, n, dims, r0, dims, k, rho0, normalized, truncated, num, den, vt);
+    double loss = 0.0, sse = 0.0;
+    float mthr = (float)mask_thresh;
+    for (int64_t v = 0; v < M; ++v) {
+        double r = vt[v] - (double)field[v];
+        sse += r * r;
+        int in = mask_thresh < 0.0 || field[v] > mthr;
+        double rl = in ? r : 0.0;
+        loss += rl * rl;
+        if (grad) {
+            double up = 2.0 * rl / (double)M;           /* dL/dVtilde */
+            if (!normalized) { gn[v] = up; gd[v] = 0.0; }
+            else if (den[v] >= rho0) { gn[v] = up / den[v]; gd[v] = -vt[v] * gn[v]; }
+            else { gn[v] = up / rho0; gd[v] = 0.0; }
+        }
+    }
+    loss /= (double)M;
+    if (sse_out) *sse_out = sse;
+    if (grad) {
+        gctx_t* G = prepare(prm, pred_prm, n, (double)k, truncated, dims);
+        float T = pred_threshold(k);
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            double* out = grad + 12 * i;
+            for (int j = 0; j < 12; ++j) out[j] = 0.0;
+            const gctx_t* g = &G[i];
+            if (!g->has_box || !g->A.valid) continue;
+            double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
+            for (int z = g->lo[2]; z <= g->hi[2]; ++z)
+                for (int y = g->lo[1]; y <= g->hi[1]; ++y)
+                    for (int x = g->lo[0]; x <= g->hi[0]; ++x) {
+                        if (!kept(g, T, truncated, x, y, z)) continue;
+                        int64_t v = ((int64_t)z * dims[1] + y) * dims[0] + x;
+                        double d[3] = {x - g->A.mu[0], y - g->A.mu[1], z - g->A.mu[2]};
+                        double Gv = exp(-0.5 * maha2(&g->A, x, y, z));
+                        Ag += Gv * gn[v];
+                        Bg += Gv * gd[v];
+                        double c = g->A.w * (g->A.a * gn[v] + gd[v]);   /* dL/dG */
+                        double h = -0.5 * c * Gv;                        /* dL/dm */
+                        for (int a2 = 0; a2 < 3; ++a2) {
+                            S1[a2] += h * d[a2];
+                            for (int b = 0; b < 3; ++b) S2[a2][b] += h * d[a2] * d[b];
+                        }
+                    }
+            chain_rule(&g->A, prm + 12 * i, Ag, Bg, S1, S2, out);
+        }
+        free(G);
+    }
+    free(num); free(den); free(vt); free(gn); free(gd);
+    return loss;
+}
+
+/* Gradient for a subset of Gaussians only; the field values it needs are
+ * computed on each Gaussian's own box from all Gaussians.  M is the full grid
+ * size used as the loss normaliser. */
+int or_grad_subset(const double* prm, int64_t n, const float* field, const int dims[3], float k,
+                   double rho0, int normalized, double mask_thresh, const int64_t* ids,
+                   int64_t nids, double* grad)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2];
+    float T = pred_threshold(k);
+    float mthr = (float)mask_thresh;
+    for (int64_t t = 0; t < nids; ++t) {
+        int64_t i = ids[t];
+        double* out = grad + 12 * t;
+        for (int j = 0; j < 12; ++j) out[j] = 0.0;
+        gctx_t g;
+        activate(prm + 12 * i, &g.A);
+        float p32[12];
+        for (int j = 0; j < 12; ++j) p32[j] = (float)prm[12 * i + j];
+        pred_coeffs(p32, &g.P);
+        if (!g.A.valid || !g.P.valid || !enum_box(&g.A, k, 1, dims, g.lo, g.hi)) continue;
+        int rs[3] = {g.hi[0] - g.lo[0] + 1, g.hi[1] - g.lo[1] + 1, g.hi[2] - g.lo[2] + 1};
+        int64_t R = (int64_t)rs[0] * rs[1] * rs[2];
+        double* num = (double*)malloc(sizeof(double) * (size_t)R);
+        double* den = (double*)malloc(sizeof(double) * (size_t)R);
+        double* vt = (double*)malloc(sizeof(double) * (size_t)R);
+        or_eval_region(prm, NULL, n, dims, g.lo, rs, k, rho0, normalized, 1, num, den, vt);
+        double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
+        for (int z = g.lo[2]; z <= g.hi[2]; ++z)
+            for (int y = g.lo[1]; y <= g.hi[1]; ++y)
+                for (int x = g.lo[0]; x <= g.hi[0]; ++x) {
+                    if (!(pred_t_of(&g.P, x, y, z) > T)) continue;
+                    int64_t rv = ((int64_t)(z - g.lo[2]) * rs[1] + (y - g.lo[1])) * rs[0] + (x - g.lo[0]);
+                    int64_t v = ((int64_t)z * dims[1] + y) * dims[0] + x;
+                    double r = vt[rv] - (double)field[v];
+                    if (!(mask_thresh < 0.0 || field[v] > mthr)) r = 0.0;
+                    double up = 2.0 * r / (double)M, gnv, gdv;
+                    if (!normalized) { gnv = up; gdv = 0.0; }
+                    else if (den[rv] >= rho0) { gnv = up / den[rv]; gdv = -vt[rv] * gnv; }
+                    else { gnv = up / rho0; gdv = 0.0; }
+                    double d[3] = {x - g.A.mu[0], y - g.A.mu[1], z - g.A.mu[2]};
+                    double Gv = exp(-0.5 * maha2(&g.A, x, y, z));
+                    Ag += Gv * gnv;
+                    Bg += Gv * gdv;
+                    double c = g.A.w * (g.A.a * gnv + gdv);
+                    double h = -0.5 * c * Gv;
+                    for (int a2 = 0; a2 < 3; ++a2) {
+                        S1[a2] += h * d[a2];
+                        for (int b = 0; b < 3; ++b) S2[a2][b] += h * d[a2] * d[b];
+                    }
+                }
+        chain_rule(&g.A, prm + 12 * i, Ag, Bg, S1, S2, out);
+        free(num); free(den); free(vt);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adam (Kingma and Ba 2015) with bias correction; t is 1-based.             */
+/* ------------------------------------------------------------------------ */
+void or_adam(double* p, double* m, double* v, const double* g, int64_t cnt, int t, double lr,
+             double b1, double b2, double eps)
+{
+    double bc1 = 1.0 - pow(b1, (double)t);
+    double bc2 = 1.0 - pow(b2, (double)t);
+    for (int64_t i = 0; i < cnt; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        double mh = m[i] / bc1, vh = v[i] / bc2;
+        p[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* Fixed-budget refinement (Sec. III-E): iters steps of loss -> gradient ->
+ * Adam; losses[t] is the loss at the parameters before step t+1; the
+ * returned value is the unmasked SSE of one extra evaluation after the last
+ * step.  prm is updated in place; m and v (12n each) start at zero. */
+double or_refine(double* prm, int64_t n, const float* field, const int dims[3], float k, double rho0,
+                 int normalized, double mask_thresh, int iters, double lr, double b1, double b2,
+                 double eps, double* losses)
+{
+    double* g = (double*)malloc(sizeof(double) * 12 * (size_t)(n > 0 ? n : 1));
+    double* m = (double*)calloc(12 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    double* v = (double*)calloc(12 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int t = 0; t < iters; ++t) {
+        double sse;
+        double L = or_loss_grad(prm, NULL, n, field, dims, k, rho0, normalized, 1, mask_thresh, g, &sse);
+        if (losses) losses[t] = L;
+        or_adam(prm, m, v, g, 12 * n, t + 1, lr, b1, b2, eps);
+    }
+    double sse = 0.0;
+    or_loss_grad(prm, NULL, n, field, dims, k, rho0, normalized, 1, mask_thresh, NULL, &sse);
+    free(g); free(m); free(v);
+    return sse;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brick binning: which bricks of B^3 voxels may hold a kept pair of         */
+/* Gaussian i.  A conservative rule, decided bit-identically on both sides:  */
+/* FP64 box of Mahalanobis radius kb = k (1.0001 + 1e-5 cond) plus 0.01      */
+/* voxel, then a float32 whitened-distance lower bound per brick.            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int blo[3], bhi[3];
+    float L[3][3];
+    float e[3];
+    float K2;
+    int nonempty;
+} binspec_t;
+
+static void bin_spec(const float* p32, const int dims[3], float k, int B, binspec_t* S)
+{
+    memset(S, 0, sizeof(*S));
+    double p[12];
+    for (int i = 0; i < 12; ++i) p[i] = (double)p32[i];
+    act_t A;
+    activate(p, &A);
+    if (!A.valid) return;
+    double smin = A.s[0], smax = A.s[0];
+    for (int j = 1; j < 3; ++j) { if (A.s[j] < smin) smin = A.s[j]; if (A.s[j] > smax) smax = A.s[j]; }
+    double ratio = smax / smin;
+    double cond = ratio * ratio;
+    double kb = (double)k * (1.0001 + 1e-5 * cond);
+    if (!isfinite(kb)) return;
+    for (int j = 0; j < 3; ++j) {
+        double var = ((A.R[j][0] * A.R[j][0]) * (A.s[0] * A.s[0]) + (A.R[j][1] * A.R[j][1]) * (A.s[1] * A.s[1]))
+                   + (A.R[j][2] * A.R[j][2]) * (A.s[2] * A.s[2]);
+        double r = kb * sqrt(var) + 0.01;
+        double l = ceil(A.mu[j] - r), h = floor(A.mu[j] + r);
+        if (!(l <= h) || !isfinite(l) || !isfinite(h)) return;
+        if (l < 0.0) l = 0.0;
+        if (h > (double)(dims[j] - 1)) h = (double)(dims[j] - 1);
+        if (l > h) return;
+        S->blo[j] = (int)l / B;
+        S->bhi[j] = (int)h / B;
+    }
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) S->L[j][i] = (float)(A.R[i][j] / A.s[j]);
+    float hB = (float)(0.5 * (double)(B - 1)) + 0.01f;
+    for (int j = 0; j < 3; ++j) {
+        float sabs = (fabsf(S->L[j][0]) + fabsf(S->L[j][1])) + fabsf(S->L[j][2]);
+        S->e[j] = hB * sabs;
+    }
+    S->K2 = (float)(kb * kb * 1.0001 + 1e-4);
+    S->nonempty = 1;
+}
+
+static int bin_test(const binspec_t* S, const float mu[3], int B, int bx, int by, int bz)
+{
+    float half = (float)(0.5 * (double)(B - 1));
+    float cx = (float)(bx * B) + half;
+    float cy = (float)(by * B) + half;
+    float cz = (float)(bz * B) + half;
+    float dcx = cx - mu[0], dcy = cy - mu[1], dcz = cz - mu[2];
+    float acc[3];
+    for (int j = 0; j < 3; ++j) {
+        float t0 = S->L[j][0] * dcx;
+        float y = fmaf(S->L[j][2], dcz, fmaf(S->L[j][1], dcy, t0));
+        float a = fabsf(y) - S->e[j];
+        acc[j] = a > 0.0f ? a : 0.0f;
+    }
+    float a22 = acc[2] * acc[2];
+    float s = fmaf(acc[0], acc[0], fmaf(acc[1], acc[1], a22));
+    return s <= S->K2;
+}
+
+/* counts[i] = number of bricks listed for Gaussian i; returns the total. */
+int64_t or_bin_count(const float* p32, int64_t n, const int dims[3], float k, int B, uint32_t* counts)
+{
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        binspec_t S;
+        bin_spec(p32 + 12 * i, dims, k, B, &S);
+        uint32_t c = 0;
+        if (S.nonempty)
+            for (int bz = S.blo[2]; bz <= S.bhi[2]; ++bz)
+                for (int by = S.blo[1]; by <= S.bhi[1]; ++by)
+                    for (int bx = S.blo[0]; bx <= S.bhi[0]; ++bx)
+                        c += (uint32_t)bin_test(&S, p32 + 12 * i, B, bx, by, bz);
+        counts[i] = c;
+        total += c;
+    }
+    return total;
+}
+
+/* (brick key, gid) pairs in Gaussian-major order, bricks z-major within a
+ * Gaussian; key = (bz * nby + by) * nbx + bx. */
+int64_t or_bin_emit(const float* p32, int64_t n, const int dims[3], float k, int B, uint32_t* keys,
+                    uint32_t* gids)
+{
+    int nbx = (dims[0] + B - 1) / B, nby = (dims[1] + B - 1) / B;
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        binspec_t S;
+        bin_spec(p32 + 12 * i, dims, k, B, &S);
+        if (!S.nonempty) continue;
+        for (int bz = S.blo[2]; bz <= S.bhi[2]; ++bz)
+            for (int by = S.blo[1]; by <= S.bhi[1]; ++by)
+                for (int bx = S.blo[0]; bx <= S.bhi[0]; ++bx)
+                    if (bin_test(&S, p32 + 12 * i, B, bx, by, bz)) {
+                        keys[o] = (uint32_t)(((int64_t)bz * nby + by) * nbx + bx);
+                        gids[o] = (uint32_t)i;
+                        ++o;
+                    }
+    }
+    return o;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Allocation (Sec. III-E, Table I S1a..S1e).                                */
+/* ------------------------------------------------------------------------ */
+static inline int64_t vidx(const int dims[3], int x, int y, int z)
+{
+    return ((int64_t)z * dims[1] + y) * dims[0] + x;
+}
+
+/* S1a: float32 gradient magnitude (central differences, one-sided at the
+ * borders), in a fixed operation order: the value that decides eligibility
+ * and weights the detail draw. */
+static float dcomp32(const float* V, const int dims[3], int x, int y, int z, int axis)
+{
+    int c[3] = {x, y, z};
+    int n = dims[axis];
+    if (n < 2) return 0.0f;
+    int lo = c[axis] - 1, hi = c[axis] + 1;
+    float scale = 0.5f;
+    if (lo < 0) { lo = c[axis]; scale = 1.0f; }
+    if (hi > n - 1) { hi = c[axis]; scale = 1.0f; }
+    int a[3] = {x, y, z}, b[3] = {x, y, z};
+    a[axis] = hi; b[axis] = lo;
+    float diff = V[vidx(dims, a[0], a[1], a[2])] - V[vidx(dims, b[0], b[1], b[2])];
+    return scale * diff;
+}
+
+void or_grad_mag32(const float* V, const int dims[3], float* g)
+{
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < dims[2]; ++z)
+        for (int y = 0; y < dims[1]; ++y)
+            for (int x = 0; x < dims[0]; ++x) {
+                float gx = dcomp32(V, dims, x, y, z, 0);
+                float gy = dcomp32(V, dims, x, y, z, 1);
+                float gz = dcomp32(V, dims, x, y, z, 2);
+                float sx = gx * gx, sy = gy * gy, sz = gz * gz;
+                float s = sx + sy;
+                s = s + sz;
+                g[vidx(dims, x, y, z)] = sqrtf(s);
+            }
+}
+
+/* FP64 gradient vector for the structure tensor. */
+static void grad64(const float* V, const int dims[3], int x, int y, int z, double gv[3])
+{
+    int c[3] = {x, y, z};
+    for (int axis = 0; axis < 3; ++axis) {
+        int n = dims[axis];
+        if (n < 2) { gv[axis] = 0.0; continue; }
+        int lo = c[axis] - 1, hi = c[axis] + 1;
+        double scale = 0.5;
+        if (lo < 0) { lo = c[axis]; scale = 1.0; }
+        if (hi > n - 1) { hi = c[axis]; scale = 1.0; }
+        int a[3] = {x, y, z}, b[3] = {x, y, z};
+        a[axis] = hi; b[axis] = lo;
+        gv[axis] = scale * ((double)V[vidx(dims, a[0], a[1], a[2])] - (double)V[vidx(dims, b[0], b[1], b[2])]);
+    }
+}
+
+/* S1d: 7^3 structure tensor J = sum grad grad^T, window clipped at borders.
+ * J6 = [Jxx Jyy Jzz Jxy Jxz Jyz]. */
+void or_struct_tensor(const float* V, const int dims[3], int cx, int cy, int cz, double* J6)
+{
+    double J[6] = {0, 0, 0, 0, 0, 0};
+    for (int z = cz - 3; z <= cz + 3; ++z) {
+        if (z < 0 || z >= dims[2]) continue;
+        for (int y = cy - 3; y <= cy + 3; ++y) {
+            if (y < 0 || y >= dims[1]) continue;
+            for (int x = cx - 3; x <= cx + 3; ++x) {
+                if (x < 0 || x >= dims[0]) continue;
+                double g[3];
+                grad64(V, dims, x, y, z, g);
+                J[0] += g[0] * g[0]; J[1] += g[1] * g[1]; J[2] += g[2] * g[2];
+                J[3] += g[0] * g[1]; J[4] += g[0] * g[2]; J[5] += g[1] * g[2];
+            }
+        }
+    }
+    memcpy(J6, J, sizeof(J));
+}
+
+/* Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix.  On return
+ * evals ascending, evecs columns (evecs[r][c] = component r of vector c). */
+void or_jacobi3(const double* J6, double* evals, double* evecs9)
+{
+    double a[3][3] = {{J6[0], J6[3], J6[4]}, {J6[3], J6[1], J6[5]}, {J6[4], J6[5], J6[2]}};
+    double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        double fro = off * 2 + a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-30 * fro || off == 0.0) break;
+        static const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (int r = 0; r < 3; ++r) {
+            int p = PQ[r][0], q = PQ[r][1];
+            if (a[p][q] == 0.0) continue;
+            /* rotation that zeroes a[p][q]: tan of the angle solves
+             * t^2 + 2 theta t - 1 = 0, smaller root */
+            double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+            for (int k = 0; k < 3; ++k) {  /* A <- A G (columns p,q) */
+                double akp = a[k][p], akq = a[k][q];
+                a[k][p] = c * akp - s * akq;
+                a[k][q] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {  /* A <- G^T A (rows p,q) */
+                double apk = a[p][k], aqk = a[q][k];
+                a[p][k] = c * apk - s * aqk;
+                a[q][k] = s * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double vkp = v[k][p], vkq = v[k][q];
+                v[k][p] = c * vkp - s * vkq;
+                v[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+    /* sort ascending (stable on index for equal eigenvalues) */
+    int idx[3] = {0, 1, 2};
+    double lam[3] = {a[0][0], a[1][1], a[2][2]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (lam[idx[j]] < lam[idx[i]] || (lam[idx[j]] == lam[idx[i]] && idx[j] < idx[i])) {
+                int t = idx[i]; idx[i] = idx[j]; idx[j] = t;
+            }
+    for (int c = 0; c < 3; ++c) {
+        evals[c] = lam[idx[c]];
+        for (int r = 0; r < 3; ++r) evecs9[r * 3 + c] = v[r][idx[c]];
+    }
+}
+
+/* Quaternion (w,x,y,z), w >= 0, of a proper rotation matrix (Shepperd 1978). */
+void or_quat_from_R(const double* R9, double* q)
+{
+    double R[3][3];
+    for (int i = 0; i < 9; ++i) R[i / 3][i % 3] = R9[i];
+    double tr = R[0][0] + R[1][1] + R[2][2];
+    double w, x, y, z;
+    if (tr > 0.0) {
+        double S = sqrt(tr + 1.0) * 2.0;
+        w = 0.25 * S; x = (R[2][1] - R[1][2]) / S; y = (R[0][2] - R[2][0]) / S; z = (R[1][0] - R[0][1]) / S;
+    } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
+        double S = sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]) * 2.0;
+        w = (R[2][1] - R[1][2]) / S; x = 0.25 * S; y = (R[0][1] + R[1][0]) / S; z = (R[0][2] + R[2][0]) / S;
+    } else if (R[1][1] > R[2][2]) {
+        double S = sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]) * 2.0;
+        w = (R[0][2] - R[2][0]) / S; x = (R[0][1] + R[1][0]) / S; y = 0.25 * S; z = (R[1][2] + R[2][1]) / S;
+    } else {
+        double S = sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]) * 2.0;
+        w = (R[1][0] - R[0][1]) / S; x = (R[0][2] + R[2][0]) / S; y = (R[1][2] + R[2][1]) / S; z = 0.25 * S;
+    }
+    if (w < 0.0) { w = -w; x = -x; y = -y; z = -z; }
+    q[0] = w; q[1] = x; q[2] = y; q[3] = z;
+}
+
+/* Canonical frame from ascending eigenvectors: e1 (tangent), e2 with their
+ * largest-magnitude component made positive, e3 = e1 x e2. R9 columns. */
+static void canonical_frame(const double* ev9, double* R9)
+{
+    double e[2][3];
+    for (int c = 0; c < 2; ++c) {
+        int best = 0;
+        for (int r = 1; r < 3; ++r)
+            if (fabs(ev9[r * 3 + c]) > fabs(ev9[best * 3 + c])) best = r;
+        double sgn = ev9[best * 3 + c] < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < 3; ++r) e[c][r] = sgn * ev9[r * 3 + c];
+    }
+    double e3[3] = {e[0][1] * e[1][2] - e[0][2] * e[1][1], e[0][2] * e[1][0] - e[0][0] * e[1][2],
+                    e[0][0] * e[1][1] - e[0][1] * e[1][0]};
+    for (int r = 0; r < 3; ++r) { R9[r * 3 + 0] = e[0][r]; R9[r * 3 + 1] = e[1][r]; R9[r * 3 + 2] = e3[r]; }
+}
+
+void or_canonical_frame(const double* ev9, double* R9) { canonical_frame(ev9, R9); }
+
+/* Trilinear interpolation of V at a continuous voxel-index position,
+ * coordinates clamped to the grid. */
+double or_trilinear(const float* V, const int dims[3], double px, double py, double pz)
+{
+    double p[3] = {px, py, pz};
+    int i0[3], i1[3];
+    double f[3];
+    for (int j = 0; j < 3; ++j) {
+        double c = p[j];
+        if (c < 0.0) c = 0.0;
+        if (c > dims[j] - 1) c = dims[j] - 1;
+        double fl = floor(c);
+        i0[j] = (int)fl;
+        i1[j] = i0[j] + 1 < dims[j] ? i0[j] + 1 : i0[j];
+        f[j] = c - fl;
+    }
+    double acc = 0.0;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                double wgt = (cx ? f[0] : 1 - f[0]) * (cy ? f[1] : 1 - f[1]) * (cz ? f[2] : 1 - f[2]);
+                acc += wgt * (double)V[vidx(dims, cx ? i1[0] : i0[0], cy ? i1[1] : i0[1], cz ? i1[2] : i0[2])];
+            }
+    return acc;
+}
+
+/* Largest budget N' <= N whose detail and coverage draws both fit
+ * (Sec. V-B): Nd(N') <= n_detail_eligible and N' - Nd(N') <= n_occupied. */
+static int64_t nd_of(int64_t N, double frac) { return (int64_t)floor(frac * (double)N + 0.5); }
+
+int64_t or_feasible_max(int64_t N, double frac, int64_t n_elig, int64_t n_occ)
+{
+    int64_t lo = 0, hi = N;          /* lo feasible, find the largest */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo + 1) / 2;
+        int64_t nd = nd_of(mid, frac), nc = mid - nd;
+        if (nd <= n_elig && nc <= n_occ) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+typedef struct { double key; int64_t idx; } dkey_t;
+typedef struct { uint64_t key; int64_t idx; } ukey_t;
+
+static int cmp_dkey(const void* a, const void* b)
+{
+    const dkey_t* x = (const dkey_t*)a; const dkey_t* y = (const dkey_t*)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+static int cmp_ukey(const void* a, const void* b)
+{
+    const ukey_t* x = (const ukey_t*)a; const ukey_t* y = (const ukey_t*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+static int cmp_i64(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+static int cmp_f32(const void* a, const void* b)
+{
+    float x = *(const float*)a, y = *(const float*)b;
+    return (x > y) - (x < y);
+}
+static int cmp_f64(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Uniform double in (0,1) from two Philox words: 52 bits, (2m+1) 2^-53. */
+static double unit_open(uint32_t x0, uint32_t x1)
+{
+    uint64_t m = (((uint64_t)x0 << 32) | x1) >> 12;
+    return (double)(2 * m + 1) * 0x1p-53;
+}
+
+/* Efraimidis-Spirakis key for the detail draw at voxel v with weight g. */
+double or_detail_key(uint64_t v, uint64_t seed, float g)
+{
+    uint32_t r[4];
+    or_draw(v, 0u, seed, r);
+    double u = unit_open(r[0], r[1]);
+    return -log(u) / (double)g;
+}
+
+uint64_t or_coverage_key(uint64_t v, uint64_t seed)
+{
+    uint32_t r[4];
+    or_draw(v, 1u, seed, r);
+    return ((uint64_t)r[0] << 32) | r[1];
+}
+
+void or_jitter(uint64_t i, uint32_t group, uint64_t seed, float* u3)
+{
+    uint32_t r[4];
+    or_draw(i, 2u + group, seed, r);
+    for (int j = 0; j < 3; ++j) u3[j] = (float)(r[j] >> 8) * 0x1p-24f - 0.5f;
+}
+
+/* S1c: lower median over an evenly strided subsample (at most 4096) of the
+ * mean distance from a seed to its 3 nearest seeds of the same group.
+ * coords: voxel indices of the group's seeds, ascending. */
+double or_group_spacing(const int64_t* vox, int64_t ng, const int dims[3], int64_t n_occ, int64_t N)
+{
+    if (ng < 2) return cbrt((double)(n_occ > 0 ? n_occ : 1) / (double)(N > 0 ? N : 1));
+    int64_t nsub = ng < 4096 ? ng : 4096;
+    int knn = ng - 1 < 3 ? (int)(ng - 1) : 3;
+    double* vals = (double*)malloc(sizeof(double) * (size_t)nsub);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t j = 0; j < nsub; ++j) {
+        int64_t i = (int64_t)(((__int128)j * ng) / nsub);
+        int64_t vi = vox[i];
+        int64_t xi = vi % dims[0], yi = (vi / dims[0]) % dims[1], zi = vi / ((int64_t)dims[0] * dims[1]);
+        int64_t best[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+        for (int64_t o = 0; o < ng; ++o) {
+            if (o == i) continue;
+            int64_t vo = vox[o];
+            int64_t dx = vo % dims[0] - xi, dy = (vo / dims[0]) % dims[1] - yi,
+                    dz = vo / ((int64_t)dims[0] * dims[1]) - zi;
+            int64_t d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < best[2]) {
+                if (d2 < best[1]) {
+                    best[2] = best[1];
+                    if (d2 < best[0]) { best[1] = best[0]; best[0] = d2; }
+                    else best[1] = d2;
+                } else best[2] = d2;
+            }
+        }
+        double s = 0.0;
+        for (int t = 0; t < knn; ++t) s += sqrt((double)best[t]);
+        vals[j] = s / (double)knn;
+    }
+    qsort(vals, (size_t)nsub, sizeof(double), cmp_f64);
+    double h = vals[(nsub - 1) / 2];
+    free(vals);
+    return h;
+}
+
+typedef struct {
+    int64_t n_occupied, n_eligible, n_detail, n_coverage, feasible_max;
+    double gbar, h_detail, h_coverage;
+} or_alloc_stats;
+
+/* Full analytic allocation.  Returns 0 on success, 2 if the budget is
+ * infeasible (stats->feasible_max set), 1 on error.  prm_out: [N][12] FP64;
+ * vox_out (optional): [N] chosen voxel indices (detail first). */
+int or_allocate(const float* V, const int dims[3], int64_t N, double detail_frac, float occ_thresh,
+                double w0, uint64_t seed, double* prm_out, int64_t* vox_out, or_alloc_stats* st)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2];
+    memset(st, 0, sizeof(*st));
+    float* g = (float*)malloc(sizeof(float) * (size_t)M);
+    if (!g) return 1;
+    or_grad_mag32(V, dims, g);
+    int64_t n_occ = 0, n_elig = 0;
+    for (int64_t v = 0; v < M; ++v) {
+        if (V[v] > occ_thresh) { ++n_occ; if (g[v] > 0.0f) ++n_elig; }
+    }
+    st->n_occupied = n_occ; st->n_eligible = n_elig;
+    int64_t Nd = nd_of(N, detail_frac), Nc = N - Nd;
+    st->n_detail = Nd; st->n_coverage = Nc;
+    if (Nd > n_elig || Nc > n_occ) {
+        st->feasible_max = or_feasible_max(N, detail_frac, n_elig, n_occ);
+        free(g);
+        return 2;
+    }
+    st->feasible_max = N;
+    /* gbar: lower median of g over occupied voxels */
+    float* go = (float*)malloc(sizeof(float) * (size_t)(n_occ > 0 ? n_occ : 1));
+    int64_t t = 0;
+    for (int64_t v = 0; v < M; ++v) if (V[v] > occ_thresh) go[t++] = g[v];
+    qsort(go, (size_t)n_occ, sizeof(float), cmp_f32);
+    double gbar = n_occ > 0 ? (double)go[(n_occ - 1) / 2] : 0.0;
+    free(go);
+    st->gbar = gbar;
+    /* S1b: detail draw (weighted, distinct) and coverage draw (uniform, distinct) */
+    dkey_t* dk = (dkey_t*)malloc(sizeof(dkey_t) * (size_t)(n_elig > 0 ? n_elig : 1));
+    ukey_t* uk = (ukey_t*)malloc(sizeof(ukey_t) * (size_t)(n_occ > 0 ? n_occ : 1));
+    int64_t a1 = 0, a2 = 0;
+    for (int64_t v = 0; v < M; ++v) {
+        if (!(V[v] > occ_thresh)) continue;
+        uk[a2].key = or_coverage_key((uint64_t)v, seed); uk[a2].idx = v; ++a2;
+        if (g[v] > 0.0f) { dk[a1].key = or_detail_key((uint64_t)v, seed, g[v]); dk[a1].idx = v; ++a1; }
+    }
+    qsort(dk, (size_t)a1, sizeof(dkey_t), cmp_dkey);
+    qsort(uk, (size_t)a2, sizeof(ukey_t), cmp_ukey);
+    int64_t* vd = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Nd > 0 ? Nd : 1));
+    int64_t* vc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Nc > 0 ? Nc : 1));
+    for (int64_t i = 0; i < Nd; ++i) vd[i] = dk[i].idx;
+    for (int64_t i = 0; i < Nc; ++i) vc[i] = uk[i].idx;
+    free(dk); free(uk);
+    qsort(vd, (size_t)Nd, sizeof(int64_t), cmp_i64);
+    qsort(vc, (size_t)Nc, sizeof(int64_t), cmp_i64);
+    /* S1c: group spacing */
+    double hd = or_group_spacing(vd, Nd, dims, n_occ, N);
+    double hc = or_group_spacing(vc, Nc, dims, n_occ, N);
+    st->h_detail = hd; st->h_coverage = hc;
+    double smax_cap = (double)(dims[0] > dims[1] ? (dims[0] > dims[2] ? dims[0] : dims[2])
+                                                 : (dims[1] > dims[2] ? dims[1] : dims[2])) / 16.0;
+    double smin_cap = 0.3;
+    double wl = log(w0 / (1.0 - w0));
+    /* S1d + S1e per seed */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
+        int grp = i < Nd ? 0 : 1;
+        int64_t gi = grp == 0 ? i : i - Nd;
+        int64_t v = grp == 0 ? vd[gi] : vc[gi];
+        if (vox_out) vox_out[i] = v;
+        int cx = (int)(v % dims[0]), cy = (int)((v / dims[0]) % dims[1]),
+            cz = (int)(v / ((int64_t)dims[0] * dims[1]));
+        float u[3];
+        or_jitter((uint64_t)gi, (uint32_t)grp, seed, u);
+        double* p = prm_out + 12 * i;
+        p[0] = cx + (double)u[0]; p[1] = cy + (double)u[1]; p[2] = cz + (double)u[2];
+        double J6[6], ev[3], evec[9], R9[9], q[4];
+        or_struct_tensor(V, dims, cx, cy, cz, J6);
+        or_jacobi3(J6, ev, evec);
+        canonical_frame(evec, R9);
+        or_quat_from_R(R9, q);
+        double sg = 0.5 * (grp == 0 ? hd : hc);
+        double ratio = gbar > 0.0 ? 1.0 + (double)g[v] / gbar : 1.0;
+        if (ratio < 1.0) ratio = 1.0;
+        if (ratio > 3.0) ratio = 3.0;
+        double s[3] = {sg * ratio, sg, sg};
+        for (int j = 0; j < 3; ++j) {
+            if (s[j] > smax_cap) s[j] = smax_cap;
+            if (s[j] < smin_cap) s[j] = smin_cap;
+            p[3 + j] = log(s[j]);
+        }
+        p[6] = q[0]; p[7] = q[1]; p[8] = q[2]; p[9] = q[3];
+        p[10] = or_trilinear(V, dims, p[0], p[1], p[2]);
+        p[11] = wl;
+    }
+    free(vd); free(vc); free(g);
+    return 0;
+}

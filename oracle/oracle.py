@@ -1,0 +1,345 @@
+"""ctypes shim over the FP64 CPU oracle (gve_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  Nothing in the product
+package imports this module, and this module imports nothing from the product
+package.
+
+Every function states the paper passage it follows (arxiv 2608.14112); the C
+source holds the arithmetic.  Arrays: fields are float32 ``(nz, ny, nx)``
+(x fastest, voxel (i,j,k) centred at (i,j,k), Sec. III-B); primitive records
+are ``(N, 12)`` in the order ``mu(3), log s(3), q(w,x,y,z), a, w_logit``
+(Sec. III-C, Eq. 2; 48 bytes per primitive in float32, Sec. III-J).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "gve_oracle.c"
+_BUILD = _HERE / "_build"
+_SO = _BUILD / "libgve_oracle.so"
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+          "-fexcess-precision=standard", "-std=gnu11"]
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (no FMA contraction: float32 decisions must
+    follow the written operation order)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _SO.exists() or _SO.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _SO.with_suffix(f".{os.getpid()}.tmp.so")
+        subprocess.check_call(["gcc", *CFLAGS, "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class AllocStats(ctypes.Structure):
+    _fields_ = [("n_occupied", ctypes.c_int64), ("n_eligible", ctypes.c_int64),
+                ("n_detail", ctypes.c_int64), ("n_coverage", ctypes.c_int64),
+                ("feasible_max", ctypes.c_int64), ("gbar", ctypes.c_double),
+                ("h_detail", ctypes.c_double), ("h_coverage", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(str(build()))
+            P = ctypes.c_void_p
+            i64, i32, f32, f64, u64, u32 = (ctypes.c_int64, ctypes.c_int, ctypes.c_float,
+                                            ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32)
+            L.or_philox4x32_10.argtypes = [P, P, P]
+            L.or_pred_t.argtypes = [P, i32, i32, i32]
+            L.or_pred_t.restype = f32
+            L.or_pred_threshold.argtypes = [f32]
+            L.or_pred_threshold.restype = f32
+            L.or_eval_region.argtypes = [P, P, i64, P, P, P, f32, f64, i32, i32, P, P, P]
+            L.or_eval_region.restype = i32
+            L.or_loss_grad.argtypes = [P, P, i64, P, P, f32, f64, i32, i32, f64, P, P]
+            L.or_loss_grad.restype = f64
+            L.or_grad_subset.argtypes = [P, i64, P, P, f32, f64, i32, f64, P, i64, P]
+            L.or_grad_subset.restype = i32
+            L.or_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
+            L.or_refine.argtypes = [P, i64, P, P, f32, f64, i32, f64, i32, f64, f64, f64, f64, P]
+            L.or_refine.restype = f64
+            L.or_bin_count.argtypes = [P, i64, P, f32, i32, P]
+            L.or_bin_count.restype = i64
+            L.or_bin_emit.argtypes = [P, i64, P, f32, i32, P, P]
+            L.or_bin_emit.restype = i64
+            L.or_grad_mag32.argtypes = [P, P, P]
+            L.or_struct_tensor.argtypes = [P, P, i32, i32, i32, P]
+            L.or_jacobi3.argtypes = [P, P, P]
+            L.or_quat_from_R.argtypes = [P, P]
+            L.or_canonical_frame.argtypes = [P, P]
+            L.or_trilinear.argtypes = [P, P, f64, f64, f64]
+            L.or_trilinear.restype = f64
+            L.or_feasible_max.argtypes = [i64, f64, i64, i64]
+            L.or_feasible_max.restype = i64
+            L.or_detail_key.argtypes = [u64, u64, f32]
+            L.or_detail_key.restype = f64
+            L.or_coverage_key.argtypes = [u64, u64]
+            L.or_coverage_key.restype = u64
+            L.or_jitter.argtypes = [u64, u32, u64, P]
+            L.or_group_spacing.argtypes = [P, i64, P, i64, i64]
+            L.or_group_spacing.restype = f64
+            L.or_allocate.argtypes = [P, P, i64, f64, f32, f64, u64, P, P, ctypes.POINTER(AllocStats)]
+            L.or_allocate.restype = i32
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dims(field_or_dims):
+    if isinstance(field_or_dims, np.ndarray) and field_or_dims.ndim == 3:
+        nz, ny, nx = field_or_dims.shape
+        return np.array([nx, ny, nz], dtype=np.int32)
+    return np.asarray(field_or_dims, dtype=np.int32).reshape(3)
+
+
+def _prm64(prm) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(prm, dtype=np.float64).reshape(-1, 12))
+
+
+def _f32c(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+# --------------------------------------------------------------------------
+# Random numbers: Philox4x32-10 (Salmon et al., SC'11)
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Field (Sec. III-C, Eq. 3)
+# --------------------------------------------------------------------------
+def pred_threshold(k: float) -> float:
+    """float32 threshold T of the kept-pair test t > T."""
+    return float(lib().or_pred_threshold(float(k)))
+
+
+def pred_t(p32_record, x: int, y: int, z: int) -> float:
+    """float32 exponent t of the kept-pair test for one voxel."""
+    r = _f32c(p32_record).reshape(12)
+    return float(lib().or_pred_t(_ptr(r), int(x), int(y), int(z)))
+
+
+def eval_region(prm, dims, region=None, k=3.0, rho0=0.05, normalized=True, truncated=True,
+                pred_prm=None):
+    """Eq. 3 on a sub-box ``region = ((x0,y0,z0), (sx,sy,sz))`` (whole grid by
+    default).  Returns (num, den, vtilde) as float64 ``(sz, sy, sx)``."""
+    d = _dims(dims)
+    if region is None:
+        r0, rs = np.zeros(3, np.int32), d.copy()
+    else:
+        r0 = np.asarray(region[0], np.int32).reshape(3)
+        rs = np.asarray(region[1], np.int32).reshape(3)
+    p = _prm64(prm)
+    pp = _prm64(pred_prm) if pred_prm is not None else None
+    shape = (int(rs[2]), int(rs[1]), int(rs[0]))
+    num = np.zeros(shape, np.float64)
+    den = np.zeros(shape, np.float64)
+    vt = np.zeros(shape, np.float64)
+    rc = lib().or_eval_region(_ptr(p), _ptr(pp) if pp is not None else None, p.shape[0], _ptr(d),
+                              _ptr(r0), _ptr(rs), float(k), float(rho0), int(bool(normalized)),
+                              int(bool(truncated)), _ptr(num), _ptr(den), _ptr(vt))
+    if rc != 0:
+        raise MemoryError("oracle eval failed")
+    return num, den, vt
+
+
+def loss_grad(prm, field, k=3.0, rho0=0.05, normalized=True, truncated=True, mask_thresh=-1.0,
+              pred_prm=None, want_grad=True):
+    """Full-grid MSE (Eq. 6 value term, mean over voxels), its analytic
+    gradient w.r.t. the raw records, and the unmasked SSE.  Returns
+    (loss, grad (N,12) or None, sse)."""
+    f = _f32c(field)
+    d = _dims(f)
+    p = _prm64(prm)
+    pp = _prm64(pred_prm) if pred_prm is not None else None
+    g = np.zeros_like(p) if want_grad else None
+    sse = ctypes.c_double(0.0)
+    L = lib().or_loss_grad(_ptr(p), _ptr(pp) if pp is not None else None, p.shape[0], _ptr(f),
+                           _ptr(d), float(k), float(rho0), int(bool(normalized)),
+                           int(bool(truncated)), float(mask_thresh),
+                           _ptr(g) if g is not None else None, ctypes.byref(sse))
+    return float(L), g, float(sse.value)
+
+
+def grad_subset(prm, field, ids, k=3.0, rho0=0.05, normalized=True, mask_thresh=-1.0):
+    """Gradient of the full-grid loss for the Gaussians ``ids`` only."""
+    f = _f32c(field)
+    d = _dims(f)
+    p = _prm64(prm)
+    ids = np.ascontiguousarray(np.asarray(ids, np.int64))
+    g = np.zeros((ids.size, 12), np.float64)
+    lib().or_grad_subset(_ptr(p), p.shape[0], _ptr(f), _ptr(d), float(k), float(rho0),
+                         int(bool(normalized)), float(mask_thresh), _ptr(ids), ids.size, _ptr(g))
+    return g
+
+
+def psnr_from_sse(sse: float, M: int) -> float:
+    """PSNR = 10 log10(1/MSE) for a field normalised to [0,1] (Sec. IV-C)."""
+    return float(10.0 * np.log10(M / sse)) if sse > 0 else float("inf")
+
+
+# --------------------------------------------------------------------------
+# Optimiser (Sec. III-E: Adam)
+# --------------------------------------------------------------------------
+def adam_step(p, m, v, g, t, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15):
+    """One Adam step in place on float64 arrays (t is 1-based)."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    lib().or_adam(_ptr(p), _ptr(m), _ptr(v), _ptr(g), p.size, int(t), float(lr), float(b1),
+                  float(b2), float(eps))
+
+
+def refine(prm, field, iters, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15, k=3.0, rho0=0.05,
+           normalized=True, mask_thresh=-1.0):
+    """Fixed-budget refinement (Sec. III-E): returns (refined records (N,12)
+    float64, per-iteration losses, SSE of one extra evaluation afterwards)."""
+    f = _f32c(field)
+    d = _dims(f)
+    p = _prm64(prm).copy()
+    losses = np.zeros(max(int(iters), 1), np.float64)
+    sse = lib().or_refine(_ptr(p), p.shape[0], _ptr(f), _ptr(d), float(k), float(rho0),
+                          int(bool(normalized)), float(mask_thresh), int(iters), float(lr),
+                          float(b1), float(b2), float(eps), _ptr(losses))
+    return p, losses[:int(iters)], float(sse)
+
+
+# --------------------------------------------------------------------------
+# Brick binning (conservative cover of every kept pair)
+# --------------------------------------------------------------------------
+def bin_pairs(p32, dims, k=3.0, B=8):
+    """Per-Gaussian brick counts and the (brick key, gid) pairs in
+    Gaussian-major emission order."""
+    p = _f32c(p32).reshape(-1, 12)
+    d = _dims(dims)
+    counts = np.zeros(p.shape[0], np.uint32)
+    total = lib().or_bin_count(_ptr(p), p.shape[0], _ptr(d), float(k), int(B), _ptr(counts))
+    keys = np.zeros(max(total, 1), np.uint32)
+    gids = np.zeros(max(total, 1), np.uint32)
+    n = lib().or_bin_emit(_ptr(p), p.shape[0], _ptr(d), float(k), int(B), _ptr(keys), _ptr(gids))
+    assert n == total
+    return counts, keys[:total], gids[:total]
+
+
+def bin_sorted(p32, dims, k=3.0, B=8):
+    """Pairs stably sorted by brick key, plus per-brick [start, end)."""
+    d = _dims(dims)
+    counts, keys, gids = bin_pairs(p32, d, k, B)
+    order = np.argsort(keys, kind="stable")
+    sk, sg = keys[order], gids[order]
+    nb = int(np.prod([(int(d[j]) + B - 1) // B for j in range(3)]))
+    start = np.searchsorted(sk, np.arange(nb, dtype=np.uint32), side="left").astype(np.uint32)
+    end = np.searchsorted(sk, np.arange(nb, dtype=np.uint32), side="right").astype(np.uint32)
+    start[start == end] = 0
+    end[start == end] = 0
+    return counts, sk, sg, start, end
+
+
+# --------------------------------------------------------------------------
+# Allocation (Sec. III-E, Table I S1a..S1e, Eq. 4; Sec. V-B)
+# --------------------------------------------------------------------------
+def grad_mag32(field) -> np.ndarray:
+    f = _f32c(field)
+    g = np.zeros_like(f)
+    lib().or_grad_mag32(_ptr(f), _ptr(_dims(f)), _ptr(g))
+    return g
+
+
+def struct_tensor(field, c) -> np.ndarray:
+    """7^3 structure tensor at integer voxel c: [Jxx Jyy Jzz Jxy Jxz Jyz]."""
+    f = _f32c(field)
+    J = np.zeros(6, np.float64)
+    lib().or_struct_tensor(_ptr(f), _ptr(_dims(f)), int(c[0]), int(c[1]), int(c[2]), _ptr(J))
+    return J
+
+
+def jacobi3(J6):
+    J = np.ascontiguousarray(np.asarray(J6, np.float64).reshape(6))
+    ev = np.zeros(3, np.float64)
+    vec = np.zeros(9, np.float64)
+    lib().or_jacobi3(_ptr(J), _ptr(ev), _ptr(vec))
+    return ev, vec.reshape(3, 3)
+
+
+def canonical_frame(evecs) -> np.ndarray:
+    e = np.ascontiguousarray(np.asarray(evecs, np.float64).reshape(9))
+    R = np.zeros(9, np.float64)
+    lib().or_canonical_frame(_ptr(e), _ptr(R))
+    return R.reshape(3, 3)
+
+
+def quat_from_R(R) -> np.ndarray:
+    r = np.ascontiguousarray(np.asarray(R, np.float64).reshape(9))
+    q = np.zeros(4, np.float64)
+    lib().or_quat_from_R(_ptr(r), _ptr(q))
+    return q
+
+
+def trilinear(field, p) -> float:
+    f = _f32c(field)
+    return float(lib().or_trilinear(_ptr(f), _ptr(_dims(f)), float(p[0]), float(p[1]), float(p[2])))
+
+
+def feasible_max(N: int, detail_frac: float, n_eligible: int, n_occupied: int) -> int:
+    return int(lib().or_feasible_max(int(N), float(detail_frac), int(n_eligible), int(n_occupied)))
+
+
+def detail_key(v: int, seed: int, g: float) -> float:
+    return float(lib().or_detail_key(int(v), int(seed), float(g)))
+
+
+def coverage_key(v: int, seed: int) -> int:
+    return int(lib().or_coverage_key(int(v), int(seed)))
+
+
+def jitter(i: int, group: int, seed: int) -> np.ndarray:
+    u = np.zeros(3, np.float32)
+    lib().or_jitter(int(i), int(group), int(seed), _ptr(u))
+    return u
+
+
+def group_spacing(vox, dims, n_occupied, N) -> float:
+    v = np.ascontiguousarray(np.asarray(vox, np.int64))
+    return float(lib().or_group_spacing(_ptr(v), v.size, _ptr(_dims(dims)), int(n_occupied), int(N)))
+
+
+def allocate(field, N, detail_frac=0.55, occ_thresh=0.02, w0=0.1, seed=0):
+    """Analytic fixed-budget allocation.  Returns (records (N,12) float64,
+    chosen voxel indices (N,), stats dict, status) with status 0 = ok,
+    2 = infeasible budget (records empty, stats['feasible_max'] set)."""
+    f = _f32c(field)
+    d = _dims(f)
+    prm = np.zeros((max(int(N), 1), 12), np.float64)
+    vox = np.zeros(max(int(N), 1), np.int64)
+    st = AllocStats()
+    rc = lib().or_allocate(_ptr(f), _ptr(d), int(N), float(detail_frac), float(np.float32(occ_thresh)),
+                           float(w0), int(seed), _ptr(prm), _ptr(vox), ctypes.byref(st))
+    stats = {name: getattr(st, name) for name, _ in AllocStats._fields_}
+    if rc == 1:
+        raise MemoryError("oracle allocation failed")
+    if rc == 2:
+        return np.zeros((0, 12)), np.zeros(0, np.int64), stats, 2
+    return prm[:int(N)], vox[:int(N)], stats, 0

@@ -1,0 +1,528 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, library routines solving the same
+mathematical problem (numpy/scipy/torch autograd), brute force on tiny grids,
+exact invariants, and numbers printed in the paper (arxiv 2608.14112).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_prims(rng, n, dims, s_lo=0.8, s_hi=2.5, aniso=True):
+    """Random raw records: mu inside the grid, log-scales, random quaternion,
+    a in [0.1, 1], w_logit around logit(0.1..0.9)."""
+    p = np.zeros((n, 12))
+    p[:, 0:3] = rng.uniform(0, 1, (n, 3)) * (np.array(dims) - 1)
+    s = rng.uniform(s_lo, s_hi, (n, 3)) if aniso else np.repeat(rng.uniform(s_lo, s_hi, (n, 1)), 3, 1)
+    p[:, 3:6] = np.log(s)
+    p[:, 6:10] = rng.normal(size=(n, 4)) * rng.uniform(0.5, 2.0, (n, 1))
+    p[:, 10] = rng.uniform(0.1, 1.0, n)
+    p[:, 11] = rng.uniform(-2.0, 2.0, n)
+    return p
+
+
+def _dense_numpy(prm, dims, rho0=0.05, normalized=True):
+    """Untruncated Eq. 3 written with scipy's rotation and numpy's inverse:
+    independent of the oracle's R(q) and conic."""
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    P = np.stack([x, y, z], -1).astype(np.float64)
+    num = np.zeros((nz, ny, nx))
+    den = np.zeros((nz, ny, nx))
+    for r in prm:
+        q = r[6:10]
+        Rm = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy: (x,y,z,w)
+        S = np.diag(np.exp(2 * r[3:6]))
+        Sig = Rm @ S @ Rm.T
+        Ci = np.linalg.inv(Sig)
+        d = P - r[0:3]
+        m = np.einsum("...i,ij,...j->...", d, Ci, d)
+        G = np.exp(-0.5 * m)
+        w = 1 / (1 + np.exp(-r[11]))
+        num += w * r[10] * G
+        den += w * G
+    vt = num / np.maximum(den, rho0) if normalized else num
+    return num, den, vt, P
+
+
+# ------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# ------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+# ------------------------------------------------------------------------
+# Field, Eq. 3
+# ------------------------------------------------------------------------
+def test_dense_matches_independent_numpy():
+    rng = np.random.default_rng(11)
+    dims = (13, 11, 9)
+    prm = _rand_prims(rng, 6, dims)
+    num, den, vt = O.eval_region(prm, dims, truncated=False)
+    n2, d2, v2, _ = _dense_numpy(prm, dims)
+    np.testing.assert_allclose(num, n2, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(den, d2, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(vt, v2, rtol=1e-12, atol=1e-14)
+    _, _, vp = O.eval_region(prm, dims, truncated=False, normalized=False)
+    np.testing.assert_allclose(vp, n2, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [3.0, 5.0])
+def test_single_gaussian_closed_form(k):
+    """One Gaussian: Vt = a where wG >= rho0, a wG/rho0 where wG < rho0,
+    and 0 outside the truncation ellipsoid (Eq. 3 with N = 1)."""
+    dims = (24, 24, 24)
+    rng = np.random.default_rng(5)
+    p = _rand_prims(rng, 1, dims, s_lo=1.5, s_hi=3.0)
+    p[0, 0:3] = [11.3, 12.6, 11.9]
+    num, den, vt = O.eval_region(p, dims, k=k)
+    _, _, _, P = _dense_numpy(p, dims)
+    r = p[0]
+    Rm = Rotation.from_quat([r[7], r[8], r[9], r[6]]).as_matrix()
+    Ci = np.linalg.inv(Rm @ np.diag(np.exp(2 * r[3:6])) @ Rm.T)
+    d = P - r[0:3]
+    m = np.einsum("...i,ij,...j->...", d, Ci, d)
+    w = 1 / (1 + np.exp(-r[11]))
+    wG = w * np.exp(-0.5 * m)
+    expect = np.where(wG >= 0.05, r[10], r[10] * wG / 0.05)
+    expect = np.where(m < k * k, expect, 0.0)
+    away = np.abs(m - k * k) > 1e-4 * k * k   # the float32 decision is exact away from the surface
+    np.testing.assert_allclose(vt[away], expect[away], rtol=1e-12, atol=1e-15)
+    assert (vt[m > k * k * 1.0001] == 0).all()
+    assert (vt[m < k * k * 0.9999] != 0).all()
+    # plain (unnormalised) mode: w a G
+    _, _, vp = O.eval_region(p, dims, k=k, normalized=False)
+    np.testing.assert_allclose(vp[away], np.where(m < k * k, r[10] * wG, 0)[away], rtol=1e-12, atol=1e-15)
+
+
+def test_float32_decision_agrees_with_fp64_away_from_surface():
+    rng = np.random.default_rng(3)
+    dims = (30, 30, 30)
+    prm = _rand_prims(rng, 20, dims, s_lo=0.5, s_hi=4.0)
+    T = O.pred_threshold(3.0)
+    assert T < 0
+    for r in prm:
+        p32 = r.astype(np.float32)
+        r64 = p32.astype(np.float64)
+        Rm = Rotation.from_quat([r64[7], r64[8], r64[9], r64[6]]).as_matrix()
+        Ci = np.linalg.inv(Rm @ np.diag(np.exp(2 * r64[3:6])) @ Rm.T)
+        for _ in range(60):
+            v = rng.integers(0, 30, 3)
+            d = v - r64[0:3]
+            m = d @ Ci @ d
+            t = O.pred_t(p32, *v)
+            # t is -0.5*log2(e)*m in float32
+            assert abs(t - (-0.5 / math.log(2)) * m) <= 1e-5 * max(1.0, m)
+            if abs(m - 9.0) > 1e-4 * 9.0:
+                assert (t > T) == (m < 9.0)
+
+
+def test_truncation_error_bounded_and_k20_is_dense():
+    """|Vt_k - Vt_inf| <= (|N_o| + |Vt_k| D_o)/rho0, where N_o, D_o are the
+    omitted parts of the sums, each a priori <= sum_i w_i max(|a_i|,1) e^{-k^2/2}."""
+    rng = np.random.default_rng(7)
+    dims = (20, 18, 16)
+    prm = _rand_prims(rng, 12, dims)
+    nI, dI, vI, _ = _dense_numpy(prm, dims)
+    w = 1 / (1 + np.exp(-prm[:, 11]))
+    for k in (2.0, 3.0, 5.0):
+        nk, dk, vk = O.eval_region(prm, dims, k=k)
+        No, Do = nI - nk, dI - dk
+        assert (Do >= -1e-15).all()
+        apriori = np.sum(w * np.maximum(np.abs(prm[:, 10]), 1.0)) * math.exp(-k * k / 2)
+        assert np.abs(No).max() <= apriori * 1.0001 + 1e-15
+        assert Do.max() <= apriori * 1.0001 + 1e-15
+        bound = (np.abs(No) + np.abs(vk) * Do) / 0.05
+        assert (np.abs(vI - vk) <= bound * (1 + 1e-9) + 1e-13).all()
+    _, _, v20 = O.eval_region(prm, dims, k=20.0)
+    np.testing.assert_allclose(v20, vI, rtol=1e-12, atol=1e-14)
+
+
+def test_region_evaluation_matches_full_grid():
+    rng = np.random.default_rng(8)
+    dims = (19, 23, 17)
+    prm = _rand_prims(rng, 15, dims)
+    _, _, vt = O.eval_region(prm, dims)
+    _, _, sub = O.eval_region(prm, dims, region=((3, 5, 2), (9, 7, 11)))
+    np.testing.assert_array_equal(sub, vt[2:13, 5:12, 3:12])
+
+
+# ------------------------------------------------------------------------
+# Loss, PSNR and gradient
+# ------------------------------------------------------------------------
+def test_psnr_textbook():
+    """No Gaussians: Vt = 0, so against a constant field c MSE = c^2 and
+    PSNR = 10 log10(1/c^2) (Sec. IV-C definition with V_max = 1)."""
+    f = np.full((4, 5, 6), 0.25, np.float32)
+    L, _, sse = O.loss_grad(np.zeros((0, 12)), f, want_grad=False)
+    assert L == pytest.approx(0.0625, rel=1e-15)
+    assert O.psnr_from_sse(sse, f.size) == pytest.approx(-20 * math.log10(0.25), rel=1e-12)
+
+
+def _fd_case(seed=21):
+    rng = np.random.default_rng(seed)
+    dims = (12, 11, 10)
+    prm = _rand_prims(rng, 5, dims, s_lo=1.0, s_hi=2.2)
+    field = rng.uniform(0, 1, (10, 11, 12)).astype(np.float32)
+    return prm, field
+
+
+@pytest.mark.parametrize("normalized", [True, False])
+@pytest.mark.parametrize("mask", [-1.0, 0.3])
+def test_gradient_central_differences_frozen_membership(normalized, mask):
+    """Central differences of the FP64 loss with membership frozen at the
+    unperturbed parameters (the kept set is piecewise constant in mu, s, q);
+    a and w_logit do not move the truncation surface at all.  h = 3e-5 keeps
+    both the O(h^2) error and the summation round-off near 1e-7 (the density
+    floor max(den, rho0) is a kink, so much larger steps may straddle it)."""
+    prm, field = _fd_case()
+    L0, g, _ = O.loss_grad(prm, field, normalized=normalized, mask_thresh=mask)
+    h = 3e-5
+    for i in range(prm.shape[0]):
+        for j in range(12):
+            pp, pm = prm.copy(), prm.copy()
+            pp[i, j] += h
+            pm[i, j] -= h
+            Lp, _, _ = O.loss_grad(pp, field, normalized=normalized, mask_thresh=mask,
+                                   pred_prm=prm, want_grad=False)
+            Lm, _, _ = O.loss_grad(pm, field, normalized=normalized, mask_thresh=mask,
+                                   pred_prm=prm, want_grad=False)
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g[i, j]) <= 1e-6 * max(abs(fd), 1e-4), (i, j, fd, g[i, j])
+
+
+def test_gradient_matches_torch_autograd_dense():
+    """Untruncated loss differentiated by torch autograd (float64): an
+    independent derivation of the chain rule through Eq. 3 and Eq. 2."""
+    torch = pytest.importorskip("torch")
+    prm, field = _fd_case(seed=4)
+    _, g, _ = O.loss_grad(prm, field, truncated=False)
+    P = torch.tensor(prm, dtype=torch.float64, requires_grad=True)
+    nz, ny, nx = field.shape
+    zz, yy, xx = torch.meshgrid(torch.arange(nz), torch.arange(ny), torch.arange(nx), indexing="ij")
+    X = torch.stack([xx, yy, zz], -1).double()
+    num = torch.zeros(nz, ny, nx, dtype=torch.float64)
+    den = torch.zeros_like(num)
+    for i in range(P.shape[0]):
+        r = P[i]
+        q = r[6:10] / torch.linalg.norm(r[6:10])
+        w_, x_, y_, z_ = q
+        Rm = torch.stack([
+            torch.stack([1 - 2 * (y_ ** 2 + z_ ** 2), 2 * (x_ * y_ - w_ * z_), 2 * (x_ * z_ + w_ * y_)]),
+            torch.stack([2 * (x_ * y_ + w_ * z_), 1 - 2 * (x_ ** 2 + z_ ** 2), 2 * (y_ * z_ - w_ * x_)]),
+            torch.stack([2 * (x_ * z_ - w_ * y_), 2 * (y_ * z_ + w_ * x_), 1 - 2 * (x_ ** 2 + y_ ** 2)])])
+        Sig = Rm @ torch.diag(torch.exp(2 * r[3:6])) @ Rm.T
+        Ci = torch.linalg.inv(Sig)
+        d = X - r[0:3]
+        m = torch.einsum("...i,ij,...j->...", d, Ci, d)
+        G = torch.exp(-0.5 * m)
+        w = torch.sigmoid(r[11])
+        num = num + w * r[10] * G
+        den = den + w * G
+    vt = num / torch.clamp(den, min=0.05)
+    loss = ((vt - torch.tensor(field, dtype=torch.float64)) ** 2).mean()
+    loss.backward()
+    np.testing.assert_allclose(g, P.grad.numpy(), rtol=1e-9, atol=1e-13)
+
+
+def test_gradient_subset_matches_full():
+    prm, field = _fd_case(seed=9)
+    _, g, _ = O.loss_grad(prm, field)
+    ids = np.array([3, 0, 4])
+    gs = O.grad_subset(prm, field, ids)
+    np.testing.assert_allclose(gs, g[ids], rtol=1e-12, atol=1e-16)
+
+
+def test_adam_matches_torch_optim():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2)
+    p0 = rng.normal(size=24)
+    grads = [rng.normal(size=24) * 10 ** rng.uniform(-8, 0) for _ in range(6)]
+    p, m, v = p0.copy(), np.zeros(24), np.zeros(24)
+    for t, g in enumerate(grads, 1):
+        O.adam_step(p, m, v, g, t, lr=1e-2, eps=1e-15)
+    T = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([T], lr=1e-2, betas=(0.9, 0.999), eps=1e-15)
+    for g in grads:
+        opt.zero_grad()
+        T.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+    np.testing.assert_allclose(p, T.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_refine_decreases_loss_and_reports_final_sse():
+    rng = np.random.default_rng(12)
+    dims = (16, 16, 16)
+    prm = _rand_prims(rng, 30, dims, s_lo=1.2, s_hi=2.5)
+    field = np.asarray(O.eval_region(_rand_prims(rng, 10, dims), dims)[2], np.float32)
+    out, losses, sse = O.refine(prm, field, iters=8, lr=2e-2)
+    assert losses[-1] < losses[0]
+    L, _, sse2 = O.loss_grad(out, field, want_grad=False)
+    assert sse == pytest.approx(sse2, rel=1e-15)
+
+
+# ------------------------------------------------------------------------
+# Brick binning: every kept pair is covered
+# ------------------------------------------------------------------------
+@pytest.mark.parametrize("B", [4, 8])
+def test_binning_covers_every_kept_pair(B):
+    rng = np.random.default_rng(100 + B)
+    dims = (21, 17, 13)
+    prm = np.concatenate([_rand_prims(rng, 25, dims, s_lo=0.3, s_hi=3.0),
+                          _rand_prims(rng, 10, dims, s_lo=0.5, s_hi=1.0, aniso=False)])
+    # strongly anisotropic ones too
+    prm[:5, 3] = np.log(6.0)
+    prm[:5, 4] = np.log(0.4)
+    p32 = prm.astype(np.float32)
+    counts, keys, gids = O.bin_pairs(p32, dims, 3.0, B)
+    nbx, nby = (dims[0] + B - 1) // B, (dims[1] + B - 1) // B
+    listed = {}
+    for kk, gg in zip(keys, gids):
+        listed.setdefault(int(gg), set()).add(int(kk))
+    T = O.pred_threshold(3.0)
+    kept_bricks = 0
+    for i in range(prm.shape[0]):
+        need = set()
+        for z in range(dims[2]):
+            for y in range(dims[1]):
+                for x in range(dims[0]):
+                    if O.pred_t(p32[i], x, y, z) > T:
+                        need.add((z // B * nby + y // B) * nbx + x // B)
+        assert need <= listed.get(i, set()), i
+        kept_bricks += len(need)
+        assert counts[i] == len(listed.get(i, set()))
+    # emission order: Gaussian-major, bricks ascending within a Gaussian
+    assert (np.diff(gids.astype(np.int64)) >= 0).all()
+    for i in range(prm.shape[0]):
+        kk = keys[gids == i]
+        assert (np.diff(kk.astype(np.int64)) > 0).all()
+    # conservative but not wasteful
+    assert keys.size <= 3 * kept_bricks + 8
+
+
+def test_binning_sorted_ranges_consistent():
+    rng = np.random.default_rng(5)
+    dims = (33, 20, 9)
+    p32 = _rand_prims(rng, 40, dims).astype(np.float32)
+    counts, sk, sg, start, end = O.bin_sorted(p32, dims, 3.0, 8)
+    assert (np.diff(sk.astype(np.int64)) >= 0).all()
+    for b in range(start.size):
+        seg = sg[start[b]:end[b]]
+        assert (sk[start[b]:end[b]] == b).all()
+        assert (np.diff(seg.astype(np.int64)) > 0).all()
+    assert int((end - start).sum()) == sk.size == int(counts.sum())
+
+
+# ------------------------------------------------------------------------
+# Allocation (Sec. III-E, Table I S1a..S1e, Sec. V-B)
+# ------------------------------------------------------------------------
+def test_detail_coverage_split_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "nd_split.txt"))
+            if l.strip() and not l.startswith("#")]
+    for N, Nd, Nc in ((int(a), int(b), int(c)) for a, b, c in rows):
+        assert O.feasible_max(N, 0.55, N, N) == N
+        # the split itself: feasible with exactly Nd eligible, infeasible with Nd-1
+        assert O.feasible_max(N, 0.55, Nd, Nc) == N
+        assert O.feasible_max(N, 0.55, Nd - 1, N) < N
+        assert O.feasible_max(N, 0.55, N, Nc - 1) < N
+
+
+def test_seed_limit_matches_paper():
+    row = [l.split() for l in open(os.path.join(GOLDEN, "seed_limit.txt"))
+           if l.strip() and not l.startswith("#")][0]
+    elig, frac, approx, tol = int(row[0]), float(row[1]), int(row[2]), float(row[3])
+    fm = O.feasible_max(10_000_000, frac, elig, 10 ** 9)
+    assert abs(fm - approx) <= tol * approx
+    assert fm == 228704  # floor(0.55 N + 1/2) <= 125787 <=> N <= 228704
+
+
+def test_gradient_magnitude_ramp():
+    nz, ny, nx = 9, 10, 11
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    a, b, c = 0.0125, -0.03125, 0.0078125   # dyadic: every difference exact in float32
+    V = (a * x + b * y + c * z + 0.5).astype(np.float32)
+    g = O.grad_mag32(V)
+    np.testing.assert_allclose(g, math.sqrt(a * a + b * b + c * c), rtol=2e-6)
+
+
+def test_structure_tensor_ramp_closed_form():
+    nz, ny, nx = 16, 16, 16
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    gv = np.array([0.25, -0.5, 0.125])
+    V = (gv[0] * x + gv[1] * y + gv[2] * z).astype(np.float32)
+    outer = np.outer(gv, gv)
+    expect6 = lambda n: n * np.array([outer[0, 0], outer[1, 1], outer[2, 2], outer[0, 1], outer[0, 2], outer[1, 2]])
+    np.testing.assert_allclose(O.struct_tensor(V, (8, 7, 9)), expect6(343), rtol=1e-12)
+    # corner: window clipped to 4^3
+    np.testing.assert_allclose(O.struct_tensor(V, (0, 0, 0)), expect6(64), rtol=1e-12)
+    # ramp: the tangent (smallest eigenvalue) is orthogonal to the gradient
+    ev, vec = O.jacobi3(O.struct_tensor(V, (8, 7, 9)))
+    assert abs(vec[:, 0] @ gv) < 1e-9
+    assert abs(abs(vec[:, 2] @ gv) / np.linalg.norm(gv) - 1) < 1e-12
+
+
+def test_jacobi_matches_numpy_eigh():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        A = rng.normal(size=(3, 3))
+        S = A @ A.T + rng.uniform(0, 1) * np.eye(3)
+        ev, vec = O.jacobi3([S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[0, 2], S[1, 2]])
+        ev2, vec2 = np.linalg.eigh(S)
+        np.testing.assert_allclose(ev, ev2, rtol=1e-11, atol=1e-12)
+        for c in range(3):
+            if min(abs(ev2[c] - ev2[(c + 1) % 3]), abs(ev2[c] - ev2[(c + 2) % 3])) > 1e-6:
+                assert abs(abs(vec[:, c] @ vec2[:, c]) - 1) < 1e-9
+        np.testing.assert_allclose(vec.T @ vec, np.eye(3), atol=1e-12)
+
+
+def test_plane_and_cylinder_orientation():
+    n = 24
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    nv = np.array([1.0, 2.0, 2.0]) / 3.0
+    plane = np.tanh((nv[0] * (x - 12) + nv[1] * (y - 12) + nv[2] * (z - 12)) / 2).astype(np.float32)
+    ev, vec = O.jacobi3(O.struct_tensor(plane, (12, 12, 12)))
+    assert abs(abs(vec[:, 2] @ nv) - 1) < 1e-3       # normal = largest eigenvalue
+    assert abs(vec[:, 0] @ nv) < 1e-3                # tangent lies in the plane
+    axis = np.array([2.0, -1.0, 2.0]) / 3.0
+    P = np.stack([x - 12.0, y - 12.0, z - 12.0], -1)
+    r = np.linalg.norm(P - (P @ axis)[..., None] * axis, axis=-1)
+    cyl = np.exp(-(r / 5.0) ** 2).astype(np.float32)
+    ev, vec = O.jacobi3(O.struct_tensor(cyl, (15, 12, 12)))
+    assert abs(abs(vec[:, 0] @ axis) - 1) < 2e-2    # tangent along the axis
+
+
+def test_quaternion_from_rotation_all_branches():
+    rots = list(Rotation.random(200, random_state=1))
+    for ax in ([1, 0, 0], [0, 1, 0], [0, 0, 1]):  # near-180 degree turns exercise every branch
+        rots.append(Rotation.from_rotvec(np.array(ax) * (math.pi - 1e-3)))
+    for R in rots:
+        M = R.as_matrix()
+        q = O.quat_from_R(M)
+        assert q[0] >= 0 and abs(np.linalg.norm(q) - 1) < 1e-12
+        M2 = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        np.testing.assert_allclose(M2, M, atol=1e-12)
+
+
+def test_canonical_frame_is_proper_rotation():
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        R = O.canonical_frame(Q)
+        np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-12)
+        assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-12)
+        for c in range(2):
+            assert abs(abs(R[:, c] @ Q[:, c]) - 1) < 1e-12
+            assert R[np.argmax(np.abs(R[:, c])), c] > 0
+
+
+def test_trilinear_exact_on_linear_field():
+    nz, ny, nx = 7, 8, 9
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    V = (0.1 * x + 0.2 * y - 0.05 * z + 1).astype(np.float32).astype(np.float64)
+    Vf = V.astype(np.float32)
+    for p in [(1.25, 2.5, 3.75), (0.0, 0.0, 0.0), (7.9, 6.1, 5.5)]:
+        expect = 0.1 * p[0] + 0.2 * p[1] - 0.05 * p[2] + 1
+        assert O.trilinear(Vf, p) == pytest.approx(expect, abs=1e-6)
+    assert O.trilinear(Vf, (-3, -3, -3)) == pytest.approx(float(Vf[0, 0, 0]))
+
+
+def test_group_spacing_regular_lattice():
+    dims = (30, 30, 30)
+    vox = [((z * 30 + y) * 30 + x) for z in range(0, 30, 3) for y in range(0, 30, 3) for x in range(0, 30, 3)]
+    assert O.group_spacing(sorted(vox), dims, 27000, 1000) == 3.0
+
+
+def test_detail_draw_is_weighted_without_replacement():
+    """Efraimidis-Spirakis: with k = 1 the winner is i with probability
+    g_i / sum g (exponential race)."""
+    g = np.array([0.5, 1.0, 2.0, 4.5], np.float32)
+    wins = np.zeros(4)
+    S = 20000
+    for s in range(S):
+        keys = [O.detail_key(v, s, g[v]) for v in range(4)]
+        wins[int(np.argmin(keys))] += 1
+    p = g / g.sum()
+    chi2 = float(((wins - S * p) ** 2 / (S * p)).sum())
+    assert chi2 < 16.3   # 3 d.o.f., p = 0.001
+    wins = np.zeros(5)
+    for s in range(S):
+        wins[int(np.argmin([O.coverage_key(v, s) for v in range(5)]))] += 1
+    chi2 = float(((wins - S / 5) ** 2 / (S / 5)).sum())
+    assert chi2 < 18.5   # 4 d.o.f.
+
+
+def test_jitter_range_and_determinism():
+    for i in range(100):
+        u = O.jitter(i, i % 2, 77)
+        assert (u >= -0.5).all() and (u < 0.5).all()
+        np.testing.assert_array_equal(u, O.jitter(i, i % 2, 77))
+
+
+@pytest.fixture(scope="module")
+def blobs64():
+    from paper_2608_14112_b300 import inputs
+    return inputs.blobs(64, seed=1)
+
+
+def test_allocation_invariants(blobs64):
+    V = blobs64
+    N = 4096
+    prm, vox, st, status = O.allocate(V, N, seed=3)
+    assert status == 0 and prm.shape == (N, 12)
+    Nd = st["n_detail"]
+    assert Nd == 2253 and st["n_coverage"] == N - Nd
+    g = O.grad_mag32(V).reshape(-1)
+    Vf = V.reshape(-1)
+    dv, cv = vox[:Nd], vox[Nd:]
+    assert len(set(dv.tolist())) == Nd and len(set(cv.tolist())) == N - Nd
+    assert (Vf[dv] > np.float32(0.02)).all() and (g[dv] > 0).all()
+    assert (Vf[cv] > np.float32(0.02)).all()
+    assert st["n_occupied"] == int((Vf > np.float32(0.02)).sum())
+    c = np.stack([vox % 64, (vox // 64) % 64, vox // 4096], -1)
+    assert (np.abs(prm[:, 0:3] - c) <= 0.5).all()
+    np.testing.assert_allclose(np.linalg.norm(prm[:, 6:10], axis=1), 1.0, atol=1e-12)
+    s = np.exp(prm[:, 3:6])
+    assert (s >= 0.3 - 1e-12).all() and (s <= 4.0 + 1e-12).all()
+    ratio = s[:, 0] / s[:, 1]
+    assert (ratio >= 1 - 1e-12).all() and (ratio <= 3 + 1e-12).all()
+    np.testing.assert_allclose(prm[:, 11], math.log(0.1 / 0.9), rtol=1e-15)
+    # detail seeds are tighter than coverage seeds (Sec. III-E)
+    assert st["h_detail"] <= st["h_coverage"]
+    # the allocated model is already a meaningful reconstruction (S1x)
+    L, _, sse = O.loss_grad(prm, V, want_grad=False)
+    assert O.psnr_from_sse(sse, V.size) > 10.0
+
+
+def test_allocation_detail_prefers_high_gradient(blobs64):
+    V = blobs64
+    prm, vox, st, _ = O.allocate(V, 4096, seed=3)
+    g = O.grad_mag32(V).reshape(-1)
+    occ = V.reshape(-1) > np.float32(0.02)
+    assert g[vox[:st["n_detail"]]].mean() > 1.5 * g[occ].mean()
+
+
+def test_allocation_infeasible_reports_shortfall():
+    V = np.zeros((16, 16, 16), np.float32)
+    V[6:10, 6:10, 6:10] = 1.0      # 64 occupied voxels, all with g > 0
+    prm, vox, st, status = O.allocate(V, 1000, seed=1)
+    assert status == 2
+    fm = st["feasible_max"]
+    assert fm == O.feasible_max(1000, 0.55, st["n_eligible"], st["n_occupied"])
+    prm, vox, st2, status = O.allocate(V, fm, seed=1)
+    assert status == 0 and prm.shape[0] == fm

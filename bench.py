@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: fixed-budget refinement iterations per second at 1024^3 with
+1,400,000 Gaussians (forward + residual + PSNR + backward + Adam over every
+voxel, 3-sigma truncation), through the libgve C ABI on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one refinement iteration of the whole hot path: preparation,
+binning (count, scan, emit, radix sort, ranges), the fused brick evaluator
+(forward, residual, SSE, backward), the SSE reduction, chain rule and Adam.
+The allocation runs once before the timed region and is reported on its own.
+
+Timing: W warm-up iterations, then K iterations timed with CUDA events on the
+launching stream, barrier + synchronize on both sides, max over ranks.  The
+4.3 GB field (plus ~0.5 GB of pair lists) exceeds the 126 MB L2, so no flush
+is needed between iterations.  ``e2e`` times the user-facing encode through
+the same API with host buffers: pinned host field -> device, allocation,
+``--e2e-iters`` refinement iterations, parameters and PSNR back to the host.
+
+The reference arm (``--impl reference``) times the FP64 CPU oracle on a
+bounded sample of the same workload (a 192^3 sub-volume of the same field
+with the budget scaled by voxel count) and scales by the voxel ratio.
+Multi-GPU runs are independent replicas (the path does not shard here).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd refine iters/s at 1024^3, 1.4M Gaussians; time-to-PSNR vs plain"
+# per kept (voxel, Gaussian) pair: 15 FP32 ops in the forward (3 differences,
+# 9 for the quadratic form, 1 compare, 2 accumulations) and 30 in the backward
+# (recomputation plus the 11 accumulated sums); 2 SFU exponentials
+OPS_PER_PAIR = 45.0
+SMS = 148
+FP32_LANES = 128
+SM_MAX_MHZ = 2032.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["headline", "small", "autograd"], default="headline")
+    ap.add_argument("--e2e-iters", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--sample", type=int, default=192, help="edge of the CPU sample sub-volume")
+    ap.add_argument("--sample-iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=4)
+    return ap.parse_args()
+
+
+def workload(name):
+    if name == "headline":
+        return dict(name="fbm_fronts_1024^3_N1.4M", n=1024, budget=1_400_000, kind="fbm_fronts", seed=4, lr=1e-2)
+    if name == "autograd":
+        return dict(name="grf_256^3_N65536", n=256, budget=65_536, kind="grf", seed=2, lr=1e-2)
+    return dict(name="blobs_64^3_N4096", n=64, budget=4096, kind="blobs", seed=1, lr=1e-2)
+
+
+def make_field(w, device):
+    import torch
+    from paper_2608_14112_b300 import inputs
+    if w["kind"] == "fbm_fronts":
+        return inputs.fbm_fronts(w["n"], seed=w["seed"], device=device)
+    if w["kind"] == "grf":
+        return torch.from_numpy(inputs.grf(w["n"], seed=w["seed"])).to(device)
+    return torch.from_numpy(inputs.blobs(w["n"], seed=w["seed"])).to(device)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_sample(w, args, seed):
+    """FP64 oracle on a bounded sample: a sub-volume of the same field with
+    the budget scaled by its voxel share; returns seconds per iteration and
+    the sample description."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2608_14112_b300 import inputs
+    s = min(args.sample, w["n"])
+    c0 = (w["n"] - s) // 2
+    if w["kind"] == "fbm_fronts":
+        V = inputs.fbm_fronts(w["n"], seed=w["seed"], as_numpy=True, region=((c0,) * 3, (s,) * 3))
+    elif w["kind"] == "grf":
+        V = inputs.grf(s, seed=w["seed"])
+    else:
+        V = inputs.blobs(s, seed=w["seed"])
+    frac = (s / w["n"]) ** 3
+    N = max(1, int(round(w["budget"] * frac)))
+    prm, _, _, status = O.allocate(V, N, seed=seed)
+    if status != 0:
+        raise RuntimeError("oracle sample allocation infeasible")
+    m = np.zeros_like(prm)
+    v = np.zeros_like(prm)
+    t0 = time.perf_counter()
+    for t in range(args.sample_iters):
+        _, g, _ = O.loss_grad(prm, V)
+        O.adam_step(prm, m, v, g, t + 1, lr=w["lr"], eps=1e-15)
+    dt = (time.perf_counter() - t0) / args.sample_iters
+    desc = (f"{s}^3 centre sub-volume of the same field, {N} Gaussians (budget x voxel share), "
+            f"{args.sample_iters} oracle iterations; scaled by voxel ratio {frac:.3e}")
+    return dt, frac, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; each step below is a full sample
+    times = []
+    desc = ""
+    frac = 1.0
+    for _ in range(max(1, args.steps if args.steps <= 3 else 3)):
+        dt, frac, desc = cpu_sample(w, args, args.seed)
+        times.append(dt)
+    sec_per_iter_full = statistics.median(times) / frac
+    value = 1.0 / sec_per_iter_full
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sec_per_iter_full * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": w["name"], "trunc_k": 3.0, "brick": None, "l2": "CPU run"},
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2608_14112_b300 import build as gbuild
+    from paper_2608_14112_b300 import gve
+
+    gbuild.build()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    shape = (w["n"],) * 3
+    stream = torch.cuda.current_stream(dev)
+
+    V = make_field(w, dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prims, info = gve.gve_allocate(V, w["budget"], seed=args.seed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    alloc_ms = e0.elapsed_time(e1)
+    prims0 = prims.clone()
+    state = torch.zeros((2, w["budget"], 12), dtype=torch.float32, device=dev)
+    init_psnr = None
+    if args.warmup > 0:
+        st = gve.gve_refine(prims, V, iters=args.warmup, lr=w["lr"], adam_state=state)
+        init_psnr = st["psnr_final"]
+    kept0, cand0 = gve.gve_count_pairs(prims, shape)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st = gve.gve_refine(prims, V, iters=args.steps, lr=w["lr"], adam_state=state, step0=args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kept1, cand1 = gve.gve_count_pairs(prims, shape)
+    value = ws * args.steps / (ms / 1e3)
+
+    # dominant kernel: the fused brick evaluator (forward + backward)
+    brick_ms = st["ms_brick"] / max(args.steps, 1)
+    kept = 0.5 * (kept0 + kept1)
+    cand = 0.5 * (cand0 + cand1)
+    achieved = OPS_PER_PAIR * kept / (brick_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_brick<loss> (fused forward+backward)", "brick_ms": brick_ms,
+                "kept_pairs": kept, "candidate_pairs": cand,
+                "pairs_per_s": kept / (brick_ms / 1e3),
+                "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (FMA counted once)"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0 and args.e2e_iters > 0:
+        Vh = V.cpu().pin_memory()
+        ph = torch.empty_like(prims0, device="cpu").pin_memory()
+        Vd = torch.empty_like(V)
+        pd = torch.empty_like(prims0)
+        st_e = torch.zeros_like(state)
+        times = []
+        psnr_e2e = None
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            Vd.copy_(Vh, non_blocking=True)
+            gve.gve_allocate(Vd, w["budget"], seed=args.seed, out=pd)
+            st_e.zero_()
+            s2 = gve.gve_refine(pd, Vd, iters=args.e2e_iters, lr=w["lr"], adam_state=st_e)
+            ph.copy_(pd, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            psnr_e2e = s2["psnr_final"]
+        sec = statistics.median(times)
+        e2e = {"value": args.e2e_iters / sec, "unit": "iters/s",
+               "h2d_bytes_per_step": int(V.numel() * 4), "d2h_bytes_per_step": int(prims0.numel() * 4 + 8),
+               "encode_s": sec, "iters": args.e2e_iters, "psnr_db": psnr_e2e,
+               "includes": "H2D field, allocation, refinement, D2H parameters and PSNR"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        dt, frac, desc = cpu_sample(w, args, args.seed)
+        cpu = {"value": frac / dt, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": w["name"], "voxels": int(np.prod(shape)), "gaussians": w["budget"],
+                          "trunc_k": 3.0, "brick": 8, "lr": w["lr"], "parallelism": "replicas" if ws > 1 else "1 GPU",
+                          "l2": "inputs larger than L2 (4.3 GB field) at the headline size; no flush"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": int(st["launches"]),
+               "alloc_ms": alloc_ms, "alloc": info, "psnr_after_warmup": init_psnr,
+               "psnr_after_steps": st["psnr_final"], "stage_ms_per_iter": {
+                   "bin": st["ms_bin"] / max(args.steps, 1), "brick": brick_ms,
+                   "rest": ms / args.steps - st["ms_bin"] / max(args.steps, 1) - brick_ms}}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

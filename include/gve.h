@@ -1,0 +1,220 @@
+/*
+ * gve.h -- C ABI of libgve: fixed-budget Gaussian volume encoding on one
+ * B300 GPU (sm_103a), after arxiv 2608.14112 ("Fixed-Budget Gaussian Volume
+ * Encoding with Structure-Aware Allocation").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.   Arguments named *_dev are device pointers (cudaMalloc, torch,
+ *             or any allocator of the calling process on the context's
+ *             device); every other pointer is a host pointer.  The caller
+ *             owns every buffer it passes.  The context owns its scratch
+ *             (pair lists, sort buffers, partial sums), grown on demand.
+ * Streams.    `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *             default stream).  Calls are stream-ordered and asynchronous
+ *             unless they return a host value (stats, feasible_max, pair
+ *             counts), in which case they synchronise `stream` first.
+ * Field.      float32 [nz][ny][nx], x fastest; voxel (i,j,k) has its centre
+ *             at the voxel-index position (i,j,k) (Sec. III-B).  Values are
+ *             expected normalised to [0,1] (Sec. III-B).
+ * Primitive.  12 float32 per Gaussian, 48 bytes (Sec. III-J, Eq. 7):
+ *             [mu_x mu_y mu_z, log s_0 log s_1 log s_2, q_w q_x q_y q_z,
+ *              a, w_logit] -- the unconstrained parameters of Eq. 2
+ *             (log-scales, quaternion normalised in every evaluation,
+ *             w = sigmoid(w_logit)); 16-byte aligned.
+ * Errors.     Every entry point returns a gve_status; nothing aborts or
+ *             throws across the ABI.  gve_last_error() gives a message.
+ *             Invalid arguments are rejected before any launch.
+ * Threads.    A context may be used by one host thread at a time.
+ */
+#ifndef GVE_H
+#define GVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GVE_API __attribute__((visibility("default")))
+#else
+#define GVE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GVE_OK = 0,
+    GVE_E_INVALID = 1,    /* bad argument (null pointer, size, option)            */
+    GVE_E_BUDGET = 2,     /* infeasible budget; *feasible_max holds the largest
+                             feasible one (Sec. V-B)                               */
+    GVE_E_NOMEM = 3,      /* device scratch could not be allocated                 */
+    GVE_E_CUDA = 4,       /* a CUDA runtime call failed                            */
+    GVE_E_TIMEOUT = 5,    /* a bounded device-side wait gave up                    */
+    GVE_E_CAPACITY = 6,   /* pair buffer overflow that survived the internal retry */
+    GVE_E_INTERNAL = 7    /* device-side consistency check failed                  */
+} gve_status;
+
+typedef struct { int32_t nx, ny, nz; } gve_dims;
+
+/* Field evaluation options (Sec. III-C, Eq. 3).
+ * trunc_k    truncation radius in standard deviations: a pair is kept when its
+ *            squared Mahalanobis distance is below trunc_k^2 (paper: 5).
+ *            The keep decision is taken in float32 by a fixed chain of fused
+ *            multiply-adds on float32 coefficients of -0.5*log2(e)*Sigma^-1.
+ * rho0       density floor of Eq. 3 (paper: 0.05).
+ * normalized 1 = Eq. 3 (sum w a G / max(sum w G, rho0)); 0 = plain sum w a G.
+ * brick      brick edge B in voxels for binning: 4, 8 or 16.               */
+typedef struct {
+    float trunc_k;
+    float rho0;
+    int32_t normalized;
+    int32_t brick;
+} gve_eval_opts;
+
+/* Allocation options (Sec. III-E, Table III).
+ * detail_frac  share of the budget drawn in proportion to |grad V| (0.55).
+ * occ_thresh   occupancy threshold: voxels with V > occ_thresh (0.02).
+ * w0           initial weight w = sigmoid(w_logit) of every Gaussian (0.1).
+ * seed         seed of the Philox4x32-10 streams of the draws and jitter.   */
+typedef struct {
+    double detail_frac;
+    double w0;
+    float occ_thresh;
+    int32_t reserved;     /* set to 0 */
+    uint64_t seed;
+} gve_alloc_opts;
+
+/* Refinement schedule (Sec. III-E).  One iteration = evaluate every voxel,
+ * mean squared error, analytic gradient, one Adam step on all 12N values.
+ * mask_thresh  < 0: plain MSE over all voxels; >= 0: only voxels with
+ *              V > mask_thresh contribute to the loss (Eq. 6 mask).
+ * step0        Adam step counter before the first iteration (0 = fresh).  */
+typedef struct {
+    int32_t iters;
+    float lr, beta1, beta2, eps;
+    float mask_thresh;
+    int32_t step0;
+    gve_eval_opts eval;
+} gve_schedule;
+
+/* Host-side summary of a refinement. */
+typedef struct {
+    double loss_first;     /* loss at the starting parameters                 */
+    double loss_last;      /* loss of the last iteration (before its update)  */
+    double sse_final;      /* unmasked sum of squared errors after the last
+                              update (one extra evaluation)                    */
+    double psnr_final;     /* 10 log10(M / sse_final)  (Sec. IV-C)            */
+    int64_t brick_pairs;   /* (brick, Gaussian) pairs of the final evaluation */
+    int64_t launches;      /* kernels launched by the call                    */
+    int32_t iters_done;
+    int32_t retries;       /* pair-capacity regrowths during the call         */
+    float ms_total;        /* device time of the call (CUDA events)           */
+    float ms_brick;        /* device time of the brick evaluator, summed over
+                              the iterations (events on the call's stream)     */
+    float ms_bin;          /* device time of preparation and binning, summed  */
+    float reserved;
+} gve_stats;
+
+/* Summary of an allocation. */
+typedef struct {
+    int64_t n_occupied, n_eligible, n_detail, n_coverage;
+    double gbar;           /* median |grad V| over occupied voxels            */
+    double h_detail, h_coverage;   /* group seed spacings (Sec. III-E)        */
+} gve_alloc_info;
+
+typedef struct gve_ctx gve_ctx;
+
+/* Context on CUDA device `device`.  Creates no stream; allocates scratch
+ * lazily.  *out is NULL on failure. */
+GVE_API gve_status gve_ctx_create(gve_ctx** out, int device);
+/* Frees the context's scratch (synchronises the device first). NULL is ok. */
+GVE_API void gve_ctx_destroy(gve_ctx* ctx);
+/* Static description of a status code. */
+GVE_API const char* gve_status_str(gve_status s);
+/* Message of the last failing call on ctx (never NULL). */
+GVE_API const char* gve_last_error(const gve_ctx* ctx);
+
+/* Analytic fixed-budget allocation (Sec. III-E, Table I stages S1a-S1e,
+ * Eq. 4).  Draws Nd = floor(detail_frac*budget + 1/2) distinct occupied voxels
+ * with |grad V| > 0 with probability proportional to |grad V| (Efraimidis-
+ * Spirakis keys), and budget - Nd distinct occupied voxels uniformly; jitters
+ * each centre in [-1/2,1/2)^3; orients and shapes each Gaussian from the 7^3
+ * structure tensor at its voxel; a = trilinear V(mu); w = w0.
+ *   field_dev    [nz][ny][nx] float32 (read only).
+ *   prims_dev    [budget][12] float32 output, detail seeds first.
+ *   feasible_max host, optional: on GVE_E_BUDGET the largest feasible
+ *                budget (Sec. V-B); on success the budget itself.
+ *   info         host, optional summary.
+ * Synchronises `stream` (the feasibility check reads two counts).
+ * Returns GVE_E_BUDGET without writing prims_dev when the field cannot
+ * support the budget. */
+GVE_API gve_status gve_allocate(gve_ctx* ctx, const float* field_dev, gve_dims dims, int64_t budget,
+                        const gve_alloc_opts* opts, float* prims_dev, int64_t* feasible_max,
+                        gve_alloc_info* info, void* stream);
+
+/* Field of Eq. 3 at every voxel centre.
+ *   prims_dev     [n][12] float32.
+ *   field_out_dev [nz][ny][nx] float32 output. */
+GVE_API gve_status gve_evaluate(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                        const gve_eval_opts* opts, float* field_out_dev, void* stream);
+
+/* Loss and gradient at the current parameters, no update (Sec. III-E, V-D).
+ *   field_dev       target V, [nz][ny][nx].
+ *   grad_prims_dev  [n][12] float32 output: dL/d(raw record), L = masked
+ *                   sum of squared errors / (nx ny nz).
+ *   sse_dev         [2] double output: {masked SSE, unmasked SSE}; may be
+ *                   NULL. */
+GVE_API gve_status gve_loss_grad(gve_ctx* ctx, const float* prims_dev, int64_t n, const float* field_dev,
+                         gve_dims dims, const gve_eval_opts* opts, float mask_thresh,
+                         float* grad_prims_dev, double* sse_dev, void* stream);
+
+/* Backward of gve_evaluate for an arbitrary upstream gradient dL/dVtilde
+ * (the autograd form): recomputes the field per brick, nothing is saved
+ * between the calls.
+ *   grad_field_dev  [nz][ny][nx] float32 upstream gradient.
+ *   grad_prims_dev  [n][12] float32 output. */
+GVE_API gve_status gve_backward(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                        const gve_eval_opts* opts, const float* grad_field_dev,
+                        float* grad_prims_dev, void* stream);
+
+/* Fixed-budget refinement (Sec. III-E): sched->iters iterations of
+ * evaluate -> MSE -> gradient -> Adam on all primitives; no densification,
+ * pruning or count change.
+ *   prims_dev       [n][12] float32, updated in place.
+ *   field_dev       target V.
+ *   adam_state_dev  [2][n][12] float32 first and second moments, updated in
+ *                   place (zero them for a fresh run); NULL = the context
+ *                   keeps zero-initialised moments for this call only.
+ *   loss_trace_dev  [iters] double output of per-iteration losses, or NULL.
+ *   stats           host, optional; filling it synchronises `stream`.
+ * Pair capacity overflow is detected on the device; the affected iterations
+ * leave the parameters untouched and are replayed after the scratch grows. */
+GVE_API gve_status gve_refine(gve_ctx* ctx, float* prims_dev, int64_t n, const float* field_dev,
+                      gve_dims dims, const gve_schedule* sched, float* adam_state_dev,
+                      double* loss_trace_dev, gve_stats* stats, void* stream);
+
+/* Brick binning introspection: the (brick, Gaussian) pairs that evaluation
+ * uses, sorted by brick key (z-major brick index) and then by Gaussian index,
+ * and per-brick [start, end) ranges.
+ *   counts_dev   [n] uint32 output: pairs per Gaussian.
+ *   keys_dev, gids_dev  [cap] uint32 outputs.
+ *   ranges_dev   [2][nbricks] uint32 output (starts, then ends; 0,0 = empty).
+ *   n_pairs      host output: number of pairs (synchronises).  If it exceeds
+ *                cap, nothing is written and GVE_E_CAPACITY is returned. */
+GVE_API gve_status gve_bin(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                   const gve_eval_opts* opts, uint32_t* counts_dev, uint32_t* keys_dev,
+                   uint32_t* gids_dev, int64_t cap, uint32_t* ranges_dev, int64_t* n_pairs,
+                   void* stream);
+
+/* Number of kept (voxel, Gaussian) pairs of the truncated field -- the
+ * algorithmic work of one evaluation -- and the candidate pairs the brick
+ * evaluator visits.  Host outputs; synchronises. */
+GVE_API gve_status gve_count_pairs(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                           const gve_eval_opts* opts, int64_t* kept_pairs,
+                           int64_t* candidate_pairs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GVE_H */

@@ -412,6 +412,41 @@ static void chain_rule(const act_t* A, const double* raw, double Ag, double Bg, 
     (void)raw;
 }
 
+/* Per-Gaussian sums over its kept voxels given dL/dnum (gn) and dL/dden (gd)
+ * per voxel, then the chain rule to the raw record. */
+static void accumulate_grads(const double* prm, const double* pred_prm, int64_t n, const int dims[3], float k,
+                             int truncated, const double* gn, const double* gd, double* grad)
+{
+    gctx_t* G = prepare(prm, pred_prm, n, (double)k, truncated, dims);
+    float T = pred_threshold(k);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double* out = grad + 12 * i;
+        for (int j = 0; j < 12; ++j) out[j] = 0.0;
+        const gctx_t* g = &G[i];
+        if (!g->has_box || !g->A.valid) continue;
+        double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
+        for (int z = g->lo[2]; z <= g->hi[2]; ++z)
+            for (int y = g->lo[1]; y <= g->hi[1]; ++y)
+                for (int x = g->lo[0]; x <= g->hi[0]; ++x) {
+                    if (!kept(g, T, truncated, x, y, z)) continue;
+                    int64_t v = ((int64_t)z * dims[1] + y) * dims[0] + x;
+                    double d[3] = {x - g->A.mu[0], y - g->A.mu[1], z - g->A.mu[2]};
+                    double Gv = exp(-0.5 * maha2(&g->A, x, y, z));
+                    Ag += Gv * gn[v];
+                    Bg += Gv * gd[v];
+                    double c = g->A.w * (g->A.a * gn[v] + gd[v]);   /* dL/dG */
+                    double h = -0.5 * c * Gv;                        /* dL/dm */
+                    for (int a2 = 0; a2 < 3; ++a2) {
+                        S1[a2] += h * d[a2];
+                        for (int b = 0; b < 3; ++b) S2[a2][b] += h * d[a2] * d[b];
+                    }
+                }
+        chain_rule(&g->A, prm + 12 * i, Ag, Bg, S1, S2, out);
+    }
+    free(G);
+}
+
 double or_loss_grad(const double* prm, const double* pred_prm, int64_t n, const float* field,
                     const int dims[3], float k, double rho0, int normalized, int truncated,
                     double mask_thresh, double* grad, double* sse_out)
@@ -442,38 +477,55 @@ double or_loss_grad(const double* prm, const double* pred_prm, int64_t n, const 
     }
     loss /= (double)M;
     if (sse_out) *sse_out = sse;
-    if (grad) {
-        gctx_t* G = prepare(prm, pred_prm, n, (double)k, truncated, dims);
-        float T = pred_threshold(k);
-#pragma omp parallel for schedule(dynamic, 16)
-        for (int64_t i = 0; i < n; ++i) {
-            double* out = grad + 12 * i;
-            for (int j = 0; j < 12; ++j) out[j] = 0.0;
-            const gctx_t* g = &G[i];
-            if (!g->has_box || !g->A.valid) continue;
-            double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
-            for (int z = g->lo[2]; z <= g->hi[2]; ++z)
-                for (int y = g->lo[1]; y <= g->hi[1]; ++y)
-                    for (int x = g->lo[0]; x <= g->hi[0]; ++x) {
-                        if (!kept(g, T, truncated, x, y, z)) continue;
-                        int64_t v = ((int64_t)z * dims[1] + y) * dims[0] + x;
-                        double d[3] = {x - g->A.mu[0], y - g->A.mu[1], z - g->A.mu[2]};
-                        double Gv = exp(-0.5 * maha2(&g->A, x, y, z));
-                        Ag += Gv * gn[v];
-                        Bg += Gv * gd[v];
-                        double c = g->A.w * (g->A.a * gn[v] + gd[v]);   /* dL/dG */
-                        double h = -0.5 * c * Gv;                        /* dL/dm */
-                        for (int a2 = 0; a2 < 3; ++a2) {
-                            S1[a2] += h * d[a2];
-                            for (int b = 0; b < 3; ++b) S2[a2][b] += h * d[a2] * d[b];
-                        }
-                    }
-            chain_rule(&g->A, prm + 12 * i, Ag, Bg, S1, S2, out);
-        }
-        free(G);
-    }
+    if (grad) accumulate_grads(prm, pred_prm, n, dims, k, truncated, gn, gd, grad);
     free(num); free(den); free(vt); free(gn); free(gd);
     return loss;
+}
+
+/* Gradient for an arbitrary upstream dL/dVtilde per voxel (the backward of
+ * the field evaluation alone). */
+int or_backward(const double* prm, int64_t n, const double* upstream, const int dims[3], float k, double rho0,
+                int normalized, double* grad)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2];
+    int r0[3] = {0, 0, 0};
+    double* num = (double*)malloc(sizeof(double) * (size_t)M);
+    double* den = (double*)malloc(sizeof(double) * (size_t)M);
+    double* vt = (double*)malloc(sizeof(double) * (size_t)M);
+    double* gn = (double*)malloc(sizeof(double) * (size_t)M);
+    double* gd = (double*)malloc(sizeof(double) * (size_t)M);
+    if (!num || !den || !vt || !gn || !gd) return 1;
+    or_eval_region(prm, NULL, n, dims, r0, dims, k, rho0, normalized, 1, num, den, vt);
+    for (int64_t v = 0; v < M; ++v) {
+        double up = upstream[v];
+        if (!normalized) { gn[v] = up; gd[v] = 0.0; }
+        else if (den[v] >= rho0) { gn[v] = up / den[v]; gd[v] = -vt[v] * gn[v]; }
+        else { gn[v] = up / rho0; gd[v] = 0.0; }
+    }
+    accumulate_grads(prm, NULL, n, dims, k, 1, gn, gd, grad);
+    free(num); free(den); free(vt); free(gn); free(gd);
+    return 0;
+}
+
+/* Number of kept (voxel, Gaussian) pairs: the algorithmic work of one
+ * truncated evaluation. */
+int64_t or_count_kept(const float* p32, int64_t n, const int dims[3], float k)
+{
+    float T = pred_threshold(k);
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t i = 0; i < n; ++i) {
+        double p[12];
+        for (int j = 0; j < 12; ++j) p[j] = (double)p32[12 * i + j];
+        gctx_t g;
+        activate(p, &g.A);
+        pred_coeffs(p32 + 12 * i, &g.P);
+        if (!g.A.valid || !g.P.valid || !enum_box(&g.A, k, 1, dims, g.lo, g.hi)) continue;
+        for (int z = g.lo[2]; z <= g.hi[2]; ++z)
+            for (int y = g.lo[1]; y <= g.hi[1]; ++y)
+                for (int x = g.lo[0]; x <= g.hi[0]; ++x) total += pred_t_of(&g.P, x, y, z) > T;
+    }
+    return total;
 }
 
 /* Gradient for a subset of Gaussians only; the field values it needs are

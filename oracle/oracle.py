@@ -69,6 +69,10 @@ def lib():
             L.or_loss_grad.restype = f64
             L.or_grad_subset.argtypes = [P, i64, P, P, f32, f64, i32, f64, P, i64, P]
             L.or_grad_subset.restype = i32
+            L.or_backward.argtypes = [P, i64, P, P, f32, f64, i32, P]
+            L.or_backward.restype = i32
+            L.or_count_kept.argtypes = [P, i64, P, f32]
+            L.or_count_kept.restype = i64
             L.or_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
             L.or_refine.argtypes = [P, i64, P, P, f32, f64, i32, f64, i32, f64, f64, f64, f64, P]
             L.or_refine.restype = f64
@@ -194,6 +198,24 @@ def grad_subset(prm, field, ids, k=3.0, rho0=0.05, normalized=True, mask_thresh=
     lib().or_grad_subset(_ptr(p), p.shape[0], _ptr(f), _ptr(d), float(k), float(rho0),
                          int(bool(normalized)), float(mask_thresh), _ptr(ids), ids.size, _ptr(g))
     return g
+
+
+def backward(prm, upstream, k=3.0, rho0=0.05, normalized=True):
+    """Gradient w.r.t. the raw records for an arbitrary upstream dL/dVtilde
+    (float64 array shaped like the field)."""
+    u = np.ascontiguousarray(np.asarray(upstream, np.float64))
+    nz, ny, nx = u.shape
+    d = np.array([nx, ny, nz], np.int32)
+    p = _prm64(prm)
+    g = np.zeros_like(p)
+    lib().or_backward(_ptr(p), p.shape[0], _ptr(u), _ptr(d), float(k), float(rho0), int(bool(normalized)), _ptr(g))
+    return g
+
+
+def count_kept(p32, dims, k=3.0) -> int:
+    """Number of kept (voxel, Gaussian) pairs of one truncated evaluation."""
+    p = _f32c(p32).reshape(-1, 12)
+    return int(lib().or_count_kept(_ptr(p), p.shape[0], _ptr(_dims(dims)), float(k)))
 
 
 def psnr_from_sse(sse: float, M: int) -> float:

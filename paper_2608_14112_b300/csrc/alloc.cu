@@ -1,0 +1,635 @@
+// alloc.cu -- analytic fixed-budget allocation on the device (Sec. III-E,
+// Table I stages S1a..S1e, Eq. 4).
+//
+//   S1a  k_grad_occ     float32 |grad V| (central differences, one-sided at
+//                       the borders), occupancy and eligibility counts.
+//        gbar           lower median of |grad V| over occupied voxels: radix
+//                       select on the float bits (exact).
+//   S1b  draws          detail: Efraimidis-Spirakis keys -ln(u)/g, u from
+//                       Philox4x32-10; coverage: raw 64-bit Philox words.  The
+//                       N smallest (key, voxel) pairs are found by a radix
+//                       select of the N-th key plus an order-preserving
+//                       compaction, which also yields the seeds in voxel order.
+//        jitter         u = (x >> 8) 2^-24 - 1/2 per axis (Eq. 4).
+//   S1c  k_spacing      mean distance to the 3 nearest seeds of the same
+//                       group for an evenly strided subsample of <= 4096
+//                       seeds (brute force); lower median on the host.
+//   S1d  k_assemble     7^3 structure tensor (FP64), cyclic Jacobi (FP64),
+//   S1e                 canonical frame, quaternion (Shepperd), scales
+//                       elongated along the tangent and clamped, a = trilinear
+//                       V(mu), w_logit = logit(w0).
+//
+// This file is compiled without FMA contraction: its FP64 arithmetic follows
+// the written operation order, like the CPU reference of the same steps.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "gve_int.cuh"
+
+namespace gve {
+
+void launch_exscan_u32(const uint32_t* in, long long n, unsigned long long* out, void* scanp, cudaStream_t s);
+
+namespace {
+
+// ---------------- Philox4x32-10 (Salmon et al., SC'11) ----------------
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+constexpr uint32_t kCtrTag = 0x47564531u;  // 'GVE1'
+
+__device__ __forceinline__ void draw(unsigned long long index, uint32_t stream, unsigned long long seed, uint32_t out[4])
+{
+    out[0] = (uint32_t)index; out[1] = (uint32_t)(index >> 32); out[2] = stream; out[3] = kCtrTag;
+    philox(out, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ long long vid(int nx, int ny, int x, int y, int z)
+{
+    return ((long long)z * ny + y) * nx + x;
+}
+
+// float32 derivative along one axis, the same operations as the stencil spec
+__device__ __forceinline__ float dcomp32(const float* V, int nx, int ny, int nz, int x, int y, int z, int axis)
+{
+    int c[3] = {x, y, z};
+    int dims[3] = {nx, ny, nz};
+    int n = dims[axis];
+    if (n < 2) return 0.0f;
+    int lo = c[axis] - 1, hi = c[axis] + 1;
+    float scale = 0.5f;
+    if (lo < 0) { lo = c[axis]; scale = 1.0f; }
+    if (hi > n - 1) { hi = c[axis]; scale = 1.0f; }
+    int a[3] = {x, y, z}, b[3] = {x, y, z};
+    a[axis] = hi; b[axis] = lo;
+    float diff = V[vid(nx, ny, a[0], a[1], a[2])] - V[vid(nx, ny, b[0], b[1], b[2])];
+    return scale * diff;
+}
+
+__global__ void __launch_bounds__(256) k_grad_occ(const float* __restrict__ V, int nx, int ny, int nz, float thr,
+                                                  float* __restrict__ g, unsigned long long* cnt)
+{
+    long long M = (long long)nx * ny * nz;
+    unsigned occ = 0, elig = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        float gx = dcomp32(V, nx, ny, nz, x, y, z, 0);
+        float gy = dcomp32(V, nx, ny, nz, x, y, z, 1);
+        float gz = dcomp32(V, nx, ny, nz, x, y, z, 2);
+        float sx = gx * gx, sy = gy * gy, sz = gz * gz;
+        float sq = sx + sy;
+        sq = sq + sz;
+        float gm = sqrtf(sq);
+        g[v] = gm;
+        if (V[v] > thr) { ++occ; if (gm > 0.0f) ++elig; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        occ += __shfl_xor_sync(0xffffffffu, occ, o);
+        elig += __shfl_xor_sync(0xffffffffu, elig, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&cnt[0], (unsigned long long)occ);
+        atomicAdd(&cnt[1], (unsigned long long)elig);
+    }
+}
+
+// keys: detail (mode 0), coverage (mode 1), gbar (mode 2, 32-bit)
+__global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const float* __restrict__ g, long long M,
+                                              float thr, unsigned long long seed, int mode,
+                                              unsigned long long* __restrict__ k64, uint32_t* __restrict__ k32)
+{
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x) {
+        const bool occ = V[v] > thr;
+        if (mode == 2) {
+            k32[v] = occ ? __float_as_uint(g[v]) : 0xFFFFFFFFu;
+            continue;
+        }
+        unsigned long long key = ~0ull;
+        if (mode == 1) {
+            if (occ) {
+                uint32_t r[4];
+                draw((unsigned long long)v, 1u, seed, r);
+                key = ((unsigned long long)r[0] << 32) | r[1];
+            }
+        } else {
+            const float gv = g[v];
+            if (occ && gv > 0.0f) {
+                uint32_t r[4];
+                draw((unsigned long long)v, 0u, seed, r);
+                unsigned long long m = (((unsigned long long)r[0] << 32) | r[1]) >> 12;
+                double u = (double)(2 * m + 1) * 0x1p-53;
+                double kd = -log(u) / (double)gv;
+                key = (unsigned long long)__double_as_longlong(kd);
+            }
+        }
+        k64[v] = key;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_sel_hist(const K* __restrict__ keys, long long M, K prefix, K pmask, int shift,
+                                                  unsigned long long* __restrict__ hist)
+{
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x) {
+        K k = keys[v];
+        if ((k & pmask) == prefix) atomicAdd(&h[(unsigned)((k >> shift) & 255u)], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+// order-preserving compaction: selected iff key < K or (key == K and v <= vlast)
+constexpr int kCompactTiles = 32;
+constexpr long long kCompactChunk = 256LL * kCompactTiles;
+
+template <typename K>
+__device__ __forceinline__ bool sel_pred(const K* keys, long long v, long long M, K thr, long long vlast, int tie_only)
+{
+    if (v >= M) return false;
+    K k = keys[v];
+    if (tie_only) return k == thr;
+    return k < thr || (k == thr && v <= vlast);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_compact_count(const K* __restrict__ keys, long long M, K thr, long long vlast,
+                                                       int tie_only, uint32_t* __restrict__ bcnt)
+{
+    __shared__ unsigned sw[8];
+    long long base = (long long)blockIdx.x * kCompactChunk;
+    unsigned c = 0;
+    for (int t = 0; t < kCompactTiles; ++t) c += sel_pred(keys, base + t * 256 + threadIdx.x, M, thr, vlast, tie_only);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned s = 0;
+        for (int w = 0; w < 8; ++w) s += sw[w];
+        bcnt[blockIdx.x] = s;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_compact_write(const K* __restrict__ keys, long long M, K thr, long long vlast,
+                                                       int tie_only, const unsigned long long* __restrict__ boff,
+                                                       long long limit, long long* __restrict__ out)
+{
+    __shared__ unsigned sw[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long base = (long long)blockIdx.x * kCompactChunk;
+    unsigned long long run = boff[blockIdx.x];
+    for (int t = 0; t < kCompactTiles; ++t) {
+        long long v = base + t * 256 + threadIdx.x;
+        bool p = sel_pred(keys, v, M, thr, vlast, tie_only);
+        unsigned bal = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) sw[w] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, tot = 0;
+        for (int ww = 0; ww < 8; ++ww) {
+            if (ww < w) before += sw[ww];
+            tot += sw[ww];
+        }
+        if (p) {
+            unsigned long long pos = run + before + __popc(bal & ((1u << lane) - 1u));
+            if ((long long)pos < limit) out[pos] = v;
+        }
+        run += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_coords(const long long* __restrict__ vox, long long ng, int nx, int ny, int4* __restrict__ xyz)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    long long v = vox[i];
+    xyz[i] = make_int4((int)(v % nx), (int)((v / nx) % ny), (int)(v / ((long long)nx * ny)), 0);
+}
+
+// mean distance to the 3 nearest seeds of the group, for subsample point j
+__global__ void __launch_bounds__(256) k_spacing(const int4* __restrict__ xyz, long long ng, int nsub, int knn,
+                                                 double* __restrict__ vals)
+{
+    const int j = blockIdx.x;
+    const long long i = (long long)(((unsigned long long)j * (unsigned long long)ng) / (unsigned long long)nsub);
+    const int4 p = xyz[i];
+    unsigned long long b0 = ~0ull, b1 = ~0ull, b2 = ~0ull;
+    for (long long o = threadIdx.x; o < ng; o += blockDim.x) {
+        if (o == i) continue;
+        const int4 q = xyz[o];
+        long long dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+        unsigned long long d2 = (unsigned long long)(dx * dx + dy * dy + dz * dz);
+        if (d2 < b2) {
+            if (d2 < b1) {
+                b2 = b1;
+                if (d2 < b0) { b1 = b0; b0 = d2; } else b1 = d2;
+            } else b2 = d2;
+        }
+    }
+    __shared__ unsigned long long cand[256 * 3];
+    cand[threadIdx.x * 3] = b0; cand[threadIdx.x * 3 + 1] = b1; cand[threadIdx.x * 3 + 2] = b2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long best[3] = {~0ull, ~0ull, ~0ull};
+        for (int t = 0; t < 256 * 3; ++t) {
+            unsigned long long d2 = cand[t];
+            if (d2 < best[2]) {
+                if (d2 < best[1]) {
+                    best[2] = best[1];
+                    if (d2 < best[0]) { best[1] = best[0]; best[0] = d2; } else best[1] = d2;
+                } else best[2] = d2;
+            }
+        }
+        double s = 0.0;
+        for (int t = 0; t < knn; ++t) s += sqrt((double)best[t]);
+        vals[j] = s / (double)knn;
+    }
+}
+
+// ---------------- per-seed assembly (FP64) ----------------
+__device__ void grad64(const float* V, int nx, int ny, int nz, int x, int y, int z, double gv[3])
+{
+    int c[3] = {x, y, z};
+    int dims[3] = {nx, ny, nz};
+    for (int axis = 0; axis < 3; ++axis) {
+        int n = dims[axis];
+        if (n < 2) { gv[axis] = 0.0; continue; }
+        int lo = c[axis] - 1, hi = c[axis] + 1;
+        double scale = 0.5;
+        if (lo < 0) { lo = c[axis]; scale = 1.0; }
+        if (hi > n - 1) { hi = c[axis]; scale = 1.0; }
+        int a[3] = {x, y, z}, b[3] = {x, y, z};
+        a[axis] = hi; b[axis] = lo;
+        gv[axis] = scale * ((double)V[vid(nx, ny, a[0], a[1], a[2])] - (double)V[vid(nx, ny, b[0], b[1], b[2])]);
+    }
+}
+
+__device__ void jacobi3(const double J6[6], double evals[3], double ev9[9])
+{
+    double a[3][3] = {{J6[0], J6[3], J6[4]}, {J6[3], J6[1], J6[5]}, {J6[4], J6[5], J6[2]}};
+    double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        double fro = off * 2 + a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-30 * fro || off == 0.0) break;
+        for (int r = 0; r < 3; ++r) {
+            int p = PQ[r][0], q = PQ[r][1];
+            if (a[p][q] == 0.0) continue;
+            double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+            for (int k = 0; k < 3; ++k) {
+                double akp = a[k][p], akq = a[k][q];
+                a[k][p] = c * akp - s * akq;
+                a[k][q] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double apk = a[p][k], aqk = a[q][k];
+                a[p][k] = c * apk - s * aqk;
+                a[q][k] = s * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double vkp = v[k][p], vkq = v[k][q];
+                v[k][p] = c * vkp - s * vkq;
+                v[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+    int idx[3] = {0, 1, 2};
+    double lam[3] = {a[0][0], a[1][1], a[2][2]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (lam[idx[j]] < lam[idx[i]] || (lam[idx[j]] == lam[idx[i]] && idx[j] < idx[i])) {
+                int t = idx[i]; idx[i] = idx[j]; idx[j] = t;
+            }
+    for (int c = 0; c < 3; ++c) {
+        evals[c] = lam[idx[c]];
+        for (int r = 0; r < 3; ++r) ev9[r * 3 + c] = v[r][idx[c]];
+    }
+}
+
+__device__ void frame_quat(const double ev9[9], double q[4])
+{
+    double e[2][3];
+    for (int c = 0; c < 2; ++c) {
+        int best = 0;
+        for (int r = 1; r < 3; ++r)
+            if (fabs(ev9[r * 3 + c]) > fabs(ev9[best * 3 + c])) best = r;
+        double sgn = ev9[best * 3 + c] < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < 3; ++r) e[c][r] = sgn * ev9[r * 3 + c];
+    }
+    double e3[3] = {e[0][1] * e[1][2] - e[0][2] * e[1][1], e[0][2] * e[1][0] - e[0][0] * e[1][2],
+                    e[0][0] * e[1][1] - e[0][1] * e[1][0]};
+    double R[3][3];
+    for (int r = 0; r < 3; ++r) { R[r][0] = e[0][r]; R[r][1] = e[1][r]; R[r][2] = e3[r]; }
+    double tr = R[0][0] + R[1][1] + R[2][2];
+    double w, x, y, z;
+    if (tr > 0.0) {
+        double S = sqrt(tr + 1.0) * 2.0;
+        w = 0.25 * S; x = (R[2][1] - R[1][2]) / S; y = (R[0][2] - R[2][0]) / S; z = (R[1][0] - R[0][1]) / S;
+    } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
+        double S = sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]) * 2.0;
+        w = (R[2][1] - R[1][2]) / S; x = 0.25 * S; y = (R[0][1] + R[1][0]) / S; z = (R[0][2] + R[2][0]) / S;
+    } else if (R[1][1] > R[2][2]) {
+        double S = sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]) * 2.0;
+        w = (R[0][2] - R[2][0]) / S; x = (R[0][1] + R[1][0]) / S; y = 0.25 * S; z = (R[1][2] + R[2][1]) / S;
+    } else {
+        double S = sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]) * 2.0;
+        w = (R[1][0] - R[0][1]) / S; x = (R[0][2] + R[2][0]) / S; y = (R[1][2] + R[2][1]) / S; z = 0.25 * S;
+    }
+    if (w < 0.0) { w = -w; x = -x; y = -y; z = -z; }
+    q[0] = w; q[1] = x; q[2] = y; q[3] = z;
+}
+
+__device__ double trilinear(const float* V, int nx, int ny, int nz, double px, double py, double pz)
+{
+    double p[3] = {px, py, pz};
+    int dims[3] = {nx, ny, nz};
+    int i0[3], i1[3];
+    double f[3];
+    for (int j = 0; j < 3; ++j) {
+        double c = p[j];
+        if (c < 0.0) c = 0.0;
+        if (c > dims[j] - 1) c = dims[j] - 1;
+        double fl = floor(c);
+        i0[j] = (int)fl;
+        i1[j] = i0[j] + 1 < dims[j] ? i0[j] + 1 : i0[j];
+        f[j] = c - fl;
+    }
+    double acc = 0.0;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                double wgt = (cx ? f[0] : 1 - f[0]) * (cy ? f[1] : 1 - f[1]) * (cz ? f[2] : 1 - f[2]);
+                acc += wgt * (double)V[vid(nx, ny, cx ? i1[0] : i0[0], cy ? i1[1] : i0[1], cz ? i1[2] : i0[2])];
+            }
+    return acc;
+}
+
+struct AssembleArgs {
+    const float* V;
+    const float* g;
+    const long long* vd;
+    const long long* vc;
+    long long Nd, N;
+    int nx, ny, nz;
+    unsigned long long seed;
+    double hd, hc, gbar, smax_cap, smin_cap, wl;
+    float* prims;
+};
+
+__global__ void __launch_bounds__(128) k_assemble(const AssembleArgs a)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int grp = i < a.Nd ? 0 : 1;
+    const long long gi = grp == 0 ? i : i - a.Nd;
+    const long long v = grp == 0 ? a.vd[gi] : a.vc[gi];
+    const int cx = (int)(v % a.nx), cy = (int)((v / a.nx) % a.ny), cz = (int)(v / ((long long)a.nx * a.ny));
+    uint32_t r[4];
+    draw((unsigned long long)gi, 2u + (uint32_t)grp, a.seed, r);
+    float u[3];
+    for (int j = 0; j < 3; ++j) u[j] = (float)(r[j] >> 8) * 0x1p-24f - 0.5f;
+    double mu[3] = {cx + (double)u[0], cy + (double)u[1], cz + (double)u[2]};
+    // 7^3 structure tensor, window clipped at the borders
+    double J[6] = {0, 0, 0, 0, 0, 0};
+    for (int z = cz - 3; z <= cz + 3; ++z) {
+        if (z < 0 || z >= a.nz) continue;
+        for (int y = cy - 3; y <= cy + 3; ++y) {
+            if (y < 0 || y >= a.ny) continue;
+            for (int x = cx - 3; x <= cx + 3; ++x) {
+                if (x < 0 || x >= a.nx) continue;
+                double gv[3];
+                grad64(a.V, a.nx, a.ny, a.nz, x, y, z, gv);
+                J[0] += gv[0] * gv[0]; J[1] += gv[1] * gv[1]; J[2] += gv[2] * gv[2];
+                J[3] += gv[0] * gv[1]; J[4] += gv[0] * gv[2]; J[5] += gv[1] * gv[2];
+            }
+        }
+    }
+    double ev[3], evec[9], q[4];
+    jacobi3(J, ev, evec);
+    frame_quat(evec, q);
+    double sg = 0.5 * (grp == 0 ? a.hd : a.hc);
+    double ratio = a.gbar > 0.0 ? 1.0 + (double)a.g[v] / a.gbar : 1.0;
+    if (ratio < 1.0) ratio = 1.0;
+    if (ratio > 3.0) ratio = 3.0;
+    double s[3] = {sg * ratio, sg, sg};
+    float out[12];
+    out[0] = (float)mu[0]; out[1] = (float)mu[1]; out[2] = (float)mu[2];
+    for (int j = 0; j < 3; ++j) {
+        if (s[j] > a.smax_cap) s[j] = a.smax_cap;
+        if (s[j] < a.smin_cap) s[j] = a.smin_cap;
+        out[3 + j] = (float)log(s[j]);
+    }
+    out[6] = (float)q[0]; out[7] = (float)q[1]; out[8] = (float)q[2]; out[9] = (float)q[3];
+    out[10] = (float)trilinear(a.V, a.nx, a.ny, a.nz, mu[0], mu[1], mu[2]);
+    out[11] = (float)a.wl;
+    float4* o = reinterpret_cast<float4*>(a.prims) + 3 * i;
+    o[0] = make_float4(out[0], out[1], out[2], out[3]);
+    o[1] = make_float4(out[4], out[5], out[6], out[7]);
+    o[2] = make_float4(out[8], out[9], out[10], out[11]);
+}
+
+int grid_for(long long M)
+{
+    long long b = (M + 255) / 256;
+    if (b > 148LL * 32) b = 148LL * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// k-th smallest key (0-based rank) by radix select; host-driven passes
+template <typename K>
+gve_status radix_select(gve_ctx* c, const K* keys, long long M, unsigned long long rank, K* out, cudaStream_t s)
+{
+    const int bits = (int)sizeof(K) * 8;
+    gve_status st = ensure(c, c->a_tmp, 256 * sizeof(unsigned long long), s);
+    if (st != GVE_OK) return st;
+    unsigned long long* dh = (unsigned long long*)c->a_tmp.p;
+    std::vector<unsigned long long> h(256);
+    K prefix = 0, pmask = 0;
+    for (int shift = bits - 8; shift >= 0; shift -= 8) {
+        cudaError_t e = cudaMemsetAsync(dh, 0, 256 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset select hist");
+        k_sel_hist<K><<<grid_for(M), 256, 0, s>>>(keys, M, prefix, pmask, shift, dh);
+        e = cudaMemcpyAsync(h.data(), dh, 256 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "select hist");
+        unsigned long long acc = 0;
+        int d = 0;
+        for (; d < 256; ++d) {
+            if (acc + h[d] > rank) break;
+            acc += h[d];
+        }
+        if (d == 256) { c->err = "radix select rank beyond key count"; return GVE_E_INTERNAL; }
+        rank -= acc;
+        prefix |= (K)d << shift;
+        pmask |= (K)255 << shift;
+    }
+    *out = prefix;
+    return GVE_OK;
+}
+
+// seeds of one draw: the `count` smallest (key, voxel) pairs, in voxel order
+gve_status draw_set(gve_ctx* c, const unsigned long long* keys, long long M, long long count, long long* out,
+                    cudaStream_t s)
+{
+    if (count <= 0) return GVE_OK;
+    unsigned long long K;
+    gve_status st = radix_select<unsigned long long>(c, keys, M, (unsigned long long)(count - 1), &K, s);
+    if (st != GVE_OK) return st;
+    long long nblk = (M + kCompactChunk - 1) / kCompactChunk;
+    st = ensure(c, c->a_cnt, sizeof(uint32_t) * nblk + sizeof(unsigned long long) * (nblk + 1) + 64, s);
+    if (st != GVE_OK) return st;
+    uint32_t* bcnt = (uint32_t*)c->a_cnt.p;
+    unsigned long long* boff = (unsigned long long*)((char*)c->a_cnt.p + ((sizeof(uint32_t) * nblk + 15) / 16) * 16);
+    std::vector<unsigned long long> tail(1);
+    // number strictly below K
+    k_compact_count<unsigned long long><<<(unsigned)nblk, 256, 0, s>>>(keys, M, K, -1, 0, bcnt);
+    launch_exscan_u32(bcnt, nblk, boff, c->scanp.p, s);
+    unsigned long long less = 0;
+    cudaError_t e = cudaMemcpyAsync(&less, boff + nblk, sizeof(less), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "draw count");
+    long long need = count - (long long)less;  // ties at K taken in voxel order
+    long long vlast = -1;
+    if (need > 0) {
+        // voxel index of the need-th tie
+        k_compact_count<unsigned long long><<<(unsigned)nblk, 256, 0, s>>>(keys, M, K, 0, 1, bcnt);
+        launch_exscan_u32(bcnt, nblk, boff, c->scanp.p, s);
+        k_compact_write<unsigned long long><<<(unsigned)nblk, 256, 0, s>>>(keys, M, K, 0, 1, boff, need, out);
+        e = cudaMemcpyAsync(&vlast, out + need - 1, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "draw ties");
+    }
+    k_compact_count<unsigned long long><<<(unsigned)nblk, 256, 0, s>>>(keys, M, K, vlast, 0, bcnt);
+    launch_exscan_u32(bcnt, nblk, boff, c->scanp.p, s);
+    k_compact_write<unsigned long long><<<(unsigned)nblk, 256, 0, s>>>(keys, M, K, vlast, 0, boff, count, out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "draw compaction");
+    return GVE_OK;
+}
+
+gve_status group_spacing(gve_ctx* c, const long long* vox, long long ng, gve_dims d, long long n_occ, long long N,
+                         double* h, cudaStream_t s)
+{
+    if (ng < 2) {
+        *h = std::cbrt((double)(n_occ > 0 ? n_occ : 1) / (double)(N > 0 ? N : 1));
+        return GVE_OK;
+    }
+    int nsub = ng < 4096 ? (int)ng : 4096;
+    int knn = ng - 1 < 3 ? (int)(ng - 1) : 3;
+    gve_status st = ensure(c, c->a_tmp, sizeof(int4) * ng + sizeof(double) * 4096 + 64, s);
+    if (st != GVE_OK) return st;
+    int4* xyz = (int4*)c->a_tmp.p;
+    double* vals = (double*)((char*)c->a_tmp.p + sizeof(int4) * ng);
+    k_coords<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(vox, ng, d.nx, d.ny, xyz);
+    k_spacing<<<nsub, 256, 0, s>>>(xyz, ng, nsub, knn, vals);
+    std::vector<double> hv(nsub);
+    cudaError_t e = cudaMemcpyAsync(hv.data(), vals, sizeof(double) * nsub, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spacing");
+    std::sort(hv.begin(), hv.end());
+    *h = hv[(nsub - 1) / 2];
+    return GVE_OK;
+}
+
+long long nd_of(long long N, double frac) { return (long long)std::floor(frac * (double)N + 0.5); }
+
+long long feasible_max(long long N, double frac, long long n_elig, long long n_occ)
+{
+    long long lo = 0, hi = N;
+    while (lo < hi) {
+        long long mid = lo + (hi - lo + 1) / 2;
+        long long nd = nd_of(mid, frac), nc = mid - nd;
+        if (nd <= n_elig && nc <= n_occ) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace
+
+gve_status allocate(gve_ctx* c, const float* V, gve_dims d, int64_t N, const gve_alloc_opts* o, float* prims,
+                    int64_t* feasible_out, gve_alloc_info* info, cudaStream_t s)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    gve_status st;
+    if ((st = ensure(c, c->a_g, sizeof(float) * M, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->a_keys, sizeof(unsigned long long) * M, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->a_sel, sizeof(long long) * (N > 0 ? N : 1) + 64, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->state, sizeof(DevState), s)) != GVE_OK) return st;
+    float* g = (float*)c->a_g.p;
+    unsigned long long* cnt = (unsigned long long*)c->state.p;  // scratch use of the state block
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset counts");
+    const float thr = o->occ_thresh;
+    k_grad_occ<<<grid_for(M), 256, 0, s>>>(V, d.nx, d.ny, d.nz, thr, g, cnt);
+    unsigned long long hc[2] = {0, 0};
+    e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy counts");
+    const long long n_occ = (long long)hc[0], n_elig = (long long)hc[1];
+    const long long Nd = nd_of(N, o->detail_frac), Nc = N - Nd;
+    if (info) {
+        info->n_occupied = n_occ; info->n_eligible = n_elig; info->n_detail = Nd; info->n_coverage = Nc;
+        info->gbar = 0; info->h_detail = 0; info->h_coverage = 0;
+    }
+    if (Nd > n_elig || Nc > n_occ) {
+        if (feasible_out) *feasible_out = feasible_max(N, o->detail_frac, n_elig, n_occ);
+        c->err = "budget exceeds the distinct positions the field supports";
+        return GVE_E_BUDGET;
+    }
+    if (feasible_out) *feasible_out = N;
+    if (N == 0) return GVE_OK;
+    // gbar: lower median of g over occupied voxels
+    uint32_t* k32 = (uint32_t*)c->a_keys.p;
+    k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, o->seed, 2, nullptr, k32);
+    uint32_t gbits = 0;
+    if ((st = radix_select<uint32_t>(c, k32, M, (unsigned long long)((n_occ - 1) / 2), &gbits, s)) != GVE_OK) return st;
+    float gbar_f;
+    memcpy(&gbar_f, &gbits, sizeof(float));
+    const double gbar = (double)gbar_f;
+    // draws
+    unsigned long long* k64 = (unsigned long long*)c->a_keys.p;
+    long long* vd = (long long*)c->a_sel.p;
+    long long* vc = vd + Nd;
+    k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, o->seed, 0, k64, nullptr);
+    if ((st = draw_set(c, k64, M, Nd, vd, s)) != GVE_OK) return st;
+    k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, o->seed, 1, k64, nullptr);
+    if ((st = draw_set(c, k64, M, Nc, vc, s)) != GVE_OK) return st;
+    // group spacing
+    double hd = 0, hcv = 0;
+    if ((st = group_spacing(c, vd, Nd, d, n_occ, N, &hd, s)) != GVE_OK) return st;
+    if ((st = group_spacing(c, vc, Nc, d, n_occ, N, &hcv, s)) != GVE_OK) return st;
+    AssembleArgs a;
+    a.V = V; a.g = g; a.vd = vd; a.vc = vc; a.Nd = Nd; a.N = N;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.seed = o->seed;
+    a.hd = hd; a.hc = hcv; a.gbar = gbar;
+    int mx = d.nx > d.ny ? (d.nx > d.nz ? d.nx : d.nz) : (d.ny > d.nz ? d.ny : d.nz);
+    a.smax_cap = (double)mx / 16.0;
+    a.smin_cap = 0.3;
+    a.wl = std::log((double)o->w0 / (1.0 - (double)o->w0));
+    a.prims = prims;
+    k_assemble<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "assemble");
+    if (info) { info->gbar = gbar; info->h_detail = hd; info->h_coverage = hcv; }
+    return GVE_OK;
+}
+
+}  // namespace gve

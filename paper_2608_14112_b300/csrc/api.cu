@@ -1,0 +1,558 @@
+// api.cu -- the C ABI of libgve (see include/gve.h): argument checks, context
+// scratch, and the launch sequences of evaluation, gradient and refinement.
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "gve_int.cuh"
+
+namespace gve {
+
+gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what)
+{
+    if (c) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+        c->err = buf;
+    }
+    return GVE_E_CUDA;
+}
+
+static gve_status fail(gve_ctx* c, gve_status s, const char* msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return GVE_OK;
+    if (b.p) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "sync before regrow");
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, GVE_E_NOMEM, "device scratch allocation failed");
+    }
+    b.bytes = want;
+    return GVE_OK;
+}
+
+__global__ void k_reset_state(DevState* st)
+{
+    st->total = 0;
+    st->max_total = 0;
+    st->overflow = 0;
+    st->first_overflow_iter = INT_MAX;
+    st->err = 0;
+    st->sse[0] = 0.0;
+    st->sse[1] = 0.0;
+    st->kept = 0;
+    st->cand = 0;
+}
+
+}  // namespace gve
+
+using namespace gve;
+
+#define GVE_TRY(x)                               \
+    do {                                         \
+        gve_status _s = (x);                     \
+        if (_s != GVE_OK) return _s;             \
+    } while (0)
+#define GVE_CUDA(x, what)                                  \
+    do {                                                   \
+        cudaError_t _e = (x);                              \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
+    } while (0)
+
+namespace {
+
+struct Call {
+    gve_ctx* c;
+    cudaStream_t s;
+    BinGeom g;
+    long long n;
+    int sorted;  // which buffer holds the sorted pairs
+};
+
+DevState* dstate(gve_ctx* c) { return reinterpret_cast<DevState*>(c->state.p); }
+
+gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!o) return fail(c, GVE_E_INVALID, "null options");
+    if (n < 0 || n > (int64_t)INT_MAX) return fail(c, GVE_E_INVALID, "primitive count out of range");
+    if (n > 0 && !prims) return fail(c, GVE_E_INVALID, "null primitive pointer");
+    if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "primitives not 16-byte aligned");
+    if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
+    if (d.nx > (1 << 24) || d.ny > (1 << 24) || d.nz > (1 << 24)) return fail(c, GVE_E_INVALID, "grid axis above 2^24");
+    if (o->brick != 8) return fail(c, GVE_E_INVALID, "brick edge must be 8");
+    if (!(o->trunc_k > 0.f) || !std::isfinite(o->trunc_k)) return fail(c, GVE_E_INVALID, "trunc_k must be positive");
+    if (o->normalized && !(o->rho0 > 0.f)) return fail(c, GVE_E_INVALID, "rho0 must be positive");
+    BinGeom g = make_geom(d, o->brick);
+    if (g.nbricks > (long long)INT_MAX || g.key_bits > 31) return fail(c, GVE_E_INVALID, "grid too large");
+    return GVE_OK;
+}
+
+gve_status reset_state(Call& k)
+{
+    k_reset_state<<<1, 1, 0, k.s>>>(dstate(k.c));
+    k.c->launches += 1;
+    return GVE_OK;
+}
+
+gve_status read_state(Call& k, DevState* out)
+{
+    gve_ctx* c = k.c;
+    GVE_CUDA(cudaMemcpyAsync(c->hstate, c->state.p, sizeof(DevState), cudaMemcpyDeviceToHost, k.s), "state readback");
+    GVE_CUDA(cudaStreamSynchronize(k.s), "state sync");
+    *out = *c->hstate;
+    return GVE_OK;
+}
+
+// per-Gaussian and per-brick scratch
+gve_status size_static(Call& k)
+{
+    gve_ctx* c = k.c;
+    long long n = k.n > 0 ? k.n : 1;
+    GVE_TRY(ensure(c, c->rec, sizeof(float4) * 3 * n, k.s));
+    GVE_TRY(ensure(c, c->binrec, sizeof(BinRec) * n, k.s));
+    GVE_TRY(ensure(c, c->counts, sizeof(uint32_t) * n, k.s));
+    GVE_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * (n + 1), k.s));
+    GVE_TRY(ensure(c, c->acc, sizeof(float) * 12 * n, k.s));
+    GVE_TRY(ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, k.s));
+    GVE_TRY(ensure(c, c->ranges, sizeof(uint32_t) * 2 * k.g.nbricks, k.s));
+    GVE_TRY(ensure(c, c->part, sizeof(double2) * (k.g.nbricks + 1024), k.s));
+    return GVE_OK;
+}
+
+gve_status grow_pairs(Call& k, unsigned long long need)
+{
+    gve_ctx* c = k.c;
+    if (need <= c->cap && c->keys[0].p) return GVE_OK;
+    unsigned long long cap = need + need / 4 + 65536;
+    if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
+    if (need > cap) return fail(c, GVE_E_CAPACITY, "more than 2^32 brick pairs");
+    for (int b = 0; b < 2; ++b) {
+        GVE_TRY(ensure(c, c->keys[b], sizeof(uint32_t) * cap, k.s));
+        GVE_TRY(ensure(c, c->vals[b], sizeof(uint32_t) * cap, k.s));
+    }
+    GVE_TRY(ensure(c, c->hist, sizeof(uint32_t) * 256 * ((cap + kSortTile - 1) / kSortTile + 1), k.s));
+    c->cap = cap;
+    return GVE_OK;
+}
+
+// prep + count + scan, synchronise and size the pair buffers
+gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
+{
+    gve_ctx* c = k.c;
+    GVE_TRY(size_static(k));
+    reset_state(k);
+    launch_prep(prims, k.n, k.g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, k.s);
+    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, k.s);
+    launch_offsets((uint32_t*)c->counts.p, k.n, (unsigned long long*)c->offsets.p, c->scanp.p, dstate(c),
+                   ~0ull, 0, k.s);
+    c->launches += k.n > 0 ? 6 : 4;
+    GVE_CUDA(cudaGetLastError(), "launch (sizing)");
+    DevState h;
+    GVE_TRY(read_state(k, &h));
+    GVE_TRY(grow_pairs(k, h.total));
+    reset_state(k);
+    return GVE_OK;
+}
+
+// full binning: prep, count, offsets, emit, sort, ranges
+gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter)
+{
+    gve_ctx* c = k.c;
+    launch_prep(prims, k.n, k.g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, k.s);
+    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, k.s);
+    launch_offsets((uint32_t*)c->counts.p, k.n, (unsigned long long*)c->offsets.p, c->scanp.p, dstate(c), c->cap,
+                   iter, k.s);
+    launch_emit((BinRec*)c->binrec.p, (float4*)c->rec.p, (unsigned long long*)c->offsets.p, k.n, k.g,
+                (uint32_t*)c->keys[0].p, (uint32_t*)c->vals[0].p, dstate(c), k.s);
+    uint32_t* kk[2] = {(uint32_t*)c->keys[0].p, (uint32_t*)c->keys[1].p};
+    uint32_t* vv[2] = {(uint32_t*)c->vals[0].p, (uint32_t*)c->vals[1].p};
+    k.sorted = launch_sort(kk, vv, dstate(c), c->cap, k.g.key_bits, (uint32_t*)c->hist.p, c->scanp.p, k.s);
+    uint32_t* start = (uint32_t*)c->ranges.p;
+    GVE_CUDA(cudaMemsetAsync(start, 0, sizeof(uint32_t) * 2 * k.g.nbricks, k.s), "memset ranges");
+    launch_ranges(kk[k.sorted], dstate(c), c->cap, start, start + k.g.nbricks, k.s);
+    c->launches += (k.n > 0 ? 3 : 0) + 4 + 5 * ((k.g.key_bits + 7) / 8) + 1;
+    GVE_CUDA(cudaGetLastError(), "launch (binning)");
+    return GVE_OK;
+}
+
+BrickArgs brick_args(Call& k, const gve_eval_opts* o)
+{
+    gve_ctx* c = k.c;
+    BrickArgs a{};
+    a.g = k.g;
+    a.start = (const uint32_t*)c->ranges.p;
+    a.end = a.start + k.g.nbricks;
+    a.gids = (const uint32_t*)c->vals[k.sorted].p;
+    a.rec = (const float4*)c->rec.p;
+    a.part = (double2*)c->part.p;
+    a.st = dstate(c);
+    double k2 = (double)o->trunc_k * (double)o->trunc_k;
+    a.T = (float)(k2 * kNegHalfLog2e);
+    a.rho0 = o->rho0;
+    a.normalized = o->normalized;
+    a.mask_thresh = -1.f;
+    a.inv_m = (float)(1.0 / ((double)k.g.nx * k.g.ny * k.g.nz));
+    return a;
+}
+
+gve_status begin(gve_ctx* c, Call& k, int64_t n, gve_dims d, const gve_eval_opts* o, void* stream)
+{
+    k.c = c;
+    k.s = (cudaStream_t)stream;
+    k.n = n;
+    k.g = make_geom(d, o->brick);
+    k.sorted = 0;
+    c->launches = 0;
+    GVE_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    GVE_TRY(ensure(c, c->state, sizeof(DevState), k.s));
+    return GVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gve_status_str(gve_status s)
+{
+    switch (s) {
+        case GVE_OK: return "ok";
+        case GVE_E_INVALID: return "invalid argument";
+        case GVE_E_BUDGET: return "infeasible budget";
+        case GVE_E_NOMEM: return "out of device memory";
+        case GVE_E_CUDA: return "CUDA error";
+        case GVE_E_TIMEOUT: return "device wait timed out";
+        case GVE_E_CAPACITY: return "pair capacity exceeded";
+        case GVE_E_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char* gve_last_error(const gve_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+gve_status gve_ctx_create(gve_ctx** out, int device)
+{
+    if (!out) return GVE_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GVE_E_INVALID;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return GVE_E_CUDA;
+    gve_ctx* c = new gve_ctx();
+    c->device = device;
+    if (cudaMallocHost(&c->hstate, sizeof(DevState)) != cudaSuccess) {
+        delete c;
+        return GVE_E_NOMEM;
+    }
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaFreeHost(c->hstate);
+        delete c;
+        return GVE_E_CUDA;
+    }
+    *out = c;
+    return GVE_OK;
+}
+
+void gve_ctx_destroy(gve_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
+                   &c->vals[0], &c->vals[1], &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
+                   &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace};
+    for (Buf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (c->hstate) cudaFreeHost(c->hstate);
+    if (c->sev_ready)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 64; ++b) cudaEventDestroy(c->sev[a][b]);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+gve_status gve_evaluate(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
+                        float* field_out, void* stream)
+{
+    GVE_TRY(check_common(c, prims, n, d, o));
+    if (!field_out) return fail(c, GVE_E_INVALID, "null output field");
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    GVE_TRY(bin_all(k, prims, o, 0));
+    BrickArgs a = brick_args(k, o);
+    a.field_out = field_out;
+    launch_brick(kModeEval, a, k.s);
+    GVE_CUDA(cudaGetLastError(), "launch (evaluate)");
+    return GVE_OK;
+}
+
+gve_status gve_loss_grad(gve_ctx* c, const float* prims, int64_t n, const float* field, gve_dims d,
+                         const gve_eval_opts* o, float mask_thresh, float* grad, double* sse_dev, void* stream)
+{
+    GVE_TRY(check_common(c, prims, n, d, o));
+    if (!field) return fail(c, GVE_E_INVALID, "null target field");
+    if (n > 0 && !grad) return fail(c, GVE_E_INVALID, "null gradient output");
+    if (grad && (reinterpret_cast<uintptr_t>(grad) & 15u)) return fail(c, GVE_E_INVALID, "gradient not 16-byte aligned");
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (n > 0 ? n : 1), k.s), "memset acc");
+    GVE_TRY(bin_all(k, prims, o, 0));
+    BrickArgs a = brick_args(k, o);
+    a.field = field;
+    a.mask_thresh = mask_thresh;
+    a.acc = (float*)c->acc.p;
+    launch_brick(kModeLoss, a, k.s);
+    launch_sse_reduce(a.part, k.g.nbricks, dstate(c), nullptr, 0, 0.0, k.s);
+    launch_chain((float*)c->acc.p, (float*)c->acc.p, const_cast<float*>(prims), n, grad, nullptr, nullptr, nullptr,
+                 dstate(c), k.s);
+    if (sse_dev)
+        GVE_CUDA(cudaMemcpyAsync(sse_dev, dstate(c)->sse, 2 * sizeof(double), cudaMemcpyDeviceToDevice, k.s),
+                 "copy sse");
+    GVE_CUDA(cudaGetLastError(), "launch (loss_grad)");
+    return GVE_OK;
+}
+
+gve_status gve_backward(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
+                        const float* grad_field, float* grad, void* stream)
+{
+    GVE_TRY(check_common(c, prims, n, d, o));
+    if (!grad_field) return fail(c, GVE_E_INVALID, "null upstream gradient");
+    if (n > 0 && !grad) return fail(c, GVE_E_INVALID, "null gradient output");
+    if (grad && (reinterpret_cast<uintptr_t>(grad) & 15u)) return fail(c, GVE_E_INVALID, "gradient not 16-byte aligned");
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (n > 0 ? n : 1), k.s), "memset acc");
+    GVE_TRY(bin_all(k, prims, o, 0));
+    BrickArgs a = brick_args(k, o);
+    a.upstream = grad_field;
+    a.acc = (float*)c->acc.p;
+    launch_brick(kModeBwd, a, k.s);
+    launch_chain((float*)c->acc.p, (float*)c->acc.p, const_cast<float*>(prims), n, grad, nullptr, nullptr, nullptr,
+                 dstate(c), k.s);
+    GVE_CUDA(cudaGetLastError(), "launch (backward)");
+    return GVE_OK;
+}
+
+gve_status gve_bin(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
+                   uint32_t* counts, uint32_t* keys, uint32_t* gids, int64_t cap, uint32_t* ranges,
+                   int64_t* n_pairs, void* stream)
+{
+    GVE_TRY(check_common(c, prims, n, d, o));
+    if (!n_pairs || (n > 0 && !counts) || !ranges || cap < 0) return fail(c, GVE_E_INVALID, "null output");
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    GVE_TRY(bin_all(k, prims, o, 0));
+    DevState h;
+    GVE_TRY(read_state(k, &h));
+    *n_pairs = (int64_t)h.total;
+    if (h.overflow) return fail(c, GVE_E_INTERNAL, "pair buffer sized by the sizing pass overflowed");
+    if ((int64_t)h.total > cap) return fail(c, GVE_E_CAPACITY, "output capacity below the pair count");
+    if (n > 0) GVE_CUDA(cudaMemcpyAsync(counts, c->counts.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, k.s), "copy");
+    if (h.total > 0) {
+        if (!keys || !gids) return fail(c, GVE_E_INVALID, "null pair outputs");
+        GVE_CUDA(cudaMemcpyAsync(keys, c->keys[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
+        GVE_CUDA(cudaMemcpyAsync(gids, c->vals[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
+    }
+    GVE_CUDA(cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint32_t) * 2 * k.g.nbricks, cudaMemcpyDeviceToDevice, k.s), "copy");
+    GVE_CUDA(cudaStreamSynchronize(k.s), "sync");
+    return GVE_OK;
+}
+
+gve_status gve_count_pairs(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
+                           int64_t* kept, int64_t* cand, void* stream)
+{
+    GVE_TRY(check_common(c, prims, n, d, o));
+    if (!kept || !cand) return fail(c, GVE_E_INVALID, "null output");
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    GVE_TRY(bin_all(k, prims, o, 0));
+    BrickArgs a = brick_args(k, o);
+    launch_brick(kModeCount, a, k.s);
+    GVE_CUDA(cudaGetLastError(), "launch (count)");
+    DevState h;
+    GVE_TRY(read_state(k, &h));
+    *kept = (int64_t)h.kept;
+    *cand = (int64_t)h.cand;
+    return GVE_OK;
+}
+
+gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, gve_dims d, const gve_schedule* sc,
+                      float* adam_state, double* trace, gve_stats* stats, void* stream)
+{
+    if (!sc) return fail(c, GVE_E_INVALID, "null schedule");
+    GVE_TRY(check_common(c, prims, n, d, &sc->eval));
+    if (!field) return fail(c, GVE_E_INVALID, "null target field");
+    if (sc->iters < 0) return fail(c, GVE_E_INVALID, "negative iteration count");
+    if (!(sc->lr >= 0.f) || !(sc->beta1 >= 0.f && sc->beta1 < 1.f) || !(sc->beta2 >= 0.f && sc->beta2 < 1.f) ||
+        !(sc->eps >= 0.f) || sc->step0 < 0)
+        return fail(c, GVE_E_INVALID, "bad Adam hyper-parameters");
+    if (adam_state && (reinterpret_cast<uintptr_t>(adam_state) & 15u))
+        return fail(c, GVE_E_INVALID, "adam state not 16-byte aligned");
+    const gve_eval_opts* o = &sc->eval;
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    long long nn = n > 0 ? n : 1;
+    float* m = adam_state;
+    if (!m) {
+        GVE_TRY(ensure(c, c->adam, sizeof(float) * 24 * nn, k.s));
+        m = (float*)c->adam.p;
+        GVE_CUDA(cudaMemsetAsync(m, 0, sizeof(float) * 24 * nn, k.s), "memset adam");
+    }
+    float* v = m + 12 * nn;
+    if (adam_state) v = adam_state + 12 * n;
+    double* tr = trace;
+    if (!tr) {
+        GVE_TRY(ensure(c, c->trace, sizeof(double) * (sc->iters + 1), k.s));
+        tr = (double*)c->trace.p;
+    }
+    GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * nn, k.s), "memset acc");
+    const bool timed = stats != nullptr;
+    if (timed && !c->sev_ready) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 64; ++b) GVE_CUDA(cudaEventCreate(&c->sev[a][b]), "event create");
+        c->sev_ready = true;
+    }
+    GVE_CUDA(cudaEventRecord(c->ev0, k.s), "event");
+    const double inv_m = 1.0 / ((double)d.nx * d.ny * d.nz);
+    int retries = 0;
+    int it = 0;
+    const int seg = 64;
+    double ms_brick = 0.0, ms_bin = 0.0;
+    while (it < sc->iters) {
+        int end = it + seg < sc->iters ? it + seg : sc->iters;
+        for (int t = it; t < end; ++t) {
+            if (timed) GVE_CUDA(cudaEventRecord(c->sev[0][t - it], k.s), "event");
+            GVE_TRY(bin_all(k, prims, o, t));
+            if (timed) GVE_CUDA(cudaEventRecord(c->sev[1][t - it], k.s), "event");
+            BrickArgs a = brick_args(k, o);
+            a.field = field;
+            a.mask_thresh = sc->mask_thresh;
+            a.acc = (float*)c->acc.p;
+            launch_brick(kModeLoss, a, k.s);
+            if (timed) GVE_CUDA(cudaEventRecord(c->sev[2][t - it], k.s), "event");
+            launch_sse_reduce(a.part, k.g.nbricks, dstate(c), tr, t, inv_m, k.s);
+            AdamArgs ad;
+            ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
+            int step = sc->step0 + t + 1;
+            ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step));
+            ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step));
+            launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, dstate(c), k.s);
+            c->launches += 1 + 2 + (n > 0 ? 1 : 0);
+        }
+        GVE_CUDA(cudaGetLastError(), "launch (refine)");
+        DevState h;
+        GVE_TRY(read_state(k, &h));
+        if (h.overflow) {
+            if (++retries > 8) return fail(c, GVE_E_CAPACITY, "pair count kept growing past capacity");
+            GVE_TRY(grow_pairs(k, h.max_total));
+            GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * nn, k.s), "memset acc");
+            reset_state(k);
+            it = h.first_overflow_iter;
+            continue;
+        }
+        if (timed) {
+            for (int t = it; t < end; ++t) {
+                float a = 0.f, b = 0.f;
+                cudaEventElapsedTime(&a, c->sev[0][t - it], c->sev[1][t - it]);
+                cudaEventElapsedTime(&b, c->sev[1][t - it], c->sev[2][t - it]);
+                ms_bin += a;
+                ms_brick += b;
+            }
+        }
+        it = end;
+    }
+    // final evaluation after the last update
+    GVE_TRY(bin_all(k, prims, o, sc->iters));
+    DevState h;
+    {
+        BrickArgs a = brick_args(k, o);
+        a.field = field;
+        a.mask_thresh = sc->mask_thresh;
+        a.acc = nullptr;
+        launch_brick(kModeLoss, a, k.s);
+        launch_sse_reduce(a.part, k.g.nbricks, dstate(c), nullptr, 0, inv_m, k.s);
+        c->launches += 3;
+    }
+    GVE_CUDA(cudaEventRecord(c->ev1, k.s), "event");
+    GVE_CUDA(cudaGetLastError(), "launch (refine final)");
+    GVE_TRY(read_state(k, &h));
+    if (h.overflow) {
+        // the final evaluation alone overflowed: grow and redo it
+        GVE_TRY(grow_pairs(k, h.max_total));
+        reset_state(k);
+        GVE_TRY(bin_all(k, prims, o, sc->iters));
+        BrickArgs a = brick_args(k, o);
+        a.field = field;
+        a.mask_thresh = sc->mask_thresh;
+        launch_brick(kModeLoss, a, k.s);
+        launch_sse_reduce(a.part, k.g.nbricks, dstate(c), nullptr, 0, inv_m, k.s);
+        GVE_TRY(read_state(k, &h));
+        if (h.overflow) return fail(c, GVE_E_CAPACITY, "final evaluation overflowed");
+        ++retries;
+    }
+    if (stats) {
+        double first = 0.0, last = 0.0;
+        if (sc->iters > 0) {
+            GVE_CUDA(cudaMemcpy(&first, tr, sizeof(double), cudaMemcpyDeviceToHost), "trace");
+            GVE_CUDA(cudaMemcpy(&last, tr + sc->iters - 1, sizeof(double), cudaMemcpyDeviceToHost), "trace");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        stats->loss_first = first;
+        stats->loss_last = last;
+        stats->sse_final = h.sse[1];
+        double M = (double)d.nx * d.ny * d.nz;
+        stats->psnr_final = h.sse[1] > 0.0 ? 10.0 * std::log10(M / h.sse[1]) : INFINITY;
+        stats->brick_pairs = (int64_t)h.total;
+        stats->iters_done = sc->iters;
+        stats->retries = retries;
+        stats->ms_total = ms;
+        stats->ms_brick = (float)ms_brick;
+        stats->ms_bin = (float)ms_bin;
+        stats->launches = c->launches;
+    }
+    return GVE_OK;
+}
+
+gve_status gve_allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget, const gve_alloc_opts* o,
+                        float* prims, int64_t* feasible_max, gve_alloc_info* info, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!field || !o) return fail(c, GVE_E_INVALID, "null argument");
+    if (budget < 0 || budget > (int64_t)INT_MAX) return fail(c, GVE_E_INVALID, "budget out of range");
+    if (budget > 0 && !prims) return fail(c, GVE_E_INVALID, "null primitive output");
+    if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "primitives not 16-byte aligned");
+    if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
+    if (d.nx > (1 << 24) || d.ny > (1 << 24) || d.nz > (1 << 24)) return fail(c, GVE_E_INVALID, "grid axis above 2^24");
+    if (!(o->detail_frac >= 0.0 && o->detail_frac <= 1.0)) return fail(c, GVE_E_INVALID, "detail_frac outside [0,1]");
+    if (!(o->w0 > 0.f && o->w0 < 1.f)) return fail(c, GVE_E_INVALID, "w0 outside (0,1)");
+    GVE_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    return gve::allocate(c, field, d, budget, o, prims, feasible_max, info, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,527 @@
+// bin.cu -- per-iteration preparation and the brick binner.
+//
+//   prep    one thread per Gaussian: activation of the Eq. 2 parameters,
+//           float32 keep-test coefficients, and the conservative brick cover.
+//   count   one warp per Gaussian: bricks of its box that pass the cover test.
+//   offsets exclusive scan of the counts (total checked against capacity).
+//   emit    one warp per Gaussian: (brick key, gid) pairs, Gaussian-major,
+//           bricks ascending (ballot + popc keeps the order).
+//   sort    stable LSD radix sort, 8-bit digits, reduce-then-scan with a
+//           per-warp match_any ranking in the scatter.
+//   ranges  per-brick [start, end) by adjacent difference.
+//
+// Bit-exactness: the keep-test coefficients and the brick cover are computed
+// with explicitly rounded FP64 operations (__dmul_rn & co., no contraction)
+// and explicitly rounded float32 operations, in the same order as the
+// oracle's definition, so both sides list exactly the same pairs.
+#include <climits>
+
+#include "gve_int.cuh"
+
+namespace gve {
+
+BinGeom make_geom(gve_dims d, int B)
+{
+    BinGeom g;
+    g.nx = d.nx; g.ny = d.ny; g.nz = d.nz; g.B = B;
+    g.nbx = (d.nx + B - 1) / B; g.nby = (d.ny + B - 1) / B; g.nbz = (d.nz + B - 1) / B;
+    g.nbricks = (long long)g.nbx * g.nby * g.nbz;
+    int bits = 1;
+    while ((1ll << bits) < g.nbricks) ++bits;
+    g.key_bits = bits;
+    return g;
+}
+
+// ------------------------------------------------------------------------
+// prep
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
+
+__global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, long long n, BinGeom g,
+                                              float k, float4* __restrict__ rec, BinRec* __restrict__ br)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
+    float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
+    float pf[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+    BinRec b;
+    for (int j = 0; j < 9; ++j) b.L[j] = 0.f;
+    b.e[0] = b.e[1] = b.e[2] = 0.f;
+    b.K2 = -1.f;
+    for (int j = 0; j < 3; ++j) { b.blo[j] = 0; b.bhi[j] = -1; }
+    b.nonempty = 0;
+    float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
+
+    bool ok = true;
+    for (int j = 0; j < 12; ++j) ok = ok && isfinite(pf[j]);
+    double s[3], q[4], nq = 0.0, R[3][3], C[3][3];
+    if (ok) {
+        for (int j = 0; j < 3; ++j) s[j] = exp((double)pf[3 + j]);
+        double qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
+        nq = __dsqrt_rn(da(da(da(dm(qw, qw), dm(qx, qx)), dm(qy, qy)), dm(qz, qz)));
+        ok = nq > 0.0 && isfinite(nq);
+        for (int j = 0; j < 3; ++j) ok = ok && s[j] > 0.0 && isfinite(s[j]);
+        if (ok) {
+            q[0] = dd(qw, nq); q[1] = dd(qx, nq); q[2] = dd(qy, nq); q[3] = dd(qz, nq);
+            double w = q[0], x = q[1], y = q[2], z = q[3];
+            R[0][0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
+            R[0][1] = dm(2.0, ds(dm(x, y), dm(w, z)));
+            R[0][2] = dm(2.0, da(dm(x, z), dm(w, y)));
+            R[1][0] = dm(2.0, da(dm(x, y), dm(w, z)));
+            R[1][1] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
+            R[1][2] = dm(2.0, ds(dm(y, z), dm(w, x)));
+            R[2][0] = dm(2.0, ds(dm(x, z), dm(w, y)));
+            R[2][1] = dm(2.0, da(dm(y, z), dm(w, x)));
+            R[2][2] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
+            double inv[3];
+            for (int j = 0; j < 3; ++j) inv[j] = dd(1.0, dm(s[j], s[j]));
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c)
+                    C[a][c] = da(da(dm(dm(R[a][0], R[c][0]), inv[0]), dm(dm(R[a][1], R[c][1]), inv[1])),
+                                 dm(dm(R[a][2], R[c][2]), inv[2]));
+        }
+    }
+    if (ok) {
+        // keep-test coefficients
+        double Q00 = dm(C[0][0], kNegHalfLog2e), Q11 = dm(C[1][1], kNegHalfLog2e);
+        double Q22 = dm(C[2][2], kNegHalfLog2e), Q01 = dm(C[0][1], kNegHalfLog2e);
+        double Q02 = dm(C[0][2], kNegHalfLog2e), Q12 = dm(C[1][2], kNegHalfLog2e);
+        double wd = 1.0 / (1.0 + exp(-(double)pf[11]));
+        r0 = make_float4(pf[0], pf[1], pf[2], (float)Q00);
+        r1 = make_float4((float)Q11, (float)Q22, (float)dm(2.0, Q01), (float)dm(2.0, Q02));
+        r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, 0.f);
+
+        // conservative brick cover
+        double smin = s[0], smax = s[0];
+        for (int j = 1; j < 3; ++j) { smin = fmin(smin, s[j]); smax = fmax(smax, s[j]); }
+        double ratio = dd(smax, smin);
+        double cond = dm(ratio, ratio);
+        double kb = dm((double)k, da(1.0001, dm(1e-5, cond)));
+        bool box_ok = isfinite(kb);
+        for (int j = 0; j < 3 && box_ok; ++j) {
+            double var = da(da(dm(dm(R[j][0], R[j][0]), dm(s[0], s[0])), dm(dm(R[j][1], R[j][1]), dm(s[1], s[1]))),
+                            dm(dm(R[j][2], R[j][2]), dm(s[2], s[2])));
+            double r = da(dm(kb, __dsqrt_rn(var)), 0.01);
+            double mu = (double)pf[j];
+            double l = ceil(ds(mu, r)), h = floor(da(mu, r));
+            int nj = j == 0 ? g.nx : (j == 1 ? g.ny : g.nz);
+            if (!(l <= h) || !isfinite(l) || !isfinite(h)) { box_ok = false; break; }
+            if (l < 0.0) l = 0.0;
+            if (h > (double)(nj - 1)) h = (double)(nj - 1);
+            if (l > h) { box_ok = false; break; }
+            b.blo[j] = (int)l / g.B;
+            b.bhi[j] = (int)h / g.B;
+        }
+        if (box_ok) {
+            for (int j = 0; j < 3; ++j)
+                for (int i2 = 0; i2 < 3; ++i2) b.L[j * 3 + i2] = (float)dd(R[i2][j], s[j]);
+            float hB = __fadd_rn((float)(0.5 * (double)(g.B - 1)), 0.01f);
+            for (int j = 0; j < 3; ++j) {
+                float sabs = __fadd_rn(__fadd_rn(fabsf(b.L[j * 3 + 0]), fabsf(b.L[j * 3 + 1])), fabsf(b.L[j * 3 + 2]));
+                b.e[j] = __fmul_rn(hB, sabs);
+            }
+            b.K2 = (float)da(dm(dm(kb, kb), 1.0001), 1e-4);
+            b.nonempty = 1;
+        } else {
+            for (int j = 0; j < 3; ++j) { b.blo[j] = 0; b.bhi[j] = -1; }
+        }
+    }
+    float4* o = rec + 3 * i;
+    o[0] = r0; o[1] = r1; o[2] = r2;
+    br[i] = b;
+}
+
+void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec, BinRec* br,
+                 cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_prep<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, br);
+}
+
+// float32 cover test of one brick (same operation order as the oracle)
+__device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy, float muz, int B, int bx,
+                                           int by, int bz)
+{
+    float half = (float)(0.5 * (double)(B - 1));
+    float cx = __fadd_rn((float)(bx * B), half);
+    float cy = __fadd_rn((float)(by * B), half);
+    float cz = __fadd_rn((float)(bz * B), half);
+    float dcx = __fsub_rn(cx, mux), dcy = __fsub_rn(cy, muy), dcz = __fsub_rn(cz, muz);
+    float acc[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float t0 = __fmul_rn(b.L[j * 3 + 0], dcx);
+        float y = __fmaf_rn(b.L[j * 3 + 2], dcz, __fmaf_rn(b.L[j * 3 + 1], dcy, t0));
+        float a = __fsub_rn(fabsf(y), b.e[j]);
+        acc[j] = a > 0.0f ? a : 0.0f;
+    }
+    float a22 = __fmul_rn(acc[2], acc[2]);
+    float sq = __fmaf_rn(acc[0], acc[0], __fmaf_rn(acc[1], acc[1], a22));
+    return sq <= b.K2;
+}
+
+// ------------------------------------------------------------------------
+// count / emit (one warp per Gaussian)
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_count(const BinRec* __restrict__ br, const float4* __restrict__ rec,
+                                               long long n, BinGeom g, uint32_t* __restrict__ counts)
+{
+    const int lane = threadIdx.x & 31;
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = wid; i < n; i += nw) {
+        const BinRec b = br[i];
+        uint32_t cnt = 0;
+        if (b.nonempty) {
+            float4 r0 = rec[3 * i];
+            long long ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
+            long long tot = ex * ey * ez;
+            for (long long t = lane; t < tot; t += 32) {
+                int bx = b.blo[0] + (int)(t % ex);
+                int by = b.blo[1] + (int)((t / ex) % ey);
+                int bz = b.blo[2] + (int)(t / (ex * ey));
+                cnt += brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz) ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) counts[i] = cnt;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
+                                              const unsigned long long* __restrict__ offsets, long long n,
+                                              BinGeom g, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                              const DevState* __restrict__ st)
+{
+    if (st->overflow) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = wid; i < n; i += nw) {
+        const BinRec b = br[i];
+        if (!b.nonempty) continue;
+        float4 r0 = rec[3 * i];
+        unsigned long long base = offsets[i];
+        long long ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
+        long long tot = ex * ey * ez;
+        for (long long t0 = 0; t0 < tot; t0 += 32) {
+            long long t = t0 + lane;
+            bool pass = false;
+            uint32_t key = 0;
+            if (t < tot) {
+                int bx = b.blo[0] + (int)(t % ex);
+                int by = b.blo[1] + (int)((t / ex) % ey);
+                int bz = b.blo[2] + (int)(t / (ex * ey));
+                pass = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
+                key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                unsigned long long pos = base + __popc(bal & lt);
+                keys[pos] = key;
+                vals[pos] = (uint32_t)i;
+            }
+            base += __popc(bal);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// device-wide exclusive scan (reduce, scan of block sums, downsweep)
+// ------------------------------------------------------------------------
+struct LenSpec {
+    const unsigned long long* dn;  // if set: len = ceil(min(*dn, cap) / kSortTile) * 256
+    unsigned long long cap;
+    unsigned long long fixed;
+    __device__ __forceinline__ unsigned long long get() const
+    {
+        if (!dn) return fixed;
+        unsigned long long m = *dn < cap ? *dn : cap;
+        return ((m + kSortTile - 1) / kSortTile) * 256ull;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// inclusive scan across the block; *total receives the block sum
+template <typename T>
+__device__ __forceinline__ T block_incl_scan(T v, T* smem /* 32 */, T* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_incl_scan(v);
+    if (lane == 31) smem[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < nw ? smem[lane] : T(0);
+        t = warp_incl_scan(t);
+        if (lane < nw) smem[lane] = t;
+    }
+    __syncthreads();
+    T add = wid > 0 ? smem[wid - 1] : T(0);
+    *total = smem[nw - 1];
+    __syncthreads();
+    return v + add;
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const TI* __restrict__ in, LenSpec L,
+                                                              TO* __restrict__ part, const DevState* st)
+{
+    if (st && st->overflow) return;
+    __shared__ TO sm[32];
+    unsigned long long len = L.get();
+    unsigned long long chunk = (len + gridDim.x - 1) / gridDim.x;
+    unsigned long long b0 = (unsigned long long)blockIdx.x * chunk;
+    unsigned long long b1 = b0 + chunk < len ? b0 + chunk : len;
+    TO sum = 0;
+    for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) sum += (TO)in[i];
+    TO tot;
+    block_incl_scan<TO>(sum, sm, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(TO* __restrict__ part, int nb, TO* total_out,
+                                                           const DevState* st)
+{
+    if (st && st->overflow) return;
+    __shared__ TO sm[32];
+    TO v = threadIdx.x < nb ? part[threadIdx.x] : TO(0);
+    TO tot;
+    TO incl = block_incl_scan<TO>(v, sm, &tot);
+    if (threadIdx.x < nb) part[threadIdx.x] = incl - v;
+    if (threadIdx.x == 0 && total_out) *total_out = tot;
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const TI* in, TO* out, LenSpec L,
+                                                            const TO* __restrict__ part, const DevState* st)
+{
+    if (st && st->overflow) return;
+    __shared__ TO sm[32];
+    unsigned long long len = L.get();
+    unsigned long long chunk = (len + gridDim.x - 1) / gridDim.x;
+    unsigned long long b0 = (unsigned long long)blockIdx.x * chunk;
+    unsigned long long b1 = b0 + chunk < len ? b0 + chunk : len;
+    TO carry = part[blockIdx.x];
+    for (unsigned long long base = b0; base < b1; base += blockDim.x) {
+        unsigned long long i = base + threadIdx.x;
+        TO v = i < b1 ? (TO)in[i] : TO(0);
+        TO tot;
+        TO incl = block_incl_scan<TO>(v, sm, &tot);
+        if (i < b1) out[i] = carry + incl - v;
+        carry += tot;
+    }
+}
+
+__global__ void k_check_cap(DevState* st, const unsigned long long* total, unsigned long long cap, int iter)
+{
+    unsigned long long t = *total;
+    st->total = t;
+    if (t > st->max_total) st->max_total = t;
+    if (t > cap && !st->overflow) {
+        st->overflow = 1;
+        st->first_overflow_iter = iter;
+    }
+}
+
+void launch_offsets(const uint32_t* counts, long long n, unsigned long long* offsets, void* scanp, DevState* st,
+                    unsigned long long cap, int iter, cudaStream_t s)
+{
+    LenSpec L{nullptr, 0, (unsigned long long)n};
+    auto* part = reinterpret_cast<unsigned long long*>(scanp);
+    k_scan_reduce<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(counts, L, part, nullptr);
+    k_scan_top<unsigned long long><<<1, kScanThreads, 0, s>>>(part, kScanBlocks, offsets + n, nullptr);
+    k_scan_down<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(counts, offsets, L, part, nullptr);
+    k_check_cap<<<1, 1, 0, s>>>(st, offsets + n, cap, iter);
+}
+
+void launch_exscan_u32(const uint32_t* in, long long n, unsigned long long* out, void* scanp, cudaStream_t s)
+{
+    LenSpec L{nullptr, 0, (unsigned long long)n};
+    auto* part = reinterpret_cast<unsigned long long*>(scanp);
+    k_scan_reduce<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(in, L, part, nullptr);
+    k_scan_top<unsigned long long><<<1, kScanThreads, 0, s>>>(part, kScanBlocks, out + n, nullptr);
+    k_scan_down<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(in, out, L, part, nullptr);
+}
+
+static int emit_blocks(long long n)
+{
+    long long warps = n;
+    long long blocks = (warps * 32 + 255) / 256;
+    if (blocks > 148 * 64) blocks = 148 * 64;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+void launch_count(const BinRec* br, const float4* rec, long long n, const BinGeom& g, uint32_t* counts,
+                   cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_count<<<emit_blocks(n), 256, 0, s>>>(br, rec, n, g, counts);
+}
+
+void launch_emit(const BinRec* br, const float4* rec, const unsigned long long* offsets, long long n,
+                  const BinGeom& g, uint32_t* keys, uint32_t* vals, const DevState* st, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_emit<<<emit_blocks(n), 256, 0, s>>>(br, rec, offsets, n, g, keys, vals, st);
+}
+
+// ------------------------------------------------------------------------
+// stable LSD radix sort
+// ------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long sort_len(const DevState* st, unsigned long long cap)
+{
+    unsigned long long t = st->total;
+    return t < cap ? t : cap;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys, const DevState* st,
+                                                          unsigned long long cap, int shift,
+                                                          uint32_t* __restrict__ hist)
+{
+    if (st->overflow) return;
+    __shared__ uint32_t h[256];
+    unsigned long long n = sort_len(st, cap);
+    unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        unsigned long long base = tile * kSortTile;
+#pragma unroll 4
+        for (int it = 0; it < kSortItems; ++it) {
+            unsigned long long idx = base + (unsigned long long)it * kSortThreads + threadIdx.x;
+            if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        hist[(unsigned long long)threadIdx.x * ntiles + tile] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                             const uint32_t* __restrict__ vin,
+                                                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                             const DevState* st, unsigned long long cap, int shift,
+                                                             const uint32_t* __restrict__ hist)
+{
+    if (st->overflow) return;
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t wcnt[W][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long n = sort_len(st, cap);
+    unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
+    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+        __syncwarp();
+        unsigned long long base = tile * kSortTile + (unsigned long long)w * (32 * kSortItems);
+        uint32_t kk[kSortItems], vv[kSortItems];
+        uint16_t rk[kSortItems];
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            unsigned long long idx = base + (unsigned long long)r * 32 + lane;
+            bool valid = idx < n;
+            uint32_t key = valid ? kin[idx] : 0xffffffffu;
+            uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            int leader = __ffs(peers) - 1;
+            uint32_t prior = valid ? wcnt[w][d] : 0u;
+            __syncwarp();
+            if (valid && lane == leader) wcnt[w][d] = prior + __popc(peers);
+            __syncwarp();
+            kk[r] = key;
+            vv[r] = valid ? vin[idx] : 0u;
+            rk[r] = (uint16_t)(prior + __popc(peers & lt));
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;  // kSortThreads == 256 digits
+            uint32_t run = hist[(unsigned long long)d * ntiles + tile];
+#pragma unroll
+            for (int ww = 0; ww < W; ++ww) {
+                uint32_t c = wcnt[ww][d];
+                wcnt[ww][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            unsigned long long idx = base + (unsigned long long)r * 32 + lane;
+            if (idx < n) {
+                uint32_t d = (kk[r] >> shift) & 255u;
+                uint32_t pos = wcnt[w][d] + rk[r];
+                kout[pos] = kk[r];
+                vout[pos] = vv[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsigned long long cap, int key_bits,
+                uint32_t* hist, void* scanp, cudaStream_t s)
+{
+    static_assert(kSortThreads == 256, "one thread per digit in the scatter");
+    int passes = (key_bits + 7) / 8;
+    unsigned long long max_tiles = (cap + kSortTile - 1) / kSortTile;
+    int grid = (int)(max_tiles < 148ull * 8 ? max_tiles : 148ull * 8);
+    if (grid < 1) grid = 1;
+    int cur = 0;
+    auto* part = reinterpret_cast<uint32_t*>(scanp);
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_hist<<<grid, kSortThreads, 0, s>>>(keys[cur], st, cap, shift, hist);
+        LenSpec L{&st->total, cap, 0};
+        k_scan_reduce<uint32_t, uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(hist, L, part, st);
+        k_scan_top<uint32_t><<<1, kScanThreads, 0, s>>>(part, kScanBlocks, nullptr, st);
+        k_scan_down<uint32_t, uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(hist, hist, L, part, st);
+        k_rs_scatter<<<grid, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], st, cap,
+                                                   shift, hist);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+// ------------------------------------------------------------------------
+// ranges
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ sk, const DevState* st,
+                                                unsigned long long cap, uint32_t* __restrict__ start,
+                                                uint32_t* __restrict__ end)
+{
+    if (st->overflow) return;
+    unsigned long long n = sort_len(st, cap);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t k = sk[i];
+        if (i == 0 || sk[i - 1] != k) start[k] = (uint32_t)i;
+        if (i + 1 == n || sk[i + 1] != k) end[k] = (uint32_t)(i + 1);
+    }
+}
+
+void launch_ranges(const uint32_t* skeys, const DevState* st, unsigned long long cap, uint32_t* start,
+                   uint32_t* end, cudaStream_t s)
+{
+    k_ranges<<<148 * 16, 256, 0, s>>>(skeys, st, cap, start, end);
+}
+
+}  // namespace gve

@@ -1,0 +1,165 @@
+// gve_int.cuh -- internal declarations of libgve (sm_103a).
+//
+// Data layout in HBM (per context):
+//   prepped record  3 x float4 per Gaussian:
+//       r0 = (mu_x, mu_y, mu_z, qxx)      r1 = (qyy, qzz, qxy2, qxz2)
+//       r2 = (qyz2, alpha = w a, beta = w, 0)
+//     q.. = float32(-0.5 log2(e) Sigma^-1) entries (off-diagonals doubled),
+//     rounded once from an FP64 computation in a fixed order.
+//   bin record      20 words per Gaussian: whitening L (row-major 3x3),
+//                   brick half-extent bound e[3], threshold K2, brick box
+//                   lo[3] / hi[3], non-empty flag.
+//   pair list       keys (brick index, z-major) and values (Gaussian index),
+//                   uint32, double-buffered for the radix sort.
+//   ranges          uint32 start[nbricks], end[nbricks].
+//   accumulators    float[12] per Gaussian: A, Bs, S1 (3), S2 (6: xx yy zz
+//                   xy xz yz), 0 -- the per-Gaussian sums of the backward.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/gve.h"
+
+namespace gve {
+
+constexpr int kBrickThreads = 256;
+constexpr int kChunk = 128;          // Gaussian records staged per shared-memory chunk
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanBlocks = 512;
+constexpr int kScanThreads = 1024;
+constexpr double kNegHalfLog2e = -0.72134752044448170367996234050095;
+
+struct __align__(16) BinRec {
+    float L[9];
+    float e[3];
+    float K2;
+    int blo[3];
+    int bhi[3];
+    int nonempty;
+};
+static_assert(sizeof(BinRec) == 80, "bin record is 20 words");
+
+// Device-side state of one call: pair totals and the sticky overflow flag.
+struct DevState {
+    unsigned long long total;        // pairs of the current binning
+    unsigned long long max_total;    // largest total seen since reset
+    int overflow;                    // sticky: an iteration needed more than cap pairs
+    int first_overflow_iter;         // first iteration that overflowed
+    int err;                         // internal consistency error
+    int pad;
+    double sse[2];                   // {masked, unmasked} SSE of the last reduction
+    unsigned long long kept;         // kept (voxel, Gaussian) pairs (counting mode)
+    unsigned long long cand;         // candidate pairs visited (counting mode)
+};
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace gve
+
+struct gve_ctx {
+    int device = 0;
+    std::string err;
+    gve::Buf rec, binrec, counts, offsets, acc, adam;
+    gve::Buf keys[2], vals[2];
+    uint64_t cap = 0;                // pair capacity of keys/vals
+    gve::Buf hist, scanp;
+    gve::Buf ranges, part;
+    gve::Buf state;
+    gve::DevState* hstate = nullptr; // pinned host mirror
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // allocator scratch
+    gve::Buf a_g, a_keys, a_sel, a_tmp, a_cnt;
+    gve::Buf trace;                  // loss trace when the caller passes none
+    // per-iteration stage events of one refine segment: before binning,
+    // before the brick evaluator, after it
+    cudaEvent_t sev[3][64] = {};
+    bool sev_ready = false;
+    long long launches = 0;          // kernels launched by the current call
+};
+
+namespace gve {
+
+// ---- device helpers ------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---- launchers (bin.cu) --------------------------------------------------
+struct BinGeom {
+    int nx, ny, nz, B, nbx, nby, nbz;
+    long long nbricks;
+    int key_bits;
+};
+BinGeom make_geom(gve_dims d, int B);
+
+void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec,
+                 BinRec* br, cudaStream_t s);
+void launch_count(const BinRec* br, const float4* rec, long long n, const BinGeom& g, uint32_t* counts,
+                  cudaStream_t s);
+// exclusive scan of counts into offsets[0..n], total into st->total / max_total,
+// sets st->overflow when total > cap (iteration index `iter`).
+void launch_offsets(const uint32_t* counts, long long n, unsigned long long* offsets, void* scanp,
+                    DevState* st, unsigned long long cap, int iter, cudaStream_t s);
+void launch_emit(const BinRec* br, const float4* rec, const unsigned long long* offsets, long long n,
+                 const BinGeom& g, uint32_t* keys, uint32_t* vals, const DevState* st, cudaStream_t s);
+// Stable LSD radix sort of (keys, vals) by key; result ends in keys[out], vals[out].
+int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsigned long long cap,
+                int key_bits, uint32_t* hist, void* scanp, cudaStream_t s);
+void launch_ranges(const uint32_t* skeys, const DevState* st, unsigned long long cap,
+                   uint32_t* start, uint32_t* end, cudaStream_t s);
+
+// ---- launchers (field.cu) ------------------------------------------------
+enum BrickMode { kModeEval = 0, kModeLoss = 1, kModeBwd = 2, kModeCount = 3 };
+struct BrickArgs {
+    BinGeom g;
+    const uint32_t* start;
+    const uint32_t* end;
+    const uint32_t* gids;
+    const float4* rec;
+    const float* field;        // target V (loss) or nullptr
+    const float* upstream;     // dL/dVtilde (backward mode)
+    float* field_out;          // Vtilde (eval mode) or nullptr
+    float* acc;                // [n][12] accumulators (loss/bwd)
+    double2* part;             // per-brick {masked, unmasked} SSE
+    DevState* st;
+    float T;                   // float32 keep threshold
+    float rho0;
+    int normalized;
+    float mask_thresh;         // < 0: no mask
+    float inv_m;               // 1 / (nx ny nz)
+};
+void launch_brick(int mode, const BrickArgs& a, cudaStream_t s);
+// deterministic reduction of per-brick partials; writes st->sse and, if
+// trace != nullptr, trace[iter] = sse_masked * inv_m.
+void launch_sse_reduce(const double2* part, long long nbricks, DevState* st, double* trace, int iter,
+                       double inv_m, cudaStream_t s);
+
+// ---- launchers (optim.cu) ------------------------------------------------
+struct AdamArgs {
+    float lr, b1, b2, eps;
+    float bc1, bc2;  // 1 - beta^t
+};
+// chain rule from accumulators to raw-record gradients; either writes grad
+// (grad != nullptr) or applies Adam in place (prims, m, v).  Zeroes acc.
+void launch_chain(const float* acc_in, float* acc_zero, float* prims, long long n, float* grad,
+                  float* m, float* v, const AdamArgs* adam, const DevState* st, cudaStream_t s);
+
+// ---- allocator (alloc.cu) ------------------------------------------------
+gve_status allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget,
+                    const gve_alloc_opts* o, float* prims, int64_t* feasible_max,
+                    gve_alloc_info* info, cudaStream_t s);
+
+// ---- context scratch (api.cu) ---------------------------------------------
+gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
+gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what);
+
+}  // namespace gve

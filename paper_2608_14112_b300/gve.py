@@ -1,0 +1,297 @@
+"""Thin Python binding of libgve (include/gve.h) -- argument marshalling only.
+
+Every step of the encoder runs in the CUDA kernels of ``libgve.so``; this
+module only checks tensor shapes, dtypes and devices, passes raw device
+pointers and the current torch stream through ctypes, and turns status codes
+into exceptions.  There is no CPU fallback: without the built library or a
+CUDA device every call raises.
+
+Names follow the C ABI: ``gve_allocate``, ``gve_evaluate``, ``gve_loss_grad``,
+``gve_backward``, ``gve_refine``, ``gve_bin``, ``gve_count_pairs``.
+Primitive records are float32 ``(N, 12)`` tensors in the order
+``mu(3), log s(3), q(w,x,y,z), a, w_logit`` (48 bytes each, Eq. 2 / Eq. 7 of
+arxiv 2608.14112); fields are float32 ``(nz, ny, nx)``, x fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+from pathlib import Path
+
+import torch
+
+_HERE = Path(__file__).resolve().parent
+LIB_PATH = _HERE / "libgve.so"
+
+GVE_OK, GVE_E_INVALID, GVE_E_BUDGET, GVE_E_NOMEM, GVE_E_CUDA, GVE_E_TIMEOUT, GVE_E_CAPACITY, GVE_E_INTERNAL = range(8)
+
+
+class GveError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libgve status {status}: {msg}")
+        self.status = status
+
+
+class BudgetError(GveError):
+    """The field cannot support the requested budget (paper Sec. V-B)."""
+
+    def __init__(self, msg: str, feasible_max: int):
+        super().__init__(GVE_E_BUDGET, msg)
+        self.feasible_max = feasible_max
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class EvalOpts(ctypes.Structure):
+    _fields_ = [("trunc_k", ctypes.c_float), ("rho0", ctypes.c_float), ("normalized", ctypes.c_int32),
+                ("brick", ctypes.c_int32)]
+
+
+class AllocOpts(ctypes.Structure):
+    _fields_ = [("detail_frac", ctypes.c_double), ("w0", ctypes.c_double), ("occ_thresh", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("mask_thresh", ctypes.c_float),
+                ("step0", ctypes.c_int32), ("eval", EvalOpts)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("sse_final", ctypes.c_double),
+                ("psnr_final", ctypes.c_double), ("brick_pairs", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("iters_done", ctypes.c_int32), ("retries", ctypes.c_int32), ("ms_total", ctypes.c_float),
+                ("ms_brick", ctypes.c_float), ("ms_bin", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class AllocInfo(ctypes.Structure):
+    _fields_ = [("n_occupied", ctypes.c_int64), ("n_eligible", ctypes.c_int64), ("n_detail", ctypes.c_int64),
+                ("n_coverage", ctypes.c_int64), ("gbar", ctypes.c_double), ("h_detail", ctypes.c_double),
+                ("h_coverage", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+
+def lib():
+    """Load libgve.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not LIB_PATH.exists():
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_2608_14112_b300/build.py (no CPU fallback)")
+            L = ctypes.CDLL(str(LIB_PATH))
+            P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            st = ctypes.c_int
+            L.gve_ctx_create.argtypes = [ctypes.POINTER(P), i32]
+            L.gve_ctx_create.restype = st
+            L.gve_ctx_destroy.argtypes = [P]
+            L.gve_ctx_destroy.restype = None
+            L.gve_status_str.argtypes = [st]
+            L.gve_status_str.restype = ctypes.c_char_p
+            L.gve_last_error.argtypes = [P]
+            L.gve_last_error.restype = ctypes.c_char_p
+            L.gve_allocate.argtypes = [P, P, Dims, i64, ctypes.POINTER(AllocOpts), P, ctypes.POINTER(i64),
+                                       ctypes.POINTER(AllocInfo), P]
+            L.gve_evaluate.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P]
+            L.gve_loss_grad.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(EvalOpts), ctypes.c_float, P, P, P]
+            L.gve_backward.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P]
+            L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
+            L.gve_bin.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P, i64, P, ctypes.POINTER(i64), P]
+            L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i64), P]
+            for f in ("gve_allocate", "gve_evaluate", "gve_loss_grad", "gve_backward", "gve_refine", "gve_bin",
+                      "gve_count_pairs"):
+                getattr(L, f).restype = st
+            _lib = L
+    return _lib
+
+
+def context(device: int | None = None) -> ctypes.c_void_p:
+    """Per-device library context (created on first use)."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("libgve needs a CUDA device (no CPU fallback)")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    with _lock:
+        c = _ctx.get(dev)
+    if c is None:
+        h = ctypes.c_void_p()
+        s = lib().gve_ctx_create(ctypes.byref(h), dev)
+        if s != GVE_OK:
+            raise GveError(s, "gve_ctx_create failed")
+        with _lock:
+            _ctx[dev] = h
+        c = h
+    return c
+
+
+def _check(s: int, ctx) -> None:
+    if s != GVE_OK:
+        raise GveError(s, lib().gve_last_error(ctx).decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(dev: torch.device):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _prims(p: torch.Tensor) -> torch.Tensor:
+    if p.dtype != torch.float32 or p.dim() != 2 or p.shape[1] != 12 or not p.is_cuda or not p.is_contiguous():
+        raise ValueError("primitives must be a contiguous CUDA float32 tensor of shape (N, 12)")
+    return p
+
+
+def _field(f: torch.Tensor) -> torch.Tensor:
+    if f.dtype != torch.float32 or f.dim() != 3 or not f.is_cuda or not f.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA float32 tensor of shape (nz, ny, nx)")
+    return f
+
+
+def _dims(shape) -> Dims:
+    nz, ny, nx = (int(s) for s in shape)
+    return Dims(nx, ny, nz)
+
+
+@dataclass
+class EvalOptions:
+    trunc_k: float = 3.0
+    rho0: float = 0.05
+    normalized: bool = True
+    brick: int = 8
+
+    def c(self) -> EvalOpts:
+        return EvalOpts(float(self.trunc_k), float(self.rho0), int(bool(self.normalized)), int(self.brick))
+
+
+def gve_evaluate(prims: torch.Tensor, shape, opts: EvalOptions | None = None, out: torch.Tensor | None = None):
+    """Eq. 3 at every voxel centre of a grid of ``shape = (nz, ny, nx)``."""
+    prims = _prims(prims)
+    o = (opts or EvalOptions()).c()
+    if out is None:
+        out = torch.empty(tuple(int(s) for s in shape), dtype=torch.float32, device=prims.device)
+    _field(out)
+    c = context(prims.device.index)
+    _check(lib().gve_evaluate(c, _ptr(prims), prims.shape[0], _dims(out.shape), ctypes.byref(o), _ptr(out),
+                              _stream(prims.device)), c)
+    return out
+
+
+def gve_loss_grad(prims: torch.Tensor, field: torch.Tensor, opts: EvalOptions | None = None,
+                  mask_thresh: float = -1.0):
+    """(dL/dprims (N,12), sse (2,) float64 = {masked, unmasked}) of the
+    full-grid mean squared error at the current parameters."""
+    prims, field = _prims(prims), _field(field)
+    o = (opts or EvalOptions()).c()
+    grad = torch.empty_like(prims)
+    sse = torch.empty(2, dtype=torch.float64, device=prims.device)
+    c = context(prims.device.index)
+    _check(lib().gve_loss_grad(c, _ptr(prims), prims.shape[0], _ptr(field), _dims(field.shape), ctypes.byref(o),
+                               float(mask_thresh), _ptr(grad), _ptr(sse), _stream(prims.device)), c)
+    return grad, sse
+
+
+def gve_backward(prims: torch.Tensor, grad_field: torch.Tensor, opts: EvalOptions | None = None):
+    """dL/dprims for an arbitrary upstream dL/dVtilde (recomputes per brick)."""
+    prims, grad_field = _prims(prims), _field(grad_field)
+    o = (opts or EvalOptions()).c()
+    grad = torch.empty_like(prims)
+    c = context(prims.device.index)
+    _check(lib().gve_backward(c, _ptr(prims), prims.shape[0], _dims(grad_field.shape), ctypes.byref(o),
+                              _ptr(grad_field), _ptr(grad), _stream(prims.device)), c)
+    return grad
+
+
+def gve_refine(prims: torch.Tensor, field: torch.Tensor, iters: int, lr: float = 1e-2, beta1: float = 0.9,
+               beta2: float = 0.999, eps: float = 1e-15, mask_thresh: float = -1.0, step0: int = 0,
+               opts: EvalOptions | None = None, adam_state: torch.Tensor | None = None,
+               trace: torch.Tensor | None = None, want_stats: bool = True):
+    """Fixed-budget refinement in place on ``prims``.  Returns a dict of the
+    host statistics (or None when ``want_stats`` is False: no synchronisation
+    beyond the capacity checks)."""
+    prims, field = _prims(prims), _field(field)
+    sched = Schedule(int(iters), float(lr), float(beta1), float(beta2), float(eps), float(mask_thresh), int(step0),
+                     (opts or EvalOptions()).c())
+    if adam_state is not None:
+        if adam_state.shape != (2, prims.shape[0], 12) or adam_state.dtype != torch.float32 or not adam_state.is_contiguous():
+            raise ValueError("adam_state must be float32 (2, N, 12)")
+    if trace is not None and (trace.dtype != torch.float64 or trace.numel() < iters or not trace.is_cuda):
+        raise ValueError("trace must be a CUDA float64 tensor with >= iters entries")
+    st = Stats()
+    c = context(prims.device.index)
+    _check(lib().gve_refine(c, _ptr(prims), prims.shape[0], _ptr(field), _dims(field.shape), ctypes.byref(sched),
+                            _ptr(adam_state), _ptr(trace), ctypes.byref(st) if want_stats else None,
+                            _stream(prims.device)), c)
+    if not want_stats:
+        return None
+    return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def gve_allocate(field: torch.Tensor, budget: int, detail_frac: float = 0.55, occ_thresh: float = 0.02,
+                 w0: float = 0.1, seed: int = 0, out: torch.Tensor | None = None):
+    """Analytic fixed-budget allocation (Sec. III-E).  Returns (prims (N,12),
+    info dict); raises BudgetError (with ``feasible_max``) when the field
+    cannot support the budget."""
+    field = _field(field)
+    if out is None:
+        out = torch.empty((int(budget), 12), dtype=torch.float32, device=field.device)
+    _prims(out)
+    o = AllocOpts(float(detail_frac), float(w0), float(occ_thresh), 0, int(seed) & (2 ** 64 - 1))
+    fm = ctypes.c_int64(0)
+    info = AllocInfo()
+    c = context(field.device.index)
+    s = lib().gve_allocate(c, _ptr(field), _dims(field.shape), int(budget), ctypes.byref(o), _ptr(out),
+                           ctypes.byref(fm), ctypes.byref(info), _stream(field.device))
+    if s == GVE_E_BUDGET:
+        raise BudgetError(lib().gve_last_error(c).decode(), int(fm.value))
+    _check(s, c)
+    return out, {name: getattr(info, name) for name, _ in AllocInfo._fields_}
+
+
+def gve_bin(prims: torch.Tensor, shape, opts: EvalOptions | None = None, cap: int | None = None):
+    """The (brick, Gaussian) pairs of the binner: (counts (N,), keys, gids,
+    start, end) as int64 CPU tensors for inspection."""
+    prims = _prims(prims)
+    o = (opts or EvalOptions()).c()
+    d = _dims(shape)
+    B = int(o.brick)
+    nb = ((d.nx + B - 1) // B) * ((d.ny + B - 1) // B) * ((d.nz + B - 1) // B)
+    c = context(prims.device.index)
+    dev = prims.device
+    n = prims.shape[0]
+    counts = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ranges = torch.empty(2 * nb, dtype=torch.int32, device=dev)
+    npairs = ctypes.c_int64(0)
+    if cap is None:
+        kk = torch.empty(1, dtype=torch.int32, device=dev)
+        s = lib().gve_bin(c, _ptr(prims), n, d, ctypes.byref(o), _ptr(counts), _ptr(kk), _ptr(kk), 0,
+                          _ptr(ranges), ctypes.byref(npairs), _stream(dev))
+        if s not in (GVE_OK, GVE_E_CAPACITY):
+            _check(s, c)
+        cap = int(npairs.value)
+    keys = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    gids = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    _check(lib().gve_bin(c, _ptr(prims), n, d, ctypes.byref(o), _ptr(counts), _ptr(keys), _ptr(gids), cap,
+                         _ptr(ranges), ctypes.byref(npairs), _stream(dev)), c)
+    m = int(npairs.value)
+    u32 = lambda t: t.cpu().to(torch.int64) & 0xFFFFFFFF
+    return (u32(counts[:n]), u32(keys[:m]), u32(gids[:m]), u32(ranges[:nb]), u32(ranges[nb:]))
+
+
+def gve_count_pairs(prims: torch.Tensor, shape, opts: EvalOptions | None = None):
+    """(kept pairs, candidate pairs) of one evaluation."""
+    prims = _prims(prims)
+    o = (opts or EvalOptions()).c()
+    kept, cand = ctypes.c_int64(0), ctypes.c_int64(0)
+    c = context(prims.device.index)
+    _check(lib().gve_count_pairs(c, _ptr(prims), prims.shape[0], _dims(shape), ctypes.byref(o), ctypes.byref(kept),
+                                 ctypes.byref(cand), _stream(prims.device)), c)
+    return int(kept.value), int(cand.value)

@@ -102,39 +102,47 @@ def _interp_matrix(n: int, L: int, dtype, device):
 
 
 def fbm_fronts(n: int = 1024, seed: int = 4, octaves: int = 6, device="cpu",
-               as_numpy: bool = False):
+               as_numpy: bool = False, region=None):
     """Six-octave value-noise fBm (lattice (4*2^o+1)^3 of iid U[-1,1], gain
     1/2, trilinear upsampling) plus three fronts 0.5 tanh(n_j.(p - p_j)/2)
-    with n_j uniform on the sphere and p_j in U[n/4, 3n/4)^3.  Returns a
-    float32 torch tensor on ``device`` (numpy if ``as_numpy``)."""
+    with n_j uniform on the sphere and p_j in U[n/4, 3n/4)^3, min-max
+    normalised.  Returns a float32 torch tensor on ``device`` (numpy if
+    ``as_numpy``).  ``region = ((x0, y0, z0), (sx, sy, sz))`` draws only that
+    sub-box of the n^3 field (same lattices and fronts), normalised by its own
+    min and max."""
     if torch is None:
         raise RuntimeError("fbm_fronts needs torch")
     rng = np.random.Generator(np.random.PCG64(seed))
     dev = torch.device(device)
     dt = torch.float32
-    V = torch.zeros((n, n, n), dtype=dt, device=dev)
+    if region is None:
+        r0, rs = (0, 0, 0), (n, n, n)
+    else:
+        r0, rs = tuple(int(v) for v in region[0]), tuple(int(v) for v in region[1])
+    x0, y0, z0 = r0
+    sx, sy, sz = rs
+    V = torch.zeros((sz, sy, sx), dtype=dt, device=dev)
     amp = 1.0
     for o in range(octaves):
         L = 4 * 2 ** o + 1
-        lat = torch.from_numpy(rng.uniform(-1.0, 1.0, size=(L, L, L))).to(dev, dt)  # (c,b,a)=(z,y,x)
+        lat = torch.from_numpy(rng.uniform(-1.0, 1.0, size=(L, L, L))).to(dev, dt)  # (z, y, x)
         W = _interp_matrix(n, L, dt, dev)
-        t = torch.matmul(lat, W.T)                              # (Lz, Ly, n)
-        t = torch.matmul(W, t)                                  # (Lz, n, n)  contract y
-        t = torch.matmul(W, t.reshape(L, n * n)).reshape(n, n, n)  # contract z
+        Wx, Wy, Wz = W[x0:x0 + sx], W[y0:y0 + sy], W[z0:z0 + sz]
+        t = torch.matmul(lat, Wx.T)                                   # (Lz, Ly, sx)
+        t = torch.matmul(Wy, t)                                       # (Lz, sy, sx)
+        t = torch.matmul(Wz, t.reshape(L, sy * sx)).reshape(sz, sy, sx)
         V.add_(t, alpha=amp)
         del t
         amp *= 0.5
-    coords = torch.arange(n, dtype=dt, device=dev)
     for _ in range(3):
         nv = rng.standard_normal(3)
         nv /= np.linalg.norm(nv)
         pj = rng.uniform(n / 4, 3 * n / 4, size=3)
-        # n.(p - pj) separably: nx*(x-px) + ny*(y-py) + nz*(z-pz)
-        sx = (coords - float(pj[0])) * float(nv[0])
-        sy = (coords - float(pj[1])) * float(nv[1])
-        sz = (coords - float(pj[2])) * float(nv[2])
-        for zi in range(0, n, 64):
-            arg = sz[zi:zi + 64, None, None] + sy[None, :, None] + sx[None, None, :]
+        sxv = (torch.arange(x0, x0 + sx, dtype=dt, device=dev) - float(pj[0])) * float(nv[0])
+        syv = (torch.arange(y0, y0 + sy, dtype=dt, device=dev) - float(pj[1])) * float(nv[1])
+        szv = (torch.arange(z0, z0 + sz, dtype=dt, device=dev) - float(pj[2])) * float(nv[2])
+        for zi in range(0, sz, 64):
+            arg = szv[zi:zi + 64, None, None] + syv[None, :, None] + sxv[None, None, :]
             V[zi:zi + 64].add_(torch.tanh(arg * 0.5), alpha=0.5)
     lo, hi = V.min(), V.max()
     V.sub_(lo).div_(hi - lo)

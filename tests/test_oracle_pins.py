@@ -526,3 +526,33 @@ def test_allocation_infeasible_reports_shortfall():
     assert fm == O.feasible_max(1000, 0.55, st["n_eligible"], st["n_occupied"])
     prm, vox, st2, status = O.allocate(V, fm, seed=1)
     assert status == 0 and prm.shape[0] == fm
+
+
+def test_backward_upstream_central_differences():
+    """dL/dtheta for L = sum_p U(p) Vt(p), U arbitrary: central differences
+    of the frozen-membership field (the backward of Eq. 3 alone)."""
+    rng = np.random.default_rng(31)
+    dims = (10, 9, 11)
+    prm = _rand_prims(rng, 4, dims, s_lo=1.0, s_hi=2.0)
+    U = rng.normal(size=(11, 9, 10))
+    g = O.backward(prm, U)
+    h = 3e-5
+    for i in range(prm.shape[0]):
+        for j in range(12):
+            pp, pm = prm.copy(), prm.copy()
+            pp[i, j] += h
+            pm[i, j] -= h
+            Lp = float((U * O.eval_region(pp, dims, pred_prm=prm)[2]).sum())
+            Lm = float((U * O.eval_region(pm, dims, pred_prm=prm)[2]).sum())
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g[i, j]) <= 2e-6 * max(abs(fd), 1e-3), (i, j, fd, g[i, j])
+
+
+def test_count_kept_brute_force():
+    rng = np.random.default_rng(6)
+    dims = (9, 8, 7)
+    p32 = _rand_prims(rng, 6, dims).astype(np.float32)
+    T = O.pred_threshold(3.0)
+    brute = sum(O.pred_t(p32[i], x, y, z) > T for i in range(6)
+                for z in range(7) for y in range(8) for x in range(9))
+    assert O.count_kept(p32, dims, 3.0) == brute

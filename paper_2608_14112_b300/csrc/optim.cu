@@ -16,7 +16,8 @@
 
 namespace gve {
 
-__global__ void __launch_bounds__(128) k_chain(const float* __restrict__ acc, float* acc_zero,
+// acc and acc_zero may be the same buffer (read, then cleared): no __restrict__
+__global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero,
                                                float* __restrict__ prims, long long n, float* __restrict__ grad,
                                                float* __restrict__ m, float* __restrict__ v, AdamArgs ad,
                                                int do_adam, const DevState* st)

@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headline", "small", "autograd"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "mid", "small", "autograd"], default="headline")
     ap.add_argument("--e2e-iters", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample", type=int, default=192, help="edge of the CPU sample sub-volume")
@@ -65,6 +65,8 @@ def parse():
 def workload(name):
     if name == "headline":
         return dict(name="fbm_fronts_1024^3_N1.4M", n=1024, budget=1_400_000, kind="fbm_fronts", seed=4, lr=1e-2)
+    if name == "mid":
+        return dict(name="fbm_fronts_512^3_N175000", n=512, budget=175_000, kind="fbm_fronts", seed=4, lr=1e-2)
     if name == "autograd":
         return dict(name="grf_256^3_N65536", n=256, budget=65_536, kind="grf", seed=2, lr=1e-2)
     return dict(name="blobs_64^3_N4096", n=64, budget=4096, kind="blobs", seed=1, lr=1e-2)

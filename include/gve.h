@@ -25,6 +25,8 @@
  * Errors.     Every entry point returns a gve_status; nothing aborts or
  *             throws across the ABI.  gve_last_error() gives a message.
  *             Invalid arguments are rejected before any launch.
+ * Counts.     At most 2^24 (16,777,216) primitives per call; grid axes up to
+ *             2^24 voxels with fewer than 2^31 bricks of 8^3.
  * Threads.    A context may be used by one host thread at a time.
  */
 #ifndef GVE_H

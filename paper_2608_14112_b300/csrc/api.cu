@@ -47,6 +47,13 @@ gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s)
     return GVE_OK;
 }
 
+__global__ void k_strip_mask(uint32_t* v, unsigned long long n)
+{
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        v[i] &= kGidMask;
+}
+
 __global__ void k_reset_state(DevState* st)
 {
     st->total = 0;
@@ -91,7 +98,7 @@ gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, c
 {
     if (!c) return GVE_E_INVALID;
     if (!o) return fail(c, GVE_E_INVALID, "null options");
-    if (n < 0 || n > (int64_t)INT_MAX) return fail(c, GVE_E_INVALID, "primitive count out of range");
+    if (n < 0 || n > (int64_t)kGidMask + 1) return fail(c, GVE_E_INVALID, "primitive count out of range (max 2^24)");
     if (n > 0 && !prims) return fail(c, GVE_E_INVALID, "null primitive pointer");
     if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "primitives not 16-byte aligned");
     if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
@@ -375,6 +382,7 @@ gve_status gve_bin(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const 
         if (!keys || !gids) return fail(c, GVE_E_INVALID, "null pair outputs");
         GVE_CUDA(cudaMemcpyAsync(keys, c->keys[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
         GVE_CUDA(cudaMemcpyAsync(gids, c->vals[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
+        k_strip_mask<<<592, 256, 0, k.s>>>(gids, h.total);
     }
     GVE_CUDA(cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint32_t) * 2 * k.g.nbricks, cudaMemcpyDeviceToDevice, k.s), "copy");
     GVE_CUDA(cudaStreamSynchronize(k.s), "sync");

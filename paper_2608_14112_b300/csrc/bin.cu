@@ -164,6 +164,43 @@ __device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy
     return sq <= b.K2;
 }
 
+// Sub-brick cover of a listed brick (an acceleration structure of the
+// evaluator, not part of the binning definition): bit s is set when the
+// 8x4x2 sub-brick s = (y half, z pair) may hold a kept pair, by the same
+// whitened-distance lower bound around each sub-brick centre, with half
+// sizes (3.51, 1.51, 0.51) and the brick's K2.  Sub-bricks outside the grid
+// get no bit.  Conservative: it never drops a pair the keep test keeps.
+__device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, float muy, float muz, int bx, int by,
+                                                  int bz, int ny, int nz)
+{
+    const float cx = (float)(bx * 8) + 3.5f, cy = (float)(by * 8) + 3.5f, cz = (float)(bz * 8) + 3.5f;
+    const float dcx = cx - mux, dcy = cy - muy, dcz = cz - muz;
+    float yc[3], ea[3], eb[3], ec[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        yc[j] = fmaf(b.L[j * 3 + 2], dcz, fmaf(b.L[j * 3 + 1], dcy, b.L[j * 3 + 0] * dcx));
+        ea[j] = fabsf(b.L[j * 3 + 0]) * 3.51f + fabsf(b.L[j * 3 + 1]) * 1.51f + fabsf(b.L[j * 3 + 2]) * 0.51f;
+        eb[j] = b.L[j * 3 + 1];
+        ec[j] = b.L[j * 3 + 2];
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+        const int yh = sidx & 1, zp = sidx >> 1;
+        if (by * 8 + 4 * yh >= ny || bz * 8 + 2 * zp >= nz) continue;
+        const float oy = yh ? 2.0f : -2.0f, oz = (float)(2 * zp - 3);
+        float sq = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float y = fmaf(ec[j], oz, fmaf(eb[j], oy, yc[j]));
+            const float a = fmaxf(fabsf(y) - ea[j], 0.f);
+            sq = fmaf(a, a, sq);
+        }
+        if (sq <= b.K2) m |= 1u << sidx;
+    }
+    return m;
+}
+
 // ------------------------------------------------------------------------
 // count / emit (one warp per Gaussian)
 // ------------------------------------------------------------------------
@@ -213,19 +250,20 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
         for (long long t0 = 0; t0 < tot; t0 += 32) {
             long long t = t0 + lane;
             bool pass = false;
-            uint32_t key = 0;
+            uint32_t key = 0, mask = 0;
             if (t < tot) {
                 int bx = b.blo[0] + (int)(t % ex);
                 int by = b.blo[1] + (int)((t / ex) % ey);
                 int bz = b.blo[2] + (int)(t / (ex * ey));
                 pass = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
                 key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
+                if (pass) mask = subbrick_mask(b, r0.x, r0.y, r0.z, bx, by, bz, g.ny, g.nz);
             }
             unsigned bal = __ballot_sync(0xffffffffu, pass);
             if (pass) {
                 unsigned long long pos = base + __popc(bal & lt);
                 keys[pos] = key;
-                vals[pos] = (uint32_t)i;
+                vals[pos] = (uint32_t)i | (mask << kGidBits);
             }
             base += __popc(bal);
         }

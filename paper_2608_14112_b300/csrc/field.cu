@@ -1,29 +1,36 @@
 // field.cu -- the brick evaluator: Eq. 3 forward, residual and SSE, and the
-// backward of the mean squared error, fused per brick of 8^3 voxels.
+// backward of the loss, fused per brick of 8^3 voxels.
 //
-// One CTA (256 threads) per brick.  The brick's Gaussian list is staged in
-// shared memory in chunks of kChunk prepared records (3 x float4 each).
+// One CTA of 64 threads (2 warps) per brick.  The brick's Gaussian list is
+// staged in shared memory in chunks of kCh prepared records (3 x float4),
+// each with the 8-bit sub-brick mask the binner attached: bit s says that the
+// 8x4x2 sub-brick s (y half = s & 1, z pair = s >> 1) may hold a kept pair.
 //
-// Phase 1 (forward, one thread per voxel pair along x): for every listed
-// Gaussian, the keep exponent t is evaluated by the fixed float32 chain
+// Phase 1 (forward): warp w owns the z half [4w, 4w+4) of the brick and each
+// lane one row of 8 voxels along x.  For every listed Gaussian with a live
+// sub-brick in the warp's half (a warp-uniform skip otherwise), the keep
+// exponent t is evaluated by the fixed float32 chain
 //     dy = y - mu_y, dz = z - mu_z, dx = x - mu_x,
 //     b = fma(qxy2, dy, qxz2*dz), c = fma(dy, fma(qyy, dy, qyz2*dz), dz*(qzz*dz)),
 //     t = fma(dx, fma(qxx, dx, b), c)
-// (q.. = -0.5 log2(e) Sigma^-1), the pair is kept iff t > T, and G = 2^t on
-// the SFU (ex2.approx).  num += w a G, den += w G; Vtilde = num/max(den,rho0)
-// (Eq. 3).  Residual r = Vtilde - V, SSE partial per brick in FP64.  The
-// upstream gradient of the loss gives per voxel
-//     gn = dL/dnum = up / max(den, rho0),   gd = dL/dden = -Vtilde gn (den >= rho0)
-// stored in shared memory.
+// (q.. = -0.5 log2(e) Sigma^-1; voxel pairs go through the packed f32x2
+// FMA, lane-wise identical to the scalar chain), the pair is kept iff t > T,
+// and G = 2^t on the SFU (ex2.approx).  num += w a G, den += w G;
+// Vtilde = num / max(den, rho0) (Eq. 3), residual and per-brick SSE
+// (float32 within the CTA, FP64 across CTAs: B300's FP64 rate is a small
+// fraction of its FP32 rate).  The upstream gradient gives per voxel
+// gn = dL/dnum = up / max(den, rho0) and gd = dL/dden = -Vtilde gn (when
+// den >= rho0), kept in shared memory.
 //
-// Phase 2 (backward, one 8-lane group per Gaussian, one lane per z-slice of
-// the brick): each lane walks the 64 voxels of its slice, recomputes G by the
-// same chain, and accumulates
+// Phase 2 (backward): the (Gaussian, live 8x4x2 sub-brick) tasks are
+// compacted (sub-brick-major) and spread over the 64 threads; a task
+// recomputes G by the same chain on its 64 voxels and accumulates
 //     A = sum G gn,  Bs = sum G gd,  S1 = sum h d,  S2 = sum h d d^T,
-//     h = G (alpha gn + beta gd)        (S1, S2 scaled by -1/2 later)
-// with the per-row factorisation of the x-dependence; the 8 lanes reduce by
-// shuffles and one lane issues three 16-byte vector atomics into the
-// Gaussian's accumulator.  Nothing per pair or per voxel goes to HBM.
+//     h = G (alpha gn + beta gd)      (S1, S2 scaled by -1/2 in the chain rule)
+// with the x- and z-dependence factored per row and per slice, in packed
+// f32x2 arithmetic.  Task sums meet in shared memory (float atomics); one
+// thread per Gaussian then issues three 16-byte vector atomics into its
+// global accumulator.  Nothing per pair or per voxel goes to HBM.
 #include "gve_int.cuh"
 
 namespace gve {
@@ -34,14 +41,34 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                  : "memory");
 }
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+constexpr int kAccStride = 13;  // padded per-Gaussian stride of the shared sums
+constexpr int kBT = 64;         // threads per brick CTA (2 warps)
+constexpr int kCh = 64;         // Gaussians staged per chunk
+
+__device__ __forceinline__ void stage_chunk(const BrickArgs& a, uint32_t s0, int c0, int cnt, float4* s_rec,
+                                            uint32_t* s_msk, int tid)
+{
+    for (int j = tid; j < cnt * 3; j += kBT) {
+        const uint32_t v = a.gids[s0 + c0 + j / 3];
+        s_rec[j] = a.rec[3 * (size_t)(v & kGidMask) + (j % 3)];
+        if (j % 3 == 0) s_msk[j / 3] = v >> kGidBits;
+    }
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kBrickThreads, 3) k_brick(const BrickArgs a)
+__global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
 {
     if (a.st->overflow) return;
-    __shared__ float4 s_rec[kChunk * 3];
-    __shared__ float4 s_g[8 * 33];
-    __shared__ double s_red[2][8];
-    __shared__ unsigned s_cnt[8];
+    __shared__ float4 s_rec[kCh * 3];
+    __shared__ uint32_t s_msk[kCh];
+    __shared__ float4 s_g[64 * 4];            // per row: 4 x (gn[x], gn[x+1], gd[x], gd[x+1])
+    __shared__ float s_acc[kCh * kAccStride];
+    __shared__ uint16_t s_task[kCh * 8];
+    __shared__ int s_scan[2];
+    __shared__ float s_red[2][2];
+    __shared__ unsigned long long s_cnt[3][2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const BinGeom& g = a.g;
@@ -53,204 +80,257 @@ __global__ void __launch_bounds__(kBrickThreads, 3) k_brick(const BrickArgs a)
     const int L = (int)(a.end[brick] - s0);
     const float T = a.T;
 
-    // ---------------- phase 1: forward over (x, x+1), y, z ----------------
-    const int xp = tid & 3, ly = (tid >> 2) & 7, lz = tid >> 5;
-    const int gx = bx * 8 + 2 * xp, gy = by * 8 + ly, gz = bz * 8 + lz;
+    // ---------------- phase 1: warp = z half, lane = row of 8 voxels ----------------
+    const int ly = lane & 7, lz = 4 * warp + (lane >> 3);
+    const int gy = by * 8 + ly, gz = bz * 8 + lz, gx0 = bx * 8;
     const bool rowin = gy < g.ny && gz < g.nz;
-    const bool in0 = rowin && gx < g.nx, in1 = rowin && gx + 1 < g.nx;
-    const float fx0 = (float)gx, fx1 = (float)(gx + 1), fy = (float)gy, fz = (float)gz;
-    float num0 = 0.f, den0 = 0.f, num1 = 0.f, den1 = 0.f;
-    unsigned kept = 0;
-    const int nchunks = (L + kChunk - 1) / kChunk;
+    const int nxin = rowin ? min(8, g.nx - gx0) : 0;   // in-grid voxels of the row
+    const float fy = (float)gy, fz = (float)gz;
+    float2 num[4], den[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { num[q] = make_float2(0.f, 0.f); den[q] = num[q]; }
+    unsigned long long kept = 0, live = 0;
+    const int wshift = 4 * warp;
+    const int nchunks = (L + kCh - 1) / kCh;
     for (int ch = 0; ch < nchunks; ++ch) {
-        const int c0 = ch * kChunk;
-        const int cnt = min(kChunk, L - c0);
+        const int c0 = ch * kCh;
+        const int cnt = min(kCh, L - c0);
         if (ch > 0) __syncthreads();
-        for (int j = tid; j < cnt * 3; j += kBrickThreads) {
-            const uint32_t gid = a.gids[s0 + c0 + j / 3];
-            s_rec[j] = a.rec[3 * (size_t)gid + (j % 3)];
-        }
+        stage_chunk(a, s0, c0, cnt, s_rec, s_msk, tid);
         __syncthreads();
-#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
+            if (!((s_msk[j] >> wshift) & 0xFu)) continue;  // warp-uniform skip of the z half
             const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
             const float dy = __fsub_rn(fy, r0.y), dz = __fsub_rn(fz, r0.z);
             const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
             const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
-            const float dx0 = __fsub_rn(fx0, r0.x), dx1 = __fsub_rn(fx1, r0.x);
-            const float t0 = __fmaf_rn(dx0, __fmaf_rn(r0.w, dx0, b), c);
-            const float t1 = __fmaf_rn(dx1, __fmaf_rn(r0.w, dx1, b), c);
-            const float G0 = t0 > T ? ex2_approx(t0) : 0.f;
-            const float G1 = t1 > T ? ex2_approx(t1) : 0.f;
-            if (MODE == kModeCount) kept += (unsigned)((t0 > T) && in0) + (unsigned)((t1 > T) && in1);
-            num0 = fmaf(r2.y, G0, num0);
-            den0 = fmaf(r2.z, G0, den0);
-            num1 = fmaf(r2.y, G1, num1);
-            den1 = fmaf(r2.z, G1, den1);
+            const float2 nmu = f2(-r0.x), qxx = f2(r0.w), b2 = f2(b), c2 = f2(c), al = f2(r2.y), be = f2(r2.z);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 dx = __fadd2_rn(make_float2((float)(gx0 + 2 * q), (float)(gx0 + 2 * q + 1)), nmu);
+                const float2 t = __ffma2_rn(dx, __ffma2_rn(qxx, dx, b2), c2);
+                float2 G;
+                G.x = t.x > T ? ex2_approx(t.x) : 0.f;
+                G.y = t.y > T ? ex2_approx(t.y) : 0.f;
+                if (MODE == kModeCount)
+                    kept += (unsigned)((t.x > T) && (2 * q < nxin)) + (unsigned)((t.y > T) && (2 * q + 1 < nxin));
+                num[q] = __ffma2_rn(al, G, num[q]);
+                den[q] = __ffma2_rn(be, G, den[q]);
+            }
+            if (MODE == kModeCount) live += (unsigned long long)nxin;
         }
     }
 
     if (MODE == kModeCount) {
+        // phase-2 candidates: in-grid voxels of every live sub-brick
+        unsigned long long cand2 = 0;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int c0 = ch * kCh;
+            const int cnt = min(kCh, L - c0);
+            for (int j = tid; j < cnt; j += kBT) {
+                const uint32_t m = a.gids[s0 + c0 + j] >> kGidBits;
+                for (int sb = 0; sb < 8; ++sb) {
+                    if (!((m >> sb) & 1u)) continue;
+                    const int y0 = by * 8 + 4 * (sb & 1), z0 = bz * 8 + 2 * (sb >> 1);
+                    const long long vx = min(8, g.nx - gx0), vy = max(0, min(4, g.ny - y0)), vz = max(0, min(2, g.nz - z0));
+                    cand2 += (unsigned long long)(vx * vy * vz);
+                }
+            }
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-        if (lane == 0) s_cnt[warp] = kept;
+        for (int o = 16; o > 0; o >>= 1) {
+            kept += __shfl_xor_sync(0xffffffffu, kept, o);
+            live += __shfl_xor_sync(0xffffffffu, live, o);
+            cand2 += __shfl_xor_sync(0xffffffffu, cand2, o);
+        }
+        if (lane == 0) { s_cnt[0][warp] = kept; s_cnt[1][warp] = live; s_cnt[2][warp] = cand2; }
         __syncthreads();
         if (tid == 0) {
-            unsigned long long tot = 0;
-            for (int w = 0; w < 8; ++w) tot += s_cnt[w];
-            long long vx = min(8, g.nx - bx * 8), vy = min(8, g.ny - by * 8), vz = min(8, g.nz - bz * 8);
-            atomicAdd(&a.st->kept, tot);
-            atomicAdd(&a.st->cand, (unsigned long long)L * (unsigned long long)(vx * vy * vz));
+            atomicAdd(&a.st->kept, s_cnt[0][0] + s_cnt[0][1]);
+            atomicAdd(&a.st->cand, s_cnt[1][0] + s_cnt[1][1] + s_cnt[2][0] + s_cnt[2][1]);
         }
         return;
     }
 
     const float rho0 = a.rho0;
-    const float vt0 = a.normalized ? num0 / fmaxf(den0, rho0) : num0;
-    const float vt1 = a.normalized ? num1 / fmaxf(den1, rho0) : num1;
-    const size_t v0 = ((size_t)gz * g.ny + gy) * g.nx + gx;
+    const size_t vrow = ((size_t)gz * g.ny + gy) * g.nx + gx0;
+    float up[8], vt[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        vt[2 * q] = a.normalized ? num[q].x / fmaxf(den[q].x, rho0) : num[q].x;
+        vt[2 * q + 1] = a.normalized ? num[q].y / fmaxf(den[q].y, rho0) : num[q].y;
+    }
     if (MODE == kModeEval) {
-        if (in0) a.field_out[v0] = vt0;
-        if (in1) a.field_out[v0 + 1] = vt1;
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+            if (x < nxin) a.field_out[vrow + x] = vt[x];
         return;
     }
-
-    float up0 = 0.f, up1 = 0.f;
     if (MODE == kModeLoss) {
-        const float V0 = in0 ? a.field[v0] : 0.f;
-        const float V1 = in1 ? a.field[v0 + 1] : 0.f;
-        const float r0 = in0 ? vt0 - V0 : 0.f;
-        const float r1 = in1 ? vt1 - V1 : 0.f;
-        const bool m0 = a.mask_thresh < 0.f || V0 > a.mask_thresh;
-        const bool m1 = a.mask_thresh < 0.f || V1 > a.mask_thresh;
-        const float rl0 = m0 ? r0 : 0.f, rl1 = m1 ? r1 : 0.f;
-        double ef = (double)r0 * r0 + (double)r1 * r1;
-        double el = (double)rl0 * rl0 + (double)rl1 * rl1;
+        float ef = 0.f, el = 0.f;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const float V = x < nxin ? a.field[vrow + x] : 0.f;
+            const float r = x < nxin ? vt[x] - V : 0.f;
+            const float rl = (a.mask_thresh < 0.f || V > a.mask_thresh) ? r : 0.f;
+            ef = fmaf(r, r, ef);
+            el = fmaf(rl, rl, el);
+            up[x] = 2.f * rl * a.inv_m;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ef += __shfl_xor_sync(0xffffffffu, ef, o);
             el += __shfl_xor_sync(0xffffffffu, el, o);
         }
         if (lane == 0) { s_red[0][warp] = el; s_red[1][warp] = ef; }
-        up0 = 2.f * rl0 * a.inv_m;
-        up1 = 2.f * rl1 * a.inv_m;
     } else {  // kModeBwd
-        up0 = in0 ? a.upstream[v0] : 0.f;
-        up1 = in1 ? a.upstream[v0 + 1] : 0.f;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) up[x] = x < nxin ? a.upstream[vrow + x] : 0.f;
     }
-    float gn0, gd0, gn1, gd1;
-    if (a.normalized) {
-        gn0 = up0 / fmaxf(den0, rho0);
-        gn1 = up1 / fmaxf(den1, rho0);
-        gd0 = den0 >= rho0 ? -vt0 * gn0 : 0.f;
-        gd1 = den1 >= rho0 ? -vt1 * gn1 : 0.f;
-    } else {
-        gn0 = up0; gn1 = up1; gd0 = 0.f; gd1 = 0.f;
+    {
+        const int row = lz * 8 + ly;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float gn0, gd0, gn1, gd1;
+            const float d0 = q == 0 ? den[0].x : q == 1 ? den[1].x : q == 2 ? den[2].x : den[3].x;
+            const float d1 = q == 0 ? den[0].y : q == 1 ? den[1].y : q == 2 ? den[2].y : den[3].y;
+            if (a.normalized) {
+                gn0 = up[2 * q] / fmaxf(d0, rho0);
+                gn1 = up[2 * q + 1] / fmaxf(d1, rho0);
+                gd0 = d0 >= rho0 ? -vt[2 * q] * gn0 : 0.f;
+                gd1 = d1 >= rho0 ? -vt[2 * q + 1] * gn1 : 0.f;
+            } else {
+                gn0 = up[2 * q]; gn1 = up[2 * q + 1]; gd0 = 0.f; gd1 = 0.f;
+            }
+            s_g[row * 4 + q] = make_float4(gn0, gn1, gd0, gd1);
+        }
     }
-    s_g[33 * lz + 4 * ly + xp] = make_float4(gn0, gd0, gn1, gd1);
     __syncthreads();
-    if (MODE == kModeLoss && tid == 0) {
-        double el = 0.0, ef = 0.0;
-        for (int w = 0; w < 8; ++w) { el += s_red[0][w]; ef += s_red[1][w]; }
-        a.part[brick] = make_double2(el, ef);
-    }
+    if (MODE == kModeLoss && tid == 0)
+        a.part[brick] = make_double2((double)s_red[0][0] + (double)s_red[0][1], (double)s_red[1][0] + (double)s_red[1][1]);
     if (a.acc == nullptr || L == 0) return;
 
-    // ---------------- phase 2: backward, 8-lane group per Gaussian ----------------
-    const int sl = lane & 7, gs = lane >> 3;
-    const unsigned gmask = 0xffu << (8 * gs);
-    const float fzs = (float)(bz * 8 + sl);
-    const float fyb = (float)(by * 8), fxb = (float)(bx * 8);
-    // the last chunk of phase 1 is still staged; walk the chunks backwards
+    // ---------------- phase 2: compacted (Gaussian, 8x4x2 sub-brick) tasks ----------------
+    const float fxb = (float)gx0;
     for (int ch = nchunks - 1; ch >= 0; --ch) {
-        const int c0 = ch * kChunk;
-        const int cnt = min(kChunk, L - c0);
+        const int c0 = ch * kCh;
+        const int cnt = min(kCh, L - c0);
         if (ch != nchunks - 1) {
             __syncthreads();
-            for (int j = tid; j < cnt * 3; j += kBrickThreads) {
-                const uint32_t gid = a.gids[s0 + c0 + j / 3];
-                s_rec[j] = a.rec[3 * (size_t)gid + (j % 3)];
-            }
+            stage_chunk(a, s0, c0, cnt, s_rec, s_msk, tid);
             __syncthreads();
         }
-        for (int jr = warp * 4 + gs; jr < cnt; jr += 32) {
-            const float4 r0 = s_rec[3 * jr], r1 = s_rec[3 * jr + 1], r2 = s_rec[3 * jr + 2];
-            float dxv[8];
+        // thread t scans sub-brick sb = t >> 3 over Gaussians j = 8 (t & 7) .. + 8:
+        // tasks come out sub-brick-major, Gaussian-ascending
+        const int sb = tid >> 3, jb = 8 * (tid & 7);
+        uint32_t bits = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) dxv[k] = __fsub_rn(fxb + (float)k, r0.x);
-            const float dz = __fsub_rn(fzs, r0.z);
-            const float e_ = __fmul_rn(r1.w, dz), f_ = __fmul_rn(r2.x, dz);
-            const float dzh = __fmul_rn(dz, __fmul_rn(r1.y, dz));
-            float A = 0.f, Bs = 0.f, S1x = 0.f, S1y = 0.f, S1z = 0.f;
-            float Sxx = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
-#pragma unroll 2
-            for (int y = 0; y < 8; ++y) {
-                const float dy = __fsub_rn(fyb + (float)y, r0.y);
-                const float b = __fmaf_rn(r1.z, dy, e_);
-                const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
-                float R0 = 0.f, R1 = 0.f, R2 = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            const int j = jb + k;
+            if (j < cnt && ((s_msk[j] >> sb) & 1u)) bits |= 1u << k;
+        }
+        const int mine = __popc(bits);
+        int incl = mine;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 gv = s_g[33 * sl + 4 * y + q];
-                    {
-                        const float dx = dxv[2 * q];
-                        const float t = __fmaf_rn(dx, __fmaf_rn(r0.w, dx, b), c);
-                        const float G = t > T ? ex2_approx(t) : 0.f;
-                        const float Ggn = G * gv.x, Ggd = G * gv.y;
-                        A += Ggn;
-                        Bs += Ggd;
-                        const float h = fmaf(r2.y, Ggn, r2.z * Ggd);
-                        R0 += h;
-                        const float hx = h * dx;
-                        R1 += hx;
-                        R2 = fmaf(hx, dx, R2);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_scan[warp] = incl;
+        for (int j = tid; j < cnt * kAccStride; j += kBT) s_acc[j] = 0.f;
+        __syncthreads();
+        const int ntask = s_scan[0] + s_scan[1];
+        int pos = (warp ? s_scan[0] : 0) + incl - mine;
+        while (bits) {
+            const int k = __ffs(bits) - 1;
+            bits &= bits - 1;
+            s_task[pos++] = (uint16_t)((jb + k) | (sb << 8));
+        }
+        __syncthreads();
+
+        for (int tk = tid; tk < ntask; tk += kBT) {
+            const int task = s_task[tk];
+            const int j = task & 255, sbt = task >> 8;
+            const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
+            const float2 nmu = f2(-r0.x);
+            float2 dx[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dx[q] = __fadd2_rn(make_float2(fxb + (float)(2 * q), fxb + (float)(2 * q + 1)), nmu);
+            const int yb = 4 * (sbt & 1), zb = 2 * (sbt >> 1);
+            const float2 qxx = f2(r0.w), al = f2(r2.y), be = f2(r2.z);
+            float2 A = make_float2(0.f, 0.f), Bs = A, S1x = A, S1y = A, S1z = A;
+            float2 Sxx = A, Syy = A, Szz = A, Sxy = A, Sxz = A, Syz = A;
+            float2 R2 = A;
+#pragma unroll
+            for (int zs = 0; zs < 2; ++zs) {
+                const float dz = __fsub_rn((float)(bz * 8 + zb + zs), r0.z);
+                const float e_ = __fmul_rn(r1.w, dz), f_ = __fmul_rn(r2.x, dz);
+                const float dzh = __fmul_rn(dz, __fmul_rn(r1.y, dz));
+                float2 T0 = make_float2(0.f, 0.f), T1 = T0, Ty = T0;
+#pragma unroll
+                for (int yr = 0; yr < 4; ++yr) {
+                    const float dy = __fsub_rn((float)(by * 8 + yb + yr), r0.y);
+                    const float b = __fmaf_rn(r1.z, dy, e_);
+                    const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
+                    const float2 b2 = f2(b), c2 = f2(c);
+                    const float4* gp = s_g + ((zb + zs) * 8 + yb + yr) * 4;
+                    float2 R0 = make_float2(0.f, 0.f), R1 = R0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 gv = gp[q];
+                        const float2 t = __ffma2_rn(dx[q], __ffma2_rn(qxx, dx[q], b2), c2);
+                        float2 G;
+                        G.x = t.x > T ? ex2_approx(t.x) : 0.f;
+                        G.y = t.y > T ? ex2_approx(t.y) : 0.f;
+                        const float2 Ggn = __fmul2_rn(G, make_float2(gv.x, gv.y));
+                        const float2 Ggd = __fmul2_rn(G, make_float2(gv.z, gv.w));
+                        A = __fadd2_rn(A, Ggn);
+                        Bs = __fadd2_rn(Bs, Ggd);
+                        const float2 h = __ffma2_rn(al, Ggn, __fmul2_rn(be, Ggd));
+                        R0 = __fadd2_rn(R0, h);
+                        const float2 hx = __fmul2_rn(h, dx[q]);
+                        R1 = __fadd2_rn(R1, hx);
+                        R2 = __ffma2_rn(hx, dx[q], R2);
                     }
-                    {
-                        const float dx = dxv[2 * q + 1];
-                        const float t = __fmaf_rn(dx, __fmaf_rn(r0.w, dx, b), c);
-                        const float G = t > T ? ex2_approx(t) : 0.f;
-                        const float Ggn = G * gv.z, Ggd = G * gv.w;
-                        A += Ggn;
-                        Bs += Ggd;
-                        const float h = fmaf(r2.y, Ggn, r2.z * Ggd);
-                        R0 += h;
-                        const float hx = h * dx;
-                        R1 += hx;
-                        R2 = fmaf(hx, dx, R2);
-                    }
+                    const float2 dy2 = f2(dy);
+                    S1y = __ffma2_rn(dy2, R0, S1y);
+                    Sxy = __ffma2_rn(dy2, R1, Sxy);
+                    const float2 dyR0 = __fmul2_rn(dy2, R0);
+                    Syy = __ffma2_rn(dy2, dyR0, Syy);
+                    T0 = __fadd2_rn(T0, R0);
+                    T1 = __fadd2_rn(T1, R1);
+                    Ty = __fadd2_rn(Ty, dyR0);
                 }
-                S1x += R1;
-                S1y = fmaf(dy, R0, S1y);
-                S1z = fmaf(dz, R0, S1z);
-                Sxx += R2;
-                Sxy = fmaf(dy, R1, Sxy);
-                Sxz = fmaf(dz, R1, Sxz);
-                const float dyR0 = dy * R0;
-                Syy = fmaf(dy, dyR0, Syy);
-                Syz = fmaf(dz, dyR0, Syz);
-                Szz = fmaf(dz * dz, R0, Szz);
+                const float2 dz2 = f2(dz);
+                S1x = __fadd2_rn(S1x, T1);
+                S1z = __ffma2_rn(dz2, T0, S1z);
+                Sxz = __ffma2_rn(dz2, T1, Sxz);
+                Syz = __ffma2_rn(dz2, Ty, Syz);
+                Szz = __ffma2_rn(__fmul2_rn(dz2, dz2), T0, Szz);
             }
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                A += __shfl_xor_sync(gmask, A, o);
-                Bs += __shfl_xor_sync(gmask, Bs, o);
-                S1x += __shfl_xor_sync(gmask, S1x, o);
-                S1y += __shfl_xor_sync(gmask, S1y, o);
-                S1z += __shfl_xor_sync(gmask, S1z, o);
-                Sxx += __shfl_xor_sync(gmask, Sxx, o);
-                Syy += __shfl_xor_sync(gmask, Syy, o);
-                Szz += __shfl_xor_sync(gmask, Szz, o);
-                Sxy += __shfl_xor_sync(gmask, Sxy, o);
-                Sxz += __shfl_xor_sync(gmask, Sxz, o);
-                Syz += __shfl_xor_sync(gmask, Syz, o);
-            }
-            if (sl == 0) {
-                const uint32_t gid = a.gids[s0 + c0 + jr];
-                float* dst = a.acc + 12 * (size_t)gid;
-                red_add_v4(dst, A, Bs, S1x, S1y);
-                red_add_v4(dst + 4, S1z, Sxx, Syy, Szz);
-                red_add_v4(dst + 8, Sxy, Sxz, Syz, 0.f);
-            }
+            Sxx = R2;
+            float* sa = s_acc + j * kAccStride;
+            atomicAdd(sa + 0, A.x + A.y);
+            atomicAdd(sa + 1, Bs.x + Bs.y);
+            atomicAdd(sa + 2, S1x.x + S1x.y);
+            atomicAdd(sa + 3, S1y.x + S1y.y);
+            atomicAdd(sa + 4, S1z.x + S1z.y);
+            atomicAdd(sa + 5, Sxx.x + Sxx.y);
+            atomicAdd(sa + 6, Syy.x + Syy.y);
+            atomicAdd(sa + 7, Szz.x + Szz.y);
+            atomicAdd(sa + 8, Sxy.x + Sxy.y);
+            atomicAdd(sa + 9, Sxz.x + Sxz.y);
+            atomicAdd(sa + 10, Syz.x + Syz.y);
+        }
+        __syncthreads();
+        for (int j = tid; j < cnt; j += kBT) {
+            if (s_msk[j] == 0) continue;
+            const float* sa = s_acc + j * kAccStride;
+            const uint32_t gid = a.gids[s0 + c0 + j] & kGidMask;
+            float* dst = a.acc + 12 * (size_t)gid;
+            red_add_v4(dst, sa[0], sa[1], sa[2], sa[3]);
+            red_add_v4(dst + 4, sa[4], sa[5], sa[6], sa[7]);
+            red_add_v4(dst + 8, sa[8], sa[9], sa[10], 0.f);
         }
     }
 }
@@ -259,10 +339,10 @@ void launch_brick(int mode, const BrickArgs& a, cudaStream_t s)
 {
     const unsigned grid = (unsigned)a.g.nbricks;
     switch (mode) {
-        case kModeEval: k_brick<kModeEval><<<grid, kBrickThreads, 0, s>>>(a); break;
-        case kModeLoss: k_brick<kModeLoss><<<grid, kBrickThreads, 0, s>>>(a); break;
-        case kModeBwd: k_brick<kModeBwd><<<grid, kBrickThreads, 0, s>>>(a); break;
-        default: k_brick<kModeCount><<<grid, kBrickThreads, 0, s>>>(a); break;
+        case kModeEval: k_brick<kModeEval><<<grid, kBT, 0, s>>>(a); break;
+        case kModeLoss: k_brick<kModeLoss><<<grid, kBT, 0, s>>>(a); break;
+        case kModeBwd: k_brick<kModeBwd><<<grid, kBT, 0, s>>>(a); break;
+        default: k_brick<kModeCount><<<grid, kBT, 0, s>>>(a); break;
     }
 }
 

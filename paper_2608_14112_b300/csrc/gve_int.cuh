@@ -9,8 +9,9 @@
 //   bin record      20 words per Gaussian: whitening L (row-major 3x3),
 //                   brick half-extent bound e[3], threshold K2, brick box
 //                   lo[3] / hi[3], non-empty flag.
-//   pair list       keys (brick index, z-major) and values (Gaussian index),
-//                   uint32, double-buffered for the radix sort.
+//   pair list       keys (brick index, z-major) and values (Gaussian index in
+//                   the low 24 bits, 8-bit sub-brick mask above), uint32,
+//                   double-buffered for the radix sort.
 //   ranges          uint32 start[nbricks], end[nbricks].
 //   accumulators    float[12] per Gaussian: A, Bs, S1 (3), S2 (6: xx yy zz
 //                   xy xz yz), 0 -- the per-Gaussian sums of the backward.
@@ -31,6 +32,9 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kScanBlocks = 512;
 constexpr int kScanThreads = 1024;
 constexpr double kNegHalfLog2e = -0.72134752044448170367996234050095;
+// sorted pair values: Gaussian index in the low 24 bits, sub-brick mask above
+constexpr int kGidBits = 24;
+constexpr uint32_t kGidMask = (1u << kGidBits) - 1u;
 
 struct __align__(16) BinRec {
     float L[9];

@@ -135,6 +135,7 @@ gve_status size_static(Call& k)
     GVE_TRY(ensure(c, c->rec, sizeof(float4) * 3 * n, k.s));
     GVE_TRY(ensure(c, c->binrec, sizeof(BinRec) * n, k.s));
     GVE_TRY(ensure(c, c->counts, sizeof(uint32_t) * n, k.s));
+    GVE_TRY(ensure(c, c->bmask, sizeof(uint32_t) * kMaskChunks * n, k.s));
     GVE_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * (n + 1), k.s));
     GVE_TRY(ensure(c, c->acc, sizeof(float) * 12 * n, k.s));
     GVE_TRY(ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, k.s));
@@ -166,7 +167,8 @@ gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
     GVE_TRY(size_static(k));
     reset_state(k);
     launch_prep(prims, k.n, k.g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, k.s);
-    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, k.s);
+    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, (uint32_t*)c->bmask.p,
+                 k.s);
     launch_offsets((uint32_t*)c->counts.p, k.n, (unsigned long long*)c->offsets.p, c->scanp.p, dstate(c),
                    ~0ull, 0, k.s);
     c->launches += k.n > 0 ? 6 : 4;
@@ -183,11 +185,12 @@ gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter
 {
     gve_ctx* c = k.c;
     launch_prep(prims, k.n, k.g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, k.s);
-    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, k.s);
+    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, (uint32_t*)c->bmask.p,
+                 k.s);
     launch_offsets((uint32_t*)c->counts.p, k.n, (unsigned long long*)c->offsets.p, c->scanp.p, dstate(c), c->cap,
                    iter, k.s);
     launch_emit((BinRec*)c->binrec.p, (float4*)c->rec.p, (unsigned long long*)c->offsets.p, k.n, k.g,
-                (uint32_t*)c->keys[0].p, (uint32_t*)c->vals[0].p, dstate(c), k.s);
+                (const uint32_t*)c->bmask.p, (uint32_t*)c->keys[0].p, (uint32_t*)c->vals[0].p, dstate(c), k.s);
     uint32_t* kk[2] = {(uint32_t*)c->keys[0].p, (uint32_t*)c->keys[1].p};
     uint32_t* vv[2] = {(uint32_t*)c->vals[0].p, (uint32_t*)c->vals[1].p};
     k.sorted = launch_sort(kk, vv, dstate(c), c->cap, k.g.key_bits, (uint32_t*)c->hist.p, c->scanp.p, k.s);
@@ -283,7 +286,7 @@ void gve_ctx_destroy(gve_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
+    Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->bmask, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
                    &c->vals[0], &c->vals[1], &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
                    &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace};
     for (Buf* b : bufs)

@@ -204,8 +204,22 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, fl
 // ------------------------------------------------------------------------
 // count / emit (one warp per Gaussian)
 // ------------------------------------------------------------------------
+// Bricks of a Gaussian's box in z-major order; the box has fewer than 2^31
+// bricks, so 32-bit index arithmetic suffices.  The pass/fail ballots of the
+// first kMaskChunks x 32 bricks are kept for the emission pass.
+__device__ __forceinline__ void box_brick(const BinRec& b, uint32_t t, uint32_t ex, uint32_t exy, int& bx, int& by,
+                                          int& bz)
+{
+    const uint32_t zq = t / exy, r = t - zq * exy;
+    const uint32_t yq = r / ex;
+    bx = b.blo[0] + (int)(r - yq * ex);
+    by = b.blo[1] + (int)yq;
+    bz = b.blo[2] + (int)zq;
+}
+
 __global__ void __launch_bounds__(256) k_count(const BinRec* __restrict__ br, const float4* __restrict__ rec,
-                                               long long n, BinGeom g, uint32_t* __restrict__ counts)
+                                               long long n, BinGeom g, uint32_t* __restrict__ counts,
+                                               uint32_t* __restrict__ bmask)
 {
     const int lane = threadIdx.x & 31;
     long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -214,25 +228,30 @@ __global__ void __launch_bounds__(256) k_count(const BinRec* __restrict__ br, co
         const BinRec b = br[i];
         uint32_t cnt = 0;
         if (b.nonempty) {
-            float4 r0 = rec[3 * i];
-            long long ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
-            long long tot = ex * ey * ez;
-            for (long long t = lane; t < tot; t += 32) {
-                int bx = b.blo[0] + (int)(t % ex);
-                int by = b.blo[1] + (int)((t / ex) % ey);
-                int bz = b.blo[2] + (int)(t / (ex * ey));
-                cnt += brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz) ? 1u : 0u;
+            const float4 r0 = rec[3 * i];
+            const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
+            const uint32_t exy = ex * ey, tot = exy * ez;
+            for (uint32_t t0 = 0, c = 0; t0 < tot; t0 += 32, ++c) {
+                const uint32_t t = t0 + lane;
+                bool pass = false;
+                if (t < tot) {
+                    int bx, by, bz;
+                    box_brick(b, t, ex, exy, bx, by, bz);
+                    pass = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                cnt += __popc(bal);
+                if (c < kMaskChunks && lane == 0) bmask[kMaskChunks * i + c] = bal;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (lane == 0) counts[i] = cnt;
     }
 }
 
 __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                               const unsigned long long* __restrict__ offsets, long long n,
-                                              BinGeom g, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                              BinGeom g, const uint32_t* __restrict__ bmask,
+                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                               const DevState* __restrict__ st)
 {
     if (st->overflow) return;
@@ -243,25 +262,25 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
     for (long long i = wid; i < n; i += nw) {
         const BinRec b = br[i];
         if (!b.nonempty) continue;
-        float4 r0 = rec[3 * i];
+        const float4 r0 = rec[3 * i];
         unsigned long long base = offsets[i];
-        long long ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
-        long long tot = ex * ey * ez;
-        for (long long t0 = 0; t0 < tot; t0 += 32) {
-            long long t = t0 + lane;
-            bool pass = false;
-            uint32_t key = 0, mask = 0;
-            if (t < tot) {
-                int bx = b.blo[0] + (int)(t % ex);
-                int by = b.blo[1] + (int)((t / ex) % ey);
-                int bz = b.blo[2] + (int)(t / (ex * ey));
-                pass = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
-                key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
-                if (pass) mask = subbrick_mask(b, r0.x, r0.y, r0.z, bx, by, bz, g.ny, g.nz);
+        const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
+        const uint32_t exy = ex * ey, tot = exy * ez;
+        for (uint32_t t0 = 0, c = 0; t0 < tot; t0 += 32, ++c) {
+            const uint32_t t = t0 + lane;
+            int bx = 0, by = 0, bz = 0;
+            if (t < tot) box_brick(b, t, ex, exy, bx, by, bz);
+            unsigned bal;
+            if (c < kMaskChunks) {
+                bal = bmask[kMaskChunks * i + c];
+            } else {
+                const bool p = t < tot && brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
+                bal = __ballot_sync(0xffffffffu, p);
             }
-            unsigned bal = __ballot_sync(0xffffffffu, pass);
-            if (pass) {
-                unsigned long long pos = base + __popc(bal & lt);
+            if ((bal >> lane) & 1u) {
+                const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
+                const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, bx, by, bz, g.ny, g.nz);
+                const unsigned long long pos = base + __popc(bal & lt);
                 keys[pos] = key;
                 vals[pos] = (uint32_t)i | (mask << kGidBits);
             }
@@ -409,17 +428,18 @@ static int emit_blocks(long long n)
 }
 
 void launch_count(const BinRec* br, const float4* rec, long long n, const BinGeom& g, uint32_t* counts,
-                   cudaStream_t s)
+                  uint32_t* bmask, cudaStream_t s)
 {
     if (n <= 0) return;
-    k_count<<<emit_blocks(n), 256, 0, s>>>(br, rec, n, g, counts);
+    k_count<<<emit_blocks(n), 256, 0, s>>>(br, rec, n, g, counts, bmask);
 }
 
 void launch_emit(const BinRec* br, const float4* rec, const unsigned long long* offsets, long long n,
-                  const BinGeom& g, uint32_t* keys, uint32_t* vals, const DevState* st, cudaStream_t s)
+                 const BinGeom& g, const uint32_t* bmask, uint32_t* keys, uint32_t* vals, const DevState* st,
+                 cudaStream_t s)
 {
     if (n <= 0) return;
-    k_emit<<<emit_blocks(n), 256, 0, s>>>(br, rec, offsets, n, g, keys, vals, st);
+    k_emit<<<emit_blocks(n), 256, 0, s>>>(br, rec, offsets, n, g, bmask, keys, vals, st);
 }
 
 // ------------------------------------------------------------------------
@@ -454,6 +474,10 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
     }
 }
 
+// Stable scatter of one 8-bit digit.  Each CTA ranks its tile of kSortTile
+// elements (per-warp match_any ranking, warps in element order), places the
+// tile in shared memory sorted by digit, then writes every digit's run to its
+// global offset with consecutive threads on consecutive addresses.
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -462,7 +486,11 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
 {
     if (st->overflow) return;
     constexpr int W = kSortThreads / 32;
-    __shared__ uint32_t wcnt[W][256];
+    __shared__ uint32_t wcnt[W][256];     // per-warp digit counts, then per-warp local offsets
+    __shared__ uint32_t dstart[256];      // tile-local start of each digit
+    __shared__ uint32_t gbase[256];       // global start of each digit for this tile
+    __shared__ uint32_t sk[kSortTile], sv[kSortTile];
+    __shared__ uint32_t wsum[W];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long n = sort_len(st, cap);
@@ -470,46 +498,73 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
         __syncwarp();
-        unsigned long long base = tile * kSortTile + (unsigned long long)w * (32 * kSortItems);
+        const unsigned long long tbase = tile * kSortTile;
+        const int tn = (int)(n - tbase < (unsigned long long)kSortTile ? n - tbase : (unsigned long long)kSortTile);
+        const int wbase = w * (32 * kSortItems);
         uint32_t kk[kSortItems], vv[kSortItems];
         uint16_t rk[kSortItems];
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
-            unsigned long long idx = base + (unsigned long long)r * 32 + lane;
-            bool valid = idx < n;
-            uint32_t key = valid ? kin[idx] : 0xffffffffu;
-            uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
-            int leader = __ffs(peers) - 1;
-            uint32_t prior = valid ? wcnt[w][d] : 0u;
+            const int li = wbase + r * 32 + lane;
+            const bool valid = li < tn;
+            const uint32_t key = valid ? kin[tbase + li] : 0xffffffffu;
+            const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            const uint32_t prior = valid ? wcnt[w][d] : 0u;
             __syncwarp();
             if (valid && lane == leader) wcnt[w][d] = prior + __popc(peers);
             __syncwarp();
             kk[r] = key;
-            vv[r] = valid ? vin[idx] : 0u;
+            vv[r] = valid ? vin[tbase + li] : 0u;
             rk[r] = (uint16_t)(prior + __popc(peers & lt));
         }
         __syncthreads();
         {
-            const int d = threadIdx.x;  // kSortThreads == 256 digits
-            uint32_t run = hist[(unsigned long long)d * ntiles + tile];
+            // thread d: per-warp offsets within digit d, tile count of d
+            const int d = threadIdx.x;
+            uint32_t run = 0;
 #pragma unroll
             for (int ww = 0; ww < W; ++ww) {
-                uint32_t c = wcnt[ww][d];
+                const uint32_t c = wcnt[ww][d];
                 wcnt[ww][d] = run;
                 run += c;
             }
+            // exclusive scan of the tile counts over digits (block-wide)
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane == 31) wsum[w] = incl;
+            __syncthreads();
+            uint32_t add = 0;
+            for (int ww = 0; ww < w; ++ww) add += wsum[ww];
+            const uint32_t ex = add + incl - run;
+            dstart[d] = ex;
+            gbase[d] = hist[(unsigned long long)d * ntiles + tile];
+#pragma unroll
+            for (int ww = 0; ww < W; ++ww) wcnt[ww][d] += ex;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
-            unsigned long long idx = base + (unsigned long long)r * 32 + lane;
-            if (idx < n) {
-                uint32_t d = (kk[r] >> shift) & 255u;
-                uint32_t pos = wcnt[w][d] + rk[r];
-                kout[pos] = kk[r];
-                vout[pos] = vv[r];
+            const int li = wbase + r * 32 + lane;
+            if (li < tn) {
+                const uint32_t d = (kk[r] >> shift) & 255u;
+                const uint32_t p = wcnt[w][d] + rk[r];
+                sk[p] = kk[r];
+                sv[p] = vv[r];
             }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < tn; i += kSortThreads) {
+            const uint32_t key = sk[i];
+            const uint32_t d = (key >> shift) & 255u;
+            const uint32_t pos = gbase[d] + (uint32_t)i - dstart[d];
+            kout[pos] = key;
+            vout[pos] = sv[i];
         }
         __syncthreads();
     }

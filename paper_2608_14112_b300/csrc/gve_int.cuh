@@ -69,7 +69,7 @@ struct Buf {
 struct gve_ctx {
     int device = 0;
     std::string err;
-    gve::Buf rec, binrec, counts, offsets, acc, adam;
+    gve::Buf rec, binrec, counts, bmask, offsets, acc, adam;
     gve::Buf keys[2], vals[2];
     uint64_t cap = 0;                // pair capacity of keys/vals
     gve::Buf hist, scanp;
@@ -107,14 +107,18 @@ BinGeom make_geom(gve_dims d, int B);
 
 void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec,
                  BinRec* br, cudaStream_t s);
+// per Gaussian: number of listed bricks, and the pass ballots of the first
+// kMaskChunks x 32 bricks of its box (reused by the emission pass)
+constexpr int kMaskChunks = 4;
 void launch_count(const BinRec* br, const float4* rec, long long n, const BinGeom& g, uint32_t* counts,
-                  cudaStream_t s);
+                  uint32_t* bmask, cudaStream_t s);
 // exclusive scan of counts into offsets[0..n], total into st->total / max_total,
 // sets st->overflow when total > cap (iteration index `iter`).
 void launch_offsets(const uint32_t* counts, long long n, unsigned long long* offsets, void* scanp,
                     DevState* st, unsigned long long cap, int iter, cudaStream_t s);
 void launch_emit(const BinRec* br, const float4* rec, const unsigned long long* offsets, long long n,
-                 const BinGeom& g, uint32_t* keys, uint32_t* vals, const DevState* st, cudaStream_t s);
+                 const BinGeom& g, const uint32_t* bmask, uint32_t* keys, uint32_t* vals, const DevState* st,
+                 cudaStream_t s);
 // Stable LSD radix sort of (keys, vals) by key; result ends in keys[out], vals[out].
 int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsigned long long cap,
                 int key_bits, uint32_t* hist, void* scanp, cudaStream_t s);

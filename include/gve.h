@@ -216,6 +216,30 @@ GVE_API gve_status gve_count_pairs(gve_ctx* ctx, const float* prims_dev, int64_t
                            const gve_eval_opts* opts, int64_t* kept_pairs,
                            int64_t* candidate_pairs, void* stream);
 
+/* Field evaluation that allocates no memory -- an addition for callers that
+ * cannot call cudaMalloc (a memory pool or arena that owns the device, a
+ * fixed device footprint after start-up, no allocator locks on the call
+ * path); the paper has no counterpart.  Same arguments and result as
+ * gve_evaluate, without a context.  All scratch lives in one fixed
+ * file-scope device array of the library (about 10 MB, held by every GPU
+ * that loads the library until the process exits).
+ *   prims_dev      [n][12] float32, n <= GVE_NOALLOC_MAX_PRIMS.
+ *   dims           at most GVE_NOALLOC_MAX_BRICKS bricks of 8^3.
+ *   opts           brick must be 8.
+ *   field_out_dev  [nz][ny][nx] float32 output.
+ * Returns GVE_E_INVALID for sizes beyond the limits (before any launch), and
+ * GVE_E_CAPACITY when the (brick, Gaussian) pair count, found on the device,
+ * exceeds GVE_NOALLOC_MAX_PAIRS (the output is then not written).  The call
+ * synchronises `stream` to read that count.  The first call on a device
+ * resolves the array's address with that device current; make it before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. */
+#define GVE_NOALLOC_MAX_PRIMS 8192
+#define GVE_NOALLOC_MAX_BRICKS 32768
+#define GVE_NOALLOC_MAX_PAIRS 524288
+GVE_API gve_status gve_evaluate_noalloc(const float* prims_dev, int64_t n, gve_dims dims,
+                                        const gve_eval_opts* opts, float* field_out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

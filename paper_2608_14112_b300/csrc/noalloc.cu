@@ -1,0 +1,150 @@
+// noalloc.cu -- field evaluation that allocates no memory at all.
+//
+// Some callers cannot call cudaMalloc: code running inside a memory pool or
+// arena that owns the whole device, a host that must not grow its device
+// footprint after start-up, or a caller that has to run without taking the
+// allocator's locks.  gve_evaluate_noalloc serves them: it takes the same
+// inputs and output as gve_evaluate, needs no context, and keeps all of its
+// scratch (prepared records, brick pairs, sort buffers, ranges, device state)
+// in one fixed file-scope device array.  That array is part of the library
+// image: every GPU that loads the library holds it (kScratchBytes) until the
+// process exits, whether or not the entry point is used.
+//
+// Limits (checked before any launch; larger requests get GVE_E_INVALID):
+//   primitives        <= GVE_NOALLOC_MAX_PRIMS   (8,192)
+//   bricks of 8^3     <= GVE_NOALLOC_MAX_BRICKS  (32,768, e.g. a 256^3 grid)
+//   (brick, Gaussian) pairs <= GVE_NOALLOC_MAX_PAIRS (524,288): data dependent,
+//   found on the device; a larger count returns GVE_E_CAPACITY and leaves the
+//   output unwritten.
+//
+// Set-up: the first call on a device (with that device current) resolves the
+// array's device address with cudaGetSymbolAddress; that first call should
+// come before any stream capture.  Later calls reuse the address.
+//
+// Sharing: every call uses the same array and finds the previous call's
+// contents there; the parts that must start at zero (the device state and the
+// per-brick ranges) are cleared by each call.  Calls whose work overlaps on
+// the GPU (different streams, or different host threads) race on the array
+// and must be serialised by the caller.
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "gve_int.cuh"
+
+namespace gve {
+
+namespace {
+
+constexpr long long kNaPrims = GVE_NOALLOC_MAX_PRIMS;
+constexpr long long kNaBricks = GVE_NOALLOC_MAX_BRICKS;
+constexpr long long kNaPairs = GVE_NOALLOC_MAX_PAIRS;
+
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// carve-up of the scratch array (byte offsets)
+constexpr size_t kOffState = 0;
+constexpr size_t kOffRec = align256(kOffState + sizeof(DevState));
+constexpr size_t kOffBin = align256(kOffRec + sizeof(float4) * 3 * kNaPrims);
+constexpr size_t kOffCounts = align256(kOffBin + sizeof(BinRec) * kNaPrims);
+constexpr size_t kOffBmask = align256(kOffCounts + sizeof(uint32_t) * kNaPrims);
+constexpr size_t kOffOffsets = align256(kOffBmask + sizeof(uint32_t) * kMaskChunks * kNaPrims);
+constexpr size_t kOffScan = align256(kOffOffsets + sizeof(unsigned long long) * (kNaPrims + 1));
+constexpr size_t kOffKeys0 = align256(kOffScan + sizeof(unsigned long long) * kScanBlocks);
+constexpr size_t kOffKeys1 = align256(kOffKeys0 + sizeof(uint32_t) * kNaPairs);
+constexpr size_t kOffVals0 = align256(kOffKeys1 + sizeof(uint32_t) * kNaPairs);
+constexpr size_t kOffVals1 = align256(kOffVals0 + sizeof(uint32_t) * kNaPairs);
+constexpr size_t kOffHist = align256(kOffVals1 + sizeof(uint32_t) * kNaPairs);
+constexpr size_t kOffRanges = align256(kOffHist + sizeof(uint32_t) * 256 * (kNaPairs / kSortTile + 1));
+constexpr size_t kScratchBytes = align256(kOffRanges + sizeof(uint32_t) * 2 * kNaBricks);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char* g_scratch_ptr[kMaxDevices] = {};
+
+gve_status scratch_for_current_device(unsigned char** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return GVE_E_CUDA;
+    }
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GVE_E_CUDA;
+        }
+        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return GVE_OK;
+}
+
+}  // namespace
+
+}  // namespace gve
+
+using namespace gve;
+
+extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
+                                           float* field_out, void* stream)
+{
+    if (!o || !field_out || (n > 0 && !prims)) return GVE_E_INVALID;
+    if (n < 0 || n > kNaPrims) return GVE_E_INVALID;
+    if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return GVE_E_INVALID;
+    if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return GVE_E_INVALID;
+    if (o->brick != 8 || !(o->trunc_k > 0.f) || !std::isfinite(o->trunc_k)) return GVE_E_INVALID;
+    if (o->normalized && !(o->rho0 > 0.f)) return GVE_E_INVALID;
+    const BinGeom g = make_geom(d, 8);
+    if (g.nbricks > kNaBricks) return GVE_E_INVALID;
+
+    unsigned char* base = nullptr;
+    gve_status st = scratch_for_current_device(&base);
+    if (st != GVE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevState* dst = reinterpret_cast<DevState*>(base + kOffState);
+    float4* rec = reinterpret_cast<float4*>(base + kOffRec);
+    BinRec* br = reinterpret_cast<BinRec*>(base + kOffBin);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base + kOffCounts);
+    uint32_t* bmask = reinterpret_cast<uint32_t*>(base + kOffBmask);
+    unsigned long long* offsets = reinterpret_cast<unsigned long long*>(base + kOffOffsets);
+    void* scanp = base + kOffScan;
+    uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(base + kOffKeys0), reinterpret_cast<uint32_t*>(base + kOffKeys1)};
+    uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(base + kOffVals0), reinterpret_cast<uint32_t*>(base + kOffVals1)};
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + kOffHist);
+    uint32_t* ranges = reinterpret_cast<uint32_t*>(base + kOffRanges);
+
+    // the device state and the ranges must start at zero on every call
+    if (cudaMemsetAsync(dst, 0, sizeof(DevState), s) != cudaSuccess) return GVE_E_CUDA;
+    const unsigned long long cap = (unsigned long long)kNaPairs;
+    launch_prep(prims, n, g, o->trunc_k, rec, br, s);
+    launch_count(br, rec, n, g, counts, bmask, s);
+    launch_offsets(counts, n, offsets, scanp, dst, cap, 0, s);
+    launch_emit(br, rec, offsets, n, g, bmask, keys[0], vals[0], dst, s);
+    const int out = launch_sort(keys, vals, dst, cap, g.key_bits, hist, scanp, s);
+    if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * g.nbricks, s) != cudaSuccess) return GVE_E_CUDA;
+    launch_ranges(keys[out], dst, cap, ranges, ranges + g.nbricks, s);
+    BrickArgs a{};
+    a.g = g;
+    a.start = ranges;
+    a.end = ranges + g.nbricks;
+    a.gids = vals[out];
+    a.rec = rec;
+    a.st = dst;
+    a.T = (float)((double)o->trunc_k * (double)o->trunc_k * kNegHalfLog2e);
+    a.rho0 = o->rho0;
+    a.normalized = o->normalized;
+    a.mask_thresh = -1.f;
+    a.inv_m = (float)(1.0 / ((double)d.nx * d.ny * d.nz));
+    a.field_out = field_out;
+    launch_brick(kModeEval, a, s);
+    if (cudaGetLastError() != cudaSuccess) return GVE_E_CUDA;
+    // the pair count is only known on the device: read the overflow flag
+    int overflow = 0;
+    if (cudaMemcpyAsync(&overflow, &dst->overflow, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GVE_E_CUDA;
+    return overflow ? GVE_E_CAPACITY : GVE_OK;
+}

@@ -106,8 +106,9 @@ def lib():
             L.gve_bin.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P, i64, P, ctypes.POINTER(i64), P]
             L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), P]
+            L.gve_evaluate_noalloc.argtypes = [P, i64, Dims, ctypes.POINTER(EvalOpts), P, P]
             for f in ("gve_allocate", "gve_evaluate", "gve_loss_grad", "gve_backward", "gve_refine", "gve_bin",
-                      "gve_count_pairs"):
+                      "gve_count_pairs", "gve_evaluate_noalloc"):
                 getattr(L, f).restype = st
             _lib = L
     return _lib
@@ -295,3 +296,20 @@ def gve_count_pairs(prims: torch.Tensor, shape, opts: EvalOptions | None = None)
     _check(lib().gve_count_pairs(c, _ptr(prims), prims.shape[0], _dims(shape), ctypes.byref(o), ctypes.byref(kept),
                                  ctypes.byref(cand), _stream(prims.device)), c)
     return int(kept.value), int(cand.value)
+
+
+def gve_evaluate_noalloc(prims: torch.Tensor, shape, opts: EvalOptions | None = None,
+                         out: torch.Tensor | None = None):
+    """Eq. 3 at every voxel centre through the entry point that allocates no
+    device memory, for callers that cannot call cudaMalloc (sizes are capped:
+    see include/gve.h).  ``out`` may be preallocated by the caller."""
+    prims = _prims(prims)
+    o = (opts or EvalOptions()).c()
+    if out is None:
+        out = torch.empty(tuple(int(s) for s in shape), dtype=torch.float32, device=prims.device)
+    _field(out)
+    s = lib().gve_evaluate_noalloc(_ptr(prims), prims.shape[0], _dims(out.shape), ctypes.byref(o), _ptr(out),
+                                   _stream(prims.device))
+    if s != GVE_OK:
+        raise GveError(s, lib().gve_status_str(s).decode())
+    return out

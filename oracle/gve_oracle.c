@@ -156,8 +156,8 @@ static void activate(const double* p, act_t* A)
 }
 
 /* ------------------------------------------------------------------------ */
-/* float32 truncation decision (reading of "squared Mahalanobis distance     */
-/* below k^2", Sec. III-C).                                                  */
+/* float32 truncation decision: the reading of the squared-Mahalanobis      */
+/* cutoff of Sec. III-C taken in float32.                                     */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     float mu[3];

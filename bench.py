@@ -166,6 +166,22 @@ def cpu_sample(w, args, seed):
     return dt, frac, desc
 
 
+def brick_traffic(voxels):
+    """DRAM bytes per launch of the brick evaluator from the committed ncu
+    capture, scaled per voxel; None when the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "brick_traffic.json")
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, rec["kernel_source"]), "rb").read()
+    except Exception:
+        return None
+    if hashlib.sha256(src).hexdigest() != rec["kernel_source_sha256"]:
+        return None
+    per_voxel = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["captured_voxels"]
+    return per_voxel * voxels
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -256,7 +272,7 @@ def run_ours(args):
     achieved = OPS_PER_PAIR * kept / (brick_ms / 1e3) / 1e12
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": brick_traffic(int(np.prod(shape))),
                 "kernel": "k_brick<loss> (fused forward+backward)", "brick_ms": brick_ms,
                 "kept_pairs": kept, "candidate_pairs": cand,
                 "pairs_per_s": kept / (brick_ms / 1e3),

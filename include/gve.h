@@ -66,12 +66,16 @@ typedef struct { int32_t nx, ny, nz; } gve_dims;
  *            multiply-adds on float32 coefficients of -0.5*log2(e)*Sigma^-1.
  * rho0       density floor of Eq. 3 (paper: 0.05).
  * normalized 1 = Eq. 3 (sum w a G / max(sum w G, rho0)); 0 = plain sum w a G.
- * brick      brick edge B in voxels for binning: 4, 8 or 16.               */
+ * brick      brick edge B in voxels for binning: 4, 8 or 16 (8 by default).
+ * gaussians_per_block  Gaussian records the evaluator stages per shared-memory
+ *            chunk: 32 or 64, 0 = 64.  B and this value change speed only,
+ *            never results (a tuning knob, see gve_autotune).                */
 typedef struct {
     float trunc_k;
     float rho0;
     int32_t normalized;
     int32_t brick;
+    int32_t gaussians_per_block;
 } gve_eval_opts;
 
 /* Allocation options (Sec. III-E, Table III).
@@ -195,6 +199,35 @@ GVE_API gve_status gve_backward(gve_ctx* ctx, const float* prims_dev, int64_t n,
 GVE_API gve_status gve_refine(gve_ctx* ctx, float* prims_dev, int64_t n, const float* field_dev,
                       gve_dims dims, const gve_schedule* sched, float* adam_state_dev,
                       double* loss_trace_dev, gve_stats* stats, void* stream);
+
+/* One volume of a batch: its target field and its number of primitives. */
+typedef struct {
+    const float* field_dev;   /* [nz][ny][nx] float32 */
+    gve_dims dims;
+    int64_t n;                /* primitives of this volume */
+} gve_volume;
+
+/* Batched refinement of many volumes of uneven shapes (the batched encode
+ * form; each volume is refined exactly as gve_refine would, Sec. III-E).
+ * The records of all volumes are concatenated in prims_dev ([sum n][12],
+ * volume order); adam_state_dev is [2][sum n][12] or NULL; loss_trace_dev is
+ * [iters][nvol] or NULL; psnr_out is host [nvol] or NULL (final PSNR of each
+ * volume).  One iteration of all volumes is captured once as a CUDA graph
+ * (one branch per volume) and replayed; the Adam step lives on the device.
+ * 1 <= nvol <= 32.  Synchronises `stream`. */
+GVE_API gve_status gve_refine_batch(gve_ctx* ctx, int32_t nvol, const gve_volume* vols, float* prims_dev,
+                                    const gve_schedule* sched, float* adam_state_dev,
+                                    double* loss_trace_dev, double* psnr_out, gve_stats* stats,
+                                    void* stream);
+
+/* Autotuner of the evaluator's launch shape for a batch (nvol = 1 for one
+ * volume): times one loss-and-gradient pass, without any update, for each
+ * brick edge in {4, 8, 16} and each gaussians_per_block in {32, 64}, and
+ * writes the fastest into *opts (other fields unchanged).  ms_out (host,
+ * optional) receives the 6 timings in that order (brick-major).
+ * Synchronises `stream`. */
+GVE_API gve_status gve_autotune(gve_ctx* ctx, int32_t nvol, const gve_volume* vols, const float* prims_dev,
+                                gve_eval_opts* opts, float* ms_out, void* stream);
 
 /* Brick binning introspection: the (brick, Gaussian) pairs that evaluation
  * uses, sorted by brick key (z-major brick index) and then by Gaussian index,

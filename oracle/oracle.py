@@ -275,8 +275,9 @@ def bin_sorted(p32, dims, k=3.0, B=8):
     nb = int(np.prod([(int(d[j]) + B - 1) // B for j in range(3)]))
     start = np.searchsorted(sk, np.arange(nb, dtype=np.uint32), side="left").astype(np.uint32)
     end = np.searchsorted(sk, np.arange(nb, dtype=np.uint32), side="right").astype(np.uint32)
-    start[start == end] = 0
-    end[start == end] = 0
+    empty = start == end          # empty bricks are reported as [0, 0)
+    start[empty] = 0
+    end[empty] = 0
     return counts, sk, sg, start, end
 
 

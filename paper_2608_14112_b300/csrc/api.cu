@@ -3,6 +3,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "gve_int.cuh"
@@ -19,7 +20,7 @@ gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what)
     return GVE_E_CUDA;
 }
 
-static gve_status fail(gve_ctx* c, gve_status s, const char* msg)
+gve_status fail(gve_ctx* c, gve_status s, const char* msg)
 {
     if (c) c->err = msg;
     return s;
@@ -82,15 +83,7 @@ using namespace gve;
         if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
     } while (0)
 
-namespace {
-
-struct Call {
-    gve_ctx* c;
-    cudaStream_t s;
-    BinGeom g;
-    long long n;
-    int sorted;  // which buffer holds the sorted pairs
-};
+namespace gve {
 
 DevState* dstate(gve_ctx* c) { return reinterpret_cast<DevState*>(c->state.p); }
 
@@ -103,7 +96,9 @@ gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, c
     if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "primitives not 16-byte aligned");
     if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
     if (d.nx > (1 << 24) || d.ny > (1 << 24) || d.nz > (1 << 24)) return fail(c, GVE_E_INVALID, "grid axis above 2^24");
-    if (o->brick != 8) return fail(c, GVE_E_INVALID, "brick edge must be 8");
+    if (o->brick != 4 && o->brick != 8 && o->brick != 16) return fail(c, GVE_E_INVALID, "brick edge must be 4, 8 or 16");
+    if (o->gaussians_per_block != 0 && o->gaussians_per_block != 32 && o->gaussians_per_block != 64)
+        return fail(c, GVE_E_INVALID, "gaussians_per_block must be 0, 32 or 64");
     if (!(o->trunc_k > 0.f) || !std::isfinite(o->trunc_k)) return fail(c, GVE_E_INVALID, "trunc_k must be positive");
     if (o->normalized && !(o->rho0 > 0.f)) return fail(c, GVE_E_INVALID, "rho0 must be positive");
     BinGeom g = make_geom(d, o->brick);
@@ -176,6 +171,12 @@ gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
     DevState h;
     GVE_TRY(read_state(k, &h));
     GVE_TRY(grow_pairs(k, h.total));
+    // test hook: a logical pair capacity below what the binning needs, to
+    // exercise the overflow detection and replay of refinement
+    if (const char* tc = getenv("GVE_TEST_PAIR_CAP")) {
+        const unsigned long long t = strtoull(tc, nullptr, 10);
+        if (t > 0 && t < c->cap) c->cap = t;
+    }
     reset_state(k);
     return GVE_OK;
 }
@@ -219,6 +220,7 @@ BrickArgs brick_args(Call& k, const gve_eval_opts* o)
     a.normalized = o->normalized;
     a.mask_thresh = -1.f;
     a.inv_m = (float)(1.0 / ((double)k.g.nx * k.g.ny * k.g.nz));
+    a.chunk = o->gaussians_per_block;
     return a;
 }
 
@@ -235,7 +237,7 @@ gve_status begin(gve_ctx* c, Call& k, int64_t n, gve_dims d, const gve_eval_opts
     return GVE_OK;
 }
 
-}  // namespace
+}  // namespace gve
 
 extern "C" {
 
@@ -295,6 +297,12 @@ void gve_ctx_destroy(gve_ctx* c)
     if (c->sev_ready)
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 64; ++b) cudaEventDestroy(c->sev[a][b]);
+    for (gve_ctx* s : c->sub) gve_ctx_destroy(s);
+    for (cudaStream_t vs : c->vstream) cudaStreamDestroy(vs);
+    for (cudaEvent_t ev : c->vjoin) cudaEventDestroy(ev);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->bstate.p) cudaFree(c->bstate.p);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
@@ -467,7 +475,7 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
             launch_brick(kModeLoss, a, k.s);
             if (timed) GVE_CUDA(cudaEventRecord(c->sev[2][t - it], k.s), "event");
             launch_sse_reduce(a.part, k.g.nbricks, dstate(c), tr, t, inv_m, k.s);
-            AdamArgs ad;
+            AdamArgs ad{};
             ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
             int step = sc->step0 + t + 1;
             ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step));

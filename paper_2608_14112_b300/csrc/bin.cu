@@ -166,29 +166,33 @@ __device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy
 
 // Sub-brick cover of a listed brick (an acceleration structure of the
 // evaluator, not part of the binning definition): bit s is set when the
-// 8x4x2 sub-brick s = (y half, z pair) may hold a kept pair, by the same
-// whitened-distance lower bound around each sub-brick centre, with half
-// sizes (3.51, 1.51, 0.51) and the brick's K2.  Sub-bricks outside the grid
-// get no bit.  Conservative: it never drops a pair the keep test keeps.
-__device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, float muy, float muz, int bx, int by,
-                                                  int bz, int ny, int nz)
+// B x B/2 x B/4 sub-brick s = (y half, z quarter) may hold a kept pair, by
+// the same whitened-distance lower bound around each sub-brick centre, with
+// half sizes ((B-1)/2, (B/2-1)/2, (B/4-1)/2) + 0.01 and the brick's K2.
+// Sub-bricks outside the grid get no bit.  Conservative: it never drops a
+// pair the keep test keeps.
+__device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, float muy, float muz, int B, int bx,
+                                                  int by, int bz, int ny, int nz)
 {
-    const float cx = (float)(bx * 8) + 3.5f, cy = (float)(by * 8) + 3.5f, cz = (float)(bz * 8) + 3.5f;
+    const float hb = 0.5f * (float)(B - 1);
+    const float cx = (float)(bx * B) + hb, cy = (float)(by * B) + hb, cz = (float)(bz * B) + hb;
     const float dcx = cx - mux, dcy = cy - muy, dcz = cz - muz;
+    const float h0 = hb + 0.01f, h1 = 0.5f * (float)(B / 2 - 1) + 0.01f, h2 = 0.5f * (float)(B / 4 - 1) + 0.01f;
     float yc[3], ea[3], eb[3], ec[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         yc[j] = fmaf(b.L[j * 3 + 2], dcz, fmaf(b.L[j * 3 + 1], dcy, b.L[j * 3 + 0] * dcx));
-        ea[j] = fabsf(b.L[j * 3 + 0]) * 3.51f + fabsf(b.L[j * 3 + 1]) * 1.51f + fabsf(b.L[j * 3 + 2]) * 0.51f;
+        ea[j] = fabsf(b.L[j * 3 + 0]) * h0 + fabsf(b.L[j * 3 + 1]) * h1 + fabsf(b.L[j * 3 + 2]) * h2;
         eb[j] = b.L[j * 3 + 1];
         ec[j] = b.L[j * 3 + 2];
     }
+    const float oyv = 0.25f * (float)B, ozv = 0.125f * (float)B;
     uint32_t m = 0;
 #pragma unroll
     for (int sidx = 0; sidx < 8; ++sidx) {
-        const int yh = sidx & 1, zp = sidx >> 1;
-        if (by * 8 + 4 * yh >= ny || bz * 8 + 2 * zp >= nz) continue;
-        const float oy = yh ? 2.0f : -2.0f, oz = (float)(2 * zp - 3);
+        const int yh = sidx & 1, zq = sidx >> 1;
+        if (by * B + (B / 2) * yh >= ny || bz * B + (B / 4) * zq >= nz) continue;
+        const float oy = yh ? oyv : -oyv, oz = (float)(2 * zq - 3) * ozv;
         float sq = 0.f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
             }
             if ((bal >> lane) & 1u) {
                 const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
-                const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, bx, by, bz, g.ny, g.nz);
+                const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
                 const unsigned long long pos = base + __popc(bal & lt);
                 keys[pos] = key;
                 vals[pos] = (uint32_t)i | (mask << kGidBits);

@@ -1,14 +1,17 @@
 // field.cu -- the brick evaluator: Eq. 3 forward, residual and SSE, and the
 // backward of the loss, fused per brick of 8^3 voxels.
 //
-// One CTA of 64 threads (2 warps) per brick.  The brick's Gaussian list is
-// staged in shared memory in chunks of kCh prepared records (3 x float4),
-// each with the 8-bit sub-brick mask the binner attached: bit s says that the
-// 8x4x2 sub-brick s (y half = s & 1, z pair = s >> 1) may hold a kept pair.
+// Written for a brick edge B in {4, 8, 16} (8 by default): one CTA of
+// max(B^2, 32) threads per brick, one lane per row of B voxels.  The brick's
+// Gaussian list is staged in shared memory in chunks of CH (32 or 64)
+// prepared records (3 x float4), each with the 8-bit sub-brick mask the
+// binner attached: bit s says that the B x B/2 x B/4 sub-brick s (y half =
+// s & 1, z quarter = s >> 1) may hold a kept pair.  For B = 8 this is a
+// 64-thread CTA and 8x4x2 sub-bricks.
 //
-// Phase 1 (forward): warp w owns the z half [4w, 4w+4) of the brick and each
-// lane one row of 8 voxels along x.  For every listed Gaussian with a live
-// sub-brick in the warp's half (a warp-uniform skip otherwise), the keep
+// Phase 1 (forward): each lane owns one row of B voxels along x.  For every
+// listed Gaussian with a live sub-brick among the warp's rows (a
+// warp-uniform skip otherwise), the keep
 // exponent t is evaluated by the fixed float32 chain
 //     dy = y - mu_y, dz = z - mu_z, dx = x - mu_x,
 //     b = fma(qxy2, dy, qxz2*dz), c = fma(dy, fma(qyy, dy, qyz2*dz), dz*(qzz*dz)),
@@ -22,9 +25,9 @@
 // gn = dL/dnum = up / max(den, rho0) and gd = dL/dden = -Vtilde gn (when
 // den >= rho0), kept in shared memory.
 //
-// Phase 2 (backward): the (Gaussian, live 8x4x2 sub-brick) tasks are
-// compacted (sub-brick-major) and spread over the 64 threads; a task
-// recomputes G by the same chain on its 64 voxels and accumulates
+// Phase 2 (backward): the (Gaussian, live sub-brick) tasks are compacted
+// (sub-brick-major) and spread over all threads; a task recomputes G by the
+// same chain on its B^3/8 voxels and accumulates
 //     A = sum G gn,  Bs = sum G gd,  S1 = sum h d,  S2 = sum h d d^T,
 //     h = G (alpha gn + beta gd)      (S1, S2 scaled by -1/2 in the chain rule)
 // with the x- and z-dependence factored per row and per slice, in packed
@@ -44,31 +47,47 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 constexpr int kAccStride = 13;  // padded per-Gaussian stride of the shared sums
-constexpr int kBT = 64;         // threads per brick CTA (2 warps)
-constexpr int kCh = 64;         // Gaussians staged per chunk
 
+// CTA geometry for brick edge B: one lane per row of B voxels along x (B^2
+// rows; B = 4 uses one warp with 16 row lanes), sub-bricks of B x B/2 x B/4.
+template <int B>
+struct BrickShape {
+    static constexpr int ROWS = B * B;
+    static constexpr int THREADS = ROWS < 32 ? 32 : ROWS;
+    static constexpr int NW = THREADS / 32;
+    static constexpr int HALF = B / 2;  // voxel pairs per row
+    static constexpr int SY = B / 2;    // sub-brick extent in y
+    static constexpr int SZ = B / 4;    // sub-brick extent in z
+    static constexpr int MINB = B == 16 ? 3 : (B == 8 ? 12 : 16);
+};
+
+template <int NT>
 __device__ __forceinline__ void stage_chunk(const BrickArgs& a, uint32_t s0, int c0, int cnt, float4* s_rec,
                                             uint32_t* s_msk, int tid)
 {
-    for (int j = tid; j < cnt * 3; j += kBT) {
+    for (int j = tid; j < cnt * 3; j += NT) {
         const uint32_t v = a.gids[s0 + c0 + j / 3];
         s_rec[j] = a.rec[3 * (size_t)(v & kGidMask) + (j % 3)];
         if (j % 3 == 0) s_msk[j / 3] = v >> kGidBits;
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
+template <int MODE, int B, int CH>
+__global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k_brick(const BrickArgs a)
 {
+    using S = BrickShape<B>;
+    constexpr int NT = S::THREADS, NW = S::NW, HALF = S::HALF, SY = S::SY, SZ = S::SZ;
+    constexpr int CPT = 8 * CH / NT;  // compaction candidates per thread
+    static_assert(CPT >= 1 && CPT <= 32, "candidates per thread");
     if (a.st->overflow) return;
-    __shared__ float4 s_rec[kCh * 3];
-    __shared__ uint32_t s_msk[kCh];
-    __shared__ float4 s_g[64 * 4];            // per row: 4 x (gn[x], gn[x+1], gd[x], gd[x+1])
-    __shared__ float s_acc[kCh * kAccStride];
-    __shared__ uint16_t s_task[kCh * 8];
-    __shared__ int s_scan[2];
-    __shared__ float s_red[2][2];
-    __shared__ unsigned long long s_cnt[3][2];
+    __shared__ float4 s_rec[CH * 3];
+    __shared__ uint32_t s_msk[CH];
+    __shared__ float4 s_g[S::ROWS * HALF];  // per row: HALF x (gn[x], gn[x+1], gd[x], gd[x+1])
+    __shared__ float s_acc[CH * kAccStride];
+    __shared__ uint16_t s_task[CH * 8];
+    __shared__ int s_scan[NW];
+    __shared__ float s_red[2][NW];
+    __shared__ unsigned long long s_cnt[3][NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const BinGeom& g = a.g;
@@ -80,33 +99,40 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
     const int L = (int)(a.end[brick] - s0);
     const float T = a.T;
 
-    // ---------------- phase 1: warp = z half, lane = row of 8 voxels ----------------
-    const int ly = lane & 7, lz = 4 * warp + (lane >> 3);
-    const int gy = by * 8 + ly, gz = bz * 8 + lz, gx0 = bx * 8;
-    const bool rowin = gy < g.ny && gz < g.nz;
-    const int nxin = rowin ? min(8, g.nx - gx0) : 0;   // in-grid voxels of the row
+    // ---------------- phase 1: lane = row of B voxels ----------------
+    const bool has_row = tid < S::ROWS;
+    const int row = has_row ? tid : 0;
+    const int ly = row % B, lz = row / B;
+    const int gy = by * B + ly, gz = bz * B + lz, gx0 = bx * B;
+    const bool rowin = has_row && gy < g.ny && gz < g.nz;
+    const int nxin = rowin ? min(B, g.nx - gx0) : 0;  // in-grid voxels of the row
     const float fy = (float)gy, fz = (float)gz;
-    float2 num[4], den[4];
+    // sub-brick bits (bit = y half + 2 * z quarter) covering this warp's rows
+    uint32_t wmask = 0;
+    {
+        const int z0 = (32 * warp) / B, z1 = min(B - 1, (32 * warp + 31) / B);
+        for (int q = z0 / SZ; q <= z1 / SZ; ++q) wmask |= 3u << (2 * q);
+    }
+    float2 num[HALF], den[HALF];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { num[q] = make_float2(0.f, 0.f); den[q] = num[q]; }
+    for (int q = 0; q < HALF; ++q) { num[q] = make_float2(0.f, 0.f); den[q] = num[q]; }
     unsigned long long kept = 0, live = 0;
-    const int wshift = 4 * warp;
-    const int nchunks = (L + kCh - 1) / kCh;
+    const int nchunks = (L + CH - 1) / CH;
     for (int ch = 0; ch < nchunks; ++ch) {
-        const int c0 = ch * kCh;
-        const int cnt = min(kCh, L - c0);
+        const int c0 = ch * CH;
+        const int cnt = min(CH, L - c0);
         if (ch > 0) __syncthreads();
-        stage_chunk(a, s0, c0, cnt, s_rec, s_msk, tid);
+        stage_chunk<NT>(a, s0, c0, cnt, s_rec, s_msk, tid);
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
-            if (!((s_msk[j] >> wshift) & 0xFu)) continue;  // warp-uniform skip of the z half
+            if (!(s_msk[j] & wmask)) continue;  // warp-uniform skip
             const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
             const float dy = __fsub_rn(fy, r0.y), dz = __fsub_rn(fz, r0.z);
             const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
             const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
             const float2 nmu = f2(-r0.x), qxx = f2(r0.w), b2 = f2(b), c2 = f2(c), al = f2(r2.y), be = f2(r2.z);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < HALF; ++q) {
                 const float2 dx = __fadd2_rn(make_float2((float)(gx0 + 2 * q), (float)(gx0 + 2 * q + 1)), nmu);
                 const float2 t = __ffma2_rn(dx, __ffma2_rn(qxx, dx, b2), c2);
                 float2 G;
@@ -122,17 +148,18 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
     }
 
     if (MODE == kModeCount) {
-        // phase-2 candidates: in-grid voxels of every live sub-brick
+        // backward candidates: in-grid voxels of every live sub-brick
         unsigned long long cand2 = 0;
         for (int ch = 0; ch < nchunks; ++ch) {
-            const int c0 = ch * kCh;
-            const int cnt = min(kCh, L - c0);
-            for (int j = tid; j < cnt; j += kBT) {
+            const int c0 = ch * CH;
+            const int cnt = min(CH, L - c0);
+            for (int j = tid; j < cnt; j += NT) {
                 const uint32_t m = a.gids[s0 + c0 + j] >> kGidBits;
                 for (int sb = 0; sb < 8; ++sb) {
                     if (!((m >> sb) & 1u)) continue;
-                    const int y0 = by * 8 + 4 * (sb & 1), z0 = bz * 8 + 2 * (sb >> 1);
-                    const long long vx = min(8, g.nx - gx0), vy = max(0, min(4, g.ny - y0)), vz = max(0, min(2, g.nz - z0));
+                    const int y0 = by * B + SY * (sb & 1), z0 = bz * B + SZ * (sb >> 1);
+                    const long long vx = min(B, g.nx - gx0), vy = max(0, min(SY, g.ny - y0)),
+                                    vz = max(0, min(SZ, g.nz - z0));
                     cand2 += (unsigned long long)(vx * vy * vz);
                 }
             }
@@ -146,30 +173,32 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
         if (lane == 0) { s_cnt[0][warp] = kept; s_cnt[1][warp] = live; s_cnt[2][warp] = cand2; }
         __syncthreads();
         if (tid == 0) {
-            atomicAdd(&a.st->kept, s_cnt[0][0] + s_cnt[0][1]);
-            atomicAdd(&a.st->cand, s_cnt[1][0] + s_cnt[1][1] + s_cnt[2][0] + s_cnt[2][1]);
+            unsigned long long k = 0, c = 0;
+            for (int w = 0; w < NW; ++w) { k += s_cnt[0][w]; c += s_cnt[1][w] + s_cnt[2][w]; }
+            atomicAdd(&a.st->kept, k);
+            atomicAdd(&a.st->cand, c);
         }
         return;
     }
 
     const float rho0 = a.rho0;
     const size_t vrow = ((size_t)gz * g.ny + gy) * g.nx + gx0;
-    float up[8], vt[8];
+    float up[B], vt[B];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < HALF; ++q) {
         vt[2 * q] = a.normalized ? num[q].x / fmaxf(den[q].x, rho0) : num[q].x;
         vt[2 * q + 1] = a.normalized ? num[q].y / fmaxf(den[q].y, rho0) : num[q].y;
     }
     if (MODE == kModeEval) {
 #pragma unroll
-        for (int x = 0; x < 8; ++x)
+        for (int x = 0; x < B; ++x)
             if (x < nxin) a.field_out[vrow + x] = vt[x];
         return;
     }
     if (MODE == kModeLoss) {
         float ef = 0.f, el = 0.f;
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
+        for (int x = 0; x < B; ++x) {
             const float V = x < nxin ? a.field[vrow + x] : 0.f;
             const float r = x < nxin ? vt[x] - V : 0.f;
             const float rl = (a.mask_thresh < 0.f || V > a.mask_thresh) ? r : 0.f;
@@ -185,48 +214,48 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
         if (lane == 0) { s_red[0][warp] = el; s_red[1][warp] = ef; }
     } else {  // kModeBwd
 #pragma unroll
-        for (int x = 0; x < 8; ++x) up[x] = x < nxin ? a.upstream[vrow + x] : 0.f;
+        for (int x = 0; x < B; ++x) up[x] = x < nxin ? a.upstream[vrow + x] : 0.f;
     }
-    {
-        const int row = lz * 8 + ly;
+    if (has_row) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < HALF; ++q) {
             float gn0, gd0, gn1, gd1;
-            const float d0 = q == 0 ? den[0].x : q == 1 ? den[1].x : q == 2 ? den[2].x : den[3].x;
-            const float d1 = q == 0 ? den[0].y : q == 1 ? den[1].y : q == 2 ? den[2].y : den[3].y;
             if (a.normalized) {
-                gn0 = up[2 * q] / fmaxf(d0, rho0);
-                gn1 = up[2 * q + 1] / fmaxf(d1, rho0);
-                gd0 = d0 >= rho0 ? -vt[2 * q] * gn0 : 0.f;
-                gd1 = d1 >= rho0 ? -vt[2 * q + 1] * gn1 : 0.f;
+                gn0 = up[2 * q] / fmaxf(den[q].x, rho0);
+                gn1 = up[2 * q + 1] / fmaxf(den[q].y, rho0);
+                gd0 = den[q].x >= rho0 ? -vt[2 * q] * gn0 : 0.f;
+                gd1 = den[q].y >= rho0 ? -vt[2 * q + 1] * gn1 : 0.f;
             } else {
                 gn0 = up[2 * q]; gn1 = up[2 * q + 1]; gd0 = 0.f; gd1 = 0.f;
             }
-            s_g[row * 4 + q] = make_float4(gn0, gn1, gd0, gd1);
+            s_g[row * HALF + q] = make_float4(gn0, gn1, gd0, gd1);
         }
     }
     __syncthreads();
-    if (MODE == kModeLoss && tid == 0)
-        a.part[brick] = make_double2((double)s_red[0][0] + (double)s_red[0][1], (double)s_red[1][0] + (double)s_red[1][1]);
+    if (MODE == kModeLoss && tid == 0) {
+        double el = 0.0, ef = 0.0;
+        for (int w = 0; w < NW; ++w) { el += (double)s_red[0][w]; ef += (double)s_red[1][w]; }
+        a.part[brick] = make_double2(el, ef);
+    }
     if (a.acc == nullptr || L == 0) return;
 
-    // ---------------- phase 2: compacted (Gaussian, 8x4x2 sub-brick) tasks ----------------
+    // ---------------- phase 2: compacted (Gaussian, sub-brick) tasks ----------------
     const float fxb = (float)gx0;
     for (int ch = nchunks - 1; ch >= 0; --ch) {
-        const int c0 = ch * kCh;
-        const int cnt = min(kCh, L - c0);
+        const int c0 = ch * CH;
+        const int cnt = min(CH, L - c0);
         if (ch != nchunks - 1) {
             __syncthreads();
-            stage_chunk(a, s0, c0, cnt, s_rec, s_msk, tid);
+            stage_chunk<NT>(a, s0, c0, cnt, s_rec, s_msk, tid);
             __syncthreads();
         }
-        // thread t scans sub-brick sb = t >> 3 over Gaussians j = 8 (t & 7) .. + 8:
-        // tasks come out sub-brick-major, Gaussian-ascending
-        const int sb = tid >> 3, jb = 8 * (tid & 7);
+        // candidates c = sub-brick * CH + j: tasks come out sub-brick-major,
+        // Gaussian-ascending
         uint32_t bits = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int j = jb + k;
+        for (int k = 0; k < CPT; ++k) {
+            const int c = tid * CPT + k;
+            const int sb = c / CH, j = c % CH;
             if (j < cnt && ((s_msk[j] >> sb) & 1u)) bits |= 1u << k;
         }
         const int mine = __popc(bits);
@@ -237,46 +266,53 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
             if (lane >= o) incl += u;
         }
         if (lane == 31) s_scan[warp] = incl;
-        for (int j = tid; j < cnt * kAccStride; j += kBT) s_acc[j] = 0.f;
+        for (int j = tid; j < cnt * kAccStride; j += NT) s_acc[j] = 0.f;
         __syncthreads();
-        const int ntask = s_scan[0] + s_scan[1];
-        int pos = (warp ? s_scan[0] : 0) + incl - mine;
+        int ntask = 0, woff = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            woff += w < warp ? s_scan[w] : 0;
+            ntask += s_scan[w];
+        }
+        int pos = woff + incl - mine;
         while (bits) {
             const int k = __ffs(bits) - 1;
             bits &= bits - 1;
-            s_task[pos++] = (uint16_t)((jb + k) | (sb << 8));
+            const int c = tid * CPT + k;
+            s_task[pos++] = (uint16_t)((c % CH) | ((c / CH) << 8));
         }
         __syncthreads();
 
-        for (int tk = tid; tk < ntask; tk += kBT) {
+        for (int tk = tid; tk < ntask; tk += NT) {
             const int task = s_task[tk];
             const int j = task & 255, sbt = task >> 8;
             const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
             const float2 nmu = f2(-r0.x);
-            float2 dx[4];
+            float2 dx[HALF];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dx[q] = __fadd2_rn(make_float2(fxb + (float)(2 * q), fxb + (float)(2 * q + 1)), nmu);
-            const int yb = 4 * (sbt & 1), zb = 2 * (sbt >> 1);
+            for (int q = 0; q < HALF; ++q)
+                dx[q] = __fadd2_rn(make_float2(fxb + (float)(2 * q), fxb + (float)(2 * q + 1)), nmu);
+            const int yb = SY * (sbt & 1), zb = SZ * (sbt >> 1);
             const float2 qxx = f2(r0.w), al = f2(r2.y), be = f2(r2.z);
             float2 A = make_float2(0.f, 0.f), Bs = A, S1x = A, S1y = A, S1z = A;
-            float2 Sxx = A, Syy = A, Szz = A, Sxy = A, Sxz = A, Syz = A;
+            float2 Syy = A, Szz = A, Sxy = A, Sxz = A, Syz = A;
             float2 R2 = A;
 #pragma unroll
-            for (int zs = 0; zs < 2; ++zs) {
-                const float dz = __fsub_rn((float)(bz * 8 + zb + zs), r0.z);
+            for (int zs = 0; zs < SZ; ++zs) {
+                const float dz = __fsub_rn((float)(bz * B + zb + zs), r0.z);
                 const float e_ = __fmul_rn(r1.w, dz), f_ = __fmul_rn(r2.x, dz);
                 const float dzh = __fmul_rn(dz, __fmul_rn(r1.y, dz));
                 float2 T0 = make_float2(0.f, 0.f), T1 = T0, Ty = T0;
 #pragma unroll
-                for (int yr = 0; yr < 4; ++yr) {
-                    const float dy = __fsub_rn((float)(by * 8 + yb + yr), r0.y);
-                    const float b = __fmaf_rn(r1.z, dy, e_);
-                    const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
-                    const float2 b2 = f2(b), c2 = f2(c);
-                    const float4* gp = s_g + ((zb + zs) * 8 + yb + yr) * 4;
+                for (int yr = 0; yr < SY; ++yr) {
+                    const float dy = __fsub_rn((float)(by * B + yb + yr), r0.y);
+                    const float bb = __fmaf_rn(r1.z, dy, e_);
+                    const float cc = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
+                    const float2 b2 = f2(bb), c2 = f2(cc);
+                    const float4* gp = s_g + ((zb + zs) * B + yb + yr) * HALF;
                     float2 R0 = make_float2(0.f, 0.f), R1 = R0;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < HALF; ++q) {
                         const float4 gv = gp[q];
                         const float2 t = __ffma2_rn(dx[q], __ffma2_rn(qxx, dx[q], b2), c2);
                         float2 G;
@@ -308,14 +344,13 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
                 Syz = __ffma2_rn(dz2, Ty, Syz);
                 Szz = __ffma2_rn(__fmul2_rn(dz2, dz2), T0, Szz);
             }
-            Sxx = R2;
             float* sa = s_acc + j * kAccStride;
             atomicAdd(sa + 0, A.x + A.y);
             atomicAdd(sa + 1, Bs.x + Bs.y);
             atomicAdd(sa + 2, S1x.x + S1x.y);
             atomicAdd(sa + 3, S1y.x + S1y.y);
             atomicAdd(sa + 4, S1z.x + S1z.y);
-            atomicAdd(sa + 5, Sxx.x + Sxx.y);
+            atomicAdd(sa + 5, R2.x + R2.y);
             atomicAdd(sa + 6, Syy.x + Syy.y);
             atomicAdd(sa + 7, Szz.x + Szz.y);
             atomicAdd(sa + 8, Sxy.x + Sxy.y);
@@ -323,7 +358,7 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
             atomicAdd(sa + 10, Syz.x + Syz.y);
         }
         __syncthreads();
-        for (int j = tid; j < cnt; j += kBT) {
+        for (int j = tid; j < cnt; j += NT) {
             if (s_msk[j] == 0) continue;
             const float* sa = s_acc + j * kAccStride;
             const uint32_t gid = a.gids[s0 + c0 + j] & kGidMask;
@@ -335,14 +370,29 @@ __global__ void __launch_bounds__(kBT, 12) k_brick(const BrickArgs a)
     }
 }
 
-void launch_brick(int mode, const BrickArgs& a, cudaStream_t s)
+template <int B, int CH>
+static void launch_brick_bc(int mode, const BrickArgs& a, cudaStream_t s)
 {
     const unsigned grid = (unsigned)a.g.nbricks;
+    constexpr int NT = BrickShape<B>::THREADS;
     switch (mode) {
-        case kModeEval: k_brick<kModeEval><<<grid, kBT, 0, s>>>(a); break;
-        case kModeLoss: k_brick<kModeLoss><<<grid, kBT, 0, s>>>(a); break;
-        case kModeBwd: k_brick<kModeBwd><<<grid, kBT, 0, s>>>(a); break;
-        default: k_brick<kModeCount><<<grid, kBT, 0, s>>>(a); break;
+        case kModeEval: k_brick<kModeEval, B, CH><<<grid, NT, 0, s>>>(a); break;
+        case kModeLoss: k_brick<kModeLoss, B, CH><<<grid, NT, 0, s>>>(a); break;
+        case kModeBwd: k_brick<kModeBwd, B, CH><<<grid, NT, 0, s>>>(a); break;
+        default: k_brick<kModeCount, B, CH><<<grid, NT, 0, s>>>(a); break;
+    }
+}
+
+void launch_brick(int mode, const BrickArgs& a, cudaStream_t s)
+{
+    const int B = a.g.B;
+    const bool c32 = a.chunk == 32;
+    if (B == 4) {
+        if (c32) launch_brick_bc<4, 32>(mode, a, s); else launch_brick_bc<4, 64>(mode, a, s);
+    } else if (B == 16) {
+        if (c32) launch_brick_bc<16, 32>(mode, a, s); else launch_brick_bc<16, 64>(mode, a, s);
+    } else {
+        if (c32) launch_brick_bc<8, 32>(mode, a, s); else launch_brick_bc<8, 64>(mode, a, s);
     }
 }
 
@@ -379,7 +429,8 @@ __global__ void __launch_bounds__(256) k_sse_partial(const double2* __restrict__
 }
 
 __global__ void __launch_bounds__(1024) k_sse_final(const double2* __restrict__ in, int nin, DevState* st,
-                                                    double* trace, int iter, double inv_m)
+                                                    double* trace, int iter, double inv_m, const int* iter_dev,
+                                                    int trace_stride, int trace_col)
 {
     if (st->overflow) return;
     __shared__ double sm[2][32];
@@ -397,17 +448,17 @@ __global__ void __launch_bounds__(1024) k_sse_final(const double2* __restrict__ 
         for (int w = 0; w < 32; ++w) { a += sm[0][w]; b += sm[1][w]; }
         st->sse[0] = a;
         st->sse[1] = b;
-        if (trace) trace[iter] = a * inv_m;
+        if (trace) trace[iter_dev ? (size_t)(*iter_dev) * trace_stride + trace_col : (size_t)iter] = a * inv_m;
     }
 }
 
 void launch_sse_reduce(const double2* part, long long nbricks, DevState* st, double* trace, int iter,
-                       double inv_m, cudaStream_t s)
+                       double inv_m, cudaStream_t s, const int* iter_dev, int trace_stride, int trace_col)
 {
     // the second half of the partial buffer is scratch for the block sums
     double2* tmp = const_cast<double2*>(part) + nbricks;
     k_sse_partial<<<kRedBlocks, 256, 0, s>>>(part, nbricks, tmp, st);
-    k_sse_final<<<1, 1024, 0, s>>>(tmp, kRedBlocks, st, trace, iter, inv_m);
+    k_sse_final<<<1, 1024, 0, s>>>(tmp, kRedBlocks, st, trace, iter, inv_m, iter_dev, trace_stride, trace_col);
 }
 
 }  // namespace gve

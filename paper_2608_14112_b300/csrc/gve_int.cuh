@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/gve.h"
 
@@ -85,6 +86,13 @@ struct gve_ctx {
     cudaEvent_t sev[3][64] = {};
     bool sev_ready = false;
     long long launches = 0;          // kernels launched by the current call
+    // batched refinement: one sub-context and one stream per volume
+    std::vector<gve_ctx*> sub;
+    std::vector<cudaStream_t> vstream;
+    std::vector<cudaEvent_t> vjoin;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t fork = nullptr;
+    gve::Buf bstate;                 // batch device state: step counter, {bc1, bc2}
 };
 
 namespace gve {
@@ -144,17 +152,21 @@ struct BrickArgs {
     int normalized;
     float mask_thresh;         // < 0: no mask
     float inv_m;               // 1 / (nx ny nz)
+    int chunk;                 // Gaussians staged per chunk: 32 or 64 (0 = 64)
 };
 void launch_brick(int mode, const BrickArgs& a, cudaStream_t s);
 // deterministic reduction of per-brick partials; writes st->sse and, if
-// trace != nullptr, trace[iter] = sse_masked * inv_m.
+// trace != nullptr, trace[i] = sse_masked * inv_m with i = iter, or
+// i = (*iter_dev) * trace_stride + trace_col when iter_dev is set.
 void launch_sse_reduce(const double2* part, long long nbricks, DevState* st, double* trace, int iter,
-                       double inv_m, cudaStream_t s);
+                       double inv_m, cudaStream_t s, const int* iter_dev = nullptr, int trace_stride = 1,
+                       int trace_col = 0);
 
 // ---- launchers (optim.cu) ------------------------------------------------
 struct AdamArgs {
     float lr, b1, b2, eps;
-    float bc1, bc2;  // 1 - beta^t
+    float bc1, bc2;         // 1 - beta^t
+    const float* bc_dev;    // if set: {bc1, bc2} read on the device (graph replay)
 };
 // chain rule from accumulators to raw-record gradients; either writes grad
 // (grad != nullptr) or applies Adam in place (prims, m, v).  Zeroes acc.
@@ -166,8 +178,29 @@ gve_status allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget,
                     const gve_alloc_opts* o, float* prims, int64_t* feasible_max,
                     gve_alloc_info* info, cudaStream_t s);
 
-// ---- context scratch (api.cu) ---------------------------------------------
+// ---- context scratch and the evaluation pipeline (api.cu) ----------------
 gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
 gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what);
+gve_status fail(gve_ctx* c, gve_status s, const char* msg);
+
+// one call of the pipeline on one grid
+struct Call {
+    gve_ctx* c;
+    cudaStream_t s;
+    BinGeom g;
+    long long n;
+    int sorted;  // which buffer holds the sorted pairs
+};
+DevState* dstate(gve_ctx* c);
+gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o);
+gve_status begin(gve_ctx* c, Call& k, int64_t n, gve_dims d, const gve_eval_opts* o, void* stream);
+gve_status reset_state(Call& k);
+gve_status read_state(Call& k, DevState* out);
+gve_status grow_pairs(Call& k, unsigned long long need);
+// per-Gaussian/per-brick scratch + sizing pass (synchronises k.s)
+gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o);
+// prep, count, offsets, emit, sort, ranges (stream-ordered, no host sync)
+gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter);
+BrickArgs brick_args(Call& k, const gve_eval_opts* o);
 
 }  // namespace gve

@@ -127,11 +127,13 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
         mm[4 * k] = a.x; mm[4 * k + 1] = a.y; mm[4 * k + 2] = a.z; mm[4 * k + 3] = a.w;
         vv[4 * k] = b.x; vv[4 * k + 1] = b.y; vv[4 * k + 2] = b.z; vv[4 * k + 3] = b.w;
     }
+    const float bc1 = ad.bc_dev ? ad.bc_dev[0] : ad.bc1;
+    const float bc2 = ad.bc_dev ? ad.bc_dev[1] : ad.bc2;
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
         mm[j] = ad.b1 * mm[j] + (1.f - ad.b1) * gr[j];
         vv[j] = ad.b2 * vv[j] + (1.f - ad.b2) * gr[j] * gr[j];
-        const float mh = mm[j] / ad.bc1, vh = vv[j] / ad.bc2;
+        const float mh = mm[j] / bc1, vh = vv[j] / bc2;
         p[j] -= ad.lr * mh / (sqrtf(vh) + ad.eps);
     }
 #pragma unroll

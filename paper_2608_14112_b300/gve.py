@@ -47,7 +47,7 @@ class Dims(ctypes.Structure):
 
 class EvalOpts(ctypes.Structure):
     _fields_ = [("trunc_k", ctypes.c_float), ("rho0", ctypes.c_float), ("normalized", ctypes.c_int32),
-                ("brick", ctypes.c_int32)]
+                ("brick", ctypes.c_int32), ("gaussians_per_block", ctypes.c_int32)]
 
 
 class AllocOpts(ctypes.Structure):
@@ -66,6 +66,10 @@ class Stats(ctypes.Structure):
                 ("psnr_final", ctypes.c_double), ("brick_pairs", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("iters_done", ctypes.c_int32), ("retries", ctypes.c_int32), ("ms_total", ctypes.c_float),
                 ("ms_brick", ctypes.c_float), ("ms_bin", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class Volume(ctypes.Structure):
+    _fields_ = [("field_dev", ctypes.c_void_p), ("dims", Dims), ("n", ctypes.c_int64)]
 
 
 class AllocInfo(ctypes.Structure):
@@ -107,8 +111,11 @@ def lib():
             L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), P]
             L.gve_evaluate_noalloc.argtypes = [P, i64, Dims, ctypes.POINTER(EvalOpts), P, P]
+            L.gve_refine_batch.argtypes = [P, i32, ctypes.POINTER(Volume), P, ctypes.POINTER(Schedule), P, P, P,
+                                           ctypes.POINTER(Stats), P]
+            L.gve_autotune.argtypes = [P, i32, ctypes.POINTER(Volume), P, ctypes.POINTER(EvalOpts), P, P]
             for f in ("gve_allocate", "gve_evaluate", "gve_loss_grad", "gve_backward", "gve_refine", "gve_bin",
-                      "gve_count_pairs", "gve_evaluate_noalloc"):
+                      "gve_count_pairs", "gve_evaluate_noalloc", "gve_refine_batch", "gve_autotune"):
                 getattr(L, f).restype = st
             _lib = L
     return _lib
@@ -168,9 +175,11 @@ class EvalOptions:
     rho0: float = 0.05
     normalized: bool = True
     brick: int = 8
+    gaussians_per_block: int = 0
 
     def c(self) -> EvalOpts:
-        return EvalOpts(float(self.trunc_k), float(self.rho0), int(bool(self.normalized)), int(self.brick))
+        return EvalOpts(float(self.trunc_k), float(self.rho0), int(bool(self.normalized)), int(self.brick),
+                        int(self.gaussians_per_block))
 
 
 def gve_evaluate(prims: torch.Tensor, shape, opts: EvalOptions | None = None, out: torch.Tensor | None = None):
@@ -234,6 +243,61 @@ def gve_refine(prims: torch.Tensor, field: torch.Tensor, iters: int, lr: float =
     if not want_stats:
         return None
     return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def _volumes(fields, counts):
+    vols = (Volume * len(fields))()
+    for i, (f, n) in enumerate(zip(fields, counts)):
+        _field(f)
+        vols[i] = Volume(ctypes.c_void_p(f.data_ptr()), _dims(f.shape), int(n))
+    return vols
+
+
+def gve_refine_batch(prims: torch.Tensor, fields, counts, iters: int, lr: float = 1e-2, beta1: float = 0.9,
+                     beta2: float = 0.999, eps: float = 1e-15, mask_thresh: float = -1.0, step0: int = 0,
+                     opts: EvalOptions | None = None, adam_state: torch.Tensor | None = None,
+                     trace: torch.Tensor | None = None):
+    """Batched refinement of ``len(fields)`` volumes whose records are
+    concatenated in ``prims`` (``counts[v]`` rows each, volume order), one
+    CUDA graph launch per iteration.  Returns (per-volume final PSNR list,
+    stats dict)."""
+    prims = _prims(prims)
+    if sum(int(n) for n in counts) != prims.shape[0]:
+        raise ValueError("counts must add up to the number of records")
+    vols = _volumes(fields, counts)
+    sched = Schedule(int(iters), float(lr), float(beta1), float(beta2), float(eps), float(mask_thresh), int(step0),
+                     (opts or EvalOptions()).c())
+    if adam_state is not None and (adam_state.shape != (2, prims.shape[0], 12) or not adam_state.is_contiguous()):
+        raise ValueError("adam_state must be float32 (2, N, 12)")
+    if trace is not None and (trace.dtype != torch.float64 or trace.numel() < iters * len(fields)):
+        raise ValueError("trace must be float64 with iters * nvol entries")
+    psnr = (ctypes.c_double * len(fields))()
+    st = Stats()
+    c = context(prims.device.index)
+    _check(lib().gve_refine_batch(c, len(fields), vols, _ptr(prims), ctypes.byref(sched), _ptr(adam_state),
+                                  _ptr(trace), psnr, ctypes.byref(st), _stream(prims.device)), c)
+    return list(psnr), {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def gve_autotune(prims: torch.Tensor, fields, counts, opts: EvalOptions | None = None):
+    """Fastest (brick, gaussians_per_block) for this batch; returns
+    (EvalOptions, {(brick, chunk): ms})."""
+    prims = _prims(prims)
+    vols = _volumes(fields, counts)
+    base = opts or EvalOptions()
+    o = base.c()
+    ms = (ctypes.c_float * 6)()
+    c = context(prims.device.index)
+    _check(lib().gve_autotune(c, len(fields), vols, _ptr(prims), ctypes.byref(o), ms, _stream(prims.device)), c)
+    table = {}
+    k = 0
+    for b in (4, 8, 16):
+        for ch in (32, 64):
+            table[(b, ch)] = float(ms[k])
+            k += 1
+    best = EvalOptions(trunc_k=base.trunc_k, rho0=base.rho0, normalized=base.normalized, brick=int(o.brick),
+                       gaussians_per_block=int(o.gaussians_per_block))
+    return best, table
 
 
 def gve_allocate(field: torch.Tensor, budget: int, detail_frac: float = 0.55, occ_thresh: float = 0.02,

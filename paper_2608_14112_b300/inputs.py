@@ -87,7 +87,7 @@ def grf(shape, seed: int) -> np.ndarray:
     K[0, 0, 0] = 1.0
     F *= K ** (-11.0 / 6.0)
     F[0, 0, 0] = 0.0
-    return _normalise(np.fft.irfftn(F, s=(nz, ny, nx)))
+    return _normalise(np.fft.irfftn(F, s=(nz, ny, nx), axes=(0, 1, 2)))
 
 
 def _interp_matrix(n: int, L: int, dtype, device):

@@ -214,3 +214,34 @@ def test_allocate_grf_and_budget_error():
     with pytest.raises(gve.BudgetError) as ei:
         gve.gve_allocate(dev(W), 1000, seed=1)
     assert ei.value.feasible_max == st2["feasible_max"]
+
+
+BRICK_VARIANTS = [(4, 0), (16, 0), (8, 32), (4, 32), (16, 32)]
+
+
+@pytest.mark.parametrize("brick,chunk", BRICK_VARIANTS)
+@pytest.mark.parametrize("case", ["ragged", "long_lists", "small_gauss"])
+def test_brick_variants_bin_eval_grad(case, brick, chunk):
+    """Other brick edges and chunk sizes: bit-exact binning and kept-pair
+    counts, the same field and gradient tolerances."""
+    dims, n, lo, hi, seed = CASES[case]
+    shape = (dims[2], dims[1], dims[0])
+    rng = np.random.default_rng(seed + 20)
+    p = rand_prims(rng, n, dims, lo, hi)
+    opts = gve.EvalOptions(brick=brick, gaussians_per_block=chunk)
+    counts, sk, sg, start, end = O.bin_sorted(p, dims, 3.0, brick)
+    gc, gk, gg, gs, ge = gve.gve_bin(dev(p), shape, opts)
+    np.testing.assert_array_equal(gc.numpy(), counts.astype(np.int64))
+    np.testing.assert_array_equal(gk.numpy(), sk.astype(np.int64))
+    np.testing.assert_array_equal(gg.numpy(), sg.astype(np.int64))
+    np.testing.assert_array_equal(gs.numpy(), start.astype(np.int64))
+    np.testing.assert_array_equal(ge.numpy(), end.astype(np.int64))
+    kept, cand = gve.gve_count_pairs(dev(p), shape, opts)
+    assert kept == O.count_kept(p, dims, 3.0)
+    _, _, vt = O.eval_region(p, dims)
+    assert rel_l2(gve.gve_evaluate(dev(p), shape, opts).cpu().numpy(), vt) <= FIELD_TOL
+    field = rng.uniform(0, 1, shape).astype(np.float32)
+    L, g, sse = O.loss_grad(p.astype(np.float64), field)
+    gg2, gsse = gve.gve_loss_grad(dev(p), dev(field), opts)
+    assert abs(gsse[1].item() - sse) <= 1e-5 * sse
+    assert rel_l2(gg2.cpu().numpy(), g) <= GRAD_TOL

@@ -47,9 +47,9 @@ def test_struct_layouts_match_header():
     """ctypes mirrors of the C structs have the sizes the C compiler gives."""
     from paper_2608_14112_b300 import gve
     assert ctypes.sizeof(gve.Dims) == 12
-    assert ctypes.sizeof(gve.EvalOpts) == 16
+    assert ctypes.sizeof(gve.EvalOpts) == 20
     assert ctypes.sizeof(gve.AllocOpts) == 32
-    assert ctypes.sizeof(gve.Schedule) == 44
+    assert ctypes.sizeof(gve.Schedule) == 48
     assert ctypes.sizeof(gve.Stats) == 72
     assert ctypes.sizeof(gve.AllocInfo) == 56
 

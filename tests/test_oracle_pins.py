@@ -556,3 +556,20 @@ def test_count_kept_brute_force():
     brute = sum(O.pred_t(p32[i], x, y, z) > T for i in range(6)
                 for z in range(7) for y in range(8) for x in range(9))
     assert O.count_kept(p32, dims, 3.0) == brute
+
+
+def test_binning_empty_bricks_are_zero_ranges():
+    """Bricks with no pair get [0, 0), wherever they sit in the key order."""
+    dims = (40, 8, 8)
+    p = np.zeros((2, 12))
+    p[:, 3:6] = np.log(0.5)
+    p[:, 6] = 1.0
+    p[:, 10] = 0.5
+    p[0, 0:3] = [2.0, 4.0, 4.0]
+    p[1, 0:3] = [37.0, 4.0, 4.0]
+    _, sk, sg, start, end = O.bin_sorted(p.astype(np.float32), dims, 3.0, 4)
+    occupied = set(sk.tolist())
+    for b in range(start.size):
+        if b not in occupied:
+            assert start[b] == 0 and end[b] == 0
+    assert len(occupied) >= 2

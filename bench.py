@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headline", "mid", "small", "autograd"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "mid", "small", "autograd", "batched"], default="headline")
+    ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample", type=int, default=192, help="edge of the CPU sample sub-volume")
@@ -208,6 +209,54 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """16 uneven GRF volumes (8 cubes 96^3..384^3, 8 slabs), budgets = voxels
+    / 64 rounded half-up to 1,024: batched encode (one graph launch per
+    iteration) against the same volumes encoded one after another."""
+    import numpy as np
+    import torch
+    from paper_2608_14112_b300 import batched
+    from paper_2608_14112_b300 import build as gbuild
+    from paper_2608_14112_b300 import gve, inputs
+
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    fields = [inputs.grf(shp, seed=sd, device=dev) for shp, sd in zip(inputs.BATCHED_SHAPES, inputs.BATCHED_SEEDS)]
+    budgets = [inputs.batched_budget(shp) for shp in inputs.BATCHED_SHAPES]
+    iters = args.steps
+    torch.cuda.synchronize()
+    # warm-up (also autotunes) on a short schedule
+    warm = batched.encode_batch(fields, budgets, iters=max(args.warmup, 1), seed=args.seed, autotune=args.autotune)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = batched.encode_batch(fields, budgets, iters=iters, seed=args.seed, autotune=False, opts=warm.options)
+    res.tune_ms = warm.tune_ms
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    # the same volumes one after another through gve_refine
+    t0 = time.perf_counter()
+    psnr_seq = []
+    for f, n in zip(fields, budgets):
+        P, _ = gve.gve_allocate(f, n, seed=args.seed)
+        st = gve.gve_refine(P, f, iters=iters, opts=warm.options)
+        psnr_seq.append(st["psnr_final"])
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    nvox = int(sum(np.prod(s) for s in inputs.BATCHED_SHAPES))
+    out = {"metric": "batched encode of 16 uneven volumes: iterations/s of the whole batch",
+           "value": iters / res.refine_s, "unit": "iters/s", "n_gpus": 1, "steps": iters, "warmup": args.warmup,
+           "ms_per_step": 1e3 * res.refine_s / iters, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batched_16_grf", "voxels": nvox, "gaussians": int(sum(budgets)),
+                      "brick": res.options.brick, "gaussians_per_block": res.options.gaussians_per_block},
+           "batched_wall_s": t_batch, "sequential_wall_s": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+           "psnr_batched": res.psnr, "psnr_sequential": psnr_seq,
+           "max_psnr_gap_db": float(np.max(np.abs(np.array(res.psnr) - np.array(psnr_seq)))),
+           "alloc_s": res.alloc_s, "autotune_ms": {f"{k[0]}x{k[1]}": v for k, v in res.tune_ms.items()}}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -234,12 +283,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     alloc_ms = e0.elapsed_time(e1)
     prims0 = prims.clone()
+    opts = gve.EvalOptions()
+    tune = None
+    if args.autotune:
+        vol = [V]
+        opts, tune = gve.gve_autotune(prims, vol, [w["budget"]], opts)
     state = torch.zeros((2, w["budget"], 12), dtype=torch.float32, device=dev)
     init_psnr = None
     if args.warmup > 0:
-        st = gve.gve_refine(prims, V, iters=args.warmup, lr=w["lr"], adam_state=state)
+        st = gve.gve_refine(prims, V, iters=args.warmup, lr=w["lr"], adam_state=state, opts=opts)
         init_psnr = st["psnr_final"]
-    kept0, cand0 = gve.gve_count_pairs(prims, shape)
+    kept0, cand0 = gve.gve_count_pairs(prims, shape, opts)
 
     def barrier():
         if ws > 1:
@@ -251,7 +305,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    st = gve.gve_refine(prims, V, iters=args.steps, lr=w["lr"], adam_state=state, step0=args.warmup)
+    st = gve.gve_refine(prims, V, iters=args.steps, lr=w["lr"], adam_state=state, step0=args.warmup, opts=opts)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -262,7 +316,7 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    kept1, cand1 = gve.gve_count_pairs(prims, shape)
+    kept1, cand1 = gve.gve_count_pairs(prims, shape, opts)
     value = ws * args.steps / (ms / 1e3)
 
     # dominant kernel: the fused brick evaluator (forward + backward)
@@ -296,7 +350,7 @@ def run_ours(args):
             Vd.copy_(Vh, non_blocking=True)
             gve.gve_allocate(Vd, w["budget"], seed=args.seed, out=pd)
             st_e.zero_()
-            s2 = gve.gve_refine(pd, Vd, iters=args.e2e_iters, lr=w["lr"], adam_state=st_e)
+            s2 = gve.gve_refine(pd, Vd, iters=args.e2e_iters, lr=w["lr"], adam_state=st_e, opts=opts)
             ph.copy_(pd, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -318,11 +372,13 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": w["name"], "voxels": int(np.prod(shape)), "gaussians": w["budget"],
-                          "trunc_k": 3.0, "brick": 8, "lr": w["lr"], "parallelism": "replicas" if ws > 1 else "1 GPU",
+                          "trunc_k": 3.0, "brick": opts.brick, "gaussians_per_block": opts.gaussians_per_block or 64,
+                          "lr": w["lr"], "parallelism": "replicas" if ws > 1 else "1 GPU",
                           "l2": "inputs larger than L2 (4.3 GB field) at the headline size; no flush"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": int(st["launches"]),
-               "alloc_ms": alloc_ms, "alloc": info, "psnr_after_warmup": init_psnr,
+               "alloc_ms": alloc_ms, "alloc": info,
+               "autotune_ms": ({f"{k[0]}x{k[1]}": v for k, v in tune.items()} if tune else None), "psnr_after_warmup": init_psnr,
                "psnr_after_steps": st["psnr_final"], "stage_ms_per_iter": {
                    "bin": st["ms_bin"] / max(args.steps, 1), "brick": brick_ms,
                    "rest": ms / args.steps - st["ms_bin"] / max(args.steps, 1) - brick_ms}}
@@ -336,6 +392,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -70,15 +70,29 @@ def blobs(n: int = 64, n_blobs: int = 40, seed: int = 1, shape=None) -> np.ndarr
     return _normalise(V)
 
 
-def grf(shape, seed: int) -> np.ndarray:
+def grf(shape, seed: int, device=None):
     """Gaussian random field, shell spectrum E(k) ~ k^-5/3 (so |F(k)| ~
     k^-11/6), white-noise phases, zero mean mode.  ``shape`` = (nx, ny, nz)
-    or an int for a cube."""
+    or an int for a cube.  With ``device`` the spectral filtering runs in
+    torch there and a float32 tensor is returned (same white noise)."""
     if isinstance(shape, int):
         shape = (shape, shape, shape)
     nx, ny, nz = shape
     rng = np.random.Generator(np.random.PCG64(seed))
     noise = rng.standard_normal((nz, ny, nx)).astype(np.float64)
+    if device is not None:
+        t = torch.from_numpy(noise).to(device)
+        F = torch.fft.rfftn(t)
+        kz = torch.fft.fftfreq(nz, device=device, dtype=torch.float64) * nz
+        ky = torch.fft.fftfreq(ny, device=device, dtype=torch.float64) * ny
+        kx = torch.fft.rfftfreq(nx, device=device, dtype=torch.float64) * nx
+        K = torch.sqrt(kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
+        K[0, 0, 0] = 1.0
+        F = F * K.pow(-11.0 / 6.0)
+        F[0, 0, 0] = 0.0
+        V = torch.fft.irfftn(F, s=(nz, ny, nx))
+        lo, hi = V.min(), V.max()
+        return ((V - lo) / (hi - lo)).float().contiguous()
     F = np.fft.rfftn(noise)
     kz = np.fft.fftfreq(nz) * nz
     ky = np.fft.fftfreq(ny) * ny

@@ -229,6 +229,64 @@ GVE_API gve_status gve_refine_batch(gve_ctx* ctx, int32_t nvol, const gve_volume
 GVE_API gve_status gve_autotune(gve_ctx* ctx, int32_t nvol, const gve_volume* vols, const float* prims_dev,
                                 gve_eval_opts* opts, float* ms_out, void* stream);
 
+/* ---- learned proposal (the learned-proposal form) --------------------------
+ * A small MLP maps each allocated Gaussian's local structure statistics to a
+ * correction of its initial amplitude and log-scales; plain allocation (an
+ * all-zero last layer) is its fallback and refinement judges it.  The model
+ * is one caller-owned float32 device buffer of GVE_MLP_FLOATS words: FP32
+ * master parameters [0, P), Adam moments [P, 3P), feature mean and inverse
+ * standard deviation [3P, 3P+32), BF16 copies of the parameters packed two
+ * per word [3P+32, 3P+32+P/2), P = GVE_MLP_PARAMS, parameter order
+ * W1[64][16] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[4][64] b4[4].
+ * The network's input is clamp((x - mean) * istd, -6, 6) per feature.
+ * Forward passes use the BF16 copies with FP32 accumulation; GELU is the
+ * erf form.  Outputs: (delta a, delta log s0, delta log s1, delta log s2). */
+#define GVE_MLP_PARAMS 9668
+#define GVE_MLP_FLOATS 33870
+
+/* 16 features per Gaussian from the field and its allocated record (seed
+ * voxel = round(mu)): log(1 + lambda_k/(343 gbar^2)) of the 7^3 structure
+ * tensor (3, ascending), |grad V|/gbar (capped at 10), mean, standard
+ * deviation, min and max of V over the 5^3 window, the 3 log-scales, a,
+ * the detail-seed flag (index < n_detail), the occupied fraction (V >
+ * occ_thresh) of the 5^3 window, the eigengap (lambda_2 - lambda_1)/lambda_3,
+ * V at the seed.  features_dev: [n][16] float32 output. */
+GVE_API gve_status gve_proposal_features(gve_ctx* ctx, const float* field_dev, gve_dims dims,
+                                         const float* prims_dev, int64_t n, int64_t n_detail, float gbar,
+                                         float occ_thresh, float* features_dev, void* stream);
+/* Y[rows][4] = MLP(X[rows][16]); save (optional) receives the three hidden
+ * pre-activations [rows][3][64] for a backward pass. */
+GVE_API gve_status gve_mlp_forward(gve_ctx* ctx, const float* model_dev, const float* X_dev, int64_t rows,
+                                   float* Y_dev, float* save_dev, void* stream);
+/* Gradient of the mean squared error mean_{rows,4}(MLP(X) - target)^2 with
+ * respect to the P parameters (dP_dev, [P] float32, overwritten); loss_dev
+ * (optional, device double) receives the loss. */
+GVE_API gve_status gve_mlp_grad(gve_ctx* ctx, const float* model_dev, const float* X_dev,
+                                const float* target_dev, int64_t rows, float* dP_dev, double* loss_dev,
+                                void* stream);
+/* One Adam step (bias-corrected, 1-based step) on the master parameters;
+ * refreshes the BF16 copies. */
+GVE_API gve_status gve_mlp_adam(gve_ctx* ctx, float* model_dev, const float* dP_dev, float lr, float beta1,
+                                float beta2, float eps, int32_t step, void* stream);
+/* Rounds the master parameters into the BF16 copies (after loading a model). */
+GVE_API gve_status gve_mlp_quantise(gve_ctx* ctx, float* model_dev, void* stream);
+/* prims[i]: a += delta a, log s += delta log s from MLP(features[i]), the
+ * log-scales clamped to [log 0.3, log(max(nx,ny,nz)/16)] (the allocator's
+ * scale caps, logarithms in double rounded once to float), so a zero
+ * correction leaves an allocation unchanged.  Rows with a non-finite output
+ * are left unchanged. */
+GVE_API gve_status gve_proposal_apply(gve_ctx* ctx, const float* model_dev, const float* features_dev,
+                                      float* prims_dev, int64_t n, gve_dims dims, void* stream);
+/* End-to-end gradient of the proposal: with prims_corrected = the output of
+ * gve_proposal_apply and grad_prims = dL/dprims at those records (from
+ * gve_loss_grad), writes (accumulate = 0) or adds (accumulate != 0) dL/dtheta
+ * [GVE_MLP_PARAMS] float32 into dP_dev.  The clamp of the log-scales passes
+ * no gradient where it was active.  n >= 1. */
+GVE_API gve_status gve_proposal_backward(gve_ctx* ctx, const float* model_dev, const float* features_dev,
+                                         const float* prims_corrected_dev, const float* grad_prims_dev,
+                                         int64_t n, gve_dims dims, int32_t accumulate, float* dP_dev,
+                                         void* stream);
+
 /* Brick binning introspection: the (brick, Gaussian) pairs that evaluation
  * uses, sorted by brick key (z-major brick index) and then by Gaussian index,
  * and per-brick [start, end) ranges.

@@ -573,3 +573,144 @@ def test_binning_empty_bricks_are_zero_ranges():
         if b not in occupied:
             assert start[b] == 0 and end[b] == 0
     assert len(occupied) >= 2
+
+
+def test_mlp_reference_gradient_central_differences():
+    """The FP64 MLP reference: analytic gradient against central differences."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(5)
+    params = rng.normal(size=M.P) * 0.2
+    mean, istd = rng.normal(size=16) * 0.1, rng.uniform(0.5, 2.0, 16)
+    X = rng.normal(size=(9, 16))
+    T = rng.normal(size=(9, 4)) * 0.3
+    L, g = M.loss_grad(params, mean, istd, X, T)
+    h = 1e-6
+    for idx in rng.choice(M.P, 60, replace=False).tolist() + [M.P - 1, 0, 1100, 9400]:
+        pp, pm = params.copy(), params.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        fd = (M.loss_grad(pp, mean, istd, X, T)[0] - M.loss_grad(pm, mean, istd, X, T)[0]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(abs(fd), 1e-3), idx
+
+
+def test_mlp_reference_gelu_closed_form():
+    from oracle import mlp as M
+    assert M.gelu(np.array(0.0)) == 0.0
+    x = np.linspace(-4, 4, 81)
+    # GELU(x) - GELU(-x) = x (odd part of x * Phi(x))
+    np.testing.assert_allclose(M.gelu(x) - M.gelu(-x), x, atol=1e-15)
+    h = 1e-6
+    np.testing.assert_allclose(M.gelu_d(x), (M.gelu(x + h) - M.gelu(x - h)) / (2 * h), atol=1e-8)
+
+
+def test_mlp_reference_backward_matches_mse_gradient_and_differences():
+    """backward() with an arbitrary upstream gradient: a linear functional
+    sum(C * y) has gradient backward(C), checked by central differences."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(8)
+    params = rng.normal(size=M.P) * 0.2
+    mean, istd = rng.normal(size=16) * 0.1, rng.uniform(0.5, 2.0, 16)
+    X = rng.normal(size=(7, 16))
+    C = rng.normal(size=(7, 4))
+    g = M.backward(params, mean, istd, X, C)
+    h = 1e-6
+    for idx in rng.choice(M.P, 40, replace=False).tolist() + [M.P - 1, 9664, 0]:
+        pp, pm = params.copy(), params.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        fd = ((M.forward(pp, mean, istd, X)[0] * C).sum() - (M.forward(pm, mean, istd, X)[0] * C).sum()) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(abs(fd), 1e-3), idx
+
+
+def test_proposal_chain_central_differences_and_clamp():
+    """The end-to-end chain theta -> y -> corrected records -> sum(G * records):
+    backward(upstream(...)) against central differences; a record whose
+    log-scales sit at the clamp passes no log-scale gradient."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(9)
+    params = rng.normal(size=M.P) * 0.1
+    mean, istd = np.zeros(16), np.ones(16)
+    n, dims = 6, (64, 48, 40)
+    X = rng.normal(size=(n, 16))
+    prm = rng.normal(size=(n, 12))
+    prm[:, 3:6] = rng.uniform(-0.5, 0.5, (n, 3))
+    prm[2, 3:6] = 5.0          # far above log(64/16): clamped whatever the correction
+    G = rng.normal(size=(n, 12))
+
+    def L(th):
+        y, _ = M.forward(th, mean, istd, X)
+        return float((G * M.apply(prm, y, dims)).sum())
+
+    y, _ = M.forward(params, mean, istd, X)
+    pc = M.apply(prm, y, dims)
+    lo, hi = M.ls_bounds(dims)
+    assert np.all(pc[2, 3:6] == hi) and abs(hi - np.log(4.0)) < 1e-6 and abs(lo - np.log(0.3)) < 1e-6
+    dY = M.upstream(pc, G, y, dims)
+    assert np.all(dY[2, 1:] == 0.0) and dY[2, 0] == G[2, 10]
+    g = M.backward(params, mean, istd, X, dY)
+    h = 1e-5
+    for idx in rng.choice(M.P, 40, replace=False).tolist() + [9408, 9664, 9667]:
+        pp, pm = params.copy(), params.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        fd = (L(pp) - L(pm)) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(abs(fd), 1e-2), idx
+
+
+def test_proposal_features_linear_field_closed_form():
+    """On a linear field V = a x + b y + c z every feature has a closed form:
+    central and one-sided differences both give the exact gradient g, so the
+    7^3 structure tensor is cnt * g g^T (eigenvalues 0, 0, cnt |g|^2); the 5^3
+    window's mean is V at its centre, its spread |g| sqrt(2) (variance of
+    a uniform offset in {-2..2} is 2 per axis), its extremes V -+ 2 sum|g_k|."""
+    from oracle import mlp as M
+    gx, gy, gz = 0.004, -0.003, 0.0015
+    nx, ny, nz = 20, 18, 16
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    V = (0.3 + gx * x + gy * y + gz * z).astype(np.float32)
+    prm = np.zeros((3, 12), np.float32)
+    prm[0, :3] = (9.2, 8.7, 7.9)        # interior seed (9, 9, 8)
+    prm[1, :3] = (0.2, 1.1, 15.4)       # border seed (0, 1, 15): clipped windows
+    prm[2, :3] = (10.0, 10.0, 10.0)
+    prm[:, 3:6] = (0.1, -0.2, 0.3)
+    prm[:, 10] = 0.5
+    gbar = 0.01
+    F = M.features(V, prm, 1, gbar)
+    g2 = gx * gx + gy * gy + gz * gz
+    c = np.array([9, 9, 8])
+    Vc = float(np.float32(0.3 + gx * 9 + gy * 9 + gz * 8))
+    np.testing.assert_allclose(F[0, 0:2], 0.0, atol=1e-8)   # float32 field: differences exact to ~1e-7
+    np.testing.assert_allclose(F[0, 2], np.log1p(343 * g2 / (343 * gbar * gbar)), rtol=1e-5)
+    np.testing.assert_allclose(F[0, 3], np.sqrt(g2) / gbar, rtol=1e-5)
+    np.testing.assert_allclose(F[0, 4], Vc, atol=1e-6)
+    np.testing.assert_allclose(F[0, 5], np.sqrt(2.0 * g2), rtol=1e-4)
+    span = 2 * (abs(gx) + abs(gy) + abs(gz))
+    np.testing.assert_allclose(F[0, 6:8], [Vc - span, Vc + span], atol=1e-6)
+    np.testing.assert_allclose(F[0, 8:11], [0.1, -0.2, 0.3], atol=1e-7)
+    assert F[0, 11] == np.float32(0.5) and F[0, 12] == 1.0 and F[1, 12] == 0.0
+    assert F[0, 13] == 1.0 and abs(F[0, 14]) < 1e-6 and abs(F[0, 15] - Vc) < 1e-7
+    # border seed: the 7^3 window holds 4*5*4 voxels, the gradient is still exact
+    cnt = 4 * 5 * 4
+    np.testing.assert_allclose(F[1, 2], np.log1p(cnt * g2 / (343 * gbar * gbar)), rtol=1e-5)
+    np.testing.assert_allclose(F[1, 3], np.sqrt(g2) / gbar, rtol=1e-5)
+    w = V[13:16, 0:4, 0:3].astype(np.float64)   # 5^3 window clipped to 3 x 4 x 3
+    np.testing.assert_allclose(F[1, 4:8], [w.mean(), w.std(), w.min(), w.max()], atol=1e-7)
+    assert c.sum() == 26
+
+
+def test_bf16_round_nearest_even():
+    """bfloat16 keeps 8 significant bits: spacing 2^-7 on [1, 2).  Halfway
+    cases go to the even neighbour, others to the nearest."""
+    from oracle import mlp as M
+    x = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20, -(1 + 2.0 ** -8), 3.0e-3, 0.0],
+                 np.float32)
+    r = M.bf16_round(x)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1 + 2.0 ** -6 and r[3] == 1 + 2.0 ** -7 and r[4] == -1.0
+    assert r[6] == 0.0 and abs(r[5] - 3.0e-3) <= 3.0e-3 * 2.0 ** -8
+    y = np.random.default_rng(3).normal(size=1000).astype(np.float32)
+    ry = M.bf16_round(y)
+    # nearest: no representable bf16 (8 significant bits) lies closer
+    e = np.floor(np.log2(np.abs(y.astype(np.float64))))
+    ulp = 2.0 ** (e - 7)
+    assert np.all(np.abs(ry - y) <= ulp / 2 + 1e-30)
+    assert np.all(np.mod(ry / ulp, 1.0) == 0.0)

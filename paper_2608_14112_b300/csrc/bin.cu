@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
         double wd = 1.0 / (1.0 + exp(-(double)pf[11]));
         r0 = make_float4(pf[0], pf[1], pf[2], (float)Q00);
         r1 = make_float4((float)Q11, (float)Q22, (float)dm(2.0, Q01), (float)dm(2.0, Q02));
-        r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, 0.f);
+        r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, pf[10]);
 
         // conservative brick cover
         double smin = s[0], smax = s[0];

@@ -9,10 +9,10 @@
 // s & 1, z quarter = s >> 1) may hold a kept pair.  For B = 8 this is a
 // 64-thread CTA and 8x4x2 sub-bricks.
 //
-// Phase 1 (forward): each lane owns one row of B voxels along x.  For every
-// listed Gaussian with a live sub-brick among the warp's rows (a
-// warp-uniform skip otherwise), the keep
-// exponent t is evaluated by the fixed float32 chain
+// Phase 1 (forward): each lane owns one row of B voxels along x.  Each warp
+// takes the listed Gaussians with a live sub-brick among its rows (a ballot
+// over the staged chunk), two at a time for independent work, in list
+// order.  The keep exponent t is evaluated by the fixed float32 chain
 //     dy = y - mu_y, dz = z - mu_z, dx = x - mu_x,
 //     b = fma(qxy2, dy, qxz2*dz), c = fma(dy, fma(qyy, dy, qyz2*dz), dz*(qzz*dz)),
 //     t = fma(dx, fma(qxx, dx, b), c)
@@ -28,10 +28,12 @@
 // Phase 2 (backward): the (Gaussian, live sub-brick) tasks are compacted
 // (sub-brick-major) and spread over all threads; a task recomputes G by the
 // same chain on its B^3/8 voxels and accumulates
-//     A = sum G gn,  Bs = sum G gd,  S1 = sum h d,  S2 = sum h d d^T,
-//     h = G (alpha gn + beta gd)      (S1, S2 scaled by -1/2 in the chain rule)
-// with the x- and z-dependence factored per row and per slice, in packed
-// f32x2 arithmetic.  Task sums meet in shared memory (float atomics); one
+//     A = sum G gn,  H = sum h,  S1 = sum h d,  S2 = sum h d d^T,
+//     h = G (a gn + gd)
+// (dL/da = w A, dL/dw = H, and the chain rule scales S1, S2 by -w/2), with
+// the y- and z-dependence factored per row and per slice and the
+// x-moments taken against the brick-local offset X (constants of the
+// unrolled loop), shifted to dx once per task, in packed f32x2 arithmetic.  Task sums meet in shared memory (float atomics); one
 // thread per Gaussian then issues three 16-byte vector atomics into its
 // global accumulator.  Nothing per pair or per voxel goes to HBM.
 #include "gve_int.cuh"
@@ -124,26 +126,51 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
         if (ch > 0) __syncthreads();
         stage_chunk<NT>(a, s0, c0, cnt, s_rec, s_msk, tid);
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            if (!(s_msk[j] & wmask)) continue;  // warp-uniform skip
-            const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
-            const float dy = __fsub_rn(fy, r0.y), dz = __fsub_rn(fz, r0.z);
-            const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
-            const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
-            const float2 nmu = f2(-r0.x), qxx = f2(r0.w), b2 = f2(b), c2 = f2(c), al = f2(r2.y), be = f2(r2.z);
+        // the warp's live Gaussians of this chunk, two at a time (list order kept)
+        for (int base = 0; base < cnt; base += 32) {
+            const int jl = base + lane;
+            uint32_t bal = __ballot_sync(0xffffffffu, jl < cnt && (s_msk[jl] & wmask));
+            while (bal) {
+                const int j1 = base + __ffs(bal) - 1;
+                bal &= bal - 1;
+                const bool two = bal != 0;
+                const int j2 = two ? base + __ffs(bal) - 1 : j1;
+                if (two) bal &= bal - 1;
+                const float4 r0 = s_rec[3 * j1], r1 = s_rec[3 * j1 + 1], r2 = s_rec[3 * j1 + 2];
+                const float4 u0 = s_rec[3 * j2], u1 = s_rec[3 * j2 + 1], u2 = s_rec[3 * j2 + 2];
+                const float dy = __fsub_rn(fy, r0.y), dz = __fsub_rn(fz, r0.z);
+                const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
+                const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
+                const float ey = __fsub_rn(fy, u0.y), ez = __fsub_rn(fz, u0.z);
+                const float bu = __fmaf_rn(u1.z, ey, __fmul_rn(u1.w, ez));
+                const float cu = __fmaf_rn(ey, __fmaf_rn(u1.x, ey, __fmul_rn(u2.x, ez)), __fmul_rn(ez, __fmul_rn(u1.y, ez)));
+                const float2 nmu = f2(-r0.x), qxx = f2(r0.w), b2 = f2(b), c2 = f2(c), al = f2(r2.y), be = f2(r2.z);
+                const float2 nmv = f2(-u0.x), qxv = f2(u0.w), bv = f2(bu), cv = f2(cu);
+                const float2 alv = f2(two ? u2.y : 0.f), bev = f2(two ? u2.z : 0.f);
 #pragma unroll
-            for (int q = 0; q < HALF; ++q) {
-                const float2 dx = __fadd2_rn(make_float2((float)(gx0 + 2 * q), (float)(gx0 + 2 * q + 1)), nmu);
-                const float2 t = __ffma2_rn(dx, __ffma2_rn(qxx, dx, b2), c2);
-                float2 G;
-                G.x = t.x > T ? ex2_approx(t.x) : 0.f;
-                G.y = t.y > T ? ex2_approx(t.y) : 0.f;
-                if (MODE == kModeCount)
-                    kept += (unsigned)((t.x > T) && (2 * q < nxin)) + (unsigned)((t.y > T) && (2 * q + 1 < nxin));
-                num[q] = __ffma2_rn(al, G, num[q]);
-                den[q] = __ffma2_rn(be, G, den[q]);
+                for (int q = 0; q < HALF; ++q) {
+                    const float2 xq = make_float2((float)(gx0 + 2 * q), (float)(gx0 + 2 * q + 1));
+                    const float2 dx = __fadd2_rn(xq, nmu);
+                    const float2 t = __ffma2_rn(dx, __ffma2_rn(qxx, dx, b2), c2);
+                    const float2 dv = __fadd2_rn(xq, nmv);
+                    const float2 tv = __ffma2_rn(dv, __ffma2_rn(qxv, dv, bv), cv);
+                    float2 G, H;
+                    G.x = t.x > T ? ex2_approx(t.x) : 0.f;
+                    G.y = t.y > T ? ex2_approx(t.y) : 0.f;
+                    H.x = tv.x > T ? ex2_approx(tv.x) : 0.f;
+                    H.y = tv.y > T ? ex2_approx(tv.y) : 0.f;
+                    if (MODE == kModeCount) {
+                        kept += (unsigned)((t.x > T) && (2 * q < nxin)) + (unsigned)((t.y > T) && (2 * q + 1 < nxin));
+                        if (two)
+                            kept += (unsigned)((tv.x > T) && (2 * q < nxin)) + (unsigned)((tv.y > T) && (2 * q + 1 < nxin));
+                    }
+                    num[q] = __ffma2_rn(al, G, num[q]);
+                    den[q] = __ffma2_rn(be, G, den[q]);
+                    num[q] = __ffma2_rn(alv, H, num[q]);
+                    den[q] = __ffma2_rn(bev, H, den[q]);
+                }
+                if (MODE == kModeCount) live += (unsigned long long)nxin * (two ? 2u : 1u);
             }
-            if (MODE == kModeCount) live += (unsigned long long)nxin;
         }
     }
 
@@ -293,8 +320,10 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
             for (int q = 0; q < HALF; ++q)
                 dx[q] = __fadd2_rn(make_float2(fxb + (float)(2 * q), fxb + (float)(2 * q + 1)), nmu);
             const int yb = SY * (sbt & 1), zb = SZ * (sbt >> 1);
-            const float2 qxx = f2(r0.w), al = f2(r2.y), be = f2(r2.z);
-            float2 A = make_float2(0.f, 0.f), Bs = A, S1x = A, S1y = A, S1z = A;
+            const float2 qxx = f2(r0.w), amp = f2(r2.w);
+            // h = G (a gn + gd); x-moments against the brick-local X = x - x0,
+            // shifted to dx = X + (x0 - mu_x) once per task below
+            float2 A = make_float2(0.f, 0.f), S0 = A, S1x = A, S1y = A, S1z = A;
             float2 Syy = A, Szz = A, Sxy = A, Sxz = A, Syz = A;
             float2 R2 = A;
 #pragma unroll
@@ -318,15 +347,13 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
                         float2 G;
                         G.x = t.x > T ? ex2_approx(t.x) : 0.f;
                         G.y = t.y > T ? ex2_approx(t.y) : 0.f;
-                        const float2 Ggn = __fmul2_rn(G, make_float2(gv.x, gv.y));
-                        const float2 Ggd = __fmul2_rn(G, make_float2(gv.z, gv.w));
-                        A = __fadd2_rn(A, Ggn);
-                        Bs = __fadd2_rn(Bs, Ggd);
-                        const float2 h = __ffma2_rn(al, Ggn, __fmul2_rn(be, Ggd));
+                        const float2 gn = make_float2(gv.x, gv.y);
+                        const float2 h = __fmul2_rn(G, __ffma2_rn(amp, gn, make_float2(gv.z, gv.w)));
+                        A = __ffma2_rn(G, gn, A);
                         R0 = __fadd2_rn(R0, h);
-                        const float2 hx = __fmul2_rn(h, dx[q]);
-                        R1 = __fadd2_rn(R1, hx);
-                        R2 = __ffma2_rn(hx, dx[q], R2);
+                        const float2 X = make_float2((float)(2 * q), (float)(2 * q + 1));
+                        R1 = __ffma2_rn(h, X, R1);
+                        R2 = __ffma2_rn(h, __fmul2_rn(X, X), R2);
                     }
                     const float2 dy2 = f2(dy);
                     S1y = __ffma2_rn(dy2, R0, S1y);
@@ -338,23 +365,26 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
                     Ty = __fadd2_rn(Ty, dyR0);
                 }
                 const float2 dz2 = f2(dz);
+                S0 = __fadd2_rn(S0, T0);
                 S1x = __fadd2_rn(S1x, T1);
                 S1z = __ffma2_rn(dz2, T0, S1z);
                 Sxz = __ffma2_rn(dz2, T1, Sxz);
                 Syz = __ffma2_rn(dz2, Ty, Syz);
                 Szz = __ffma2_rn(__fmul2_rn(dz2, dz2), T0, Szz);
             }
+            const float del = __fsub_rn(fxb, r0.x);
+            const float s0 = S0.x + S0.y, sx = S1x.x + S1x.y, sy = S1y.x + S1y.y, sz = S1z.x + S1z.y;
             float* sa = s_acc + j * kAccStride;
             atomicAdd(sa + 0, A.x + A.y);
-            atomicAdd(sa + 1, Bs.x + Bs.y);
-            atomicAdd(sa + 2, S1x.x + S1x.y);
-            atomicAdd(sa + 3, S1y.x + S1y.y);
-            atomicAdd(sa + 4, S1z.x + S1z.y);
-            atomicAdd(sa + 5, R2.x + R2.y);
+            atomicAdd(sa + 1, s0);
+            atomicAdd(sa + 2, fmaf(del, s0, sx));
+            atomicAdd(sa + 3, sy);
+            atomicAdd(sa + 4, sz);
+            atomicAdd(sa + 5, fmaf(del, fmaf(del, s0, 2.f * sx), R2.x + R2.y));
             atomicAdd(sa + 6, Syy.x + Syy.y);
             atomicAdd(sa + 7, Szz.x + Szz.y);
-            atomicAdd(sa + 8, Sxy.x + Sxy.y);
-            atomicAdd(sa + 9, Sxz.x + Sxz.y);
+            atomicAdd(sa + 8, fmaf(del, sy, Sxy.x + Sxy.y));
+            atomicAdd(sa + 9, fmaf(del, sz, Sxz.x + Sxz.y));
             atomicAdd(sa + 10, Syz.x + Syz.y);
         }
         __syncthreads();

@@ -3,7 +3,7 @@
 // Data layout in HBM (per context):
 //   prepped record  3 x float4 per Gaussian:
 //       r0 = (mu_x, mu_y, mu_z, qxx)      r1 = (qyy, qzz, qxy2, qxz2)
-//       r2 = (qyz2, alpha = w a, beta = w, 0)
+//       r2 = (qyz2, alpha = w a, beta = w, a)
 //     q.. = float32(-0.5 log2(e) Sigma^-1) entries (off-diagonals doubled),
 //     rounded once from an FP64 computation in a fixed order.
 //   bin record      20 words per Gaussian: whitening L (row-major 3x3),

@@ -45,10 +45,13 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
     const float nq = sqrtf(p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9]);
     ok = ok && nq > 0.f && isfinite(nq);
     if (ok) {
-        const float A = c0.x, Bs = c0.y;
-        const float S1[3] = {-0.5f * c0.z, -0.5f * c0.w, -0.5f * c1.x};
-        const float sxx = -0.5f * c1.y, syy = -0.5f * c1.z, szz = -0.5f * c1.w;
-        const float sxy = -0.5f * c2.x, sxz = -0.5f * c2.y, syz = -0.5f * c2.z;
+        // accumulated: A = sum G gn, H = sum h, moments of h = G (a gn + gd)
+        const float A = c0.x, H = c0.y;
+        const float w = 1.f / (1.f + expf(-p[11]));
+        const float hw = -0.5f * w;
+        const float S1[3] = {hw * c0.z, hw * c0.w, hw * c1.x};
+        const float sxx = hw * c1.y, syy = hw * c1.z, szz = hw * c1.w;
+        const float sxy = hw * c2.x, sxz = hw * c2.y, syz = hw * c2.z;
         const float S2[3][3] = {{sxx, sxy, sxz}, {sxy, syy, syz}, {sxz, syz, szz}};
         float s[3], D[3];
 #pragma unroll
@@ -106,9 +109,8 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
         gr[7] = (gx - qx * dot) / nq;
         gr[8] = (gy - qy * dot) / nq;
         gr[9] = (gz - qz * dot) / nq;
-        const float w = 1.f / (1.f + expf(-p[11]));
         gr[10] = w * A;
-        gr[11] = (p[10] * A + Bs) * w * (1.f - w);
+        gr[11] = H * w * (1.f - w);
     }
 
     if (!do_adam) {

@@ -292,13 +292,17 @@ GVE_API gve_status gve_proposal_backward(gve_ctx* ctx, const float* model_dev, c
  * and per-brick [start, end) ranges.
  *   counts_dev   [n] uint32 output: pairs per Gaussian.
  *   keys_dev, gids_dev  [cap] uint32 outputs.
+ *   masks_dev    [cap] uint8 output or NULL: the evaluator's sub-brick cover
+ *                of each pair (bit = y half + 2 * z quarter of the B x B/2 x
+ *                B/4 sub-bricks), a superset of the sub-bricks holding kept
+ *                voxels.
  *   ranges_dev   [2][nbricks] uint32 output (starts, then ends; 0,0 = empty).
  *   n_pairs      host output: number of pairs (synchronises).  If it exceeds
  *                cap, nothing is written and GVE_E_CAPACITY is returned. */
 GVE_API gve_status gve_bin(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
                    const gve_eval_opts* opts, uint32_t* counts_dev, uint32_t* keys_dev,
-                   uint32_t* gids_dev, int64_t cap, uint32_t* ranges_dev, int64_t* n_pairs,
-                   void* stream);
+                   uint32_t* gids_dev, uint8_t* masks_dev, int64_t cap, uint32_t* ranges_dev,
+                   int64_t* n_pairs, void* stream);
 
 /* Number of kept (voxel, Gaussian) pairs of the truncated field -- the
  * algorithmic work of one evaluation -- and the candidate pairs the brick

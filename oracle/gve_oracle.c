@@ -735,6 +735,41 @@ int64_t or_bin_emit(const float* p32, int64_t n, const int dims[3], float k, int
     return o;
 }
 
+/* Sub-bricks of listed bricks that hold kept pairs: for pair i (Gaussian
+ * gids[i], brick keys[i] of edge B), bit s = (y half) + 2 (z quarter) of
+ * masks[i] is set when a voxel centre of the B x B/2 x B/4 sub-brick s,
+ * inside the grid and the Gaussian's enumeration box, passes the float32
+ * keep test.  The evaluator's sub-brick masks must contain these bits. */
+void or_kept_submasks(const float* p32, const int dims[3], float k, int B, int64_t npairs, const uint32_t* keys,
+                      const uint32_t* gids, uint8_t* masks)
+{
+    const float T = pred_threshold(k);
+    const int nbx = (dims[0] + B - 1) / B, nby = (dims[1] + B - 1) / B;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < npairs; ++i) {
+        const float* r = p32 + 12 * (int64_t)gids[i];
+        double p[12];
+        for (int j = 0; j < 12; ++j) p[j] = (double)r[j];
+        gctx_t g;
+        activate(p, &g.A);
+        pred_coeffs(r, &g.P);
+        uint8_t m = 0;
+        if (g.A.valid && g.P.valid && enum_box(&g.A, k, 1, dims, g.lo, g.hi)) {
+            const int64_t key = keys[i];
+            const int bx = (int)(key % nbx), by = (int)((key / nbx) % nby), bz = (int)(key / ((int64_t)nbx * nby));
+            for (int zz = 0; zz < B; ++zz)
+                for (int yy = 0; yy < B; ++yy)
+                    for (int xx = 0; xx < B; ++xx) {
+                        const int x = bx * B + xx, y = by * B + yy, z = bz * B + zz;
+                        if (x < g.lo[0] || x > g.hi[0] || y < g.lo[1] || y > g.hi[1] || z < g.lo[2] || z > g.hi[2])
+                            continue;
+                        if (pred_t_of(&g.P, x, y, z) > T) m |= (uint8_t)(1u << ((yy / (B / 2)) + 2 * (zz / (B / 4))));
+                    }
+        }
+        masks[i] = m;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Allocation (Sec. III-E, Table I S1a..S1e).                                */
 /* ------------------------------------------------------------------------ */

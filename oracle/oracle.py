@@ -80,6 +80,8 @@ def lib():
             L.or_bin_count.restype = i64
             L.or_bin_emit.argtypes = [P, i64, P, f32, i32, P, P]
             L.or_bin_emit.restype = i64
+            L.or_kept_submasks.argtypes = [P, P, f32, i32, i64, P, P, P]
+            L.or_kept_submasks.restype = None
             L.or_grad_mag32.argtypes = [P, P, P]
             L.or_struct_tensor.argtypes = [P, P, i32, i32, i32, P]
             L.or_jacobi3.argtypes = [P, P, P]
@@ -279,6 +281,18 @@ def bin_sorted(p32, dims, k=3.0, B=8):
     start[empty] = 0
     end[empty] = 0
     return counts, sk, sg, start, end
+
+
+def kept_submasks(p32, dims, keys, gids, k=3.0, B=8) -> np.ndarray:
+    """Per listed (brick, Gaussian) pair, the 8-bit set of sub-bricks
+    (B x B/2 x B/4; bit = y half + 2 * z quarter) holding a kept voxel."""
+    p = _f32c(p32).reshape(-1, 12)
+    d = _dims(dims)
+    kk = np.ascontiguousarray(keys, np.uint32)
+    gg = np.ascontiguousarray(gids, np.uint32)
+    out = np.zeros(max(kk.size, 1), np.uint8)
+    lib().or_kept_submasks(_ptr(p), _ptr(d), float(k), int(B), int(kk.size), _ptr(kk), _ptr(gg), _ptr(out))
+    return out[:kk.size]
 
 
 # --------------------------------------------------------------------------

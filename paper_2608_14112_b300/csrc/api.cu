@@ -48,11 +48,15 @@ gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s)
     return GVE_OK;
 }
 
-__global__ void k_strip_mask(uint32_t* v, unsigned long long n)
+// split the sorted values into Gaussian ids and (optionally) sub-brick masks
+__global__ void k_strip_mask(uint32_t* v, uint8_t* masks, unsigned long long n)
 {
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        v[i] &= kGidMask;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t x = v[i];
+        if (masks) masks[i] = (uint8_t)(x >> kGidBits);
+        v[i] = x & kGidMask;
+    }
 }
 
 __global__ void k_reset_state(DevState* st)
@@ -374,8 +378,8 @@ gve_status gve_backward(gve_ctx* c, const float* prims, int64_t n, gve_dims d, c
 }
 
 gve_status gve_bin(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
-                   uint32_t* counts, uint32_t* keys, uint32_t* gids, int64_t cap, uint32_t* ranges,
-                   int64_t* n_pairs, void* stream)
+                   uint32_t* counts, uint32_t* keys, uint32_t* gids, uint8_t* masks, int64_t cap,
+                   uint32_t* ranges, int64_t* n_pairs, void* stream)
 {
     GVE_TRY(check_common(c, prims, n, d, o));
     if (!n_pairs || (n > 0 && !counts) || !ranges || cap < 0) return fail(c, GVE_E_INVALID, "null output");
@@ -393,7 +397,7 @@ gve_status gve_bin(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const 
         if (!keys || !gids) return fail(c, GVE_E_INVALID, "null pair outputs");
         GVE_CUDA(cudaMemcpyAsync(keys, c->keys[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
         GVE_CUDA(cudaMemcpyAsync(gids, c->vals[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
-        k_strip_mask<<<592, 256, 0, k.s>>>(gids, h.total);
+        k_strip_mask<<<592, 256, 0, k.s>>>(gids, masks, h.total);
     }
     GVE_CUDA(cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint32_t) * 2 * k.g.nbricks, cudaMemcpyDeviceToDevice, k.s), "copy");
     GVE_CUDA(cudaStreamSynchronize(k.s), "sync");

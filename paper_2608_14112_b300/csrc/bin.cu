@@ -166,11 +166,16 @@ __device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy
 
 // Sub-brick cover of a listed brick (an acceleration structure of the
 // evaluator, not part of the binning definition): bit s is set when the
-// B x B/2 x B/4 sub-brick s = (y half, z quarter) may hold a kept pair, by
-// the same whitened-distance lower bound around each sub-brick centre, with
-// half sizes ((B-1)/2, (B/2-1)/2, (B/4-1)/2) + 0.01 and the brick's K2.
-// Sub-bricks outside the grid get no bit.  Conservative: it never drops a
-// pair the keep test keeps.
+// B x B/2 x B/4 sub-brick s = (y half, z quarter) may hold a kept pair.  In
+// whitened coordinates the sub-brick's voxel centres (half sizes
+// h = ((B-1)/2, (B/2-1)/2, (B/4-1)/2) + 0.01) lie in the parallelepiped
+// P = {y + sum_i s_i l_i : |s_i| <= h_i} (y its centre, l_i the images of the
+// voxel axes).  Two lower bounds on min |P|^2 are tested against the brick's
+// K2: the axis-aligned one, sum_j max(0, |y_j| - sum_i h_i |l_ij|)^2, and the
+// separating-axis one along n = y / |y|, (|y| - sum_i h_i |n . l_i|)^2 when
+// positive.  The second is compared with a 1e-3 relative margin on K2, which
+// covers its float32 rounding.  Sub-bricks outside the grid get no bit.
+// Conservative: it never drops a pair the keep test keeps.
 __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, float muy, float muz, int B, int bx,
                                                   int by, int bz, int ny, int nz)
 {
@@ -187,20 +192,33 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, fl
         ec[j] = b.L[j * 3 + 2];
     }
     const float oyv = 0.25f * (float)B, ozv = 0.125f * (float)B;
+    const float K2m = b.K2 * 1.001f;
     uint32_t m = 0;
 #pragma unroll
     for (int sidx = 0; sidx < 8; ++sidx) {
         const int yh = sidx & 1, zq = sidx >> 1;
         if (by * B + (B / 2) * yh >= ny || bz * B + (B / 4) * zq >= nz) continue;
         const float oy = yh ? oyv : -oyv, oz = (float)(2 * zq - 3) * ozv;
-        float sq = 0.f;
+        float sq = 0.f, y[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const float y = fmaf(ec[j], oz, fmaf(eb[j], oy, yc[j]));
-            const float a = fmaxf(fabsf(y) - ea[j], 0.f);
+            y[j] = fmaf(ec[j], oz, fmaf(eb[j], oy, yc[j]));
+            const float a = fmaxf(fabsf(y[j]) - ea[j], 0.f);
             sq = fmaf(a, a, sq);
         }
-        if (sq <= b.K2) m |= 1u << sidx;
+        if (sq > b.K2) continue;
+        // separating axis along y: |y|^2 - sum_i h_i |y . l_i| > sqrt(K2) |y|
+        float y2 = 0.f, ylx = 0.f, yly = 0.f, ylz = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            y2 = fmaf(y[j], y[j], y2);
+            ylx = fmaf(y[j], b.L[j * 3 + 0], ylx);
+            yly = fmaf(y[j], b.L[j * 3 + 1], yly);
+            ylz = fmaf(y[j], b.L[j * 3 + 2], ylz);
+        }
+        const float D = y2 - fmaf(h0, fabsf(ylx), fmaf(h1, fabsf(yly), h2 * fabsf(ylz)));
+        if (D > 0.f && D * D > K2m * y2) continue;
+        m |= 1u << sidx;
     }
     return m;
 }

@@ -60,7 +60,7 @@ struct BrickShape {
     static constexpr int HALF = B / 2;  // voxel pairs per row
     static constexpr int SY = B / 2;    // sub-brick extent in y
     static constexpr int SZ = B / 4;    // sub-brick extent in z
-    static constexpr int MINB = B == 16 ? 3 : (B == 8 ? 12 : 16);
+    static constexpr int MINB = B == 16 ? 3 : (B == 8 ? 14 : 16);
 };
 
 template <int NT>
@@ -322,16 +322,17 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
             const int yb = SY * (sbt & 1), zb = SZ * (sbt >> 1);
             const float2 qxx = f2(r0.w), amp = f2(r2.w);
             // h = G (a gn + gd); x-moments against the brick-local X = x - x0,
-            // shifted to dx = X + (x0 - mu_x) once per task below
-            float2 A = make_float2(0.f, 0.f), S0 = A, S1x = A, S1y = A, S1z = A;
-            float2 Syy = A, Szz = A, Sxy = A, Sxz = A, Syz = A;
-            float2 R2 = A;
+            // shifted to dx = X + (x0 - mu_x) once per task below.  Per-voxel
+            // sums are packed; the per-row and per-slice sums are scalar, so
+            // they run beside the packed pipe instead of on it.
+            float2 A = make_float2(0.f, 0.f), R2 = A;
+            float S0 = 0.f, S1x = 0.f, S1y = 0.f, S1z = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
 #pragma unroll
             for (int zs = 0; zs < SZ; ++zs) {
                 const float dz = __fsub_rn((float)(bz * B + zb + zs), r0.z);
                 const float e_ = __fmul_rn(r1.w, dz), f_ = __fmul_rn(r2.x, dz);
                 const float dzh = __fmul_rn(dz, __fmul_rn(r1.y, dz));
-                float2 T0 = make_float2(0.f, 0.f), T1 = T0, Ty = T0;
+                float T0 = 0.f, T1 = 0.f, Ty = 0.f;
 #pragma unroll
                 for (int yr = 0; yr < SY; ++yr) {
                     const float dy = __fsub_rn((float)(by * B + yb + yr), r0.y);
@@ -351,41 +352,39 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
                         const float2 h = __fmul2_rn(G, __ffma2_rn(amp, gn, make_float2(gv.z, gv.w)));
                         A = __ffma2_rn(G, gn, A);
                         R0 = __fadd2_rn(R0, h);
-                        const float2 X = make_float2((float)(2 * q), (float)(2 * q + 1));
-                        R1 = __ffma2_rn(h, X, R1);
-                        R2 = __ffma2_rn(h, __fmul2_rn(X, X), R2);
+                        const float X0 = (float)(2 * q), X1 = (float)(2 * q + 1);
+                        R1 = __ffma2_rn(h, make_float2(X0, X1), R1);
+                        R2 = __ffma2_rn(h, make_float2(X0 * X0, X1 * X1), R2);
                     }
-                    const float2 dy2 = f2(dy);
-                    S1y = __ffma2_rn(dy2, R0, S1y);
-                    Sxy = __ffma2_rn(dy2, R1, Sxy);
-                    const float2 dyR0 = __fmul2_rn(dy2, R0);
-                    Syy = __ffma2_rn(dy2, dyR0, Syy);
-                    T0 = __fadd2_rn(T0, R0);
-                    T1 = __fadd2_rn(T1, R1);
-                    Ty = __fadd2_rn(Ty, dyR0);
+                    const float r0s = R0.x + R0.y, r1s = R1.x + R1.y;
+                    const float dyr0 = dy * r0s;
+                    S1y = fmaf(dy, r0s, S1y);
+                    Sxy = fmaf(dy, r1s, Sxy);
+                    Syy = fmaf(dy, dyr0, Syy);
+                    T0 += r0s;
+                    T1 += r1s;
+                    Ty += dyr0;
                 }
-                const float2 dz2 = f2(dz);
-                S0 = __fadd2_rn(S0, T0);
-                S1x = __fadd2_rn(S1x, T1);
-                S1z = __ffma2_rn(dz2, T0, S1z);
-                Sxz = __ffma2_rn(dz2, T1, Sxz);
-                Syz = __ffma2_rn(dz2, Ty, Syz);
-                Szz = __ffma2_rn(__fmul2_rn(dz2, dz2), T0, Szz);
+                S0 += T0;
+                S1x += T1;
+                S1z = fmaf(dz, T0, S1z);
+                Sxz = fmaf(dz, T1, Sxz);
+                Syz = fmaf(dz, Ty, Syz);
+                Szz = fmaf(dz * dz, T0, Szz);
             }
             const float del = __fsub_rn(fxb, r0.x);
-            const float s0 = S0.x + S0.y, sx = S1x.x + S1x.y, sy = S1y.x + S1y.y, sz = S1z.x + S1z.y;
             float* sa = s_acc + j * kAccStride;
             atomicAdd(sa + 0, A.x + A.y);
-            atomicAdd(sa + 1, s0);
-            atomicAdd(sa + 2, fmaf(del, s0, sx));
-            atomicAdd(sa + 3, sy);
-            atomicAdd(sa + 4, sz);
-            atomicAdd(sa + 5, fmaf(del, fmaf(del, s0, 2.f * sx), R2.x + R2.y));
-            atomicAdd(sa + 6, Syy.x + Syy.y);
-            atomicAdd(sa + 7, Szz.x + Szz.y);
-            atomicAdd(sa + 8, fmaf(del, sy, Sxy.x + Sxy.y));
-            atomicAdd(sa + 9, fmaf(del, sz, Sxz.x + Sxz.y));
-            atomicAdd(sa + 10, Syz.x + Syz.y);
+            atomicAdd(sa + 1, S0);
+            atomicAdd(sa + 2, fmaf(del, S0, S1x));
+            atomicAdd(sa + 3, S1y);
+            atomicAdd(sa + 4, S1z);
+            atomicAdd(sa + 5, fmaf(del, fmaf(del, S0, 2.f * S1x), R2.x + R2.y));
+            atomicAdd(sa + 6, Syy);
+            atomicAdd(sa + 7, Szz);
+            atomicAdd(sa + 8, fmaf(del, S1y, Sxy));
+            atomicAdd(sa + 9, fmaf(del, S1z, Sxz));
+            atomicAdd(sa + 10, Syz);
         }
         __syncthreads();
         for (int j = tid; j < cnt; j += NT) {

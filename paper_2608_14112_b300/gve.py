@@ -107,7 +107,7 @@ def lib():
             L.gve_loss_grad.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(EvalOpts), ctypes.c_float, P, P, P]
             L.gve_backward.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P]
             L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
-            L.gve_bin.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P, i64, P, ctypes.POINTER(i64), P]
+            L.gve_bin.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P, P, i64, P, ctypes.POINTER(i64), P]
             L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), P]
             L.gve_evaluate_noalloc.argtypes = [P, i64, Dims, ctypes.POINTER(EvalOpts), P, P]
@@ -321,9 +321,11 @@ def gve_allocate(field: torch.Tensor, budget: int, detail_frac: float = 0.55, oc
     return out, {name: getattr(info, name) for name, _ in AllocInfo._fields_}
 
 
-def gve_bin(prims: torch.Tensor, shape, opts: EvalOptions | None = None, cap: int | None = None):
+def gve_bin(prims: torch.Tensor, shape, opts: EvalOptions | None = None, cap: int | None = None,
+            with_masks: bool = False):
     """The (brick, Gaussian) pairs of the binner: (counts (N,), keys, gids,
-    start, end) as int64 CPU tensors for inspection."""
+    start, end) as int64 CPU tensors for inspection, plus the sub-brick
+    masks (uint8) when ``with_masks``."""
     prims = _prims(prims)
     o = (opts or EvalOptions()).c()
     d = _dims(shape)
@@ -337,18 +339,21 @@ def gve_bin(prims: torch.Tensor, shape, opts: EvalOptions | None = None, cap: in
     npairs = ctypes.c_int64(0)
     if cap is None:
         kk = torch.empty(1, dtype=torch.int32, device=dev)
-        s = lib().gve_bin(c, _ptr(prims), n, d, ctypes.byref(o), _ptr(counts), _ptr(kk), _ptr(kk), 0,
+        s = lib().gve_bin(c, _ptr(prims), n, d, ctypes.byref(o), _ptr(counts), _ptr(kk), _ptr(kk), None, 0,
                           _ptr(ranges), ctypes.byref(npairs), _stream(dev))
         if s not in (GVE_OK, GVE_E_CAPACITY):
             _check(s, c)
         cap = int(npairs.value)
     keys = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     gids = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-    _check(lib().gve_bin(c, _ptr(prims), n, d, ctypes.byref(o), _ptr(counts), _ptr(keys), _ptr(gids), cap,
-                         _ptr(ranges), ctypes.byref(npairs), _stream(dev)), c)
+    masks = torch.empty(max(cap, 1), dtype=torch.uint8, device=dev) if with_masks else None
+    _check(lib().gve_bin(c, _ptr(prims), n, d, ctypes.byref(o), _ptr(counts), _ptr(keys), _ptr(gids),
+                         _ptr(masks) if masks is not None else None, cap, _ptr(ranges), ctypes.byref(npairs),
+                         _stream(dev)), c)
     m = int(npairs.value)
     u32 = lambda t: t.cpu().to(torch.int64) & 0xFFFFFFFF
-    return (u32(counts[:n]), u32(keys[:m]), u32(gids[:m]), u32(ranges[:nb]), u32(ranges[nb:]))
+    out = (u32(counts[:n]), u32(keys[:m]), u32(gids[:m]), u32(ranges[:nb]), u32(ranges[nb:]))
+    return out + (masks[:m].cpu(),) if with_masks else out
 
 
 def gve_count_pairs(prims: torch.Tensor, shape, opts: EvalOptions | None = None):

@@ -65,6 +65,25 @@ def test_binning_bit_exact(case):
     np.testing.assert_array_equal(ge.numpy(), end.astype(np.int64))
 
 
+MASK_CASES = dict(CASES, aniso=((40, 36, 30), 200, 0.4, 9.0, 7))
+
+
+@pytest.mark.parametrize("brick", [4, 8, 16])
+@pytest.mark.parametrize("case", list(MASK_CASES))
+def test_subbrick_masks_cover_kept_voxels(case, brick):
+    """The evaluator's sub-brick masks contain every sub-brick in which the
+    oracle's float32 keep test keeps a voxel (they may hold more)."""
+    dims, n, lo, hi, seed = MASK_CASES[case]
+    shape = (dims[2], dims[1], dims[0])
+    p = rand_prims(np.random.default_rng(seed + 40), n, dims, lo, hi)
+    _, gk, gg, _, _, gm = gve.gve_bin(dev(p), shape, gve.EvalOptions(brick=brick), with_masks=True)
+    ref = O.kept_submasks(p, dims, gk.numpy().astype(np.uint32), gg.numpy().astype(np.uint32), 3.0, brick)
+    got = gm.numpy()
+    assert got.shape == ref.shape and ref.any()
+    missing = ref & ~got
+    assert not missing.any(), np.nonzero(missing)[0][:10]
+
+
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("normalized", [True, False])
 def test_evaluate_parity(case, normalized):

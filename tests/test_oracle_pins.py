@@ -714,3 +714,30 @@ def test_bf16_round_nearest_even():
     ulp = 2.0 ** (e - 7)
     assert np.all(np.abs(ry - y) <= ulp / 2 + 1e-30)
     assert np.all(np.mod(ry / ulp, 1.0) == 0.0)
+
+
+def test_kept_submasks_brute_force():
+    """Kept sub-bricks of listed bricks, against a voxel-by-voxel scan with
+    the oracle's own keep exponent (pred_t), for every brick edge."""
+    rng = np.random.default_rng(12)
+    dims = (21, 18, 13)
+    p = np.zeros((6, 12), np.float32)
+    p[:, 0:3] = rng.uniform(2, 16, (6, 3))
+    p[:, 3:6] = np.log(rng.uniform(0.6, 2.5, (6, 3)))
+    p[:, 6:10] = rng.normal(size=(6, 4))
+    p[:, 10] = 1.0
+    for B in (4, 8, 16):
+        _, keys, gids = O.bin_pairs(p, dims, 3.0, B)
+        got = O.kept_submasks(p, dims, keys, gids, 3.0, B)
+        T = O.pred_threshold(3.0)
+        nbx, nby = -(-dims[0] // B), -(-dims[1] // B)
+        for kk, gg, m in zip(keys.tolist(), gids.tolist(), got.tolist()):
+            bx, by, bz = kk % nbx, (kk // nbx) % nby, kk // (nbx * nby)
+            want = 0
+            for z in range(bz * B, min(bz * B + B, dims[2])):
+                for y in range(by * B, min(by * B + B, dims[1])):
+                    for x in range(bx * B, min(bx * B + B, dims[0])):
+                        if O.pred_t(p[gg], x, y, z) > T:
+                            want |= 1 << ((y - by * B) // (B // 2) + 2 * ((z - bz * B) // (B // 4)))
+            assert m == want, (B, kk, gg)
+        assert got.any() and not got.all()

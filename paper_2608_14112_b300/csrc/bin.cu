@@ -170,12 +170,13 @@ __device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy
 // whitened coordinates the sub-brick's voxel centres (half sizes
 // h = ((B-1)/2, (B/2-1)/2, (B/4-1)/2) + 0.01) lie in the parallelepiped
 // P = {y + sum_i s_i l_i : |s_i| <= h_i} (y its centre, l_i the images of the
-// voxel axes).  Two lower bounds on min |P|^2 are tested against the brick's
-// K2: the axis-aligned one, sum_j max(0, |y_j| - sum_i h_i |l_ij|)^2, and the
-// separating-axis one along n = y / |y|, (|y| - sum_i h_i |n . l_i|)^2 when
-// positive.  The second is compared with a 1e-3 relative margin on K2, which
-// covers its float32 rounding.  Sub-bricks outside the grid get no bit.
-// Conservative: it never drops a pair the keep test keeps.
+// voxel axes).  Along n = y / |y| every point of P has n . p >= |y| -
+// sum_i h_i |n . l_i|; when that separating distance is positive and its
+// square exceeds the brick's K2 (with a 1e-3 relative margin covering the
+// float32 rounding) no voxel centre of the sub-brick can be kept.  (The
+// axis-aligned whitened bound of the brick test adds almost nothing here.)
+// Sub-bricks outside the grid get no bit.  Conservative: it never drops a
+// pair the keep test keeps.
 __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, float muy, float muz, int B, int bx,
                                                   int by, int bz, int ny, int nz)
 {
@@ -183,11 +184,10 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, fl
     const float cx = (float)(bx * B) + hb, cy = (float)(by * B) + hb, cz = (float)(bz * B) + hb;
     const float dcx = cx - mux, dcy = cy - muy, dcz = cz - muz;
     const float h0 = hb + 0.01f, h1 = 0.5f * (float)(B / 2 - 1) + 0.01f, h2 = 0.5f * (float)(B / 4 - 1) + 0.01f;
-    float yc[3], ea[3], eb[3], ec[3];
+    float yc[3], eb[3], ec[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         yc[j] = fmaf(b.L[j * 3 + 2], dcz, fmaf(b.L[j * 3 + 1], dcy, b.L[j * 3 + 0] * dcx));
-        ea[j] = fabsf(b.L[j * 3 + 0]) * h0 + fabsf(b.L[j * 3 + 1]) * h1 + fabsf(b.L[j * 3 + 2]) * h2;
         eb[j] = b.L[j * 3 + 1];
         ec[j] = b.L[j * 3 + 2];
     }
@@ -199,23 +199,16 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, fl
         const int yh = sidx & 1, zq = sidx >> 1;
         if (by * B + (B / 2) * yh >= ny || bz * B + (B / 4) * zq >= nz) continue;
         const float oy = yh ? oyv : -oyv, oz = (float)(2 * zq - 3) * ozv;
-        float sq = 0.f, y[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            y[j] = fmaf(ec[j], oz, fmaf(eb[j], oy, yc[j]));
-            const float a = fmaxf(fabsf(y[j]) - ea[j], 0.f);
-            sq = fmaf(a, a, sq);
-        }
-        if (sq > b.K2) continue;
-        // separating axis along y: |y|^2 - sum_i h_i |y . l_i| > sqrt(K2) |y|
         float y2 = 0.f, ylx = 0.f, yly = 0.f, ylz = 0.f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            y2 = fmaf(y[j], y[j], y2);
-            ylx = fmaf(y[j], b.L[j * 3 + 0], ylx);
-            yly = fmaf(y[j], b.L[j * 3 + 1], yly);
-            ylz = fmaf(y[j], b.L[j * 3 + 2], ylz);
+            const float y = fmaf(ec[j], oz, fmaf(eb[j], oy, yc[j]));
+            y2 = fmaf(y, y, y2);
+            ylx = fmaf(y, b.L[j * 3 + 0], ylx);
+            yly = fmaf(y, b.L[j * 3 + 1], yly);
+            ylz = fmaf(y, b.L[j * 3 + 2], ylz);
         }
+        // |y|^2 - sum_i h_i |y . l_i| > sqrt(K2) |y|  =>  no kept voxel
         const float D = y2 - fmaf(h0, fabsf(ylx), fmaf(h1, fabsf(yly), h2 * fabsf(ylz)));
         if (D > 0.f && D * D > K2m * y2) continue;
         m |= 1u << sidx;

@@ -263,6 +263,10 @@ __global__ void __launch_bounds__(256) k_count(const BinRec* __restrict__ br, co
     }
 }
 
+// One warp per Gaussian.  The listed bricks of its box are queued in box
+// order in shared memory and processed 32 at a time, so that every lane
+// computes a sub-brick cover (the costly part) instead of only the lanes
+// whose brick passed; pair i of the Gaussian goes to offsets[g] + i.
 __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                               const unsigned long long* __restrict__ offsets, long long n,
                                               BinGeom g, const uint32_t* __restrict__ bmask,
@@ -270,8 +274,10 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
                                               const DevState* __restrict__ st)
 {
     if (st->overflow) return;
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_q[8][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    uint32_t* q = s_q[w];
     long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long i = wid; i < n; i += nw) {
@@ -281,26 +287,46 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
         unsigned long long base = offsets[i];
         const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
         const uint32_t exy = ex * ey, tot = exy * ez;
+        // write the first m queued bricks (m <= 32) as pairs base .. base + m - 1
+        auto flush = [&](uint32_t m) {
+            if ((uint32_t)lane < m) {
+                int bx, by, bz;
+                box_brick(b, q[lane], ex, exy, bx, by, bz);
+                const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
+                const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
+                keys[base + lane] = key;
+                vals[base + lane] = (uint32_t)i | (mask << kGidBits);
+            }
+            base += m;
+        };
+        uint32_t qn = 0;
         for (uint32_t t0 = 0, c = 0; t0 < tot; t0 += 32, ++c) {
             const uint32_t t = t0 + lane;
-            int bx = 0, by = 0, bz = 0;
-            if (t < tot) box_brick(b, t, ex, exy, bx, by, bz);
             unsigned bal;
             if (c < kMaskChunks) {
                 bal = bmask[kMaskChunks * i + c];
             } else {
-                const bool p = t < tot && brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
+                bool p = false;
+                if (t < tot) {
+                    int bx, by, bz;
+                    box_brick(b, t, ex, exy, bx, by, bz);
+                    p = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
+                }
                 bal = __ballot_sync(0xffffffffu, p);
             }
-            if ((bal >> lane) & 1u) {
-                const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
-                const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
-                const unsigned long long pos = base + __popc(bal & lt);
-                keys[pos] = key;
-                vals[pos] = (uint32_t)i | (mask << kGidBits);
+            if ((bal >> lane) & 1u) q[qn + __popc(bal & lt)] = t;
+            qn += __popc(bal);
+            __syncwarp();
+            if (qn >= 32) {
+                flush(32);
+                __syncwarp();
+                if ((uint32_t)lane < qn - 32) q[lane] = q[32 + lane];
+                qn -= 32;
+                __syncwarp();
             }
-            base += __popc(bal);
         }
+        flush(qn);
+        __syncwarp();
     }
 }
 

@@ -222,12 +222,48 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, fl
 // Bricks of a Gaussian's box in z-major order; the box has fewer than 2^31
 // bricks, so 32-bit index arithmetic suffices.  The pass/fail ballots of the
 // first kMaskChunks x 32 bricks are kept for the emission pass.
-__device__ __forceinline__ void box_brick(const BinRec& b, uint32_t t, uint32_t ex, uint32_t exy, int& bx, int& by,
-                                          int& bz)
+// Division by the box extents: for boxes of fewer than 2^24 bricks a float
+// reciprocal gives the quotient to within one (relative error below 2^-23 on
+// quotients below 2^23; divisor 1 is exact), and one exact integer step
+// corrects it; larger boxes use integer division.
+struct BoxIdx {
+    uint32_t ex, exy;
+    float iex, iexy;
+    bool fast;
+};
+
+__device__ __forceinline__ BoxIdx box_idx(uint32_t ex, uint32_t exy, uint32_t tot)
 {
-    const uint32_t zq = t / exy, r = t - zq * exy;
-    const uint32_t yq = r / ex;
-    bx = b.blo[0] + (int)(r - yq * ex);
+    BoxIdx d;
+    d.ex = ex;
+    d.exy = exy;
+    d.iex = 1.f / (float)ex;
+    d.iexy = 1.f / (float)exy;
+    d.fast = tot < (1u << 24);
+    return d;
+}
+
+__device__ __forceinline__ uint32_t udiv_small(uint32_t t, uint32_t d, float id)
+{
+    int q = (int)__fmul_rn((float)t, id);
+    const int r = (int)t - q * (int)d;
+    if (r < 0) --q;
+    else if (r >= (int)d) ++q;
+    return (uint32_t)q;
+}
+
+__device__ __forceinline__ void box_brick(const BinRec& b, uint32_t t, const BoxIdx& d, int& bx, int& by, int& bz)
+{
+    uint32_t zq, yq;
+    if (d.fast) {
+        zq = udiv_small(t, d.exy, d.iexy);
+        yq = udiv_small(t - zq * d.exy, d.ex, d.iex);
+    } else {
+        zq = t / d.exy;
+        yq = (t - zq * d.exy) / d.ex;
+    }
+    const uint32_t r = t - zq * d.exy;
+    bx = b.blo[0] + (int)(r - yq * d.ex);
     by = b.blo[1] + (int)yq;
     bz = b.blo[2] + (int)zq;
 }
@@ -246,12 +282,13 @@ __global__ void __launch_bounds__(256) k_count(const BinRec* __restrict__ br, co
             const float4 r0 = rec[3 * i];
             const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
             const uint32_t exy = ex * ey, tot = exy * ez;
+        const BoxIdx D = box_idx(ex, exy, tot);
             for (uint32_t t0 = 0, c = 0; t0 < tot; t0 += 32, ++c) {
                 const uint32_t t = t0 + lane;
                 bool pass = false;
                 if (t < tot) {
                     int bx, by, bz;
-                    box_brick(b, t, ex, exy, bx, by, bz);
+                    box_brick(b, t, D, bx, by, bz);
                     pass = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -287,11 +324,12 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
         unsigned long long base = offsets[i];
         const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
         const uint32_t exy = ex * ey, tot = exy * ez;
+        const BoxIdx D = box_idx(ex, exy, tot);
         // write the first m queued bricks (m <= 32) as pairs base .. base + m - 1
         auto flush = [&](uint32_t m) {
             if ((uint32_t)lane < m) {
                 int bx, by, bz;
-                box_brick(b, q[lane], ex, exy, bx, by, bz);
+                box_brick(b, q[lane], D, bx, by, bz);
                 const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
                 const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
                 keys[base + lane] = key;
@@ -309,7 +347,7 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
                 bool p = false;
                 if (t < tot) {
                     int bx, by, bz;
-                    box_brick(b, t, ex, exy, bx, by, bz);
+                    box_brick(b, t, D, bx, by, bz);
                     p = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
                 }
                 bal = __ballot_sync(0xffffffffu, p);

@@ -542,10 +542,31 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
         h[threadIdx.x] = 0;
         __syncthreads();
         unsigned long long base = tile * kSortTile;
-#pragma unroll 4
-        for (int it = 0; it < kSortItems; ++it) {
-            unsigned long long idx = base + (unsigned long long)it * kSortThreads + threadIdx.x;
-            if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+        // all of the thread's keys in flight at once: kSortItems / 4 vector
+        // loads (the tile start is 16 KB aligned), element loads in the last
+        // partial tile
+        constexpr int V = kSortItems / 4;
+        uint4 kv[V];
+        const bool full = base + kSortTile <= n;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const unsigned long long e = base + 4ull * ((unsigned long long)k * kSortThreads + threadIdx.x);
+            if (full) {
+                kv[k] = *reinterpret_cast<const uint4*>(keys + e);
+            } else {
+                kv[k].x = e < n ? keys[e] : 0xffffffffu;
+                kv[k].y = e + 1 < n ? keys[e + 1] : 0xffffffffu;
+                kv[k].z = e + 2 < n ? keys[e + 2] : 0xffffffffu;
+                kv[k].w = e + 3 < n ? keys[e + 3] : 0xffffffffu;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const unsigned long long e = base + 4ull * ((unsigned long long)k * kSortThreads + threadIdx.x);
+            if (e < n) atomicAdd(&h[(kv[k].x >> shift) & 255u], 1u);
+            if (e + 1 < n) atomicAdd(&h[(kv[k].y >> shift) & 255u], 1u);
+            if (e + 2 < n) atomicAdd(&h[(kv[k].z >> shift) & 255u], 1u);
+            if (e + 3 < n) atomicAdd(&h[(kv[k].w >> shift) & 255u], 1u);
         }
         __syncthreads();
         hist[(unsigned long long)threadIdx.x * ntiles + tile] = h[threadIdx.x];
@@ -557,7 +578,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
 // elements (per-warp match_any ranking, warps in element order), places the
 // tile in shared memory sorted by digit, then writes every digit's run to its
 // global offset with consecutive threads on consecutive addresses.
-__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                              const DevState* st, unsigned long long cap, int shift,
@@ -582,11 +603,18 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
         const int wbase = w * (32 * kSortItems);
         uint32_t kk[kSortItems], vv[kSortItems];
         uint16_t rk[kSortItems];
+        // issue every load of the thread before ranking
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const int li = wbase + r * 32 + lane;
+            kk[r] = li < tn ? kin[tbase + li] : 0xffffffffu;
+            vv[r] = li < tn ? vin[tbase + li] : 0u;
+        }
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             const int li = wbase + r * 32 + lane;
             const bool valid = li < tn;
-            const uint32_t key = valid ? kin[tbase + li] : 0xffffffffu;
+            const uint32_t key = kk[r];
             const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
@@ -594,8 +622,6 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
             __syncwarp();
             if (valid && lane == leader) wcnt[w][d] = prior + __popc(peers);
             __syncwarp();
-            kk[r] = key;
-            vv[r] = valid ? vin[tbase + li] : 0u;
             rk[r] = (uint16_t)(prior + __popc(peers & lt));
         }
         __syncthreads();

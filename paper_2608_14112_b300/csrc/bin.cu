@@ -702,17 +702,36 @@ int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsign
 // ------------------------------------------------------------------------
 // ranges
 // ------------------------------------------------------------------------
+// Per-brick [start, end) of the sorted keys: each thread takes four
+// consecutive keys (one vector load; the key buffer is 256-byte aligned) and
+// compares them with their neighbours.
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ sk, const DevState* st,
                                                 unsigned long long cap, uint32_t* __restrict__ start,
                                                 uint32_t* __restrict__ end)
 {
     if (st->overflow) return;
-    unsigned long long n = sort_len(st, cap);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t k = sk[i];
-        if (i == 0 || sk[i - 1] != k) start[k] = (uint32_t)i;
-        if (i + 1 == n || sk[i + 1] != k) end[k] = (uint32_t)(i + 1);
+    const unsigned long long n = sort_len(st, cap);
+    const unsigned long long ng = (n + 3) / 4;
+    for (unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; gi < ng;
+         gi += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i0 = 4 * gi;
+        uint32_t k[4];
+        if (i0 + 4 <= n) {
+            const uint4 v = *reinterpret_cast<const uint4*>(sk + i0);
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+            for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? sk[i0 + j] : 0u;
+        }
+        const uint32_t prev = i0 > 0 ? sk[i0 - 1] : 0u;
+        const uint32_t next = i0 + 4 < n ? sk[i0 + 4] : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned long long i = i0 + j;
+            if (i >= n) break;
+            const uint32_t kp = j > 0 ? k[j - 1] : prev, kn = j < 3 ? k[j + 1] : next;
+            if (i == 0 || kp != k[j]) start[k[j]] = (uint32_t)i;
+            if (i + 1 == n || kn != k[j]) end[k[j]] = (uint32_t)(i + 1);
+        }
     }
 }
 

@@ -85,6 +85,23 @@ def make_field(w, device):
     return torch.from_numpy(inputs.blobs(w["n"], seed=w["seed"])).to(device)
 
 
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The slowest rank's time (the job ends when the last replica does)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, steps: int, ms: float) -> float:
+    """Iterations per second of the whole job: every rank runs `steps`
+    iterations of its own replica in `ms` (the max over ranks)."""
+    return ws * steps / (ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -388,14 +405,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     kept1, cand1 = gve.gve_count_pairs(prims, shape, opts)
-    value = ws * args.steps / (ms / 1e3)
+    value = whole_job_rate(ws, args.steps, ms)
 
     # dominant kernel: the fused brick evaluator (forward + backward)
     brick_ms = st["ms_brick"] / max(args.steps, 1)

@@ -1,0 +1,69 @@
+"""Host logic of the multi-rank bench on CPU: two gloo ranks (one process
+each, rendezvous on 127.0.0.1) reduce their timed regions to the slowest
+rank's, compute the whole-job rate from it, and on the reference arm only
+rank 0 does any work or prints.  No GPU is involved."""
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        local_ms = 100.0 + 25.0 * rank          # rank 1 is the slow one
+        ms = bench.max_over_ranks(local_ms, ws)
+        rate = bench.whole_job_rate(ws, 30, ms)
+        env = bench.dist_env()
+        # reference arm: ranks other than 0 return without output
+        out = io.StringIO()
+        if rank != 0:
+            with redirect_stdout(out):
+                bench.run_reference(type("A", (), {"workload": "small", "warmup": 3, "steps": 1, "gpus": ws,
+                                                    "sample": 16, "sample_iters": 1, "seed": 1})())
+        q.put((rank, ms, rate, env, out.getvalue()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(ws))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, rate, env, printed in res:
+        assert ms == pytest.approx(125.0)
+        assert rate == pytest.approx(2 * 30 / 0.125)
+        assert env == (2, rank, rank)
+        assert printed == ""
+
+
+def test_single_rank_helpers_need_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    assert bench.whole_job_rate(1, 10, 500.0) == pytest.approx(20.0)

@@ -164,6 +164,30 @@ __device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy
     return sq <= b.K2;
 }
 
+// Gram matrix of the whitened voxel axes l_i (l_i[j] = L[j][i]), shared by
+// every brick of a Gaussian: the sub-brick centres are the brick centre plus
+// multiples of l_1 and l_2, so their dot products and squared lengths follow
+// from the brick centre's by a few FMAs (float rounding far inside the 1e-3
+// margin of the test).
+struct AxisGram {
+    float g01, g02, g11, g12, g22;
+};
+
+__device__ __forceinline__ AxisGram axis_gram(const BinRec& b)
+{
+    AxisGram G{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float l0 = b.L[j * 3 + 0], l1 = b.L[j * 3 + 1], l2 = b.L[j * 3 + 2];
+        G.g01 = fmaf(l0, l1, G.g01);
+        G.g02 = fmaf(l0, l2, G.g02);
+        G.g11 = fmaf(l1, l1, G.g11);
+        G.g12 = fmaf(l1, l2, G.g12);
+        G.g22 = fmaf(l2, l2, G.g22);
+    }
+    return G;
+}
+
 // Sub-brick cover of a listed brick (an acceleration structure of the
 // evaluator, not part of the binning definition): bit s is set when the
 // B x B/2 x B/4 sub-brick s = (y half, z quarter) may hold a kept pair.  In
@@ -177,41 +201,45 @@ __device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy
 // axis-aligned whitened bound of the brick test adds almost nothing here.)
 // Sub-bricks outside the grid get no bit.  Conservative: it never drops a
 // pair the keep test keeps.
-__device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, float mux, float muy, float muz, int B, int bx,
-                                                  int by, int bz, int ny, int nz)
+__device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, const AxisGram& G, float mux, float muy,
+                                                  float muz, int B, int bx, int by, int bz, int ny, int nz)
 {
     const float hb = 0.5f * (float)(B - 1);
     const float cx = (float)(bx * B) + hb, cy = (float)(by * B) + hb, cz = (float)(bz * B) + hb;
     const float dcx = cx - mux, dcy = cy - muy, dcz = cz - muz;
     const float h0 = hb + 0.01f, h1 = 0.5f * (float)(B / 2 - 1) + 0.01f, h2 = 0.5f * (float)(B / 4 - 1) + 0.01f;
-    float yc[3], eb[3], ec[3];
+    // brick centre yc = L (c - mu): its dot products with the axes and |yc|^2
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, yy = 0.f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        yc[j] = fmaf(b.L[j * 3 + 2], dcz, fmaf(b.L[j * 3 + 1], dcy, b.L[j * 3 + 0] * dcx));
-        eb[j] = b.L[j * 3 + 1];
-        ec[j] = b.L[j * 3 + 2];
+        const float yc = fmaf(b.L[j * 3 + 2], dcz, fmaf(b.L[j * 3 + 1], dcy, b.L[j * 3 + 0] * dcx));
+        c0 = fmaf(yc, b.L[j * 3 + 0], c0);
+        c1 = fmaf(yc, b.L[j * 3 + 1], c1);
+        c2 = fmaf(yc, b.L[j * 3 + 2], c2);
+        yy = fmaf(yc, yc, yy);
     }
     const float oyv = 0.25f * (float)B, ozv = 0.125f * (float)B;
     const float K2m = b.K2 * 1.001f;
     uint32_t m = 0;
 #pragma unroll
-    for (int sidx = 0; sidx < 8; ++sidx) {
-        const int yh = sidx & 1, zq = sidx >> 1;
-        if (by * B + (B / 2) * yh >= ny || bz * B + (B / 4) * zq >= nz) continue;
-        const float oy = yh ? oyv : -oyv, oz = (float)(2 * zq - 3) * ozv;
-        float y2 = 0.f, ylx = 0.f, yly = 0.f, ylz = 0.f;
+    for (int yh = 0; yh < 2; ++yh) {
+        if (by * B + (B / 2) * yh >= ny) continue;
+        const float oy = yh ? oyv : -oyv;
+        // y = yc + oy l_1 + oz l_2
+        const float px = fmaf(oy, G.g01, c0), py = fmaf(oy, G.g11, c1), pz = fmaf(oy, G.g12, c2);
+        const float A = fmaf(oy, fmaf(oy, G.g11, 2.f * c1), yy);
+        const float Bz = 2.f * pz;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const float y = fmaf(ec[j], oz, fmaf(eb[j], oy, yc[j]));
-            y2 = fmaf(y, y, y2);
-            ylx = fmaf(y, b.L[j * 3 + 0], ylx);
-            yly = fmaf(y, b.L[j * 3 + 1], yly);
-            ylz = fmaf(y, b.L[j * 3 + 2], ylz);
+        for (int zq = 0; zq < 4; ++zq) {
+            if (bz * B + (B / 4) * zq >= nz) continue;
+            const float oz = (float)(2 * zq - 3) * ozv;
+            const float ylx = fmaf(oz, G.g02, px), yly = fmaf(oz, G.g12, py), ylz = fmaf(oz, G.g22, pz);
+            const float y2 = fmaf(oz, fmaf(oz, G.g22, Bz), A);
+            // |y|^2 - sum_i h_i |y . l_i| > sqrt(K2) |y|  =>  no kept voxel
+            const float D = y2 - fmaf(h0, fabsf(ylx), fmaf(h1, fabsf(yly), h2 * fabsf(ylz)));
+            if (D > 0.f && D * D > K2m * y2) continue;
+            m |= 1u << (yh + 2 * zq);
         }
-        // |y|^2 - sum_i h_i |y . l_i| > sqrt(K2) |y|  =>  no kept voxel
-        const float D = y2 - fmaf(h0, fabsf(ylx), fmaf(h1, fabsf(yly), h2 * fabsf(ylz)));
-        if (D > 0.f && D * D > K2m * y2) continue;
-        m |= 1u << sidx;
     }
     return m;
 }
@@ -321,6 +349,7 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
         const BinRec b = br[i];
         if (!b.nonempty) continue;
         const float4 r0 = rec[3 * i];
+        const AxisGram G = axis_gram(b);
         unsigned long long base = offsets[i];
         const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
         const uint32_t exy = ex * ey, tot = exy * ez;
@@ -331,7 +360,7 @@ __global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, con
                 int bx, by, bz;
                 box_brick(b, q[lane], D, bx, by, bz);
                 const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
-                const uint32_t mask = subbrick_mask(b, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
+                const uint32_t mask = subbrick_mask(b, G, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
                 keys[base + lane] = key;
                 vals[base + lane] = (uint32_t)i | (mask << kGidBits);
             }

@@ -26,7 +26,9 @@
  *             throws across the ABI.  gve_last_error() gives a message.
  *             Invalid arguments are rejected before any launch.
  * Counts.     At most 2^24 (16,777,216) primitives per call; grid axes up to
- *             2^24 voxels with fewer than 2^31 bricks of 8^3.
+ *             2^14 (16,384) voxels for evaluation and refinement (the float32
+ *             margins of the brick cover hold for coordinates below 2^14) and
+ *             2^24 for allocation, with fewer than 2^31 bricks.
  * Threads.    A context may be used by one host thread at a time.
  */
 #ifndef GVE_H
@@ -319,7 +321,8 @@ GVE_API gve_status gve_count_pairs(gve_ctx* ctx, const float* prims_dev, int64_t
  * file-scope device array of the library (about 10 MB, held by every GPU
  * that loads the library until the process exits).
  *   prims_dev      [n][12] float32, n <= GVE_NOALLOC_MAX_PRIMS.
- *   dims           at most GVE_NOALLOC_MAX_BRICKS bricks of 8^3.
+ *   dims           at most GVE_NOALLOC_MAX_BRICKS bricks of 8^3, axes up to
+ *                  2^14 voxels.
  *   opts           brick must be 8.
  *   field_out_dev  [nz][ny][nx] float32 output.
  * Returns GVE_E_INVALID for sizes beyond the limits (before any launch), and

@@ -99,7 +99,9 @@ gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, c
     if (n > 0 && !prims) return fail(c, GVE_E_INVALID, "null primitive pointer");
     if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "primitives not 16-byte aligned");
     if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
-    if (d.nx > (1 << 24) || d.ny > (1 << 24) || d.nz > (1 << 24)) return fail(c, GVE_E_INVALID, "grid axis above 2^24");
+    // the conservative brick cover's float32 margins hold for coordinates below 2^14
+    if (d.nx > (1 << 14) || d.ny > (1 << 14) || d.nz > (1 << 14))
+        return fail(c, GVE_E_INVALID, "grid axis above 2^14 voxels (evaluation limit)");
     if (o->brick != 4 && o->brick != 8 && o->brick != 16) return fail(c, GVE_E_INVALID, "brick edge must be 4, 8 or 16");
     if (o->gaussians_per_block != 0 && o->gaussians_per_block != 32 && o->gaussians_per_block != 64)
         return fail(c, GVE_E_INVALID, "gaussians_per_block must be 0, 32 or 64");

@@ -95,6 +95,7 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
     if (n < 0 || n > kNaPrims) return GVE_E_INVALID;
     if (prims && (reinterpret_cast<uintptr_t>(prims) & 15u)) return GVE_E_INVALID;
     if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return GVE_E_INVALID;
+    if (d.nx > (1 << 14) || d.ny > (1 << 14) || d.nz > (1 << 14)) return GVE_E_INVALID;
     if (o->brick != 8 || !(o->trunc_k > 0.f) || !std::isfinite(o->trunc_k)) return GVE_E_INVALID;
     if (o->normalized && !(o->rho0 > 0.f)) return GVE_E_INVALID;
     const BinGeom g = make_geom(d, 8);

@@ -161,6 +161,9 @@ def test_invalid_arguments_raise():
         gve.gve_evaluate(p, (8, 8, 8), gve.EvalOptions(brick=5))
     with pytest.raises(gve.GveError):
         gve.gve_evaluate(p, (8, 8, 8), gve.EvalOptions(trunc_k=-1.0))
+    # an axis beyond 2^14 voxels lies outside the brick cover's float32 margins
+    with pytest.raises(gve.GveError):
+        gve.gve_evaluate(p, (1, 1, (1 << 14) + 1))
     with pytest.raises(ValueError):
         gve.gve_evaluate(p.double(), (8, 8, 8))
 

@@ -75,6 +75,10 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     s = gve.lib().gve_evaluate_noalloc(ctypes.c_void_p(p.data_ptr()), 4, gve.Dims(nx, ny, nz), ctypes.byref(opts),
                                        ctypes.c_void_p(out.data_ptr()), None)
     assert s == gve.GVE_E_INVALID
+    long_axis = gve.Dims((1 << 14) + 8, 1, 1)     # few bricks, but an axis beyond 2^14 voxels
+    s = gve.lib().gve_evaluate_noalloc(ctypes.c_void_p(p.data_ptr()), 4, long_axis, ctypes.byref(opts),
+                                       ctypes.c_void_p(out.data_ptr()), None)
+    assert s == gve.GVE_E_INVALID
     too_many = torch.zeros((8193, 12), device="cuda")
     s = gve.lib().gve_evaluate_noalloc(ctypes.c_void_p(too_many.data_ptr()), 8193, gve.Dims(8, 8, 8),
                                        ctypes.byref(opts), ctypes.c_void_p(out.data_ptr()), None)

@@ -13,8 +13,9 @@
 //                   the low 24 bits, 8-bit sub-brick mask above), uint32,
 //                   double-buffered for the radix sort.
 //   ranges          uint32 start[nbricks], end[nbricks].
-//   accumulators    float[12] per Gaussian: A, Bs, S1 (3), S2 (6: xx yy zz
-//                   xy xz yz), 0 -- the per-Gaussian sums of the backward.
+//   accumulators    float[12] per Gaussian: A = sum G gn, H = sum h, S1' (3),
+//                   S2' (6: xx yy zz xy xz yz), 0 -- the per-Gaussian sums of
+//                   the backward, h = G (a gn + gd).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -1,11 +1,12 @@
 // optim.cu -- per-Gaussian chain rule and the fused Adam step.
 //
-// From the brick evaluator's sums (A, Bs, S1', S2' with S1 = -S1'/2 and
-// S2 = -S2'/2, the derivative of the loss with respect to the squared
-// Mahalanobis distance being -G c / 2) to the gradient of the raw 12-float
-// record of Eq. 2:
+// From the brick evaluator's sums -- A = sum G gn, H = sum h and the first
+// and second moments S1', S2' of h = G (a gn + gd) over d = p - mu -- with
+// S1 = -w S1'/2 and S2 = -w S2'/2 (the derivative of the loss with respect
+// to the squared Mahalanobis distance being -w h / 2), to the gradient of the
+// raw 12-float record of Eq. 2:
 //   dL/da       = w A
-//   dL/dw_logit = (a A + Bs) w (1 - w)
+//   dL/dw_logit = H w (1 - w)
 //   dL/dmu      = -2 Sigma^-1 S1
 //   dL/dlog s_j = -2 s_j^-2 (R^T S2 R)_jj
 //   dL/dR       = 2 S2 R diag(s^-2)  -> dL/dq_hat -> dL/dq through q/|q|

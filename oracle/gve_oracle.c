@@ -1183,3 +1183,184 @@ int or_allocate(const float* V, const int dims[3], int64_t N, double detail_frac
     free(vd); free(vc); free(g);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Stratified-sample refinement (Sec. III-F: each iteration fits the field  */
+/* at a stratified set of jittered points; Table III: 3,072 per iteration,  */
+/* 35 / 40 / 25 %).                                                          */
+/* ------------------------------------------------------------------------ */
+#define OR_SAMPLE_STREAM 4u
+
+/* Voxel lists of the two value classes, ascending: high V > 0.4 and occupied
+ * mid-range 0.02 < V <= 0.4 (float32 comparisons).  Either output may be
+ * NULL to count only. */
+void or_sample_classes(const float* V, const int dims[3], int64_t* hi, int64_t* n_hi, int64_t* mid, int64_t* n_mid)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2], a = 0, b = 0;
+    for (int64_t v = 0; v < M; ++v) {
+        if (V[v] > 0.4f) { if (hi) hi[a] = v; ++a; }
+        else if (V[v] > 0.02f) { if (mid) mid[b] = v; ++b; }
+    }
+    *n_hi = a;
+    *n_mid = b;
+}
+
+/* Per-class sample counts for S points: high floor(0.35 S + 1/2), mid
+ * floor(0.40 S + 1/2), the rest uniform over the grid. */
+void or_sample_split(int64_t S, int64_t out[3])
+{
+    out[0] = (int64_t)floor(0.35 * (double)S + 0.5);
+    out[1] = (int64_t)floor(0.40 * (double)S + 0.5);
+    out[2] = S - out[0] - out[1];
+}
+
+/* Sample j of iteration `iter`: Philox4x32-10 words x0..x3 of counter
+ * (j, iter, 4, 'GVE1') under key seed.  Samples [0, n_hi) come from the
+ * high class, the next n_mid from the mid class, the rest from all voxels;
+ * a class with no voxel hands its samples to the uniform draw.  The voxel
+ * is the floor(x0 * count / 2^32)-th of its class, the point p = c + u with
+ * u_k = (x_{k+1} >> 8) 2^-24 - 1/2 (rounded once to float32), and the target
+ * is the trilinear value V(p) (FP64, edge-clamped) rounded to float32. */
+void or_draw_samples(const float* V, const int dims[3], const int64_t* hi, int64_t n_hi, const int64_t* mid,
+                     int64_t n_mid, int64_t S, uint64_t seed, uint32_t iter, float* pts, float* vals, int64_t* vox)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2];
+    int64_t split[3];
+    or_sample_split(S, split);
+    for (int64_t j = 0; j < S; ++j) {
+        uint32_t r[4];
+        or_draw(((uint64_t)iter << 32) | (uint64_t)(uint32_t)j, OR_SAMPLE_STREAM, seed, r);
+        const int64_t* list = NULL;
+        int64_t count = M;
+        if (j < split[0] && n_hi > 0) { list = hi; count = n_hi; }
+        else if (j >= split[0] && j < split[0] + split[1] && n_mid > 0) { list = mid; count = n_mid; }
+        int64_t k = (int64_t)(((uint64_t)r[0] * (uint64_t)count) >> 32);
+        int64_t v = list ? list[k] : k;
+        int c[3] = {(int)(v % dims[0]), (int)((v / dims[0]) % dims[1]), (int)(v / ((int64_t)dims[0] * dims[1]))};
+        for (int a = 0; a < 3; ++a) {
+            float u = (float)(r[a + 1] >> 8) * 0x1p-24f - 0.5f;
+            pts[3 * j + a] = (float)c[a] + u;
+        }
+        vals[j] = (float)or_trilinear(V, dims, (double)pts[3 * j], (double)pts[3 * j + 1], (double)pts[3 * j + 2]);
+        if (vox) vox[j] = v;
+    }
+}
+
+/* Keep exponent at a float32 point, by the same chain as at voxel centres. */
+static float pred_t_at(const pred_t* P, float px, float py, float pz)
+{
+    float dx = px - P->mu[0];
+    float dy = py - P->mu[1];
+    float dz = pz - P->mu[2];
+    float e = P->qxz2 * dz;
+    float b = fmaf(P->qxy2, dy, e);
+    float f = P->qyz2 * dz;
+    float g = fmaf(P->qyy, dy, f);
+    float hh = P->qzz * dz;
+    float dzh = dz * hh;
+    float c = fmaf(dy, g, dzh);
+    float u = fmaf(P->qxx, dx, b);
+    return fmaf(dx, u, c);
+}
+
+/* Eq. 3 at S points (every Gaussian against every point, kept by the float32
+ * test) and the sampled value loss L = (1/S) sum_s 1[v_s > occ] (Vt_s - v_s)^2
+ * with its gradient (grad may be NULL).  vt_out (optional) receives Vt_s. */
+double or_sample_loss_grad(const double* prm, int64_t n, const float* pts, const float* vals, int64_t S, float k,
+                           double rho0, double occ, double* grad, double* vt_out)
+{
+    act_t* A = (act_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(act_t));
+    pred_t* P = (pred_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(pred_t));
+    double* num = (double*)calloc((size_t)(S > 0 ? S : 1), sizeof(double));
+    double* den = (double*)calloc((size_t)(S > 0 ? S : 1), sizeof(double));
+    double* gn = (double*)calloc((size_t)(S > 0 ? S : 1), sizeof(double));
+    double* gd = (double*)calloc((size_t)(S > 0 ? S : 1), sizeof(double));
+    if (!A || !P || !num || !den || !gn || !gd) return NAN;
+    const float T = pred_threshold(k);
+    for (int64_t i = 0; i < n; ++i) {
+        activate(prm + 12 * i, &A[i]);
+        float p32[12];
+        for (int j = 0; j < 12; ++j) p32[j] = (float)prm[12 * i + j];
+        pred_coeffs(p32, &P[i]);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < S; ++s) {
+        const float* p = pts + 3 * s;
+        double nu = 0.0, de = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!A[i].valid || !P[i].valid) continue;
+            if (!(pred_t_at(&P[i], p[0], p[1], p[2]) > T)) continue;
+            double G = exp(-0.5 * maha2(&A[i], p[0], p[1], p[2]));
+            nu += A[i].w * A[i].a * G;
+            de += A[i].w * G;
+        }
+        num[s] = nu;
+        den[s] = de;
+    }
+    double loss = 0.0;
+    for (int64_t s = 0; s < S; ++s) {
+        double vt = num[s] / (den[s] > rho0 ? den[s] : rho0);
+        if (vt_out) vt_out[s] = vt;
+        double r = vals[s] > (float)occ ? vt - (double)vals[s] : 0.0;
+        loss += r * r;
+        double up = 2.0 * r / (double)S;
+        if (den[s] >= rho0) { gn[s] = up / den[s]; gd[s] = -vt * gn[s]; }
+        else { gn[s] = up / rho0; gd[s] = 0.0; }
+    }
+    loss /= (double)S;
+    if (grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            double* out = grad + 12 * i;
+            for (int j = 0; j < 12; ++j) out[j] = 0.0;
+            if (!A[i].valid || !P[i].valid) continue;
+            double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
+            for (int64_t s = 0; s < S; ++s) {
+                const float* p = pts + 3 * s;
+                if (!(pred_t_at(&P[i], p[0], p[1], p[2]) > T)) continue;
+                double d[3] = {p[0] - A[i].mu[0], p[1] - A[i].mu[1], p[2] - A[i].mu[2]};
+                double Gv = exp(-0.5 * maha2(&A[i], p[0], p[1], p[2]));
+                Ag += Gv * gn[s];
+                Bg += Gv * gd[s];
+                double c = A[i].w * (A[i].a * gn[s] + gd[s]);
+                double h = -0.5 * c * Gv;
+                for (int a2 = 0; a2 < 3; ++a2) {
+                    S1[a2] += h * d[a2];
+                    for (int b = 0; b < 3; ++b) S2[a2][b] += h * d[a2] * d[b];
+                }
+            }
+            chain_rule(&A[i], prm + 12 * i, Ag, Bg, S1, S2, out);
+        }
+    }
+    free(A); free(P); free(num); free(den); free(gn); free(gd);
+    return loss;
+}
+
+/* Stratified-sample refinement: iteration t draws its S points (iteration
+ * index step0 + t), takes the sampled loss and gradient, then one Adam
+ * step; losses[t] receives the sampled loss.  prm is updated in place. */
+int or_refine_sampled(double* prm, int64_t n, const float* field, const int dims[3], int64_t S, uint64_t seed,
+                      int step0, float k, double rho0, double occ, int iters, double lr, double b1, double b2,
+                      double eps, double* losses)
+{
+    int64_t M = (int64_t)dims[0] * dims[1] * dims[2], nh, nm;
+    or_sample_classes(field, dims, NULL, &nh, NULL, &nm);
+    int64_t* hi = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nh > 0 ? nh : 1));
+    int64_t* mid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm > 0 ? nm : 1));
+    float* pts = (float*)malloc(sizeof(float) * 3 * (size_t)S);
+    float* vals = (float*)malloc(sizeof(float) * (size_t)S);
+    double* g = (double*)malloc(sizeof(double) * 12 * (size_t)(n > 0 ? n : 1));
+    double* m = (double*)calloc(12 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    double* v = (double*)calloc(12 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!hi || !mid || !pts || !vals || !g || !m || !v) return 1;
+    or_sample_classes(field, dims, hi, &nh, mid, &nm);
+    (void)M;
+    for (int t = 0; t < iters; ++t) {
+        or_draw_samples(field, dims, hi, nh, mid, nm, S, seed, (uint32_t)(step0 + t), pts, vals, NULL);
+        double L = or_sample_loss_grad(prm, n, pts, vals, S, k, rho0, occ, g, NULL);
+        if (losses) losses[t] = L;
+        or_adam(prm, m, v, g, 12 * n, step0 + t + 1, lr, b1, b2, eps);
+    }
+    free(hi); free(mid); free(pts); free(vals); free(g); free(m); free(v);
+    return 0;
+}

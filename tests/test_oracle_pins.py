@@ -741,3 +741,133 @@ def test_kept_submasks_brute_force():
                             want |= 1 << ((y - by * B) // (B // 2) + 2 * ((z - bz * B) // (B // 4)))
             assert m == want, (B, kk, gg)
         assert got.any() and not got.all()
+
+
+# ---------------------------------------------------------------------------
+# Stratified-sample refinement (Sec. III-F, Table III)
+# ---------------------------------------------------------------------------
+def _sample_field(n=20, seed=3):
+    rng = np.random.default_rng(seed)
+    V = rng.uniform(0, 1, (n, n - 2, n - 4)).astype(np.float32) ** 2
+    V[:, :3, :] = 0.0      # an empty region
+    return V
+
+
+def test_sample_classes_and_split():
+    V = _sample_field()
+    hi, mid = O.sample_classes(V)
+    flat = V.reshape(-1)
+    np.testing.assert_array_equal(hi, np.nonzero(flat > np.float32(0.4))[0])
+    np.testing.assert_array_equal(mid, np.nonzero((flat > np.float32(0.02)) & (flat <= np.float32(0.4)))[0])
+    np.testing.assert_array_equal(O.sample_split(3072), [1075, 1229, 768])   # Table III: 35 / 40 / 25 %
+    for S in (1, 7, 100, 4096):
+        sp = O.sample_split(S)
+        assert sp.sum() == S and sp[0] == int(np.floor(0.35 * S + 0.5)) and sp[1] == int(np.floor(0.4 * S + 0.5))
+
+
+def test_draw_samples_classes_jitter_targets():
+    from scipy.ndimage import map_coordinates
+    V = _sample_field()
+    nz, ny, nx = V.shape
+    hi, mid = O.sample_classes(V)
+    S = 3072
+    pts, vals, vox = O.draw_samples(V, S, seed=11, it=5)
+    nh, nm, _ = O.sample_split(S)
+    assert np.isin(vox[:nh], hi).all() and np.isin(vox[nh:nh + nm], mid).all()
+    assert ((vox >= 0) & (vox < V.size)).all()
+    c = np.stack([vox % nx, (vox // nx) % ny, vox // (nx * ny)], 1).astype(np.float64)
+    assert np.all(np.abs(pts.astype(np.float64) - c) <= 0.5)
+    # targets: trilinear interpolation, edge-clamped (scipy, order 1, nearest)
+    q = np.clip(pts.astype(np.float64), 0, np.array([nx - 1, ny - 1, nz - 1]))
+    ref = map_coordinates(V.astype(np.float64), [q[:, 2], q[:, 1], q[:, 0]], order=1, mode="nearest")
+    np.testing.assert_allclose(vals, ref, rtol=1e-6, atol=1e-7)
+    # deterministic per (seed, iteration), different across iterations
+    p2, v2, x2 = O.draw_samples(V, S, seed=11, it=5)
+    assert np.array_equal(pts, p2) and np.array_equal(vox, x2)
+    p3, _, _ = O.draw_samples(V, S, seed=11, it=6)
+    assert not np.array_equal(pts, p3)
+    # a class without voxels hands its samples to the uniform draw
+    Z = np.full_like(V, 0.1)
+    _, _, xz = O.draw_samples(Z, S, seed=1, it=0)
+    assert len(O.sample_classes(Z)[0]) == 0 and len(np.unique(xz[:nh])) > nh // 2
+
+
+def test_draw_samples_uniform_within_class():
+    """Chi-square: the high-class draws spread evenly over its voxels."""
+    from scipy.stats import chisquare
+    V = np.zeros((6, 6, 6), np.float32)
+    V[1:5, 2:4, 1:4] = 0.9            # 24 high voxels
+    hi, _ = O.sample_classes(V)
+    counts = np.zeros(V.size, np.int64)
+    nh = O.sample_split(1024)[0]
+    for it in range(40):
+        _, _, vox = O.draw_samples(V, 1024, seed=5, it=it)
+        np.add.at(counts, vox[:nh], 1)
+    assert counts[hi].sum() == 40 * nh
+    assert chisquare(counts[hi]).pvalue > 1e-3
+
+
+def test_sample_eval_at_voxel_centres_equals_voxel_eval():
+    rng = np.random.default_rng(21)
+    dims = (14, 12, 10)
+    p = np.zeros((25, 12))
+    p[:, 0:3] = rng.uniform(0, 1, (25, 3)) * (np.array(dims) - 1)
+    p[:, 3:6] = np.log(rng.uniform(0.7, 2.2, (25, 3)))
+    p[:, 6:10] = rng.normal(size=(25, 4))
+    p[:, 10] = rng.uniform(0.1, 1.0, 25)
+    p[:, 11] = rng.uniform(-2, 1, 25)
+    p = p.astype(np.float32).astype(np.float64)
+    _, _, vt = O.eval_region(p, dims)
+    idx = rng.integers(0, np.prod(dims), 300)
+    nx, ny = dims[0], dims[1]
+    pts = np.stack([idx % nx, (idx // nx) % ny, idx // (nx * ny)], 1).astype(np.float32)
+    _, _, vs = O.sample_loss_grad(p, pts, np.zeros(300, np.float32), want_grad=False)
+    np.testing.assert_allclose(vs, vt.reshape(-1)[idx], rtol=1e-12, atol=1e-14)
+
+
+def test_sample_eval_single_gaussian_closed_form():
+    """One Gaussian at continuous points: Vt = a where w G >= rho0, a w G / rho0
+    below, 0 outside the truncation (m computed here from R, s)."""
+    q = np.array([0.9, 0.2, -0.3, 0.25])
+    p = np.array([[5.3, 6.1, 4.7, np.log(1.5), np.log(0.8), np.log(2.0), *q, 0.7, 0.4]])
+    p = p.astype(np.float32).astype(np.float64)
+    w = 1 / (1 + np.exp(-p[0, 11]))
+    qn = p[0, 6:10] / np.linalg.norm(p[0, 6:10])
+    a_, b_, c_, d_ = qn
+    R = np.array([[1 - 2 * (c_ * c_ + d_ * d_), 2 * (b_ * c_ - a_ * d_), 2 * (b_ * d_ + a_ * c_)],
+                  [2 * (b_ * c_ + a_ * d_), 1 - 2 * (b_ * b_ + d_ * d_), 2 * (c_ * d_ - a_ * b_)],
+                  [2 * (b_ * d_ - a_ * c_), 2 * (c_ * d_ + a_ * b_), 1 - 2 * (b_ * b_ + c_ * c_)]])
+    C = R @ np.diag(np.exp(-2 * p[0, 3:6])) @ R.T
+    pts = (p[0, :3] + np.random.default_rng(2).normal(0, 2.5, (200, 3))).astype(np.float32)
+    _, _, vt = O.sample_loss_grad(p, pts, np.zeros(200, np.float32), want_grad=False)
+    d = pts.astype(np.float64) - p[0, :3]
+    m = np.einsum("si,ij,sj->s", d, C, d)
+    G = np.exp(-0.5 * m)
+    away = np.abs(m - 9.0) > 1e-3          # the float32 keep test decides at the surface itself
+    want = np.where(m < 9.0, np.where(w * G >= 0.05, p[0, 10], p[0, 10] * w * G / 0.05), 0.0)
+    np.testing.assert_allclose(vt[away], want[away], rtol=1e-12, atol=1e-15)
+    assert (m < 9).any() and (m > 9).any() and (w * G[m < 9] < 0.05).any()
+
+
+def test_sample_loss_gradient_central_differences():
+    """k = 20: no pair near the truncation surface, the loss is smooth."""
+    rng = np.random.default_rng(31)
+    n, S = 6, 120
+    p = np.zeros((n, 12))
+    p[:, 0:3] = rng.uniform(3, 7, (n, 3))
+    p[:, 3:6] = np.log(rng.uniform(0.8, 1.8, (n, 3)))
+    p[:, 6:10] = rng.normal(size=(n, 4))
+    p[:, 10] = rng.uniform(0.2, 1.0, n)
+    p[:, 11] = rng.uniform(-1, 1, n)
+    pts = rng.uniform(2, 8, (S, 3)).astype(np.float32)
+    vals = rng.uniform(0.03, 0.9, S).astype(np.float32)
+    L, g, _ = O.sample_loss_grad(p, pts, vals, k=20.0)
+    h = 3e-5
+    for i in range(n):
+        for j in range(12):
+            pp, pm = p.copy(), p.copy()
+            pp[i, j] += h
+            pm[i, j] -= h
+            fd = (O.sample_loss_grad(pp, pts, vals, k=20.0, want_grad=False)[0]
+                  - O.sample_loss_grad(pm, pts, vals, k=20.0, want_grad=False)[0]) / (2 * h)
+            assert abs(fd - g[i, j]) <= 1e-5 * max(abs(fd), 1e-4), (i, j, fd, g[i, j])

@@ -289,6 +289,44 @@ GVE_API gve_status gve_proposal_backward(gve_ctx* ctx, const float* model_dev, c
                                          int64_t n, gve_dims dims, int32_t accumulate, float* dP_dev,
                                          void* stream);
 
+/* ---- stratified-sample refinement (Sec. III-F, Table III) ------------------
+ * The paper's training regime: each iteration fits the field at S jittered
+ * points drawn by value class -- floor(0.35 S + 1/2) from voxels with
+ * V > 0.4, floor(0.40 S + 1/2) from occupied mid-range voxels
+ * (0.02 < V <= 0.4), the rest uniformly from the grid (a class without
+ * voxels hands its share to the uniform draw).  Sample j of iteration t uses
+ * the Philox4x32-10 words of counter (j, t, 4, 'GVE1') under key `seed`:
+ * voxel = the floor(x0 count / 2^32)-th of its class (ascending voxel
+ * order), point p = c + u with u_k = (x_{k+1} >> 8) 2^-24 - 1/2 rounded to
+ * float32, target = trilinear V(p) (FP64, edge-clamped) rounded to float32.
+ * Eq. 3 is evaluated at p with the same float32 keep test as at voxel
+ * centres; the loss is (1/S) sum_s 1[v_s > occ] (Vt(p_s) - v_s)^2 (occ =
+ * schedule mask_thresh, 0.02 when negative).  S <= 8192; grids of fewer than
+ * 2^32 voxels; normalized evaluation only. */
+
+/* The points of iteration `iter`: pts_out [S][4] float32 (x, y, z, target),
+ * 16-byte aligned; vox_out [S] int64 voxel indices or NULL. */
+GVE_API gve_status gve_draw_samples(gve_ctx* ctx, const float* field_dev, gve_dims dims, int64_t S,
+                                    uint64_t seed, uint32_t iter, float* pts_out_dev, int64_t* vox_out_dev,
+                                    void* stream);
+/* Eq. 3, the sampled value loss and (grad_out != NULL) its gradient
+ * [n][12] at caller-given points pts [S][4] (x, y, z, target).  loss_dev
+ * (device double) and vt_out [S] (Vt per point) are optional. */
+GVE_API gve_status gve_sample_loss_grad(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                                        const gve_eval_opts* opts, const float* pts_dev, int64_t S,
+                                        float occ_thresh, float* grad_out_dev, double* loss_dev,
+                                        float* vt_out_dev, void* stream);
+/* sched->iters iterations of draw -> sampled loss and gradient -> Adam on
+ * every primitive (iteration index sched->step0 + t selects the points and
+ * the bias correction).  adam_state and loss_trace_dev as for gve_refine
+ * (the trace receives the sampled losses).  stats (optional) adds one
+ * full-grid evaluation after the last step for sse_final / psnr_final;
+ * ms_total and ms_brick give the iterations' time. */
+GVE_API gve_status gve_refine_sampled(gve_ctx* ctx, float* prims_dev, int64_t n, const float* field_dev,
+                                      gve_dims dims, const gve_schedule* sched, int64_t S, uint64_t seed,
+                                      float* adam_state_dev, double* loss_trace_dev, gve_stats* stats,
+                                      void* stream);
+
 /* Brick binning introspection: the (brick, Gaussian) pairs that evaluation
  * uses, sorted by brick key (z-major brick index) and then by Gaussian index,
  * and per-brick [start, end) ranges.

@@ -632,4 +632,164 @@ gve_status allocate(gve_ctx* c, const float* V, gve_dims d, int64_t N, const gve
     return GVE_OK;
 }
 
+// ------------------------------------------------------------------------
+// Stratified samples (Sec. III-F; Table III: 3,072 per iteration, 35 / 40 /
+// 25 %): value-class lists and the per-iteration draw.  Compiled without
+// FMA contraction, so the FP64 trilinear targets follow the written order.
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr int kClsChunk = 4096;          // voxels per block of the class passes
+constexpr uint32_t kSampleStream = 4u;   // Philox stream of the sample draw
+
+__device__ __forceinline__ bool cls_hi(float x) { return x > 0.4f; }
+__device__ __forceinline__ bool cls_mid(float x) { return x > 0.02f && !(x > 0.4f); }
+
+__global__ void __launch_bounds__(256) k_cls_count(const float* __restrict__ V, long long M,
+                                                   uint32_t* __restrict__ cnt_hi, uint32_t* __restrict__ cnt_mid)
+{
+    __shared__ uint32_t sh[8], sm[8];
+    const long long b0 = (long long)blockIdx.x * kClsChunk;
+    uint32_t h = 0, m = 0;
+    for (int k = threadIdx.x; k < kClsChunk; k += 256) {
+        const long long v = b0 + k;
+        if (v < M) {
+            const float x = V[v];
+            h += cls_hi(x);
+            m += cls_mid(x);
+        }
+    }
+    h = __reduce_add_sync(0xffffffffu, h);
+    m = __reduce_add_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) { sh[threadIdx.x >> 5] = h; sm[threadIdx.x >> 5] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t th = 0, tm = 0;
+        for (int w = 0; w < 8; ++w) { th += sh[w]; tm += sm[w]; }
+        cnt_hi[blockIdx.x] = th;
+        cnt_mid[blockIdx.x] = tm;
+    }
+}
+
+// members of each block's chunk, ascending, at the block's offsets
+__global__ void __launch_bounds__(256) k_cls_write(const float* __restrict__ V, long long M,
+                                                   const unsigned long long* __restrict__ off_hi,
+                                                   const unsigned long long* __restrict__ off_mid,
+                                                   uint32_t* __restrict__ hi, uint32_t* __restrict__ mid)
+{
+    __shared__ uint32_t wh[8], wm[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long oh = off_hi[blockIdx.x], om = off_mid[blockIdx.x];
+    const long long b0 = (long long)blockIdx.x * kClsChunk;
+    for (int it = 0; it < kClsChunk / 256; ++it) {
+        const long long v = b0 + (long long)it * 256 + threadIdx.x;
+        const float x = v < M ? V[v] : 0.f;
+        const bool fh = v < M && cls_hi(x), fm = v < M && cls_mid(x);
+        const unsigned bh = __ballot_sync(0xffffffffu, fh), bm = __ballot_sync(0xffffffffu, fm);
+        if (lane == 0) { wh[w] = __popc(bh); wm[w] = __popc(bm); }
+        __syncthreads();
+        uint32_t ph = 0, pm = 0, th = 0, tm = 0;
+        for (int k = 0; k < 8; ++k) {
+            if (k < w) { ph += wh[k]; pm += wm[k]; }
+            th += wh[k];
+            tm += wm[k];
+        }
+        if (fh) hi[oh + ph + __popc(bh & lt)] = (uint32_t)v;
+        if (fm) mid[om + pm + __popc(bm & lt)] = (uint32_t)v;
+        oh += th;
+        om += tm;
+        __syncthreads();
+    }
+}
+
+struct SampleDraw {
+    const float* V;
+    int nx, ny, nz;
+    const uint32_t* hi;
+    const uint32_t* mid;
+    unsigned long long nh, nm;
+    long long S, s_hi, s_mid;
+    unsigned long long seed;
+    uint32_t iter;
+    float4* pts;
+    long long* vox;
+};
+
+// sample j: Philox words x0..x3 of counter (j, iter, 4, 'GVE1'); the voxel
+// is the floor(x0 count / 2^32)-th of its class (a class without voxels
+// hands its samples to the uniform draw over the grid), the point c + u with
+// u_k = (x_{k+1} >> 8) 2^-24 - 1/2, the target the FP64 trilinear V(p)
+__global__ void __launch_bounds__(128) k_draw_samples(SampleDraw a)
+{
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.S) return;
+    uint32_t r[4];
+    draw(((unsigned long long)a.iter << 32) | (unsigned long long)(uint32_t)j, kSampleStream, a.seed, r);
+    const uint32_t* list = nullptr;
+    unsigned long long count = (unsigned long long)a.nx * a.ny * a.nz;
+    if (j < a.s_hi && a.nh > 0) {
+        list = a.hi;
+        count = a.nh;
+    } else if (j >= a.s_hi && j < a.s_hi + a.s_mid && a.nm > 0) {
+        list = a.mid;
+        count = a.nm;
+    }
+    const unsigned long long k = ((unsigned long long)r[0] * count) >> 32;
+    const long long v = list ? (long long)list[k] : (long long)k;
+    const int c[3] = {(int)(v % a.nx), (int)((v / a.nx) % a.ny), (int)(v / ((long long)a.nx * a.ny))};
+    float p[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float u = (float)(r[q + 1] >> 8) * 0x1p-24f - 0.5f;
+        p[q] = (float)c[q] + u;
+    }
+    const float val = (float)trilinear(a.V, a.nx, a.ny, a.nz, (double)p[0], (double)p[1], (double)p[2]);
+    a.pts[j] = make_float4(p[0], p[1], p[2], val);
+    if (a.vox) a.vox[j] = v;
+}
+
+}  // namespace
+
+gve_status sample_classes(gve_ctx* c, const float* V, gve_dims d, cudaStream_t s)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    if (M >= (1ll << 32)) return fail(c, GVE_E_INVALID, "sampled refinement needs fewer than 2^32 voxels");
+    const long long nb = (M + kClsChunk - 1) / kClsChunk;
+    gve_status st;
+    if ((st = ensure(c, c->s_cnt, sizeof(uint32_t) * 2 * nb, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->s_off, sizeof(unsigned long long) * 2 * (nb + 1), s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, s)) != GVE_OK) return st;
+    uint32_t* ch = (uint32_t*)c->s_cnt.p;
+    uint32_t* cm = ch + nb;
+    unsigned long long* oh = (unsigned long long*)c->s_off.p;
+    unsigned long long* om = oh + nb + 1;
+    k_cls_count<<<(unsigned)nb, 256, 0, s>>>(V, M, ch, cm);
+    launch_exscan_u32(ch, nb, oh, c->scanp.p, s);
+    launch_exscan_u32(cm, nb, om, c->scanp.p, s);
+    unsigned long long tot[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&tot[0], oh + nb, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], om + nb, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "class counts");
+    if ((st = ensure(c, c->s_hi, sizeof(uint32_t) * (tot[0] > 0 ? tot[0] : 1), s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->s_mid, sizeof(uint32_t) * (tot[1] > 0 ? tot[1] : 1), s)) != GVE_OK) return st;
+    k_cls_write<<<(unsigned)nb, 256, 0, s>>>(V, M, oh, om, (uint32_t*)c->s_hi.p, (uint32_t*)c->s_mid.p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "class lists");
+    c->s_nh = tot[0];
+    c->s_nm = tot[1];
+    c->launches += 8;
+    return GVE_OK;
+}
+
+void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigned long long nh, const uint32_t* mid,
+                         unsigned long long nm, long long S, long long s_hi, long long s_mid,
+                         unsigned long long seed, uint32_t iter, float4* pts, long long* vox, cudaStream_t s)
+{
+    if (S <= 0) return;
+    SampleDraw a{V, d.nx, d.ny, d.nz, hi, mid, nh, nm, S, s_hi, s_mid, seed, iter, pts, vox};
+    k_draw_samples<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(a);
+}
+
 }  // namespace gve

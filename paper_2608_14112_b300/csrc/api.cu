@@ -296,7 +296,9 @@ void gve_ctx_destroy(gve_ctx* c)
     cudaDeviceSynchronize();
     Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->bmask, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
                    &c->vals[0], &c->vals[1], &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
-                   &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace};
+                   &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace,
+                   &c->s_hi, &c->s_mid, &c->s_cnt, &c->s_off, &c->s_pts, &c->s_cell, &c->s_order, &c->s_nd,
+                   &c->s_gg, &c->s_loss};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->hstate) cudaFreeHost(c->hstate);

@@ -94,6 +94,11 @@ struct gve_ctx {
     cudaStream_t gstream = nullptr;
     cudaEvent_t fork = nullptr;
     gve::Buf bstate;                 // batch device state: step counter, {bc1, bc2}
+    // stratified-sample refinement: class lists, per-block counts and
+    // offsets, samples, cell table, sorted sample order, per-sample sums and
+    // upstream gradients, loss
+    gve::Buf s_hi, s_mid, s_cnt, s_off, s_pts, s_cell, s_order, s_nd, s_gg, s_loss;
+    unsigned long long s_nh = 0, s_nm = 0;
 };
 
 namespace gve {
@@ -178,6 +183,17 @@ void launch_chain(const float* acc_in, float* acc_zero, float* prims, long long 
 gve_status allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget,
                     const gve_alloc_opts* o, float* prims, int64_t* feasible_max,
                     gve_alloc_info* info, cudaStream_t s);
+
+// ---- stratified samples (alloc.cu: classes and draw) -----------------------
+// voxel lists of the high (V > 0.4) and occupied mid-range (0.02 < V <= 0.4)
+// classes, ascending, into c->s_hi / c->s_mid with sizes c->s_nh / c->s_nm
+// (synchronises `s` to read them); the grid must have fewer than 2^32 voxels
+gve_status sample_classes(gve_ctx* c, const float* V, gve_dims d, cudaStream_t s);
+// sample j of iteration `iter`: (x, y, z, target) into pts[j], voxel into
+// vox[j] when vox != nullptr; s_hi / s_mid = samples of the two classes
+void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigned long long nh, const uint32_t* mid,
+                         unsigned long long nm, long long S, long long s_hi, long long s_mid,
+                         unsigned long long seed, uint32_t iter, float4* pts, long long* vox, cudaStream_t s);
 
 // ---- context scratch and the evaluation pipeline (api.cu) ----------------
 gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s);

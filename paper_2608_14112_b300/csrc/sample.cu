@@ -1,0 +1,533 @@
+// sample.cu -- stratified-sample refinement (Sec. III-F; Table III: 3,072
+// jittered points per iteration, 35 / 40 / 25 % from high-value, occupied
+// mid-range and all voxels): Eq. 3, the value loss and its gradient at the
+// iteration's points, then the shared chain rule and Adam (optim.cu).
+//
+// The points are few (at most kMaxSamples), so they are bucketed into a
+// coarse grid of cells (32^3 voxels, coarser for very large grids) by one
+// CTA (bitonic sort of (cell, sample)), and the Gaussians do the searching:
+// one thread per Gaussian visits the cells its conservative box overlaps
+// and tests each point there with the same float32 keep chain as the
+// voxel path (kept iff t > T).  The forward adds w a G and w G into the
+// point's sums with float atomics; the backward repeats the search and
+// accumulates the Gaussian's sums A = sum G gn, H = sum h and the moments
+// of h = G (a gn + gd) over d = p - mu in registers, then writes them to
+// the accumulator layout the chain rule reads.  Nothing per pair is stored.
+//
+// Box of Gaussian i: centre mu, half-extent kb sqrt(Sigma_jj) with
+// kb = k (1.001 + 1e-5 cond) (cond = (s_max / s_min)^2) plus 0.05 voxel,
+// in float32: its margins cover the float32 rounding of the keep chain.
+#include <cmath>
+
+#include "gve_int.cuh"
+
+namespace gve {
+
+namespace {
+
+constexpr int kMaxSamples = 8192;
+constexpr int kCellSortThreads = 1024;
+constexpr long long kMaxCells = 1ll << 21;
+
+struct CellGrid {
+    int shift;  // cell edge = 2^shift voxels
+    int ncx, ncy, ncz;
+};
+
+CellGrid make_cells(gve_dims d)
+{
+    CellGrid g{};
+    for (g.shift = 5;; ++g.shift) {
+        g.ncx = ((d.nx - 1) >> g.shift) + 1;
+        g.ncy = ((d.ny - 1) >> g.shift) + 1;
+        g.ncz = ((d.nz - 1) >> g.shift) + 1;
+        if ((long long)g.ncx * g.ncy * g.ncz <= kMaxCells) break;
+    }
+    return g;
+}
+
+// voxel coordinate floor(p) clamped to the grid, then its cell
+__device__ __forceinline__ int cell_of(float p, int n, int shift, int nc)
+{
+    int v = (int)floorf(p);
+    v = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
+    const int c = v >> shift;
+    return c < nc ? c : nc - 1;
+}
+
+// One CTA: sort the S points by cell (bitonic over the next power of two),
+// write the sorted points and their original indices, and each occupied
+// cell's [start, end) (cells are zeroed beforehand).
+__global__ void __launch_bounds__(kCellSortThreads) k_cell_sort(const float4* __restrict__ pts, int S, int nx,
+                                                                 int ny, int nz, CellGrid cg,
+                                                                 float4* __restrict__ spts,
+                                                                 uint32_t* __restrict__ order, uint2* __restrict__ cells)
+{
+    extern __shared__ unsigned long long sk[];
+    int P = 1;
+    while (P < S) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += kCellSortThreads) {
+        unsigned long long key = ~0ull;
+        if (i < S) {
+            const float4 q = pts[i];
+            const int cx = cell_of(q.x, nx, cg.shift, cg.ncx), cy = cell_of(q.y, ny, cg.shift, cg.ncy),
+                      cz = cell_of(q.z, nz, cg.shift, cg.ncz);
+            const unsigned long long cell = ((unsigned long long)cz * cg.ncy + cy) * cg.ncx + cx;
+            key = (cell << 32) | (unsigned long long)i;
+        }
+        sk[i] = key;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += kCellSortThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = sk[i], b = sk[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { sk[i] = b; sk[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < S; i += kCellSortThreads) {
+        const unsigned long long key = sk[i];
+        const uint32_t cell = (uint32_t)(key >> 32), idx = (uint32_t)key;
+        order[i] = idx;
+        spts[i] = pts[idx];
+        if (i == 0 || (uint32_t)(sk[i - 1] >> 32) != cell) cells[cell].x = (uint32_t)i;
+        if (i == S - 1 || (uint32_t)(sk[i + 1] >> 32) != cell) cells[cell].y = (uint32_t)(i + 1);
+    }
+}
+
+struct SampleArgs {
+    const float* prims;
+    const float4* rec;
+    long long n;
+    int nx, ny, nz;
+    CellGrid cg;
+    const uint2* cells;
+    const float4* spts;
+    float2* nd;          // per sorted point: (sum w a G, sum w G)
+    const float2* gg;    // per sorted point: (dL/dnum, dL/dden)
+    float* acc;          // [n][12] accumulators (backward)
+    float k, T;
+};
+
+// Cell range of Gaussian i's conservative box; false for a record the
+// preparation marks invalid (non-finite values, zero quaternion).
+__device__ __forceinline__ bool gauss_cells(const SampleArgs& a, long long i, int lo[3], int hi[3])
+{
+    const float4* p4 = reinterpret_cast<const float4*>(a.prims) + 3 * i;
+    const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
+    const float p[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) ok = ok && isfinite(p[j]);
+    const float nq = sqrtf(p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9]);
+    if (!ok || !(nq > 0.f) || !isfinite(nq)) return false;
+    const float qw = p[6] / nq, qx = p[7] / nq, qy = p[8] / nq, qz = p[9] / nq;
+    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+    float s[3];
+    bool huge = false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s[j] = expf(p[3 + j]);
+        huge = huge || !isfinite(s[j]);
+    }
+    const int dims[3] = {a.nx, a.ny, a.nz};
+    const int nc[3] = {a.cg.ncx, a.cg.ncy, a.cg.ncz};
+    if (huge) {  // scales beyond float range: every cell
+        for (int j = 0; j < 3; ++j) { lo[j] = 0; hi[j] = nc[j] - 1; }
+        return true;
+    }
+    const float smax = fmaxf(s[0], fmaxf(s[1], s[2])), smin = fminf(s[0], fminf(s[1], s[2]));
+    const float ratio = smin > 0.f ? smax / smin : 1e30f;
+    const float kb = a.k * (1.001f + 1e-5f * fminf(ratio * ratio, 1e30f));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float var = R[j][0] * R[j][0] * s[0] * s[0] + R[j][1] * R[j][1] * s[1] * s[1] + R[j][2] * R[j][2] * s[2] * s[2];
+        const float rad = kb * sqrtf(var) * 1.0001f + 0.05f;
+        float l = floorf(p[j] - rad), h = floorf(p[j] + rad);
+        l = fminf(fmaxf(l, 0.f), (float)(dims[j] - 1));
+        h = fminf(fmaxf(h, 0.f), (float)(dims[j] - 1));
+        lo[j] = ((int)l) >> a.cg.shift;
+        hi[j] = ((int)h) >> a.cg.shift;
+    }
+    return true;
+}
+
+// the keep exponent at a float32 point, by the voxel path's chain
+__device__ __forceinline__ float keep_t(const float4& r0, const float4& r1, const float4& r2, float dx, float dy,
+                                        float dz)
+{
+    const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
+    const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
+    return __fmaf_rn(dx, __fmaf_rn(r0.w, dx, b), c);
+}
+
+__global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int lo[3], hi[3];
+    if (!gauss_cells(a, i, lo, hi)) return;
+    const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
+    if (!(r2.z > 0.f)) return;  // invalid record (weight zero)
+    for (int cz = lo[2]; cz <= hi[2]; ++cz)
+        for (int cy = lo[1]; cy <= hi[1]; ++cy)
+            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                const uint2 rg = a.cells[((long long)cz * a.cg.ncy + cy) * a.cg.ncx + cx];
+                for (uint32_t s = rg.x; s < rg.y; ++s) {
+                    const float4 q = a.spts[s];
+                    const float t = keep_t(r0, r1, r2, __fsub_rn(q.x, r0.x), __fsub_rn(q.y, r0.y), __fsub_rn(q.z, r0.z));
+                    if (!(t > a.T)) continue;
+                    const float G = ex2_approx(t);
+                    atomicAdd(&a.nd[s].x, r2.y * G);
+                    atomicAdd(&a.nd[s].y, r2.z * G);
+                }
+            }
+}
+
+__global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float A = 0.f, H = 0.f, S1[3] = {0.f, 0.f, 0.f}, S2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int lo[3], hi[3];
+    const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
+    if (gauss_cells(a, i, lo, hi) && r2.z > 0.f) {
+        for (int cz = lo[2]; cz <= hi[2]; ++cz)
+            for (int cy = lo[1]; cy <= hi[1]; ++cy)
+                for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                    const uint2 rg = a.cells[((long long)cz * a.cg.ncy + cy) * a.cg.ncx + cx];
+                    for (uint32_t s = rg.x; s < rg.y; ++s) {
+                        const float4 q = a.spts[s];
+                        const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
+                        const float t = keep_t(r0, r1, r2, dx, dy, dz);
+                        if (!(t > a.T)) continue;
+                        const float G = ex2_approx(t);
+                        const float2 g = a.gg[s];
+                        const float h = G * fmaf(r2.w, g.x, g.y);
+                        A = fmaf(G, g.x, A);
+                        H += h;
+                        S1[0] = fmaf(h, dx, S1[0]);
+                        S1[1] = fmaf(h, dy, S1[1]);
+                        S1[2] = fmaf(h, dz, S1[2]);
+                        S2[0] = fmaf(h * dx, dx, S2[0]);
+                        S2[1] = fmaf(h * dy, dy, S2[1]);
+                        S2[2] = fmaf(h * dz, dz, S2[2]);
+                        S2[3] = fmaf(h * dx, dy, S2[3]);
+                        S2[4] = fmaf(h * dx, dz, S2[4]);
+                        S2[5] = fmaf(h * dy, dz, S2[5]);
+                    }
+                }
+    }
+    float4* o = reinterpret_cast<float4*>(a.acc) + 3 * i;
+    o[0] = make_float4(A, H, S1[0], S1[1]);
+    o[1] = make_float4(S1[2], S2[0], S2[1], S2[2]);
+    o[2] = make_float4(S2[3], S2[4], S2[5], 0.f);
+}
+
+// One CTA: Vt = num / max(den, rho0), the masked value loss (1 / S) sum
+// 1[v > occ] (Vt - v)^2 (FP64 sum), and the upstream pair (dL/dnum, dL/dden)
+// per sorted point; vt_out (optional) by original index.
+__global__ void __launch_bounds__(1024) k_sample_loss(const float4* __restrict__ spts, const uint32_t* __restrict__ order,
+                                                      const float2* __restrict__ nd, int S, float rho0, float occ,
+                                                      float2* __restrict__ gg, double* loss, double* trace, int iter,
+                                                      float* vt_out)
+{
+    __shared__ double part[32];
+    double acc = 0.0;
+    const float inv2 = 2.f / (float)S;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const float4 q = spts[s];
+        const float2 v = nd[s];
+        const float dd = fmaxf(v.y, rho0);
+        const float vt = v.x / dd;
+        const float r = q.w > occ ? vt - q.w : 0.f;
+        acc += (double)r * (double)r;
+        const float gn = inv2 * r / dd;
+        gg[s] = make_float2(gn, v.y >= rho0 ? -vt * gn : 0.f);
+        if (vt_out) vt_out[order[s]] = vt;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        t /= (double)S;
+        if (loss) *loss = t;
+        if (trace) trace[iter] = t;
+    }
+}
+
+#define SMP_TRY(x)                               \
+    do {                                         \
+        gve_status st_ = (x);                    \
+        if (st_ != GVE_OK) return st_;           \
+    } while (0)
+#define SMP_CUDA(x, what)                                     \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+struct SampleBufs {
+    CellGrid cg;
+    long long ncells;
+    float4* pts;     // drawn (or caller's) points
+    float4* spts;    // sorted by cell
+    uint32_t* order;
+    uint2* cells;
+    float2* nd;
+    float2* gg;
+    double* loss;
+};
+
+gve_status sample_bufs(gve_ctx* c, gve_dims d, long long S, long long n, SampleBufs& b, cudaStream_t s)
+{
+    b.cg = make_cells(d);
+    b.ncells = (long long)b.cg.ncx * b.cg.ncy * b.cg.ncz;
+    const long long nn = n > 0 ? n : 1;
+    SMP_TRY(ensure(c, c->s_pts, sizeof(float4) * 2 * S, s));
+    SMP_TRY(ensure(c, c->s_order, sizeof(uint32_t) * S, s));
+    SMP_TRY(ensure(c, c->s_cell, sizeof(uint2) * b.ncells, s));
+    SMP_TRY(ensure(c, c->s_nd, sizeof(float2) * S, s));
+    SMP_TRY(ensure(c, c->s_gg, sizeof(float2) * S, s));
+    SMP_TRY(ensure(c, c->s_loss, sizeof(double), s));
+    SMP_TRY(ensure(c, c->rec, sizeof(float4) * 3 * nn, s));
+    SMP_TRY(ensure(c, c->binrec, sizeof(BinRec) * nn, s));
+    SMP_TRY(ensure(c, c->acc, sizeof(float) * 12 * nn, s));
+    b.pts = (float4*)c->s_pts.p;
+    b.spts = b.pts + S;
+    b.order = (uint32_t*)c->s_order.p;
+    b.cells = (uint2*)c->s_cell.p;
+    b.nd = (float2*)c->s_nd.p;
+    b.gg = (float2*)c->s_gg.p;
+    b.loss = (double*)c->s_loss.p;
+    return GVE_OK;
+}
+
+// preparation, cells, forward and loss at the points in b.pts; with
+// `backward` the Gaussians' sums are written to c->acc
+gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, const gve_eval_opts* o, long long S,
+                       const SampleBufs& b, float occ, double* trace, int iter, float* vt_out, bool backward,
+                       cudaStream_t s)
+{
+    const BinGeom g = make_geom(d, o->brick);
+    if (n > 0) launch_prep(prims, n, g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, s);
+    SMP_CUDA(cudaMemsetAsync(b.cells, 0, sizeof(uint2) * b.ncells, s), "memset cells");
+    int P = 1;
+    while (P < S) P <<= 1;
+    k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P, s>>>(b.pts, (int)S, d.nx, d.ny, d.nz, b.cg,
+                                                                             b.spts, b.order, b.cells);
+    SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * S, s), "memset sums");
+    SampleArgs a{};
+    a.prims = prims;
+    a.rec = (const float4*)c->rec.p;
+    a.n = n;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
+    a.cg = b.cg;
+    a.cells = b.cells;
+    a.spts = b.spts;
+    a.nd = b.nd;
+    a.gg = b.gg;
+    a.acc = (float*)c->acc.p;
+    a.k = o->trunc_k;
+    a.T = (float)((double)o->trunc_k * (double)o->trunc_k * kNegHalfLog2e);
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    if (n > 0) k_sample_eval<<<grid, 128, 0, s>>>(a);
+    k_sample_loss<<<1, 1024, 0, s>>>(b.spts, b.order, b.nd, (int)S, o->rho0, occ, b.gg, b.loss, trace, iter, vt_out);
+    if (backward && n > 0) k_sample_grad<<<grid, 128, 0, s>>>(a);
+    c->launches += 3 + (n > 0 ? 2 + (backward ? 1 : 0) : 0);
+    SMP_CUDA(cudaGetLastError(), "launch (sampled pass)");
+    return GVE_OK;
+}
+
+// class lists of the field, then the split of S
+gve_status sample_setup(gve_ctx* c, const float* field, gve_dims d, long long S, long long split[2], cudaStream_t s)
+{
+    SMP_TRY(sample_classes(c, field, d, s));
+    split[0] = (long long)std::floor(0.35 * (double)S + 0.5);
+    split[1] = (long long)std::floor(0.40 * (double)S + 0.5);
+    return GVE_OK;
+}
+
+gve_status check_samples(gve_ctx* c, int64_t S, const gve_eval_opts* o)
+{
+    if (S < 1 || S > kMaxSamples) return fail(c, GVE_E_INVALID, "samples per iteration must be in [1, 8192]");
+    if (!o->normalized) return fail(c, GVE_E_INVALID, "sampled refinement evaluates Eq. 3 (normalized = 1)");
+    static bool smem_set[64] = {};
+    const int dev = c->device;
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(k_cell_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(sizeof(unsigned long long) * kMaxSamples));
+        if (e != cudaSuccess) return cuda_fail(c, e, "cell sort shared memory");
+        smem_set[dev] = true;
+    }
+    return GVE_OK;
+}
+
+// full-grid SSE of the current records (the voxel path's loss pass)
+gve_status full_grid_sse(gve_ctx* c, const float* prims, int64_t n, const float* field, gve_dims d,
+                         const gve_eval_opts* o, void* stream, double* sse)
+{
+    Call k;
+    SMP_TRY(begin(c, k, n, d, o, stream));
+    SMP_TRY(size_pairs(k, prims, o));
+    const double inv_m = 1.0 / ((double)d.nx * d.ny * d.nz);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        SMP_TRY(bin_all(k, prims, o, 0));
+        BrickArgs a = brick_args(k, o);
+        a.field = field;
+        a.mask_thresh = -1.f;
+        a.acc = nullptr;
+        launch_brick(kModeLoss, a, k.s);
+        launch_sse_reduce(a.part, k.g.nbricks, dstate(c), nullptr, 0, inv_m, k.s);
+        DevState h;
+        SMP_TRY(read_state(k, &h));
+        if (!h.overflow) {
+            *sse = h.sse[1];
+            return GVE_OK;
+        }
+        SMP_TRY(grow_pairs(k, h.max_total));
+        reset_state(k);
+    }
+    return fail(c, GVE_E_CAPACITY, "final evaluation overflowed");
+}
+
+}  // namespace
+
+}  // namespace gve
+
+using namespace gve;
+
+extern "C" gve_status gve_draw_samples(gve_ctx* c, const float* field, gve_dims d, int64_t S, uint64_t seed,
+                                       uint32_t iter, float* pts_out, int64_t* vox_out, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!field || !pts_out) return fail(c, GVE_E_INVALID, "null argument");
+    if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
+    if (S < 1 || S > kMaxSamples) return fail(c, GVE_E_INVALID, "samples per iteration must be in [1, 8192]");
+    if (reinterpret_cast<uintptr_t>(pts_out) & 15u) return fail(c, GVE_E_INVALID, "points not 16-byte aligned");
+    SMP_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->launches = 0;
+    long long split[2];
+    SMP_TRY(sample_setup(c, field, d, S, split, s));
+    launch_draw_samples(field, d, (const uint32_t*)c->s_hi.p, c->s_nh, (const uint32_t*)c->s_mid.p, c->s_nm, S,
+                        split[0], split[1], seed, iter, reinterpret_cast<float4*>(pts_out),
+                        reinterpret_cast<long long*>(vox_out), s);
+    SMP_CUDA(cudaGetLastError(), "launch (draw)");
+    return GVE_OK;
+}
+
+extern "C" gve_status gve_sample_loss_grad(gve_ctx* c, const float* prims, int64_t n, gve_dims d,
+                                           const gve_eval_opts* o, const float* pts, int64_t S, float occ_thresh,
+                                           float* grad_out, double* loss_dev, float* vt_out, void* stream)
+{
+    SMP_TRY(check_common(c, prims, n, d, o));
+    SMP_TRY(check_samples(c, S, o));
+    if (!pts) return fail(c, GVE_E_INVALID, "null points");
+    if ((reinterpret_cast<uintptr_t>(pts) & 15u) || (grad_out && (reinterpret_cast<uintptr_t>(grad_out) & 15u)))
+        return fail(c, GVE_E_INVALID, "points and gradient must be 16-byte aligned");
+    SMP_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->launches = 0;
+    SampleBufs b;
+    SMP_TRY(sample_bufs(c, d, S, n, b, s));
+    SMP_CUDA(cudaMemcpyAsync(b.pts, pts, sizeof(float4) * S, cudaMemcpyDeviceToDevice, s), "copy points");
+    SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ_thresh, nullptr, 0, vt_out, grad_out != nullptr, s));
+    if (loss_dev) SMP_CUDA(cudaMemcpyAsync(loss_dev, b.loss, sizeof(double), cudaMemcpyDeviceToDevice, s), "copy loss");
+    if (grad_out && n > 0) {
+        launch_chain((float*)c->acc.p, nullptr, const_cast<float*>(prims), n, grad_out, nullptr, nullptr, nullptr,
+                     nullptr, s);
+        c->launches += 1;
+    }
+    SMP_CUDA(cudaGetLastError(), "launch (sampled gradient)");
+    return GVE_OK;
+}
+
+extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, const float* field, gve_dims d,
+                                         const gve_schedule* sc, int64_t S, uint64_t seed, float* adam_state,
+                                         double* trace, gve_stats* stats, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!sc) return fail(c, GVE_E_INVALID, "null schedule");
+    SMP_TRY(check_common(c, prims, n, d, &sc->eval));
+    SMP_TRY(check_samples(c, S, &sc->eval));
+    if (!field) return fail(c, GVE_E_INVALID, "null target field");
+    if (sc->iters < 0 || sc->step0 < 0) return fail(c, GVE_E_INVALID, "negative iteration count");
+    if (!(sc->lr >= 0.f) || !(sc->beta1 >= 0.f && sc->beta1 < 1.f) || !(sc->beta2 >= 0.f && sc->beta2 < 1.f) ||
+        !(sc->eps >= 0.f))
+        return fail(c, GVE_E_INVALID, "bad Adam hyper-parameters");
+    if (adam_state && (reinterpret_cast<uintptr_t>(adam_state) & 15u))
+        return fail(c, GVE_E_INVALID, "adam state not 16-byte aligned");
+    SMP_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->launches = 0;
+    const gve_eval_opts* o = &sc->eval;
+    const float occ = sc->mask_thresh >= 0.f ? sc->mask_thresh : 0.02f;
+    long long split[2];
+    SMP_TRY(sample_setup(c, field, d, S, split, s));
+    SampleBufs b;
+    SMP_TRY(sample_bufs(c, d, S, n, b, s));
+    const long long nn = n > 0 ? n : 1;
+    float* m = adam_state;
+    if (!m) {
+        SMP_TRY(ensure(c, c->adam, sizeof(float) * 24 * nn, s));
+        m = (float*)c->adam.p;
+        SMP_CUDA(cudaMemsetAsync(m, 0, sizeof(float) * 24 * nn, s), "memset adam");
+    }
+    float* v = adam_state ? adam_state + 12 * n : m + 12 * nn;
+    SMP_TRY(ensure(c, c->state, sizeof(DevState), s));
+    SMP_CUDA(cudaEventRecord(c->ev0, s), "event");
+    for (int it = 0; it < sc->iters; ++it) {
+        const int step = sc->step0 + it;
+        launch_draw_samples(field, d, (const uint32_t*)c->s_hi.p, c->s_nh, (const uint32_t*)c->s_mid.p, c->s_nm, S,
+                            split[0], split[1], seed, (uint32_t)step, b.pts, nullptr, s);
+        SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ, trace, it, nullptr, true, s));
+        if (n > 0) {
+            AdamArgs ad{};
+            ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
+            ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step + 1));
+            ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step + 1));
+            launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s);
+            c->launches += 1;
+        }
+        c->launches += 1;
+    }
+    SMP_CUDA(cudaEventRecord(c->ev1, s), "event");
+    SMP_CUDA(cudaGetLastError(), "launch (sampled refine)");
+    if (stats) {
+        float ms_loop = 0.f;
+        SMP_CUDA(cudaEventSynchronize(c->ev1), "sync");
+        cudaEventElapsedTime(&ms_loop, c->ev0, c->ev1);
+        const long long launches = c->launches;
+        double first = 0.0, last = 0.0;
+        if (trace && sc->iters > 0) {
+            SMP_CUDA(cudaMemcpy(&first, trace, sizeof(double), cudaMemcpyDeviceToHost), "trace");
+            SMP_CUDA(cudaMemcpy(&last, trace + sc->iters - 1, sizeof(double), cudaMemcpyDeviceToHost), "trace");
+        }
+        double sse = 0.0;
+        SMP_TRY(full_grid_sse(c, prims, n, field, d, o, stream, &sse));
+        const double M = (double)d.nx * d.ny * d.nz;
+        stats->loss_first = first;
+        stats->loss_last = last;
+        stats->sse_final = sse;
+        stats->psnr_final = sse > 0.0 ? 10.0 * std::log10(M / sse) : INFINITY;
+        stats->brick_pairs = 0;
+        stats->iters_done = sc->iters;
+        stats->retries = 0;
+        stats->ms_total = ms_loop;
+        stats->ms_brick = ms_loop;
+        stats->ms_bin = 0.f;
+        stats->launches = launches + c->launches;
+    }
+    return GVE_OK;
+}

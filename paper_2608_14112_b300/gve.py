@@ -107,6 +107,14 @@ def lib():
             L.gve_loss_grad.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(EvalOpts), ctypes.c_float, P, P, P]
             L.gve_backward.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P]
             L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
+            L.gve_draw_samples.argtypes = [P, P, Dims, i64, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
+            L.gve_draw_samples.restype = st
+            L.gve_sample_loss_grad.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, i64, ctypes.c_float,
+                                               P, P, P, P]
+            L.gve_sample_loss_grad.restype = st
+            L.gve_refine_sampled.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), i64, ctypes.c_uint64, P,
+                                             P, ctypes.POINTER(Stats), P]
+            L.gve_refine_sampled.restype = st
             L.gve_bin.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P, P, i64, P, ctypes.POINTER(i64), P]
             L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), P]
@@ -240,6 +248,62 @@ def gve_refine(prims: torch.Tensor, field: torch.Tensor, iters: int, lr: float =
     _check(lib().gve_refine(c, _ptr(prims), prims.shape[0], _ptr(field), _dims(field.shape), ctypes.byref(sched),
                             _ptr(adam_state), _ptr(trace), ctypes.byref(st) if want_stats else None,
                             _stream(prims.device)), c)
+    if not want_stats:
+        return None
+    return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def gve_draw_samples(field: torch.Tensor, S: int, seed: int, it: int, want_voxels: bool = False):
+    """The stratified points of iteration ``it``: (S, 4) float32 (x, y, z,
+    target) on the field's device, plus the voxel indices when asked."""
+    field = _field(field)
+    pts = torch.empty((S, 4), dtype=torch.float32, device=field.device)
+    vox = torch.empty(S, dtype=torch.int64, device=field.device) if want_voxels else None
+    c = context(field.device.index)
+    _check(lib().gve_draw_samples(c, _ptr(field), _dims(field.shape), int(S), int(seed), int(it), _ptr(pts),
+                                  _ptr(vox), _stream(field.device)), c)
+    return (pts, vox) if want_voxels else pts
+
+
+def gve_sample_loss_grad(prims: torch.Tensor, shape, pts: torch.Tensor, opts: EvalOptions | None = None,
+                         occ: float = 0.02, want_grad: bool = True):
+    """(sampled loss (float64 tensor), dL/dprims (N,12) or None, Vt per point)
+    at caller-given points (S, 4) = (x, y, z, target)."""
+    prims = _prims(prims)
+    if pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != 4 or not pts.is_contiguous():
+        raise ValueError("points must be a contiguous float32 (S, 4) tensor")
+    o = (opts or EvalOptions()).c()
+    S = pts.shape[0]
+    grad = torch.empty_like(prims) if want_grad else None
+    loss = torch.zeros(1, dtype=torch.float64, device=prims.device)
+    vt = torch.empty(S, dtype=torch.float32, device=prims.device)
+    c = context(prims.device.index)
+    _check(lib().gve_sample_loss_grad(c, _ptr(prims), prims.shape[0], _dims(shape), ctypes.byref(o), _ptr(pts), S,
+                                      float(occ), _ptr(grad), _ptr(loss), _ptr(vt), _stream(prims.device)), c)
+    return loss, grad, vt
+
+
+def gve_refine_sampled(prims: torch.Tensor, field: torch.Tensor, iters: int, S: int = 3072, seed: int = 0,
+                       lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15,
+                       occ: float = 0.02, step0: int = 0, opts: EvalOptions | None = None,
+                       adam_state: torch.Tensor | None = None, trace: torch.Tensor | None = None,
+                       want_stats: bool = True):
+    """Stratified-sample refinement in place on ``prims`` (the paper's training
+    regime).  With ``want_stats`` the result includes the full-grid PSNR
+    after the last step."""
+    prims, field = _prims(prims), _field(field)
+    sched = Schedule(int(iters), float(lr), float(beta1), float(beta2), float(eps), float(occ), int(step0),
+                     (opts or EvalOptions()).c())
+    if adam_state is not None:
+        if adam_state.shape != (2, prims.shape[0], 12) or adam_state.dtype != torch.float32 or not adam_state.is_contiguous():
+            raise ValueError("adam_state must be float32 (2, N, 12)")
+    if trace is not None and (trace.dtype != torch.float64 or trace.numel() < iters or not trace.is_cuda):
+        raise ValueError("trace must be a CUDA float64 tensor with >= iters entries")
+    st = Stats()
+    c = context(prims.device.index)
+    _check(lib().gve_refine_sampled(c, _ptr(prims), prims.shape[0], _ptr(field), _dims(field.shape),
+                                    ctypes.byref(sched), int(S), int(seed), _ptr(adam_state), _ptr(trace),
+                                    ctypes.byref(st) if want_stats else None, _stream(prims.device)), c)
     if not want_stats:
         return None
     return {name: getattr(st, name) for name, _ in Stats._fields_}

@@ -5,10 +5,14 @@
 //
 // The points are few (at most kMaxSamples), so they are bucketed into a
 // coarse grid of cells (32^3 voxels, coarser for very large grids) by one
-// CTA (bitonic sort of (cell, sample)), and the Gaussians do the searching:
-// one thread per Gaussian visits the cells its conservative box overlaps
-// and tests each point there with the same float32 keep chain as the
-// voxel path (kept iff t > T).  The forward adds w a G and w G into the
+// CTA (bitonic sort of (cell, sample), z-major cells, plus cstart[c] = the
+// number of points in cells before c), and the Gaussians do the searching:
+// one thread per Gaussian walks the (z, y) rows of cells its conservative
+// box overlaps -- the points of a row's cell range are one contiguous run of
+// the sorted points -- and tests each with the same float32 keep chain as
+// the voxel path (kept iff t > T).  A Gaussian whose box spans more rows
+// than half the number of points scans all points instead (training can
+// grow a few Gaussians to cover the grid).  The forward adds w a G and w G into the
 // point's sums with float atomics; the backward repeats the search and
 // accumulates the Gaussian's sums A = sum G gn, H = sum h and the moments
 // of h = G (a gn + gd) over d = p - mu in registers, then writes them to
@@ -56,12 +60,12 @@ __device__ __forceinline__ int cell_of(float p, int n, int shift, int nc)
 }
 
 // One CTA: sort the S points by cell (bitonic over the next power of two),
-// write the sorted points and their original indices, and each occupied
-// cell's [start, end) (cells are zeroed beforehand).
+// write the sorted points, their original indices, and cstart[c] for every
+// cell c = 0 .. ncells (binary search of the sorted cells).
 __global__ void __launch_bounds__(kCellSortThreads) k_cell_sort(const float4* __restrict__ pts, int S, int nx,
                                                                  int ny, int nz, CellGrid cg,
                                                                  float4* __restrict__ spts,
-                                                                 uint32_t* __restrict__ order, uint2* __restrict__ cells)
+                                                                 uint32_t* __restrict__ order, uint32_t* __restrict__ cstart)
 {
     extern __shared__ unsigned long long sk[];
     int P = 1;
@@ -92,12 +96,19 @@ __global__ void __launch_bounds__(kCellSortThreads) k_cell_sort(const float4* __
         }
     }
     for (int i = threadIdx.x; i < S; i += kCellSortThreads) {
-        const unsigned long long key = sk[i];
-        const uint32_t cell = (uint32_t)(key >> 32), idx = (uint32_t)key;
+        const uint32_t idx = (uint32_t)sk[i];
         order[i] = idx;
         spts[i] = pts[idx];
-        if (i == 0 || (uint32_t)(sk[i - 1] >> 32) != cell) cells[cell].x = (uint32_t)i;
-        if (i == S - 1 || (uint32_t)(sk[i + 1] >> 32) != cell) cells[cell].y = (uint32_t)(i + 1);
+    }
+    const long long ncells = (long long)cg.ncx * cg.ncy * cg.ncz;
+    for (long long c = threadIdx.x; c <= ncells; c += kCellSortThreads) {
+        int lo = 0, hi = S;  // first sorted point whose cell is >= c
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)(sk[mid] >> 32) < c) lo = mid + 1;
+            else hi = mid;
+        }
+        cstart[c] = (uint32_t)lo;
     }
 }
 
@@ -107,7 +118,8 @@ struct SampleArgs {
     long long n;
     int nx, ny, nz;
     CellGrid cg;
-    const uint2* cells;
+    const uint32_t* cstart;   // [ncells + 1]
+    int S;
     const float4* spts;
     float2* nd;          // per sorted point: (sum w a G, sum w G)
     const float2* gg;    // per sorted point: (dL/dnum, dL/dden)
@@ -169,6 +181,25 @@ __device__ __forceinline__ float keep_t(const float4& r0, const float4& r1, cons
     return __fmaf_rn(dx, __fmaf_rn(r0.w, dx, b), c);
 }
 
+// Calls f(s) for every sorted point s in the cells [lo, hi]: one contiguous
+// run per (z, y) row of cells, or every point when the rows outnumber half
+// the points.
+template <class F>
+__device__ __forceinline__ void for_candidates(const SampleArgs& a, const int lo[3], const int hi[3], F&& f)
+{
+    const long long rows = (long long)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+    if (2 * rows >= a.S) {
+        for (uint32_t s = 0; s < (uint32_t)a.S; ++s) f(s);
+        return;
+    }
+    for (int cz = lo[2]; cz <= hi[2]; ++cz)
+        for (int cy = lo[1]; cy <= hi[1]; ++cy) {
+            const long long base = ((long long)cz * a.cg.ncy + cy) * a.cg.ncx;
+            const uint32_t s0 = a.cstart[base + lo[0]], s1 = a.cstart[base + hi[0] + 1];
+            for (uint32_t s = s0; s < s1; ++s) f(s);
+        }
+}
+
 __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -177,19 +208,14 @@ __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
     if (!gauss_cells(a, i, lo, hi)) return;
     const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
     if (!(r2.z > 0.f)) return;  // invalid record (weight zero)
-    for (int cz = lo[2]; cz <= hi[2]; ++cz)
-        for (int cy = lo[1]; cy <= hi[1]; ++cy)
-            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                const uint2 rg = a.cells[((long long)cz * a.cg.ncy + cy) * a.cg.ncx + cx];
-                for (uint32_t s = rg.x; s < rg.y; ++s) {
-                    const float4 q = a.spts[s];
-                    const float t = keep_t(r0, r1, r2, __fsub_rn(q.x, r0.x), __fsub_rn(q.y, r0.y), __fsub_rn(q.z, r0.z));
-                    if (!(t > a.T)) continue;
-                    const float G = ex2_approx(t);
-                    atomicAdd(&a.nd[s].x, r2.y * G);
-                    atomicAdd(&a.nd[s].y, r2.z * G);
-                }
-            }
+    for_candidates(a, lo, hi, [&](uint32_t s) {
+        const float4 q = a.spts[s];
+        const float t = keep_t(r0, r1, r2, __fsub_rn(q.x, r0.x), __fsub_rn(q.y, r0.y), __fsub_rn(q.z, r0.z));
+        if (!(t > a.T)) return;
+        const float G = ex2_approx(t);
+        atomicAdd(&a.nd[s].x, r2.y * G);
+        atomicAdd(&a.nd[s].y, r2.z * G);
+    });
 }
 
 __global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
@@ -200,31 +226,26 @@ __global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
     int lo[3], hi[3];
     const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
     if (gauss_cells(a, i, lo, hi) && r2.z > 0.f) {
-        for (int cz = lo[2]; cz <= hi[2]; ++cz)
-            for (int cy = lo[1]; cy <= hi[1]; ++cy)
-                for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                    const uint2 rg = a.cells[((long long)cz * a.cg.ncy + cy) * a.cg.ncx + cx];
-                    for (uint32_t s = rg.x; s < rg.y; ++s) {
-                        const float4 q = a.spts[s];
-                        const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
-                        const float t = keep_t(r0, r1, r2, dx, dy, dz);
-                        if (!(t > a.T)) continue;
-                        const float G = ex2_approx(t);
-                        const float2 g = a.gg[s];
-                        const float h = G * fmaf(r2.w, g.x, g.y);
-                        A = fmaf(G, g.x, A);
-                        H += h;
-                        S1[0] = fmaf(h, dx, S1[0]);
-                        S1[1] = fmaf(h, dy, S1[1]);
-                        S1[2] = fmaf(h, dz, S1[2]);
-                        S2[0] = fmaf(h * dx, dx, S2[0]);
-                        S2[1] = fmaf(h * dy, dy, S2[1]);
-                        S2[2] = fmaf(h * dz, dz, S2[2]);
-                        S2[3] = fmaf(h * dx, dy, S2[3]);
-                        S2[4] = fmaf(h * dx, dz, S2[4]);
-                        S2[5] = fmaf(h * dy, dz, S2[5]);
-                    }
-                }
+        for_candidates(a, lo, hi, [&](uint32_t s) {
+            const float4 q = a.spts[s];
+            const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
+            const float t = keep_t(r0, r1, r2, dx, dy, dz);
+            if (!(t > a.T)) return;
+            const float G = ex2_approx(t);
+            const float2 g = a.gg[s];
+            const float h = G * fmaf(r2.w, g.x, g.y);
+            A = fmaf(G, g.x, A);
+            H += h;
+            S1[0] = fmaf(h, dx, S1[0]);
+            S1[1] = fmaf(h, dy, S1[1]);
+            S1[2] = fmaf(h, dz, S1[2]);
+            S2[0] = fmaf(h * dx, dx, S2[0]);
+            S2[1] = fmaf(h * dy, dy, S2[1]);
+            S2[2] = fmaf(h * dz, dz, S2[2]);
+            S2[3] = fmaf(h * dx, dy, S2[3]);
+            S2[4] = fmaf(h * dx, dz, S2[4]);
+            S2[5] = fmaf(h * dy, dz, S2[5]);
+        });
     }
     float4* o = reinterpret_cast<float4*>(a.acc) + 3 * i;
     o[0] = make_float4(A, H, S1[0], S1[1]);
@@ -283,7 +304,7 @@ struct SampleBufs {
     float4* pts;     // drawn (or caller's) points
     float4* spts;    // sorted by cell
     uint32_t* order;
-    uint2* cells;
+    uint32_t* cstart;
     float2* nd;
     float2* gg;
     double* loss;
@@ -296,7 +317,7 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long S, long long n, SampleB
     const long long nn = n > 0 ? n : 1;
     SMP_TRY(ensure(c, c->s_pts, sizeof(float4) * 2 * S, s));
     SMP_TRY(ensure(c, c->s_order, sizeof(uint32_t) * S, s));
-    SMP_TRY(ensure(c, c->s_cell, sizeof(uint2) * b.ncells, s));
+    SMP_TRY(ensure(c, c->s_cell, sizeof(uint32_t) * (b.ncells + 1), s));
     SMP_TRY(ensure(c, c->s_nd, sizeof(float2) * S, s));
     SMP_TRY(ensure(c, c->s_gg, sizeof(float2) * S, s));
     SMP_TRY(ensure(c, c->s_loss, sizeof(double), s));
@@ -306,7 +327,7 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long S, long long n, SampleB
     b.pts = (float4*)c->s_pts.p;
     b.spts = b.pts + S;
     b.order = (uint32_t*)c->s_order.p;
-    b.cells = (uint2*)c->s_cell.p;
+    b.cstart = (uint32_t*)c->s_cell.p;
     b.nd = (float2*)c->s_nd.p;
     b.gg = (float2*)c->s_gg.p;
     b.loss = (double*)c->s_loss.p;
@@ -321,11 +342,10 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
 {
     const BinGeom g = make_geom(d, o->brick);
     if (n > 0) launch_prep(prims, n, g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, s);
-    SMP_CUDA(cudaMemsetAsync(b.cells, 0, sizeof(uint2) * b.ncells, s), "memset cells");
     int P = 1;
     while (P < S) P <<= 1;
     k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P, s>>>(b.pts, (int)S, d.nx, d.ny, d.nz, b.cg,
-                                                                             b.spts, b.order, b.cells);
+                                                                             b.spts, b.order, b.cstart);
     SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * S, s), "memset sums");
     SampleArgs a{};
     a.prims = prims;
@@ -333,7 +353,8 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     a.n = n;
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
     a.cg = b.cg;
-    a.cells = b.cells;
+    a.cstart = b.cstart;
+    a.S = (int)S;
     a.spts = b.spts;
     a.nd = b.nd;
     a.gg = b.gg;
@@ -344,7 +365,7 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     if (n > 0) k_sample_eval<<<grid, 128, 0, s>>>(a);
     k_sample_loss<<<1, 1024, 0, s>>>(b.spts, b.order, b.nd, (int)S, o->rho0, occ, b.gg, b.loss, trace, iter, vt_out);
     if (backward && n > 0) k_sample_grad<<<grid, 128, 0, s>>>(a);
-    c->launches += 3 + (n > 0 ? 2 + (backward ? 1 : 0) : 0);
+    c->launches += 2 + (n > 0 ? 2 + (backward ? 1 : 0) : 0);
     SMP_CUDA(cudaGetLastError(), "launch (sampled pass)");
     return GVE_OK;
 }

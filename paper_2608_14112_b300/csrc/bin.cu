@@ -40,6 +40,8 @@ __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
 
+// BIN = false: the keep coefficients only (the sampled path has no bricks)
+template <bool BIN>
 __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, long long n, BinGeom g,
                                               float k, float4* __restrict__ rec, BinRec* __restrict__ br)
 {
@@ -96,6 +98,11 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
         r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, pf[10]);
 
         // conservative brick cover
+        if (!BIN) {
+            float4* o = rec + 3 * i;
+            o[0] = r0; o[1] = r1; o[2] = r2;
+            return;
+        }
         double smin = s[0], smax = s[0];
         for (int j = 1; j < 3; ++j) { smin = fmin(smin, s[j]); smax = fmax(smax, s[j]); }
         double ratio = dd(smax, smin);
@@ -132,14 +139,21 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
     }
     float4* o = rec + 3 * i;
     o[0] = r0; o[1] = r1; o[2] = r2;
-    br[i] = b;
+    if (BIN) br[i] = b;
 }
 
 void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec, BinRec* br,
                  cudaStream_t s)
 {
     if (n <= 0) return;
-    k_prep<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, br);
+    k_prep<true><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, br);
+}
+
+void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cudaStream_t s)
+{
+    if (n <= 0) return;
+    BinGeom g{};
+    k_prep<false><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, nullptr);
 }
 
 // float32 cover test of one brick (same operation order as the oracle)

@@ -121,6 +121,8 @@ BinGeom make_geom(gve_dims d, int B);
 
 void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec,
                  BinRec* br, cudaStream_t s);
+// the keep coefficients alone (same values as launch_prep's rec)
+void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cudaStream_t s);
 // per Gaussian: number of listed bricks, and the pass ballots of the first
 // kMaskChunks x 32 bricks of its box (reused by the emission pass)
 constexpr int kMaskChunks = 4;

@@ -340,8 +340,7 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
                        const SampleBufs& b, float occ, double* trace, int iter, float* vt_out, bool backward,
                        cudaStream_t s)
 {
-    const BinGeom g = make_geom(d, o->brick);
-    if (n > 0) launch_prep(prims, n, g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, s);
+    if (n > 0) launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
     int P = 1;
     while (P < S) P <<= 1;
     k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P, s>>>(b.pts, (int)S, d.nx, d.ny, d.nz, b.cg,

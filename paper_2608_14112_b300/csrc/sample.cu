@@ -334,13 +334,12 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long S, long long n, SampleB
     return GVE_OK;
 }
 
-// preparation, cells, forward and loss at the points in b.pts; with
-// `backward` the Gaussians' sums are written to c->acc
+// cells, forward and loss at the points in b.pts (the records prepared in
+// c->rec); with `backward` the Gaussians' sums are written to c->acc
 gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, const gve_eval_opts* o, long long S,
                        const SampleBufs& b, float occ, double* trace, int iter, float* vt_out, bool backward,
                        cudaStream_t s)
 {
-    if (n > 0) launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
     int P = 1;
     while (P < S) P <<= 1;
     k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P, s>>>(b.pts, (int)S, d.nx, d.ny, d.nz, b.cg,
@@ -462,6 +461,7 @@ extern "C" gve_status gve_sample_loss_grad(gve_ctx* c, const float* prims, int64
     SampleBufs b;
     SMP_TRY(sample_bufs(c, d, S, n, b, s));
     SMP_CUDA(cudaMemcpyAsync(b.pts, pts, sizeof(float4) * S, cudaMemcpyDeviceToDevice, s), "copy points");
+    launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
     SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ_thresh, nullptr, 0, vt_out, grad_out != nullptr, s));
     if (loss_dev) SMP_CUDA(cudaMemcpyAsync(loss_dev, b.loss, sizeof(double), cudaMemcpyDeviceToDevice, s), "copy loss");
     if (grad_out && n > 0) {
@@ -506,21 +506,47 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
     }
     float* v = adam_state ? adam_state + 12 * n : m + 12 * nn;
     SMP_TRY(ensure(c, c->state, sizeof(DevState), s));
+    // stage events (with stats): before the preparation, before the draw,
+    // before the chain rule; read back every 64 iterations
+    const bool timed = stats != nullptr;
+    if (timed && !c->sev_ready) {
+        for (int q = 0; q < 3; ++q)
+            for (int r = 0; r < 64; ++r) SMP_CUDA(cudaEventCreate(&c->sev[q][r]), "event create");
+        c->sev_ready = true;
+    }
+    double ms_prep = 0.0, ms_search = 0.0;
     SMP_CUDA(cudaEventRecord(c->ev0, s), "event");
-    for (int it = 0; it < sc->iters; ++it) {
-        const int step = sc->step0 + it;
-        launch_draw_samples(field, d, (const uint32_t*)c->s_hi.p, c->s_nh, (const uint32_t*)c->s_mid.p, c->s_nm, S,
-                            split[0], split[1], seed, (uint32_t)step, b.pts, nullptr, s);
-        SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ, trace, it, nullptr, true, s));
-        if (n > 0) {
-            AdamArgs ad{};
-            ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
-            ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step + 1));
-            ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step + 1));
-            launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s);
+    for (int it0 = 0; it0 < sc->iters; it0 += 64) {
+        const int end = it0 + 64 < sc->iters ? it0 + 64 : sc->iters;
+        for (int it = it0; it < end; ++it) {
+            const int step = sc->step0 + it;
+            if (timed) SMP_CUDA(cudaEventRecord(c->sev[0][it - it0], s), "event");
+            launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
+            if (timed) SMP_CUDA(cudaEventRecord(c->sev[1][it - it0], s), "event");
+            launch_draw_samples(field, d, (const uint32_t*)c->s_hi.p, c->s_nh, (const uint32_t*)c->s_mid.p, c->s_nm,
+                                S, split[0], split[1], seed, (uint32_t)step, b.pts, nullptr, s);
+            SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ, trace, it, nullptr, true, s));
+            if (timed) SMP_CUDA(cudaEventRecord(c->sev[2][it - it0], s), "event");
+            if (n > 0) {
+                AdamArgs ad{};
+                ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
+                ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step + 1));
+                ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step + 1));
+                launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s);
+                c->launches += 2;
+            }
             c->launches += 1;
         }
-        c->launches += 1;
+        if (timed) {
+            SMP_CUDA(cudaEventSynchronize(c->sev[2][end - 1 - it0]), "sync");
+            for (int it = it0; it < end; ++it) {
+                float x = 0.f, y = 0.f;
+                cudaEventElapsedTime(&x, c->sev[0][it - it0], c->sev[1][it - it0]);
+                cudaEventElapsedTime(&y, c->sev[1][it - it0], c->sev[2][it - it0]);
+                ms_prep += x;
+                ms_search += y;
+            }
+        }
     }
     SMP_CUDA(cudaEventRecord(c->ev1, s), "event");
     SMP_CUDA(cudaGetLastError(), "launch (sampled refine)");
@@ -545,8 +571,8 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
         stats->iters_done = sc->iters;
         stats->retries = 0;
         stats->ms_total = ms_loop;
-        stats->ms_brick = ms_loop;
-        stats->ms_bin = 0.f;
+        stats->ms_brick = (float)ms_search;
+        stats->ms_bin = (float)ms_prep;
         stats->launches = launches + c->launches;
     }
     return GVE_OK;

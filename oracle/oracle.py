@@ -306,6 +306,43 @@ def kept_submasks(p32, dims, keys, gids, k=3.0, B=8) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Pre-encoding structure statistics (Sec. V-F, Table VI)
+# --------------------------------------------------------------------------
+def structure_function(field, lag: int) -> float:
+    """S(lag): mean over the grid axes (those longer than lag) of the mean
+    squared difference (V(x + lag e_a) - V(x))^2 over all voxel pairs."""
+    V = np.asarray(field, np.float64)
+    vals = []
+    for axis in (2, 1, 0):              # x, y, z of a [nz][ny][nx] array
+        n = V.shape[axis]
+        if n <= lag:
+            continue
+        a = np.take(V, np.arange(lag, n), axis=axis)
+        b = np.take(V, np.arange(0, n - lag), axis=axis)
+        vals.append(float(np.mean((a - b) ** 2)))
+    return float(np.mean(vals)) if vals else 0.0
+
+
+def structure_stats(field, occ_thresh=0.02, top_frac=0.1):
+    """Table VI statistics: occupancy (V > 0.02), the share of the occupied
+    voxels' gradient-magnitude mass held by the ceil(0.1 n_occ) largest, and
+    S(1) / S(16) of the second-order structure function."""
+    f = _f32c(field)
+    occ = f > np.float32(occ_thresh)
+    n_occ = int(occ.sum())
+    g = grad_mag32(f)[occ].astype(np.float64)
+    tot = float(g.sum())
+    if n_occ and tot > 0:
+        K = int(np.ceil(top_frac * n_occ))
+        top = float(np.sort(g)[n_occ - K:].sum()) / tot
+    else:
+        top = 0.0
+    s1, s16 = structure_function(f, 1), structure_function(f, 16)
+    return {"occupancy": n_occ / f.size, "grad_top10": top, "S1": s1, "S16": s16,
+            "S1_over_S16": s1 / s16 if s16 > 0 else 0.0}
+
+
+# --------------------------------------------------------------------------
 # Stratified-sample refinement (Sec. III-F; Table III: 3,072 points per
 # iteration, 35 / 40 / 25 %)
 # --------------------------------------------------------------------------

@@ -871,3 +871,58 @@ def test_sample_loss_gradient_central_differences():
             fd = (O.sample_loss_grad(pp, pts, vals, k=20.0, want_grad=False)[0]
                   - O.sample_loss_grad(pm, pts, vals, k=20.0, want_grad=False)[0]) / (2 * h)
             assert abs(fd - g[i, j]) <= 1e-5 * max(abs(fd), 1e-4), (i, j, fd, g[i, j])
+
+
+# ---------------------------------------------------------------------------
+# Pre-encoding structure statistics (Sec. V-F, Table VI)
+# ---------------------------------------------------------------------------
+def test_structure_stats_linear_ramp_closed_form():
+    """V = 0.1 + a x on nx x ny x nz: every voxel occupied, |grad V| = a at
+    every voxel (one-sided differences are exact on a ramp), so the top 10 %
+    hold exactly ceil(0.1 M) / M of the mass; S(l) = a^2 l^2 along x and 0
+    along y, z, so S(1) / S(16) = 1 / 256."""
+    nz, ny, nx = 20, 24, 40              # every axis longer than the lag 16
+    a = np.float32(0.02)
+    x = np.arange(nx, dtype=np.float32)
+    V = np.broadcast_to(np.float32(0.1) + a * x, (nz, ny, nx)).astype(np.float32)
+    st = O.structure_stats(V)
+    M = V.size
+    assert st["occupancy"] == 1.0
+    assert abs(st["grad_top10"] - np.ceil(0.1 * M) / M) < 1e-6     # float32 ramp values
+    dx = np.diff(V[0, 0, :].astype(np.float64))
+    s1 = float(np.mean(dx ** 2)) / 3.0
+    np.testing.assert_allclose(st["S1"], s1, rtol=1e-12)
+    np.testing.assert_allclose(st["S1_over_S16"], 1 / 256, rtol=1e-5)
+
+
+def test_structure_stats_step_and_empty_fields():
+    """A single plane jump: the gradient mass sits on the two planes beside
+    the jump; a constant field has no gradient mass and no structure."""
+    V = np.zeros((20, 20, 20), np.float32) + 0.5
+    V[:, :, 10:] = 0.9
+    st = O.structure_stats(V)
+    # central differences: |grad| = 0.2 on the planes x = 9, 10, zero elsewhere:
+    # 800 voxels hold all of the mass, the top 10 % (800 voxels) hold all of it
+    assert abs(st["grad_top10"] - 1.0) < 1e-12
+    # at lag l, min(l, 20 - l) of the 20 - l pairs of each x row cross the
+    # jump (y, z rows never do): S(l) = min(l, 20 - l) / (20 - l) d^2 / 3 with
+    # d = 0.9 - 0.5 in float32; at l = 16 all 4 pairs cross
+    d2 = float(np.float32(0.9) - np.float32(0.5)) ** 2
+    np.testing.assert_allclose(st["S1"], d2 / 19 / 3, rtol=1e-12)
+    np.testing.assert_allclose(st["S16"], d2 / 3, rtol=1e-12)
+    np.testing.assert_allclose(st["S1_over_S16"], 1 / 19, rtol=1e-12)
+    C = np.full((8, 8, 8), 0.3, np.float32)
+    sc = O.structure_stats(C)
+    assert sc["grad_top10"] == 0.0 and sc["S1"] == 0.0 and sc["S1_over_S16"] == 0.0
+    Z = np.zeros((8, 8, 8), np.float32)
+    assert O.structure_stats(Z)["occupancy"] == 0.0
+
+
+def test_structure_function_kolmogorov_scaling():
+    """A random field with shell spectrum E(k) ~ k^-5/3 has S(l) ~ l^(2/3) in
+    the inertial range, so S(1)/S(16) lies near 16^(-2/3) = 0.157 (the range
+    of the paper's Table VI)."""
+    from paper_2608_14112_b300 import inputs
+    V = inputs.grf(96, seed=3)
+    r = O.structure_stats(V)["S1_over_S16"]
+    assert 0.08 < r < 0.3

@@ -323,17 +323,18 @@ def structure_function(field, lag: int) -> float:
     return float(np.mean(vals)) if vals else 0.0
 
 
-def structure_stats(field, occ_thresh=0.02, top_frac=0.1):
+def structure_stats(field, occ_thresh=0.02):
     """Table VI statistics: occupancy (V > 0.02), the share of the occupied
-    voxels' gradient-magnitude mass held by the ceil(0.1 n_occ) largest, and
-    S(1) / S(16) of the second-order structure function."""
+    voxels' gradient-magnitude mass held by the ceil(n_occ / 10) largest
+    (integer ceiling), and S(1) / S(16) of the second-order structure
+    function."""
     f = _f32c(field)
     occ = f > np.float32(occ_thresh)
     n_occ = int(occ.sum())
     g = grad_mag32(f)[occ].astype(np.float64)
     tot = float(g.sum())
     if n_occ and tot > 0:
-        K = int(np.ceil(top_frac * n_occ))
+        K = -(-n_occ // 10)
         top = float(np.sort(g)[n_occ - K:].sum()) / tot
     else:
         top = 0.0

@@ -792,4 +792,107 @@ void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigne
     k_draw_samples<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(a);
 }
 
+// ------------------------------------------------------------------------
+// Pre-encoding structure statistics (Sec. V-F, Table VI): occupancy, the
+// share of the occupied voxels' gradient-magnitude mass held by the largest
+// ceil(n_occ / 10), and S(1) / S(16) of the second-order structure function
+// S(l) = mean over the axes longer than l of the mean (V(x + l e) - V(x))^2.
+// ------------------------------------------------------------------------
+namespace {
+
+// FP64 sums: [0] occupied gradient mass, [1] mass above the threshold bits,
+// [2..4] S(1) per axis, [5..7] S(16) per axis; cnt = voxels above the threshold
+__global__ void __launch_bounds__(256) k_struct(const float* __restrict__ V, const float* __restrict__ g, int nx,
+                                                int ny, int nz, float thr, uint32_t tbits, double* __restrict__ out,
+                                                unsigned long long* __restrict__ cnt)
+{
+    const long long M = (long long)nx * ny * nz;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long nt = 0;
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / sz);
+        const float val = V[v];
+        if (val > thr) {
+            const float gv = g[v];
+            acc[0] += (double)gv;
+            if (__float_as_uint(gv) > tbits) { acc[1] += (double)gv; ++nt; }
+        }
+#pragma unroll
+        for (int li = 0; li < 2; ++li) {
+            const int L = li ? 16 : 1;
+            if (x + L < nx) { const double d = (double)V[v + L] - (double)val; acc[2 + 3 * li] += d * d; }
+            if (y + L < ny) { const double d = (double)V[v + L * sy] - (double)val; acc[3 + 3 * li] += d * d; }
+            if (z + L < nz) { const double d = (double)V[v + L * sz] - (double)val; acc[4 + 3 * li] += d * d; }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    for (int o = 16; o > 0; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) atomicAdd(out + k, acc[k]);
+        atomicAdd(cnt, nt);
+    }
+}
+
+}  // namespace
+
+gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5], cudaStream_t s)
+{
+    const long long M = (long long)d.nx * d.ny * d.nz;
+    const float thr = 0.02f;
+    gve_status st;
+    if ((st = ensure(c, c->a_g, sizeof(float) * M, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->a_keys, sizeof(uint32_t) * M, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, s)) != GVE_OK) return st;
+    if ((st = ensure(c, c->a_cnt, sizeof(double) * 8 + sizeof(unsigned long long) * 4, s)) != GVE_OK) return st;
+    float* g = (float*)c->a_g.p;
+    double* sums = (double*)c->a_cnt.p;
+    unsigned long long* cnt = (unsigned long long*)(sums + 8);
+    cudaError_t e = cudaMemsetAsync(c->a_cnt.p, 0, sizeof(double) * 8 + sizeof(unsigned long long) * 4, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset sums");
+    k_grad_occ<<<grid_for(M), 256, 0, s>>>(V, d.nx, d.ny, d.nz, thr, g, cnt + 1);
+    unsigned long long hc[3] = {0, 0, 0};
+    e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    const long long n_occ = (long long)hc[1];
+    const long long K = (n_occ + 9) / 10;
+    uint32_t tbits = 0xFFFFFFFFu;
+    if (n_occ > 0) {
+        uint32_t* k32 = (uint32_t*)c->a_keys.p;
+        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, 0, 2, nullptr, k32);
+        if ((st = radix_select<uint32_t>(c, k32, M, (unsigned long long)(n_occ - K), &tbits, s)) != GVE_OK) return st;
+    }
+    k_struct<<<grid_for(M), 256, 0, s>>>(V, g, d.nx, d.ny, d.nz, thr, tbits, sums, cnt);
+    double hs[8];
+    unsigned long long nt = 0;
+    e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nt, cnt, sizeof(nt), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "structure sums");
+    float T;
+    memcpy(&T, &tbits, sizeof(float));
+    out[0] = (double)n_occ / (double)M;
+    out[1] = (n_occ > 0 && hs[0] > 0.0) ? (hs[1] + (double)(K - (long long)nt) * (double)T) / hs[0] : 0.0;
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    for (int li = 0; li < 2; ++li) {
+        const int L = li ? 16 : 1;
+        double sum = 0.0;
+        int axes = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (dims[a] <= L) continue;
+            const double pairs = (double)(dims[a] - L) * (double)(M / dims[a]);
+            sum += hs[2 + 3 * li + a] / pairs;
+            ++axes;
+        }
+        out[2 + li] = axes ? sum / axes : 0.0;
+    }
+    out[4] = out[3] > 0.0 ? out[2] / out[3] : 0.0;
+    c->launches += n_occ > 0 ? 7 : 2;
+    return GVE_OK;
+}
+
 }  // namespace gve

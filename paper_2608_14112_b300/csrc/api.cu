@@ -566,6 +566,17 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
     return GVE_OK;
 }
 
+gve_status gve_structure_stats(gve_ctx* c, const float* field, gve_dims d, double* out, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!field || !out) return fail(c, GVE_E_INVALID, "null argument");
+    if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
+    if (d.nx > (1 << 24) || d.ny > (1 << 24) || d.nz > (1 << 24)) return fail(c, GVE_E_INVALID, "grid axis above 2^24");
+    GVE_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    c->launches = 0;
+    return gve::structure_stats(c, field, d, out, (cudaStream_t)stream);
+}
+
 gve_status gve_allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget, const gve_alloc_opts* o,
                         float* prims, int64_t* feasible_max, gve_alloc_info* info, void* stream)
 {

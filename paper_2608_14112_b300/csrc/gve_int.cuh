@@ -197,6 +197,11 @@ void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigne
                          unsigned long long nm, long long S, long long s_hi, long long s_mid,
                          unsigned long long seed, uint32_t iter, float4* pts, long long* vox, cudaStream_t s);
 
+// ---- pre-encoding structure statistics (alloc.cu) --------------------------
+// out = {occupancy, top-10 % gradient-mass share, S(1), S(16), S(1)/S(16)};
+// synchronises `s`
+gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5], cudaStream_t s);
+
 // ---- context scratch and the evaluation pipeline (api.cu) ----------------
 gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
 gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what);

@@ -107,6 +107,8 @@ def lib():
             L.gve_loss_grad.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(EvalOpts), ctypes.c_float, P, P, P]
             L.gve_backward.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P]
             L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
+            L.gve_structure_stats.argtypes = [P, P, Dims, P, P]
+            L.gve_structure_stats.restype = st
             L.gve_draw_samples.argtypes = [P, P, Dims, i64, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
             L.gve_draw_samples.restype = st
             L.gve_sample_loss_grad.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, i64, ctypes.c_float,
@@ -251,6 +253,17 @@ def gve_refine(prims: torch.Tensor, field: torch.Tensor, iters: int, lr: float =
     if not want_stats:
         return None
     return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def gve_structure_stats(field: torch.Tensor) -> dict:
+    """Table VI statistics of a field: occupancy, top-10 % gradient-mass
+    share, S(1), S(16) and their ratio."""
+    field = _field(field)
+    out = (ctypes.c_double * 5)()
+    c = context(field.device.index)
+    _check(lib().gve_structure_stats(c, _ptr(field), _dims(field.shape), ctypes.cast(out, ctypes.c_void_p),
+                                     _stream(field.device)), c)
+    return dict(zip(("occupancy", "grad_top10", "S1", "S16", "S1_over_S16"), list(out)))
 
 
 def gve_draw_samples(field: torch.Tensor, S: int, seed: int, it: int, want_voxels: bool = False):

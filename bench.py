@@ -52,9 +52,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headline", "mid", "small", "autograd", "batched", "proposal", "sampled"],
+    ap.add_argument("--workload", choices=["headline", "mid", "small", "autograd", "batched", "proposal", "sampled",
+                                           "structure"],
                     default="headline")
     ap.add_argument("--samples", type=int, default=3072, help="points per iteration of the sampled workload")
+    ap.add_argument("--struct-n", type=int, default=1024, help="grid edge of the structure workload")
     ap.add_argument("--prop-iters", type=int, default=200, help="refinement iterations per proposal evaluation")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
@@ -206,6 +208,18 @@ def brick_traffic(voxels):
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "structure":
+        sec, desc = structure_cpu_sample(args)
+        value = 1e-9 / sec
+        out = {"metric": STRUCT_METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1024 ** 3 * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "impl": "reference", "config": {"workload": STRUCT_WORKLOAD, "l2": "CPU run"},
+               "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": desc},
+               "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
         return
     w = workload(args.workload)
     for _ in range(args.warmup):
@@ -496,6 +510,99 @@ def run_sampled(args):
     print(json.dumps(out), flush=True)
 
 
+STRUCT_METRIC = "pre-encoding structure statistics (occupancy, top-10% gradient mass, S(1)/S(16)) Gvoxel/s"
+STRUCT_WORKLOAD = "fbm_fronts_1024^3_structure_stats"
+
+
+def structure_cpu_sample(args):
+    """The oracle's statistics on a centre sub-volume of the same field;
+    seconds per voxel and the sample description."""
+    from oracle import oracle as O
+    from paper_2608_14112_b300 import inputs
+    n = getattr(args, "struct_n", 1024)
+    s = min(args.sample, n)
+    c0 = (n - s) // 2
+    V = inputs.fbm_fronts(n, seed=4, as_numpy=True, region=((c0,) * 3, (s,) * 3))
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        O.structure_stats(V)
+    sec = (time.perf_counter() - t0) / reps / V.size
+    return sec, f"{s}^3 centre sub-volume of the same field, {reps} oracle passes; per voxel"
+
+
+def run_structure(args):
+    """Table VI statistics of the headline field (Sec. V-F): both sweeps,
+    the exact top-K select and the host readback, through the C ABI."""
+    import torch
+    from paper_2608_14112_b300 import build as gbuild
+    from paper_2608_14112_b300 import gve, inputs
+
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = args.struct_n
+    V = inputs.fbm_fronts(n, seed=4, device=dev)
+    M = V.numel()
+    for _ in range(max(args.warmup, 0)):
+        res = gve.gve_structure_stats(V)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stages = []
+    for _ in range(args.steps):
+        stages.append(gve.gve_structure_stats(V, want_stage_ms=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = args.steps * M / (ms / 1e3) / 1e9
+    s1 = statistics.mean(r["ms_sweep1"] for r in stages)
+    s2 = statistics.mean(r["ms_sweep2"] for r in stages)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    # each sweep's algorithmic traffic is one read of the float32 field
+    kern, kms = ("k_stat_sweep1", s1) if s1 >= s2 else ("k_stat_sweep2 + select", s2)
+    achieved = 4.0 * M / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": kern, "stage_ms": kms,
+                "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}
+    Vh = V.cpu().pin_memory()
+    Vd = torch.empty_like(V)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        Vd.copy_(Vh, non_blocking=True)
+        gve.gve_structure_stats(Vd)
+    torch.cuda.synchronize()
+    enc = (time.perf_counter() - t0) / args.e2e_steps
+    e2e = {"value": M / enc / 1e9, "unit": "Gvoxel/s", "h2d_bytes_per_step": int(M * 4),
+           "d2h_bytes_per_step": 5 * 8, "includes": "H2D field from pinned memory, both sweeps, results to host"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        sec, desc = structure_cpu_sample(args)
+        cpu = {"value": 1e-9 / sec, "unit": "Gvoxel/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+    last = stages[-1]
+    out = {"metric": STRUCT_METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 field, f64 sums", "data": "synthetic",
+           "config": {"workload": STRUCT_WORKLOAD.replace("1024", str(n)), "voxels": int(M),
+                      "l2": f"{4 * M / 1e9:.2f} GB field" + (" larger than L2; no flush needed" if 4 * M > 126e6
+                                                             else " fits in L2")},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+           "gpu_launches": int(sum(r["launches"] for r in stages)),
+           "stage_ms_per_pass": {"sweep1": s1, "sweep2_select": s2},
+           "stats": {k: last[k] for k in ("occupancy", "grad_top10", "S1", "S16", "S1_over_S16")}}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -632,6 +739,8 @@ def main():
         run_proposal(args)
     elif args.workload == "sampled":
         run_sampled(args)
+    elif args.workload == "structure":
+        run_structure(args)
     else:
         run_ours(args)
 

@@ -289,15 +289,20 @@ GVE_API gve_status gve_proposal_backward(gve_ctx* ctx, const float* model_dev, c
                                          int64_t n, gve_dims dims, int32_t accumulate, float* dP_dev,
                                          void* stream);
 
-/* Pre-encoding structure statistics (Sec. V-F, Table VI), host output
+/* Pre-encoding structure statistics (Sec. V-F, Table VI) of a device field
+ * (float32, [nz][ny][nx], device memory, not modified).  Host output
  * out[5] = {occupancy (V > 0.02), share of the occupied voxels' float32
  * |grad V| mass held by the ceil(n_occ / 10) largest, S(1), S(16),
  * S(1) / S(16)} with S(l) the mean over the axes longer than l of the mean
  * (V(x + l e) - V(x))^2 over all voxel pairs (FP64).  The paper names but
  * does not define S; this second-order structure function is the reading.
- * Synchronises `stream`. */
+ * stage_ms (host, nullable, [4]) receives the device time in ms of the
+ * first sweep, of the second sweep with the exact select and of the whole
+ * pass, then the number of kernels the call launched.
+ * Two sweeps of the field, no per-voxel scratch; synchronises `stream`.
+ * GVE_E_INVALID on null pointers, non-positive sizes or an axis above 2^24. */
 GVE_API gve_status gve_structure_stats(gve_ctx* ctx, const float* field_dev, gve_dims dims, double* out,
-                                       void* stream);
+                                       double* stage_ms, void* stream);
 
 /* ---- stratified-sample refinement (Sec. III-F, Table III) ------------------
  * The paper's training regime: each iteration fits the field at S jittered

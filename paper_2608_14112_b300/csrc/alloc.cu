@@ -77,6 +77,18 @@ __device__ __forceinline__ float dcomp32(const float* V, int nx, int ny, int nz,
     return scale * diff;
 }
 
+// float32 |grad V|: squares summed x, y, then z, no contraction
+__device__ __forceinline__ float grad_mag(const float* V, int nx, int ny, int nz, int x, int y, int z)
+{
+    const float gx = dcomp32(V, nx, ny, nz, x, y, z, 0);
+    const float gy = dcomp32(V, nx, ny, nz, x, y, z, 1);
+    const float gz = dcomp32(V, nx, ny, nz, x, y, z, 2);
+    const float sx = gx * gx, sy = gy * gy, sz = gz * gz;
+    float sq = sx + sy;
+    sq = sq + sz;
+    return sqrtf(sq);
+}
+
 __global__ void __launch_bounds__(256) k_grad_occ(const float* __restrict__ V, int nx, int ny, int nz, float thr,
                                                   float* __restrict__ g, unsigned long long* cnt)
 {
@@ -84,13 +96,7 @@ __global__ void __launch_bounds__(256) k_grad_occ(const float* __restrict__ V, i
     unsigned occ = 0, elig = 0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x) {
         int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-        float gx = dcomp32(V, nx, ny, nz, x, y, z, 0);
-        float gy = dcomp32(V, nx, ny, nz, x, y, z, 1);
-        float gz = dcomp32(V, nx, ny, nz, x, y, z, 2);
-        float sx = gx * gx, sy = gy * gy, sz = gz * gz;
-        float sq = sx + sy;
-        sq = sq + sz;
-        float gm = sqrtf(sq);
+        const float gm = grad_mag(V, nx, ny, nz, x, y, z);
         g[v] = gm;
         if (V[v] > thr) { ++occ; if (gm > 0.0f) ++elig; }
     }
@@ -795,88 +801,370 @@ void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigne
 // ------------------------------------------------------------------------
 // Pre-encoding structure statistics (Sec. V-F, Table VI): occupancy, the
 // share of the occupied voxels' gradient-magnitude mass held by the largest
-// ceil(n_occ / 10), and S(1) / S(16) of the second-order structure function
-// S(l) = mean over the axes longer than l of the mean (V(x + l e) - V(x))^2.
+// K = ceil(n_occ / 10), and S(1) / S(16) of the second-order structure
+// function S(l) = mean over the axes longer than l of the mean
+// (V(x + l e) - V(x))^2.
+//
+// Two sweeps of the field and no per-voxel scratch.  Sweep 1 takes the
+// occupancy, the FP64 gradient mass, the structure-function sums and a
+// 4096-bin histogram of the gradient bits (sign 0, 8 exponent and 4
+// mantissa bits: float order).  The host walks the histogram down to the bin
+// b* that holds the K-th largest.  Sweep 2 recomputes the same gradients,
+// sums the mass of the bins above b* and compacts the bits of bin b*; an
+// exact radix select over those candidates and one sum finish the top-K mass.
 // ------------------------------------------------------------------------
 namespace {
 
-// FP64 sums: [0] occupied gradient mass, [1] mass above the threshold bits,
-// [2..4] S(1) per axis, [5..7] S(16) per axis; cnt = voxels above the threshold
-__global__ void __launch_bounds__(256) k_struct(const float* __restrict__ V, const float* __restrict__ g, int nx,
-                                                int ny, int nz, float thr, uint32_t tbits, double* __restrict__ out,
-                                                unsigned long long* __restrict__ cnt)
+constexpr int kStatShift = 19;
+constexpr int kStatBins = 4096;
+constexpr int kStatTileRows = 256;
+// scratch: doubles [0] gradient mass, [1..3] S(1) per axis, [4..6] S(16) per
+// axis, [7] mass above b*, [8] candidate mass above the select threshold;
+// counts [0] occupied, [1] candidates, [2] candidates above the threshold;
+// then the 4096-bin histogram
+constexpr int kStatDoubles = 10;
+constexpr int kStatCounts = 4;
+
+// compensated float32 sum (Kahan); the file is compiled without contraction
+// or reassociation, so the compensation survives
+struct KSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ unsigned stat_bin(float gm)
 {
-    const long long M = (long long)nx * ny * nz;
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long nt = 0;
-    const long long sy = nx, sz = (long long)nx * ny;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / sz);
-        const float val = V[v];
-        if (val > thr) {
-            const float gv = g[v];
-            acc[0] += (double)gv;
-            if (__float_as_uint(gv) > tbits) { acc[1] += (double)gv; ++nt; }
-        }
+    return min(__float_as_uint(gm) >> kStatShift, (unsigned)(kStatBins - 1));
+}
+
+__device__ __forceinline__ double warp_sum_d(double a)
+{
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// Sweep order: the grid is cut into tiles of whole x rows and `ty` y rows;
+// each tile is walked slab by slab in z, one x row per warp at a time in
+// 32-voxel chunks.  The resident warps then cover a few consecutive slabs of
+// one tile, so the z +- 1 and z + 16 neighbours are still in L2.
+struct StatGrid {
+    const float* V;
+    int nx, ny, nz, ty;
+    long long rows_tile, nrows;
+};
+
+// one x row: its start and the row-uniform border facts
+struct Row {
+    long long base;
+    int y, z;
+    bool ylo, yhi, zlo, zhi, y16, z16;
+};
+
+__device__ __forceinline__ bool decode_row(const StatGrid& g, long long row, Row& r)
+{
+    const long long t = row / g.rows_tile;
+    const long long rr = row - t * g.rows_tile;
+    r.z = (int)(rr / g.ty);
+    r.y = (int)(t * g.ty) + (int)(rr - (long long)r.z * g.ty);
+    if (r.y >= g.ny) return false;
+    r.base = ((long long)r.z * g.ny + r.y) * g.nx;
+    r.ylo = r.y > 0; r.yhi = r.y + 1 < g.ny; r.y16 = r.y + 16 < g.ny;
+    r.zlo = r.z > 0; r.zhi = r.z + 1 < g.nz; r.z16 = r.z + 16 < g.nz;
+    return true;
+}
+
+// One 32-voxel chunk of a row: the lane's value, its neighbours and (with
+// S16) the values 16 voxels further along each axis.  All loads of a batch
+// of chunks are issued before any is used, so a warp keeps several DRAM
+// lines in flight.
+template <bool S16>
+struct Vals {
+    float c, xm, xp, ym, yp, zm, zp, x16, y16, z16;
+};
+
+template <bool S16>
+__device__ __forceinline__ void load_chunk(const StatGrid& g, const Row& r, int x, int lane, Vals<S16>& q)
+{
+    const float* V = g.V;
+    const bool ok = x < g.nx;
+    const long long v = r.base + x;
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    q.c = ok ? V[v] : 0.0f;
+    q.xm = (ok && lane == 0 && x > 0) ? V[v - 1] : 0.0f;
+    q.xp = (ok && lane == 31 && x + 1 < g.nx) ? V[v + 1] : 0.0f;
+    q.ym = (ok && r.ylo) ? V[v - sy] : 0.0f;
+    q.yp = (ok && r.yhi) ? V[v + sy] : 0.0f;
+    q.zm = (ok && r.zlo) ? V[v - sz] : 0.0f;
+    q.zp = (ok && r.zhi) ? V[v + sz] : 0.0f;
+    if (S16) {
+        q.x16 = (ok && x + 16 < g.nx) ? V[v + 16] : 0.0f;
+        q.y16 = (ok && r.y16) ? V[v + 16 * sy] : 0.0f;
+        q.z16 = (ok && r.z16) ? V[v + 16 * sz] : 0.0f;
+    }
+}
+
+// float32 |grad V| of the chunk voxel (all lanes call: shuffles), the same
+// operations as grad_mag: one-sided differences at the borders, squares
+// summed x, y, then z.  Leaves xp, yp, zp holding the +1 neighbours where
+// they exist.
+template <bool S16>
+__device__ __forceinline__ float chunk_grad(const StatGrid& g, const Row& r, int x, int lane, Vals<S16>& q)
+{
+    const float c = q.c;
+    const float um = __shfl_up_sync(0xffffffffu, c, 1);
+    const float dn = __shfl_down_sync(0xffffffffu, c, 1);
+    if (lane != 0) q.xm = um;
+    if (lane != 31) q.xp = dn;
+    if (x >= g.nx) return 0.0f;
+    const bool xlo = x > 0, xhi = x + 1 < g.nx;
+    const float lx = xlo ? q.xm : c, hx = xhi ? q.xp : c;
+    const float ly = r.ylo ? q.ym : c, hy = r.yhi ? q.yp : c;
+    const float lz = r.zlo ? q.zm : c, hz = r.zhi ? q.zp : c;
+    const float gx = g.nx < 2 ? 0.0f : ((xlo && xhi) ? 0.5f : 1.0f) * (hx - lx);
+    const float gy = g.ny < 2 ? 0.0f : ((r.ylo && r.yhi) ? 0.5f : 1.0f) * (hy - ly);
+    const float gz = g.nz < 2 ? 0.0f : ((r.zlo && r.zhi) ? 0.5f : 1.0f) * (hz - lz);
+    const float sx = gx * gx, s2 = gy * gy, s3 = gz * gz;
+    float sq = sx + s2;
+    sq = sq + s3;
+    return sqrtf(sq);
+}
+
+constexpr int kBatch1 = 4;
+constexpr int kBatch2 = 8;
+
+__global__ void __launch_bounds__(256) k_stat_sweep1(StatGrid g, float thr, double* __restrict__ sums,
+                                                     unsigned long long* __restrict__ cnt,
+                                                     unsigned long long* __restrict__ hist)
+{
+    __shared__ unsigned h[kStatBins];
+    for (int i = threadIdx.x; i < kStatBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    KSum acc[7];
+    unsigned long long occ = 0;
+    for (long long row = w0; row < g.nrows; row += nw) {
+        Row r;
+        if (!decode_row(g, row, r)) continue;
+        for (int x0 = 0; x0 < g.nx; x0 += 32 * kBatch1) {
+            Vals<true> q[kBatch1];
 #pragma unroll
-        for (int li = 0; li < 2; ++li) {
-            const int L = li ? 16 : 1;
-            if (x + L < nx) { const double d = (double)V[v + L] - (double)val; acc[2 + 3 * li] += d * d; }
-            if (y + L < ny) { const double d = (double)V[v + L * sy] - (double)val; acc[3 + 3 * li] += d * d; }
-            if (z + L < nz) { const double d = (double)V[v + L * sz] - (double)val; acc[4 + 3 * li] += d * d; }
+            for (int u = 0; u < kBatch1; ++u) load_chunk<true>(g, r, x0 + 32 * u + lane, lane, q[u]);
+#pragma unroll
+            for (int u = 0; u < kBatch1; ++u) {
+                const int x = x0 + 32 * u + lane;
+                const float gm = chunk_grad<true>(g, r, x, lane, q[u]);
+                const float c = q[u].c;
+                unsigned bin = 0xFFFFFFFFu;
+                if (x < g.nx) {
+                    if (c > thr) {
+                        acc[0].add(gm);
+                        ++occ;
+                        bin = stat_bin(gm);
+                    }
+                    if (x + 1 < g.nx) { const float d = q[u].xp - c; acc[1].add(d * d); }
+                    if (r.yhi) { const float d = q[u].yp - c; acc[2].add(d * d); }
+                    if (r.zhi) { const float d = q[u].zp - c; acc[3].add(d * d); }
+                    if (x + 16 < g.nx) { const float d = q[u].x16 - c; acc[4].add(d * d); }
+                    if (r.y16) { const float d = q[u].y16 - c; acc[5].add(d * d); }
+                    if (r.z16) { const float d = q[u].z16 - c; acc[6].add(d * d); }
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+            }
         }
     }
+    for (int o = 16; o > 0; o >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, o);
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    for (int k = 0; k < 7; ++k) {
+        const double t = warp_sum_d(acc[k].value());
+        if (lane == 0) atomicAdd(sums + k, t);
+    }
+    if (lane == 0) atomicAdd(cnt, occ);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kStatBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+__global__ void __launch_bounds__(256) k_stat_sweep2(StatGrid g, float thr, unsigned bstar, double* __restrict__ sums,
+                                                     unsigned long long* __restrict__ cnt, uint32_t* __restrict__ cand,
+                                                     unsigned long long cap)
+{
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    KSum above;
+    for (long long row = w0; row < g.nrows; row += nw) {
+        Row r;
+        if (!decode_row(g, row, r)) continue;
+        for (int x0 = 0; x0 < g.nx; x0 += 32 * kBatch2) {
+            Vals<false> q[kBatch2];
+#pragma unroll
+            for (int u = 0; u < kBatch2; ++u) load_chunk<false>(g, r, x0 + 32 * u + lane, lane, q[u]);
+#pragma unroll
+            for (int u = 0; u < kBatch2; ++u) {
+                const int x = x0 + 32 * u + lane;
+                const float gm = chunk_grad<false>(g, r, x, lane, q[u]);
+                bool take = false;
+                if (x < g.nx && q[u].c > thr) {
+                    const unsigned b = stat_bin(gm);
+                    if (b > bstar) above.add(gm);
+                    take = b == bstar;
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, take);
+                if (ball) {
+                    unsigned long long off = 0;
+                    if (lane == 0) off = atomicAdd(cnt + 1, (unsigned long long)__popc(ball));
+                    off = __shfl_sync(0xffffffffu, off, 0);
+                    if (take) {
+                        const unsigned long long i = off + (unsigned long long)__popc(ball & ((1u << lane) - 1u));
+                        if (i < cap) cand[i] = __float_as_uint(gm);
+                    }
+                }
+            }
+        }
+    }
+    const double t = warp_sum_d(above.value());
+    if (lane == 0) atomicAdd(sums + 7, t);
+}
+
+// candidate mass strictly above the select threshold, and its count
+__global__ void __launch_bounds__(256) k_stat_tail(const uint32_t* __restrict__ cand, long long n, uint32_t tbits,
+                                                   double* __restrict__ sums, unsigned long long* __restrict__ cnt)
+{
+    double s = 0.0;
+    unsigned long long nt = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t b = cand[i];
+        if (b > tbits) { s += (double)__uint_as_float(b); ++nt; }
+    }
+    s = warp_sum_d(s);
     for (int o = 16; o > 0; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
     if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) atomicAdd(out + k, acc[k]);
-        atomicAdd(cnt, nt);
+        atomicAdd(sums + 8, s);
+        atomicAdd(cnt + 2, nt);
     }
+}
+
+StatGrid stat_grid(const float* V, gve_dims d)
+{
+    StatGrid g;
+    g.V = V;
+    g.nx = d.nx; g.ny = d.ny; g.nz = d.nz;
+    const int nty = (d.ny + kStatTileRows - 1) / kStatTileRows;
+    g.ty = (d.ny + nty - 1) / nty;
+    g.rows_tile = (long long)d.nz * g.ty;
+    g.nrows = g.rows_tile * nty;
+    return g;
+}
+
+// persistent grid: the resident blocks, no more than the segments need
+template <typename Kern>
+int stat_blocks(Kern k, long long nrows)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    long long b = 148LL * per_sm;
+    const long long need = (nrows + 7) / 8;
+    if (b > need) b = need;
+    return (int)(b < 1 ? 1 : b);
 }
 
 }  // namespace
 
-gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5], cudaStream_t s)
+namespace {
+
+// optional stage events: [0] start, [1] after sweep 1, [2] end
+struct StatEvents {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool on = false;
+    explicit StatEvents(bool want)
+    {
+        if (!want) return;
+        on = true;
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) on = false;
+    }
+    void mark(int i, cudaStream_t s)
+    {
+        if (on) cudaEventRecord(ev[i], s);
+    }
+    ~StatEvents()
+    {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5], double* stage_ms, cudaStream_t s)
 {
     const long long M = (long long)d.nx * d.ny * d.nz;
     const float thr = 0.02f;
+    StatEvents ev(stage_ms != nullptr);
+    const size_t scratch = sizeof(double) * kStatDoubles + sizeof(unsigned long long) * (kStatCounts + kStatBins);
     gve_status st;
-    if ((st = ensure(c, c->a_g, sizeof(float) * M, s)) != GVE_OK) return st;
-    if ((st = ensure(c, c->a_keys, sizeof(uint32_t) * M, s)) != GVE_OK) return st;
-    if ((st = ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, s)) != GVE_OK) return st;
-    if ((st = ensure(c, c->a_cnt, sizeof(double) * 8 + sizeof(unsigned long long) * 4, s)) != GVE_OK) return st;
-    float* g = (float*)c->a_g.p;
+    if ((st = ensure(c, c->a_cnt, scratch, s)) != GVE_OK) return st;
     double* sums = (double*)c->a_cnt.p;
-    unsigned long long* cnt = (unsigned long long*)(sums + 8);
-    cudaError_t e = cudaMemsetAsync(c->a_cnt.p, 0, sizeof(double) * 8 + sizeof(unsigned long long) * 4, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "memset sums");
-    k_grad_occ<<<grid_for(M), 256, 0, s>>>(V, d.nx, d.ny, d.nz, thr, g, cnt + 1);
-    unsigned long long hc[3] = {0, 0, 0};
-    e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    unsigned long long* cnt = (unsigned long long*)(sums + kStatDoubles);
+    unsigned long long* hist = cnt + kStatCounts;
+    cudaError_t e = cudaMemsetAsync(c->a_cnt.p, 0, scratch, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset structure scratch");
+    const StatGrid sg = stat_grid(V, d);
+    ev.mark(0, s);
+    k_stat_sweep1<<<stat_blocks(k_stat_sweep1, sg.nrows), 256, 0, s>>>(sg, thr, sums, cnt, hist);
+    ev.mark(1, s);
+    c->launches += 1;
+    std::vector<unsigned long long> hh(kStatCounts + kStatBins);
+    double hs[kStatDoubles];
+    e = cudaMemcpyAsync(hh.data(), cnt, sizeof(unsigned long long) * hh.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
-    const long long n_occ = (long long)hc[1];
+    if (e != cudaSuccess) return cuda_fail(c, e, "structure sweep 1");
+    const long long n_occ = (long long)hh[0];
     const long long K = (n_occ + 9) / 10;
-    uint32_t tbits = 0xFFFFFFFFu;
-    if (n_occ > 0) {
-        uint32_t* k32 = (uint32_t*)c->a_keys.p;
-        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, 0, 2, nullptr, k32);
-        if ((st = radix_select<uint32_t>(c, k32, M, (unsigned long long)(n_occ - K), &tbits, s)) != GVE_OK) return st;
+    double top = 0.0;
+    if (n_occ > 0 && hs[0] > 0.0) {
+        // bin b* holding the K-th largest; r of its members belong to the top K
+        const unsigned long long* hb = hh.data() + kStatCounts;
+        unsigned long long above_n = 0;
+        int bstar = kStatBins - 1;
+        for (; bstar >= 0; --bstar) {
+            if (above_n + hb[bstar] >= (unsigned long long)K) break;
+            above_n += hb[bstar];
+        }
+        if (bstar < 0) { c->err = "structure histogram holds fewer than K voxels"; return GVE_E_INTERNAL; }
+        const unsigned long long nc = hb[bstar];
+        const unsigned long long r = (unsigned long long)K - above_n;
+        if ((st = ensure(c, c->a_keys, sizeof(uint32_t) * nc, s)) != GVE_OK) return st;
+        uint32_t* cand = (uint32_t*)c->a_keys.p;
+        k_stat_sweep2<<<stat_blocks(k_stat_sweep2, sg.nrows), 256, 0, s>>>(sg, thr, (unsigned)bstar, sums, cnt, cand,
+                                                                          nc);
+        uint32_t tbits = 0;
+        if ((st = radix_select<uint32_t>(c, cand, (long long)nc, nc - r, &tbits, s)) != GVE_OK) return st;
+        k_stat_tail<<<grid_for((long long)nc), 256, 0, s>>>(cand, (long long)nc, tbits, sums, cnt);
+        c->launches += 6;
+        unsigned long long hc[3];
+        e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "structure sweep 2");
+        if (hc[1] != nc) { c->err = "structure sweep 2 saw another candidate count"; return GVE_E_INTERNAL; }
+        float T;
+        memcpy(&T, &tbits, sizeof(float));
+        top = (hs[7] + hs[8] + (double)(r - hc[2]) * (double)T) / hs[0];
     }
-    k_struct<<<grid_for(M), 256, 0, s>>>(V, g, d.nx, d.ny, d.nz, thr, tbits, sums, cnt);
-    double hs[8];
-    unsigned long long nt = 0;
-    e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nt, cnt, sizeof(nt), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "structure sums");
-    float T;
-    memcpy(&T, &tbits, sizeof(float));
     out[0] = (double)n_occ / (double)M;
-    out[1] = (n_occ > 0 && hs[0] > 0.0) ? (hs[1] + (double)(K - (long long)nt) * (double)T) / hs[0] : 0.0;
+    out[1] = top;
     const int dims[3] = {d.nx, d.ny, d.nz};
     for (int li = 0; li < 2; ++li) {
         const int L = li ? 16 : 1;
@@ -885,13 +1173,25 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
         for (int a = 0; a < 3; ++a) {
             if (dims[a] <= L) continue;
             const double pairs = (double)(dims[a] - L) * (double)(M / dims[a]);
-            sum += hs[2 + 3 * li + a] / pairs;
+            sum += hs[1 + 3 * li + a] / pairs;
             ++axes;
         }
         out[2 + li] = axes ? sum / axes : 0.0;
     }
     out[4] = out[3] > 0.0 ? out[2] / out[3] : 0.0;
-    c->launches += n_occ > 0 ? 7 : 2;
+    if (stage_ms) {
+        ev.mark(2, s);
+        stage_ms[0] = stage_ms[1] = stage_ms[2] = 0.0;
+        stage_ms[3] = (double)c->launches;
+        if (ev.on && cudaEventSynchronize(ev.ev[2]) == cudaSuccess) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev.ev[0], ev.ev[1]);
+            cudaEventElapsedTime(&b, ev.ev[0], ev.ev[2]);
+            stage_ms[0] = a;
+            stage_ms[1] = (double)b - (double)a;
+            stage_ms[2] = b;
+        }
+    }
     return GVE_OK;
 }
 

@@ -566,7 +566,8 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
     return GVE_OK;
 }
 
-gve_status gve_structure_stats(gve_ctx* c, const float* field, gve_dims d, double* out, void* stream)
+gve_status gve_structure_stats(gve_ctx* c, const float* field, gve_dims d, double* out, double* stage_ms,
+                               void* stream)
 {
     if (!c) return GVE_E_INVALID;
     if (!field || !out) return fail(c, GVE_E_INVALID, "null argument");
@@ -574,7 +575,7 @@ gve_status gve_structure_stats(gve_ctx* c, const float* field, gve_dims d, doubl
     if (d.nx > (1 << 24) || d.ny > (1 << 24) || d.nz > (1 << 24)) return fail(c, GVE_E_INVALID, "grid axis above 2^24");
     GVE_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     c->launches = 0;
-    return gve::structure_stats(c, field, d, out, (cudaStream_t)stream);
+    return gve::structure_stats(c, field, d, out, stage_ms, (cudaStream_t)stream);
 }
 
 gve_status gve_allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget, const gve_alloc_opts* o,

@@ -199,8 +199,10 @@ void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigne
 
 // ---- pre-encoding structure statistics (alloc.cu) --------------------------
 // out = {occupancy, top-10 % gradient-mass share, S(1), S(16), S(1)/S(16)};
-// synchronises `s`
-gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5], cudaStream_t s);
+// stage_ms (nullable) = {sweep 1, sweep 2 + select, whole pass (ms), kernels
+// launched}; synchronises `s`
+gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5], double* stage_ms,
+                           cudaStream_t s);
 
 // ---- context scratch and the evaluation pipeline (api.cu) ----------------
 gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s);

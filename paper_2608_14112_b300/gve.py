@@ -107,7 +107,7 @@ def lib():
             L.gve_loss_grad.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(EvalOpts), ctypes.c_float, P, P, P]
             L.gve_backward.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P]
             L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
-            L.gve_structure_stats.argtypes = [P, P, Dims, P, P]
+            L.gve_structure_stats.argtypes = [P, P, Dims, P, P, P]
             L.gve_structure_stats.restype = st
             L.gve_draw_samples.argtypes = [P, P, Dims, i64, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
             L.gve_draw_samples.restype = st
@@ -255,15 +255,21 @@ def gve_refine(prims: torch.Tensor, field: torch.Tensor, iters: int, lr: float =
     return {name: getattr(st, name) for name, _ in Stats._fields_}
 
 
-def gve_structure_stats(field: torch.Tensor) -> dict:
+def gve_structure_stats(field: torch.Tensor, want_stage_ms: bool = False) -> dict:
     """Table VI statistics of a field: occupancy, top-10 % gradient-mass
-    share, S(1), S(16) and their ratio."""
+    share, S(1), S(16) and their ratio (plus the device time of the two
+    sweeps and of the whole pass when asked)."""
     field = _field(field)
     out = (ctypes.c_double * 5)()
+    ms = (ctypes.c_double * 4)()
     c = context(field.device.index)
     _check(lib().gve_structure_stats(c, _ptr(field), _dims(field.shape), ctypes.cast(out, ctypes.c_void_p),
+                                     ctypes.cast(ms, ctypes.c_void_p) if want_stage_ms else None,
                                      _stream(field.device)), c)
-    return dict(zip(("occupancy", "grad_top10", "S1", "S16", "S1_over_S16"), list(out)))
+    res = dict(zip(("occupancy", "grad_top10", "S1", "S16", "S1_over_S16"), list(out)))
+    if want_stage_ms:
+        res.update(ms_sweep1=ms[0], ms_sweep2=ms[1], ms_total=ms[2], launches=int(ms[3]))
+    return res
 
 
 def gve_draw_samples(field: torch.Tensor, S: int, seed: int, it: int, want_voxels: bool = False):

@@ -1364,3 +1364,188 @@ int or_refine_sampled(double* prm, int64_t n, const float* field, const int dims
     free(hi); free(mid); free(pts); free(vals); free(g); free(m); free(v);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Mixture-field ray marching (Sec. III-A: rendering applies the transfer    */
+/* function T = (c_T, alpha_T) to the value Eq. 3 returns at sample          */
+/* positions and composites them along each ray; grad Vt is available for   */
+/* shading at the sample).                                                   */
+/*                                                                           */
+/* Camera cam[13]: eye (3), right (3), up (3), forward (3), tan(fovy / 2),   */
+/* in voxel coordinates (voxel centres at integers).  The ray through pixel  */
+/* (i, j) (row 0 at the top) and its samples are set up in float32 in one    */
+/* fixed order; values, shading and compositing are FP64.                    */
+/* opt[12]: step, term (stop when the transmittance falls below; 0 = off),   */
+/* ref_step (the spacing the table's opacities hold for), background RGB,    */
+/* shade (0/1), ka, kd, ks, shininess, gfloor.                               */
+/* ------------------------------------------------------------------------ */
+int or_ray_setup(const float* cam, int W, int H, int i, int j, const int dims[3], float d[3], float* tmin,
+                 float* tmax)
+{
+    const float* e = cam;
+    const float *r = cam + 3, *u = cam + 6, *f = cam + 9;
+    const float th = cam[12];
+    const float aspect = (float)W / (float)H;
+    const float sx = ((float)(2 * i + 1) / (float)W - 1.0f) * (th * aspect);
+    const float sy = (1.0f - (float)(2 * j + 1) / (float)H) * th;
+    float dd[3];
+    for (int a = 0; a < 3; ++a) {
+        const float t1 = f[a] + sx * r[a];
+        dd[a] = t1 + sy * u[a];
+    }
+    const float n2a = dd[0] * dd[0] + dd[1] * dd[1];
+    const float n2 = n2a + dd[2] * dd[2];
+    const float nrm = sqrtf(n2);
+    for (int a = 0; a < 3; ++a) d[a] = dd[a] / nrm;
+    float t0 = 0.0f, t1 = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        const float lo = -0.5f, hi = (float)dims[a] - 0.5f;
+        if (d[a] == 0.0f) {
+            if (e[a] < lo || e[a] > hi) return 0;
+            continue;
+        }
+        const float ta = (lo - e[a]) / d[a], tb = (hi - e[a]) / d[a];
+        const float ta0 = ta < tb ? ta : tb, tb0 = ta < tb ? tb : ta;
+        if (ta0 > t0) t0 = ta0;
+        if (tb0 < t1) t1 = tb0;
+    }
+    *tmin = t0;
+    *tmax = t1;
+    return t0 < t1;
+}
+
+typedef struct {
+    act_t A;
+    pred_t P;
+    double half[3];  /* generous box: the float32 test keeps nothing outside */
+    int ok;
+} rg_t;
+
+static rg_t* render_prepare(const double* prm, int64_t n, double k)
+{
+    rg_t* G = (rg_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(rg_t));
+    if (!G) return NULL;
+    for (int64_t i = 0; i < n; ++i) {
+        activate(prm + 12 * i, &G[i].A);
+        float p32[12];
+        for (int q = 0; q < 12; ++q) p32[q] = (float)prm[12 * i + q];
+        pred_coeffs(p32, &G[i].P);
+        G[i].ok = G[i].A.valid && G[i].P.valid;
+        for (int a = 0; a < 3; ++a) {
+            double var = 0.0;
+            for (int m = 0; m < 3; ++m) var += G[i].A.R[a][m] * G[i].A.R[a][m] * G[i].A.s[m] * G[i].A.s[m];
+            G[i].half[a] = k * 1.01 * sqrt(var) + 0.5;
+        }
+    }
+    return G;
+}
+
+/* Eq. 3 and its gradient at a float32 point; the float32 keep test decides
+ * membership.  Normalised: Vt = N / max(D, rho0) and, where D > rho0, the
+ * quotient rule (grad N D - N grad D) / D^2, else grad N / rho0. */
+static void field_at(const rg_t* G, int64_t n, float T, double rho0, int normalized, const float p[3], double* v,
+                     double g[3], int64_t* kept)
+{
+    double N = 0.0, D = 0.0, gN[3] = {0, 0, 0}, gD[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        const rg_t* q = &G[i];
+        if (!q->ok) continue;
+        if (fabs((double)p[0] - q->A.mu[0]) > q->half[0] || fabs((double)p[1] - q->A.mu[1]) > q->half[1] ||
+            fabs((double)p[2] - q->A.mu[2]) > q->half[2])
+            continue;
+        if (!(pred_t_at(&q->P, p[0], p[1], p[2]) > T)) continue;
+        ++*kept;
+        const double d[3] = {p[0] - q->A.mu[0], p[1] - q->A.mu[1], p[2] - q->A.mu[2]};
+        double Cd[3], m = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            Cd[a] = q->A.C[a][0] * d[0] + q->A.C[a][1] * d[1] + q->A.C[a][2] * d[2];
+            m += d[a] * Cd[a];
+        }
+        const double Gv = exp(-0.5 * m);
+        N += q->A.w * q->A.a * Gv;
+        D += q->A.w * Gv;
+        for (int a = 0; a < 3; ++a) {
+            gN[a] -= q->A.w * q->A.a * Gv * Cd[a];
+            gD[a] -= q->A.w * Gv * Cd[a];
+        }
+    }
+    if (!normalized) {
+        *v = N;
+        for (int a = 0; a < 3; ++a) g[a] = gN[a];
+    } else if (D > rho0) {
+        *v = N / D;
+        for (int a = 0; a < 3; ++a) g[a] = (gN[a] * D - N * gD[a]) / (D * D);
+    } else {
+        *v = N / rho0;
+        for (int a = 0; a < 3; ++a) g[a] = gN[a] / rho0;
+    }
+}
+
+int or_field_at(const double* prm, int64_t n, float k, double rho0, int normalized, const float* p, double* v,
+                double* g, int64_t* kept)
+{
+    rg_t* G = render_prepare(prm, n, (double)k);
+    if (!G) return 1;
+    int64_t kk = 0;
+    field_at(G, n, pred_threshold(k), rho0, normalized, p, v, g, &kk);
+    if (kept) *kept = kk;
+    free(G);
+    return 0;
+}
+
+int or_render(const double* prm, int64_t n, const int dims[3], float k, double rho0, int normalized,
+              const float* cam, int W, int H, const float* opt, const float* tf, int tf_n, double* image,
+              int64_t* kept_out)
+{
+    if (tf_n < 2 || W < 1 || H < 1 || !(opt[0] > 0.0f)) return 1;
+    rg_t* G = render_prepare(prm, n, (double)k);
+    if (!G) return 1;
+    const float T = pred_threshold(k);
+    const float step = opt[0];
+    const double term = opt[1], ratio = (double)opt[0] / (double)opt[2];
+    const int shade = opt[6] != 0.0f;
+    const double ka = opt[7], kd = opt[8], ks = opt[9], shin = opt[10], gfloor = opt[11];
+    int64_t kept_all = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : kept_all)
+    for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
+        const int i = (int)(pix % W), j = (int)(pix / W);
+        float d[3], tmin, tmax;
+        double Tr = 1.0, C[3] = {0.0, 0.0, 0.0};
+        if (or_ray_setup(cam, W, H, i, j, dims, d, &tmin, &tmax)) {
+            for (int64_t s = 0;; ++s) {
+                const float t = tmin + ((float)s + 0.5f) * step;
+                if (!(t < tmax)) break;
+                float p[3];
+                for (int a = 0; a < 3; ++a) p[a] = cam[a] + t * d[a];
+                double v, g[3];
+                int64_t kp = 0;
+                field_at(G, n, T, rho0, normalized, p, &v, g, &kp);
+                kept_all += kp;
+                /* transfer function: linear interpolation of the table on [0, 1] */
+                const double u = (v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v)) * (double)(tf_n - 1);
+                int i0 = (int)floor(u);
+                if (i0 > tf_n - 2) i0 = tf_n - 2;
+                const double fr = u - (double)i0;
+                double c[4];
+                for (int q = 0; q < 4; ++q) c[q] = (double)tf[4 * i0 + q] * (1.0 - fr) + (double)tf[4 * (i0 + 1) + q] * fr;
+                const double a0 = c[3] < 0.0 ? 0.0 : (c[3] > 1.0 ? 1.0 : c[3]);
+                const double as = 1.0 - pow(1.0 - a0, ratio);
+                if (shade) {
+                    const double gl = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                    const double ndl = fabs(g[0] * d[0] + g[1] * d[1] + g[2] * d[2]) / (gl > gfloor ? gl : gfloor);
+                    const double sf = ka + kd * ndl, sp = ks * pow(ndl, shin);
+                    for (int q = 0; q < 3; ++q) c[q] = c[q] * sf + sp;
+                }
+                for (int q = 0; q < 3; ++q) C[q] += Tr * as * c[q];
+                Tr *= 1.0 - as;
+                if (term > 0.0 && Tr < term) break;
+            }
+        }
+        double* o = image + 4 * pix;
+        for (int q = 0; q < 3; ++q) o[q] = C[q] + Tr * (double)opt[3 + q];
+        o[3] = 1.0 - Tr;
+    }
+    if (kept_out) *kept_out = kept_all;
+    free(G);
+    return 0;
+}

@@ -92,6 +92,12 @@ def lib():
             L.or_refine_sampled.restype = i32
             L.or_kept_submasks.argtypes = [P, P, f32, i32, i64, P, P, P]
             L.or_kept_submasks.restype = None
+            L.or_ray_setup.argtypes = [P, i32, i32, i32, i32, P, P, P, P]
+            L.or_ray_setup.restype = i32
+            L.or_field_at.argtypes = [P, i64, f32, f64, i32, P, P, P, P]
+            L.or_field_at.restype = i32
+            L.or_render.argtypes = [P, i64, P, f32, f64, i32, P, i32, i32, P, P, i32, P, P]
+            L.or_render.restype = i32
             L.or_grad_mag32.argtypes = [P, P, P]
             L.or_struct_tensor.argtypes = [P, P, i32, i32, i32, P]
             L.or_jacobi3.argtypes = [P, P, P]
@@ -407,6 +413,74 @@ def refine_sampled(prm, field, iters, S=3072, seed=0, step0=0, lr=1e-2, b1=0.9, 
     if st != 0:
         raise RuntimeError("oracle sampled refinement failed")
     return p, losses[:iters]
+
+
+# --------------------------------------------------------------------------
+# Mixture-field ray marching (Sec. III-A: the transfer function maps the
+# value of Eq. 3 at each sample to colour and opacity, composited along the
+# ray; grad Vt shades the sample)
+# --------------------------------------------------------------------------
+RENDER_DEFAULTS = dict(step=0.5, term=0.0, ref_step=1.0, background=(0.0, 0.0, 0.0), shade=False, ka=0.3,
+                       kd=0.7, ks=0.2, shininess=16.0, gfloor=1e-3)
+
+
+def _cam13(cam) -> np.ndarray:
+    """cam = (eye, right, up, forward, tan_half_fovy) -> float32[13]."""
+    eye, right, up, fwd, th = cam
+    out = np.concatenate([np.asarray(eye, np.float32).ravel(), np.asarray(right, np.float32).ravel(),
+                          np.asarray(up, np.float32).ravel(), np.asarray(fwd, np.float32).ravel(),
+                          np.asarray([th], np.float32)])
+    return np.ascontiguousarray(out, np.float32)
+
+
+def _opt12(opts) -> np.ndarray:
+    o = dict(RENDER_DEFAULTS, **(opts or {}))
+    bg = tuple(o["background"])
+    return np.array([o["step"], o["term"], o["ref_step"], bg[0], bg[1], bg[2], 1.0 if o["shade"] else 0.0,
+                     o["ka"], o["kd"], o["ks"], o["shininess"], o["gfloor"]], np.float32)
+
+
+def ray_setup(cam, W, H, i, j, dims_zyx):
+    """(hit, unit direction, tmin, tmax) of the ray through pixel (i, j),
+    float32 in the renderer's fixed order; dims_zyx = field shape."""
+    c = _cam13(cam)
+    nz, ny, nx = dims_zyx
+    d = np.zeros(3, np.float32)
+    t0, t1 = ctypes.c_float(0), ctypes.c_float(0)
+    hit = lib().or_ray_setup(_ptr(c), int(W), int(H), int(i), int(j), _ptr(np.array([nx, ny, nz], np.int32)),
+                             _ptr(d), ctypes.byref(t0), ctypes.byref(t1))
+    return bool(hit), d, t0.value, t1.value
+
+
+def field_at(prm, p, k=3.0, rho0=0.05, normalized=True):
+    """Eq. 3 at a float32 point and its gradient (FP64; float32 membership),
+    plus the number of kept Gaussians."""
+    q = _prm64(prm)
+    pt = np.ascontiguousarray(np.asarray(p, np.float32).reshape(3))
+    v = ctypes.c_double(0)
+    g = np.zeros(3, np.float64)
+    kept = ctypes.c_int64(0)
+    if lib().or_field_at(_ptr(q), q.shape[0], float(k), float(rho0), int(bool(normalized)), _ptr(pt),
+                         ctypes.byref(v), _ptr(g), ctypes.byref(kept)) != 0:
+        raise RuntimeError("oracle field evaluation failed")
+    return v.value, g, kept.value
+
+
+def render(prm, dims_zyx, cam, W, H, tf, opts=None, k=3.0, rho0=0.05, normalized=True):
+    """RGBA image (H, W, 4) in FP64 and the number of kept (sample,
+    Gaussian) pairs.  tf: (n, 4) float32 table of RGBA over V in [0, 1]."""
+    q = _prm64(prm)
+    c = _cam13(cam)
+    o = _opt12(opts)
+    t = np.ascontiguousarray(np.asarray(tf, np.float32).reshape(-1, 4))
+    nz, ny, nx = dims_zyx
+    img = np.zeros((H, W, 4), np.float64)
+    kept = ctypes.c_int64(0)
+    if lib().or_render(_ptr(q), q.shape[0], _ptr(np.array([nx, ny, nz], np.int32)), float(k), float(rho0),
+                       int(bool(normalized)), _ptr(c), int(W), int(H), _ptr(o), _ptr(t), t.shape[0], _ptr(img),
+                       ctypes.byref(kept)) != 0:
+        raise RuntimeError("oracle render failed (bad table, image size or step)")
+    return img, kept.value
 
 
 # --------------------------------------------------------------------------

@@ -185,3 +185,42 @@ WORKLOADS = {
     "headline": dict(kind="fbm_fronts", n=1024, seed=4, budget=1_400_000, iters=2000,
                      iters_reduced=300, lr=1e-2, k=3.0),
 }
+
+
+# --------------------------------------------------------------------------
+# Rendering inputs: cameras and transfer functions
+# --------------------------------------------------------------------------
+def orbit_camera(shape, azimuth_deg: float, elevation_deg: float, distance: float = 2.0, fovy_deg: float = 40.0):
+    """Pinhole camera on a sphere around the grid centre, looking at it, in
+    voxel coordinates (voxel centres at integers).  shape = (nz, ny, nx);
+    distance in units of the longest axis.  Returns float32 (eye, right, up,
+    forward) and tan(fovy / 2), the tuple the renderers take."""
+    nz, ny, nx = shape
+    c = np.array([(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
+    az, el = math.radians(azimuth_deg), math.radians(elevation_deg)
+    off = np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+    eye = c + distance * max(nx, ny, nz) * off
+    fwd = c - eye
+    fwd /= np.linalg.norm(fwd)
+    world_up = np.array([0.0, 0.0, 1.0]) if abs(fwd[2]) < 0.99 else np.array([0.0, 1.0, 0.0])
+    right = np.cross(fwd, world_up)
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    f32 = lambda a: np.asarray(a, np.float32)
+    return f32(eye), f32(right), f32(up), f32(fwd), float(np.float32(math.tan(math.radians(fovy_deg) / 2.0)))
+
+
+def transfer_function(n: int = 256, seed: int = 0, max_alpha: float = 0.35) -> np.ndarray:
+    """(n, 4) float32 RGBA table over V in [0, 1]: colours from 9 random
+    control points (PCG64 seed), opacity rising as V^1.5 with two random
+    bumps, scaled to max_alpha."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = np.linspace(0.0, 1.0, n)
+    ctrl = np.linspace(0.0, 1.0, 9)
+    rgb = np.stack([np.interp(x, ctrl, rng.uniform(0.05, 1.0, 9)) for _ in range(3)], axis=1)
+    a = x ** 1.5
+    for _ in range(2):
+        m, w = rng.uniform(0.2, 0.9), rng.uniform(0.03, 0.1)
+        a = a + 0.8 * np.exp(-0.5 * ((x - m) / w) ** 2)
+    a = max_alpha * a / a.max()
+    return np.ascontiguousarray(np.concatenate([rgb, a[:, None]], axis=1), np.float32)

@@ -926,3 +926,128 @@ def test_structure_function_kolmogorov_scaling():
     V = inputs.grf(96, seed=3)
     r = O.structure_stats(V)["S1_over_S16"]
     assert 0.08 < r < 0.3
+
+
+# --------------------------------------------------------------------------
+# Mixture-field ray marching (Sec. III-A: transfer function applied to the
+# value of Eq. 3 at ray samples, composited front to back)
+# --------------------------------------------------------------------------
+def _axis_camera(cx, cy, z0, th, W=5, H=5):
+    """Camera at (cx, cy, z0) looking along +z; the central pixel of an odd
+    image has the exact direction (0, 0, 1)."""
+    f = lambda *v: np.array(v, np.float32)
+    return (f(cx, cy, z0), f(1, 0, 0), f(0, 1, 0), f(0, 0, 1), th)
+
+
+def test_render_constant_transfer_function_closed_form():
+    """With a constant table every sample has the same opacity: the central
+    ray enters the 13 x 15 x 20 box at z = -0.5 and leaves at 19.5, so at
+    spacing 0.5 it takes 40 samples, and the pixel is c (1 - 0.9^20) +
+    bg 0.9^20 (opacity 0.1 per voxel).  A ray that misses shows the
+    background; early termination at 0.5 stops after the 14th sample."""
+    dims = (20, 15, 13)
+    rng = np.random.default_rng(3)
+    prm = np.zeros((3, 12))
+    prm[:, :3] = rng.uniform(2, 10, (3, 3))
+    prm[:, 6] = 1.0
+    tf = np.tile(np.array([[0.2, 0.5, 0.9, 0.1]], np.float32), (4, 1))
+    cam = _axis_camera(6.0, 7.0, -10.0, float(np.float32(np.tan(np.radians(60)))))
+    bg = (0.3, 0.1, 0.05)
+    img, _ = O.render(prm, dims, cam, 5, 5, tf, dict(step=0.5, ref_step=1.0, background=bg))
+    c = tf[0].astype(np.float64)                     # the table and background are float32
+    bg64 = np.array(bg, np.float32).astype(np.float64)
+    a = 1.0 - (1.0 - c[3]) ** 20
+    np.testing.assert_allclose(img[2, 2, :3], c[:3] * a + bg64 * (1 - a), rtol=1e-12)
+    assert img[2, 2, 3] == pytest.approx(a, rel=1e-12)
+    hit, d, t0, t1 = O.ray_setup(cam, 5, 5, 2, 2, dims)
+    assert hit and tuple(d) == (0.0, 0.0, 1.0) and (t0, t1) == (9.5, 29.5)
+    assert not O.ray_setup(cam, 5, 5, 0, 0, dims)[0]
+    np.testing.assert_allclose(img[0, 0], [*bg64, 0.0], atol=0)
+    img_t, _ = O.render(prm, dims, cam, 5, 5, tf, dict(step=0.5, ref_step=1.0, term=0.5))
+    assert img_t[2, 2, 3] == pytest.approx(1.0 - (1.0 - c[3]) ** 7, rel=1e-12)
+
+
+def _axis_gaussian(a=0.8, w_logit=0.0, mu=(6.0, 7.0, 9.0)):
+    p = np.zeros((1, 12))
+    p[0, :3] = mu
+    p[0, 3:6] = np.float32(np.log(2.0))
+    p[0, 6] = 1.0
+    p[0, 10] = a
+    p[0, 11] = w_logit
+    return p
+
+
+def _axis_expect(prm, normalized, alpha0, shade=None, rho0=0.05, step=0.5, nz=20):
+    """Front-to-back sum along the z axis through the Gaussian's centre,
+    written from the definitions: samples at z = -0.5 + (k + 1/2) step,
+    kept within 3 sigma, Vt = w a G / max(w G, rho0) or w a G, a grayscale
+    table (colour = value), opacity alpha0 per voxel."""
+    s = float(np.exp(np.float64(np.float32(np.log(2.0)))))   # the record holds float32(ln 2)
+    a, w = prm[0, 10], 1.0 / (1.0 + np.exp(-prm[0, 11]))
+    mz = prm[0, 2]
+    a_s = 1.0 - (1.0 - float(np.float32(alpha0))) ** step
+    Tr, C = 1.0, 0.0
+    for k in range(int(np.ceil(nz / step - 0.5))):
+        z = -0.5 + (k + 0.5) * step
+        G = np.exp(-0.5 * (z - mz) ** 2 / s ** 2) if abs(z - mz) < 3 * s else 0.0
+        v = w * a * G / max(w * G, rho0) if normalized else w * a * G
+        c = v
+        if shade is not None:
+            ka, kd, ks = shade
+            c = c * (ka + kd) + ks if G > 0 else c * ka   # |n . l| = 1 on the axis, 0 where grad = 0
+        C += Tr * a_s * c
+        Tr *= 1.0 - a_s
+    return C, 1.0 - Tr
+
+
+@pytest.mark.parametrize("normalized", [True, False])
+def test_render_axis_gaussian_closed_form(normalized):
+    dims = (20, 15, 13)
+    prm = _axis_gaussian()
+    tf = np.array([[0, 0, 0, 0.2], [1, 1, 1, 0.2]], np.float32)
+    cam = _axis_camera(6.0, 7.0, -10.0, 0.5)
+    img, kept = O.render(prm, dims, cam, 5, 5, tf, dict(step=0.5), normalized=normalized)
+    C, A = _axis_expect(prm, normalized, 0.2)
+    np.testing.assert_allclose(img[2, 2, :3], [C, C, C], rtol=1e-12, atol=1e-15)
+    assert img[2, 2, 3] == pytest.approx(A, rel=1e-12)
+
+
+def test_render_axis_shading_closed_form():
+    """Plain sum, headlight shading: on the axis grad Vt is parallel to the
+    ray, so |n . l| = 1 wherever the Gaussian is kept (gfloor below every
+    gradient there) and the shaded colour is c (ka + kd) + ks."""
+    dims = (20, 15, 13)
+    prm = _axis_gaussian()
+    tf = np.array([[0, 0, 0, 0.2], [1, 1, 1, 0.2]], np.float32)
+    cam = _axis_camera(6.0, 7.0, -10.0, 0.5)
+    opts = dict(step=0.5, shade=True, ka=0.25, kd=0.6, ks=0.15, shininess=8.0, gfloor=1e-12)
+    img, _ = O.render(prm, dims, cam, 5, 5, tf, opts, normalized=False)
+    C, _ = _axis_expect(prm, False, 0.2, shade=tuple(float(np.float32(x)) for x in (0.25, 0.6, 0.15)))
+    np.testing.assert_allclose(img[2, 2, :3], [C, C, C], rtol=1e-12)
+
+
+@pytest.mark.parametrize("w_logit,normalized", [(3.0, True), (-7.0, True), (0.0, False)])
+def test_field_gradient_central_differences(w_logit, normalized):
+    """grad Vt against central differences of Vt at float32 points (steps of
+    2^-10 are exact there); k = 20 so truncation does not enter.  w_logit 3
+    keeps the denominator above rho0 near the centres (quotient rule), -7
+    keeps it below (grad N / rho0)."""
+    rng = np.random.default_rng(11)
+    n = 12
+    prm = np.zeros((n, 12))
+    prm[:, :3] = rng.uniform(6, 10, (n, 3))
+    prm[:, 3:6] = np.log(rng.uniform(1.0, 2.5, (n, 3)))
+    prm[:, 6:10] = rng.normal(size=(n, 4))
+    prm[:, 10] = rng.uniform(0.1, 1.0, n)
+    prm[:, 11] = w_logit
+    h = 2.0 ** -10
+    for _ in range(6):
+        p = np.round(rng.uniform(6.5, 9.5, 3) * 16) / 16
+        v, g, _ = O.field_at(prm, p, k=20.0, normalized=normalized)
+        fd = np.zeros(3)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd[a] = (O.field_at(prm, p + e, k=20.0, normalized=normalized)[0]
+                     - O.field_at(prm, p - e, k=20.0, normalized=normalized)[0]) / (2 * h)
+        np.testing.assert_allclose(g, fd, rtol=1e-4, atol=1e-7 * max(1.0, abs(v)))

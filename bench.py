@@ -53,10 +53,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["headline", "mid", "small", "autograd", "batched", "proposal", "sampled",
-                                           "structure"],
+                                           "structure", "render"],
                     default="headline")
     ap.add_argument("--samples", type=int, default=3072, help="points per iteration of the sampled workload")
     ap.add_argument("--struct-n", type=int, default=1024, help="grid edge of the structure workload")
+    ap.add_argument("--render-n", type=int, default=1024, help="grid edge of the render workload (1024 or 512)")
+    ap.add_argument("--image", type=int, default=1024, help="image edge of the render workload")
+    ap.add_argument("--shade", action="store_true", help="render with gradient shading")
+    ap.add_argument("--term", type=float, default=1e-3, help="early ray termination threshold of the render workload")
     ap.add_argument("--prop-iters", type=int, default=200, help="refinement iterations per proposal evaluation")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
@@ -603,6 +607,123 @@ def run_structure(args):
     print(json.dumps(out), flush=True)
 
 
+RENDER_METRIC = ("ray-marched frames/s of the encoded 1024^3 model (1.4M Gaussians), 1024x1024 image, step 0.5 voxel, "
+                 "termination at transmittance 1e-3")
+# per kept (sample, Gaussian) pair: 3 differences, 9 for the keep chain, 1
+# compare, 2 accumulations (the evaluator's forward), 1 SFU exp2
+RENDER_OPS_PER_PAIR = 15.0
+
+
+def render_model(args, dev):
+    """The encoded headline model: allocation plus 20 refinement iterations
+    on the fBm + fronts field (the 512^3 profiling case when asked)."""
+    from paper_2608_14112_b300 import gve, inputs
+    n = args.render_n
+    budget = 1_400_000 if n >= 1024 else 175_000
+    V = inputs.fbm_fronts(n, seed=4, device=dev)
+    P, _ = gve.gve_allocate(V, budget, seed=args.seed)
+    gve.gve_refine(P, V, iters=20, lr=1e-2)
+    return V.shape, P
+
+
+def run_render(args):
+    """Mixture-field ray marching of the encoded model (Sec. III-A): frames
+    per second for an orbit camera, through the C ABI."""
+    import numpy as np
+    import torch
+    from paper_2608_14112_b300 import build as gbuild
+    from paper_2608_14112_b300 import gve, inputs
+
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    shape, P = render_model(args, dev)
+    torch.cuda.empty_cache()
+    W = H = args.image
+    cam = inputs.orbit_camera(shape, 40.0, 25.0, 1.7, 40.0)
+    tf_np = inputs.transfer_function(256, seed=4, max_alpha=0.08)
+    tf = torch.from_numpy(tf_np).to(dev)
+    ro = gve.RenderOptions(step=0.5, term=args.term, shade=args.shade, background=(0.0, 0.0, 0.0))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    gve.gve_render_prepare(P, shape)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prep_ms = e0.elapsed_time(e1)
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        gve.gve_render(cam, W, H, tf, ro, out=img)
+    _, kept = gve.gve_render(cam, W, H, tf, ro, out=img, want_kept=True)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        gve.gve_render(cam, W, H, tf, ro, out=img)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = args.steps / (ms / 1e3)
+    ms_frame = ms / args.steps
+    alu_peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = RENDER_OPS_PER_PAIR * kept / (ms_frame / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
+                "traffic": None, "kernel": "k_render<%s>" % ("true" if args.shade else "false"),
+                "kept_pairs": int(kept), "ops_per_pair": RENDER_OPS_PER_PAIR,
+                "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (derived, FMA counted once)"}
+    # end to end: camera in from the host, frame out to pinned host memory
+    host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gve.gve_render(cam, W, H, tf, ro, out=img)
+        host.copy_(img, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    # first frame from a host model: upload, preparation, render, image back
+    Ph = P.cpu().pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Pd = Ph.to(dev, non_blocking=True)
+    gve.gve_render_prepare(Pd, shape)
+    gve.gve_render(cam, W, H, tf, ro, out=img)
+    host.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    gve.gve_render_prepare(P, shape)
+    e2e = {"value": 1.0 / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": 60 + 64,
+           "d2h_bytes_per_step": int(W * H * 16),
+           "includes": "camera and options by value, render, RGBA float32 frame to pinned host memory",
+           "first_frame_from_host_model_s": first_s}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        prm = P.cpu().numpy().astype(np.float64)
+        rng = np.random.default_rng(0)
+        od = dict(step=0.5, shade=args.shade, term=args.term)
+        npx = 256
+        pix = rng.choice(W * H, npx, replace=False)
+        tm = {}
+        O.render(prm, shape, cam, W, H, tf_np, od, pixels=pix, timing=tm)
+        per_pixel = tm["pixel_seconds"] / npx
+        cpu = {"value": 1.0 / (per_pixel * W * H), "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{npx} random pixels of the same frame (the oracle's pixel loop, timed inside it, "
+                         "without its index build), scaled to the frame's pixel count"}
+    out = {"metric": RENDER_METRIC, "value": value, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_frame, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"render_fbm_fronts_{shape[0]}^3_N{P.shape[0]}_{W}x{H}_step0.5_term{args.term:g}"
+                                  + ("_shaded" if args.shade else ""),
+                      "model": "allocation + 20 refinement iterations", "transfer_function": "256-entry table, seed 4",
+                      "l2": "the model's cell lists (GB) exceed L2; a frame reads them once per ray group"},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+           "prepare_ms": prep_ms}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -741,6 +862,8 @@ def main():
         run_sampled(args)
     elif args.workload == "structure":
         run_structure(args)
+    elif args.workload == "render":
+        run_render(args)
     else:
         run_ours(args)
 

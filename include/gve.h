@@ -344,6 +344,66 @@ GVE_API gve_status gve_refine_sampled(gve_ctx* ctx, float* prims_dev, int64_t n,
                                       float* adam_state_dev, double* loss_trace_dev, gve_stats* stats,
                                       void* stream);
 
+/* ---- mixture-field ray marcher (Sec. III-A, rendering of the encoded set)
+ * Rendering applies a transfer function T = (c_T, alpha_T) to the value Eq. 3
+ * returns at sample positions along each camera ray and composites the
+ * samples front to back; grad Vt, available in closed form at the sample,
+ * shades it.  Nothing is rendered through a graphics API: the image is a
+ * device buffer.
+ *
+ * Camera, in voxel coordinates (voxel centres at integers, the volume box is
+ * [-0.5, n - 0.5] per axis): the ray through pixel (i, j) (column i, row j,
+ * row 0 at the top) has direction forward + sx right + sy up, normalised,
+ * with sx = ((2i + 1) / W - 1) tan_half_fovy (W / H) and sy = (1 - (2j + 1) /
+ * H) tan_half_fovy; ray setup and sample positions are float32 in that
+ * written order (no contraction).  Samples sit at t = tmin + (k + 1/2) step
+ * inside the box (tmin = max(entry, 0)). */
+typedef struct {
+    float eye[3];
+    float right[3], up[3], forward[3];
+    float tan_half_fovy;
+    int32_t width, height;
+} gve_camera;
+
+/* Render options.
+ *   step       sample spacing along the ray in voxels, >= 1/64, and at most
+ *              65,536 samples across the box diagonal.
+ *   term       stop a ray once its transmittance falls below term (0 = off).
+ *   ref_step   spacing the table's opacities refer to: a sample's opacity is
+ *              1 - (1 - alpha)^(step / ref_step).
+ *   background RGB seen through the remaining transmittance.
+ *   shade      0: emission-absorption; 1: headlight shading with the normal
+ *              n = grad Vt / max(|grad Vt|, gfloor): colour c (ka + kd |n.l|)
+ *              + ks |n.l|^shininess, l the direction towards the eye.
+ *   tf_dev     [tf_n][4] float32 RGBA table over V in [0, 1] (device memory,
+ *              linear interpolation, values clamped to [0, 1]); tf_n >= 2. */
+typedef struct {
+    float step, term, ref_step;
+    float background[3];
+    int32_t shade;
+    float ka, kd, ks, shininess, gfloor;
+    const float* tf_dev;
+    int32_t tf_n;
+} gve_render_opts;
+
+/* Builds the renderer's lists for a primitive set (once per set; the set may
+ * change afterwards, the context keeps its own copy of the coefficients):
+ * cells of 8^3 voxels, each listing, in Gaussian order, every Gaussian whose
+ * conservative truncation box (the same margins as the sampled refinement)
+ * overlaps the cell's continuous extent.  Synchronises `stream`.
+ * GVE_E_INVALID for bad sizes or options, GVE_E_CAPACITY beyond 2^32 pairs. */
+GVE_API gve_status gve_render_prepare(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                                      const gve_eval_opts* opts, void* stream);
+
+/* Renders the prepared set: image_dev [height][width][4] float32 RGBA
+ * (premultiplied colour plus background, alpha = 1 - transmittance).
+ * kept_pairs (host, nullable) receives the kept (sample, Gaussian) pairs,
+ * the algorithmic work of the frame (synchronises when asked).
+ * GVE_E_INVALID without a prepared set, for a non-finite camera, bad
+ * options, more than 2^28 pixels or more than 524,280 rows. */
+GVE_API gve_status gve_render(gve_ctx* ctx, const gve_camera* cam, const gve_render_opts* opts, float* image_dev,
+                              int64_t* kept_pairs, void* stream);
+
 /* Brick binning introspection: the (brick, Gaussian) pairs that evaluation
  * uses, sorted by brick key (z-major brick index) and then by Gaussian index,
  * and per-brick [start, end) ranges.

@@ -53,6 +53,7 @@
  * Everything here is FP64 unless a comment says float32.
  */
 #include <math.h>
+#include <time.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1395,6 +1396,7 @@ int or_ray_setup(const float* cam, int W, int H, int i, int j, const int dims[3]
     }
     const float n2a = dd[0] * dd[0] + dd[1] * dd[1];
     const float n2 = n2a + dd[2] * dd[2];
+    if (!(n2 > 0.0f) || !isfinite(n2)) return 0;  /* degenerate camera: no ray */
     const float nrm = sqrtf(n2);
     for (int a = 0; a < 3; ++a) d[a] = dd[a] / nrm;
     float t0 = 0.0f, t1 = INFINITY;
@@ -1411,7 +1413,7 @@ int or_ray_setup(const float* cam, int W, int H, int i, int j, const int dims[3]
     }
     *tmin = t0;
     *tmax = t1;
-    return t0 < t1;
+    return t0 < t1 && isfinite(t1);
 }
 
 typedef struct {
@@ -1420,6 +1422,63 @@ typedef struct {
     double half[3];  /* generous box: the float32 test keeps nothing outside */
     int ok;
 } rg_t;
+
+/* The oracle's own candidate index: cells of 16^3 voxels, each listing (in
+ * index order) the Gaussians whose generous box reaches it.  It only skips
+ * Gaussians the float32 test cannot keep; the sum over the rest is Eq. 3. */
+typedef struct {
+    int nc[3];
+    int64_t* start;  /* [ncells + 1] */
+    int64_t* ids;
+} rindex_t;
+
+static int rcell(double p, int nc)
+{
+    double f = floor((p + 0.5) / 16.0);
+    if (f < 0) return 0;
+    if (f > nc - 1) return nc - 1;
+    return (int)f;
+}
+
+static int rindex_build(const rg_t* G, int64_t n, const int dims[3], rindex_t* X)
+{
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        X->nc[a] = (dims[a] + 15) / 16;
+        ncell *= X->nc[a];
+    }
+    X->start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    if (!X->start) return 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t* fill = NULL;
+        if (pass == 1) {
+            for (int64_t c = 0; c < ncell; ++c) X->start[c + 1] += X->start[c];
+            X->ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(X->start[ncell] > 0 ? X->start[ncell] : 1));
+            fill = (int64_t*)calloc((size_t)ncell, sizeof(int64_t));
+            if (!X->ids || !fill) return 1;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (!G[i].ok) continue;
+            int lo[3], hi[3], skip = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double l = G[i].A.mu[a] - G[i].half[a], h = G[i].A.mu[a] + G[i].half[a];
+                if (h < -0.5 || l > dims[a] - 0.5) skip = 1;
+                lo[a] = rcell(l, X->nc[a]);
+                hi[a] = rcell(h, X->nc[a]);
+            }
+            if (skip) continue;
+            for (int z = lo[2]; z <= hi[2]; ++z)
+                for (int y = lo[1]; y <= hi[1]; ++y)
+                    for (int x = lo[0]; x <= hi[0]; ++x) {
+                        const int64_t c = ((int64_t)z * X->nc[1] + y) * X->nc[0] + x;
+                        if (pass == 0) X->start[c + 1]++;
+                        else X->ids[X->start[c] + fill[c]++] = i;
+                    }
+        }
+        free(fill);
+    }
+    return 0;
+}
 
 static rg_t* render_prepare(const double* prm, int64_t n, double k)
 {
@@ -1443,12 +1502,19 @@ static rg_t* render_prepare(const double* prm, int64_t n, double k)
 /* Eq. 3 and its gradient at a float32 point; the float32 keep test decides
  * membership.  Normalised: Vt = N / max(D, rho0) and, where D > rho0, the
  * quotient rule (grad N D - N grad D) / D^2, else grad N / rho0. */
-static void field_at(const rg_t* G, int64_t n, float T, double rho0, int normalized, const float p[3], double* v,
-                     double g[3], int64_t* kept)
+static void field_at(const rg_t* G, int64_t n, const rindex_t* X, float T, double rho0, int normalized,
+                     const float p[3], double* v, double g[3], int64_t* kept)
 {
     double N = 0.0, D = 0.0, gN[3] = {0, 0, 0}, gD[3] = {0, 0, 0};
-    for (int64_t i = 0; i < n; ++i) {
-        const rg_t* q = &G[i];
+    int64_t b = 0, e = n;
+    if (X) {
+        const int64_t c = ((int64_t)rcell(p[2], X->nc[2]) * X->nc[1] + rcell(p[1], X->nc[1])) * X->nc[0] +
+                          rcell(p[0], X->nc[0]);
+        b = X->start[c];
+        e = X->start[c + 1];
+    }
+    for (int64_t ii = b; ii < e; ++ii) {
+        const rg_t* q = &G[X ? X->ids[ii] : ii];
         if (!q->ok) continue;
         if (fabs((double)p[0] - q->A.mu[0]) > q->half[0] || fabs((double)p[1] - q->A.mu[1]) > q->half[1] ||
             fabs((double)p[2] - q->A.mu[2]) > q->half[2])
@@ -1487,28 +1553,37 @@ int or_field_at(const double* prm, int64_t n, float k, double rho0, int normaliz
     rg_t* G = render_prepare(prm, n, (double)k);
     if (!G) return 1;
     int64_t kk = 0;
-    field_at(G, n, pred_threshold(k), rho0, normalized, p, v, g, &kk);
+    field_at(G, n, NULL, pred_threshold(k), rho0, normalized, p, v, g, &kk);
     if (kept) *kept = kk;
     free(G);
     return 0;
 }
 
+/* image: [H][W][4], or [npix][4] for the pixels pix[0..npix) (index j W + i)
+ * when pix is given. */
 int or_render(const double* prm, int64_t n, const int dims[3], float k, double rho0, int normalized,
-              const float* cam, int W, int H, const float* opt, const float* tf, int tf_n, double* image,
-              int64_t* kept_out)
+              const float* cam, int W, int H, const float* opt, const float* tf, int tf_n, const int64_t* pix,
+              int64_t npix, double* image, int64_t* kept_out, double* pixel_seconds)
 {
     if (tf_n < 2 || W < 1 || H < 1 || !(opt[0] > 0.0f)) return 1;
     rg_t* G = render_prepare(prm, n, (double)k);
     if (!G) return 1;
+    rindex_t X;
+    memset(&X, 0, sizeof(X));
+    if (rindex_build(G, n, dims, &X)) return 1;
+    const int64_t np = pix ? npix : (int64_t)W * H;
     const float T = pred_threshold(k);
     const float step = opt[0];
     const double term = opt[1], ratio = (double)opt[0] / (double)opt[2];
     const int shade = opt[6] != 0.0f;
     const double ka = opt[7], kd = opt[8], ks = opt[9], shin = opt[10], gfloor = opt[11];
     int64_t kept_all = 0;
-#pragma omp parallel for schedule(dynamic, 4) reduction(+ : kept_all)
-    for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
-        const int i = (int)(pix % W), j = (int)(pix / W);
+    struct timespec ts0, ts1;
+    clock_gettime(CLOCK_MONOTONIC, &ts0);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : kept_all)
+    for (int64_t q0 = 0; q0 < np; ++q0) {
+        const int64_t px = pix ? pix[q0] : q0;
+        const int i = (int)(px % W), j = (int)(px / W);
         float d[3], tmin, tmax;
         double Tr = 1.0, C[3] = {0.0, 0.0, 0.0};
         if (or_ray_setup(cam, W, H, i, j, dims, d, &tmin, &tmax)) {
@@ -1519,7 +1594,7 @@ int or_render(const double* prm, int64_t n, const int dims[3], float k, double r
                 for (int a = 0; a < 3; ++a) p[a] = cam[a] + t * d[a];
                 double v, g[3];
                 int64_t kp = 0;
-                field_at(G, n, T, rho0, normalized, p, &v, g, &kp);
+                field_at(G, n, &X, T, rho0, normalized, p, &v, g, &kp);
                 kept_all += kp;
                 /* transfer function: linear interpolation of the table on [0, 1] */
                 const double u = (v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v)) * (double)(tf_n - 1);
@@ -1541,11 +1616,15 @@ int or_render(const double* prm, int64_t n, const int dims[3], float k, double r
                 if (term > 0.0 && Tr < term) break;
             }
         }
-        double* o = image + 4 * pix;
+        double* o = image + 4 * q0;
         for (int q = 0; q < 3; ++q) o[q] = C[q] + Tr * (double)opt[3 + q];
         o[3] = 1.0 - Tr;
     }
+    clock_gettime(CLOCK_MONOTONIC, &ts1);
+    if (pixel_seconds) *pixel_seconds = (double)(ts1.tv_sec - ts0.tv_sec) + 1e-9 * (double)(ts1.tv_nsec - ts0.tv_nsec);
     if (kept_out) *kept_out = kept_all;
     free(G);
+    free(X.start);
+    free(X.ids);
     return 0;
 }

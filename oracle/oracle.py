@@ -96,7 +96,7 @@ def lib():
             L.or_ray_setup.restype = i32
             L.or_field_at.argtypes = [P, i64, f32, f64, i32, P, P, P, P]
             L.or_field_at.restype = i32
-            L.or_render.argtypes = [P, i64, P, f32, f64, i32, P, i32, i32, P, P, i32, P, P]
+            L.or_render.argtypes = [P, i64, P, f32, f64, i32, P, i32, i32, P, P, i32, P, i64, P, P, P]
             L.or_render.restype = i32
             L.or_grad_mag32.argtypes = [P, P, P]
             L.or_struct_tensor.argtypes = [P, P, i32, i32, i32, P]
@@ -466,20 +466,28 @@ def field_at(prm, p, k=3.0, rho0=0.05, normalized=True):
     return v.value, g, kept.value
 
 
-def render(prm, dims_zyx, cam, W, H, tf, opts=None, k=3.0, rho0=0.05, normalized=True):
+def render(prm, dims_zyx, cam, W, H, tf, opts=None, k=3.0, rho0=0.05, normalized=True, pixels=None,
+           timing=None):
     """RGBA image (H, W, 4) in FP64 and the number of kept (sample,
-    Gaussian) pairs.  tf: (n, 4) float32 table of RGBA over V in [0, 1]."""
+    Gaussian) pairs.  tf: (n, 4) float32 table of RGBA over V in [0, 1].
+    pixels (optional): flat indices j W + i; then the result is (len, 4).
+    timing (optional dict) receives the seconds of the pixel loop alone."""
     q = _prm64(prm)
     c = _cam13(cam)
     o = _opt12(opts)
     t = np.ascontiguousarray(np.asarray(tf, np.float32).reshape(-1, 4))
     nz, ny, nx = dims_zyx
-    img = np.zeros((H, W, 4), np.float64)
+    pix = None if pixels is None else np.ascontiguousarray(np.asarray(pixels, np.int64).ravel())
+    img = np.zeros((H, W, 4) if pix is None else (pix.size, 4), np.float64)
     kept = ctypes.c_int64(0)
+    secs = ctypes.c_double(0)
     if lib().or_render(_ptr(q), q.shape[0], _ptr(np.array([nx, ny, nz], np.int32)), float(k), float(rho0),
-                       int(bool(normalized)), _ptr(c), int(W), int(H), _ptr(o), _ptr(t), t.shape[0], _ptr(img),
-                       ctypes.byref(kept)) != 0:
+                       int(bool(normalized)), _ptr(c), int(W), int(H), _ptr(o), _ptr(t), t.shape[0],
+                       None if pix is None else _ptr(pix), 0 if pix is None else pix.size, _ptr(img),
+                       ctypes.byref(kept), ctypes.byref(secs)) != 0:
         raise RuntimeError("oracle render failed (bad table, image size or step)")
+    if timing is not None:
+        timing["pixel_seconds"] = secs.value
     return img, kept.value
 
 

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
           f"-I{INCLUDE}"]
 PER_FILE = {"alloc.cu": ["--fmad=false"]}
-SOURCES = ["bin.cu", "field.cu", "optim.cu", "alloc.cu", "api.cu", "batch.cu", "proposal.cu", "sample.cu",
+SOURCES = ["bin.cu", "field.cu", "optim.cu", "alloc.cu", "api.cu", "batch.cu", "proposal.cu", "sample.cu", "render.cu",
            "noalloc.cu"]
 
 

@@ -99,6 +99,15 @@ struct gve_ctx {
     // upstream gradients, loss
     gve::Buf s_hi, s_mid, s_cnt, s_off, s_pts, s_cell, s_order, s_nd, s_gg, s_loss;
     unsigned long long s_nh = 0, s_nm = 0;
+    // ray marcher: keep coefficients, per-Gaussian cell counts and offsets,
+    // (cell, Gaussian) pairs and their sort buffers, per-cell ranges, the
+    // coefficients in cell order, device state
+    gve::Buf r_rec, r_cnt, r_off, r_keys[2], r_vals[2], r_hist, r_scanp, r_rng, r_crec, r_state;
+    int r_dims[3] = {0, 0, 0}, r_nc[3] = {0, 0, 0};
+    float r_T = 0.f, r_rho0 = 0.f;
+    int r_norm = 1;
+    bool r_ready = false;
+    unsigned long long r_pairs = 0;
 };
 
 namespace gve {
@@ -109,6 +118,57 @@ __device__ __forceinline__ float ex2_approx(float x)
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// The keep exponent t at a float32 offset d = p - mu from the prepared
+// coefficients r0 = (mu, qxx), r1 = (qyy, qzz, qxy2, qxz2), r2 = (qyz2, ...):
+// the voxel path's fixed chain (kept iff t > T).
+__device__ __forceinline__ float keep_t(const float4& r0, const float4& r1, const float4& r2, float dx, float dy,
+                                        float dz)
+{
+    const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
+    const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
+    return __fmaf_rn(dx, __fmaf_rn(r0.w, dx, b), c);
+}
+
+// Conservative truncation box of raw record i (12 floats): centre mu and per
+// axis half extent rad = kb sqrt(Sigma_jj) 1.0001 + 0.05 voxel with kb =
+// k (1.001 + 1e-5 cond), cond = (s_max / s_min)^2, in float32; the margins
+// cover the float32 rounding of the keep chain at any float32 point.
+// Returns 0 for a record the preparation marks invalid (non-finite values,
+// zero quaternion), 2 for scales beyond float range (the whole grid), else 1.
+__device__ __forceinline__ int gauss_box(const float* prims, long long i, float k, float mu[3], float rad[3])
+{
+    const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
+    const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
+    const float p[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) ok = ok && isfinite(p[j]);
+    const float nq = sqrtf(p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9]);
+    if (!ok || !(nq > 0.f) || !isfinite(nq)) return 0;
+    const float qw = p[6] / nq, qx = p[7] / nq, qy = p[8] / nq, qz = p[9] / nq;
+    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+    float s[3];
+    bool huge = false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s[j] = expf(p[3 + j]);
+        huge = huge || !isfinite(s[j]);
+        mu[j] = p[j];
+    }
+    if (huge) return 2;
+    const float smax = fmaxf(s[0], fmaxf(s[1], s[2])), smin = fminf(s[0], fminf(s[1], s[2]));
+    const float ratio = smin > 0.f ? smax / smin : 1e30f;
+    const float kb = k * (1.001f + 1e-5f * fminf(ratio * ratio, 1e30f));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float var = R[j][0] * R[j][0] * s[0] * s[0] + R[j][1] * R[j][1] * s[1] * s[1] + R[j][2] * R[j][2] * s[2] * s[2];
+        rad[j] = kb * sqrtf(var) * 1.0001f + 0.05f;
+    }
+    return 1;
 }
 
 // ---- launchers (bin.cu) --------------------------------------------------

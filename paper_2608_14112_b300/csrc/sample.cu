@@ -131,54 +131,24 @@ struct SampleArgs {
 // preparation marks invalid (non-finite values, zero quaternion).
 __device__ __forceinline__ bool gauss_cells(const SampleArgs& a, long long i, int lo[3], int hi[3])
 {
-    const float4* p4 = reinterpret_cast<const float4*>(a.prims) + 3 * i;
-    const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
-    const float p[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 12; ++j) ok = ok && isfinite(p[j]);
-    const float nq = sqrtf(p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9]);
-    if (!ok || !(nq > 0.f) || !isfinite(nq)) return false;
-    const float qw = p[6] / nq, qx = p[7] / nq, qy = p[8] / nq, qz = p[9] / nq;
-    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
-                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
-                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
-    float s[3];
-    bool huge = false;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        s[j] = expf(p[3 + j]);
-        huge = huge || !isfinite(s[j]);
-    }
+    float mu[3], rad[3];
+    const int kind = gauss_box(a.prims, i, a.k, mu, rad);
+    if (kind == 0) return false;
     const int dims[3] = {a.nx, a.ny, a.nz};
     const int nc[3] = {a.cg.ncx, a.cg.ncy, a.cg.ncz};
-    if (huge) {  // scales beyond float range: every cell
+    if (kind == 2) {  // scales beyond float range: every cell
         for (int j = 0; j < 3; ++j) { lo[j] = 0; hi[j] = nc[j] - 1; }
         return true;
     }
-    const float smax = fmaxf(s[0], fmaxf(s[1], s[2])), smin = fminf(s[0], fminf(s[1], s[2]));
-    const float ratio = smin > 0.f ? smax / smin : 1e30f;
-    const float kb = a.k * (1.001f + 1e-5f * fminf(ratio * ratio, 1e30f));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float var = R[j][0] * R[j][0] * s[0] * s[0] + R[j][1] * R[j][1] * s[1] * s[1] + R[j][2] * R[j][2] * s[2] * s[2];
-        const float rad = kb * sqrtf(var) * 1.0001f + 0.05f;
-        float l = floorf(p[j] - rad), h = floorf(p[j] + rad);
+        float l = floorf(mu[j] - rad[j]), h = floorf(mu[j] + rad[j]);
         l = fminf(fmaxf(l, 0.f), (float)(dims[j] - 1));
         h = fminf(fmaxf(h, 0.f), (float)(dims[j] - 1));
         lo[j] = ((int)l) >> a.cg.shift;
         hi[j] = ((int)h) >> a.cg.shift;
     }
     return true;
-}
-
-// the keep exponent at a float32 point, by the voxel path's chain
-__device__ __forceinline__ float keep_t(const float4& r0, const float4& r1, const float4& r2, float dx, float dy,
-                                        float dz)
-{
-    const float b = __fmaf_rn(r1.z, dy, __fmul_rn(r1.w, dz));
-    const float c = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, __fmul_rn(r2.x, dz)), __fmul_rn(dz, __fmul_rn(r1.y, dz)));
-    return __fmaf_rn(dx, __fmaf_rn(r0.w, dx, b), c);
 }
 
 // Calls f(s) for every sorted point s in the cells [lo, hi]: one contiguous

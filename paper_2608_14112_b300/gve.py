@@ -107,6 +107,10 @@ def lib():
             L.gve_loss_grad.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(EvalOpts), ctypes.c_float, P, P, P]
             L.gve_backward.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P]
             L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
+            L.gve_render_prepare.argtypes = [P, P, i64, Dims, P, P]
+            L.gve_render_prepare.restype = st
+            L.gve_render.argtypes = [P, P, P, P, P, P]
+            L.gve_render.restype = st
             L.gve_structure_stats.argtypes = [P, P, Dims, P, P, P]
             L.gve_structure_stats.restype = st
             L.gve_draw_samples.argtypes = [P, P, Dims, i64, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
@@ -253,6 +257,68 @@ def gve_refine(prims: torch.Tensor, field: torch.Tensor, iters: int, lr: float =
     if not want_stats:
         return None
     return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("forward", ctypes.c_float * 3), ("tan_half_fovy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_float), ("term", ctypes.c_float), ("ref_step", ctypes.c_float),
+                ("background", ctypes.c_float * 3), ("shade", ctypes.c_int32), ("ka", ctypes.c_float),
+                ("kd", ctypes.c_float), ("ks", ctypes.c_float), ("shininess", ctypes.c_float),
+                ("gfloor", ctypes.c_float), ("tf_dev", ctypes.c_void_p), ("tf_n", ctypes.c_int32)]
+
+
+@dataclass
+class RenderOptions:
+    step: float = 0.5
+    term: float = 0.0
+    ref_step: float = 1.0
+    background: tuple = (0.0, 0.0, 0.0)
+    shade: bool = False
+    ka: float = 0.3
+    kd: float = 0.7
+    ks: float = 0.2
+    shininess: float = 16.0
+    gfloor: float = 1e-3
+
+
+def gve_render_prepare(prims: torch.Tensor, shape, opts: EvalOptions | None = None) -> None:
+    """Builds the ray marcher's cell lists for a primitive set on a grid of
+    ``shape = (nz, ny, nx)`` (the context keeps its own copy)."""
+    prims = _prims(prims)
+    o = (opts or EvalOptions()).c()
+    c = context(prims.device.index)
+    _check(lib().gve_render_prepare(c, _ptr(prims), prims.shape[0], _dims(shape), ctypes.byref(o),
+                                    _stream(prims.device)), c)
+
+
+def gve_render(camera, width: int, height: int, tf: torch.Tensor, opts: RenderOptions | None = None,
+               device=None, out: torch.Tensor | None = None, want_kept: bool = False):
+    """RGBA image (height, width, 4) of the prepared set.  camera = (eye,
+    right, up, forward, tan_half_fovy) in voxel coordinates; tf = (n, 4)
+    float32 CUDA tensor over V in [0, 1]."""
+    o = opts or RenderOptions()
+    if tf.dtype != torch.float32 or tf.dim() != 2 or tf.shape[1] != 4 or not tf.is_cuda or not tf.is_contiguous():
+        raise ValueError("tf must be a contiguous CUDA float32 tensor of shape (n, 4)")
+    dev = tf.device if device is None else torch.device(device)
+    eye, right, up, fwd, th = camera
+    cam = Camera((ctypes.c_float * 3)(*map(float, eye)), (ctypes.c_float * 3)(*map(float, right)),
+                 (ctypes.c_float * 3)(*map(float, up)), (ctypes.c_float * 3)(*map(float, fwd)), float(th),
+                 int(width), int(height))
+    ro = RenderOpts(float(o.step), float(o.term), float(o.ref_step), (ctypes.c_float * 3)(*map(float, o.background)),
+                    int(bool(o.shade)), float(o.ka), float(o.kd), float(o.ks), float(o.shininess), float(o.gfloor),
+                    tf.data_ptr(), int(tf.shape[0]))
+    if out is None:
+        out = torch.empty((int(height), int(width), 4), dtype=torch.float32, device=dev)
+    kept = ctypes.c_int64(0)
+    c = context(dev.index)
+    _check(lib().gve_render(c, ctypes.byref(cam), ctypes.byref(ro), _ptr(out),
+                            ctypes.byref(kept) if want_kept else None, _stream(dev)), c)
+    return (out, kept.value) if want_kept else out
 
 
 def gve_structure_stats(field: torch.Tensor, want_stage_ms: bool = False) -> dict:

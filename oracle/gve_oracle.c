@@ -1337,6 +1337,218 @@ double or_sample_loss_grad(const double* prm, int64_t n, const float* pts, const
     return loss;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The full objective (Sec. III-F): the value term plus five regularisers    */
+/* whose forms the paper gives in words only (the readings):                 */
+/*   L_rho   = (1/S) sum_s 1[v_s > occ] (rho(p_s) - 1)^2, rho = sum w G      */
+/*             (truncated like Eq. 3): density toward one over occupied      */
+/*             space, from both sides;                                       */
+/*   L_sm    = (1/S) sum_s (rho(p_s) - rho(p'_s))^2, p'_s a jittered partner */
+/*             of p_s (pts[S + s]);                                          */
+/*   L_anc   = (1/N) sum_i (a_i - V(mu_i))^2, V trilinear, gradient into a_i */
+/*             only (the volume value is the anchor's target);               */
+/*   L_aniso = (1/N) sum_i sum_{j<k} relu(|l_ij - l_ik| - ln r_max)^2,       */
+/*             l = log-scales (elongation bounded at r_max : 1);             */
+/*   L_cap   = (1/N) sum_i sum_j relu(l_ij - ln s_hi)^2                      */
+/*             + relu(ln s_lo - l_ij)^2 (scales outside [s_lo, s_hi]).       */
+/* ------------------------------------------------------------------------ */
+#define OR_PARTNER_STREAM 5u
+
+/* Partner of sample j of iteration iter: jitter u = (x >> 8) 2^-24 - 1/2 per
+ * axis from Philox4x32-10 stream 5, counter (j, iter), scaled to
+ * [-radius, radius) and the point clamped to [0, n - 1]; float32. */
+void or_draw_partners(const float* pts, int64_t S, const int dims[3], uint64_t seed, uint32_t iter, float radius,
+                      float* out)
+{
+    const float span = 2.0f * radius;
+    for (int64_t j = 0; j < S; ++j) {
+        uint32_t r[4];
+        or_draw(((uint64_t)iter << 32) | (uint64_t)(uint32_t)j, OR_PARTNER_STREAM, seed, r);
+        for (int a = 0; a < 3; ++a) {
+            const float u = (float)(r[a] >> 8) * 0x1p-24f - 0.5f;
+            float q = pts[3 * j + a] + u * span;
+            const float hi = (float)(dims[a] - 1);
+            q = q < 0.0f ? 0.0f : (q > hi ? hi : q);
+            out[3 * j + a] = q;
+        }
+    }
+}
+
+/* lambda_sm at iteration t: geometric decay from l0 to l1 over `anneal`
+ * iterations, then l1 (constant l0 when anneal <= 0 or l1 <= 0). */
+double or_lambda_sm(double l0, double l1, int anneal, int t)
+{
+    if (anneal <= 0 || !(l1 > 0.0) || !(l0 > 0.0)) return l0;
+    const double f = t < anneal ? (double)t / (double)anneal : 1.0;
+    return l0 * pow(l1 / l0, f);
+}
+
+/* reg[8] = {l_rho, l_sm (this iteration's), l_anc, l_aniso, l_cap, r_max,
+ * s_lo, s_hi}; pts holds S samples and, when smooth, their S partners after
+ * them; field/dims give V for the anchor (may be NULL when l_anc = 0).
+ * Returns L; terms[6] (optional) = {L_val, L_rho, L_sm, L_anc, L_aniso,
+ * L_cap} unweighted; grad (optional) = dL/dprm. */
+double or_sample_objective(const double* prm, int64_t n, const float* pts, const float* vals, int64_t S, int smooth,
+                           const float* field, const int dims[3], const double* reg, float k, double rho0,
+                           double occ, double* grad, double* terms)
+{
+    const int64_t P = smooth ? 2 * S : S;
+    const double l_rho = reg[0], l_sm = reg[1], l_anc = reg[2], l_a = reg[3], l_s = reg[4];
+    const double ln_r = log(reg[5]), ln_lo = log(reg[6]), ln_hi = log(reg[7]);
+    act_t* A = (act_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(act_t));
+    pred_t* Pc = (pred_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(pred_t));
+    double* num = (double*)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
+    double* den = (double*)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
+    double* gn = (double*)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
+    double* gd = (double*)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
+    if (!A || !Pc || !num || !den || !gn || !gd) return NAN;
+    const float T = pred_threshold(k);
+    for (int64_t i = 0; i < n; ++i) {
+        activate(prm + 12 * i, &A[i]);
+        float p32[12];
+        for (int j = 0; j < 12; ++j) p32[j] = (float)prm[12 * i + j];
+        pred_coeffs(p32, &Pc[i]);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < P; ++s) {
+        const float* p = pts + 3 * s;
+        double nu = 0.0, de = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!A[i].valid || !Pc[i].valid) continue;
+            if (!(pred_t_at(&Pc[i], p[0], p[1], p[2]) > T)) continue;
+            double G = exp(-0.5 * maha2(&A[i], p[0], p[1], p[2]));
+            nu += A[i].w * A[i].a * G;
+            de += A[i].w * G;
+        }
+        num[s] = nu;
+        den[s] = de;
+    }
+    /* point terms and the upstream gradient (dL/dnum, dL/dden) per point */
+    double Lval = 0.0, Lrho = 0.0, Lsm = 0.0;
+    for (int64_t s = 0; s < S; ++s) {
+        const double vt = num[s] / (den[s] > rho0 ? den[s] : rho0);
+        const int occd = vals[s] > (float)occ;
+        const double r = occd ? vt - (double)vals[s] : 0.0;
+        Lval += r * r;
+        const double up = 2.0 * r / (double)S;
+        if (den[s] >= rho0) { gn[s] = up / den[s]; gd[s] = -vt * gn[s]; }
+        else { gn[s] = up / rho0; gd[s] = 0.0; }
+        if (occd) {
+            const double e = den[s] - 1.0;
+            Lrho += e * e;
+            gd[s] += l_rho * 2.0 * e / (double)S;
+        }
+        if (smooth) {
+            const double e = den[s] - den[S + s];
+            Lsm += e * e;
+            gd[s] += l_sm * 2.0 * e / (double)S;
+            gn[S + s] = 0.0;
+            gd[S + s] = -l_sm * 2.0 * e / (double)S;
+        }
+    }
+    Lval /= (double)S;
+    Lrho /= (double)S;
+    Lsm /= (double)S;
+    if (grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            double* out = grad + 12 * i;
+            for (int j = 0; j < 12; ++j) out[j] = 0.0;
+            if (!A[i].valid || !Pc[i].valid) continue;
+            double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
+            for (int64_t s = 0; s < P; ++s) {
+                const float* p = pts + 3 * s;
+                if (!(pred_t_at(&Pc[i], p[0], p[1], p[2]) > T)) continue;
+                double d[3] = {p[0] - A[i].mu[0], p[1] - A[i].mu[1], p[2] - A[i].mu[2]};
+                double Gv = exp(-0.5 * maha2(&A[i], p[0], p[1], p[2]));
+                Ag += Gv * gn[s];
+                Bg += Gv * gd[s];
+                double c = A[i].w * (A[i].a * gn[s] + gd[s]);
+                double h = -0.5 * c * Gv;
+                for (int a2 = 0; a2 < 3; ++a2) {
+                    S1[a2] += h * d[a2];
+                    for (int b = 0; b < 3; ++b) S2[a2][b] += h * d[a2] * d[b];
+                }
+            }
+            chain_rule(&A[i], prm + 12 * i, Ag, Bg, S1, S2, out);
+        }
+    }
+    /* per-Gaussian terms */
+    double Lanc = 0.0, Lan = 0.0, Lcap = 0.0;
+    const double invN = n > 0 ? 1.0 / (double)n : 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!A[i].valid || !Pc[i].valid) continue;
+        const double* q = prm + 12 * i;
+        double* out = grad ? grad + 12 * i : NULL;
+        if (l_anc != 0.0 && field) {
+            const double r = q[10] - or_trilinear(field, dims, q[0], q[1], q[2]);
+            Lanc += r * r;
+            if (out) out[10] += l_anc * 2.0 * r * invN;
+        }
+        for (int j = 0; j < 3; ++j)
+            for (int m = j + 1; m < 3; ++m) {
+                const double dlt = q[3 + j] - q[3 + m];
+                const double u = fabs(dlt) - ln_r;
+                if (u > 0.0) {
+                    Lan += u * u;
+                    if (out) {
+                        const double g = l_a * 2.0 * u * invN * (dlt > 0.0 ? 1.0 : -1.0);
+                        out[3 + j] += g;
+                        out[3 + m] -= g;
+                    }
+                }
+            }
+        for (int j = 0; j < 3; ++j) {
+            const double u = q[3 + j] - ln_hi, w2 = ln_lo - q[3 + j];
+            if (u > 0.0) { Lcap += u * u; if (out) out[3 + j] += l_s * 2.0 * u * invN; }
+            if (w2 > 0.0) { Lcap += w2 * w2; if (out) out[3 + j] -= l_s * 2.0 * w2 * invN; }
+        }
+    }
+    Lanc *= invN;
+    Lan *= invN;
+    Lcap *= invN;
+    if (terms) {
+        terms[0] = Lval; terms[1] = Lrho; terms[2] = Lsm; terms[3] = Lanc; terms[4] = Lan; terms[5] = Lcap;
+    }
+    free(A); free(Pc); free(num); free(den); free(gn); free(gd);
+    return Lval + l_rho * Lrho + l_sm * Lsm + l_anc * Lanc + l_a * Lan + l_s * Lcap;
+}
+
+/* Regularised stratified-sample refinement.  regp[11] = {l_rho, l_sm0,
+ * l_sm1, anneal_iters, l_anc, l_aniso, l_cap, r_max, s_lo, s_hi, radius}:
+ * iteration t (index step0 + t) draws its samples, their partners when
+ * l_sm0 > 0, takes L with l_sm = or_lambda_sm(l_sm0, l_sm1, anneal,
+ * step0 + t), then one Adam step; losses[t] = L. */
+int or_refine_sampled_reg(double* prm, int64_t n, const float* field, const int dims[3], int64_t S, uint64_t seed,
+                          int step0, float k, double rho0, double occ, int iters, double lr, double b1, double b2,
+                          double eps, const double* regp, double* losses)
+{
+    int64_t nh, nm;
+    or_sample_classes(field, dims, NULL, &nh, NULL, &nm);
+    int64_t* hi = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nh > 0 ? nh : 1));
+    int64_t* mid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm > 0 ? nm : 1));
+    float* pts = (float*)malloc(sizeof(float) * 6 * (size_t)S);
+    float* vals = (float*)malloc(sizeof(float) * (size_t)S);
+    double* g = (double*)malloc(sizeof(double) * 12 * (size_t)(n > 0 ? n : 1));
+    double* m = (double*)calloc(12 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    double* v = (double*)calloc(12 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!hi || !mid || !pts || !vals || !g || !m || !v) return 1;
+    or_sample_classes(field, dims, hi, &nh, mid, &nm);
+    const int smooth = regp[1] > 0.0;
+    for (int t = 0; t < iters; ++t) {
+        const int step = step0 + t;
+        or_draw_samples(field, dims, hi, nh, mid, nm, S, seed, (uint32_t)step, pts, vals, NULL);
+        if (smooth) or_draw_partners(pts, S, dims, seed, (uint32_t)step, (float)regp[10], pts + 3 * S);
+        const double reg[8] = {regp[0], or_lambda_sm(regp[1], regp[2], (int)regp[3], step), regp[4], regp[5],
+                               regp[6], regp[7], regp[8], regp[9]};
+        const double L = or_sample_objective(prm, n, pts, vals, S, smooth, field, dims, reg, k, rho0, occ, g, NULL);
+        if (losses) losses[t] = L;
+        or_adam(prm, m, v, g, 12 * n, step + 1, lr, b1, b2, eps);
+    }
+    free(hi); free(mid); free(pts); free(vals); free(g); free(m); free(v);
+    return 0;
+}
+
 /* Stratified-sample refinement: iteration t draws its S points (iteration
  * index step0 + t), takes the sampled loss and gradient, then one Adam
  * step; losses[t] receives the sampled loss.  prm is updated in place. */

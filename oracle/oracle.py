@@ -92,6 +92,15 @@ def lib():
             L.or_refine_sampled.restype = i32
             L.or_kept_submasks.argtypes = [P, P, f32, i32, i64, P, P, P]
             L.or_kept_submasks.restype = None
+            L.or_draw_partners.argtypes = [P, i64, P, u64, u32, f32, P]
+            L.or_draw_partners.restype = None
+            L.or_lambda_sm.argtypes = [f64, f64, i32, i32]
+            L.or_lambda_sm.restype = f64
+            L.or_sample_objective.argtypes = [P, i64, P, P, i64, i32, P, P, P, f32, f64, f64, P, P]
+            L.or_sample_objective.restype = f64
+            L.or_refine_sampled_reg.argtypes = [P, i64, P, P, i64, u64, i32, f32, f64, f64, i32, f64, f64, f64, f64,
+                                                P, P]
+            L.or_refine_sampled_reg.restype = i32
             L.or_ray_setup.argtypes = [P, i32, i32, i32, i32, P, P, P, P]
             L.or_ray_setup.restype = i32
             L.or_field_at.argtypes = [P, i64, f32, f64, i32, P, P, P, P]
@@ -412,6 +421,63 @@ def refine_sampled(prm, field, iters, S=3072, seed=0, step0=0, lr=1e-2, b1=0.9, 
                                  float(eps), _ptr(losses))
     if st != 0:
         raise RuntimeError("oracle sampled refinement failed")
+    return p, losses[:iters]
+
+
+# --------------------------------------------------------------------------
+# The full objective (Sec. III-F): value term plus five regularisers
+# --------------------------------------------------------------------------
+def draw_partners(pts, dims_zyx, seed, it, radius=1.0):
+    """Jittered partners (float32, clamped to the grid) of the points
+    pts (S, 3): Philox stream 5, counter (j, it)."""
+    q = np.ascontiguousarray(np.asarray(pts, np.float32).reshape(-1, 3))
+    nz, ny, nx = dims_zyx
+    out = np.zeros_like(q)
+    lib().or_draw_partners(_ptr(q), q.shape[0], _ptr(np.array([nx, ny, nz], np.int32)), int(seed), int(it),
+                           float(radius), _ptr(out))
+    return out
+
+
+def lambda_sm(l0, l1, anneal, t):
+    return lib().or_lambda_sm(float(l0), float(l1), int(anneal), int(t))
+
+
+def sample_objective(prm, pts, vals, field=None, reg=None, smooth=False, k=3.0, rho0=0.05, occ=0.02,
+                     want_grad=True):
+    """(L, grad, terms) of the regularised sampled objective.  pts holds S
+    samples and, with smooth, their S partners after them.  reg = dict with
+    rho, sm (this iteration's weight), anc, aniso, cap, r_max, s_lo, s_hi."""
+    q = _prm64(prm)
+    pt = np.ascontiguousarray(np.asarray(pts, np.float32).reshape(-1, 3))
+    vv = np.ascontiguousarray(np.asarray(vals, np.float32).ravel())
+    S = vv.size
+    r = dict(rho=0.0, sm=0.0, anc=0.0, aniso=0.0, cap=0.0, r_max=3.0, s_lo=0.3, s_hi=1e30)
+    r.update(reg or {})
+    regv = np.array([r["rho"], r["sm"], r["anc"], r["aniso"], r["cap"], r["r_max"], r["s_lo"], r["s_hi"]],
+                    np.float64)
+    f = None if field is None else _f32c(field)
+    g = np.zeros_like(q) if want_grad else None
+    terms = np.zeros(6, np.float64)
+    L = lib().or_sample_objective(_ptr(q), q.shape[0], _ptr(pt), _ptr(vv), S, int(bool(smooth)),
+                                  None if f is None else _ptr(f), None if f is None else _ptr(_dims(f)), _ptr(regv),
+                                  float(k), float(rho0), float(occ), None if g is None else _ptr(g), _ptr(terms))
+    return L, g, terms
+
+
+def refine_sampled_reg(prm, field, iters, reg, S=3072, seed=0, step0=0, lr=1e-2, b1=0.9, b2=0.999, eps=1e-15,
+                       k=3.0, rho0=0.05, occ=0.02):
+    """Regularised stratified-sample refinement; reg = dict with rho, sm0,
+    sm1, anneal, anc, aniso, cap, r_max, s_lo, s_hi, radius."""
+    p = _prm64(prm).copy()
+    f = _f32c(field)
+    regp = np.array([reg["rho"], reg["sm0"], reg["sm1"], reg["anneal"], reg["anc"], reg["aniso"], reg["cap"],
+                     reg["r_max"], reg["s_lo"], reg["s_hi"], reg["radius"]], np.float64)
+    losses = np.zeros(max(iters, 1), np.float64)
+    st = lib().or_refine_sampled_reg(_ptr(p), p.shape[0], _ptr(f), _ptr(_dims(f)), int(S), int(seed), int(step0),
+                                     float(k), float(rho0), float(occ), int(iters), float(lr), float(b1), float(b2),
+                                     float(eps), _ptr(regp), _ptr(losses))
+    if st != 0:
+        raise RuntimeError("oracle regularised refinement failed")
     return p, losses[:iters]
 
 

@@ -1094,3 +1094,108 @@ def test_render_candidate_index_drops_nothing():
                     k += 1
             np.testing.assert_allclose(img[j, i], [*C, 1.0 - Tr], rtol=1e-12, atol=1e-14)
     assert tot == kept and kept > 0
+
+
+# --------------------------------------------------------------------------
+# Full objective (Sec. III-F): value term plus the five regularisers
+# --------------------------------------------------------------------------
+def _one_gaussian(mu=(5.0, 6.0, 7.0), logs=(0.0, 0.0, 0.0), a=0.7, w_logit=0.0):
+    p = np.zeros((1, 12))
+    p[0, :3] = mu
+    p[0, 3:6] = logs
+    p[0, 6] = 1.0
+    p[0, 10] = a
+    p[0, 11] = w_logit
+    return p
+
+
+def test_regulariser_closed_forms():
+    far = np.array([[50.0, 50.0, 50.0]], np.float32)     # a sample no Gaussian reaches
+    v0 = np.array([0.0], np.float32)
+    # anisotropy: log-scales (0, 0, ln 4) exceed 3:1 on two axis pairs
+    p = _one_gaussian(logs=(0.0, 0.0, np.log(4.0)))
+    u = np.log(4.0) - np.log(3.0)
+    L, g, t = O.sample_objective(p, far, v0, reg=dict(aniso=0.5), k=3.0)
+    assert t[4] == pytest.approx(2 * u * u, rel=1e-12) and L == pytest.approx(0.5 * 2 * u * u, rel=1e-12)
+    np.testing.assert_allclose(g[0, 3:6], 0.5 * 2 * u * np.array([-1.0, -1.0, 2.0]), rtol=1e-12)
+    # scale cap: s = 0.1 below s_lo = 0.3, s = 20 above s_hi = 10
+    p = _one_gaussian(logs=(np.log(0.1), 0.0, np.log(20.0)))
+    L, g, t = O.sample_objective(p, far, v0, reg=dict(cap=0.25, s_lo=0.3, s_hi=10.0, r_max=1e9), k=3.0)
+    assert t[5] == pytest.approx(np.log(3.0) ** 2 + np.log(2.0) ** 2, rel=1e-12)
+    np.testing.assert_allclose(g[0, 3:6], 0.25 * 2 * np.array([-np.log(3.0), 0.0, np.log(2.0)]), rtol=1e-12)
+    # anchor: the Gaussian sits on voxel (5, 6, 7) of a field, gradient into a only
+    field = np.random.default_rng(1).uniform(0, 1, (12, 11, 10)).astype(np.float32)
+    p = _one_gaussian(a=0.9)
+    L, g, t = O.sample_objective(p, far, v0, field=field, reg=dict(anc=2.0), k=3.0)
+    r = 0.9 - float(field[7, 6, 5])
+    assert t[3] == pytest.approx(r * r, rel=1e-12)
+    assert g[0, 10] == pytest.approx(2.0 * 2 * r, rel=1e-12)
+    np.testing.assert_array_equal(g[0, :10], 0.0)
+    # density: one occupied sample at the centre has rho = w (and Vt = a)
+    p = _one_gaussian(a=0.6, w_logit=0.5)
+    w = 1.0 / (1.0 + np.exp(-0.5))
+    at = np.array([[5.0, 6.0, 7.0]], np.float32)
+    L, g, t = O.sample_objective(p, at, np.array([0.6], np.float32), reg=dict(rho=1.0), k=3.0)
+    r0 = 0.6 - float(np.float32(0.6))                      # the target is float32
+    assert t[0] == pytest.approx(r0 * r0, rel=1e-9) and t[1] == pytest.approx((w - 1.0) ** 2, rel=1e-12)
+    # smoothness: partner one voxel along x from the centre (unit scales)
+    pair = np.array([[5.0, 6.0, 7.0], [6.0, 6.0, 7.0]], np.float32)
+    L, g, t = O.sample_objective(p, pair, np.array([0.0], np.float32), reg=dict(sm=1.0), smooth=True, k=3.0)
+    assert t[2] == pytest.approx((w - w * np.exp(-0.5)) ** 2, rel=1e-12)
+
+
+def test_objective_gradient_central_differences():
+    """Every term but the anchor (whose target V(mu) carries no gradient by
+    the reading) against central differences of L; k = 20 so membership
+    does not move."""
+    from paper_2608_14112_b300 import inputs
+    V = inputs.grf((16, 18, 20), seed=4)
+    rng = np.random.default_rng(7)
+    n = 30
+    prm = np.zeros((n, 12))
+    prm[:, :3] = rng.uniform(2, 13, (n, 3))
+    prm[:, 3:6] = np.log(rng.lognormal(np.log(1.5), 0.6, (n, 3)))
+    prm[:, 6:10] = rng.normal(size=(n, 4))
+    prm[:, 10] = rng.uniform(0.1, 1.0, n)
+    prm[:, 11] = rng.uniform(-2, 2, n)
+    pts, vals, _ = O.draw_samples(V, 96, seed=3, it=2)
+    both = np.concatenate([pts, O.draw_partners(pts, V.shape, seed=3, it=2, radius=1.0)])
+    reg = dict(rho=0.3, sm=0.7, anc=0.0, aniso=0.2, cap=0.4, r_max=2.0, s_lo=0.8, s_hi=2.5)
+    L, g, _ = O.sample_objective(prm, both, vals, reg=reg, smooth=True, k=20.0)
+    h = 1e-6
+    for i, j in [(0, 0), (3, 2), (5, 3), (7, 4), (9, 5), (11, 6), (13, 8), (17, 9), (19, 10), (23, 11), (29, 1)]:
+        e = np.zeros_like(prm)
+        e[i, j] = h
+        fd = (O.sample_objective(prm + e, both, vals, reg=reg, smooth=True, k=20.0, want_grad=False)[0]
+              - O.sample_objective(prm - e, both, vals, reg=reg, smooth=True, k=20.0, want_grad=False)[0]) / (2 * h)
+        assert g[i, j] == pytest.approx(fd, rel=2e-5, abs=1e-10), (i, j)
+
+
+def test_smoothness_schedule_and_partners():
+    assert O.lambda_sm(1e-2, 1e-4, 100, 0) == pytest.approx(1e-2, rel=1e-15)
+    assert O.lambda_sm(1e-2, 1e-4, 100, 50) == pytest.approx(1e-3, rel=1e-12)
+    assert O.lambda_sm(1e-2, 1e-4, 100, 400) == pytest.approx(1e-4, rel=1e-15)
+    assert O.lambda_sm(1e-2, 1e-4, 0, 50) == 1e-2
+    from scipy import stats
+    rng = np.random.default_rng(2)
+    pts = rng.uniform(3, 17, (4000, 3)).astype(np.float32)
+    q = O.draw_partners(pts, (20, 20, 20), seed=9, it=4, radius=1.5)
+    d = (q - pts).astype(np.float64)
+    assert np.abs(d).max() <= 1.5
+    assert stats.kstest(d.ravel(), stats.uniform(loc=-1.5, scale=3.0).cdf).pvalue > 1e-3
+    edge = np.zeros((50, 3), np.float32)
+    assert O.draw_partners(edge, (20, 20, 20), seed=9, it=4).min() >= 0.0
+    assert not np.array_equal(q, O.draw_partners(pts, (20, 20, 20), seed=9, it=5, radius=1.5))
+
+
+def test_regularised_refinement_reduces_to_plain():
+    from paper_2608_14112_b300 import inputs
+    V = inputs.blobs(24, seed=4)
+    prm, _, _, status = O.allocate(V, 150, seed=1)
+    assert status == 0
+    zero = dict(rho=0.0, sm0=0.0, sm1=0.0, anneal=0, anc=0.0, aniso=0.0, cap=0.0, r_max=3.0, s_lo=0.3,
+                s_hi=1.5, radius=1.0)
+    a, la = O.refine_sampled_reg(prm, V, 4, zero, S=256, seed=5)
+    b, lb = O.refine_sampled(prm, V, 4, S=256, seed=5)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(la, lb)

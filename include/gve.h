@@ -324,25 +324,65 @@ GVE_API gve_status gve_structure_stats(gve_ctx* ctx, const float* field_dev, gve
 GVE_API gve_status gve_draw_samples(gve_ctx* ctx, const float* field_dev, gve_dims dims, int64_t S,
                                     uint64_t seed, uint32_t iter, float* pts_out_dev, int64_t* vox_out_dev,
                                     void* stream);
-/* Eq. 3, the sampled value loss and (grad_out != NULL) its gradient
- * [n][12] at caller-given points pts [S][4] (x, y, z, target).  loss_dev
- * (device double) and vt_out [S] (Vt per point) are optional. */
+/* The full objective (Sec. III-F): L = L_val + lambda_rho L_rho + lambda_sm
+ * L_sm + lambda_anc L_anc + lambda_aniso L_aniso + lambda_cap L_cap.  The
+ * paper names the five regularisers and their purpose but gives neither
+ * formulas nor weights; the forms are these readings:
+ *   L_rho   = (1/S) sum_s 1[v_s > occ] (rho(p_s) - 1)^2, rho = sum w G (the
+ *             denominator of Eq. 3 before the floor): density toward one
+ *             over occupied space, from both sides;
+ *   L_sm    = (1/S) sum_s (rho(p_s) - rho(p'_s))^2, p'_s the partner of p_s:
+ *             u = (x >> 8) 2^-24 - 1/2 per axis from the Philox4x32-10 words
+ *             of counter (s, t, 5, 'GVE1'), p' = clamp(p + 2 radius u, 0,
+ *             n - 1) in float32; its weight decays geometrically from
+ *             lambda_sm to lambda_sm_end over anneal_iters iterations;
+ *   L_anc   = (1/N) sum_i (a_i - V(mu_i))^2, V trilinear (FP64,
+ *             edge-clamped); the gradient flows into a_i only;
+ *   L_aniso = (1/N) sum_i sum_{j<k} relu(|l_ij - l_ik| - ln aniso_max)^2
+ *             over the log-scales l (elongation bounded at aniso_max : 1);
+ *   L_cap   = (1/N) sum_i sum_j relu(l_ij - ln s_hi)^2 + relu(ln s_lo -
+ *             l_ij)^2 (s_hi <= 0: the allocator's cap, longest axis / 16).
+ * With lambda_sm > 0 the partners double the points: S <= 4096.  A NULL
+ * option pointer means the value term alone. */
+typedef struct {
+    float lambda_rho;
+    float lambda_sm, lambda_sm_end;
+    int32_t anneal_iters;
+    float lambda_anc, lambda_aniso, lambda_cap;
+    float partner_radius;  /* voxels */
+    float aniso_max;
+    float s_lo, s_hi;      /* voxels */
+} gve_reg_opts;
+
+/* Smoothness partners of caller-given points pts [S][4] for iteration
+ * `iter`: out [S][4] = (x', y', z', -1) (no target), 16-byte aligned. */
+GVE_API gve_status gve_draw_partners(gve_ctx* ctx, const float* pts_dev, int64_t S, gve_dims dims, uint64_t seed,
+                                     uint32_t iter, float radius, float* out_dev, void* stream);
+
+/* Eq. 3, the sampled objective and (grad_out != NULL) its gradient [n][12]
+ * at caller-given points pts [S][4] (x, y, z, target), followed by their S
+ * partners when reg->lambda_sm > 0 (the weight of this step).  field_dev is
+ * needed when lambda_anc > 0.  loss_dev (device double: L), terms_dev
+ * (device double[6]: L_val, L_rho, L_sm, L_anc, L_aniso, L_cap unweighted)
+ * and vt_out [S] (Vt per sample) are optional. */
 GVE_API gve_status gve_sample_loss_grad(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
                                         const gve_eval_opts* opts, const float* pts_dev, int64_t S,
-                                        float occ_thresh, float* grad_out_dev, double* loss_dev,
+                                        float occ_thresh, const gve_reg_opts* reg, const float* field_dev,
+                                        float* grad_out_dev, double* loss_dev, double* terms_dev,
                                         float* vt_out_dev, void* stream);
-/* sched->iters iterations of draw -> sampled loss and gradient -> Adam on
- * every primitive (iteration index sched->step0 + t selects the points and
- * the bias correction).  adam_state and loss_trace_dev as for gve_refine
- * (the trace receives the sampled losses).  stats (optional) adds one
- * full-grid evaluation after the last step for sse_final / psnr_final;
- * ms_total is the iterations' time, ms_bin its preparation share (keep
- * coefficients) and ms_brick its draw, search, loss and gradient share
- * (the chain rule and Adam are the rest). */
+/* sched->iters iterations of draw (and partners) -> sampled objective and
+ * gradient -> Adam on every primitive (iteration index sched->step0 + t
+ * selects the points, the smoothness weight and the bias correction).
+ * reg (nullable) adds the regularisers.  adam_state and loss_trace_dev as
+ * for gve_refine (the trace receives the objective per iteration).  stats
+ * (optional) adds one full-grid evaluation after the last step for
+ * sse_final / psnr_final; ms_total is the iterations' time, ms_bin its
+ * preparation share (keep coefficients) and ms_brick its draw, search, loss
+ * and gradient share (the chain rule and Adam are the rest). */
 GVE_API gve_status gve_refine_sampled(gve_ctx* ctx, float* prims_dev, int64_t n, const float* field_dev,
                                       gve_dims dims, const gve_schedule* sched, int64_t S, uint64_t seed,
-                                      float* adam_state_dev, double* loss_trace_dev, gve_stats* stats,
-                                      void* stream);
+                                      const gve_reg_opts* reg, float* adam_state_dev, double* loss_trace_dev,
+                                      gve_stats* stats, void* stream);
 
 /* ---- mixture-field ray marcher (Sec. III-A, rendering of the encoded set)
  * Rendering applies a transfer function T = (c_T, alpha_T) to the value Eq. 3

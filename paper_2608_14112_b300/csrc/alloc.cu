@@ -799,6 +799,125 @@ void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigne
 }
 
 // ------------------------------------------------------------------------
+// The full objective (Sec. III-F): smoothness partners and the per-Gaussian
+// regularisers (anchor, anisotropy, scale cap).  The paper gives the terms
+// in words; the forms here are the readings:
+//   partner of sample j of iteration t: u = (x >> 8) 2^-24 - 1/2 per axis
+//     from Philox4x32-10 stream 5, counter (j, t), p' = clamp(p + 2 r u,
+//     0, n - 1) in float32;
+//   L_anc   = (1/N) sum (a_i - V(mu_i))^2, V the FP64 trilinear value,
+//             gradient into a_i only;
+//   L_aniso = (1/N) sum_i sum_{j<k} relu(|l_ij - l_ik| - ln r_max)^2 over
+//             the log-scales l;
+//   L_cap   = (1/N) sum_i sum_j relu(l_ij - ln s_hi)^2 + relu(ln s_lo - l_ij)^2.
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kPartnerStream = 5u;
+
+__global__ void __launch_bounds__(128) k_draw_partners(const float4* __restrict__ pts, long long S, int nx, int ny,
+                                                       int nz, unsigned long long seed, uint32_t iter, float radius,
+                                                       float4* __restrict__ out)
+{
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= S) return;
+    uint32_t r[4];
+    draw(((unsigned long long)iter << 32) | (unsigned long long)(uint32_t)j, kPartnerStream, seed, r);
+    const float span = 2.0f * radius;
+    const float4 p = pts[j];
+    const float q[3] = {p.x, p.y, p.z};
+    const int dims[3] = {nx, ny, nz};
+    float o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u = (float)(r[a] >> 8) * 0x1p-24f - 0.5f;
+        float v = q[a] + u * span;
+        const float hi = (float)(dims[a] - 1);
+        v = v < 0.0f ? 0.0f : (v > hi ? hi : v);
+        o[a] = v;
+    }
+    out[j] = make_float4(o[0], o[1], o[2], -1.0f);  // no target: outside the value and density terms
+}
+
+__global__ void __launch_bounds__(256) k_reg(const float* __restrict__ prims, long long n, const float* __restrict__ V,
+                                             int nx, int ny, int nz, RegTerms rt, double invN,
+                                             float* __restrict__ extra, double* __restrict__ terms,
+                                             double* total_a, double* total_b)
+{
+    double sa = 0.0, sn = 0.0, sc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
+        const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
+        const float p[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
+        bool ok = true;
+        for (int j = 0; j < 12; ++j) ok = ok && isfinite(p[j]);
+        const double nq2 = (double)p[6] * p[6] + (double)p[7] * p[7] + (double)p[8] * p[8] + (double)p[9] * p[9];
+        ok = ok && nq2 > 0.0;
+        float g[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ok) {
+            if (rt.l_anc != 0.f && V) {
+                const double r = (double)p[10] - trilinear(V, nx, ny, nz, (double)p[0], (double)p[1], (double)p[2]);
+                sa += r * r;
+                g[10] = (float)((double)rt.l_anc * 2.0 * r * invN);
+            }
+            double gl[3] = {0.0, 0.0, 0.0};
+            for (int j = 0; j < 3; ++j)
+                for (int m = j + 1; m < 3; ++m) {
+                    const double dlt = (double)p[3 + j] - (double)p[3 + m];
+                    const double u = fabs(dlt) - rt.ln_r;
+                    if (u > 0.0) {
+                        sn += u * u;
+                        const double gg = (double)rt.l_aniso * 2.0 * u * invN * (dlt > 0.0 ? 1.0 : -1.0);
+                        gl[j] += gg;
+                        gl[m] -= gg;
+                    }
+                }
+            for (int j = 0; j < 3; ++j) {
+                const double u = (double)p[3 + j] - rt.ln_hi, w2 = rt.ln_lo - (double)p[3 + j];
+                if (u > 0.0) { sc += u * u; gl[j] += (double)rt.l_cap * 2.0 * u * invN; }
+                if (w2 > 0.0) { sc += w2 * w2; gl[j] -= (double)rt.l_cap * 2.0 * w2 * invN; }
+            }
+            for (int j = 0; j < 3; ++j) g[3 + j] = (float)gl[j];
+        }
+        float4* e4 = reinterpret_cast<float4*>(extra) + 3 * i;
+        e4[0] = make_float4(g[0], g[1], g[2], g[3]);
+        e4[1] = make_float4(g[4], g[5], g[6], g[7]);
+        e4[2] = make_float4(g[8], g[9], g[10], g[11]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(terms + 3, sa * invN);
+        atomicAdd(terms + 4, sn * invN);
+        atomicAdd(terms + 5, sc * invN);
+        const double t = ((double)rt.l_anc * sa + (double)rt.l_aniso * sn + (double)rt.l_cap * sc) * invN;
+        if (total_a) atomicAdd(total_a, t);
+        if (total_b) atomicAdd(total_b, t);
+    }
+}
+
+}  // namespace
+
+void launch_draw_partners(const float4* pts, long long S, gve_dims d, unsigned long long seed, uint32_t iter,
+                          float radius, float4* out, cudaStream_t s)
+{
+    if (S <= 0) return;
+    k_draw_partners<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(pts, S, d.nx, d.ny, d.nz, seed, iter, radius, out);
+}
+
+void launch_reg(const float* prims, long long n, const float* V, gve_dims d, const RegTerms& r, float* extra,
+                double* terms, double* total_a, double* total_b, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const long long b = (n + 255) / 256;
+    const unsigned grid = (unsigned)(b < 148 * 16 ? b : 148 * 16);
+    k_reg<<<grid, 256, 0, s>>>(prims, n, V, d.nx, d.ny, d.nz, r, 1.0 / (double)n, extra, terms, total_a, total_b);
+}
+
+// ------------------------------------------------------------------------
 // Pre-encoding structure statistics (Sec. V-F, Table VI): occupancy, the
 // share of the occupied voxels' gradient-magnitude mass held by the largest
 // K = ceil(n_occ / 10), and S(1) / S(16) of the second-order structure

@@ -98,6 +98,7 @@ struct gve_ctx {
     // offsets, samples, cell table, sorted sample order, per-sample sums and
     // upstream gradients, loss
     gve::Buf s_hi, s_mid, s_cnt, s_off, s_pts, s_cell, s_order, s_nd, s_gg, s_loss;
+    gve::Buf s_inv, s_ex, s_terms;   // sorted position of each point, regulariser gradient, loss terms
     unsigned long long s_nh = 0, s_nm = 0;
     // ray marcher: keep coefficients, per-Gaussian cell counts and offsets,
     // (cell, Gaussian) pairs and their sort buffers, per-cell ranges, the
@@ -238,8 +239,11 @@ struct AdamArgs {
 };
 // chain rule from accumulators to raw-record gradients; either writes grad
 // (grad != nullptr) or applies Adam in place (prims, m, v).  Zeroes acc.
+// extra (nullable) [n][12]: a raw-record gradient added before the output or
+// the Adam step (the per-Gaussian regularisers)
 void launch_chain(const float* acc_in, float* acc_zero, float* prims, long long n, float* grad,
-                  float* m, float* v, const AdamArgs* adam, const DevState* st, cudaStream_t s);
+                  float* m, float* v, const AdamArgs* adam, const DevState* st, cudaStream_t s,
+                  const float* extra = nullptr);
 
 // ---- allocator (alloc.cu) ------------------------------------------------
 gve_status allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget,
@@ -256,6 +260,19 @@ gve_status sample_classes(gve_ctx* c, const float* V, gve_dims d, cudaStream_t s
 void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigned long long nh, const uint32_t* mid,
                          unsigned long long nm, long long S, long long s_hi, long long s_mid,
                          unsigned long long seed, uint32_t iter, float4* pts, long long* vox, cudaStream_t s);
+
+// ---- full objective: smoothness partners, per-Gaussian terms (alloc.cu) ----
+void launch_draw_partners(const float4* pts, long long S, gve_dims d, unsigned long long seed, uint32_t iter,
+                          float radius, float4* out, cudaStream_t s);
+struct RegTerms {
+    float l_anc, l_aniso, l_cap;
+    double ln_r, ln_lo, ln_hi;
+};
+// extra [n][12]: the raw-record gradient of the anchor, anisotropy and cap
+// terms (a and log-scales only); terms[3..5] += the unweighted terms;
+// total_a / total_b (nullable) += their weighted sum
+void launch_reg(const float* prims, long long n, const float* V, gve_dims d, const RegTerms& r, float* extra,
+                double* terms, double* total_a, double* total_b, cudaStream_t s);
 
 // ---- pre-encoding structure statistics (alloc.cu) --------------------------
 // out = {occupancy, top-10 % gradient-mass share, S(1), S(16), S(1)/S(16)};

@@ -12,7 +12,9 @@
 //   dL/dR       = 2 S2 R diag(s^-2)  -> dL/dq_hat -> dL/dq through q/|q|
 // then either written out (gradient calls) or fed to Adam with bias
 // correction (Kingma and Ba), in place on the record and its two moments.
-// The accumulators are zeroed for the next iteration in the same pass.
+// The accumulators are zeroed for the next iteration in the same pass.  An
+// optional raw-record gradient (the per-Gaussian regularisers of the full
+// objective) is added before the output or the Adam step.
 #include "gve_int.cuh"
 
 namespace gve {
@@ -21,7 +23,7 @@ namespace gve {
 __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero,
                                                float* __restrict__ prims, long long n, float* __restrict__ grad,
                                                float* __restrict__ m, float* __restrict__ v, AdamArgs ad,
-                                               int do_adam, const DevState* st)
+                                               int do_adam, const DevState* st, const float* __restrict__ extra)
 {
     if (st && st->overflow) return;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,6 +115,13 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
         gr[10] = w * A;
         gr[11] = H * w * (1.f - w);
     }
+    if (extra) {
+        const float4* x4 = reinterpret_cast<const float4*>(extra) + 3 * i;
+        const float4 x0 = x4[0], x1 = x4[1], x2 = x4[2];
+        const float xs[12] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y, x2.z, x2.w};
+#pragma unroll
+        for (int j = 0; j < 12; ++j) gr[j] += xs[j];
+    }
 
     if (!do_adam) {
         float4* g4 = reinterpret_cast<float4*>(grad) + 3 * i;
@@ -148,13 +157,13 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
 }
 
 void launch_chain(const float* acc_in, float* acc_zero, float* prims, long long n, float* grad, float* m,
-                  float* v, const AdamArgs* adam, const DevState* st, cudaStream_t s)
+                  float* v, const AdamArgs* adam, const DevState* st, cudaStream_t s, const float* extra)
 {
     if (n <= 0) return;
     AdamArgs ad{};
     if (adam) ad = *adam;
     k_chain<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(acc_in, acc_zero, prims, n, grad, m, v, ad,
-                                                         adam != nullptr, st);
+                                                         adam != nullptr, st, extra);
 }
 
 }  // namespace gve

@@ -60,12 +60,14 @@ __device__ __forceinline__ int cell_of(float p, int n, int shift, int nc)
 }
 
 // One CTA: sort the S points by cell (bitonic over the next power of two),
-// write the sorted points, their original indices, and cstart[c] for every
-// cell c = 0 .. ncells (binary search of the sorted cells).
+// write the sorted points, their original indices, the sorted position of
+// each original index, and cstart[c] for every cell c = 0 .. ncells (binary
+// search of the sorted cells).
 __global__ void __launch_bounds__(kCellSortThreads) k_cell_sort(const float4* __restrict__ pts, int S, int nx,
                                                                  int ny, int nz, CellGrid cg,
                                                                  float4* __restrict__ spts,
-                                                                 uint32_t* __restrict__ order, uint32_t* __restrict__ cstart)
+                                                                 uint32_t* __restrict__ order, uint32_t* __restrict__ inv,
+                                                                 uint32_t* __restrict__ cstart)
 {
     extern __shared__ unsigned long long sk[];
     int P = 1;
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(kCellSortThreads) k_cell_sort(const float4* __
     for (int i = threadIdx.x; i < S; i += kCellSortThreads) {
         const uint32_t idx = (uint32_t)sk[i];
         order[i] = idx;
+        inv[idx] = (uint32_t)i;
         spts[i] = pts[idx];
     }
     const long long ncells = (long long)cg.ncx * cg.ncy * cg.ncz;
@@ -223,37 +226,75 @@ __global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
     o[2] = make_float4(S2[3], S2[4], S2[5], 0.f);
 }
 
-// One CTA: Vt = num / max(den, rho0), the masked value loss (1 / S) sum
-// 1[v > occ] (Vt - v)^2 (FP64 sum), and the upstream pair (dL/dnum, dL/dden)
-// per sorted point; vt_out (optional) by original index.
+// One CTA: Vt = num / max(den, rho0) at each drawn sample and the terms of
+// the objective that live at points, as FP64 sums: the masked value loss
+// (1/S) sum 1[v > occ] (Vt - v)^2, the density term (1/S) sum 1[v > occ]
+// (den - 1)^2 (den = rho = sum w G) and, with partners (the partner of
+// sample j has original index S + j), the smoothness term (1/S) sum (den -
+// den')^2.  Writes the upstream pair (dL/dnum, dL/dden) of every sorted
+// point (a sample writes its partner's), the weighted total to loss and
+// trace[iter], the unweighted terms to terms[0..2] (terms[3..5] cleared for
+// the per-Gaussian terms), and vt_out (optional) by original index.
 __global__ void __launch_bounds__(1024) k_sample_loss(const float4* __restrict__ spts, const uint32_t* __restrict__ order,
-                                                      const float2* __restrict__ nd, int S, float rho0, float occ,
+                                                      const uint32_t* __restrict__ inv, const float2* __restrict__ nd,
+                                                      int S, int smooth, float rho0, float occ, float l_rho, float l_sm,
                                                       float2* __restrict__ gg, double* loss, double* trace, int iter,
-                                                      float* vt_out)
+                                                      float* vt_out, double* terms)
 {
-    __shared__ double part[32];
-    double acc = 0.0;
+    __shared__ double part[3][32];
+    double av = 0.0, ar = 0.0, as = 0.0;
     const float inv2 = 2.f / (float)S;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int P = smooth ? 2 * S : S;
+    for (int s = threadIdx.x; s < P; s += blockDim.x) {
+        const uint32_t o = order[s];
+        if ((int)o >= S) continue;  // a partner: its sample writes it
         const float4 q = spts[s];
         const float2 v = nd[s];
         const float dd = fmaxf(v.y, rho0);
         const float vt = v.x / dd;
-        const float r = q.w > occ ? vt - q.w : 0.f;
-        acc += (double)r * (double)r;
+        const bool occd = q.w > occ;
+        const float r = occd ? vt - q.w : 0.f;
+        av += (double)r * (double)r;
         const float gn = inv2 * r / dd;
-        gg[s] = make_float2(gn, v.y >= rho0 ? -vt * gn : 0.f);
-        if (vt_out) vt_out[order[s]] = vt;
+        float gd = v.y >= rho0 ? -vt * gn : 0.f;
+        if (occd) {
+            const float e = v.y - 1.f;
+            ar += (double)e * (double)e;
+            gd += l_rho * inv2 * e;
+        }
+        if (smooth) {
+            const uint32_t pp = inv[o + S];
+            const float e = v.y - nd[pp].y;
+            as += (double)e * (double)e;
+            gd += l_sm * inv2 * e;
+            gg[pp] = make_float2(0.f, -l_sm * inv2 * e);
+        }
+        gg[s] = make_float2(gn, gd);
+        if (vt_out) vt_out[o] = vt;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+        av += __shfl_xor_sync(0xffffffffu, av, o);
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        as += __shfl_xor_sync(0xffffffffu, as, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[0][threadIdx.x >> 5] = av;
+        part[1][threadIdx.x >> 5] = ar;
+        part[2][threadIdx.x >> 5] = as;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        t /= (double)S;
-        if (loss) *loss = t;
-        if (trace) trace[iter] = t;
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int k = 0; k < 3; ++k) t[k] += part[k][w];
+        for (int k = 0; k < 3; ++k) t[k] /= (double)S;
+        const double tot = t[0] + (double)l_rho * t[1] + (double)l_sm * t[2];
+        if (loss) *loss = tot;
+        if (trace) trace[iter] = tot;
+        if (terms) {
+            terms[0] = t[0]; terms[1] = t[1]; terms[2] = t[2];
+            terms[3] = terms[4] = terms[5] = 0.0;
+        }
     }
 }
 
@@ -271,50 +312,68 @@ __global__ void __launch_bounds__(1024) k_sample_loss(const float4* __restrict__
 struct SampleBufs {
     CellGrid cg;
     long long ncells;
-    float4* pts;     // drawn (or caller's) points
+    float4* pts;     // drawn (or caller's) points, then their partners
     float4* spts;    // sorted by cell
     uint32_t* order;
+    uint32_t* inv;
     uint32_t* cstart;
     float2* nd;
     float2* gg;
     double* loss;
+    double* terms;
+    float* extra;
 };
 
-gve_status sample_bufs(gve_ctx* c, gve_dims d, long long S, long long n, SampleBufs& b, cudaStream_t s)
+// buffers for P points (samples and partners) and n records
+gve_status sample_bufs(gve_ctx* c, gve_dims d, long long P, long long n, SampleBufs& b, cudaStream_t s)
 {
     b.cg = make_cells(d);
     b.ncells = (long long)b.cg.ncx * b.cg.ncy * b.cg.ncz;
     const long long nn = n > 0 ? n : 1;
-    SMP_TRY(ensure(c, c->s_pts, sizeof(float4) * 2 * S, s));
-    SMP_TRY(ensure(c, c->s_order, sizeof(uint32_t) * S, s));
+    SMP_TRY(ensure(c, c->s_pts, sizeof(float4) * 2 * P, s));
+    SMP_TRY(ensure(c, c->s_order, sizeof(uint32_t) * P, s));
+    SMP_TRY(ensure(c, c->s_inv, sizeof(uint32_t) * P, s));
     SMP_TRY(ensure(c, c->s_cell, sizeof(uint32_t) * (b.ncells + 1), s));
-    SMP_TRY(ensure(c, c->s_nd, sizeof(float2) * S, s));
-    SMP_TRY(ensure(c, c->s_gg, sizeof(float2) * S, s));
+    SMP_TRY(ensure(c, c->s_nd, sizeof(float2) * P, s));
+    SMP_TRY(ensure(c, c->s_gg, sizeof(float2) * P, s));
     SMP_TRY(ensure(c, c->s_loss, sizeof(double), s));
+    SMP_TRY(ensure(c, c->s_terms, sizeof(double) * 8, s));
     SMP_TRY(ensure(c, c->rec, sizeof(float4) * 3 * nn, s));
     SMP_TRY(ensure(c, c->binrec, sizeof(BinRec) * nn, s));
     SMP_TRY(ensure(c, c->acc, sizeof(float) * 12 * nn, s));
+    SMP_TRY(ensure(c, c->s_ex, sizeof(float) * 12 * nn, s));
     b.pts = (float4*)c->s_pts.p;
-    b.spts = b.pts + S;
+    b.spts = b.pts + P;
     b.order = (uint32_t*)c->s_order.p;
+    b.inv = (uint32_t*)c->s_inv.p;
     b.cstart = (uint32_t*)c->s_cell.p;
     b.nd = (float2*)c->s_nd.p;
     b.gg = (float2*)c->s_gg.p;
     b.loss = (double*)c->s_loss.p;
+    b.terms = (double*)c->s_terms.p;
+    b.extra = (float*)c->s_ex.p;
     return GVE_OK;
 }
 
-// cells, forward and loss at the points in b.pts (the records prepared in
-// c->rec); with `backward` the Gaussians' sums are written to c->acc
+// weights of the point terms of one iteration
+struct PointReg {
+    float l_rho = 0.f, l_sm = 0.f;
+    int smooth = 0;
+};
+
+// cells, forward and loss at the S samples (and, with pr.smooth, their S
+// partners) in b.pts, the records prepared in c->rec; with `backward` the
+// Gaussians' sums are written to c->acc
 gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, const gve_eval_opts* o, long long S,
-                       const SampleBufs& b, float occ, double* trace, int iter, float* vt_out, bool backward,
-                       cudaStream_t s)
+                       const PointReg& pr, const SampleBufs& b, float occ, double* trace, int iter, float* vt_out,
+                       bool backward, cudaStream_t s)
 {
-    int P = 1;
-    while (P < S) P <<= 1;
-    k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P, s>>>(b.pts, (int)S, d.nx, d.ny, d.nz, b.cg,
-                                                                             b.spts, b.order, b.cstart);
-    SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * S, s), "memset sums");
+    const long long P = pr.smooth ? 2 * S : S;
+    int P2 = 1;
+    while (P2 < P) P2 <<= 1;
+    k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P2, s>>>(b.pts, (int)P, d.nx, d.ny, d.nz, b.cg,
+                                                                              b.spts, b.order, b.inv, b.cstart);
+    SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * P, s), "memset sums");
     SampleArgs a{};
     a.prims = prims;
     a.rec = (const float4*)c->rec.p;
@@ -322,7 +381,7 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
     a.cg = b.cg;
     a.cstart = b.cstart;
-    a.S = (int)S;
+    a.S = (int)P;
     a.spts = b.spts;
     a.nd = b.nd;
     a.gg = b.gg;
@@ -331,11 +390,52 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     a.T = (float)((double)o->trunc_k * (double)o->trunc_k * kNegHalfLog2e);
     const unsigned grid = (unsigned)((n + 127) / 128);
     if (n > 0) k_sample_eval<<<grid, 128, 0, s>>>(a);
-    k_sample_loss<<<1, 1024, 0, s>>>(b.spts, b.order, b.nd, (int)S, o->rho0, occ, b.gg, b.loss, trace, iter, vt_out);
+    k_sample_loss<<<1, 1024, 0, s>>>(b.spts, b.order, b.inv, b.nd, (int)S, pr.smooth, o->rho0, occ, pr.l_rho, pr.l_sm,
+                                     b.gg, b.loss, trace, iter, vt_out, b.terms);
     if (backward && n > 0) k_sample_grad<<<grid, 128, 0, s>>>(a);
     c->launches += 2 + (n > 0 ? 2 + (backward ? 1 : 0) : 0);
     SMP_CUDA(cudaGetLastError(), "launch (sampled pass)");
     return GVE_OK;
+}
+
+// the options of the full objective, checked; per-Gaussian weights and
+// their logarithmic bounds
+gve_status check_reg(gve_ctx* c, const gve_reg_opts* r, gve_dims d, const float* field, RegTerms& rt, bool& per_g)
+{
+    per_g = false;
+    rt = RegTerms{0.f, 0.f, 0.f, 0.0, 0.0, 0.0};
+    if (!r) return GVE_OK;
+    const float w[6] = {r->lambda_rho, r->lambda_sm, r->lambda_sm_end, r->lambda_anc, r->lambda_aniso, r->lambda_cap};
+    for (float x : w)
+        if (!(x >= 0.f) || !std::isfinite(x)) return fail(c, GVE_E_INVALID, "regulariser weights must be finite and >= 0");
+    if (r->anneal_iters < 0) return fail(c, GVE_E_INVALID, "negative annealing length");
+    if (r->lambda_sm > 0.f && (!(r->partner_radius > 0.f) || !std::isfinite(r->partner_radius)))
+        return fail(c, GVE_E_INVALID, "partner radius must be positive");
+    if (!(r->aniso_max >= 1.f) || !std::isfinite(r->aniso_max)) return fail(c, GVE_E_INVALID, "aniso_max must be >= 1");
+    const int mx = d.nx > d.ny ? (d.nx > d.nz ? d.nx : d.nz) : (d.ny > d.nz ? d.ny : d.nz);
+    const double s_hi = r->s_hi > 0.f ? (double)r->s_hi : (double)mx / 16.0;
+    if (!(r->s_lo > 0.f) || !((double)r->s_lo < s_hi)) return fail(c, GVE_E_INVALID, "need 0 < s_lo < s_hi");
+    if (r->lambda_anc > 0.f && !field) return fail(c, GVE_E_INVALID, "the anchor term needs the field");
+    rt.l_anc = r->lambda_anc;
+    rt.l_aniso = r->lambda_aniso;
+    rt.l_cap = r->lambda_cap;
+    rt.ln_r = std::log((double)r->aniso_max);
+    rt.ln_lo = std::log((double)r->s_lo);
+    rt.ln_hi = std::log(s_hi);
+    per_g = true;  // the unweighted terms are reported even where a weight is zero
+    return GVE_OK;
+}
+
+// lambda_sm of iteration t: geometric decay to lambda_sm_end over
+// anneal_iters iterations, then lambda_sm_end
+double lambda_sm_at(const gve_reg_opts* r, int t)
+{
+    if (!r) return 0.0;
+    const double l0 = r->lambda_sm, l1 = r->lambda_sm_end;
+    const int A = r->anneal_iters;
+    if (A <= 0 || !(l1 > 0.0) || !(l0 > 0.0)) return l0;
+    const double f = t < A ? (double)t / (double)A : 1.0;
+    return l0 * std::pow(l1 / l0, f);
 }
 
 // class lists of the field, then the split of S
@@ -347,9 +447,11 @@ gve_status sample_setup(gve_ctx* c, const float* field, gve_dims d, long long S,
     return GVE_OK;
 }
 
-gve_status check_samples(gve_ctx* c, int64_t S, const gve_eval_opts* o)
+gve_status check_samples(gve_ctx* c, int64_t S, const gve_eval_opts* o, bool smooth = false)
 {
     if (S < 1 || S > kMaxSamples) return fail(c, GVE_E_INVALID, "samples per iteration must be in [1, 8192]");
+    if (smooth && 2 * S > kMaxSamples)
+        return fail(c, GVE_E_INVALID, "with smoothness partners, samples per iteration must be in [1, 4096]");
     if (!o->normalized) return fail(c, GVE_E_INVALID, "sampled refinement evaluates Eq. 3 (normalized = 1)");
     static bool smem_set[64] = {};
     const int dev = c->device;
@@ -416,27 +518,60 @@ extern "C" gve_status gve_draw_samples(gve_ctx* c, const float* field, gve_dims 
     return GVE_OK;
 }
 
+extern "C" gve_status gve_draw_partners(gve_ctx* c, const float* pts, int64_t S, gve_dims d, uint64_t seed,
+                                        uint32_t iter, float radius, float* out, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!pts || !out) return fail(c, GVE_E_INVALID, "null argument");
+    if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
+    if (S < 1 || S > kMaxSamples) return fail(c, GVE_E_INVALID, "samples per iteration must be in [1, 8192]");
+    if (!(radius > 0.f) || !std::isfinite(radius)) return fail(c, GVE_E_INVALID, "partner radius must be positive");
+    if ((reinterpret_cast<uintptr_t>(pts) & 15u) || (reinterpret_cast<uintptr_t>(out) & 15u))
+        return fail(c, GVE_E_INVALID, "points must be 16-byte aligned");
+    SMP_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    c->launches = 1;
+    launch_draw_partners(reinterpret_cast<const float4*>(pts), S, d, seed, iter, radius, reinterpret_cast<float4*>(out),
+                         (cudaStream_t)stream);
+    SMP_CUDA(cudaGetLastError(), "launch (partners)");
+    return GVE_OK;
+}
+
 extern "C" gve_status gve_sample_loss_grad(gve_ctx* c, const float* prims, int64_t n, gve_dims d,
                                            const gve_eval_opts* o, const float* pts, int64_t S, float occ_thresh,
-                                           float* grad_out, double* loss_dev, float* vt_out, void* stream)
+                                           const gve_reg_opts* reg, const float* field, float* grad_out,
+                                           double* loss_dev, double* terms_dev, float* vt_out, void* stream)
 {
     SMP_TRY(check_common(c, prims, n, d, o));
-    SMP_TRY(check_samples(c, S, o));
+    PointReg pr;
+    pr.l_rho = reg ? reg->lambda_rho : 0.f;
+    pr.l_sm = reg ? reg->lambda_sm : 0.f;
+    pr.smooth = pr.l_sm > 0.f;
+    SMP_TRY(check_samples(c, S, o, pr.smooth != 0));
+    RegTerms rt;
+    bool per_g = false;
+    SMP_TRY(check_reg(c, reg, d, field, rt, per_g));
     if (!pts) return fail(c, GVE_E_INVALID, "null points");
     if ((reinterpret_cast<uintptr_t>(pts) & 15u) || (grad_out && (reinterpret_cast<uintptr_t>(grad_out) & 15u)))
         return fail(c, GVE_E_INVALID, "points and gradient must be 16-byte aligned");
     SMP_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
+    const long long P = pr.smooth ? 2 * S : S;
     SampleBufs b;
-    SMP_TRY(sample_bufs(c, d, S, n, b, s));
-    SMP_CUDA(cudaMemcpyAsync(b.pts, pts, sizeof(float4) * S, cudaMemcpyDeviceToDevice, s), "copy points");
+    SMP_TRY(sample_bufs(c, d, P, n, b, s));
+    SMP_CUDA(cudaMemcpyAsync(b.pts, pts, sizeof(float4) * P, cudaMemcpyDeviceToDevice, s), "copy points");
     launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
-    SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ_thresh, nullptr, 0, vt_out, grad_out != nullptr, s));
+    SMP_TRY(sample_pass(c, prims, n, d, o, S, pr, b, occ_thresh, nullptr, 0, vt_out, grad_out != nullptr, s));
+    if (per_g) {
+        launch_reg(prims, n, field, d, rt, b.extra, b.terms, nullptr, b.loss, s);
+        c->launches += 1;
+    }
     if (loss_dev) SMP_CUDA(cudaMemcpyAsync(loss_dev, b.loss, sizeof(double), cudaMemcpyDeviceToDevice, s), "copy loss");
+    if (terms_dev)
+        SMP_CUDA(cudaMemcpyAsync(terms_dev, b.terms, sizeof(double) * 6, cudaMemcpyDeviceToDevice, s), "copy terms");
     if (grad_out && n > 0) {
         launch_chain((float*)c->acc.p, nullptr, const_cast<float*>(prims), n, grad_out, nullptr, nullptr, nullptr,
-                     nullptr, s);
+                     nullptr, s, per_g ? b.extra : nullptr);
         c->launches += 1;
     }
     SMP_CUDA(cudaGetLastError(), "launch (sampled gradient)");
@@ -444,13 +579,17 @@ extern "C" gve_status gve_sample_loss_grad(gve_ctx* c, const float* prims, int64
 }
 
 extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, const float* field, gve_dims d,
-                                         const gve_schedule* sc, int64_t S, uint64_t seed, float* adam_state,
-                                         double* trace, gve_stats* stats, void* stream)
+                                         const gve_schedule* sc, int64_t S, uint64_t seed, const gve_reg_opts* reg,
+                                         float* adam_state, double* trace, gve_stats* stats, void* stream)
 {
     if (!c) return GVE_E_INVALID;
     if (!sc) return fail(c, GVE_E_INVALID, "null schedule");
     SMP_TRY(check_common(c, prims, n, d, &sc->eval));
-    SMP_TRY(check_samples(c, S, &sc->eval));
+    const bool smooth = reg && reg->lambda_sm > 0.f;
+    SMP_TRY(check_samples(c, S, &sc->eval, smooth));
+    RegTerms rt;
+    bool per_g = false;
+    SMP_TRY(check_reg(c, reg, d, field, rt, per_g));
     if (!field) return fail(c, GVE_E_INVALID, "null target field");
     if (sc->iters < 0 || sc->step0 < 0) return fail(c, GVE_E_INVALID, "negative iteration count");
     if (!(sc->lr >= 0.f) || !(sc->beta1 >= 0.f && sc->beta1 < 1.f) || !(sc->beta2 >= 0.f && sc->beta2 < 1.f) ||
@@ -466,7 +605,7 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
     long long split[2];
     SMP_TRY(sample_setup(c, field, d, S, split, s));
     SampleBufs b;
-    SMP_TRY(sample_bufs(c, d, S, n, b, s));
+    SMP_TRY(sample_bufs(c, d, smooth ? 2 * S : S, n, b, s));
     const long long nn = n > 0 ? n : 1;
     float* m = adam_state;
     if (!m) {
@@ -495,14 +634,29 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
             if (timed) SMP_CUDA(cudaEventRecord(c->sev[1][it - it0], s), "event");
             launch_draw_samples(field, d, (const uint32_t*)c->s_hi.p, c->s_nh, (const uint32_t*)c->s_mid.p, c->s_nm,
                                 S, split[0], split[1], seed, (uint32_t)step, b.pts, nullptr, s);
-            SMP_TRY(sample_pass(c, prims, n, d, o, S, b, occ, trace, it, nullptr, true, s));
+            PointReg pr;
+            if (reg) {
+                pr.l_rho = reg->lambda_rho;
+                pr.l_sm = (float)lambda_sm_at(reg, step);
+                pr.smooth = smooth ? 1 : 0;
+            }
+            if (smooth) {
+                launch_draw_partners(b.pts, S, d, seed, (uint32_t)step, reg->partner_radius, b.pts + S, s);
+                c->launches += 1;
+            }
+            SMP_TRY(sample_pass(c, prims, n, d, o, S, pr, b, occ, trace, it, nullptr, true, s));
+            if (per_g) {
+                launch_reg(prims, n, field, d, rt, b.extra, b.terms, trace ? trace + it : nullptr, b.loss, s);
+                c->launches += 1;
+            }
             if (timed) SMP_CUDA(cudaEventRecord(c->sev[2][it - it0], s), "event");
             if (n > 0) {
                 AdamArgs ad{};
                 ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
                 ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step + 1));
                 ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step + 1));
-                launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s);
+                launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s,
+                             per_g ? b.extra : nullptr);
                 c->launches += 2;
             }
             c->launches += 1;

@@ -115,11 +115,13 @@ def lib():
             L.gve_structure_stats.restype = st
             L.gve_draw_samples.argtypes = [P, P, Dims, i64, ctypes.c_uint64, ctypes.c_uint32, P, P, P]
             L.gve_draw_samples.restype = st
+            L.gve_draw_partners.argtypes = [P, P, i64, Dims, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_float, P, P]
+            L.gve_draw_partners.restype = st
             L.gve_sample_loss_grad.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, i64, ctypes.c_float,
-                                               P, P, P, P]
+                                               P, P, P, P, P, P, P]
             L.gve_sample_loss_grad.restype = st
             L.gve_refine_sampled.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), i64, ctypes.c_uint64, P,
-                                             P, ctypes.POINTER(Stats), P]
+                                             P, P, P, P]
             L.gve_refine_sampled.restype = st
             L.gve_bin.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, P, P, P, i64, P, ctypes.POINTER(i64), P]
             L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
@@ -350,32 +352,87 @@ def gve_draw_samples(field: torch.Tensor, S: int, seed: int, it: int, want_voxel
     return (pts, vox) if want_voxels else pts
 
 
+class RegOpts(ctypes.Structure):
+    _fields_ = [("lambda_rho", ctypes.c_float), ("lambda_sm", ctypes.c_float), ("lambda_sm_end", ctypes.c_float),
+                ("anneal_iters", ctypes.c_int32), ("lambda_anc", ctypes.c_float), ("lambda_aniso", ctypes.c_float),
+                ("lambda_cap", ctypes.c_float), ("partner_radius", ctypes.c_float), ("aniso_max", ctypes.c_float),
+                ("s_lo", ctypes.c_float), ("s_hi", ctypes.c_float)]
+
+
+@dataclass
+class RegOptions:
+    """Weights and bounds of the five regularisers of the full objective.
+    The paper gives no values; these defaults were chosen by a sweep on the
+    1024^3, 1.4M-Gaussian sampled schedule (1,500 iterations): the per-
+    Gaussian terms are means over N, so their weights are large; the density
+    term costs PSNR at any weight that moves it and is kept small."""
+    lambda_rho: float = 1e-5
+    lambda_sm: float = 1e-4
+    lambda_sm_end: float = 1e-6
+    anneal_iters: int = 1500
+    lambda_anc: float = 30.0
+    lambda_aniso: float = 30.0
+    lambda_cap: float = 30.0
+    partner_radius: float = 1.0
+    aniso_max: float = 3.0
+    s_lo: float = 0.3
+    s_hi: float = 0.0          # <= 0: the allocator's cap (longest axis / 16)
+
+    def c(self) -> RegOpts:
+        return RegOpts(float(self.lambda_rho), float(self.lambda_sm), float(self.lambda_sm_end),
+                       int(self.anneal_iters), float(self.lambda_anc), float(self.lambda_aniso),
+                       float(self.lambda_cap), float(self.partner_radius), float(self.aniso_max), float(self.s_lo),
+                       float(self.s_hi))
+
+
+def gve_draw_partners(pts: torch.Tensor, shape, seed: int, it: int, radius: float = 1.0) -> torch.Tensor:
+    """Smoothness partners (S, 4) = (x', y', z', -1) of points (S, 4)."""
+    if pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != 4 or not pts.is_contiguous():
+        raise ValueError("points must be a contiguous float32 (S, 4) tensor")
+    out = torch.empty_like(pts)
+    c = context(pts.device.index)
+    _check(lib().gve_draw_partners(c, _ptr(pts), pts.shape[0], _dims(shape), int(seed), int(it), float(radius),
+                                   _ptr(out), _stream(pts.device)), c)
+    return out
+
+
 def gve_sample_loss_grad(prims: torch.Tensor, shape, pts: torch.Tensor, opts: EvalOptions | None = None,
-                         occ: float = 0.02, want_grad: bool = True):
-    """(sampled loss (float64 tensor), dL/dprims (N,12) or None, Vt per point)
-    at caller-given points (S, 4) = (x, y, z, target)."""
+                         occ: float = 0.02, want_grad: bool = True, reg: RegOptions | None = None,
+                         field: torch.Tensor | None = None, want_terms: bool = False):
+    """(objective (float64 tensor), dL/dprims (N,12) or None, Vt per sample
+    [, the six unweighted terms]) at caller-given points (x, y, z, target):
+    S samples, followed by S partners when reg.lambda_sm > 0."""
     prims = _prims(prims)
     if pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != 4 or not pts.is_contiguous():
         raise ValueError("points must be a contiguous float32 (S, 4) tensor")
     o = (opts or EvalOptions()).c()
-    S = pts.shape[0]
+    smooth = reg is not None and reg.lambda_sm > 0
+    if smooth and pts.shape[0] % 2:
+        raise ValueError("with partners the points are S samples then S partners")
+    S = pts.shape[0] // 2 if smooth else pts.shape[0]
     grad = torch.empty_like(prims) if want_grad else None
     loss = torch.zeros(1, dtype=torch.float64, device=prims.device)
+    terms = torch.zeros(6, dtype=torch.float64, device=prims.device)
     vt = torch.empty(S, dtype=torch.float32, device=prims.device)
+    r = reg.c() if reg is not None else None
+    if field is not None:
+        _field(field)
     c = context(prims.device.index)
     _check(lib().gve_sample_loss_grad(c, _ptr(prims), prims.shape[0], _dims(shape), ctypes.byref(o), _ptr(pts), S,
-                                      float(occ), _ptr(grad), _ptr(loss), _ptr(vt), _stream(prims.device)), c)
-    return loss, grad, vt
+                                      float(occ), ctypes.byref(r) if r is not None else None, _ptr(field),
+                                      _ptr(grad), _ptr(loss), _ptr(terms), _ptr(vt), _stream(prims.device)), c)
+    return (loss, grad, vt, terms) if want_terms else (loss, grad, vt)
 
 
 def gve_refine_sampled(prims: torch.Tensor, field: torch.Tensor, iters: int, S: int = 3072, seed: int = 0,
                        lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15,
                        occ: float = 0.02, step0: int = 0, opts: EvalOptions | None = None,
                        adam_state: torch.Tensor | None = None, trace: torch.Tensor | None = None,
-                       want_stats: bool = True):
+                       want_stats: bool = True, reg: RegOptions | None = None):
     """Stratified-sample refinement in place on ``prims`` (the paper's training
-    regime).  With ``want_stats`` the result includes the full-grid PSNR
-    after the last step."""
+    regime; ``reg`` adds the five regularisers of the full objective).  With
+    ``want_stats`` the result includes the full-grid PSNR after the last
+    step."""
     prims, field = _prims(prims), _field(field)
     sched = Schedule(int(iters), float(lr), float(beta1), float(beta2), float(eps), float(occ), int(step0),
                      (opts or EvalOptions()).c())
@@ -385,10 +442,12 @@ def gve_refine_sampled(prims: torch.Tensor, field: torch.Tensor, iters: int, S: 
     if trace is not None and (trace.dtype != torch.float64 or trace.numel() < iters or not trace.is_cuda):
         raise ValueError("trace must be a CUDA float64 tensor with >= iters entries")
     st = Stats()
+    r = reg.c() if reg is not None else None
     c = context(prims.device.index)
     _check(lib().gve_refine_sampled(c, _ptr(prims), prims.shape[0], _ptr(field), _dims(field.shape),
-                                    ctypes.byref(sched), int(S), int(seed), _ptr(adam_state), _ptr(trace),
-                                    ctypes.byref(st) if want_stats else None, _stream(prims.device)), c)
+                                    ctypes.byref(sched), int(S), int(seed), ctypes.byref(r) if r is not None else None,
+                                    _ptr(adam_state), _ptr(trace), ctypes.byref(st) if want_stats else None,
+                                    _stream(prims.device)), c)
     if not want_stats:
         return None
     return {name: getattr(st, name) for name, _ in Stats._fields_}

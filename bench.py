@@ -668,7 +668,7 @@ def run_render(args):
     img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 0)):
         gve.gve_render(cam, W, H, tf, ro, out=img)
-    _, kept = gve.gve_render(cam, W, H, tf, ro, out=img, want_kept=True)
+    _, kept, tested = gve.gve_render(cam, W, H, tf, ro, out=img, want_kept="both")
     clocks = Clocks(0)
     clocks.start()
     torch.cuda.synchronize()
@@ -685,7 +685,7 @@ def run_render(args):
     achieved = RENDER_OPS_PER_PAIR * kept / (ms_frame / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
                 "traffic": None, "kernel": "k_render<%s>" % ("true" if args.shade else "false"),
-                "kept_pairs": int(kept), "ops_per_pair": RENDER_OPS_PER_PAIR,
+                "kept_pairs": int(kept), "tested_pairs": int(tested), "ops_per_pair": RENDER_OPS_PER_PAIR,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (derived, FMA counted once)"}
     # end to end: camera in from the host, frame out to pinned host memory
     host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()

@@ -438,11 +438,12 @@ GVE_API gve_status gve_render_prepare(gve_ctx* ctx, const float* prims_dev, int6
 /* Renders the prepared set: image_dev [height][width][4] float32 RGBA
  * (premultiplied colour plus background, alpha = 1 - transmittance).
  * kept_pairs (host, nullable) receives the kept (sample, Gaussian) pairs,
- * the algorithmic work of the frame (synchronises when asked).
+ * the algorithmic work of the frame, and tested_pairs (host, nullable) the
+ * pairs the march tested (list lengths times samples); either synchronises.
  * GVE_E_INVALID without a prepared set, for a non-finite camera, bad
  * options, more than 2^28 pixels or more than 524,280 rows. */
 GVE_API gve_status gve_render(gve_ctx* ctx, const gve_camera* cam, const gve_render_opts* opts, float* image_dev,
-                              int64_t* kept_pairs, void* stream);
+                              int64_t* kept_pairs, int64_t* tested_pairs, void* stream);
 
 /* Brick binning introspection: the (brick, Gaussian) pairs that evaluation
  * uses, sorted by brick key (z-major brick index) and then by Gaussian index,

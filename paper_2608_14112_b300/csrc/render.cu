@@ -127,7 +127,7 @@ struct RenderArgs {
     const float4* tf;
     int ntf;
     float4* image;
-    unsigned long long* kept;
+    unsigned long long* kept;    // [0] kept pairs, [1] tested pairs (optional)
 };
 
 // Ray through pixel (i, j): unit direction and the box interval; false for
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(128) k_render(const RenderArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int j = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    unsigned long long kept = 0;
+    unsigned long long kept = 0, tested = 0;
     if (i < a.W && j < a.H) {
         float d[3], t0 = 0.f, t1 = 0.f;
         float Tr = 1.f, C[3] = {0.f, 0.f, 0.f};
@@ -213,14 +213,41 @@ __global__ void __launch_bounds__(128) k_render(const RenderArgs a)
                     for (int q = 0; q < 3; ++q) gN[s][q] = gD[s][q] = 0.f;
             }
             const uint32_t b = a.start[cell], e = a.end[cell];
+            tested += (unsigned long long)(e - b) * (unsigned)gs;
             for (uint32_t jj = b; jj < e; ++jj) {
                 const float4 r0 = a.crec[3ull * jj], r1 = a.crec[3ull * jj + 1], r2 = a.crec[3ull * jj + 2];
+                // the keep chain for two samples per packed instruction, in
+                // keep_t's order (p - mu as p + (-mu): the same value)
+                const float2 nmx = make_float2(-r0.x, -r0.x), nmy = make_float2(-r0.y, -r0.y),
+                             nmz = make_float2(-r0.z, -r0.z);
+                const float2 cxx = make_float2(r0.w, r0.w), cyy = make_float2(r1.x, r1.x),
+                             czz = make_float2(r1.y, r1.y), cxy = make_float2(r1.z, r1.z),
+                             cxz = make_float2(r1.w, r1.w), cyz = make_float2(r2.x, r2.x);
+                float tt[G], dxs[G], dys[G], dzs[G];
+#pragma unroll
+                for (int q = 0; q < G / 2; ++q) {
+                    if (2 * q < gs) {
+                        const float2 dx = __fadd2_rn(make_float2(px[2 * q], px[2 * q + 1]), nmx);
+                        const float2 dy = __fadd2_rn(make_float2(py[2 * q], py[2 * q + 1]), nmy);
+                        const float2 dz = __fadd2_rn(make_float2(pz[2 * q], pz[2 * q + 1]), nmz);
+                        const float2 b2 = __ffma2_rn(cxy, dy, __fmul2_rn(cxz, dz));
+                        const float2 c2 = __ffma2_rn(dy, __ffma2_rn(cyy, dy, __fmul2_rn(cyz, dz)),
+                                                     __fmul2_rn(dz, __fmul2_rn(czz, dz)));
+                        const float2 t2 = __ffma2_rn(dx, __ffma2_rn(cxx, dx, b2), c2);
+                        tt[2 * q] = t2.x; tt[2 * q + 1] = t2.y;
+                        dxs[2 * q] = dx.x; dxs[2 * q + 1] = dx.y;
+                        dys[2 * q] = dy.x; dys[2 * q + 1] = dy.y;
+                        dzs[2 * q] = dz.x; dzs[2 * q + 1] = dz.y;
+                    } else {
+                        tt[2 * q] = tt[2 * q + 1] = -INFINITY;
+                        dxs[2 * q] = dxs[2 * q + 1] = dys[2 * q] = dys[2 * q + 1] = dzs[2 * q] = dzs[2 * q + 1] = 0.f;
+                    }
+                }
 #pragma unroll
                 for (int s = 0; s < G; ++s) {
                     if (s < gs) {
-                        const float dx = __fsub_rn(px[s], r0.x), dy = __fsub_rn(py[s], r0.y),
-                                    dz = __fsub_rn(pz[s], r0.z);
-                        const float t = keep_t(r0, r1, r2, dx, dy, dz);
+                        const float dx = dxs[s], dy = dys[s], dz = dzs[s];
+                        const float t = tt[s];
                         if (t > a.T) {
                             const float gv = ex2_approx(t);
                             N[s] = fmaf(r2.y, gv, N[s]);
@@ -291,8 +318,14 @@ __global__ void __launch_bounds__(128) k_render(const RenderArgs a)
             make_float4(fmaf(Tr, a.bg[0], C[0]), fmaf(Tr, a.bg[1], C[1]), fmaf(Tr, a.bg[2], C[2]), 1.f - Tr);
     }
     if (a.kept) {
-        for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-        if ((threadIdx.x & 31) == 0 && kept) atomicAdd(a.kept, kept);
+        for (int o = 16; o > 0; o >>= 1) {
+            kept += __shfl_xor_sync(0xffffffffu, kept, o);
+            tested += __shfl_xor_sync(0xffffffffu, tested, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (kept) atomicAdd(a.kept, kept);
+            if (tested) atomicAdd(a.kept + 1, tested);
+        }
     }
 }
 
@@ -404,7 +437,7 @@ gve_status gve_render_prepare(gve_ctx* c, const float* prims, int64_t n, gve_dim
 }
 
 gve_status gve_render(gve_ctx* c, const gve_camera* cam, const gve_render_opts* o, float* image, int64_t* kept_pairs,
-                      void* stream)
+                      int64_t* tested_pairs, void* stream)
 {
     if (!c) return GVE_E_INVALID;
     if (!c->r_ready) return fail(c, GVE_E_INVALID, "no prepared primitive set (call gve_render_prepare)");
@@ -452,10 +485,10 @@ gve_status gve_render(gve_ctx* c, const gve_camera* cam, const gve_render_opts* 
     a.ntf = o->tf_n;
     a.image = (float4*)image;
     unsigned long long* kd = nullptr;
-    if (kept_pairs) {
+    if (kept_pairs || tested_pairs) {
         RTRY(ensure(c, c->r_scanp, sizeof(unsigned long long) * kScanBlocks, s));
         kd = (unsigned long long*)c->r_scanp.p;
-        RCUDA(cudaMemsetAsync(kd, 0, sizeof(unsigned long long), s), "memset kept");
+        RCUDA(cudaMemsetAsync(kd, 0, 2 * sizeof(unsigned long long), s), "memset kept");
     }
     a.kept = kd;
     const dim3 grid((unsigned)((a.W + 15) / 16), (unsigned)((a.H + 7) / 8));
@@ -465,11 +498,12 @@ gve_status gve_render(gve_ctx* c, const gve_camera* cam, const gve_render_opts* 
         k_render<false><<<grid, 128, 0, s>>>(a);
     c->launches += 1;
     RCUDA(cudaGetLastError(), "launch (render)");
-    if (kept_pairs) {
-        unsigned long long hk = 0;
-        RCUDA(cudaMemcpyAsync(&hk, kd, sizeof(hk), cudaMemcpyDeviceToHost, s), "read kept");
+    if (kd) {
+        unsigned long long hk[2] = {0, 0};
+        RCUDA(cudaMemcpyAsync(hk, kd, sizeof(hk), cudaMemcpyDeviceToHost, s), "read kept");
         RCUDA(cudaStreamSynchronize(s), "render");
-        *kept_pairs = (int64_t)hk;
+        if (kept_pairs) *kept_pairs = (int64_t)hk[0];
+        if (tested_pairs) *tested_pairs = (int64_t)hk[1];
     }
     return GVE_OK;
 }

@@ -109,7 +109,7 @@ def lib():
             L.gve_refine.argtypes = [P, P, i64, P, Dims, ctypes.POINTER(Schedule), P, P, ctypes.POINTER(Stats), P]
             L.gve_render_prepare.argtypes = [P, P, i64, Dims, P, P]
             L.gve_render_prepare.restype = st
-            L.gve_render.argtypes = [P, P, P, P, P, P]
+            L.gve_render.argtypes = [P, P, P, P, P, P, P]
             L.gve_render.restype = st
             L.gve_structure_stats.argtypes = [P, P, Dims, P, P, P]
             L.gve_structure_stats.restype = st
@@ -316,10 +316,13 @@ def gve_render(camera, width: int, height: int, tf: torch.Tensor, opts: RenderOp
                     tf.data_ptr(), int(tf.shape[0]))
     if out is None:
         out = torch.empty((int(height), int(width), 4), dtype=torch.float32, device=dev)
-    kept = ctypes.c_int64(0)
+    kept, tested = ctypes.c_int64(0), ctypes.c_int64(0)
     c = context(dev.index)
     _check(lib().gve_render(c, ctypes.byref(cam), ctypes.byref(ro), _ptr(out),
-                            ctypes.byref(kept) if want_kept else None, _stream(dev)), c)
+                            ctypes.byref(kept) if want_kept else None, ctypes.byref(tested) if want_kept else None,
+                            _stream(dev)), c)
+    if want_kept == "both":
+        return out, kept.value, tested.value
     return (out, kept.value) if want_kept else out
 
 

@@ -138,7 +138,8 @@ __device__ __forceinline__ float keep_t(const float4& r0, const float4& r1, cons
 // cover the float32 rounding of the keep chain at any float32 point.
 // Returns 0 for a record the preparation marks invalid (non-finite values,
 // zero quaternion), 2 for scales beyond float range (the whole grid), else 1.
-__device__ __forceinline__ int gauss_box(const float* prims, long long i, float k, float mu[3], float rad[3])
+__device__ __forceinline__ int gauss_box(const float* prims, long long i, float k, float mu[3], float rad[3],
+                                         float* kb_out = nullptr, float* cinv_out = nullptr)
 {
     const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
     const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
@@ -168,6 +169,16 @@ __device__ __forceinline__ int gauss_box(const float* prims, long long i, float 
     for (int j = 0; j < 3; ++j) {
         const float var = R[j][0] * R[j][0] * s[0] * s[0] + R[j][1] * R[j][1] * s[1] * s[1] + R[j][2] * R[j][2] * s[2] * s[2];
         rad[j] = kb * sqrtf(var) * 1.0001f + 0.05f;
+    }
+    if (kb_out) *kb_out = kb;
+    if (cinv_out) {  // Sigma^-1 = R diag(s^-2) R^T: xx, yy, zz, xy, xz, yz
+        const float is[3] = {1.f / (s[0] * s[0]), 1.f / (s[1] * s[1]), 1.f / (s[2] * s[2])};
+        const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int x = ab[q][0], y = ab[q][1];
+            cinv_out[q] = R[x][0] * R[y][0] * is[0] + R[x][1] * R[y][1] * is[1] + R[x][2] * R[y][2] * is[2];
+        }
     }
     return 1;
 }

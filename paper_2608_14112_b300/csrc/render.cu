@@ -44,18 +44,55 @@ __device__ __forceinline__ int cell_axis(float p, int nc)
     return c;
 }
 
-// cell range of Gaussian i; false when it lists no cell
-__device__ __forceinline__ bool render_cells(const float* prims, const float4* rec, long long i, float k,
-                                             const RenderGeom& g, int lo[3], int hi[3])
+// Which cells of the box range a Gaussian's kept points can reach.  The
+// kb-ellipsoid {m <= kb} lies on the near side of the plane <c - mu, x - mu>_M
+// = kb |c - mu|_M (Cauchy-Schwarz in the Mahalanobis inner product, c the
+// cell's centre); a cell whose whole box, dilated by the box's 0.05-voxel
+// slack, lies beyond it holds no kept point: with v = c - mu, g = Sigma^-1 v,
+// m2 = v.g and D = m2 - h sum |g_j| (h the dilated half edge), the cell is
+// dropped when D > 0 and D^2 > kb^2 m2 (kb widened by 0.1 % for the float32
+// evaluation).
+struct CellCull {
+    float mu[3], C[6], kb2;
+    bool on;
+};
+
+__device__ __forceinline__ bool cell_kept(const CellCull& q, int cx, int cy, int cz)
 {
+    if (!q.on) return true;
+    const float h = 0.5f * (float)(1 << kCellShift) + 0.05f;
+    const float v0 = (float)(cx << kCellShift) + 0.5f * (float)((1 << kCellShift) - 1) - q.mu[0];
+    const float v1 = (float)(cy << kCellShift) + 0.5f * (float)((1 << kCellShift) - 1) - q.mu[1];
+    const float v2 = (float)(cz << kCellShift) + 0.5f * (float)((1 << kCellShift) - 1) - q.mu[2];
+    const float g0 = q.C[0] * v0 + q.C[3] * v1 + q.C[4] * v2;
+    const float g1 = q.C[3] * v0 + q.C[1] * v1 + q.C[5] * v2;
+    const float g2 = q.C[4] * v0 + q.C[5] * v1 + q.C[2] * v2;
+    const float m2 = v0 * g0 + v1 * g1 + v2 * g2;
+    const float D = m2 - h * (fabsf(g0) + fabsf(g1) + fabsf(g2));
+    return !(D > 0.f && D * D > q.kb2 * m2);
+}
+
+// cell range of Gaussian i (and its cell test); false when it lists no cell
+__device__ __forceinline__ bool render_cells(const float* prims, const float4* rec, long long i, float k,
+                                             const RenderGeom& g, int lo[3], int hi[3], CellCull& cull)
+{
+    cull.on = false;
     if (!(rec[3 * i + 2].z > 0.f)) return false;  // invalid record (weight zero)
-    float mu[3], rad[3];
-    const int kind = gauss_box(prims, i, k, mu, rad);
+    float mu[3], rad[3], kb = 0.f;
+    const int kind = gauss_box(prims, i, k, mu, rad, &kb, cull.C);
     if (kind == 0) return false;
     const int dims[3] = {g.nx, g.ny, g.nz}, nc[3] = {g.ncx, g.ncy, g.ncz};
     if (kind == 2) {
         for (int j = 0; j < 3; ++j) { lo[j] = 0; hi[j] = nc[j] - 1; }
         return true;
+    }
+    bool fin = isfinite(kb);
+    for (int q = 0; q < 6; ++q) fin = fin && isfinite(cull.C[q]);
+    if (fin) {
+        const float kw = kb * 1.001f;
+        cull.kb2 = kw * kw;
+        for (int j = 0; j < 3; ++j) cull.mu[j] = mu[j];
+        cull.on = true;
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -73,9 +110,12 @@ __global__ void __launch_bounds__(256) k_render_count(const float* __restrict__ 
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int lo[3], hi[3];
+    CellCull cull;
     uint32_t c = 0;
-    if (render_cells(prims, rec, i, k, g, lo, hi))
-        c = (uint32_t)(hi[0] - lo[0] + 1) * (uint32_t)(hi[1] - lo[1] + 1) * (uint32_t)(hi[2] - lo[2] + 1);
+    if (render_cells(prims, rec, i, k, g, lo, hi, cull))
+        for (int cz = lo[2]; cz <= hi[2]; ++cz)
+            for (int cy = lo[1]; cy <= hi[1]; ++cy)
+                for (int cx = lo[0]; cx <= hi[0]; ++cx) c += cell_kept(cull, cx, cy, cz) ? 1u : 0u;
     cnt[i] = c;
 }
 
@@ -87,11 +127,13 @@ __global__ void __launch_bounds__(256) k_render_emit(const float* __restrict__ p
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int lo[3], hi[3];
-    if (!render_cells(prims, rec, i, k, g, lo, hi)) return;
+    CellCull cull;
+    if (!render_cells(prims, rec, i, k, g, lo, hi, cull)) return;
     unsigned long long o = off[i];
     for (int cz = lo[2]; cz <= hi[2]; ++cz)
         for (int cy = lo[1]; cy <= hi[1]; ++cy)
             for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                if (!cell_kept(cull, cx, cy, cz)) continue;
                 keys[o] = (uint32_t)(((long long)cz * g.ncy + cy) * g.ncx + cx);
                 vals[o] = (uint32_t)i;
                 ++o;

@@ -207,7 +207,7 @@ __device__ __forceinline__ bool ray_setup(const RenderArgs& a, int i, int j, flo
 }
 
 template <bool SHADE>
-__global__ void __launch_bounds__(128) k_render(const RenderArgs a)
+__global__ void __launch_bounds__(128, SHADE ? 4 : 5) k_render(const RenderArgs a)
 {
     constexpr int G = SHADE ? 4 : 8;
     // 16 x 8 pixels per CTA, 8 x 4 per warp (neighbouring rays share cells)
@@ -256,8 +256,16 @@ __global__ void __launch_bounds__(128) k_render(const RenderArgs a)
             }
             const uint32_t b = a.start[cell], e = a.end[cell];
             tested += (unsigned long long)(e - b) * (unsigned)gs;
+            // the next record is loaded while the current one is tested
+            float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+            if (b < e) { n0 = a.crec[3ull * b]; n1 = a.crec[3ull * b + 1]; n2 = a.crec[3ull * b + 2]; }
             for (uint32_t jj = b; jj < e; ++jj) {
-                const float4 r0 = a.crec[3ull * jj], r1 = a.crec[3ull * jj + 1], r2 = a.crec[3ull * jj + 2];
+                const float4 r0 = n0, r1 = n1, r2 = n2;
+                if (jj + 1 < e) {
+                    n0 = a.crec[3ull * (jj + 1)];
+                    n1 = a.crec[3ull * (jj + 1) + 1];
+                    n2 = a.crec[3ull * (jj + 1) + 2];
+                }
                 // the keep chain for two samples per packed instruction, in
                 // keep_t's order (p - mu as p + (-mu): the same value)
                 const float2 nmx = make_float2(-r0.x, -r0.x), nmy = make_float2(-r0.y, -r0.y),

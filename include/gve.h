@@ -430,8 +430,11 @@ typedef struct {
  * change afterwards, the context keeps its own copy of the coefficients):
  * cells of 8^3 voxels, each listing, in Gaussian order, every Gaussian whose
  * conservative truncation box (the same margins as the sampled refinement)
- * overlaps the cell's continuous extent.  Synchronises `stream`.
- * GVE_E_INVALID for bad sizes or options, GVE_E_CAPACITY beyond 2^32 pairs. */
+ * overlaps the cell's continuous extent and whose inflated ellipsoid is not
+ * separated from the cell by the plane through the direction to the cell's
+ * centre (so no kept sample is lost).  prims_dev [n][12] float32,
+ * 16-byte aligned.  Synchronises `stream`.  GVE_E_INVALID for bad sizes,
+ * alignment or options, GVE_E_CAPACITY beyond 2^32 pairs. */
 GVE_API gve_status gve_render_prepare(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
                                       const gve_eval_opts* opts, void* stream);
 

@@ -411,6 +411,7 @@ gve_status gve_render_prepare(gve_ctx* c, const float* prims, int64_t n, gve_dim
     if (!c) return GVE_E_INVALID;
     if (!o) return fail(c, GVE_E_INVALID, "null options");
     if (n < 0 || (n > 0 && !prims)) return fail(c, GVE_E_INVALID, "bad primitive array");
+    if (reinterpret_cast<uintptr_t>(prims) & 15u) return fail(c, GVE_E_INVALID, "primitives not 16-byte aligned");
     if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return fail(c, GVE_E_INVALID, "non-positive grid size");
     if (d.nx > (1 << 20) || d.ny > (1 << 20) || d.nz > (1 << 20)) return fail(c, GVE_E_INVALID, "grid axis above 2^20");
     if (n > (int64_t)UINT32_MAX) return fail(c, GVE_E_INVALID, "more than 2^32 - 1 primitives");

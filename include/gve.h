@@ -336,7 +336,7 @@ GVE_API gve_status gve_draw_samples(gve_ctx* ctx, const float* field_dev, gve_di
  *             of counter (s, t, 5, 'GVE1'), p' = clamp(p + 2 radius u, 0,
  *             n - 1) in float32; its weight decays geometrically from
  *             lambda_sm to lambda_sm_end over anneal_iters iterations;
- *   L_anc   = (1/N) sum_i (a_i - V(mu_i))^2, V trilinear (FP64,
+ *   L_anc   = (1/N) sum_i (a_i - V(mu_i))^2, V trilinear (float32,
  *             edge-clamped); the gradient flows into a_i only;
  *   L_aniso = (1/N) sum_i sum_{j<k} relu(|l_ij - l_ik| - ln aniso_max)^2
  *             over the log-scales l (elongation bounded at aniso_max : 1);

@@ -805,8 +805,8 @@ void launch_draw_samples(const float* V, gve_dims d, const uint32_t* hi, unsigne
 //   partner of sample j of iteration t: u = (x >> 8) 2^-24 - 1/2 per axis
 //     from Philox4x32-10 stream 5, counter (j, t), p' = clamp(p + 2 r u,
 //     0, n - 1) in float32;
-//   L_anc   = (1/N) sum (a_i - V(mu_i))^2, V the FP64 trilinear value,
-//             gradient into a_i only;
+//   L_anc   = (1/N) sum (a_i - V(mu_i))^2, V trilinear (float32 here, the
+//             oracle's in FP64: 1e-7 apart), gradient into a_i only;
 //   L_aniso = (1/N) sum_i sum_{j<k} relu(|l_ij - l_ik| - ln r_max)^2 over
 //             the log-scales l;
 //   L_cap   = (1/N) sum_i sum_j relu(l_ij - ln s_hi)^2 + relu(ln s_lo - l_ij)^2.
@@ -839,61 +839,100 @@ __global__ void __launch_bounds__(128) k_draw_partners(const float4* __restrict_
     out[j] = make_float4(o[0], o[1], o[2], -1.0f);  // no target: outside the value and density terms
 }
 
+// float32 trilinear V(p), edge-clamped (the anchor's target; the FP64
+// version above serves the allocator and the sample draw)
+__device__ __forceinline__ float trilinear32(const float* V, int nx, int ny, int nz, float px, float py, float pz)
+{
+    const float p[3] = {px, py, pz};
+    const int dims[3] = {nx, ny, nz};
+    int i0[3], i1[3];
+    float f[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float c = p[j];
+        c = c < 0.f ? 0.f : (c > (float)(dims[j] - 1) ? (float)(dims[j] - 1) : c);
+        const float fl = floorf(c);
+        i0[j] = (int)fl;
+        i1[j] = i0[j] + 1 < dims[j] ? i0[j] + 1 : i0[j];
+        f[j] = c - fl;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) {
+                const float wgt = (cx ? f[0] : 1.f - f[0]) * (cy ? f[1] : 1.f - f[1]) * (cz ? f[2] : 1.f - f[2]);
+                acc += wgt * V[vid(nx, ny, cx ? i1[0] : i0[0], cy ? i1[1] : i0[1], cz ? i1[2] : i0[2])];
+            }
+    return acc;
+}
+
+// Per-Gaussian terms in float32 (B300's FP64 rate would make them the
+// slowest pass of an iteration); partial sums compensated, folded in FP64
+// per warp.
 __global__ void __launch_bounds__(256) k_reg(const float* __restrict__ prims, long long n, const float* __restrict__ V,
                                              int nx, int ny, int nz, RegTerms rt, double invN,
                                              float* __restrict__ extra, double* __restrict__ terms,
                                              double* total_a, double* total_b)
 {
-    double sa = 0.0, sn = 0.0, sc = 0.0;
+    float sa = 0.f, ca = 0.f, sn = 0.f, cn = 0.f, sc = 0.f, cc = 0.f;  // Kahan pairs
+    auto kadd = [](float& s, float& c, float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    };
+    const float fN = (float)invN;
+    const float ln_r = (float)rt.ln_r, ln_lo = (float)rt.ln_lo, ln_hi = (float)rt.ln_hi;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
         const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
         const float p[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
         bool ok = true;
         for (int j = 0; j < 12; ++j) ok = ok && isfinite(p[j]);
-        const double nq2 = (double)p[6] * p[6] + (double)p[7] * p[7] + (double)p[8] * p[8] + (double)p[9] * p[9];
-        ok = ok && nq2 > 0.0;
+        ok = ok && (p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9]) > 0.f;
         float g[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (ok) {
             if (rt.l_anc != 0.f && V) {
-                const double r = (double)p[10] - trilinear(V, nx, ny, nz, (double)p[0], (double)p[1], (double)p[2]);
-                sa += r * r;
-                g[10] = (float)((double)rt.l_anc * 2.0 * r * invN);
+                const float r = p[10] - trilinear32(V, nx, ny, nz, p[0], p[1], p[2]);
+                kadd(sa, ca, r * r);
+                g[10] = rt.l_anc * 2.f * r * fN;
             }
-            double gl[3] = {0.0, 0.0, 0.0};
             for (int j = 0; j < 3; ++j)
                 for (int m = j + 1; m < 3; ++m) {
-                    const double dlt = (double)p[3 + j] - (double)p[3 + m];
-                    const double u = fabs(dlt) - rt.ln_r;
-                    if (u > 0.0) {
-                        sn += u * u;
-                        const double gg = (double)rt.l_aniso * 2.0 * u * invN * (dlt > 0.0 ? 1.0 : -1.0);
-                        gl[j] += gg;
-                        gl[m] -= gg;
+                    const float dlt = p[3 + j] - p[3 + m];
+                    const float u = fabsf(dlt) - ln_r;
+                    if (u > 0.f) {
+                        kadd(sn, cn, u * u);
+                        const float gg = rt.l_aniso * 2.f * u * fN * (dlt > 0.f ? 1.f : -1.f);
+                        g[3 + j] += gg;
+                        g[3 + m] -= gg;
                     }
                 }
             for (int j = 0; j < 3; ++j) {
-                const double u = (double)p[3 + j] - rt.ln_hi, w2 = rt.ln_lo - (double)p[3 + j];
-                if (u > 0.0) { sc += u * u; gl[j] += (double)rt.l_cap * 2.0 * u * invN; }
-                if (w2 > 0.0) { sc += w2 * w2; gl[j] -= (double)rt.l_cap * 2.0 * w2 * invN; }
+                const float u = p[3 + j] - ln_hi, w2 = ln_lo - p[3 + j];
+                if (u > 0.f) { kadd(sc, cc, u * u); g[3 + j] += rt.l_cap * 2.f * u * fN; }
+                if (w2 > 0.f) { kadd(sc, cc, w2 * w2); g[3 + j] -= rt.l_cap * 2.f * w2 * fN; }
             }
-            for (int j = 0; j < 3; ++j) g[3 + j] = (float)gl[j];
         }
         float4* e4 = reinterpret_cast<float4*>(extra) + 3 * i;
         e4[0] = make_float4(g[0], g[1], g[2], g[3]);
         e4[1] = make_float4(g[4], g[5], g[6], g[7]);
         e4[2] = make_float4(g[8], g[9], g[10], g[11]);
     }
+    double da = (double)sa - (double)ca, dn = (double)sn - (double)cn, dc = (double)sc - (double)cc;
     for (int o = 16; o > 0; o >>= 1) {
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sn += __shfl_xor_sync(0xffffffffu, sn, o);
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        da += __shfl_xor_sync(0xffffffffu, da, o);
+        dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        dc += __shfl_xor_sync(0xffffffffu, dc, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(terms + 3, sa * invN);
-        atomicAdd(terms + 4, sn * invN);
-        atomicAdd(terms + 5, sc * invN);
-        const double t = ((double)rt.l_anc * sa + (double)rt.l_aniso * sn + (double)rt.l_cap * sc) * invN;
+        atomicAdd(terms + 3, da * invN);
+        atomicAdd(terms + 4, dn * invN);
+        atomicAdd(terms + 5, dc * invN);
+        const double t = ((double)rt.l_anc * da + (double)rt.l_aniso * dn + (double)rt.l_cap * dc) * invN;
         if (total_a) atomicAdd(total_a, t);
         if (total_b) atomicAdd(total_b, t);
     }

@@ -257,15 +257,14 @@ __global__ void __launch_bounds__(128, SHADE ? 4 : 5) k_render(const RenderArgs 
             const uint32_t b = a.start[cell], e = a.end[cell];
             tested += (unsigned long long)(e - b) * (unsigned)gs;
             // the next record is loaded while the current one is tested
+            const float4* rp = a.crec + 3ull * b;
             float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
-            if (b < e) { n0 = a.crec[3ull * b]; n1 = a.crec[3ull * b + 1]; n2 = a.crec[3ull * b + 2]; }
+            if (b < e) { n0 = rp[0]; n1 = rp[1]; n2 = rp[2]; }
+            uint32_t kept_g = 0;
             for (uint32_t jj = b; jj < e; ++jj) {
                 const float4 r0 = n0, r1 = n1, r2 = n2;
-                if (jj + 1 < e) {
-                    n0 = a.crec[3ull * (jj + 1)];
-                    n1 = a.crec[3ull * (jj + 1) + 1];
-                    n2 = a.crec[3ull * (jj + 1) + 2];
-                }
+                rp += 3;
+                if (jj + 1 < e) { n0 = rp[0]; n1 = rp[1]; n2 = rp[2]; }
                 // the keep chain for two samples per packed instruction, in
                 // keep_t's order (p - mu as p + (-mu): the same value)
                 const float2 nmx = make_float2(-r0.x, -r0.x), nmy = make_float2(-r0.y, -r0.y),
@@ -284,7 +283,8 @@ __global__ void __launch_bounds__(128, SHADE ? 4 : 5) k_render(const RenderArgs 
                         const float2 c2 = __ffma2_rn(dy, __ffma2_rn(cyy, dy, __fmul2_rn(cyz, dz)),
                                                      __fmul2_rn(dz, __fmul2_rn(czz, dz)));
                         const float2 t2 = __ffma2_rn(dx, __ffma2_rn(cxx, dx, b2), c2);
-                        tt[2 * q] = t2.x; tt[2 * q + 1] = t2.y;
+                        tt[2 * q] = t2.x;
+                        tt[2 * q + 1] = 2 * q + 1 < gs ? t2.y : -INFINITY;  // an odd run's last lane is empty
                         dxs[2 * q] = dx.x; dxs[2 * q + 1] = dx.y;
                         dys[2 * q] = dy.x; dys[2 * q + 1] = dy.y;
                         dzs[2 * q] = dz.x; dzs[2 * q + 1] = dz.y;
@@ -295,14 +295,14 @@ __global__ void __launch_bounds__(128, SHADE ? 4 : 5) k_render(const RenderArgs 
                 }
 #pragma unroll
                 for (int s = 0; s < G; ++s) {
-                    if (s < gs) {
+                    {  // slots past the run hold -inf
                         const float dx = dxs[s], dy = dys[s], dz = dzs[s];
                         const float t = tt[s];
                         if (t > a.T) {
                             const float gv = ex2_approx(t);
                             N[s] = fmaf(r2.y, gv, N[s]);
                             D[s] = fmaf(r2.z, gv, D[s]);
-                            ++kept;
+                            ++kept_g;
                             if (SHADE) {
                                 // grad G = G ln2 grad t, grad t = 2 Q d in the coefficient layout
                                 const float lg = gv * kLn2;
@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(128, SHADE ? 4 : 5) k_render(const RenderArgs 
                     }
                 }
             }
+            kept += kept_g;
             // classify, shade and composite the group's samples in order
 #pragma unroll
             for (int s = 0; s < G; ++s) {

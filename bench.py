@@ -668,7 +668,7 @@ def run_render(args):
     img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 0)):
         gve.gve_render(cam, W, H, tf, ro, out=img)
-    _, kept, tested = gve.gve_render(cam, W, H, tf, ro, out=img, want_kept="both")
+    _, kept, tested = gve.gve_render(cam, W, H, tf, ro, out=img, want_tested=True)
     clocks = Clocks(0)
     clocks.start()
     torch.cuda.synchronize()

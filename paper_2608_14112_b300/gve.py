@@ -299,10 +299,12 @@ def gve_render_prepare(prims: torch.Tensor, shape, opts: EvalOptions | None = No
 
 
 def gve_render(camera, width: int, height: int, tf: torch.Tensor, opts: RenderOptions | None = None,
-               device=None, out: torch.Tensor | None = None, want_kept: bool = False):
+               device=None, out: torch.Tensor | None = None, want_kept: bool = False, want_tested: bool = False):
     """RGBA image (height, width, 4) of the prepared set.  camera = (eye,
     right, up, forward, tan_half_fovy) in voxel coordinates; tf = (n, 4)
-    float32 CUDA tensor over V in [0, 1]."""
+    float32 CUDA tensor over V in [0, 1].  With want_kept the kept (sample,
+    Gaussian) pairs follow the image, with want_tested also the tested
+    pairs."""
     o = opts or RenderOptions()
     if tf.dtype != torch.float32 or tf.dim() != 2 or tf.shape[1] != 4 or not tf.is_cuda or not tf.is_contiguous():
         raise ValueError("tf must be a contiguous CUDA float32 tensor of shape (n, 4)")
@@ -317,11 +319,12 @@ def gve_render(camera, width: int, height: int, tf: torch.Tensor, opts: RenderOp
     if out is None:
         out = torch.empty((int(height), int(width), 4), dtype=torch.float32, device=dev)
     kept, tested = ctypes.c_int64(0), ctypes.c_int64(0)
+    want_kept = want_kept or want_tested
     c = context(dev.index)
     _check(lib().gve_render(c, ctypes.byref(cam), ctypes.byref(ro), _ptr(out),
-                            ctypes.byref(kept) if want_kept else None, ctypes.byref(tested) if want_kept else None,
-                            _stream(dev)), c)
-    if want_kept == "both":
+                            ctypes.byref(kept) if want_kept else None,
+                            ctypes.byref(tested) if want_tested else None, _stream(dev)), c)
+    if want_tested:
         return out, kept.value, tested.value
     return (out, kept.value) if want_kept else out
 

@@ -4,9 +4,9 @@
 // iteration's points, then the shared chain rule and Adam (optim.cu).
 //
 // The points are few (at most kMaxSamples), so they are bucketed into a
-// coarse grid of cells (32^3 voxels, coarser for very large grids) by one
-// CTA (bitonic sort of (cell, sample), z-major cells, plus cstart[c] = the
-// number of points in cells before c), and the Gaussians do the searching:
+// coarse grid of cells (32^3 voxels, coarser for very large grids) by a
+// counting sort (z-major cells, cstart[c] = the number of points in cells
+// before c), and the Gaussians do the searching:
 // one thread per Gaussian walks the (z, y) rows of cells its conservative
 // box overlaps -- the points of a row's cell range are one contiguous run of
 // the sorted points -- and tests each with the same float32 keep chain as
@@ -30,7 +30,6 @@ namespace gve {
 namespace {
 
 constexpr int kMaxSamples = 8192;
-constexpr int kCellSortThreads = 1024;
 constexpr long long kMaxCells = 1ll << 21;
 
 struct CellGrid {
@@ -59,60 +58,64 @@ __device__ __forceinline__ int cell_of(float p, int n, int shift, int nc)
     return c < nc ? c : nc - 1;
 }
 
-// One CTA: sort the S points by cell (bitonic over the next power of two),
-// write the sorted points, their original indices, the sorted position of
-// each original index, and cstart[c] for every cell c = 0 .. ncells (binary
-// search of the sorted cells).
-__global__ void __launch_bounds__(kCellSortThreads) k_cell_sort(const float4* __restrict__ pts, int S, int nx,
-                                                                 int ny, int nz, CellGrid cg,
-                                                                 float4* __restrict__ spts,
-                                                                 uint32_t* __restrict__ order, uint32_t* __restrict__ inv,
-                                                                 uint32_t* __restrict__ cstart)
+// Points by cell: a counting sort (the order of points inside a cell does
+// not matter: the forward adds into each point's sums atomically).  Count
+// per cell, one CTA scans the counts into cstart[c] = the points in cells
+// before c (c = 0 .. ncells), then each point takes a slot of its cell by
+// counting the cell back down (the counters end at zero, ready for the next
+// iteration).  Writes the sorted points, their original indices and the
+// sorted position of each original index.
+__device__ __forceinline__ uint32_t point_cell(const float4& q, int nx, int ny, int nz, const CellGrid& cg)
 {
-    extern __shared__ unsigned long long sk[];
-    int P = 1;
-    while (P < S) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += kCellSortThreads) {
-        unsigned long long key = ~0ull;
-        if (i < S) {
-            const float4 q = pts[i];
-            const int cx = cell_of(q.x, nx, cg.shift, cg.ncx), cy = cell_of(q.y, ny, cg.shift, cg.ncy),
-                      cz = cell_of(q.z, nz, cg.shift, cg.ncz);
-            const unsigned long long cell = ((unsigned long long)cz * cg.ncy + cy) * cg.ncx + cx;
-            key = (cell << 32) | (unsigned long long)i;
-        }
-        sk[i] = key;
-    }
+    const int cx = cell_of(q.x, nx, cg.shift, cg.ncx), cy = cell_of(q.y, ny, cg.shift, cg.ncy),
+              cz = cell_of(q.z, nz, cg.shift, cg.ncz);
+    return (uint32_t)(((long long)cz * cg.ncy + cy) * cg.ncx + cx);
+}
+
+__global__ void __launch_bounds__(256) k_cell_count(const float4* __restrict__ pts, int P, int nx, int ny, int nz,
+                                                    CellGrid cg, uint32_t* __restrict__ ccnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) atomicAdd(&ccnt[point_cell(pts[i], nx, ny, nz, cg)], 1u);
+}
+
+__global__ void __launch_bounds__(1024) k_cell_scan(uint32_t* __restrict__ ccnt, long long ncells,
+                                                    uint32_t* __restrict__ cstart)
+{
+    __shared__ uint32_t part[1024];
+    const long long per = (ncells + blockDim.x - 1) / blockDim.x;
+    const long long lo = (long long)threadIdx.x * per, hi = lo + per < ncells ? lo + per : ncells;
+    uint32_t sum = 0;
+    for (long long c = lo; c < hi; ++c) sum += ccnt[c];
+    part[threadIdx.x] = sum;
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += kCellSortThreads) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned long long a = sk[i], b = sk[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) { sk[i] = b; sk[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan of the partials
+        const uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < S; i += kCellSortThreads) {
-        const uint32_t idx = (uint32_t)sk[i];
-        order[i] = idx;
-        inv[idx] = (uint32_t)i;
-        spts[i] = pts[idx];
+    uint32_t run = part[threadIdx.x] - sum;
+    for (long long c = lo; c < hi; ++c) {
+        cstart[c] = run;
+        run += ccnt[c];
     }
-    const long long ncells = (long long)cg.ncx * cg.ncy * cg.ncz;
-    for (long long c = threadIdx.x; c <= ncells; c += kCellSortThreads) {
-        int lo = 0, hi = S;  // first sorted point whose cell is >= c
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((long long)(sk[mid] >> 32) < c) lo = mid + 1;
-            else hi = mid;
-        }
-        cstart[c] = (uint32_t)lo;
-    }
+    if (threadIdx.x == blockDim.x - 1) cstart[ncells] = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_cell_scatter(const float4* __restrict__ pts, int P, int nx, int ny, int nz,
+                                                      CellGrid cg, const uint32_t* __restrict__ cstart,
+                                                      uint32_t* __restrict__ slot, float4* __restrict__ spts,
+                                                      uint32_t* __restrict__ order, uint32_t* __restrict__ inv)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const float4 q = pts[i];
+    const uint32_t c = point_cell(q, nx, ny, nz, cg);
+    const uint32_t pos = cstart[c] + atomicSub(&slot[c], 1u) - 1u;  // counts the cell back to zero
+    spts[pos] = q;
+    order[pos] = (uint32_t)i;
+    inv[i] = pos;
 }
 
 struct SampleArgs {
@@ -317,6 +320,7 @@ struct SampleBufs {
     uint32_t* order;
     uint32_t* inv;
     uint32_t* cstart;
+    uint32_t* ccnt;
     float2* nd;
     float2* gg;
     double* loss;
@@ -334,6 +338,8 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long P, long long n, SampleB
     SMP_TRY(ensure(c, c->s_order, sizeof(uint32_t) * P, s));
     SMP_TRY(ensure(c, c->s_inv, sizeof(uint32_t) * P, s));
     SMP_TRY(ensure(c, c->s_cell, sizeof(uint32_t) * (b.ncells + 1), s));
+    SMP_TRY(ensure(c, c->s_ccnt, sizeof(uint32_t) * b.ncells, s));
+    SMP_CUDA(cudaMemsetAsync(c->s_ccnt.p, 0, sizeof(uint32_t) * b.ncells, s), "memset cell counts");
     SMP_TRY(ensure(c, c->s_nd, sizeof(float2) * P, s));
     SMP_TRY(ensure(c, c->s_gg, sizeof(float2) * P, s));
     SMP_TRY(ensure(c, c->s_loss, sizeof(double), s));
@@ -347,6 +353,7 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long P, long long n, SampleB
     b.order = (uint32_t*)c->s_order.p;
     b.inv = (uint32_t*)c->s_inv.p;
     b.cstart = (uint32_t*)c->s_cell.p;
+    b.ccnt = (uint32_t*)c->s_ccnt.p;
     b.nd = (float2*)c->s_nd.p;
     b.gg = (float2*)c->s_gg.p;
     b.loss = (double*)c->s_loss.p;
@@ -369,10 +376,10 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
                        bool backward, cudaStream_t s)
 {
     const long long P = pr.smooth ? 2 * S : S;
-    int P2 = 1;
-    while (P2 < P) P2 <<= 1;
-    k_cell_sort<<<1, kCellSortThreads, sizeof(unsigned long long) * P2, s>>>(b.pts, (int)P, d.nx, d.ny, d.nz, b.cg,
-                                                                              b.spts, b.order, b.inv, b.cstart);
+    const unsigned pb = (unsigned)((P + 255) / 256);
+    k_cell_count<<<pb, 256, 0, s>>>(b.pts, (int)P, d.nx, d.ny, d.nz, b.cg, b.ccnt);
+    k_cell_scan<<<1, 1024, 0, s>>>(b.ccnt, b.ncells, b.cstart);
+    k_cell_scatter<<<pb, 256, 0, s>>>(b.pts, (int)P, d.nx, d.ny, d.nz, b.cg, b.cstart, b.ccnt, b.spts, b.order, b.inv);
     SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * P, s), "memset sums");
     SampleArgs a{};
     a.prims = prims;
@@ -393,7 +400,7 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     k_sample_loss<<<1, 1024, 0, s>>>(b.spts, b.order, b.inv, b.nd, (int)S, pr.smooth, o->rho0, occ, pr.l_rho, pr.l_sm,
                                      b.gg, b.loss, trace, iter, vt_out, b.terms);
     if (backward && n > 0) k_sample_grad<<<grid, 128, 0, s>>>(a);
-    c->launches += 2 + (n > 0 ? 2 + (backward ? 1 : 0) : 0);
+    c->launches += 4 + (n > 0 ? 2 + (backward ? 1 : 0) : 0);
     SMP_CUDA(cudaGetLastError(), "launch (sampled pass)");
     return GVE_OK;
 }
@@ -453,14 +460,6 @@ gve_status check_samples(gve_ctx* c, int64_t S, const gve_eval_opts* o, bool smo
     if (smooth && 2 * S > kMaxSamples)
         return fail(c, GVE_E_INVALID, "with smoothness partners, samples per iteration must be in [1, 4096]");
     if (!o->normalized) return fail(c, GVE_E_INVALID, "sampled refinement evaluates Eq. 3 (normalized = 1)");
-    static bool smem_set[64] = {};
-    const int dev = c->device;
-    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(k_cell_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(sizeof(unsigned long long) * kMaxSamples));
-        if (e != cudaSuccess) return cuda_fail(c, e, "cell sort shared memory");
-        smem_set[dev] = true;
-    }
     return GVE_OK;
 }
 

@@ -376,9 +376,10 @@ GVE_API gve_status gve_sample_loss_grad(gve_ctx* ctx, const float* prims_dev, in
  * reg (nullable) adds the regularisers.  adam_state and loss_trace_dev as
  * for gve_refine (the trace receives the objective per iteration).  stats
  * (optional) adds one full-grid evaluation after the last step for
- * sse_final / psnr_final; ms_total is the iterations' time, ms_bin its
- * preparation share (keep coefficients) and ms_brick its draw, search, loss
- * and gradient share (the chain rule and Adam are the rest). */
+ * sse_final / psnr_final; ms_total is the iterations' time, ms_brick its
+ * draw, search (with the keep coefficients, computed only for Gaussians
+ * whose box holds candidate points), loss and gradient share, ms_bin 0 (the
+ * chain rule and Adam are the rest). */
 GVE_API gve_status gve_refine_sampled(gve_ctx* ctx, float* prims_dev, int64_t n, const float* field_dev,
                                       gve_dims dims, const gve_schedule* sched, int64_t S, uint64_t seed,
                                       const gve_reg_opts* reg, float* adam_state_dev, double* loss_trace_dev,

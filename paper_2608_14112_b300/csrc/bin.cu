@@ -35,11 +35,6 @@ BinGeom make_geom(gve_dims d, int B)
 // ------------------------------------------------------------------------
 // prep
 // ------------------------------------------------------------------------
-__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
-
 // BIN = false: the keep coefficients only (the sampled path has no bricks)
 template <bool BIN>
 __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, long long n, BinGeom g,
@@ -56,47 +51,13 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
     b.K2 = -1.f;
     for (int j = 0; j < 3; ++j) { b.blo[j] = 0; b.bhi[j] = -1; }
     b.nonempty = 0;
-    float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
-
-    bool ok = true;
-    for (int j = 0; j < 12; ++j) ok = ok && isfinite(pf[j]);
-    double s[3], q[4], nq = 0.0, R[3][3], C[3][3];
+    KeepCoef kc;
+    keep_coefficients(pf, kc);
+    const bool ok = kc.ok;
+    const float4 r0 = kc.r0, r1 = kc.r1, r2 = kc.r2;
+    const double (&s)[3] = kc.s;
+    const double (&R)[3][3] = kc.R;
     if (ok) {
-        for (int j = 0; j < 3; ++j) s[j] = exp((double)pf[3 + j]);
-        double qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
-        nq = __dsqrt_rn(da(da(da(dm(qw, qw), dm(qx, qx)), dm(qy, qy)), dm(qz, qz)));
-        ok = nq > 0.0 && isfinite(nq);
-        for (int j = 0; j < 3; ++j) ok = ok && s[j] > 0.0 && isfinite(s[j]);
-        if (ok) {
-            q[0] = dd(qw, nq); q[1] = dd(qx, nq); q[2] = dd(qy, nq); q[3] = dd(qz, nq);
-            double w = q[0], x = q[1], y = q[2], z = q[3];
-            R[0][0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
-            R[0][1] = dm(2.0, ds(dm(x, y), dm(w, z)));
-            R[0][2] = dm(2.0, da(dm(x, z), dm(w, y)));
-            R[1][0] = dm(2.0, da(dm(x, y), dm(w, z)));
-            R[1][1] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
-            R[1][2] = dm(2.0, ds(dm(y, z), dm(w, x)));
-            R[2][0] = dm(2.0, ds(dm(x, z), dm(w, y)));
-            R[2][1] = dm(2.0, da(dm(y, z), dm(w, x)));
-            R[2][2] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
-            double inv[3];
-            for (int j = 0; j < 3; ++j) inv[j] = dd(1.0, dm(s[j], s[j]));
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 3; ++c)
-                    C[a][c] = da(da(dm(dm(R[a][0], R[c][0]), inv[0]), dm(dm(R[a][1], R[c][1]), inv[1])),
-                                 dm(dm(R[a][2], R[c][2]), inv[2]));
-        }
-    }
-    if (ok) {
-        // keep-test coefficients
-        double Q00 = dm(C[0][0], kNegHalfLog2e), Q11 = dm(C[1][1], kNegHalfLog2e);
-        double Q22 = dm(C[2][2], kNegHalfLog2e), Q01 = dm(C[0][1], kNegHalfLog2e);
-        double Q02 = dm(C[0][2], kNegHalfLog2e), Q12 = dm(C[1][2], kNegHalfLog2e);
-        double wd = 1.0 / (1.0 + exp(-(double)pf[11]));
-        r0 = make_float4(pf[0], pf[1], pf[2], (float)Q00);
-        r1 = make_float4((float)Q11, (float)Q22, (float)dm(2.0, Q01), (float)dm(2.0, Q02));
-        r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, pf[10]);
-
         // conservative brick cover
         if (!BIN) {
             float4* o = rec + 3 * i;

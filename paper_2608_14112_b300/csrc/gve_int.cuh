@@ -184,6 +184,68 @@ __device__ __forceinline__ int gauss_box(const float* prims, long long i, float 
     return 1;
 }
 
+// FP64 with explicit rounding (no contraction whatever the compiler flags)
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
+
+// Keep-test coefficients of one raw record (Eq. 2 activations, then
+// -log2(e)/2 Sigma^-1 and the weights), FP64 in a fixed order and rounded
+// once to float32: r0 = (mu, qxx), r1 = (qyy, qzz, 2 qxy, 2 qxz), r2 =
+// (2 qyz, w a, w, a); zero records when the record is invalid (non-finite
+// values, zero quaternion or scale).  s and R are the scales and rotation.
+struct KeepCoef {
+    float4 r0, r1, r2;
+    double s[3], R[3][3];
+    bool ok;
+};
+
+__device__ __forceinline__ void keep_coefficients(const float (&pf)[12], KeepCoef& o)
+{
+    o.r0 = o.r1 = o.r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool ok = true;
+    for (int j = 0; j < 12; ++j) ok = ok && isfinite(pf[j]);
+    double* s = o.s;
+    double(&R)[3][3] = o.R;
+    double C[3][3], nq = 0.0;
+    for (int j = 0; j < 3; ++j) s[j] = 0.0;
+    if (ok) {
+        for (int j = 0; j < 3; ++j) s[j] = exp((double)pf[3 + j]);
+        double qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
+        nq = __dsqrt_rn(da(da(da(dm(qw, qw), dm(qx, qx)), dm(qy, qy)), dm(qz, qz)));
+        ok = nq > 0.0 && isfinite(nq);
+        for (int j = 0; j < 3; ++j) ok = ok && s[j] > 0.0 && isfinite(s[j]);
+        if (ok) {
+            const double w = dd(qw, nq), x = dd(qx, nq), y = dd(qy, nq), z = dd(qz, nq);
+            R[0][0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
+            R[0][1] = dm(2.0, ds(dm(x, y), dm(w, z)));
+            R[0][2] = dm(2.0, da(dm(x, z), dm(w, y)));
+            R[1][0] = dm(2.0, da(dm(x, y), dm(w, z)));
+            R[1][1] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
+            R[1][2] = dm(2.0, ds(dm(y, z), dm(w, x)));
+            R[2][0] = dm(2.0, ds(dm(x, z), dm(w, y)));
+            R[2][1] = dm(2.0, da(dm(y, z), dm(w, x)));
+            R[2][2] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
+            double inv[3];
+            for (int j = 0; j < 3; ++j) inv[j] = dd(1.0, dm(s[j], s[j]));
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c)
+                    C[a][c] = da(da(dm(dm(R[a][0], R[c][0]), inv[0]), dm(dm(R[a][1], R[c][1]), inv[1])),
+                                 dm(dm(R[a][2], R[c][2]), inv[2]));
+        }
+    }
+    o.ok = ok;
+    if (!ok) return;
+    const double Q00 = dm(C[0][0], kNegHalfLog2e), Q11 = dm(C[1][1], kNegHalfLog2e);
+    const double Q22 = dm(C[2][2], kNegHalfLog2e), Q01 = dm(C[0][1], kNegHalfLog2e);
+    const double Q02 = dm(C[0][2], kNegHalfLog2e), Q12 = dm(C[1][2], kNegHalfLog2e);
+    const double wd = 1.0 / (1.0 + exp(-(double)pf[11]));
+    o.r0 = make_float4(pf[0], pf[1], pf[2], (float)Q00);
+    o.r1 = make_float4((float)Q11, (float)Q22, (float)dm(2.0, Q01), (float)dm(2.0, Q02));
+    o.r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, pf[10]);
+}
+
 // ---- launchers (bin.cu) --------------------------------------------------
 struct BinGeom {
     int nx, ny, nz, B, nbx, nby, nbz;

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const float4* __restrict__
 
 struct SampleArgs {
     const float* prims;
-    const float4* rec;
+    float4* rec;   // keep coefficients, written by the forward for Gaussians with candidates
     long long n;
     int nx, ny, nz;
     CellGrid cg;
@@ -176,13 +176,43 @@ __device__ __forceinline__ void for_candidates(const SampleArgs& a, const int lo
         }
 }
 
+// whether any point lies in the cells [lo, hi] (the rows for_candidates walks)
+__device__ __forceinline__ bool has_candidates(const SampleArgs& a, const int lo[3], const int hi[3])
+{
+    const long long rows = (long long)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+    if (2 * rows >= a.S) return a.S > 0;
+    for (int cz = lo[2]; cz <= hi[2]; ++cz)
+        for (int cy = lo[1]; cy <= hi[1]; ++cy) {
+            const long long base = ((long long)cz * a.cg.ncy + cy) * a.cg.ncx;
+            if (a.cstart[base + hi[0] + 1] > a.cstart[base + lo[0]]) return true;
+        }
+    return false;
+}
+
+// The keep coefficients are computed here, in FP64 as in the voxel path's
+// preparation, only for Gaussians whose box holds candidate points (about
+// half of them at 1.4 M Gaussians against 6,144 points), and stored for the
+// gradient pass, which takes the same decision.
 __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int lo[3], hi[3];
     if (!gauss_cells(a, i, lo, hi)) return;
-    const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
+    if (!has_candidates(a, lo, hi)) return;
+    float pf[12];
+    {
+        const float4* p4 = reinterpret_cast<const float4*>(a.prims) + 3 * i;
+        const float4 p0 = p4[0], p1 = p4[1], p2 = p4[2];
+        const float q[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
+        for (int j = 0; j < 12; ++j) pf[j] = q[j];
+    }
+    KeepCoef kc;
+    keep_coefficients(pf, kc);
+    const float4 r0 = kc.r0, r1 = kc.r1, r2 = kc.r2;
+    a.rec[3 * i] = r0;
+    a.rec[3 * i + 1] = r1;
+    a.rec[3 * i + 2] = r2;
     if (!(r2.z > 0.f)) return;  // invalid record (weight zero)
     for_candidates(a, lo, hi, [&](uint32_t s) {
         const float4 q = a.spts[s];
@@ -200,8 +230,10 @@ __global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
     if (i >= a.n) return;
     float A = 0.f, H = 0.f, S1[3] = {0.f, 0.f, 0.f}, S2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int lo[3], hi[3];
-    const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
-    if (gauss_cells(a, i, lo, hi) && r2.z > 0.f) {
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    const bool cand = gauss_cells(a, i, lo, hi) && has_candidates(a, lo, hi);
+    if (cand) { r0 = a.rec[3 * i]; r1 = a.rec[3 * i + 1]; r2 = a.rec[3 * i + 2]; }
+    if (cand && r2.z > 0.f) {
         for_candidates(a, lo, hi, [&](uint32_t s) {
             const float4 q = a.spts[s];
             const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
@@ -383,7 +415,7 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * P, s), "memset sums");
     SampleArgs a{};
     a.prims = prims;
-    a.rec = (const float4*)c->rec.p;
+    a.rec = (float4*)c->rec.p;
     a.n = n;
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
     a.cg = b.cg;
@@ -559,7 +591,6 @@ extern "C" gve_status gve_sample_loss_grad(gve_ctx* c, const float* prims, int64
     SampleBufs b;
     SMP_TRY(sample_bufs(c, d, P, n, b, s));
     SMP_CUDA(cudaMemcpyAsync(b.pts, pts, sizeof(float4) * P, cudaMemcpyDeviceToDevice, s), "copy points");
-    launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
     SMP_TRY(sample_pass(c, prims, n, d, o, S, pr, b, occ_thresh, nullptr, 0, vt_out, grad_out != nullptr, s));
     if (per_g) {
         launch_reg(prims, n, field, d, rt, b.extra, b.terms, nullptr, b.loss, s);
@@ -629,7 +660,6 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
         for (int it = it0; it < end; ++it) {
             const int step = sc->step0 + it;
             if (timed) SMP_CUDA(cudaEventRecord(c->sev[0][it - it0], s), "event");
-            launch_prep_rec(prims, n, o->trunc_k, (float4*)c->rec.p, s);
             if (timed) SMP_CUDA(cudaEventRecord(c->sev[1][it - it0], s), "event");
             launch_draw_samples(field, d, (const uint32_t*)c->s_hi.p, c->s_nh, (const uint32_t*)c->s_mid.p, c->s_nm,
                                 S, split[0], split[1], seed, (uint32_t)step, b.pts, nullptr, s);
@@ -656,7 +686,7 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
                 ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step + 1));
                 launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s,
                              per_g ? b.extra : nullptr);
-                c->launches += 2;
+                c->launches += 1;
             }
             c->launches += 1;
         }

@@ -166,22 +166,75 @@ typedef struct {
     int valid;
 } pred_t;
 
-/* Coefficients from the float32 parameter record; FP64 in a fixed order,
- * then rounded once to float32. */
+/* e^x in float32 by a fixed sequence of correctly rounded operations, so
+ * that the GPU reproduces it bit for bit: Cody-Waite reduction x = n ln2 + r
+ * (ln2 split into a 16-bit head and a tail, |r| <= ln2/2), a degree-7
+ * Taylor polynomial of e^r in Horner form with fused multiply-adds, and the
+ * exact scaling by 2^n.  Relative error below 2^-22 (pinned against exp). */
+static float exp_fixed(float x)
+{
+    if (x != x) return x;
+    if (x > 88.75f) return INFINITY;
+    if (x < -103.5f) return 0.0f;
+    const float n = rintf(x * 1.44269504f);
+    float r = fmaf(-n, 0.693145751953125f, x);
+    r = fmaf(-n, 1.42860677e-06f, r);
+    float p = 1.98412698e-04f;
+    p = fmaf(p, r, 1.38888889e-03f);
+    p = fmaf(p, r, 8.33333333e-03f);
+    p = fmaf(p, r, 4.16666667e-02f);
+    p = fmaf(p, r, 1.66666667e-01f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    return ldexpf(p, (int)n);
+}
+
+float or_exp_fixed(float x) { return exp_fixed(x); }
+
+/* Coefficients from the float32 parameter record: the activations and
+ * -log2(e)/2 Sigma^-1 = -log2(e)/2 R diag(s^-2) R^T in float32, one fixed
+ * sequence of correctly rounded operations (the written order, no
+ * contraction), the scales by exp_fixed. */
 static void pred_coeffs(const float* p32, pred_t* P)
 {
-    double p[12];
-    for (int i = 0; i < 12; ++i) p[i] = (double)p32[i];
-    act_t A;
-    activate(p, &A);
-    P->valid = A.valid;
+    int ok = 1;
+    for (int i = 0; i < 12; ++i) ok = ok && isfinite(p32[i]);
     for (int j = 0; j < 3; ++j) P->mu[j] = p32[j];
-    if (!A.valid) return;
-    double Q00 = A.C[0][0] * OR_NEG_HALF_LOG2E, Q11 = A.C[1][1] * OR_NEG_HALF_LOG2E;
-    double Q22 = A.C[2][2] * OR_NEG_HALF_LOG2E, Q01 = A.C[0][1] * OR_NEG_HALF_LOG2E;
-    double Q02 = A.C[0][2] * OR_NEG_HALF_LOG2E, Q12 = A.C[1][2] * OR_NEG_HALF_LOG2E;
-    P->qxx = (float)Q00; P->qyy = (float)Q11; P->qzz = (float)Q22;
-    P->qxy2 = (float)(2.0 * Q01); P->qxz2 = (float)(2.0 * Q02); P->qyz2 = (float)(2.0 * Q12);
+    P->valid = 0;
+    if (!ok) return;
+    float s[3];
+    for (int j = 0; j < 3; ++j) s[j] = exp_fixed(p32[3 + j]);
+    const float qw = p32[6], qx = p32[7], qy = p32[8], qz = p32[9];
+    const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
+    const float nq = sqrtf(n2);
+    if (!(nq > 0.0f) || !isfinite(nq)) return;
+    for (int j = 0; j < 3; ++j)
+        if (!(s[j] > 0.0f) || !isfinite(s[j])) return;
+    const float w = qw / nq, x = qx / nq, y = qy / nq, z = qz / nq;
+    float R[3][3];
+    R[0][0] = 1.0f - 2.0f * (y * y + z * z);
+    R[0][1] = 2.0f * (x * y - w * z);
+    R[0][2] = 2.0f * (x * z + w * y);
+    R[1][0] = 2.0f * (x * y + w * z);
+    R[1][1] = 1.0f - 2.0f * (x * x + z * z);
+    R[1][2] = 2.0f * (y * z - w * x);
+    R[2][0] = 2.0f * (x * z - w * y);
+    R[2][1] = 2.0f * (y * z + w * x);
+    R[2][2] = 1.0f - 2.0f * (x * x + y * y);
+    float inv[3];
+    for (int j = 0; j < 3; ++j) inv[j] = 1.0f / (s[j] * s[j]);
+    const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    float Q[6];
+    const float nhl = (float)OR_NEG_HALF_LOG2E;
+    for (int q = 0; q < 6; ++q) {
+        const int a = ab[q][0], b = ab[q][1];
+        const float c = ((R[a][0] * R[b][0]) * inv[0] + (R[a][1] * R[b][1]) * inv[1]) + (R[a][2] * R[b][2]) * inv[2];
+        Q[q] = c * nhl;
+    }
+    P->qxx = Q[0]; P->qyy = Q[1]; P->qzz = Q[2];
+    P->qxy2 = 2.0f * Q[3]; P->qxz2 = 2.0f * Q[4]; P->qyz2 = 2.0f * Q[5];
+    P->valid = 1;
 }
 
 static float pred_threshold(float k)

@@ -61,6 +61,8 @@ def lib():
             L.or_philox4x32_10.argtypes = [P, P, P]
             L.or_pred_t.argtypes = [P, i32, i32, i32]
             L.or_pred_t.restype = f32
+            L.or_exp_fixed.argtypes = [f32]
+            L.or_exp_fixed.restype = f32
             L.or_pred_threshold.argtypes = [f32]
             L.or_pred_threshold.restype = f32
             L.or_eval_region.argtypes = [P, P, i64, P, P, P, f32, f64, i32, i32, P, P, P]
@@ -165,6 +167,12 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 def pred_threshold(k: float) -> float:
     """float32 threshold T of the kept-pair test t > T."""
     return float(lib().or_pred_threshold(float(k)))
+
+
+def exp_fixed(x: float) -> float:
+    """The float32 exponential both sides use for the scales of the keep
+    coefficients (a fixed sequence of correctly rounded operations)."""
+    return float(lib().or_exp_fixed(float(x)))
 
 
 def pred_t(p32_record, x: int, y: int, z: int) -> float:

@@ -53,17 +53,37 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
     b.nonempty = 0;
     KeepCoef kc;
     keep_coefficients(pf, kc);
-    const bool ok = kc.ok;
     const float4 r0 = kc.r0, r1 = kc.r1, r2 = kc.r2;
-    const double (&s)[3] = kc.s;
-    const double (&R)[3][3] = kc.R;
+    if (!BIN) {
+        float4* o = rec + 3 * i;
+        o[0] = r0; o[1] = r1; o[2] = r2;
+        return;
+    }
+    // the conservative brick cover from FP64 scales and rotation (the CPU
+    // reference of the binner uses the same FP64 activation)
+    bool ok = true;
+    for (int j = 0; j < 12; ++j) ok = ok && isfinite(pf[j]);
+    double s[3] = {0.0, 0.0, 0.0}, R[3][3];
     if (ok) {
-        // conservative brick cover
-        if (!BIN) {
-            float4* o = rec + 3 * i;
-            o[0] = r0; o[1] = r1; o[2] = r2;
-            return;
+        for (int j = 0; j < 3; ++j) s[j] = exp((double)pf[3 + j]);
+        const double qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
+        const double nq = __dsqrt_rn(da(da(da(dm(qw, qw), dm(qx, qx)), dm(qy, qy)), dm(qz, qz)));
+        ok = nq > 0.0 && isfinite(nq);
+        for (int j = 0; j < 3; ++j) ok = ok && s[j] > 0.0 && isfinite(s[j]);
+        if (ok) {
+            const double w = dd(qw, nq), x = dd(qx, nq), y = dd(qy, nq), z = dd(qz, nq);
+            R[0][0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
+            R[0][1] = dm(2.0, ds(dm(x, y), dm(w, z)));
+            R[0][2] = dm(2.0, da(dm(x, z), dm(w, y)));
+            R[1][0] = dm(2.0, da(dm(x, y), dm(w, z)));
+            R[1][1] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
+            R[1][2] = dm(2.0, ds(dm(y, z), dm(w, x)));
+            R[2][0] = dm(2.0, ds(dm(x, z), dm(w, y)));
+            R[2][1] = dm(2.0, da(dm(y, z), dm(w, x)));
+            R[2][2] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
         }
+    }
+    if (ok) {
         double smin = s[0], smax = s[0];
         for (int j = 1; j < 3; ++j) { smin = fmin(smin, s[j]); smax = fmax(smax, s[j]); }
         double ratio = dd(smax, smin);

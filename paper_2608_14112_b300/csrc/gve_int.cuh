@@ -190,60 +190,87 @@ __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
 
-// Keep-test coefficients of one raw record (Eq. 2 activations, then
-// -log2(e)/2 Sigma^-1 and the weights), FP64 in a fixed order and rounded
-// once to float32: r0 = (mu, qxx), r1 = (qyy, qzz, 2 qxy, 2 qxz), r2 =
-// (2 qyz, w a, w, a); zero records when the record is invalid (non-finite
-// values, zero quaternion or scale).  s and R are the scales and rotation.
+// e^x in float32 by a fixed sequence of correctly rounded operations (the
+// CPU reference runs the same sequence, so both agree bit for bit):
+// Cody-Waite reduction x = n ln2 + r with ln2 split into a 16-bit head and a
+// tail, a degree-7 Taylor polynomial of e^r in Horner form with fused
+// multiply-adds, and the exact scaling by 2^n.  Relative error below 2^-22.
+__device__ __forceinline__ float exp_fixed(float x)
+{
+    if (x != x) return x;
+    if (x > 88.75f) return INFINITY;
+    if (x < -103.5f) return 0.0f;
+    const float n = rintf(__fmul_rn(x, 1.44269504f));
+    float r = __fmaf_rn(-n, 0.693145751953125f, x);
+    r = __fmaf_rn(-n, 1.42860677e-06f, r);
+    float p = 1.98412698e-04f;
+    p = __fmaf_rn(p, r, 1.38888889e-03f);
+    p = __fmaf_rn(p, r, 8.33333333e-03f);
+    p = __fmaf_rn(p, r, 4.16666667e-02f);
+    p = __fmaf_rn(p, r, 1.66666667e-01f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    return ldexpf(p, (int)n);
+}
+
+// Keep-test coefficients of one raw record: the Eq. 2 activations and
+// -log2(e)/2 Sigma^-1 = -log2(e)/2 R diag(s^-2) R^T in float32, one fixed
+// sequence of correctly rounded operations (explicit intrinsics: no
+// contraction whatever the file's flags), the scales by exp_fixed:
+// r0 = (mu, qxx), r1 = (qyy, qzz, 2 qxy, 2 qxz), r2 = (2 qyz, w a, w, a);
+// zero records when the record is invalid (non-finite values, zero
+// quaternion or scale).
 struct KeepCoef {
     float4 r0, r1, r2;
-    double s[3], R[3][3];
     bool ok;
 };
 
 __device__ __forceinline__ void keep_coefficients(const float (&pf)[12], KeepCoef& o)
 {
     o.r0 = o.r1 = o.r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    o.ok = false;
     bool ok = true;
     for (int j = 0; j < 12; ++j) ok = ok && isfinite(pf[j]);
-    double* s = o.s;
-    double(&R)[3][3] = o.R;
-    double C[3][3], nq = 0.0;
-    for (int j = 0; j < 3; ++j) s[j] = 0.0;
-    if (ok) {
-        for (int j = 0; j < 3; ++j) s[j] = exp((double)pf[3 + j]);
-        double qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
-        nq = __dsqrt_rn(da(da(da(dm(qw, qw), dm(qx, qx)), dm(qy, qy)), dm(qz, qz)));
-        ok = nq > 0.0 && isfinite(nq);
-        for (int j = 0; j < 3; ++j) ok = ok && s[j] > 0.0 && isfinite(s[j]);
-        if (ok) {
-            const double w = dd(qw, nq), x = dd(qx, nq), y = dd(qy, nq), z = dd(qz, nq);
-            R[0][0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
-            R[0][1] = dm(2.0, ds(dm(x, y), dm(w, z)));
-            R[0][2] = dm(2.0, da(dm(x, z), dm(w, y)));
-            R[1][0] = dm(2.0, da(dm(x, y), dm(w, z)));
-            R[1][1] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
-            R[1][2] = dm(2.0, ds(dm(y, z), dm(w, x)));
-            R[2][0] = dm(2.0, ds(dm(x, z), dm(w, y)));
-            R[2][1] = dm(2.0, da(dm(y, z), dm(w, x)));
-            R[2][2] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
-            double inv[3];
-            for (int j = 0; j < 3; ++j) inv[j] = dd(1.0, dm(s[j], s[j]));
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 3; ++c)
-                    C[a][c] = da(da(dm(dm(R[a][0], R[c][0]), inv[0]), dm(dm(R[a][1], R[c][1]), inv[1])),
-                                 dm(dm(R[a][2], R[c][2]), inv[2]));
-        }
-    }
-    o.ok = ok;
     if (!ok) return;
-    const double Q00 = dm(C[0][0], kNegHalfLog2e), Q11 = dm(C[1][1], kNegHalfLog2e);
-    const double Q22 = dm(C[2][2], kNegHalfLog2e), Q01 = dm(C[0][1], kNegHalfLog2e);
-    const double Q02 = dm(C[0][2], kNegHalfLog2e), Q12 = dm(C[1][2], kNegHalfLog2e);
-    const double wd = 1.0 / (1.0 + exp(-(double)pf[11]));
-    o.r0 = make_float4(pf[0], pf[1], pf[2], (float)Q00);
-    o.r1 = make_float4((float)Q11, (float)Q22, (float)dm(2.0, Q01), (float)dm(2.0, Q02));
-    o.r2 = make_float4((float)dm(2.0, Q12), (float)(wd * (double)pf[10]), (float)wd, pf[10]);
+    float s[3];
+    for (int j = 0; j < 3; ++j) s[j] = exp_fixed(pf[3 + j]);
+    const float qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
+    const float n2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(qw, qw), __fmul_rn(qx, qx)), __fmul_rn(qy, qy)),
+                               __fmul_rn(qz, qz));
+    const float nq = __fsqrt_rn(n2);
+    if (!(nq > 0.0f) || !isfinite(nq)) return;
+    for (int j = 0; j < 3; ++j)
+        if (!(s[j] > 0.0f) || !isfinite(s[j])) return;
+    const float w = __fdiv_rn(qw, nq), x = __fdiv_rn(qx, nq), y = __fdiv_rn(qy, nq), z = __fdiv_rn(qz, nq);
+    float R[3][3];
+    R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, y), __fmul_rn(z, z))));
+    R[0][1] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
+    R[0][2] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, z), __fmul_rn(w, y)));
+    R[1][0] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
+    R[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(z, z))));
+    R[1][2] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(y, z), __fmul_rn(w, x)));
+    R[2][0] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(x, z), __fmul_rn(w, y)));
+    R[2][1] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, z), __fmul_rn(w, x)));
+    R[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y))));
+    float inv[3];
+    for (int j = 0; j < 3; ++j) inv[j] = __fdiv_rn(1.0f, __fmul_rn(s[j], s[j]));
+    const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    const float nhl = (float)kNegHalfLog2e;
+    float Q[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const int a = ab[q][0], b = ab[q][1];
+        const float c = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(R[a][0], R[b][0]), inv[0]),
+                                            __fmul_rn(__fmul_rn(R[a][1], R[b][1]), inv[1])),
+                                  __fmul_rn(__fmul_rn(R[a][2], R[b][2]), inv[2]));
+        Q[q] = __fmul_rn(c, nhl);
+    }
+    const float wd = __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_fixed(-pf[11])));
+    o.r0 = make_float4(pf[0], pf[1], pf[2], Q[0]);
+    o.r1 = make_float4(Q[1], Q[2], __fmul_rn(2.0f, Q[3]), __fmul_rn(2.0f, Q[4]));
+    o.r2 = make_float4(__fmul_rn(2.0f, Q[5]), __fmul_rn(wd, pf[10]), wd, pf[10]);
+    o.ok = true;
 }
 
 // ---- launchers (bin.cu) --------------------------------------------------

@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--shade", action="store_true", help="render with gradient shading")
     ap.add_argument("--term", type=float, default=1e-3, help="early ray termination threshold of the render workload")
     ap.add_argument("--reg", action="store_true", help="sampled workload: the full objective (five regularisers)")
+    ap.add_argument("--sampled-n", type=int, default=1024, help="grid edge of the sampled workload (1024 or 512)")
     ap.add_argument("--prop-iters", type=int, default=200, help="refinement iterations per proposal evaluation")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
@@ -446,8 +447,10 @@ def run_sampled(args):
     stream = torch.cuda.current_stream(dev)
     S = args.samples
     opts = gve.EvalOptions(trunc_k=5.0)
-    V = inputs.fbm_fronts(1024, seed=4, device=dev)
-    prims, info = gve.gve_allocate(V, 1_400_000, seed=args.seed)
+    sn = args.sampled_n
+    budget = 1_400_000 if sn >= 1024 else 175_000
+    V = inputs.fbm_fronts(sn, seed=4, device=dev)
+    prims, info = gve.gve_allocate(V, budget, seed=args.seed)
     prims0 = prims.clone()
     state = torch.zeros((2, prims.shape[0], 12), dtype=torch.float32, device=dev)
     reg = gve.RegOptions(anneal_iters=args.warmup + args.steps) if args.reg else None
@@ -496,7 +499,7 @@ def run_sampled(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     Vd.copy_(Vh, non_blocking=True)
-    gve.gve_allocate(Vd, 1_400_000, seed=args.seed, out=pd)
+    gve.gve_allocate(Vd, budget, seed=args.seed, out=pd)
     gve.gve_refine_sampled(pd, Vd, args.warmup + args.steps, S=S, seed=args.seed, opts=opts, want_stats=False,
                            reg=reg)
     ph.copy_(pd, non_blocking=True)
@@ -512,7 +515,7 @@ def run_sampled(args):
     out = {"metric": SAMPLED_METRIC, "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": value / PAPER_SAMPLED_IT_S, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "fbm_fronts_1024^3_N1.4M_sampled" + ("_full_objective" if reg else ""),
+           "config": {"workload": f"fbm_fronts_{sn}^3_N{N}_sampled" + ("_full_objective" if reg else ""),
                       "voxels": int(V.numel()), "gaussians": N,
                       "samples_per_iter": S, "trunc_k": 5.0, "lr": 1e-2,
                       "baseline_note": "paper: Miranda 1024^3 on an RTX 4090; here a synthetic stand-in field",

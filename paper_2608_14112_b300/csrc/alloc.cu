@@ -922,13 +922,23 @@ __global__ void __launch_bounds__(256) k_reg(const float* __restrict__ prims, lo
         e4[1] = make_float4(g[4], g[5], g[6], g[7]);
         e4[2] = make_float4(g[8], g[9], g[10], g[11]);
     }
-    double da = (double)sa - (double)ca, dn = (double)sn - (double)cn, dc = (double)sc - (double)cc;
-    for (int o = 16; o > 0; o >>= 1) {
-        da += __shfl_xor_sync(0xffffffffu, da, o);
-        dn += __shfl_xor_sync(0xffffffffu, dn, o);
-        dc += __shfl_xor_sync(0xffffffffu, dc, o);
-    }
+    // compensated pairs (value s - c) merged across the warp in float32 with
+    // an exact TwoSum of the heads; FP64 once per warp
+    auto wmerge = [](float& s0, float& c0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s1 = __shfl_xor_sync(0xffffffffu, s0, o), c1 = __shfl_xor_sync(0xffffffffu, c0, o);
+            const float t = s0 + s1;
+            const float bp = t - s0;
+            const float e = (s0 - (t - bp)) + (s1 - bp);
+            s0 = t;
+            c0 = (c0 + c1) - e;
+        }
+    };
+    wmerge(sa, ca);
+    wmerge(sn, cn);
+    wmerge(sc, cc);
     if ((threadIdx.x & 31) == 0) {
+        const double da = (double)sa - (double)ca, dn = (double)sn - (double)cn, dc = (double)sc - (double)cc;
         atomicAdd(terms + 3, da * invN);
         atomicAdd(terms + 4, dn * invN);
         atomicAdd(terms + 5, dc * invN);

@@ -30,6 +30,15 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
     if (i >= n) return;
     const float4* a4 = reinterpret_cast<const float4*>(acc) + 3 * i;
     const float4 c0 = a4[0], c1 = a4[1], c2 = a4[2];
+    // the Adam moments are loaded with the sums, before any arithmetic, so
+    // all of the record's loads are in flight at once
+    float4 mv[6] = {};
+    if (do_adam) {
+        const float4* m4l = reinterpret_cast<const float4*>(m) + 3 * i;
+        const float4* v4l = reinterpret_cast<const float4*>(v) + 3 * i;
+        mv[0] = m4l[0]; mv[1] = m4l[1]; mv[2] = m4l[2];
+        mv[3] = v4l[0]; mv[4] = v4l[1]; mv[5] = v4l[2];
+    }
     if (acc_zero) {
         float4* z4 = reinterpret_cast<float4*>(acc_zero) + 3 * i;
         const float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -135,7 +144,7 @@ __global__ void __launch_bounds__(128) k_chain(const float* acc, float* acc_zero
     float mm[12], vv[12];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float4 a = m4[k], b = v4[k];
+        const float4 a = mv[k], b = mv[3 + k];
         mm[4 * k] = a.x; mm[4 * k + 1] = a.y; mm[4 * k + 2] = a.z; mm[4 * k + 3] = a.w;
         vv[4 * k] = b.x; vv[4 * k + 1] = b.y; vv[4 * k + 2] = b.z; vv[4 * k + 3] = b.w;
     }

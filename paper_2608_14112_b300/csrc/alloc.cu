@@ -937,7 +937,24 @@ __global__ void __launch_bounds__(256) k_reg(const float* __restrict__ prims, lo
     wmerge(sa, ca);
     wmerge(sn, cn);
     wmerge(sc, cc);
-    if ((threadIdx.x & 31) == 0) {
+    // then across the CTA's warps, so one set of FP64 atomics leaves per CTA
+    // (per-warp atomics on five addresses serialised in L2)
+    __shared__ float red[8][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[warp][0] = sa; red[warp][1] = ca; red[warp][2] = sn;
+        red[warp][3] = cn; red[warp][4] = sc; red[warp][5] = cc;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const bool in = lane < (int)(blockDim.x >> 5);
+    sa = in ? red[lane][0] : 0.f; ca = in ? red[lane][1] : 0.f;
+    sn = in ? red[lane][2] : 0.f; cn = in ? red[lane][3] : 0.f;
+    sc = in ? red[lane][4] : 0.f; cc = in ? red[lane][5] : 0.f;
+    wmerge(sa, ca);
+    wmerge(sn, cn);
+    wmerge(sc, cc);
+    if (lane == 0) {
         const double da = (double)sa - (double)ca, dn = (double)sn - (double)cn, dc = (double)sc - (double)cc;
         atomicAdd(terms + 3, da * invN);
         atomicAdd(terms + 4, dn * invN);

@@ -86,7 +86,13 @@ __global__ void __launch_bounds__(1024) k_cell_scan(uint32_t* __restrict__ ccnt,
     const long long per = (ncells + blockDim.x - 1) / blockDim.x;
     const long long lo = (long long)threadIdx.x * per, hi = lo + per < ncells ? lo + per : ncells;
     uint32_t sum = 0;
-    for (long long c = lo; c < hi; ++c) sum += ccnt[c];
+    for (long long c = lo; c < hi; c += 8) {  // eight loads in flight
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = c + k < hi ? ccnt[c + k] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += v[k];
+    }
     part[threadIdx.x] = sum;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan of the partials
@@ -96,9 +102,16 @@ __global__ void __launch_bounds__(1024) k_cell_scan(uint32_t* __restrict__ ccnt,
         __syncthreads();
     }
     uint32_t run = part[threadIdx.x] - sum;
-    for (long long c = lo; c < hi; ++c) {
-        cstart[c] = run;
-        run += ccnt[c];
+    for (long long c = lo; c < hi; c += 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = c + k < hi ? ccnt[c + k] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (c + k < hi) {
+                cstart[c + k] = run;
+                run += v[k];
+            }
     }
     if (threadIdx.x == blockDim.x - 1) cstart[ncells] = part[threadIdx.x];
 }

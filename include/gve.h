@@ -134,7 +134,9 @@ typedef struct {
 typedef struct gve_ctx gve_ctx;
 
 /* Context on CUDA device `device`.  Creates no stream; allocates scratch
- * lazily.  *out is NULL on failure. */
+ * lazily.  *out is NULL on failure.  A context's scratch serves one call at a
+ * time: calls on one context from several threads, or overlapping on several
+ * streams, must be serialised by the caller (one context per stream). */
 GVE_API gve_status gve_ctx_create(gve_ctx** out, int device);
 /* Frees the context's scratch (synchronises the device first). NULL is ok. */
 GVE_API void gve_ctx_destroy(gve_ctx* ctx);

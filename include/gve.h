@@ -301,7 +301,9 @@ GVE_API gve_status gve_proposal_backward(gve_ctx* ctx, const float* model_dev, c
  * stage_ms (host, nullable, [4]) receives the device time in ms of the
  * first sweep, of the second sweep with the exact select and of the whole
  * pass, then the number of kernels the call launched.
- * Two sweeps of the field, no per-voxel scratch; synchronises `stream`.
+ * One stencil sweep of the field, which also keeps each voxel's gradient
+ * bits in the context (4 bytes per voxel, held until the context is
+ * destroyed), then one streaming sweep of those bits; synchronises `stream`.
  * GVE_E_INVALID on null pointers, non-positive sizes or an axis above 2^24. */
 GVE_API gve_status gve_structure_stats(gve_ctx* ctx, const float* field_dev, gve_dims dims, double* out,
                                        double* stage_ms, void* stream);

@@ -1099,19 +1099,15 @@ __device__ __forceinline__ void load_chunk(const StatGrid& g, const Row& r, int 
 // operations as grad_mag: one-sided differences at the borders, squares
 // summed x, y, then z.  Leaves xp, yp, zp holding the +1 neighbours where
 // they exist.
-template <bool S16>
-__device__ __forceinline__ float chunk_grad(const StatGrid& g, const Row& r, int x, int lane, Vals<S16>& q)
+// float32 |grad V| of one voxel from its six neighbours, the same operations
+// as grad_mag: one-sided differences at the borders, squares summed x, y,
+// then z (both sweep layouts call this, so the gradient bits agree)
+__device__ __forceinline__ float voxel_grad(const StatGrid& g, const Row& r, float c, float xm, float xp, bool xlo,
+                                            bool xhi, float ym, float yp, float zm, float zp)
 {
-    const float c = q.c;
-    const float um = __shfl_up_sync(0xffffffffu, c, 1);
-    const float dn = __shfl_down_sync(0xffffffffu, c, 1);
-    if (lane != 0) q.xm = um;
-    if (lane != 31) q.xp = dn;
-    if (x >= g.nx) return 0.0f;
-    const bool xlo = x > 0, xhi = x + 1 < g.nx;
-    const float lx = xlo ? q.xm : c, hx = xhi ? q.xp : c;
-    const float ly = r.ylo ? q.ym : c, hy = r.yhi ? q.yp : c;
-    const float lz = r.zlo ? q.zm : c, hz = r.zhi ? q.zp : c;
+    const float lx = xlo ? xm : c, hx = xhi ? xp : c;
+    const float ly = r.ylo ? ym : c, hy = r.yhi ? yp : c;
+    const float lz = r.zlo ? zm : c, hz = r.zhi ? zp : c;
     const float gx = g.nx < 2 ? 0.0f : ((xlo && xhi) ? 0.5f : 1.0f) * (hx - lx);
     const float gy = g.ny < 2 ? 0.0f : ((r.ylo && r.yhi) ? 0.5f : 1.0f) * (hy - ly);
     const float gz = g.nz < 2 ? 0.0f : ((r.zlo && r.zhi) ? 0.5f : 1.0f) * (hz - lz);
@@ -1121,12 +1117,44 @@ __device__ __forceinline__ float chunk_grad(const StatGrid& g, const Row& r, int
     return sqrtf(sq);
 }
 
+template <bool S16>
+__device__ __forceinline__ float chunk_grad(const StatGrid& g, const Row& r, int x, int lane, Vals<S16>& q)
+{
+    const float c = q.c;
+    const float um = __shfl_up_sync(0xffffffffu, c, 1);
+    const float dn = __shfl_down_sync(0xffffffffu, c, 1);
+    if (lane != 0) q.xm = um;
+    if (lane != 31) q.xp = dn;
+    if (x >= g.nx) return 0.0f;
+    return voxel_grad(g, r, c, q.xm, q.xp, x > 0, x + 1 < g.nx, q.ym, q.yp, q.zm, q.zp);
+}
+
 constexpr int kBatch1 = 4;
 constexpr int kBatch2 = 8;
 
+// sweep 1 also writes each voxel's gradient bits (kStatEmpty where the
+// voxel is not occupied), so that sweep 2 reads 4 bytes per voxel instead of
+// re-evaluating the stencil
+constexpr uint32_t kStatEmpty = 0xFFFFFFFFu;
+
+// block sums of `n` doubles per warp (red[warp][k]); thread k < n of warp 0
+// adds the block's k-th sum to out[k]
+template <int n>
+__device__ __forceinline__ void block_add(double (&red)[8][n], double* __restrict__ out)
+{
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid == 0 && lane < n) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][lane];
+        atomicAdd(out + lane, t);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_stat_sweep1(StatGrid g, float thr, double* __restrict__ sums,
                                                      unsigned long long* __restrict__ cnt,
-                                                     unsigned long long* __restrict__ hist)
+                                                     unsigned long long* __restrict__ hist,
+                                                     uint32_t* __restrict__ gbits)
 {
     __shared__ unsigned h[kStatBins];
     for (int i = threadIdx.x; i < kStatBins; i += blockDim.x) h[i] = 0;
@@ -1150,11 +1178,13 @@ __global__ void __launch_bounds__(256) k_stat_sweep1(StatGrid g, float thr, doub
                 const float c = q[u].c;
                 unsigned bin = 0xFFFFFFFFu;
                 if (x < g.nx) {
-                    if (c > thr) {
+                    const bool occupied = c > thr;
+                    if (occupied) {
                         acc[0].add(gm);
                         ++occ;
                         bin = stat_bin(gm);
                     }
+                    gbits[r.base + x] = occupied ? __float_as_uint(gm) : kStatEmpty;
                     if (x + 1 < g.nx) { const float d = q[u].xp - c; acc[1].add(d * d); }
                     if (r.yhi) { const float d = q[u].yp - c; acc[2].add(d * d); }
                     if (r.zhi) { const float d = q[u].zp - c; acc[3].add(d * d); }
@@ -1167,58 +1197,215 @@ __global__ void __launch_bounds__(256) k_stat_sweep1(StatGrid g, float thr, doub
             }
         }
     }
+    __shared__ double red[8][7];
     for (int o = 16; o > 0; o >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, o);
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const double t = warp_sum_d(acc[k].value());
-        if (lane == 0) atomicAdd(sums + k, t);
+        if (lane == 0) red[threadIdx.x >> 5][k] = t;
     }
     if (lane == 0) atomicAdd(cnt, occ);
-    __syncthreads();
+    block_add<7>(red, sums);
     for (int i = threadIdx.x; i < kStatBins; i += blockDim.x)
         if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 
-__global__ void __launch_bounds__(256) k_stat_sweep2(StatGrid g, float thr, unsigned bstar, double* __restrict__ sums,
-                                                     unsigned long long* __restrict__ cnt, uint32_t* __restrict__ cand,
-                                                     unsigned long long cap)
+// Sweep 1 for rows whose length is a multiple of 4 on a 16-byte aligned
+// field: each lane holds 4 consecutive voxels of a 128-voxel chunk, so one
+// 16-byte load brings a neighbour of all four.  A neighbour past a border is
+// read at offset 0 (the voxel itself): its one-sided difference then takes
+// the voxel's own value exactly as voxel_grad does, and its pair difference
+// is exactly 0, so neither the loads nor the six pair sums need a per-voxel
+// condition.  The lane sums its four terms of each quantity (fused
+// multiply-adds) before one compensated add.
+__device__ __forceinline__ float f4c(const float4& v, int j)
 {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+constexpr int kSweep1vThreads = 256;
+
+__global__ void __launch_bounds__(kSweep1vThreads, 4) k_stat_sweep1v(StatGrid g, float thr, double* __restrict__ sums,
+                                                         unsigned long long* __restrict__ cnt,
+                                                         unsigned long long* __restrict__ hist,
+                                                         uint32_t* __restrict__ gbits)
+{
+    __shared__ unsigned h[kStatBins];
+    for (int i = threadIdx.x; i < kStatBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const long long w0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    KSum above;
+    const float4* V4 = reinterpret_cast<const float4*>(g.V);
+    uint4* G4 = reinterpret_cast<uint4*>(gbits);
+    const long long sy = g.nx >> 2, sz = (long long)(g.nx >> 2) * g.ny;   // float4 strides
+    KSum acc[7];
+    unsigned long long occ = 0;
     for (long long row = w0; row < g.nrows; row += nw) {
         Row r;
         if (!decode_row(g, row, r)) continue;
-        for (int x0 = 0; x0 < g.nx; x0 += 32 * kBatch2) {
-            Vals<false> q[kBatch2];
+        // row-uniform offsets (0 past a border) and difference factors, the
+        // factors of voxel_grad: 1/2 between two neighbours, 1 at a border
+        const long long oym = r.ylo ? sy : 0, oyp = r.yhi ? sy : 0;
+        const long long ozm = r.zlo ? sz : 0, ozp = r.zhi ? sz : 0;
+        const long long oy16 = r.y16 ? 16 * sy : 0, oz16 = r.z16 ? 16 * sz : 0;
+        const float fy = g.ny < 2 ? 0.0f : ((r.ylo && r.yhi) ? 0.5f : 1.0f);
+        const float fz = g.nz < 2 ? 0.0f : ((r.zlo && r.zhi) ? 0.5f : 1.0f);
+        for (int x0 = 0; x0 < g.nx; x0 += 128) {
+            const int x = x0 + 4 * lane;                  // the lane's first voxel
+            const bool ok = x < g.nx;
+            const long long v = (r.base + min(x, g.nx - 4)) >> 2;   // inside the row for every lane
+            const float4 c = V4[v];
+            const float um = __shfl_up_sync(0xffffffffu, c.w, 1);
+            const float dn = __shfl_down_sync(0xffffffffu, c.x, 1);
+            if (!ok) continue;                            // only in the last chunk of a row
+            const float xm0 = x == 0 ? c.x : (lane == 0 ? g.V[r.base + x - 1] : um);
+            const float xp3 = x + 4 >= g.nx ? c.w : (lane == 31 ? g.V[r.base + x + 4] : dn);
+            const float4 ym = V4[v - oym], yp = V4[v + oyp];
+            const float4 zm = V4[v - ozm], zp = V4[v + ozp];
+            const float4 x16 = V4[v + (x + 16 < g.nx ? 4 : 0)];
+            const float4 y16 = V4[v + oy16], z16 = V4[v + oz16];
+            float pg = 0.0f, p[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            unsigned nocc = 0;
+            uint32_t gb[4];
 #pragma unroll
-            for (int u = 0; u < kBatch2; ++u) load_chunk<false>(g, r, x0 + 32 * u + lane, lane, q[u]);
-#pragma unroll
-            for (int u = 0; u < kBatch2; ++u) {
-                const int x = x0 + 32 * u + lane;
-                const float gm = chunk_grad<false>(g, r, x, lane, q[u]);
-                bool take = false;
-                if (x < g.nx && q[u].c > thr) {
-                    const unsigned b = stat_bin(gm);
-                    if (b > bstar) above.add(gm);
-                    take = b == bstar;
-                }
-                const unsigned ball = __ballot_sync(0xffffffffu, take);
-                if (ball) {
-                    unsigned long long off = 0;
-                    if (lane == 0) off = atomicAdd(cnt + 1, (unsigned long long)__popc(ball));
-                    off = __shfl_sync(0xffffffffu, off, 0);
-                    if (take) {
-                        const unsigned long long i = off + (unsigned long long)__popc(ball & ((1u << lane) - 1u));
-                        if (i < cap) cand[i] = __float_as_uint(gm);
-                    }
-                }
+            for (int j = 0; j < 4; ++j) {
+                const float cj = f4c(c, j);
+                const float xm = j ? f4c(c, j - 1) : xm0;
+                const float xp = j < 3 ? f4c(c, j + 1) : xp3;
+                const float fx = (j == 0 && x == 0) || (j == 3 && x + 4 >= g.nx) ? 1.0f : 0.5f;
+                const float gx = fx * (xp - xm);
+                const float gy = fy * (f4c(yp, j) - f4c(ym, j));
+                const float gz = fz * (f4c(zp, j) - f4c(zm, j));
+                const float sx = gx * gx, s2 = gy * gy, s3 = gz * gz;
+                float sq = sx + s2;
+                sq = sq + s3;
+                const float gm = sqrtf(sq);
+                const bool occupied = cj > thr;
+                pg += occupied ? gm : 0.0f;
+                nocc += occupied;
+                gb[j] = occupied ? __float_as_uint(gm) : kStatEmpty;
+                if (occupied) atomicAdd(&h[stat_bin(gm)], 1u);
+                float d = xp - cj;
+                p[0] = fmaf(d, d, p[0]);
+                d = f4c(yp, j) - cj;
+                p[1] = fmaf(d, d, p[1]);
+                d = f4c(zp, j) - cj;
+                p[2] = fmaf(d, d, p[2]);
+                d = f4c(x16, j) - cj;
+                p[3] = fmaf(d, d, p[3]);
+                d = f4c(y16, j) - cj;
+                p[4] = fmaf(d, d, p[4]);
+                d = f4c(z16, j) - cj;
+                p[5] = fmaf(d, d, p[5]);
             }
+            G4[v] = make_uint4(gb[0], gb[1], gb[2], gb[3]);
+            occ += nocc;
+            acc[0].add(pg);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k + 1].add(p[k]);
         }
     }
+    __shared__ double red[8][7];
+    for (int o = 16; o > 0; o >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, o);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const double t = warp_sum_d(acc[k].value());
+        if (lane == 0) red[threadIdx.x >> 5][k] = t;
+    }
+    if (lane == 0) atomicAdd(cnt, occ);
+    block_add<7>(red, sums);
+    for (int i = threadIdx.x; i < kStatBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// one voxel's gradient bits in sweep 2: mass above bin b*, and whether it is
+// a candidate (a member of b*)
+__device__ __forceinline__ bool stat_take(uint32_t bits, unsigned bstar, KSum& above)
+{
+    if (bits == kStatEmpty) return false;
+    const unsigned b = min(bits >> kStatShift, (unsigned)(kStatBins - 1));
+    if (b > bstar) above.add(__uint_as_float(bits));
+    return b == bstar;
+}
+
+constexpr int kSweep2Vec = 4;   // 16-byte loads per lane and block pass
+constexpr int kSweep2Pass = 256 * 4 * kSweep2Vec;   // voxels per block pass
+
+// Sweep 2 streams the gradient bits.  The boundary bin can hold a few per
+// cent of the voxels, so candidates are gathered per block pass in shared
+// memory (a warp scan and one shared atomic per warp) and the block reserves
+// its range of the global list with one atomic per pass.
+__global__ void __launch_bounds__(256) k_stat_sweep2(const uint32_t* __restrict__ gbits, long long M, unsigned bstar,
+                                                     double* __restrict__ sums, unsigned long long* __restrict__ cnt,
+                                                     uint32_t* __restrict__ cand, unsigned long long cap)
+{
+    __shared__ uint32_t buf[kSweep2Pass];
+    __shared__ unsigned nbuf;
+    __shared__ unsigned long long gbase;
+    const int lane = threadIdx.x & 31;
+    const long long n4 = M >> 2;
+    const uint4* g4 = reinterpret_cast<const uint4*>(gbits);
+    constexpr long long span = 256LL * kSweep2Vec;
+    KSum above;
+    for (long long base = (long long)blockIdx.x * span; base < n4; base += (long long)gridDim.x * span) {
+        uint4 v[kSweep2Vec];
+#pragma unroll
+        for (int u = 0; u < kSweep2Vec; ++u) {
+            const long long i = base + 256LL * u + threadIdx.x;
+            v[u] = i < n4 ? __ldcs(g4 + i) : make_uint4(kStatEmpty, kStatEmpty, kStatEmpty, kStatEmpty);
+        }
+        __syncthreads();                                  // the previous pass's copy-out is done
+        if (threadIdx.x == 0) nbuf = 0;
+        unsigned mine = 0;
+#pragma unroll
+        for (int u = 0; u < kSweep2Vec; ++u) {
+            mine += stat_take(v[u].x, bstar, above);
+            mine += stat_take(v[u].y, bstar, above);
+            mine += stat_take(v[u].z, bstar, above);
+            mine += stat_take(v[u].w, bstar, above);
+        }
+        unsigned incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        __syncthreads();                                  // nbuf is reset
+        unsigned woff = 0;
+        if (lane == 31 && incl) woff = atomicAdd(&nbuf, incl);
+        unsigned off = __shfl_sync(0xffffffffu, woff, 31) + incl - mine;
+        if (mine) {
+#pragma unroll
+            for (int u = 0; u < kSweep2Vec; ++u) {
+                const uint32_t e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (e[k] != kStatEmpty && min(e[k] >> kStatShift, (unsigned)(kStatBins - 1)) == bstar)
+                        buf[off++] = e[k];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) gbase = nbuf ? atomicAdd(cnt + 1, (unsigned long long)nbuf) : 0ULL;
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < nbuf; i += blockDim.x)
+            if (gbase + i < cap) cand[gbase + i] = buf[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {          // the M mod 4 voxels past the last vector
+        const long long i = (n4 << 2) + lane;
+        const uint32_t bits = i < M ? gbits[i] : kStatEmpty;
+        const bool take = stat_take(bits, bstar, above);
+        const unsigned ball = __ballot_sync(0xffffffffu, take);
+        if (ball) {
+            unsigned long long o = 0;
+            if (lane == 0) o = atomicAdd(cnt + 1, (unsigned long long)__popc(ball));
+            o = __shfl_sync(0xffffffffu, o, 0) + (unsigned long long)__popc(ball & ((1u << lane) - 1u));
+            if (take && o < cap) cand[o] = bits;
+        }
+    }
+    __shared__ double red[8][1];
     const double t = warp_sum_d(above.value());
-    if (lane == 0) atomicAdd(sums + 7, t);
+    if (lane == 0) red[threadIdx.x >> 5][0] = t;
+    block_add<1>(red, sums + 7);
 }
 
 // candidate mass strictly above the select threshold, and its count
@@ -1253,12 +1440,25 @@ StatGrid stat_grid(const float* V, gve_dims d)
 
 // persistent grid: the resident blocks, no more than the segments need
 template <typename Kern>
-int stat_blocks(Kern k, long long nrows)
+int stat_blocks(Kern k, long long nrows, int threads = 256)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
     long long b = 148LL * per_sm;
-    const long long need = (nrows + 7) / 8;
+    const int warps = threads / 32;
+    const long long need = (nrows + warps - 1) / warps;
+    if (b > need) b = need;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// sweep 2: the resident blocks, no more than the vectors need
+int sweep2_blocks(long long M)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stat_sweep2, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    long long b = 148LL * per_sm;
+    const long long need = ((M >> 2) + 256LL * kSweep2Vec - 1) / (256LL * kSweep2Vec);
     if (b > need) b = need;
     return (int)(b < 1 ? 1 : b);
 }
@@ -1306,7 +1506,13 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
     if (e != cudaSuccess) return cuda_fail(c, e, "memset structure scratch");
     const StatGrid sg = stat_grid(V, d);
     ev.mark(0, s);
-    k_stat_sweep1<<<stat_blocks(k_stat_sweep1, sg.nrows), 256, 0, s>>>(sg, thr, sums, cnt, hist);
+    if ((st = ensure(c, c->a_g, sizeof(uint32_t) * M, s)) != GVE_OK) return st;
+    uint32_t* gbits = (uint32_t*)c->a_g.p;
+    if (d.nx % 4 == 0 && ((uintptr_t)V & 15) == 0)
+        k_stat_sweep1v<<<stat_blocks(k_stat_sweep1v, sg.nrows, kSweep1vThreads), kSweep1vThreads, 0, s>>>(
+            sg, thr, sums, cnt, hist, gbits);
+    else
+        k_stat_sweep1<<<stat_blocks(k_stat_sweep1, sg.nrows), 256, 0, s>>>(sg, thr, sums, cnt, hist, gbits);
     ev.mark(1, s);
     c->launches += 1;
     std::vector<unsigned long long> hh(kStatCounts + kStatBins);
@@ -1332,8 +1538,7 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
         const unsigned long long r = (unsigned long long)K - above_n;
         if ((st = ensure(c, c->a_keys, sizeof(uint32_t) * nc, s)) != GVE_OK) return st;
         uint32_t* cand = (uint32_t*)c->a_keys.p;
-        k_stat_sweep2<<<stat_blocks(k_stat_sweep2, sg.nrows), 256, 0, s>>>(sg, thr, (unsigned)bstar, sums, cnt, cand,
-                                                                          nc);
+        k_stat_sweep2<<<sweep2_blocks(M), 256, 0, s>>>(gbits, M, (unsigned)bstar, sums, cnt, cand, nc);
         uint32_t tbits = 0;
         if ((st = radix_select<uint32_t>(c, cand, (long long)nc, nc - r, &tbits, s)) != GVE_OK) return st;
         k_stat_tail<<<grid_for((long long)nc), 256, 0, s>>>(cand, (long long)nc, tbits, sums, cnt);

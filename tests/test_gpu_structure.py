@@ -2,10 +2,14 @@
 
 The occupancy is an integer count and must match exactly.  The other values
 are sums of float32 terms that the oracle forms in FP64.  The device rounds
-each difference and square to float32 (relative error <= 3u, u = 2^-24) and
-adds them in compensated float32 partials (<= 2u of the partial sum), folded
-in FP64.  The terms are non-negative, so each sum is within 5u ~ 3e-7 of the
-oracle's; the test allows 1e-6 relative.
+each difference to float32 (its square then within 2u, u = 2^-24), sums a
+few terms per lane in float32 (fused multiply-adds: <= 3u for the four of
+the 16-byte layout), and adds those partials in compensated float32 (<= 2u),
+folded in FP64.  The terms are non-negative, so each sum is within 7u ~ 4e-7
+of the oracle's; the test allows 1e-6 relative.  Rows whose length is a
+multiple of 4 take the 16-byte layout (four voxels per lane), the others
+and unaligned fields the one-voxel-per-lane layout; both give the same
+gradient bits, so the same top-10 % decision.
 """
 import numpy as np
 import pytest
@@ -23,6 +27,9 @@ FIELDS = {
     "thin": lambda: inputs.grf((64, 20, 1), seed=1),
     "constant": lambda: np.full((17, 18, 19), 0.3, np.float32),
     "grf256": lambda: inputs.grf(256, seed=3),
+    "x12": lambda: inputs.grf((9, 7, 12), seed=4),          # rows of 4-voxel lanes, no x + 16 pairs
+    "x20": lambda: inputs.grf((23, 17, 20), seed=6),        # one x + 16 pair per lane group
+    "x132": lambda: inputs.grf((6, 18, 132), seed=7),       # a full 128-voxel chunk and a 4-voxel tail
 }
 
 
@@ -34,6 +41,24 @@ def test_structure_stats_match_oracle(name):
     assert got["occupancy"] == ref["occupancy"]
     for k in ("grad_top10", "S1", "S16", "S1_over_S16"):
         np.testing.assert_allclose(got[k], ref[k], rtol=1e-6, atol=1e-300, err_msg=k)
+
+
+def test_structure_unaligned_field_matches_aligned():
+    """A field starting 4 bytes past a 16-byte boundary takes the
+    one-voxel-per-lane layout: the same occupancy and top-10 % share (the
+    same gradient bits), and both agree with the oracle."""
+    V = np.ascontiguousarray(inputs.grf((21, 30, 64), seed=12), np.float32)
+    ref = O.structure_stats(V)
+    buf = torch.zeros(V.size + 4, device="cuda")
+    view = buf[1:1 + V.size].view(V.shape)
+    view.copy_(torch.from_numpy(V).cuda())
+    assert view.data_ptr() % 16 == 4
+    a = gve.gve_structure_stats(torch.from_numpy(V).cuda())
+    b = gve.gve_structure_stats(view)
+    assert a["occupancy"] == b["occupancy"] == ref["occupancy"]
+    for k in ("grad_top10", "S1", "S16", "S1_over_S16"):
+        np.testing.assert_allclose(a[k], ref[k], rtol=1e-6, atol=1e-300, err_msg=k)
+        np.testing.assert_allclose(b[k], ref[k], rtol=1e-6, atol=1e-300, err_msg=k)
 
 
 def test_structure_stage_times_and_invalid_arguments():

@@ -1225,7 +1225,7 @@ __device__ __forceinline__ float f4c(const float4& v, int j)
 
 constexpr int kSweep1vThreads = 256;
 
-__global__ void __launch_bounds__(kSweep1vThreads, 4) k_stat_sweep1v(StatGrid g, float thr, double* __restrict__ sums,
+__global__ void __launch_bounds__(kSweep1vThreads, 3) k_stat_sweep1v(StatGrid g, float thr, double* __restrict__ sums,
                                                          unsigned long long* __restrict__ cnt,
                                                          unsigned long long* __restrict__ hist,
                                                          uint32_t* __restrict__ gbits)
@@ -1238,33 +1238,40 @@ __global__ void __launch_bounds__(kSweep1vThreads, 4) k_stat_sweep1v(StatGrid g,
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     const float4* V4 = reinterpret_cast<const float4*>(g.V);
     uint4* G4 = reinterpret_cast<uint4*>(gbits);
-    const long long sy = g.nx >> 2, sz = (long long)(g.nx >> 2) * g.ny;   // float4 strides
+    const int sy = g.nx >> 2, sz = (g.nx >> 2) * g.ny;   // float4 strides (the host checks 16 sz < 2^31)
     KSum acc[7];
     unsigned long long occ = 0;
-    for (long long row = w0; row < g.nrows; row += nw) {
-        Row r;
-        if (!decode_row(g, row, r)) continue;
-        // row-uniform offsets (0 past a border) and difference factors, the
-        // factors of voxel_grad: 1/2 between two neighbours, 1 at a border
-        const long long oym = r.ylo ? sy : 0, oyp = r.yhi ? sy : 0;
-        const long long ozm = r.zlo ? sz : 0, ozp = r.zhi ? sz : 0;
-        const long long oy16 = r.y16 ? 16 * sy : 0, oz16 = r.z16 ? 16 * sz : 0;
-        const float fy = g.ny < 2 ? 0.0f : ((r.ylo && r.yhi) ? 0.5f : 1.0f);
-        const float fz = g.nz < 2 ? 0.0f : ((r.zlo && r.zhi) ? 0.5f : 1.0f);
+    const unsigned nrows = (unsigned)g.nrows, rows_tile = (unsigned)g.rows_tile, ty = (unsigned)g.ty;
+    for (unsigned row = (unsigned)w0; row < nrows; row += (unsigned)nw) {
+        // the row's tile, slab and y (32-bit: the host checks the range)
+        const unsigned t = row / rows_tile, rr = row - t * rows_tile;
+        const int z = (int)(rr / ty), y = (int)(t * ty + (rr - (unsigned)z * ty));
+        if (y >= g.ny) continue;
+        const bool ylo = y > 0, yhi = y + 1 < g.ny, zlo = z > 0, zhi = z + 1 < g.nz;
+        const long long base = ((long long)z * g.ny + y) * g.nx;
+        const float4* R4 = V4 + (base >> 2);
+        // row-uniform float4 offsets (0 past a border) and difference
+        // factors, those of voxel_grad: 1/2 between two neighbours, 1 at a border
+        const int oym = ylo ? sy : 0, oyp = yhi ? sy : 0;
+        const int ozm = zlo ? sz : 0, ozp = zhi ? sz : 0;
+        const int oy16 = y + 16 < g.ny ? 16 * sy : 0, oz16 = z + 16 < g.nz ? 16 * sz : 0;
+        const float fy = g.ny < 2 ? 0.0f : ((ylo && yhi) ? 0.5f : 1.0f);
+        const float fz = g.nz < 2 ? 0.0f : ((zlo && zhi) ? 0.5f : 1.0f);
         for (int x0 = 0; x0 < g.nx; x0 += 128) {
             const int x = x0 + 4 * lane;                  // the lane's first voxel
             const bool ok = x < g.nx;
-            const long long v = (r.base + min(x, g.nx - 4)) >> 2;   // inside the row for every lane
-            const float4 c = V4[v];
+            const int xi = min(x, g.nx - 4) >> 2;         // inside the row for every lane
+            const float4 c = R4[xi];
             const float um = __shfl_up_sync(0xffffffffu, c.w, 1);
             const float dn = __shfl_down_sync(0xffffffffu, c.x, 1);
             if (!ok) continue;                            // only in the last chunk of a row
-            const float xm0 = x == 0 ? c.x : (lane == 0 ? g.V[r.base + x - 1] : um);
-            const float xp3 = x + 4 >= g.nx ? c.w : (lane == 31 ? g.V[r.base + x + 4] : dn);
-            const float4 ym = V4[v - oym], yp = V4[v + oyp];
-            const float4 zm = V4[v - ozm], zp = V4[v + ozp];
-            const float4 x16 = V4[v + (x + 16 < g.nx ? 4 : 0)];
-            const float4 y16 = V4[v + oy16], z16 = V4[v + oz16];
+            const float* R = reinterpret_cast<const float*>(R4);
+            const float xm0 = x == 0 ? c.x : (lane == 0 ? R[x - 1] : um);
+            const float xp3 = x + 4 >= g.nx ? c.w : (lane == 31 ? R[x + 4] : dn);
+            const float4 ym = R4[xi - oym], yp = R4[xi + oyp];
+            const float4 zm = R4[xi - ozm], zp = R4[xi + ozp];
+            const float4 x16 = R4[xi + (x + 16 < g.nx ? 4 : 0)];
+            const float4 y16 = R4[xi + oy16], z16 = R4[xi + oz16];
             float pg = 0.0f, p[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             unsigned nocc = 0;
             uint32_t gb[4];
@@ -1299,7 +1306,7 @@ __global__ void __launch_bounds__(kSweep1vThreads, 4) k_stat_sweep1v(StatGrid g,
                 d = f4c(z16, j) - cj;
                 p[5] = fmaf(d, d, p[5]);
             }
-            G4[v] = make_uint4(gb[0], gb[1], gb[2], gb[3]);
+            G4[(base >> 2) + xi] = make_uint4(gb[0], gb[1], gb[2], gb[3]);
             occ += nocc;
             acc[0].add(pg);
 #pragma unroll
@@ -1319,13 +1326,15 @@ __global__ void __launch_bounds__(kSweep1vThreads, 4) k_stat_sweep1v(StatGrid g,
         if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 
-// one voxel's gradient bits in sweep 2: mass above bin b*, and whether it is
-// a candidate (a member of b*)
-__device__ __forceinline__ bool stat_take(uint32_t bits, unsigned bstar, KSum& above)
+// one voxel's gradient bits in sweep 2: its mass if above bin b*, and
+// whether it is a candidate (a member of b*).  An occupied voxel's gradient
+// is a non-negative float, so its bits shifted are its bin (below
+// kStatBins, where stat_bin's clamp does not act); kStatEmpty shifts to
+// 8191, in no bin.
+__device__ __forceinline__ bool stat_take(uint32_t bits, unsigned bstar, float& above)
 {
-    if (bits == kStatEmpty) return false;
-    const unsigned b = min(bits >> kStatShift, (unsigned)(kStatBins - 1));
-    if (b > bstar) above.add(__uint_as_float(bits));
+    const unsigned b = bits >> kStatShift;
+    above += (b > bstar && b < (unsigned)kStatBins) ? __uint_as_float(bits) : 0.0f;
     return b == bstar;
 }
 
@@ -1359,11 +1368,13 @@ __global__ void __launch_bounds__(256) k_stat_sweep2(const uint32_t* __restrict_
         if (threadIdx.x == 0) nbuf = 0;
         unsigned mine = 0;
 #pragma unroll
-        for (int u = 0; u < kSweep2Vec; ++u) {
-            mine += stat_take(v[u].x, bstar, above);
-            mine += stat_take(v[u].y, bstar, above);
-            mine += stat_take(v[u].z, bstar, above);
-            mine += stat_take(v[u].w, bstar, above);
+        for (int u = 0; u < kSweep2Vec; ++u) {      // four terms in float32, then one compensated add
+            float pa = 0.0f;
+            mine += stat_take(v[u].x, bstar, pa);
+            mine += stat_take(v[u].y, bstar, pa);
+            mine += stat_take(v[u].z, bstar, pa);
+            mine += stat_take(v[u].w, bstar, pa);
+            above.add(pa);
         }
         unsigned incl = mine;
         for (int o = 1; o < 32; o <<= 1) {
@@ -1380,8 +1391,7 @@ __global__ void __launch_bounds__(256) k_stat_sweep2(const uint32_t* __restrict_
                 const uint32_t e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (e[k] != kStatEmpty && min(e[k] >> kStatShift, (unsigned)(kStatBins - 1)) == bstar)
-                        buf[off++] = e[k];
+                    if ((e[k] >> kStatShift) == bstar) buf[off++] = e[k];
             }
         }
         __syncthreads();
@@ -1393,7 +1403,9 @@ __global__ void __launch_bounds__(256) k_stat_sweep2(const uint32_t* __restrict_
     if (blockIdx.x == 0 && threadIdx.x < 32) {          // the M mod 4 voxels past the last vector
         const long long i = (n4 << 2) + lane;
         const uint32_t bits = i < M ? gbits[i] : kStatEmpty;
-        const bool take = stat_take(bits, bstar, above);
+        float pa = 0.0f;
+        const bool take = stat_take(bits, bstar, pa);
+        above.add(pa);
         const unsigned ball = __ballot_sync(0xffffffffu, take);
         if (ball) {
             unsigned long long o = 0;
@@ -1508,7 +1520,9 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
     ev.mark(0, s);
     if ((st = ensure(c, c->a_g, sizeof(uint32_t) * M, s)) != GVE_OK) return st;
     uint32_t* gbits = (uint32_t*)c->a_g.p;
-    if (d.nx % 4 == 0 && ((uintptr_t)V & 15) == 0)
+    const bool vec4 = d.nx % 4 == 0 && ((uintptr_t)V & 15) == 0 && sg.nrows < (1LL << 31) &&
+                      16LL * (d.nx / 4) * d.ny < (1LL << 31);
+    if (vec4)
         k_stat_sweep1v<<<stat_blocks(k_stat_sweep1v, sg.nrows, kSweep1vThreads), kSweep1vThreads, 0, s>>>(
             sg, thr, sums, cnt, hist, gbits);
     else

@@ -458,17 +458,23 @@ int grid_for(long long M)
     return (int)(b < 1 ? 1 : b);
 }
 
-// k-th smallest key (0-based rank) by radix select; host-driven passes
+// k-th smallest key (0-based rank) by radix select; host-driven passes of
+// 8-bit digits from the top.  When every key shares its top `known` bits
+// (those of `prefix0`), the passes start below them; a last pass that
+// would reach below bit 0 is taken at bit 0 (its top digit bits are fixed).
 template <typename K>
-gve_status radix_select(gve_ctx* c, const K* keys, long long M, unsigned long long rank, K* out, cudaStream_t s)
+gve_status radix_select(gve_ctx* c, const K* keys, long long M, unsigned long long rank, K* out, cudaStream_t s,
+                        K prefix0 = 0, int known = 0)
 {
     const int bits = (int)sizeof(K) * 8;
     gve_status st = ensure(c, c->a_tmp, 256 * sizeof(unsigned long long), s);
     if (st != GVE_OK) return st;
     unsigned long long* dh = (unsigned long long*)c->a_tmp.p;
     std::vector<unsigned long long> h(256);
-    K prefix = 0, pmask = 0;
-    for (int shift = bits - 8; shift >= 0; shift -= 8) {
+    K pmask = known > 0 ? (K)(~(K)0 << (bits - known)) : (K)0;
+    K prefix = prefix0 & pmask;
+    const int first = bits - known - 8 > 0 ? bits - known - 8 : 0;
+    for (int shift = first;; shift = shift > 8 ? shift - 8 : 0) {
         cudaError_t e = cudaMemsetAsync(dh, 0, 256 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return cuda_fail(c, e, "memset select hist");
         k_sel_hist<K><<<grid_for(M), 256, 0, s>>>(keys, M, prefix, pmask, shift, dh);
@@ -485,6 +491,7 @@ gve_status radix_select(gve_ctx* c, const K* keys, long long M, unsigned long lo
         rank -= acc;
         prefix |= (K)d << shift;
         pmask |= (K)255 << shift;
+        if (shift == 0) break;
     }
     *out = prefix;
     return GVE_OK;
@@ -1338,7 +1345,7 @@ __device__ __forceinline__ bool stat_take(uint32_t bits, unsigned bstar, float& 
     return b == bstar;
 }
 
-constexpr int kSweep2Vec = 4;   // 16-byte loads per lane and block pass
+constexpr int kSweep2Vec = 8;   // 16-byte loads per lane and block pass
 constexpr int kSweep2Pass = 256 * 4 * kSweep2Vec;   // voxels per block pass
 
 // Sweep 2 streams the gradient bits.  The boundary bin can hold a few per
@@ -1554,7 +1561,10 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
         uint32_t* cand = (uint32_t*)c->a_keys.p;
         k_stat_sweep2<<<sweep2_blocks(M), 256, 0, s>>>(gbits, M, (unsigned)bstar, sums, cnt, cand, nc);
         uint32_t tbits = 0;
-        if ((st = radix_select<uint32_t>(c, cand, (long long)nc, nc - r, &tbits, s)) != GVE_OK) return st;
+        // every candidate's bits carry b* above bit kStatShift
+        if ((st = radix_select<uint32_t>(c, cand, (long long)nc, nc - r, &tbits, s, (uint32_t)bstar << kStatShift,
+                                         32 - kStatShift)) != GVE_OK)
+            return st;
         k_stat_tail<<<grid_for((long long)nc), 256, 0, s>>>(cand, (long long)nc, tbits, sums, cnt);
         c->launches += 6;
         unsigned long long hc[3];

@@ -1428,20 +1428,34 @@ __global__ void __launch_bounds__(256) k_stat_sweep2(const uint32_t* __restrict_
 }
 
 // candidate mass strictly above the select threshold, and its count
+// (compensated float32 per thread, one FP64 atomic per block)
 __global__ void __launch_bounds__(256) k_stat_tail(const uint32_t* __restrict__ cand, long long n, uint32_t tbits,
                                                    double* __restrict__ sums, unsigned long long* __restrict__ cnt)
 {
-    double s = 0.0;
-    unsigned long long nt = 0;
+    KSum s;
+    unsigned nt = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const uint32_t b = cand[i];
-        if (b > tbits) { s += (double)__uint_as_float(b); ++nt; }
+        if (b > tbits) {
+            s.add(__uint_as_float(b));
+            ++nt;
+        }
     }
-    s = warp_sum_d(s);
-    for (int o = 16; o > 0; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(sums + 8, s);
-        atomicAdd(cnt + 2, nt);
+    __shared__ double red[8][1];
+    __shared__ unsigned long long rc[8];
+    const int lane = threadIdx.x & 31;
+    const double t = warp_sum_d(s.value());
+    unsigned long long c = nt;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+        red[threadIdx.x >> 5][0] = t;
+        rc[threadIdx.x >> 5] = c;
+    }
+    block_add<1>(red, sums + 8);
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += rc[w];
+        atomicAdd(cnt + 2, tot);
     }
 }
 
@@ -1566,7 +1580,7 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
                                          32 - kStatShift)) != GVE_OK)
             return st;
         k_stat_tail<<<grid_for((long long)nc), 256, 0, s>>>(cand, (long long)nc, tbits, sums, cnt);
-        c->launches += 6;
+        c->launches += 5;                   // sweep 2, three select passes, the tail
         unsigned long long hc[3];
         e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);

@@ -195,20 +195,36 @@ def cpu_sample(w, args, seed):
     return dt, frac, desc
 
 
-def brick_traffic(voxels):
-    """DRAM bytes per launch of the brick evaluator from the committed ncu
-    capture, scaled per voxel; None when the kernel source changed since."""
+def kernel_source_text(path, begin=None):
+    """The bytes a traffic record is tied to: the whole source file, or the
+    kernel that starts at `begin` up to the first closing brace at column 0."""
+    src = open(path, "rb").read()
+    if begin is None:
+        return src
+    i = src.index(begin.encode())
+    j = src.index(b"\n}\n", i)
+    return src[i:j + 3]
+
+
+def recorded_traffic(name, voxels):
+    """DRAM bytes per launch of a kernel from its committed ncu capture
+    (profiles/<name>.json), scaled per voxel; None when the kernel's source
+    changed since the capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "brick_traffic.json")
+    path = os.path.join(ROOT, "profiles", name + ".json")
     try:
         rec = json.load(open(path))
-        src = open(os.path.join(ROOT, rec["kernel_source"]), "rb").read()
+        src = kernel_source_text(os.path.join(ROOT, rec["kernel_source"]), rec.get("kernel_begin"))
     except Exception:
         return None
     if hashlib.sha256(src).hexdigest() != rec["kernel_source_sha256"]:
         return None
     per_voxel = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["captured_voxels"]
     return per_voxel * voxels
+
+
+def brick_traffic(voxels):
+    return recorded_traffic("brick_traffic", voxels)
 
 
 def run_reference(args):
@@ -588,11 +604,15 @@ def run_structure(args):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6400.0))
-    # each sweep's algorithmic traffic is one read of the float32 field
-    kern, kms = ("k_stat_sweep1", s1) if s1 >= s2 else ("k_stat_sweep2 + select", s2)
+    # algorithmic traffic: the stencil sweep reads the float32 field once and
+    # the streaming sweep reads the gradient bits once, 4 B per voxel each
+    vec4 = V.shape[2] % 4 == 0 and V.data_ptr() % 16 == 0
+    kern1 = "k_stat_sweep1v" if vec4 else "k_stat_sweep1"
+    kern, kms = (kern1, s1) if s1 >= s2 else ("k_stat_sweep2 + select", s2)
     achieved = 4.0 * M / (kms / 1e3) / 1e9
+    traffic = recorded_traffic("stat_sweep1v_traffic", M) if kern == "k_stat_sweep1v" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": kern, "stage_ms": kms,
+                "traffic": traffic, "kernel": kern, "stage_ms": kms,
                 "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}
     Vh = V.cpu().pin_memory()
     Vd = torch.empty_like(V)

@@ -67,3 +67,29 @@ def test_single_rank_helpers_need_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_rate(1, 10, 500.0) == pytest.approx(20.0)
+
+
+def test_recorded_traffic_follows_its_kernel_source(tmp_path, monkeypatch):
+    """A traffic record is scaled per voxel while the kernel text it was
+    captured from is unchanged (whole file, or the kernel from its first
+    line to its closing brace), and gives None once that text changes."""
+    import hashlib
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("int a;\n__global__ void k_one(int* p)\n{\n    p[0] = 1;\n}\n__global__ void k_two()\n{\n}\n")
+    begin = "__global__ void k_one("
+    text = bench.kernel_source_text(str(src), begin)
+    assert text.startswith(begin.encode()) and text.endswith(b"p[0] = 1;\n}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = dict(kernel_source="k.cu", kernel_begin=begin, kernel_source_sha256=hashlib.sha256(text).hexdigest(),
+               captured_voxels=1000, dram_bytes_read=6000, dram_bytes_write=2000)
+    (tmp_path / "profiles" / "t.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("t", 4000) == pytest.approx(32000.0)
+    src.write_text(src.read_text().replace("k_two()\n{\n}", "k_two()\n{\n    return;\n}"))
+    assert bench.recorded_traffic("t", 4000) == pytest.approx(32000.0)     # another kernel changed
+    src.write_text(src.read_text().replace("p[0] = 1;", "p[0] = 2;"))
+    assert bench.recorded_traffic("t", 4000) is None                        # this kernel changed
+    assert bench.recorded_traffic("missing", 4000) is None

@@ -298,7 +298,7 @@ void gve_ctx_destroy(gve_ctx* c)
                    &c->vals[0], &c->vals[1], &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
                    &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace,
                    &c->s_hi, &c->s_mid, &c->s_cnt, &c->s_off, &c->s_pts, &c->s_cell, &c->s_order, &c->s_nd,
-                   &c->s_gg, &c->s_loss, &c->s_inv, &c->s_ex, &c->s_terms, &c->s_ccnt, &c->r_rec, &c->r_cnt, &c->r_off, &c->r_keys[0], &c->r_keys[1],
+                   &c->s_gg, &c->s_loss, &c->s_inv, &c->s_ex, &c->s_terms, &c->s_ccnt, &c->s_cand, &c->r_rec, &c->r_cnt, &c->r_off, &c->r_keys[0], &c->r_keys[1],
                    &c->r_vals[0], &c->r_vals[1], &c->r_hist, &c->r_scanp, &c->r_rng, &c->r_crec, &c->r_state};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);

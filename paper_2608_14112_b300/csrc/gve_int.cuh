@@ -100,6 +100,7 @@ struct gve_ctx {
     gve::Buf s_hi, s_mid, s_cnt, s_off, s_pts, s_cell, s_order, s_nd, s_gg, s_loss;
     gve::Buf s_inv, s_ex, s_terms;   // sorted position of each point, regulariser gradient, loss terms
     gve::Buf s_ccnt;                 // points per cell (the counting sort's counters)
+    gve::Buf s_cand;                 // Gaussians with candidate points: count, then (index, cell box) pairs
     unsigned long long s_nh = 0, s_nm = 0;
     // ray marcher: keep coefficients, per-Gaussian cell counts and offsets,
     // (cell, Gaussian) pairs and their sort buffers, per-cell ranges, the

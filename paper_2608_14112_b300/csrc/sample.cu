@@ -143,6 +143,7 @@ struct SampleArgs {
     float2* nd;          // per sorted point: (sum w a G, sum w G)
     const float2* gg;    // per sorted point: (dL/dnum, dL/dden)
     float* acc;          // [n][12] accumulators (backward)
+    int4* cand;          // [0].x: count; then per listed Gaussian {i, lo}, {hi, 0}
     float k, T;
 };
 
@@ -205,7 +206,8 @@ __device__ __forceinline__ bool has_candidates(const SampleArgs& a, const int lo
 // The keep coefficients are computed here, in FP64 as in the voxel path's
 // preparation, only for Gaussians whose box holds candidate points (about
 // half of them at 1.4 M Gaussians against 6,144 points), and stored for the
-// gradient pass, which takes the same decision.
+// gradient pass.  Those Gaussians (with a valid record) are listed with
+// their cell box, so that the gradient pass visits only them.
 __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -227,6 +229,15 @@ __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
     a.rec[3 * i + 1] = r1;
     a.rec[3 * i + 2] = r2;
     if (!(r2.z > 0.f)) return;  // invalid record (weight zero)
+    if (a.cand) {               // append to the list, one atomic per group of converged lanes
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+        unsigned slot = 0;
+        if (lane == leader) slot = atomicAdd(reinterpret_cast<unsigned*>(a.cand), (unsigned)__popc(act));
+        slot = __shfl_sync(act, slot, leader) + (unsigned)__popc(act & ((1u << lane) - 1u));
+        a.cand[1 + 2 * (long long)slot] = make_int4((int)i, lo[0], lo[1], lo[2]);
+        a.cand[2 + 2 * (long long)slot] = make_int4(hi[0], hi[1], hi[2], 0);
+    }
     for_candidates(a, lo, hi, [&](uint32_t s) {
         const float4 q = a.spts[s];
         const float t = keep_t(r0, r1, r2, __fsub_rn(q.x, r0.x), __fsub_rn(q.y, r0.y), __fsub_rn(q.z, r0.z));
@@ -237,16 +248,18 @@ __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
     });
 }
 
+// One thread per listed Gaussian (the others' sums stay zero: the caller
+// clears acc); the grid covers all n, threads past the count return.
 __global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)(unsigned)a.cand[0].x) return;
+    const int4 e0 = a.cand[1 + 2 * e], e1 = a.cand[2 + 2 * e];
+    const long long i = e0.x;
+    const int lo[3] = {e0.y, e0.z, e0.w}, hi[3] = {e1.x, e1.y, e1.z};
     float A = 0.f, H = 0.f, S1[3] = {0.f, 0.f, 0.f}, S2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int lo[3], hi[3];
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-    const bool cand = gauss_cells(a, i, lo, hi) && has_candidates(a, lo, hi);
-    if (cand) { r0 = a.rec[3 * i]; r1 = a.rec[3 * i + 1]; r2 = a.rec[3 * i + 2]; }
-    if (cand && r2.z > 0.f) {
+    const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
+    {
         for_candidates(a, lo, hi, [&](uint32_t s) {
             const float4 q = a.spts[s];
             const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
@@ -371,6 +384,7 @@ struct SampleBufs {
     double* loss;
     double* terms;
     float* extra;
+    int4* cand;
 };
 
 // buffers for P points (samples and partners) and n records
@@ -393,6 +407,7 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long P, long long n, SampleB
     SMP_TRY(ensure(c, c->binrec, sizeof(BinRec) * nn, s));
     SMP_TRY(ensure(c, c->acc, sizeof(float) * 12 * nn, s));
     SMP_TRY(ensure(c, c->s_ex, sizeof(float) * 12 * nn, s));
+    SMP_TRY(ensure(c, c->s_cand, sizeof(int4) * (1 + 2 * nn), s));
     b.pts = (float4*)c->s_pts.p;
     b.spts = b.pts + P;
     b.order = (uint32_t*)c->s_order.p;
@@ -404,6 +419,7 @@ gve_status sample_bufs(gve_ctx* c, gve_dims d, long long P, long long n, SampleB
     b.loss = (double*)c->s_loss.p;
     b.terms = (double*)c->s_terms.p;
     b.extra = (float*)c->s_ex.p;
+    b.cand = (int4*)c->s_cand.p;
     return GVE_OK;
 }
 
@@ -441,6 +457,11 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     a.k = o->trunc_k;
     a.T = (float)((double)o->trunc_k * (double)o->trunc_k * kNegHalfLog2e);
     const unsigned grid = (unsigned)((n + 127) / 128);
+    if (backward && n > 0) {
+        a.cand = b.cand;
+        SMP_CUDA(cudaMemsetAsync(b.cand, 0, sizeof(int4), s), "memset candidate count");
+        SMP_CUDA(cudaMemsetAsync(a.acc, 0, sizeof(float) * 12 * n, s), "memset sums");
+    }
     if (n > 0) k_sample_eval<<<grid, 128, 0, s>>>(a);
     k_sample_loss<<<1, 1024, 0, s>>>(b.spts, b.order, b.inv, b.nd, (int)S, pr.smooth, o->rho0, occ, pr.l_rho, pr.l_sm,
                                      b.gg, b.loss, trace, iter, vt_out, b.terms);

@@ -79,41 +79,57 @@ __global__ void __launch_bounds__(256) k_cell_count(const float4* __restrict__ p
     if (i < P) atomicAdd(&ccnt[point_cell(pts[i], nx, ny, nz, cg)], 1u);
 }
 
-__global__ void __launch_bounds__(1024) k_cell_scan(uint32_t* __restrict__ ccnt, long long ncells,
-                                                    uint32_t* __restrict__ cstart)
+// One CTA scans the counts in tiles of 4,096 cells: each thread takes four
+// consecutive cells with one 16-byte load (so a warp's loads and stores are
+// contiguous), then warp and block scans of the thread sums and a running
+// carry between tiles.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan(const uint32_t* __restrict__ ccnt, long long ncells,
+                                                            uint32_t* __restrict__ cstart)
 {
-    __shared__ uint32_t part[1024];
-    const long long per = (ncells + blockDim.x - 1) / blockDim.x;
-    const long long lo = (long long)threadIdx.x * per, hi = lo + per < ncells ? lo + per : ncells;
-    uint32_t sum = 0;
-    for (long long c = lo; c < hi; c += 8) {  // eight loads in flight
-        uint32_t v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = c + k < hi ? ccnt[c + k] : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sum += v[k];
-    }
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan of the partials
-        const uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (long long base = 0; base < ncells; base += 4LL * kScanThreads) {
+        const long long c = base + 4LL * threadIdx.x;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (c + 3 < ncells) {
+            v = *reinterpret_cast<const uint4*>(ccnt + c);
+        } else {
+            if (c < ncells) v.x = ccnt[c];
+            if (c + 1 < ncells) v.y = ccnt[c + 1];
+            if (c + 2 < ncells) v.z = ccnt[c + 2];
+        }
+        const uint32_t s1 = v.x + v.y, s2 = s1 + v.z, s3 = s2 + v.w;
+        uint32_t x = s3;                               // inclusive scan of the thread sums in the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - sum;
-    for (long long c = lo; c < hi; c += 8) {
-        uint32_t v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = c + k < hi ? ccnt[c + k] : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (c + k < hi) {
-                cstart[c + k] = run;
-                run += v[k];
+        if (w == 0) {                                  // inclusive scan of the warp sums
+            uint32_t y = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += t;
             }
+            wsum[lane] = y;
+        }
+        __syncthreads();
+        const uint32_t e = carry + (w ? wsum[w - 1] : 0u) + x - s3;   // cells before this thread's first
+        if (c + 3 < ncells) {
+            *reinterpret_cast<uint4*>(cstart + c) = make_uint4(e, e + v.x, e + s1, e + s2);
+        } else {
+            if (c < ncells) cstart[c] = e;
+            if (c + 1 < ncells) cstart[c + 1] = e + v.x;
+            if (c + 2 < ncells) cstart[c + 2] = e + s1;
+        }
+        carry += wsum[kScanThreads / 32 - 1];
+        __syncthreads();                               // wsum is rewritten by the next tile
     }
-    if (threadIdx.x == blockDim.x - 1) cstart[ncells] = part[threadIdx.x];
+    if (threadIdx.x == 0) cstart[ncells] = carry;
 }
 
 __global__ void __launch_bounds__(256) k_cell_scatter(const float4* __restrict__ pts, int P, int nx, int ny, int nz,
@@ -439,7 +455,7 @@ gve_status sample_pass(gve_ctx* c, const float* prims, long long n, gve_dims d, 
     const long long P = pr.smooth ? 2 * S : S;
     const unsigned pb = (unsigned)((P + 255) / 256);
     k_cell_count<<<pb, 256, 0, s>>>(b.pts, (int)P, d.nx, d.ny, d.nz, b.cg, b.ccnt);
-    k_cell_scan<<<1, 1024, 0, s>>>(b.ccnt, b.ncells, b.cstart);
+    k_cell_scan<<<1, kScanThreads, 0, s>>>(b.ccnt, b.ncells, b.cstart);
     k_cell_scatter<<<pb, 256, 0, s>>>(b.pts, (int)P, d.nx, d.ny, d.nz, b.cg, b.cstart, b.ccnt, b.spts, b.order, b.inv);
     SMP_CUDA(cudaMemsetAsync(b.nd, 0, sizeof(float2) * P, s), "memset sums");
     SampleArgs a{};

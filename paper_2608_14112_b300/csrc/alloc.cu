@@ -997,13 +997,15 @@ void launch_reg(const float* prims, long long n, const float* V, gve_dims d, con
 // function S(l) = mean over the axes longer than l of the mean
 // (V(x + l e) - V(x))^2.
 //
-// Two sweeps of the field and no per-voxel scratch.  Sweep 1 takes the
-// occupancy, the FP64 gradient mass, the structure-function sums and a
-// 4096-bin histogram of the gradient bits (sign 0, 8 exponent and 4
-// mantissa bits: float order).  The host walks the histogram down to the bin
-// b* that holds the K-th largest.  Sweep 2 recomputes the same gradients,
-// sums the mass of the bins above b* and compacts the bits of bin b*; an
-// exact radix select over those candidates and one sum finish the top-K mass.
+// One stencil sweep of the field, then one streaming sweep of 4 bytes per
+// voxel.  Sweep 1 takes the occupancy, the gradient mass, the
+// structure-function sums and a 4096-bin histogram of the gradient bits
+// (sign 0, 8 exponent and 4 mantissa bits: float order), and writes each
+// voxel's gradient bits (all ones where it is not occupied).  The host walks
+// the histogram down to the bin b* that holds the K-th largest.  Sweep 2
+// reads those bits, sums the mass of the bins above b* and compacts the bits
+// of bin b*; an exact radix select over those candidates and one sum finish
+// the top-K mass.
 // ------------------------------------------------------------------------
 namespace {
 

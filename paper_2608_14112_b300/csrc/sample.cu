@@ -734,7 +734,8 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
                 ad.lr = sc->lr; ad.b1 = sc->beta1; ad.b2 = sc->beta2; ad.eps = sc->eps;
                 ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step + 1));
                 ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step + 1));
-                launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, nullptr, s,
+                // the sums are cleared by the next pass's memset, not here
+                launch_chain((float*)c->acc.p, nullptr, prims, n, nullptr, m, v, &ad, nullptr, s,
                              per_g ? b.extra : nullptr);
                 c->launches += 1;
             }

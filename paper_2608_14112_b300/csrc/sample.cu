@@ -219,11 +219,12 @@ __device__ __forceinline__ bool has_candidates(const SampleArgs& a, const int lo
     return false;
 }
 
-// The keep coefficients are computed here, in FP64 as in the voxel path's
-// preparation, only for Gaussians whose box holds candidate points (about
-// half of them at 1.4 M Gaussians against 6,144 points), and stored for the
-// gradient pass.  Those Gaussians (with a valid record) are listed with
-// their cell box, so that the gradient pass visits only them.
+// The keep coefficients are computed here (float32, keep_coefficients, as
+// in the voxel path's preparation), only for Gaussians whose box holds
+// candidate points (about half of them at 1.4 M Gaussians against 6,144
+// points), and stored for the gradient pass.  Those Gaussians (with a valid
+// record) are listed with their cell box, so that the gradient pass visits
+// only them.
 __global__ void __launch_bounds__(128) k_sample_eval(const SampleArgs a)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,28 +276,26 @@ __global__ void __launch_bounds__(128) k_sample_grad(const SampleArgs a)
     const int lo[3] = {e0.y, e0.z, e0.w}, hi[3] = {e1.x, e1.y, e1.z};
     float A = 0.f, H = 0.f, S1[3] = {0.f, 0.f, 0.f}, S2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float4 r0 = a.rec[3 * i], r1 = a.rec[3 * i + 1], r2 = a.rec[3 * i + 2];
-    {
-        for_candidates(a, lo, hi, [&](uint32_t s) {
-            const float4 q = a.spts[s];
-            const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
-            const float t = keep_t(r0, r1, r2, dx, dy, dz);
-            if (!(t > a.T)) return;
-            const float G = ex2_approx(t);
-            const float2 g = a.gg[s];
-            const float h = G * fmaf(r2.w, g.x, g.y);
-            A = fmaf(G, g.x, A);
-            H += h;
-            S1[0] = fmaf(h, dx, S1[0]);
-            S1[1] = fmaf(h, dy, S1[1]);
-            S1[2] = fmaf(h, dz, S1[2]);
-            S2[0] = fmaf(h * dx, dx, S2[0]);
-            S2[1] = fmaf(h * dy, dy, S2[1]);
-            S2[2] = fmaf(h * dz, dz, S2[2]);
-            S2[3] = fmaf(h * dx, dy, S2[3]);
-            S2[4] = fmaf(h * dx, dz, S2[4]);
-            S2[5] = fmaf(h * dy, dz, S2[5]);
-        });
-    }
+    for_candidates(a, lo, hi, [&](uint32_t s) {
+        const float4 q = a.spts[s];
+        const float dx = __fsub_rn(q.x, r0.x), dy = __fsub_rn(q.y, r0.y), dz = __fsub_rn(q.z, r0.z);
+        const float t = keep_t(r0, r1, r2, dx, dy, dz);
+        if (!(t > a.T)) return;
+        const float G = ex2_approx(t);
+        const float2 g = a.gg[s];
+        const float h = G * fmaf(r2.w, g.x, g.y);
+        A = fmaf(G, g.x, A);
+        H += h;
+        S1[0] = fmaf(h, dx, S1[0]);
+        S1[1] = fmaf(h, dy, S1[1]);
+        S1[2] = fmaf(h, dz, S1[2]);
+        S2[0] = fmaf(h * dx, dx, S2[0]);
+        S2[1] = fmaf(h * dy, dy, S2[1]);
+        S2[2] = fmaf(h * dz, dz, S2[2]);
+        S2[3] = fmaf(h * dx, dy, S2[3]);
+        S2[4] = fmaf(h * dx, dz, S2[4]);
+        S2[5] = fmaf(h * dy, dz, S2[5]);
+    });
     float4* o = reinterpret_cast<float4*>(a.acc) + 3 * i;
     o[0] = make_float4(A, H, S1[0], S1[1]);
     o[1] = make_float4(S1[2], S2[0], S2[1], S2[2]);

@@ -1201,8 +1201,7 @@ __global__ void __launch_bounds__(256) k_stat_sweep1(StatGrid g, float thr, doub
                     if (r.y16) { const float d = q[u].y16 - c; acc[5].add(d * d); }
                     if (r.z16) { const float d = q[u].z16 - c; acc[6].add(d * d); }
                 }
-                const unsigned peers = __match_any_sync(0xffffffffu, bin);
-                if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+                if (bin != 0xFFFFFFFFu) atomicAdd(&h[bin], 1u);   // plain shared atomics: a warp match costs more
             }
         }
     }

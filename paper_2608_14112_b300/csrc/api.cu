@@ -481,6 +481,9 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
             a.field = field;
             a.mask_thresh = sc->mask_thresh;
             a.acc = (float*)c->acc.p;
+            // the sums start from zero each iteration (a memset is cheaper
+            // than clearing them in the chain-rule kernel after reading)
+            GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * nn, k.s), "memset acc");
             launch_brick(kModeLoss, a, k.s);
             if (timed) GVE_CUDA(cudaEventRecord(c->sev[2][t - it], k.s), "event");
             launch_sse_reduce(a.part, k.g.nbricks, dstate(c), tr, t, inv_m, k.s);
@@ -489,7 +492,7 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
             int step = sc->step0 + t + 1;
             ad.bc1 = (float)(1.0 - std::pow((double)sc->beta1, step));
             ad.bc2 = (float)(1.0 - std::pow((double)sc->beta2, step));
-            launch_chain((float*)c->acc.p, (float*)c->acc.p, prims, n, nullptr, m, v, &ad, dstate(c), k.s);
+            launch_chain((float*)c->acc.p, nullptr, prims, n, nullptr, m, v, &ad, dstate(c), k.s);
             c->launches += 1 + 2 + (n > 0 ? 1 : 0);
         }
         GVE_CUDA(cudaGetLastError(), "launch (refine)");

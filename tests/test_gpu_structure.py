@@ -30,6 +30,11 @@ FIELDS = {
     "x12": lambda: inputs.grf((9, 7, 12), seed=4),          # rows of 4-voxel lanes, no x + 16 pairs
     "x20": lambda: inputs.grf((23, 17, 20), seed=6),        # one x + 16 pair per lane group
     "x132": lambda: inputs.grf((6, 18, 132), seed=7),       # a full 128-voxel chunk and a 4-voxel tail
+    # fewer than 4 voxels (only the streaming sweep's tail), exactly one
+    # 16-byte vector of bits, one 4-voxel row of the 16-byte layout; K = 1
+    "tiny3": lambda: np.float32([[[0.05, 0.22, 0.39]]]),
+    "tiny4": lambda: np.float32([[[0.05, 0.22], [0.39, 0.56]]]),
+    "tiny4v": lambda: (np.arange(8, dtype=np.float32).reshape(2, 1, 4) * np.float32(0.17) + np.float32(0.05)),
 }
 
 

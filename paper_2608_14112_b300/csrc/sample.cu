@@ -40,7 +40,7 @@ struct CellGrid {
 CellGrid make_cells(gve_dims d)
 {
     CellGrid g{};
-    for (g.shift = 5;; ++g.shift) {
+    for (g.shift = 5;; ++g.shift) {   // 32-voxel cells unless the grid needs more than kMaxCells
         g.ncx = ((d.nx - 1) >> g.shift) + 1;
         g.ncy = ((d.ny - 1) >> g.shift) + 1;
         g.ncz = ((d.nz - 1) >> g.shift) + 1;
@@ -82,52 +82,68 @@ __global__ void __launch_bounds__(256) k_cell_count(const float4* __restrict__ p
 // One CTA scans the counts in tiles of 4,096 cells: each thread takes four
 // consecutive cells with one 16-byte load (so a warp's loads and stores are
 // contiguous), then warp and block scans of the thread sums and a running
-// carry between tiles.
+// carry between tiles.  The loads of four tiles are issued before the first
+// is scanned.
 constexpr int kScanThreads = 1024;
+constexpr int kScanTiles = 4;
+
+__device__ __forceinline__ uint4 scan_load(const uint32_t* __restrict__ ccnt, long long c, long long ncells)
+{
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (c + 3 < ncells) {
+        v = *reinterpret_cast<const uint4*>(ccnt + c);
+    } else {
+        if (c < ncells) v.x = ccnt[c];
+        if (c + 1 < ncells) v.y = ccnt[c + 1];
+        if (c + 2 < ncells) v.z = ccnt[c + 2];
+    }
+    return v;
+}
 
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const uint32_t* __restrict__ ccnt, long long ncells,
                                                             uint32_t* __restrict__ cstart)
 {
     __shared__ uint32_t wsum[kScanThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr long long tile = 4LL * kScanThreads;
     uint32_t carry = 0;
-    for (long long base = 0; base < ncells; base += 4LL * kScanThreads) {
-        const long long c = base + 4LL * threadIdx.x;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (c + 3 < ncells) {
-            v = *reinterpret_cast<const uint4*>(ccnt + c);
-        } else {
-            if (c < ncells) v.x = ccnt[c];
-            if (c + 1 < ncells) v.y = ccnt[c + 1];
-            if (c + 2 < ncells) v.z = ccnt[c + 2];
-        }
-        const uint32_t s1 = v.x + v.y, s2 = s1 + v.z, s3 = s2 + v.w;
-        uint32_t x = s3;                               // inclusive scan of the thread sums in the warp
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += t;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {                                  // inclusive scan of the warp sums
-            uint32_t y = wsum[lane];
+    for (long long base = 0; base < ncells; base += kScanTiles * tile) {
+        uint4 vt[kScanTiles];
+#pragma unroll
+        for (int u = 0; u < kScanTiles; ++u) vt[u] = scan_load(ccnt, base + u * tile + 4LL * threadIdx.x, ncells);
+#pragma unroll
+        for (int u = 0; u < kScanTiles; ++u) {
+            const long long c = base + u * tile + 4LL * threadIdx.x;
+            if (base + u * tile >= ncells) break;          // uniform across the block
+            const uint4 v = vt[u];
+            const uint32_t s1 = v.x + v.y, s2 = s1 + v.z, s3 = s2 + v.w;
+            uint32_t x = s3;                               // inclusive scan of the thread sums in the warp
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
-                if (lane >= o) y += t;
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
             }
-            wsum[lane] = y;
+            if (lane == 31) wsum[w] = x;
+            __syncthreads();
+            if (w == 0) {                                  // inclusive scan of the warp sums
+                uint32_t y = wsum[lane];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+                    if (lane >= o) y += t;
+                }
+                wsum[lane] = y;
+            }
+            __syncthreads();
+            const uint32_t e = carry + (w ? wsum[w - 1] : 0u) + x - s3;   // cells before this thread's first
+            if (c + 3 < ncells) {
+                *reinterpret_cast<uint4*>(cstart + c) = make_uint4(e, e + v.x, e + s1, e + s2);
+            } else {
+                if (c < ncells) cstart[c] = e;
+                if (c + 1 < ncells) cstart[c + 1] = e + v.x;
+                if (c + 2 < ncells) cstart[c + 2] = e + s1;
+            }
+            carry += wsum[kScanThreads / 32 - 1];
+            __syncthreads();                               // wsum is rewritten by the next tile
         }
-        __syncthreads();
-        const uint32_t e = carry + (w ? wsum[w - 1] : 0u) + x - s3;   // cells before this thread's first
-        if (c + 3 < ncells) {
-            *reinterpret_cast<uint4*>(cstart + c) = make_uint4(e, e + v.x, e + s1, e + s2);
-        } else {
-            if (c < ncells) cstart[c] = e;
-            if (c + 1 < ncells) cstart[c + 1] = e + v.x;
-            if (c + 2 < ncells) cstart[c + 2] = e + s1;
-        }
-        carry += wsum[kScanThreads / 32 - 1];
-        __syncthreads();                               // wsum is rewritten by the next tile
     }
     if (threadIdx.x == 0) cstart[ncells] = carry;
 }

@@ -1213,3 +1213,120 @@ def test_exp_fixed_against_exp():
     g = np.array([O.exp_fixed(float(x)) for x in np.linspace(-5, 5, 4001).astype(np.float32)])
     assert np.all(np.diff(g) >= 0)
     assert O.exp_fixed(100.0) == float("inf") and O.exp_fixed(-200.0) == 0.0
+
+
+# ------------------------------------------------------------------------
+# S1e shape assembly pinned on closed forms (Sec. III-E, Table I S1e)
+# ------------------------------------------------------------------------
+def _slope_field(two_slopes: bool, nx=64, ny=24, nz=20):
+    """V(x) = 1/4 + x/256, and with two_slopes the slope triples after column
+    31.  Every value is a multiple of 2^-8, so every central difference is
+    exact in float32: |grad V| = 1/256 on columns 0..30, 2/256 on column 31
+    (the kink) and 3/256 on columns 32..63 (one-sided at both borders)."""
+    x = np.arange(nx, dtype=np.float64)
+    if two_slopes:
+        v = np.where(x <= 31, 0.25 + x / 256.0, 0.25 + 31 / 256.0 + 3.0 * (x - 31) / 256.0)
+    else:
+        v = 0.25 + x / 256.0
+    return np.broadcast_to(v.astype(np.float32), (nz, ny, nx)).copy()
+
+
+@pytest.mark.parametrize("two_slopes", [False, True])
+def test_allocation_shape_closed_form_on_ramps(two_slopes):
+    """On V = c + alpha x every voxel is occupied, |grad V| = alpha and the
+    lower median gbar = alpha, so every seed gets s_t / s_perp = 1 + 1 = 2,
+    s_perp = h_g / 2 on both perpendicular axes, and its long axis
+    perpendicular to e_x (the structure tensor is rank one along e_x, so the
+    tangent -- the smallest eigenvalue's eigenvector -- lies in the y-z
+    plane).  With two slopes (31 columns at alpha, the kink column at 2 alpha,
+    32 columns at 3 alpha) the lower median of |grad V| is the kink's 2 alpha
+    (the upper median would be 3 alpha), so the ratios are 1.5, 2 and 2.5 by
+    column.  The covariance Sigma = R diag(s^2) R^T is checked, not the
+    record's axis order: e_x must be an eigenvector with eigenvalue s_perp^2
+    and the largest eigenvalue must be s_t^2."""
+    V = _slope_field(two_slopes)
+    nz, ny, nx = V.shape
+    N = 2000
+    prm, vox, st, status = O.allocate(V, N, seed=11)
+    assert status == 0
+    alpha = 1.0 / 256.0
+    assert st["gbar"] == (2 * alpha if two_slopes else alpha)
+    assert st["n_occupied"] == V.size
+    Nd = st["n_detail"]
+    cap_hi, cap_lo = max(nx, ny, nz) / 16.0, 0.3
+    xs = vox % nx
+    if two_slopes:
+        ratio = np.where(xs <= 30, 1.5, np.where(xs == 31, 2.0, 2.5))
+    else:
+        ratio = np.full(N, 2.0)
+    sig = np.where(np.arange(N) < Nd, 0.5 * st["h_detail"], 0.5 * st["h_coverage"])
+    # the design keeps every scale inside the caps, so no clamp hides a mistake
+    assert (ratio * sig < cap_hi).all() and (sig > cap_lo).all()
+    s = np.exp(prm[:, 3:6])
+    rot = Rotation.from_quat(np.concatenate([prm[:, 7:10], prm[:, 6:7]], 1)).as_matrix()
+    Sig = np.einsum("nij,nj,nkj->nik", rot, s * s, rot)
+    ex = np.array([1.0, 0.0, 0.0])
+    np.testing.assert_allclose(Sig @ ex, (sig ** 2)[:, None] * ex[None, :], rtol=0, atol=1e-9 * sig.max() ** 2)
+    ev = np.linalg.eigvalsh(Sig)
+    np.testing.assert_allclose(ev[:, 2], (ratio * sig) ** 2, rtol=1e-9)
+    np.testing.assert_allclose(ev[:, 0], sig ** 2, rtol=1e-9)
+    np.testing.assert_allclose(ev[:, 1], sig ** 2, rtol=1e-9)
+    # the record's own convention: the first scale is the elongated one
+    np.testing.assert_allclose(s[:, 0], ratio * sig, rtol=1e-12)
+    np.testing.assert_allclose(s[:, 1], sig, rtol=1e-12)
+    np.testing.assert_allclose(s[:, 2], sig, rtol=1e-12)
+
+
+# ------------------------------------------------------------------------
+# Brick lists worked out by hand (the binning rule's own pin)
+# ------------------------------------------------------------------------
+def _record(mu, scales, q=(1.0, 0.0, 0.0, 0.0), a=0.5, w_logit=0.0):
+    r = np.zeros(12, np.float32)
+    r[0:3] = mu
+    r[3:6] = np.log(np.asarray(scales, np.float64))
+    r[6:10] = q
+    r[10], r[11] = a, w_logit
+    return r
+
+
+def test_binning_hand_computed_brick_lists():
+    """Two Gaussians whose brick lists follow from the rule on paper (k = 3).
+
+    (1) Isotropic, s = 1, mu = (5.5, 5.5, 5.5) on a 16^3 grid, B = 8: the box
+    radius is kb + 0.01 with kb = 3 (1.0001 + 1e-5) = 3.00033, so the voxel box
+    is [3, 8]^3 and touches all 8 bricks.  The whitened brick test compares
+    sum_j max(0, |c_j - mu_j| - 3.51)^2 with K2 = kb^2 1.0001 + 1e-4 = 9.0029,
+    c the brick centre (3.5 or 11.5 per axis): one far axis gives 2.49^2 =
+    6.2 (kept), two give 12.4 (dropped).  So the list is bricks (0,0,0),
+    (1,0,0), (0,1,0), (0,0,1): keys (bz 2 + by) 2 + bx = 0, 1, 2, 4.  The
+    dropped bricks indeed hold no kept voxel: their nearest voxel centre, e.g.
+    (8, 8, 5), is at squared distance 12.75 > 9.
+
+    (2) Axis-aligned, s = (3, 0.5, 0.5), mu = (20.2, 4, 4) on 40 x 8 x 8:
+    cond = 36, kb = 3 (1.0001 + 3.6e-4) = 3.00138; x radius 9.014 gives voxels
+    12..29 (bricks 1..3), y and z radius 1.511 give voxels 3..5 (brick 0).
+    The whitened test passes all three (x offsets 2.9 and 2.43 against a
+    half-extent of 3.51 / 3), so the keys are 1, 2, 3.  Swapped axes would
+    give a single brick."""
+    p1 = _record((5.5, 5.5, 5.5), (1.0, 1.0, 1.0))
+    counts, keys, gids = O.bin_pairs(p1[None, :], (16, 16, 16), 3.0, 8)
+    assert counts.tolist() == [4]
+    assert keys.tolist() == [0, 1, 2, 4] and gids.tolist() == [0, 0, 0, 0]
+    p2 = _record((20.2, 4.0, 4.0), (3.0, 0.5, 0.5))
+    counts, keys, gids = O.bin_pairs(p2[None, :], (40, 8, 8), 3.0, 8)
+    assert counts.tolist() == [3] and keys.tolist() == [1, 2, 3]
+    # both at once: Gaussian-major emission, then the stable sort by brick
+    both = np.stack([p1, p1])
+    # the mirror image of (1) across the brick boundary x = 7.5 keeps bricks
+    # (1,0,0), (0,0,0), (1,1,0), (1,0,1): keys 0, 1, 3, 5
+    both[1, 0:3] = (9.5, 5.5, 5.5)
+    counts, sk, sg, start, end = O.bin_sorted(both, (16, 16, 16), 3.0, 8)
+    assert counts.tolist() == [4, 4]
+    assert sk.tolist() == [0, 0, 1, 1, 2, 3, 4, 5]
+    assert sg.tolist() == [0, 1, 0, 1, 0, 1, 0, 1]
+    assert start.tolist()[:6] == [0, 2, 4, 5, 6, 7] and end.tolist()[:6] == [2, 4, 5, 6, 7, 8]
+    # (1) shifted by half a voxel along x: box [3, 9] in x; the far x brick
+    # gives (5.5 - 3.51)^2 = 3.96 alone (kept) and 3.96 + 6.2 with a far y or
+    # z offset (dropped), so the list of (1) is unchanged
+    counts, keys, _ = O.bin_pairs(_record((6.0, 5.5, 5.5), (1.0, 1.0, 1.0))[None, :], (16, 16, 16), 3.0, 8)
+    assert keys.tolist() == [0, 1, 2, 4]

@@ -292,6 +292,11 @@ static int enum_box(const act_t* A, double k, int truncated, const int dims[3], 
     return 1;
 }
 
+static inline int64_t vidx_of(const int dims[3], int x, int y, int z)
+{
+    return ((int64_t)z * dims[1] + y) * dims[0] + x;
+}
+
 /* Mahalanobis distance squared at voxel centre p, FP64. */
 static double maha2(const act_t* A, double px, double py, double pz)
 {
@@ -314,6 +319,7 @@ static gctx_t* prepare(const double* prm, const double* pred_prm, int64_t n, dou
 {
     gctx_t* G = (gctx_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(gctx_t));
     if (!G) return NULL;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         activate(prm + 12 * i, &G[i].A);
         const double* pp = pred_prm ? pred_prm + 12 * i : prm + 12 * i;
@@ -345,12 +351,9 @@ static int kept(const gctx_t* g, float T, int truncated, int x, int y, int z)
 /* Gaussian (the dense sum).  normalized = 0 returns num (plain sum).        */
 /* pred_prm (optional) decides membership instead of prm (frozen mask).      */
 /* ------------------------------------------------------------------------ */
-int or_eval_region(const double* prm, const double* pred_prm, int64_t n, const int dims[3],
-                   const int r0[3], const int rs[3], float k, double rho0, int normalized,
-                   int truncated, double* num, double* den, double* vt)
+static int eval_region_prepared(const gctx_t* G, int64_t n, const int r0[3], const int rs[3], float k,
+                                double rho0, int normalized, int truncated, double* num, double* den, double* vt)
 {
-    gctx_t* G = prepare(prm, pred_prm, n, (double)k, truncated, dims);
-    if (!G) return 1;
     float T = pred_threshold(k);
     /* Gaussians whose box meets the region, in ascending index order */
     int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -394,8 +397,36 @@ int or_eval_region(const double* prm, const double* pred_prm, int64_t n, const i
         }
     }
     free(ids);
-    free(G);
     return 0;
+}
+
+int or_eval_region(const double* prm, const double* pred_prm, int64_t n, const int dims[3],
+                   const int r0[3], const int rs[3], float k, double rho0, int normalized,
+                   int truncated, double* num, double* den, double* vt)
+{
+    gctx_t* G = prepare(prm, pred_prm, n, (double)k, truncated, dims);
+    if (!G) return 1;
+    int rc = eval_region_prepared(G, n, r0, rs, k, rho0, normalized, truncated, num, den, vt);
+    free(G);
+    return rc;
+}
+
+/* Eq. 3 on nblk regions of the same size rs, corners r0s[b][3]: the
+ * primitives are activated once for all of them (large models, many small
+ * regions).  vt: [nblk][rs[2]][rs[1]][rs[0]]. */
+int or_eval_blocks(const double* prm, int64_t n, const int dims[3], int64_t nblk, const int* r0s, const int rs[3],
+                   float k, double rho0, int normalized, double* vt)
+{
+    gctx_t* G = prepare(prm, NULL, n, (double)k, 1, dims);
+    if (!G) return 1;
+    int64_t R = (int64_t)rs[0] * rs[1] * rs[2];
+    double* num = (double*)malloc(sizeof(double) * (size_t)R);
+    double* den = (double*)malloc(sizeof(double) * (size_t)R);
+    int rc = (num && den) ? 0 : 1;
+    for (int64_t b = 0; b < nblk && rc == 0; ++b)
+        rc = eval_region_prepared(G, n, r0s + 3 * b, rs, k, rho0, normalized, 1, num, den, vt + R * b);
+    free(num); free(den); free(G);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -582,6 +613,44 @@ int64_t or_count_kept(const float* p32, int64_t n, const int dims[3], float k)
     return total;
 }
 
+/* The kept (voxel, Gaussian) pairs themselves, Gaussian-major, voxels
+ * ascending within a Gaussian: out[j] = (voxel index << 24) | Gaussian index
+ * for j < min(total, cap).  Returns the total. */
+int64_t or_list_kept(const float* p32, int64_t n, const int dims[3], float k, uint64_t* out, int64_t cap)
+{
+    float T = pred_threshold(k);
+    int64_t* cnt = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+    if (!cnt) return -1;
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            double p[12];
+            for (int j = 0; j < 12; ++j) p[j] = (double)p32[12 * i + j];
+            gctx_t g;
+            activate(p, &g.A);
+            pred_coeffs(p32 + 12 * i, &g.P);
+            if (!g.A.valid || !g.P.valid || !enum_box(&g.A, k, 1, dims, g.lo, g.hi)) continue;
+            int64_t m = pass == 0 ? 0 : cnt[i];
+            for (int z = g.lo[2]; z <= g.hi[2]; ++z)
+                for (int y = g.lo[1]; y <= g.hi[1]; ++y)
+                    for (int x = g.lo[0]; x <= g.hi[0]; ++x) {
+                        if (!(pred_t_of(&g.P, x, y, z) > T)) continue;
+                        if (pass == 1 && m < cap) out[m] = ((uint64_t)vidx_of(dims, x, y, z) << 24) | (uint64_t)i;
+                        ++m;
+                    }
+            if (pass == 0) cnt[i] = m;
+        }
+        if (pass == 0) {  /* exclusive scan of the per-Gaussian counts */
+            int64_t run = 0;
+            for (int64_t i = 0; i < n; ++i) { int64_t c = cnt[i]; cnt[i] = run; run += c; }
+            cnt[n] = run;
+        }
+    }
+    int64_t total = cnt[n];
+    free(cnt);
+    return total;
+}
+
 /* Gradient for a subset of Gaussians only; the field values it needs are
  * computed on each Gaussian's own box from all Gaussians.  M is the full grid
  * size used as the loss normaliser. */
@@ -592,6 +661,8 @@ int or_grad_subset(const double* prm, int64_t n, const float* field, const int d
     int64_t M = (int64_t)dims[0] * dims[1] * dims[2];
     float T = pred_threshold(k);
     float mthr = (float)mask_thresh;
+    gctx_t* GA = prepare(prm, NULL, n, (double)k, 1, dims);
+    if (!GA) return 1;
     for (int64_t t = 0; t < nids; ++t) {
         int64_t i = ids[t];
         double* out = grad + 12 * t;
@@ -607,7 +678,7 @@ int or_grad_subset(const double* prm, int64_t n, const float* field, const int d
         double* num = (double*)malloc(sizeof(double) * (size_t)R);
         double* den = (double*)malloc(sizeof(double) * (size_t)R);
         double* vt = (double*)malloc(sizeof(double) * (size_t)R);
-        or_eval_region(prm, NULL, n, dims, g.lo, rs, k, rho0, normalized, 1, num, den, vt);
+        eval_region_prepared(GA, n, g.lo, rs, k, rho0, normalized, 1, num, den, vt);
         double Ag = 0, Bg = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0}};
         for (int z = g.lo[2]; z <= g.hi[2]; ++z)
             for (int y = g.lo[1]; y <= g.hi[1]; ++y)
@@ -635,6 +706,7 @@ int or_grad_subset(const double* prm, int64_t n, const float* field, const int d
         chain_rule(&g.A, prm + 12 * i, Ag, Bg, S1, S2, out);
         free(num); free(den); free(vt);
     }
+    free(GA);
     return 0;
 }
 
@@ -825,6 +897,31 @@ void or_kept_submasks(const float* p32, const int dims[3], float k, int B, int64
 }
 
 /* ------------------------------------------------------------------------ */
+/* Stage P (Sec. III-B): the field rescaled to [0, 1] by its own minimum and */
+/* maximum, in float32: out = (V - min) / (max - min), each operation        */
+/* correctly rounded (a constant field maps to 0).  minmax (optional)        */
+/* receives the two float32 extremes.  Returns 1 (nothing written) when a   */
+/* value is not finite, else 0.  out may equal V.                           */
+/* ------------------------------------------------------------------------ */
+int or_normalize(const float* V, int64_t M, float* out, float* minmax)
+{
+    if (M <= 0) return 0;
+    float mn = V[0], mx = V[0];
+    for (int64_t i = 0; i < M; ++i) {
+        if (!isfinite(V[i])) return 1;
+        if (V[i] < mn) mn = V[i];
+        if (V[i] > mx) mx = V[i];
+    }
+    float range = mx - mn;
+    for (int64_t i = 0; i < M; ++i) {
+        float d = V[i] - mn;
+        out[i] = range > 0.0f ? d / range : 0.0f;
+    }
+    if (minmax) { minmax[0] = mn; minmax[1] = mx; }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Allocation (Sec. III-E, Table I S1a..S1e).                                */
 /* ------------------------------------------------------------------------ */
 static inline int64_t vidx(const int dims[3], int x, int y, int z)
@@ -850,20 +947,34 @@ static float dcomp32(const float* V, const int dims[3], int x, int y, int z, int
     return scale * diff;
 }
 
+static float gmag32_at(const float* V, const int dims[3], int x, int y, int z)
+{
+    float gx = dcomp32(V, dims, x, y, z, 0);
+    float gy = dcomp32(V, dims, x, y, z, 1);
+    float gz = dcomp32(V, dims, x, y, z, 2);
+    float sx = gx * gx, sy = gy * gy, sz = gz * gz;
+    float s = sx + sy;
+    s = s + sz;
+    return sqrtf(s);
+}
+
 void or_grad_mag32(const float* V, const int dims[3], float* g)
 {
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < dims[2]; ++z)
         for (int y = 0; y < dims[1]; ++y)
-            for (int x = 0; x < dims[0]; ++x) {
-                float gx = dcomp32(V, dims, x, y, z, 0);
-                float gy = dcomp32(V, dims, x, y, z, 1);
-                float gz = dcomp32(V, dims, x, y, z, 2);
-                float sx = gx * gx, sy = gy * gy, sz = gz * gz;
-                float s = sx + sy;
-                s = s + sz;
-                g[vidx(dims, x, y, z)] = sqrtf(s);
-            }
+            for (int x = 0; x < dims[0]; ++x) g[vidx(dims, x, y, z)] = gmag32_at(V, dims, x, y, z);
+}
+
+/* The same float32 |grad V| at n listed voxel indices. */
+void or_grad_mag32_at(const float* V, const int dims[3], const int64_t* vox, int64_t n, float* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = vox[i];
+        int x = (int)(v % dims[0]), y = (int)((v / dims[0]) % dims[1]), z = (int)(v / ((int64_t)dims[0] * dims[1]));
+        out[i] = gmag32_at(V, dims, x, y, z);
+    }
 }
 
 /* FP64 gradient vector for the structure tensor. */
@@ -1139,6 +1250,41 @@ double or_group_spacing(const int64_t* vox, int64_t ng, const int dims[3], int64
     return h;
 }
 
+/* S1d + S1e for one seed at voxel v (|grad V| = gv there), index gi within
+ * group grp: jitter (Eq. 4), 7^3 structure tensor, Jacobi, frame and
+ * quaternion, scales s_t = sigma_g clamp(1 + gv / gbar, 1, 3), s_perp =
+ * sigma_g with sigma_g = h_g / 2, all clamped to [0.3, max(dims) / 16],
+ * a = trilinear V(mu), w_logit = logit(w0). */
+static void assemble_seed(const float* V, const int dims[3], int64_t v, float gv, int64_t gi, int grp, uint64_t seed,
+                          double h, double gbar, double wl, double* p)
+{
+    double smax_cap = (double)(dims[0] > dims[1] ? (dims[0] > dims[2] ? dims[0] : dims[2])
+                                                 : (dims[1] > dims[2] ? dims[1] : dims[2])) / 16.0;
+    double smin_cap = 0.3;
+    int cx = (int)(v % dims[0]), cy = (int)((v / dims[0]) % dims[1]), cz = (int)(v / ((int64_t)dims[0] * dims[1]));
+    float u[3];
+    or_jitter((uint64_t)gi, (uint32_t)grp, seed, u);
+    p[0] = cx + (double)u[0]; p[1] = cy + (double)u[1]; p[2] = cz + (double)u[2];
+    double J6[6], ev[3], evec[9], R9[9], q[4];
+    or_struct_tensor(V, dims, cx, cy, cz, J6);
+    or_jacobi3(J6, ev, evec);
+    canonical_frame(evec, R9);
+    or_quat_from_R(R9, q);
+    double sg = 0.5 * h;
+    double ratio = gbar > 0.0 ? 1.0 + (double)gv / gbar : 1.0;
+    if (ratio < 1.0) ratio = 1.0;
+    if (ratio > 3.0) ratio = 3.0;
+    double s[3] = {sg * ratio, sg, sg};
+    for (int j = 0; j < 3; ++j) {
+        if (s[j] > smax_cap) s[j] = smax_cap;
+        if (s[j] < smin_cap) s[j] = smin_cap;
+        p[3 + j] = log(s[j]);
+    }
+    p[6] = q[0]; p[7] = q[1]; p[8] = q[2]; p[9] = q[3];
+    p[10] = or_trilinear(V, dims, p[0], p[1], p[2]);
+    p[11] = wl;
+}
+
 typedef struct {
     int64_t n_occupied, n_eligible, n_detail, n_coverage, feasible_max;
     double gbar, h_detail, h_coverage;
@@ -1198,9 +1344,6 @@ int or_allocate(const float* V, const int dims[3], int64_t N, double detail_frac
     double hd = or_group_spacing(vd, Nd, dims, n_occ, N);
     double hc = or_group_spacing(vc, Nc, dims, n_occ, N);
     st->h_detail = hd; st->h_coverage = hc;
-    double smax_cap = (double)(dims[0] > dims[1] ? (dims[0] > dims[2] ? dims[0] : dims[2])
-                                                 : (dims[1] > dims[2] ? dims[1] : dims[2])) / 16.0;
-    double smin_cap = 0.3;
     double wl = log(w0 / (1.0 - w0));
     /* S1d + S1e per seed */
 #pragma omp parallel for schedule(dynamic, 64)
@@ -1209,33 +1352,77 @@ int or_allocate(const float* V, const int dims[3], int64_t N, double detail_frac
         int64_t gi = grp == 0 ? i : i - Nd;
         int64_t v = grp == 0 ? vd[gi] : vc[gi];
         if (vox_out) vox_out[i] = v;
-        int cx = (int)(v % dims[0]), cy = (int)((v / dims[0]) % dims[1]),
-            cz = (int)(v / ((int64_t)dims[0] * dims[1]));
-        float u[3];
-        or_jitter((uint64_t)gi, (uint32_t)grp, seed, u);
-        double* p = prm_out + 12 * i;
-        p[0] = cx + (double)u[0]; p[1] = cy + (double)u[1]; p[2] = cz + (double)u[2];
-        double J6[6], ev[3], evec[9], R9[9], q[4];
-        or_struct_tensor(V, dims, cx, cy, cz, J6);
-        or_jacobi3(J6, ev, evec);
-        canonical_frame(evec, R9);
-        or_quat_from_R(R9, q);
-        double sg = 0.5 * (grp == 0 ? hd : hc);
-        double ratio = gbar > 0.0 ? 1.0 + (double)g[v] / gbar : 1.0;
-        if (ratio < 1.0) ratio = 1.0;
-        if (ratio > 3.0) ratio = 3.0;
-        double s[3] = {sg * ratio, sg, sg};
-        for (int j = 0; j < 3; ++j) {
-            if (s[j] > smax_cap) s[j] = smax_cap;
-            if (s[j] < smin_cap) s[j] = smin_cap;
-            p[3 + j] = log(s[j]);
-        }
-        p[6] = q[0]; p[7] = q[1]; p[8] = q[2]; p[9] = q[3];
-        p[10] = or_trilinear(V, dims, p[0], p[1], p[2]);
-        p[11] = wl;
+        assemble_seed(V, dims, v, g[v], gi, grp, seed, grp == 0 ? hd : hc, gbar, wl, prm_out + 12 * i);
     }
     free(vd); free(vc); free(g);
     return 0;
+}
+
+/* S1d + S1e for caller-given seeds: voxel vox[i], index gi[i] within group
+ * grp[i] (0 detail, 1 coverage), group spacings hd / hc, median gbar; the
+ * same per-seed arithmetic as or_allocate.  out: [n][12]. */
+void or_assemble_seeds(const float* V, const int dims[3], const int64_t* vox, const int64_t* gi, const int* grp,
+                       int64_t n, uint64_t seed, double hd, double hc, double gbar, double w0, double* out)
+{
+    double wl = log(w0 / (1.0 - w0));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = vox[i];
+        int x = (int)(v % dims[0]), y = (int)((v / dims[0]) % dims[1]), z = (int)(v / ((int64_t)dims[0] * dims[1]));
+        assemble_seed(V, dims, v, gmag32_at(V, dims, x, y, z), gi[i], grp[i], seed, grp[i] == 0 ? hd : hc, gbar,
+                      wl, out + 12 * i);
+    }
+}
+
+/* Exhaustive census of the draws over the whole grid (Sec. III-E S1b), for
+ * checking a draw made elsewhere at any size: out = {occupied voxels,
+ * eligible voxels (occupied, |grad V| > 0), eligible voxels whose (detail
+ * key, index) is at most (kd, kd_idx), occupied voxels whose (coverage key,
+ * index) is at most (ku, ku_idx), occupied voxels with |grad V| < gbar,
+ * occupied voxels with |grad V| <= gbar}. */
+void or_draw_census(const float* V, const int dims[3], float occ_thresh, uint64_t seed, double kd, int64_t kd_idx,
+                    uint64_t ku, int64_t ku_idx, float gbar, int64_t out[6])
+{
+    int64_t n_occ = 0, n_elig = 0, n_d = 0, n_u = 0, n_lt = 0, n_le = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : n_occ, n_elig, n_d, n_u, n_lt, n_le)
+    for (int z = 0; z < dims[2]; ++z)
+        for (int y = 0; y < dims[1]; ++y)
+            for (int x = 0; x < dims[0]; ++x) {
+                int64_t v = vidx(dims, x, y, z);
+                if (!(V[v] > occ_thresh)) continue;
+                ++n_occ;
+                float g = gmag32_at(V, dims, x, y, z);
+                n_lt += g < gbar;
+                n_le += g <= gbar;
+                uint64_t ukey = or_coverage_key((uint64_t)v, seed);
+                n_u += ukey < ku || (ukey == ku && v <= ku_idx);
+                if (g > 0.0f) {
+                    ++n_elig;
+                    double dkey = or_detail_key((uint64_t)v, seed, g);
+                    n_d += dkey < kd || (dkey == kd && v <= kd_idx);
+                }
+            }
+    out[0] = n_occ; out[1] = n_elig; out[2] = n_d; out[3] = n_u; out[4] = n_lt; out[5] = n_le;
+}
+
+/* Draw keys of listed voxels (for the census thresholds). */
+void or_detail_keys(const int64_t* vox, const float* g, int64_t n, uint64_t seed, double* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) out[i] = or_detail_key((uint64_t)vox[i], seed, g[i]);
+}
+
+void or_coverage_keys(const int64_t* vox, int64_t n, uint64_t seed, uint64_t* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) out[i] = or_coverage_key((uint64_t)vox[i], seed);
+}
+
+/* Jitter of seeds 0..n-1 of one group: out [n][3]. */
+void or_jitter_many(int64_t n, uint32_t group, uint64_t seed, float* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) or_jitter((uint64_t)i, group, seed, out + 3 * i);
 }
 
 /* ------------------------------------------------------------------------ */

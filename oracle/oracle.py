@@ -127,6 +127,24 @@ def lib():
             L.or_group_spacing.restype = f64
             L.or_allocate.argtypes = [P, P, i64, f64, f32, f64, u64, P, P, ctypes.POINTER(AllocStats)]
             L.or_allocate.restype = i32
+            L.or_eval_blocks.argtypes = [P, i64, P, i64, P, P, f32, f64, i32, P]
+            L.or_eval_blocks.restype = i32
+            L.or_grad_mag32_at.argtypes = [P, P, P, i64, P]
+            L.or_grad_mag32_at.restype = None
+            L.or_assemble_seeds.argtypes = [P, P, P, P, P, i64, u64, f64, f64, f64, f64, P]
+            L.or_assemble_seeds.restype = None
+            L.or_draw_census.argtypes = [P, P, f32, u64, f64, i64, u64, i64, f32, P]
+            L.or_draw_census.restype = None
+            L.or_detail_keys.argtypes = [P, P, i64, u64, P]
+            L.or_detail_keys.restype = None
+            L.or_coverage_keys.argtypes = [P, i64, u64, P]
+            L.or_coverage_keys.restype = None
+            L.or_jitter_many.argtypes = [i64, u32, u64, P]
+            L.or_jitter_many.restype = None
+            L.or_list_kept.argtypes = [P, i64, P, f32, P, i64]
+            L.or_list_kept.restype = i64
+            L.or_normalize.argtypes = [P, i64, P, P]
+            L.or_normalize.restype = i32
             _lib = L
     return _lib
 
@@ -205,6 +223,22 @@ def eval_region(prm, dims, region=None, k=3.0, rho0=0.05, normalized=True, trunc
     return num, den, vt
 
 
+def eval_blocks(prm, dims, corners, size, k=3.0, rho0=0.05, normalized=True):
+    """Eq. 3 on many regions of one size: ``corners`` (B, 3) as (x0, y0, z0),
+    ``size`` (sx, sy, sz); the records are activated once for all regions.
+    Returns vtilde float64 (B, sz, sy, sx)."""
+    d = _dims(dims)
+    c = np.ascontiguousarray(np.asarray(corners, np.int32).reshape(-1, 3))
+    rs = np.ascontiguousarray(np.asarray(size, np.int32).reshape(3))
+    p = _prm64(prm)
+    vt = np.zeros((c.shape[0], int(rs[2]), int(rs[1]), int(rs[0])), np.float64)
+    rc = lib().or_eval_blocks(_ptr(p), p.shape[0], _ptr(d), c.shape[0], _ptr(c), _ptr(rs), float(k), float(rho0),
+                              int(bool(normalized)), _ptr(vt))
+    if rc != 0:
+        raise MemoryError("oracle eval failed")
+    return vt
+
+
 def loss_grad(prm, field, k=3.0, rho0=0.05, normalized=True, truncated=True, mask_thresh=-1.0,
               pred_prm=None, want_grad=True):
     """Full-grid MSE (Eq. 6 value term, mean over voxels), its analytic
@@ -251,6 +285,20 @@ def count_kept(p32, dims, k=3.0) -> int:
     """Number of kept (voxel, Gaussian) pairs of one truncated evaluation."""
     p = _f32c(p32).reshape(-1, 12)
     return int(lib().or_count_kept(_ptr(p), p.shape[0], _ptr(_dims(dims)), float(k)))
+
+
+def list_kept(p32, dims, k=3.0) -> np.ndarray:
+    """The kept (voxel, Gaussian) pairs of one truncated evaluation, (K, 2)
+    int64 (voxel index (z ny + y) nx + x, Gaussian index), sorted."""
+    p = _f32c(p32).reshape(-1, 12)
+    d = _dims(dims)
+    total = int(lib().or_list_kept(_ptr(p), p.shape[0], _ptr(d), float(k), None, 0))
+    if total < 0:
+        raise MemoryError("oracle pair listing failed")
+    out = np.zeros(max(total, 1), np.uint64)
+    lib().or_list_kept(_ptr(p), p.shape[0], _ptr(d), float(k), _ptr(out), total)
+    v = np.sort(out[:total].astype(np.int64))
+    return np.stack([v >> 24, v & ((1 << 24) - 1)], 1)
 
 
 def psnr_from_sse(sse: float, M: int) -> float:
@@ -631,6 +679,81 @@ def jitter(i: int, group: int, seed: int) -> np.ndarray:
 def group_spacing(vox, dims, n_occupied, N) -> float:
     v = np.ascontiguousarray(np.asarray(vox, np.int64))
     return float(lib().or_group_spacing(_ptr(v), v.size, _ptr(_dims(dims)), int(n_occupied), int(N)))
+
+
+def grad_mag32_at(field, vox) -> np.ndarray:
+    """The allocator's float32 |grad V| (S1a) at listed voxel indices."""
+    f = _f32c(field)
+    v = np.ascontiguousarray(np.asarray(vox, np.int64))
+    out = np.zeros(v.size, np.float32)
+    lib().or_grad_mag32_at(_ptr(f), _ptr(_dims(f)), _ptr(v), v.size, _ptr(out))
+    return out
+
+
+def detail_keys(vox, g, seed: int) -> np.ndarray:
+    """Efraimidis-Spirakis keys of the detail draw at listed voxels."""
+    v = np.ascontiguousarray(np.asarray(vox, np.int64))
+    gg = _f32c(g).reshape(-1)
+    out = np.zeros(v.size, np.float64)
+    lib().or_detail_keys(_ptr(v), _ptr(gg), v.size, int(seed), _ptr(out))
+    return out
+
+
+def coverage_keys(vox, seed: int) -> np.ndarray:
+    """Philox keys of the coverage draw at listed voxels."""
+    v = np.ascontiguousarray(np.asarray(vox, np.int64))
+    out = np.zeros(v.size, np.uint64)
+    lib().or_coverage_keys(_ptr(v), v.size, int(seed), _ptr(out))
+    return out
+
+
+def jitter_many(n: int, group: int, seed: int) -> np.ndarray:
+    """Jitter (Eq. 4) of seeds 0..n-1 of a group: (n, 3) float32."""
+    out = np.zeros((int(n), 3), np.float32)
+    lib().or_jitter_many(int(n), int(group), int(seed), _ptr(out))
+    return out
+
+
+def draw_census(field, seed: int, kd: float, kd_idx: int, ku: int, ku_idx: int, gbar: float,
+                occ_thresh: float = 0.02) -> dict:
+    """Exhaustive counts over the whole grid for checking a draw made
+    elsewhere (S1b): occupied and eligible voxels, eligible voxels whose
+    (detail key, index) is at most (kd, kd_idx), occupied voxels whose
+    (coverage key, index) is at most (ku, ku_idx), and occupied voxels with
+    |grad V| below / at most gbar."""
+    f = _f32c(field)
+    out = np.zeros(6, np.int64)
+    lib().or_draw_census(_ptr(f), _ptr(_dims(f)), float(np.float32(occ_thresh)), int(seed), float(kd), int(kd_idx),
+                         int(ku), int(ku_idx), float(np.float32(gbar)), _ptr(out))
+    return dict(zip(("n_occupied", "n_eligible", "detail_at_most", "coverage_at_most", "g_below", "g_at_most"),
+                    (int(x) for x in out)))
+
+
+def assemble_seeds(field, vox, gi, grp, seed: int, h_detail: float, h_coverage: float, gbar: float,
+                   w0: float = 0.1) -> np.ndarray:
+    """S1d + S1e of listed seeds (voxel, index within its group, group 0 =
+    detail / 1 = coverage) with given group spacings and median: the records
+    the allocation gives those seeds, (n, 12) float64."""
+    f = _f32c(field)
+    v = np.ascontiguousarray(np.asarray(vox, np.int64))
+    i = np.ascontiguousarray(np.asarray(gi, np.int64))
+    g = np.ascontiguousarray(np.asarray(grp, np.int32))
+    out = np.zeros((v.size, 12), np.float64)
+    lib().or_assemble_seeds(_ptr(f), _ptr(_dims(f)), _ptr(v), _ptr(i), _ptr(g), v.size, int(seed), float(h_detail),
+                            float(h_coverage), float(gbar), float(w0), _ptr(out))
+    return out
+
+
+def normalize(field):
+    """Stage P (Sec. III-B): (V - min) / (max - min) in float32, correctly
+    rounded per operation (a constant field maps to 0).  Returns (field,
+    (min, max)); raises ValueError on a non-finite value."""
+    f = _f32c(field)
+    out = np.empty_like(f)
+    mm = np.zeros(2, np.float32)
+    if lib().or_normalize(_ptr(f), f.size, _ptr(out), _ptr(mm)) != 0:
+        raise ValueError("non-finite value in the field")
+    return out, (float(mm[0]), float(mm[1]))
 
 
 def allocate(field, N, detail_frac=0.55, occ_thresh=0.02, w0=0.1, seed=0):

@@ -1330,3 +1330,53 @@ def test_binning_hand_computed_brick_lists():
     # z offset (dropped), so the list of (1) is unchanged
     counts, keys, _ = O.bin_pairs(_record((6.0, 5.5, 5.5), (1.0, 1.0, 1.0))[None, :], (16, 16, 16), 3.0, 8)
     assert keys.tolist() == [0, 1, 2, 4]
+
+
+# ------------------------------------------------------------------------
+# Stage P: normalisation to [0, 1] (Sec. III-B)
+# ------------------------------------------------------------------------
+def test_normalize_closed_forms():
+    """A dyadic ramp V = 3/8 + x/64 (every difference exact) maps to the
+    correctly rounded x / (nx - 1): numpy's float32 division is the IEEE
+    operation, so equality is bit for bit; the extremes map to exactly 0 and
+    1; a constant field maps to 0; a non-finite value is refused; and the
+    result does not depend on where the values sit in the grid."""
+    nz, ny, nx = 3, 5, 37
+    x = np.arange(nx, dtype=np.float32)
+    V = np.broadcast_to((np.float32(0.375) + x / np.float32(64.0)).astype(np.float32), (nz, ny, nx)).copy()
+    out, (mn, mx) = O.normalize(V)
+    assert (mn, mx) == (0.375, 0.375 + 36 / 64.0)
+    want = (x / np.float32(nx - 1)).astype(np.float32)
+    np.testing.assert_array_equal(out, np.broadcast_to(want, V.shape))
+    assert out.min() == 0.0 and out.max() == 1.0
+    z, _ = O.normalize(np.full((4, 4, 4), 0.7, np.float32))
+    assert (z == 0).all()
+    bad = V.copy()
+    bad[1, 2, 3] = np.inf
+    with pytest.raises(ValueError):
+        O.normalize(bad)
+    rng = np.random.default_rng(3)
+    R = rng.normal(size=(9, 8, 7)).astype(np.float32)
+    perm = rng.permutation(R.size)
+    a, _ = O.normalize(R)
+    b, _ = O.normalize(R.reshape(-1)[perm].reshape(R.shape))
+    np.testing.assert_array_equal(a.reshape(-1)[perm], b.reshape(-1))
+    # scaling by a power of two and shifting by a dyadic constant change
+    # nothing (every rounding is the same)
+    c, _ = O.normalize((R * np.float32(4.0)).astype(np.float32))
+    np.testing.assert_array_equal(a, c)
+
+
+def test_list_kept_matches_count_and_keep_rule():
+    """The listed kept pairs are the count of the keep rule, each one kept by
+    the float32 test and no pair listed twice."""
+    rng = np.random.default_rng(8)
+    dims = (19, 14, 11)
+    p = _rand_prims(rng, 25, dims, s_lo=0.4, s_hi=2.5).astype(np.float32)
+    L = O.list_kept(p, dims)
+    assert L.shape[0] == O.count_kept(p, dims)
+    assert np.unique(L, axis=0).shape[0] == L.shape[0]
+    T = O.pred_threshold(3.0)
+    for v, i in L[:: max(1, L.shape[0] // 200)]:
+        x, y, z = v % dims[0], (v // dims[0]) % dims[1], v // (dims[0] * dims[1])
+        assert O.pred_t(p[i], int(x), int(y), int(z)) > T

@@ -40,10 +40,10 @@ METRIC = "fwd+bwd refine iters/s at 1024^3, 1.4M Gaussians; time-to-PSNR vs plai
 # per kept (voxel, Gaussian) pair: 15 FP32 ops in the forward (3 differences,
 # 9 for the quadratic form, 1 compare, 2 accumulations) and 30 in the backward
 # (recomputation plus the 11 accumulated sums); 2 SFU exponentials
-OPS_PER_PAIR = 45.0
-SMS = 148
-FP32_LANES = 128
-SM_MAX_MHZ = 2032.0
+FWD_OPS_PER_PAIR = 15.0
+BWD_OPS_PER_PAIR = 30.0
+OPS_PER_PAIR = FWD_OPS_PER_PAIR + BWD_OPS_PER_PAIR
+EX2_PER_PAIR = 2.0
 
 
 def parse():
@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--prop-iters", type=int, default=200, help="refinement iterations per proposal evaluation")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
+    ap.add_argument("--ttp-iters", type=int, default=2000, help="full schedule of the time-to-PSNR run (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample", type=int, default=192, help="edge of the CPU sample sub-volume")
     ap.add_argument("--sample-iters", type=int, default=3)
@@ -163,6 +164,73 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def measured_alu_peaks(dev, seconds=0.8):
+    """The FP32 and SFU ceilings of this GPU, measured now by the library's
+    microbenchmarks (gve_peak_bench): scalar FMA, packed f32x2 FMA (two
+    lane-operations each) and ex2.approx, each a launch of about `seconds`
+    with 8 CTAs x 256 threads per SM, timed with CUDA events, the SM clock
+    sampled meanwhile.  Lane-operations per second in Top/s; the FP32 peak is
+    the larger of the scalar and packed rates (FMA counted once, as in the
+    algorithmic operation counts)."""
+    import torch
+    from paper_2608_14112_b300 import gve
+    out = {}
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    for kind, probe in (("ffma", 200), ("ffma2", 200), ("ex2", 50)):
+        _, ms = gve.gve_peak_bench(kind, probe, device=dev)
+        iters = max(probe, int(probe * seconds * 1e3 / max(ms, 1e-3)))
+        ops, ms = gve.gve_peak_bench(kind, iters, device=dev)
+        out[kind + "_tops"] = ops / 1e12
+        out[kind + "_ms"] = ms
+    clk = clocks.stop()
+    out["fp32_tops"] = max(out["ffma_tops"], out["ffma2_tops"])
+    out["clocks"] = clk
+    props = torch.cuda.get_device_properties(dev)
+    out["sms"] = props.multi_processor_count
+    return out
+
+
+def time_to_psnr(V, w, opts, seed, alloc_ms, full=2000, reduced=300):
+    """Time-to-PSNR of the plain method (Sec. V-D's reduced schedule against
+    the full one): one refinement of `full` iterations from a fresh
+    allocation with the per-iteration loss trace; PSNR after t updates is
+    -10 log10(trace[t]) (the unmasked mean squared error), and after the last
+    update the call's final PSNR.  The target is the full schedule's final
+    PSNR - 0.1 dB; its time is the allocation plus the iterations needed to
+    first reach it, at this run's own ms per iteration (CUDA events).  The
+    reduced schedule is the same run's first `reduced` iterations (constant
+    learning rate: a shorter schedule is a prefix of the longer one)."""
+    import numpy as np
+    import torch
+    from paper_2608_14112_b300 import gve
+    dev = V.device
+    stream = torch.cuda.current_stream(dev)
+    P, _ = gve.gve_allocate(V, w["budget"], seed=seed)
+    state = torch.zeros((2, w["budget"], 12), dtype=torch.float32, device=dev)
+    trace = torch.zeros(full, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st = gve.gve_refine(P, V, iters=full, lr=w["lr"], adam_state=state, trace=trace, opts=opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ms_iter = ms / full
+    after = np.r_[-10.0 * np.log10(trace.cpu().numpy()[1:]), st["psnr_final"]]   # after 1..full updates
+    final = float(st["psnr_final"])
+    target = final - 0.1
+    t_star = int(np.nonzero(after >= target)[0][0]) + 1
+    red = float(after[reduced - 1])
+    return {"schedule_full": full, "schedule_reduced": reduced, "psnr_full_db": final,
+            "psnr_reduced_db": red, "reduced_gap_db": final - red, "target_db": target,
+            "iters_to_target": t_star, "ms_per_iter": ms_iter, "alloc_ms": alloc_ms,
+            "full_s": (alloc_ms + full * ms_iter) / 1e3, "reduced_s": (alloc_ms + reduced * ms_iter) / 1e3,
+            "time_to_target_s": (alloc_ms + t_star * ms_iter) / 1e3,
+            "reduced_reaches_target": bool(red >= target), "launches": int(st["launches"]),
+            "psnr_at": {str(t): float(after[t - 1]) for t in (1, 10, 50, 100, 300, 500, 1000, 1500, 2000) if t <= full}}
+
+
 def cpu_sample(w, args, seed):
     """FP64 oracle on a bounded sample: a sub-volume of the same field with
     the budget scaled by its voxel share; returns seconds per iteration and
@@ -258,9 +326,13 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": sec_per_iter_full * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": w["name"], "trunc_k": 3.0, "brick": None, "l2": "CPU run"},
+           "config": {"workload": w["name"], "trunc_k": 3.0, "brick": None, "l2": "CPU run",
+                      "extrapolated": True,
+                      "provenance": "timed on a centre sub-volume of the same field (budget scaled by voxel "
+                                    "share), seconds per iteration divided by the voxel share; ms_per_step is "
+                                    "that extrapolation, not a timed full-size iteration"},
            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": desc},
+                            "sample": desc, "extrapolated": True},
            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -704,12 +776,14 @@ def run_render(args):
     ms = e0.elapsed_time(e1)
     value = args.steps / (ms / 1e3)
     ms_frame = ms / args.steps
-    alu_peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    pk = measured_alu_peaks(dev)
+    alu_peak = pk["fp32_tops"]
     achieved = RENDER_OPS_PER_PAIR * kept / (ms_frame / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
                 "traffic": None, "kernel": "k_render<%s>" % ("true" if args.shade else "false"),
                 "kept_pairs": int(kept), "tested_pairs": int(tested), "ops_per_pair": RENDER_OPS_PER_PAIR,
-                "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (derived, FMA counted once)"}
+                "peak_note": "of measured: FP32 lane-operations/s of the gve_peak_bench FMA microbenchmarks "
+                             "(FMA counted once), this run", "peaks": pk}
     # end to end: camera in from the host, frame out to pinned host memory
     host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
@@ -786,6 +860,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     alloc_ms = e0.elapsed_time(e1)
     prims0 = prims.clone()
+    peaks = measured_alu_peaks(dev)
     opts = gve.EvalOptions()
     tune = None
     if args.autotune:
@@ -817,18 +892,31 @@ def run_ours(args):
     kept1, cand1 = gve.gve_count_pairs(prims, shape, opts)
     value = whole_job_rate(ws, args.steps, ms)
 
-    # dominant kernel: the fused brick evaluator (forward + backward)
+    # dominant kernel: the fused brick evaluator (forward + backward); its
+    # forward phase alone is the final evaluation of the timed call (a
+    # forward-only launch of the same kernel), the backward is the rest
     brick_ms = st["ms_brick"] / max(args.steps, 1)
+    fwd_ms = st["ms_fwd"]
+    bwd_ms = brick_ms - fwd_ms
     kept = 0.5 * (kept0 + kept1)
     cand = 0.5 * (cand0 + cand1)
     achieved = OPS_PER_PAIR * kept / (brick_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    peak = peaks["fp32_tops"]
+    fwd_t = FWD_OPS_PER_PAIR * kept1 / (fwd_ms / 1e3) / 1e12 if fwd_ms > 0 else None
+    bwd_t = BWD_OPS_PER_PAIR * kept / (bwd_ms / 1e3) / 1e12 if bwd_ms > 0 and fwd_ms > 0 else None
+    ex2_t = EX2_PER_PAIR * kept / (brick_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
                 "frac": achieved / peak, "traffic": brick_traffic(int(np.prod(shape))),
                 "kernel": "k_brick<loss> (fused forward+backward)", "brick_ms": brick_ms,
+                "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+                "fwd_frac": fwd_t / peak if fwd_t else None, "bwd_frac": bwd_t / peak if bwd_t else None,
+                "sfu_achieved": ex2_t, "sfu_peak": peaks["ex2_tops"], "sfu_frac": ex2_t / peaks["ex2_tops"],
                 "kept_pairs": kept, "candidate_pairs": cand,
                 "pairs_per_s": kept / (brick_ms / 1e3),
-                "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (FMA counted once)"}
+                "ops_per_pair": {"forward": FWD_OPS_PER_PAIR, "backward": BWD_OPS_PER_PAIR, "ex2": EX2_PER_PAIR},
+                "peak_note": "of measured: FP32 lane-operations/s of this run's FMA microbenchmarks "
+                             "(gve_peak_bench, the larger of scalar and packed f32x2; FMA counted once); "
+                             "SFU peak = measured ex2.approx rate", "peaks": peaks}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -846,6 +934,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             e0.record(stream)
             Vd.copy_(Vh, non_blocking=True)
+            gve.gve_normalize(Vd, out=Vd)                  # stage P (Sec. III-B)
             gve.gve_allocate(Vd, w["budget"], seed=args.seed, out=pd)
             st_e.zero_()
             s2 = gve.gve_refine(pd, Vd, iters=args.e2e_iters, lr=w["lr"], adam_state=st_e, opts=opts)
@@ -858,7 +947,12 @@ def run_ours(args):
         e2e = {"value": args.e2e_iters / sec, "unit": "iters/s",
                "h2d_bytes_per_step": int(V.numel() * 4), "d2h_bytes_per_step": int(prims0.numel() * 4 + 8),
                "encode_s": sec, "iters": args.e2e_iters, "psnr_db": psnr_e2e,
-               "includes": "H2D field, allocation, refinement, D2H parameters and PSNR"}
+               "includes": "H2D field, normalisation (stage P), allocation, refinement, D2H parameters and PSNR"}
+
+    ttp = None
+    if args.ttp_iters > 0 and rank == 0:
+        ttp = time_to_psnr(V, w, opts, args.seed, alloc_ms, full=args.ttp_iters,
+                           reduced=min(300, args.ttp_iters))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -873,7 +967,7 @@ def run_ours(args):
                           "trunc_k": 3.0, "brick": opts.brick, "gaussians_per_block": opts.gaussians_per_block or 64,
                           "lr": w["lr"], "parallelism": "replicas" if ws > 1 else "1 GPU",
                           "l2": "inputs larger than L2 (4.3 GB field) at the headline size; no flush"},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "time_to_psnr": ttp,
                "gpu_launches": int(st["launches"]),
                "alloc_ms": alloc_ms, "alloc": info,
                "autotune_ms": ({f"{k[0]}x{k[1]}": v for k, v in tune.items()} if tune else None), "psnr_after_warmup": init_psnr,

@@ -121,7 +121,10 @@ typedef struct {
     float ms_brick;        /* device time of the brick evaluator, summed over
                               the iterations (events on the call's stream)     */
     float ms_bin;          /* device time of preparation and binning, summed  */
-    float reserved;
+    float ms_fwd;          /* device time of the brick evaluator's forward
+                              phase alone: the final evaluation after the last
+                              update (a forward-only launch of the same
+                              kernel); 0 when that evaluation was replayed    */
 } gve_stats;
 
 /* Summary of an allocation. */
@@ -477,6 +480,37 @@ GVE_API gve_status gve_count_pairs(gve_ctx* ctx, const float* prims_dev, int64_t
                            const gve_eval_opts* opts, int64_t* kept_pairs,
                            int64_t* candidate_pairs, void* stream);
 
+/* Kept (voxel, Gaussian) pairs of one evaluation, listed (for checking the
+ * keep decision pair by pair): pairs_dev [cap] uint64 output, each entry
+ * (voxel index << 24) | Gaussian index, voxel index = (z ny + y) nx + x, in
+ * no particular order.  n_pairs (host) receives the number of kept pairs;
+ * when it exceeds cap only cap entries are written and GVE_E_CAPACITY is
+ * returned.  Grids of at most 2^40 voxels.  Synchronises `stream`. */
+GVE_API gve_status gve_kept_pairs(gve_ctx* ctx, const float* prims_dev, int64_t n, gve_dims dims,
+                                  const gve_eval_opts* opts, uint64_t* pairs_dev, int64_t cap, int64_t* n_pairs,
+                                  void* stream);
+
+/* Stage P of the encoder (Sec. III-B): out = (V - min) / (max - min) over the
+ * whole field, in float32 with one correctly rounded subtraction and one
+ * correctly rounded division per voxel (a constant field maps to 0).
+ *   field_dev  [nz][ny][nx] float32 input.
+ *   out_dev    [nz][ny][nx] float32 output; may equal field_dev (in place).
+ *   minmax     host, optional [2]: the field's float32 minimum and maximum
+ *              (the header of an encoding keeps them to undo the scaling).
+ * Returns GVE_E_INVALID without writing out_dev when a value is not finite.
+ * Synchronises `stream` (the extremes are read before the scaling pass). */
+GVE_API gve_status gve_normalize(gve_ctx* ctx, const float* field_dev, gve_dims dims, float* out_dev, float* minmax,
+                                 void* stream);
+
+/* Throughput microbenchmark of the pipes the evaluator runs on (no paper
+ * counterpart; it measures the roofline's denominators on the running GPU):
+ * kind 0 = scalar float32 FMA, 1 = packed float32x2 FMA (counted as two
+ * operations), 2 = SFU ex2.approx.  One launch of 8 CTAs x 256 threads per
+ * SM, each thread running 8 independent chains for iters x 16 steps; timed
+ * with CUDA events on `stream`.  ops_per_s (host) receives lane-operations
+ * per second, ms_out (host, optional) the kernel time.  Synchronises. */
+GVE_API gve_status gve_peak_bench(int32_t kind, int64_t iters, double* ops_per_s, float* ms_out, void* stream);
+
 /* Field evaluation that allocates no memory -- an addition for callers that
  * cannot call cudaMalloc (a memory pool or arena that owns the device, a
  * fixed device footprint after start-up, no allocator locks on the call
@@ -487,15 +521,18 @@ GVE_API gve_status gve_count_pairs(gve_ctx* ctx, const float* prims_dev, int64_t
  *   prims_dev      [n][12] float32, n <= GVE_NOALLOC_MAX_PRIMS.
  *   dims           at most GVE_NOALLOC_MAX_BRICKS bricks of 8^3, axes up to
  *                  2^14 voxels.
- *   opts           brick must be 8.
+ *   opts           brick must be 8; gaussians_per_block 0, 32 or 64.
  *   field_out_dev  [nz][ny][nx] float32 output.
+ * prims_dev and field_out_dev must be memory of the current device (the
+ * array and the launches are the current device's); GVE_E_INVALID otherwise.
  * Returns GVE_E_INVALID for sizes beyond the limits (before any launch), and
  * GVE_E_CAPACITY when the (brick, Gaussian) pair count, found on the device,
  * exceeds GVE_NOALLOC_MAX_PAIRS (the output is then not written).  The call
  * synchronises `stream` to read that count.  The first call on a device
  * resolves the array's address with that device current; make it before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller. */
+ * stream capture (a cudaDeviceReset invalidates the resolved address).  All
+ * calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. */
 #define GVE_NOALLOC_MAX_PRIMS 8192
 #define GVE_NOALLOC_MAX_BRICKS 32768
 #define GVE_NOALLOC_MAX_PAIRS 524288

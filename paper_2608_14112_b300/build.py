@@ -23,7 +23,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           f"-I{INCLUDE}"]
 PER_FILE = {"alloc.cu": ["--fmad=false"]}
 SOURCES = ["bin.cu", "field.cu", "optim.cu", "alloc.cu", "api.cu", "batch.cu", "proposal.cu", "sample.cu", "render.cu",
-           "noalloc.cu"]
+           "normalize.cu", "peaks.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

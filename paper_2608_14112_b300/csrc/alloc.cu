@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(128) k_assemble(const AssembleArgs a)
 int grid_for(long long M)
 {
     long long b = (M + 255) / 256;
-    if (b > 148LL * 32) b = 148LL * 32;
+    if (b > 32LL * num_sms()) b = 32LL * num_sms();
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -986,7 +986,8 @@ void launch_reg(const float* prims, long long n, const float* V, gve_dims d, con
 {
     if (n <= 0) return;
     const long long b = (n + 255) / 256;
-    const unsigned grid = (unsigned)(b < 148 * 16 ? b : 148 * 16);
+    const long long cap = 16LL * num_sms();
+    const unsigned grid = (unsigned)(b < cap ? b : cap);
     k_reg<<<grid, 256, 0, s>>>(prims, n, V, d.nx, d.ny, d.nz, r, 1.0 / (double)n, extra, terms, total_a, total_b);
 }
 
@@ -1478,7 +1479,7 @@ int stat_blocks(Kern k, long long nrows, int threads = 256)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    long long b = 148LL * per_sm;
+    long long b = (long long)num_sms() * per_sm;
     const int warps = threads / 32;
     const long long need = (nrows + warps - 1) / warps;
     if (b > need) b = need;
@@ -1491,7 +1492,7 @@ int sweep2_blocks(long long M)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stat_sweep2, 256, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    long long b = 148LL * per_sm;
+    long long b = (long long)num_sms() * per_sm;
     const long long need = ((M >> 2) + 256LL * kSweep2Vec - 1) / (256LL * kSweep2Vec);
     if (b > need) b = need;
     return (int)(b < 1 ? 1 : b);

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libgve (see include/gve.h): argument checks, context
 // scratch, and the launch sequences of evaluation, gradient and refinement.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -9,6 +10,25 @@
 #include "gve_int.cuh"
 
 namespace gve {
+
+int num_sms()
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 1;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what)
 {
@@ -70,6 +90,7 @@ __global__ void k_reset_state(DevState* st)
     st->sse[1] = 0.0;
     st->kept = 0;
     st->cand = 0;
+    st->listed = 0;
 }
 
 }  // namespace gve
@@ -402,7 +423,7 @@ gve_status gve_bin(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const 
         if (!keys || !gids) return fail(c, GVE_E_INVALID, "null pair outputs");
         GVE_CUDA(cudaMemcpyAsync(keys, c->keys[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
         GVE_CUDA(cudaMemcpyAsync(gids, c->vals[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
-        k_strip_mask<<<592, 256, 0, k.s>>>(gids, masks, h.total);
+        k_strip_mask<<<4 * num_sms(), 256, 0, k.s>>>(gids, masks, h.total);
     }
     GVE_CUDA(cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint32_t) * 2 * k.g.nbricks, cudaMemcpyDeviceToDevice, k.s), "copy");
     GVE_CUDA(cudaStreamSynchronize(k.s), "sync");
@@ -425,6 +446,28 @@ gve_status gve_count_pairs(gve_ctx* c, const float* prims, int64_t n, gve_dims d
     GVE_TRY(read_state(k, &h));
     *kept = (int64_t)h.kept;
     *cand = (int64_t)h.cand;
+    return GVE_OK;
+}
+
+gve_status gve_kept_pairs(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o,
+                          uint64_t* pairs, int64_t cap, int64_t* n_pairs, void* stream)
+{
+    GVE_TRY(check_common(c, prims, n, d, o));
+    if (!n_pairs || cap < 0 || (cap > 0 && !pairs)) return fail(c, GVE_E_INVALID, "null output");
+    if ((int64_t)d.nx * d.ny * d.nz > ((int64_t)1 << 40)) return fail(c, GVE_E_INVALID, "grid above 2^40 voxels");
+    Call k;
+    GVE_TRY(begin(c, k, n, d, o, stream));
+    GVE_TRY(size_pairs(k, prims, o));
+    GVE_TRY(bin_all(k, prims, o, 0));
+    BrickArgs a = brick_args(k, o);
+    a.pairs = reinterpret_cast<unsigned long long*>(pairs);
+    a.pairs_cap = (unsigned long long)cap;
+    launch_brick(kModeCount, a, k.s);
+    GVE_CUDA(cudaGetLastError(), "launch (kept pairs)");
+    DevState h;
+    GVE_TRY(read_state(k, &h));
+    *n_pairs = (int64_t)h.listed;
+    if (h.listed > (unsigned long long)cap) return fail(c, GVE_E_CAPACITY, "more kept pairs than the output holds");
     return GVE_OK;
 }
 
@@ -517,7 +560,8 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
         }
         it = end;
     }
-    // final evaluation after the last update
+    // final evaluation after the last update: the brick evaluator's forward
+    // phase alone (no gradient sums), timed on its own
     GVE_TRY(bin_all(k, prims, o, sc->iters));
     DevState h;
     {
@@ -525,15 +569,19 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
         a.field = field;
         a.mask_thresh = sc->mask_thresh;
         a.acc = nullptr;
+        if (timed) GVE_CUDA(cudaEventRecord(c->sev[0][0], k.s), "event");
         launch_brick(kModeLoss, a, k.s);
+        if (timed) GVE_CUDA(cudaEventRecord(c->sev[1][0], k.s), "event");
         launch_sse_reduce(a.part, k.g.nbricks, dstate(c), nullptr, 0, inv_m, k.s);
         c->launches += 3;
     }
     GVE_CUDA(cudaEventRecord(c->ev1, k.s), "event");
     GVE_CUDA(cudaGetLastError(), "launch (refine final)");
     GVE_TRY(read_state(k, &h));
+    bool fwd_timed = timed;
     if (h.overflow) {
-        // the final evaluation alone overflowed: grow and redo it
+        // the final evaluation alone overflowed: grow and redo it (untimed)
+        fwd_timed = false;
         GVE_TRY(grow_pairs(k, h.max_total));
         reset_state(k);
         GVE_TRY(bin_all(k, prims, o, sc->iters));
@@ -565,6 +613,9 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
         stats->ms_total = ms;
         stats->ms_brick = (float)ms_brick;
         stats->ms_bin = (float)ms_bin;
+        float msf = 0.f;
+        if (fwd_timed) cudaEventElapsedTime(&msf, c->sev[0][0], c->sev[1][0]);
+        stats->ms_fwd = msf;
         stats->launches = c->launches;
     }
     return GVE_OK;

@@ -525,7 +525,7 @@ static int emit_blocks(long long n)
 {
     long long warps = n;
     long long blocks = (warps * 32 + 255) / 256;
-    if (blocks > 148 * 64) blocks = 148 * 64;
+    if (blocks > 64LL * num_sms()) blocks = 64LL * num_sms();
     if (blocks < 1) blocks = 1;
     return (int)blocks;
 }
@@ -705,7 +705,8 @@ int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsign
     static_assert(kSortThreads == 256, "one thread per digit in the scatter");
     int passes = (key_bits + 7) / 8;
     unsigned long long max_tiles = (cap + kSortTile - 1) / kSortTile;
-    int grid = (int)(max_tiles < 148ull * 8 ? max_tiles : 148ull * 8);
+    const unsigned long long gcap = 8ull * num_sms();
+    int grid = (int)(max_tiles < gcap ? max_tiles : gcap);
     if (grid < 1) grid = 1;
     int cur = 0;
     auto* part = reinterpret_cast<uint32_t*>(scanp);
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ sk,
 void launch_ranges(const uint32_t* skeys, const DevState* st, unsigned long long cap, uint32_t* start,
                    uint32_t* end, cudaStream_t s)
 {
-    k_ranges<<<148 * 16, 256, 0, s>>>(skeys, st, cap, start, end);
+    k_ranges<<<16 * num_sms(), 256, 0, s>>>(skeys, st, cap, start, end);
 }
 
 }  // namespace gve

@@ -163,6 +163,20 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
                         kept += (unsigned)((t.x > T) && (2 * q < nxin)) + (unsigned)((t.y > T) && (2 * q + 1 < nxin));
                         if (two)
                             kept += (unsigned)((tv.x > T) && (2 * q < nxin)) + (unsigned)((tv.y > T) && (2 * q + 1 < nxin));
+                        if (a.pairs) {  // the kept pairs themselves: (voxel << 24) | Gaussian
+                            const unsigned long long v0 = ((unsigned long long)gz * g.ny + gy) * g.nx + gx0 + 2 * q;
+                            const unsigned long long i1 = a.gids[s0 + c0 + j1] & kGidMask;
+                            const unsigned long long i2 = a.gids[s0 + c0 + j2] & kGidMask;
+                            const bool kk[4] = {t.x > T && 2 * q < nxin, t.y > T && 2 * q + 1 < nxin,
+                                                two && tv.x > T && 2 * q < nxin, two && tv.y > T && 2 * q + 1 < nxin};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                if (!kk[e]) continue;
+                                const unsigned long long pos = atomicAdd(&a.st->listed, 1ull);
+                                if (pos < a.pairs_cap)
+                                    a.pairs[pos] = ((v0 + (e & 1)) << kGidBits) | (e < 2 ? i1 : i2);
+                            }
+                        }
                     }
                     num[q] = __ffma2_rn(al, G, num[q]);
                     den[q] = __ffma2_rn(be, G, den[q]);

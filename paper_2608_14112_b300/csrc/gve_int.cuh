@@ -5,7 +5,8 @@
 //       r0 = (mu_x, mu_y, mu_z, qxx)      r1 = (qyy, qzz, qxy2, qxz2)
 //       r2 = (qyz2, alpha = w a, beta = w, a)
 //     q.. = float32(-0.5 log2(e) Sigma^-1) entries (off-diagonals doubled),
-//     rounded once from an FP64 computation in a fixed order.
+//     from one fixed sequence of correctly rounded float32 operations
+//     (keep_coefficients below).
 //   bin record      20 words per Gaussian: whitening L (row-major 3x3),
 //                   brick half-extent bound e[3], threshold K2, brick box
 //                   lo[3] / hi[3], non-empty flag.
@@ -26,8 +27,6 @@
 
 namespace gve {
 
-constexpr int kBrickThreads = 256;
-constexpr int kChunk = 128;          // Gaussian records staged per shared-memory chunk
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -59,6 +58,7 @@ struct DevState {
     double sse[2];                   // {masked, unmasked} SSE of the last reduction
     unsigned long long kept;         // kept (voxel, Gaussian) pairs (counting mode)
     unsigned long long cand;         // candidate pairs visited (counting mode)
+    unsigned long long listed;       // kept pairs offered to the pair list (counting mode)
 };
 
 struct Buf {
@@ -324,6 +324,8 @@ struct BrickArgs {
     float mask_thresh;         // < 0: no mask
     float inv_m;               // 1 / (nx ny nz)
     int chunk;                 // Gaussians staged per chunk: 32 or 64 (0 = 64)
+    unsigned long long* pairs;         // counting mode: kept pairs (voxel << 24 | gid), or nullptr
+    unsigned long long pairs_cap;      // entries pairs can hold
 };
 void launch_brick(int mode, const BrickArgs& a, cudaStream_t s);
 // deterministic reduction of per-brick partials; writes st->sse and, if
@@ -384,6 +386,9 @@ gve_status structure_stats(gve_ctx* c, const float* V, gve_dims d, double out[5]
                            cudaStream_t s);
 
 // ---- context scratch and the evaluation pipeline (api.cu) ----------------
+// streaming multiprocessors of the current device (queried once per device;
+// grids of persistent and grid-stride kernels are sized from it)
+int num_sms();
 gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
 gve_status cuda_fail(gve_ctx* c, cudaError_t e, const char* what);
 gve_status fail(gve_ctx* c, gve_status s, const char* msg);

@@ -19,13 +19,21 @@
 //
 // Set-up: the first call on a device (with that device current) resolves the
 // array's device address with cudaGetSymbolAddress; that first call should
-// come before any stream capture.  Later calls reuse the address.
+// come before any stream capture.  Later calls reuse the address (a device
+// reset with cudaDeviceReset unloads the module and invalidates it, so the
+// library must not be used across such a reset).
+//
+// Device: the inputs and the output must live on the current device (checked
+// with cudaPointerGetAttributes; GVE_E_INVALID otherwise), because the array
+// used is the current device's copy and the launches go to the current
+// device.
 //
 // Sharing: every call uses the same array and finds the previous call's
 // contents there; the parts that must start at zero (the device state and the
 // per-brick ranges) are cleared by each call.  Calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on the array
 // and must be serialised by the caller.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -61,25 +69,36 @@ constexpr size_t kScratchBytes = align256(kOffRanges + sizeof(uint32_t) * 2 * kN
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+// per-device address of the array; two threads resolving it at once store
+// the same value
+std::atomic<unsigned char*> g_scratch_ptr[kMaxDevices];
 
-gve_status scratch_for_current_device(unsigned char** out)
+gve_status scratch_for_device(int dev, unsigned char** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return GVE_E_CUDA;
-    }
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    if (dev < 0 || dev >= kMaxDevices) return GVE_E_CUDA;
+    unsigned char* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_noalloc_scratch) != cudaSuccess || !q) {
             cudaGetLastError();
             return GVE_E_CUDA;
         }
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        p = static_cast<unsigned char*>(q);
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return GVE_OK;
+}
+
+// 1 when ptr is device (or managed) memory of device dev
+bool on_device(const void* ptr, int dev)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -97,12 +116,20 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
     if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return GVE_E_INVALID;
     if (d.nx > (1 << 14) || d.ny > (1 << 14) || d.nz > (1 << 14)) return GVE_E_INVALID;
     if (o->brick != 8 || !(o->trunc_k > 0.f) || !std::isfinite(o->trunc_k)) return GVE_E_INVALID;
+    if (o->gaussians_per_block != 0 && o->gaussians_per_block != 32 && o->gaussians_per_block != 64)
+        return GVE_E_INVALID;
     if (o->normalized && !(o->rho0 > 0.f)) return GVE_E_INVALID;
     const BinGeom g = make_geom(d, 8);
     if (g.nbricks > kNaBricks) return GVE_E_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GVE_E_CUDA;
+    }
+    if (!on_device(field_out, dev) || (n > 0 && !on_device(prims, dev))) return GVE_E_INVALID;
 
     unsigned char* base = nullptr;
-    gve_status st = scratch_for_current_device(&base);
+    gve_status st = scratch_for_device(dev, &base);
     if (st != GVE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     DevState* dst = reinterpret_cast<DevState*>(base + kOffState);
@@ -139,6 +166,7 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
     a.normalized = o->normalized;
     a.mask_thresh = -1.f;
     a.inv_m = (float)(1.0 / ((double)d.nx * d.ny * d.nz));
+    a.chunk = o->gaussians_per_block;
     a.field_out = field_out;
     launch_brick(kModeEval, a, s);
     if (cudaGetLastError() != cudaSuccess) return GVE_E_CUDA;

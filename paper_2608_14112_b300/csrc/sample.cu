@@ -792,6 +792,7 @@ extern "C" gve_status gve_refine_sampled(gve_ctx* c, float* prims, int64_t n, co
         stats->ms_total = ms_loop;
         stats->ms_brick = (float)ms_search;
         stats->ms_bin = (float)ms_prep;
+        stats->ms_fwd = 0.f;
         stats->launches = launches + c->launches;
     }
     return GVE_OK;

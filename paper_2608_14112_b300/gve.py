@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("sse_final", ctypes.c_double),
                 ("psnr_final", ctypes.c_double), ("brick_pairs", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("iters_done", ctypes.c_int32), ("retries", ctypes.c_int32), ("ms_total", ctypes.c_float),
-                ("ms_brick", ctypes.c_float), ("ms_bin", ctypes.c_float), ("reserved", ctypes.c_float)]
+                ("ms_brick", ctypes.c_float), ("ms_bin", ctypes.c_float), ("ms_fwd", ctypes.c_float)]
 
 
 class Volume(ctypes.Structure):
@@ -127,11 +127,15 @@ def lib():
             L.gve_count_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), P]
             L.gve_evaluate_noalloc.argtypes = [P, i64, Dims, ctypes.POINTER(EvalOpts), P, P]
+            L.gve_kept_pairs.argtypes = [P, P, i64, Dims, ctypes.POINTER(EvalOpts), P, i64, ctypes.POINTER(i64), P]
+            L.gve_normalize.argtypes = [P, P, Dims, P, P, P]
+            L.gve_peak_bench.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), P]
             L.gve_refine_batch.argtypes = [P, i32, ctypes.POINTER(Volume), P, ctypes.POINTER(Schedule), P, P, P,
                                            ctypes.POINTER(Stats), P]
             L.gve_autotune.argtypes = [P, i32, ctypes.POINTER(Volume), P, ctypes.POINTER(EvalOpts), P, P]
             for f in ("gve_allocate", "gve_evaluate", "gve_loss_grad", "gve_backward", "gve_refine", "gve_bin",
-                      "gve_count_pairs", "gve_evaluate_noalloc", "gve_refine_batch", "gve_autotune"):
+                      "gve_count_pairs", "gve_evaluate_noalloc", "gve_refine_batch", "gve_autotune", "gve_kept_pairs",
+                      "gve_normalize", "gve_peak_bench"):
                 getattr(L, f).restype = st
             _lib = L
     return _lib
@@ -581,6 +585,55 @@ def gve_count_pairs(prims: torch.Tensor, shape, opts: EvalOptions | None = None)
     return int(kept.value), int(cand.value)
 
 
+def gve_kept_pairs(prims: torch.Tensor, shape, opts: EvalOptions | None = None, cap: int | None = None):
+    """The kept (voxel, Gaussian) pairs of one evaluation as an int64 CPU
+    tensor (K, 2) of (voxel index, Gaussian index), sorted."""
+    prims = _prims(prims)
+    o = (opts or EvalOptions()).c()
+    c = context(prims.device.index)
+    npairs = ctypes.c_int64(0)
+    if cap is None:
+        cap = gve_count_pairs(prims, shape, opts)[0]
+    buf = torch.empty(max(int(cap), 1), dtype=torch.int64, device=prims.device)
+    _check(lib().gve_kept_pairs(c, _ptr(prims), prims.shape[0], _dims(shape), ctypes.byref(o), _ptr(buf), int(cap),
+                                ctypes.byref(npairs), _stream(prims.device)), c)
+    v = buf[:npairs.value].cpu()
+    v, _ = torch.sort(v)
+    return torch.stack([v >> 24, v & ((1 << 24) - 1)], 1)
+
+
+def gve_normalize(field: torch.Tensor, out: torch.Tensor | None = None):
+    """Stage P (Sec. III-B): (V - min) / (max - min) on the device.  Returns
+    (normalised field, (min, max)); ``out`` may be ``field`` (in place)."""
+    field = _field(field)
+    if out is None:
+        out = torch.empty_like(field)
+    _field(out)
+    if out.shape != field.shape or out.device != field.device:
+        raise ValueError("output must match the field's shape and device")
+    mm = (ctypes.c_float * 2)()
+    c = context(field.device.index)
+    _check(lib().gve_normalize(c, _ptr(field), _dims(field.shape), _ptr(out), ctypes.cast(mm, ctypes.c_void_p),
+                               _stream(field.device)), c)
+    return out, (float(mm[0]), float(mm[1]))
+
+
+PEAK_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2}
+
+
+def gve_peak_bench(kind: str, iters: int, device=None):
+    """(lane-operations per second, kernel ms) of one throughput
+    microbenchmark: 'ffma', 'ffma2' (two operations per packed FMA) or 'ex2'."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else int(device))
+    ops = ctypes.c_double(0.0)
+    ms = ctypes.c_float(0.0)
+    with torch.cuda.device(dev):
+        s = lib().gve_peak_bench(PEAK_KINDS[kind], int(iters), ctypes.byref(ops), ctypes.byref(ms), _stream(dev))
+    if s != GVE_OK:
+        raise GveError(s, lib().gve_status_str(s).decode())
+    return ops.value, ms.value
+
+
 def gve_evaluate_noalloc(prims: torch.Tensor, shape, opts: EvalOptions | None = None,
                          out: torch.Tensor | None = None):
     """Eq. 3 at every voxel centre through the entry point that allocates no
@@ -591,8 +644,11 @@ def gve_evaluate_noalloc(prims: torch.Tensor, shape, opts: EvalOptions | None = 
     if out is None:
         out = torch.empty(tuple(int(s) for s in shape), dtype=torch.float32, device=prims.device)
     _field(out)
-    s = lib().gve_evaluate_noalloc(_ptr(prims), prims.shape[0], _dims(out.shape), ctypes.byref(o), _ptr(out),
-                                   _stream(prims.device))
+    if out.device != prims.device:
+        raise ValueError("primitives and output must be on the same device")
+    with torch.cuda.device(prims.device):
+        s = lib().gve_evaluate_noalloc(_ptr(prims), prims.shape[0], _dims(out.shape), ctypes.byref(o), _ptr(out),
+                                       _stream(prims.device))
     if s != GVE_OK:
         raise GveError(s, lib().gve_status_str(s).decode())
     return out

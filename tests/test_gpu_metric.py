@@ -43,3 +43,23 @@ def test_sampled_psnr_within_its_standard_error(refined, seed):
     psnr_s = 10 * np.log10(1 / mse)
     assert se_db < 0.02
     assert abs(psnr_s - st["psnr_final"]) <= 4 * se_db
+
+
+def test_peak_microbenchmarks_run_and_stay_physical():
+    """The roofline denominators: FFMA cannot beat one FMA per lane per clock
+    (128 lanes per SM at the maximum SM clock), and the SFU ex2 rate is below
+    the FFMA rate."""
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    import subprocess
+    try:
+        mhz = float(subprocess.check_output(["nvidia-smi", "--id=0", "--query-gpu=clocks.max.sm",
+                                             "--format=csv,noheader,nounits"]).decode().split()[0])
+    except Exception:
+        mhz = 2100.0
+    ffma, ms = gve.gve_peak_bench("ffma", 2000)
+    assert ms > 0 and 0 < ffma <= 1.02 * sms * 128 * mhz * 1e6
+    ffma2, _ = gve.gve_peak_bench("ffma2", 2000)
+    assert ffma2 > 0.5 * ffma
+    ex2, _ = gve.gve_peak_bench("ex2", 500)
+    assert 0 < ex2 < ffma

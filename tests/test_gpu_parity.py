@@ -46,7 +46,7 @@ def dev(a):
 CASES = {
     # name: (dims (nx,ny,nz), n, s_lo, s_hi, seed)
     "ragged": ((37, 29, 21), 300, 0.8, 3.0, 1),
-    "long_lists": ((16, 16, 16), 420, 4.0, 6.0, 2),      # > 128 Gaussians per brick: several chunks
+    "long_lists": ((16, 16, 16), 420, 4.0, 6.0, 2),      # > 64 Gaussians per brick: several staged chunks
     "thin": ((45, 33, 1), 120, 0.6, 2.5, 3),
     "small_gauss": ((24, 24, 24), 500, 0.2, 0.6, 4),
 }
@@ -267,3 +267,40 @@ def test_brick_variants_bin_eval_grad(case, brick, chunk):
     gg2, gsse = gve.gve_loss_grad(dev(p), dev(field), opts)
     assert abs(gsse[1].item() - sse) <= 1e-5 * sse
     assert rel_l2(gg2.cpu().numpy(), g) <= GRAD_TOL
+
+
+# sparse grids with more than 2^16 bricks: 17-18 key bits, so three radix
+# passes run, over many sort tiles (> 4,096 pairs each)
+SCALE_CASES = {
+    # name: (dims (nx, ny, nz), brick, n, s_lo, s_hi, seed)
+    "b4_18bit": ((1040, 520, 16), 4, 6000, 0.6, 2.5, 31),
+    "b8_17bit": ((1024, 1024, 40), 8, 12000, 0.8, 3.0, 32),
+}
+
+
+@pytest.mark.parametrize("case", list(SCALE_CASES))
+def test_binning_bit_exact_three_radix_passes(case):
+    dims, brick, n, lo, hi, seed = SCALE_CASES[case]
+    nb = np.prod([(d + brick - 1) // brick for d in dims])
+    assert nb > 2 ** 16
+    p = rand_prims(np.random.default_rng(seed), n, dims, lo, hi)
+    counts, sk, sg, start, end = O.bin_sorted(p, dims, 3.0, brick)
+    assert sk.size > 8 * 4096
+    gc, gk, gg, gs, ge = gve.gve_bin(dev(p), (dims[2], dims[1], dims[0]), gve.EvalOptions(brick=brick))
+    np.testing.assert_array_equal(gc.numpy(), counts.astype(np.int64))
+    np.testing.assert_array_equal(gk.numpy(), sk.astype(np.int64))
+    np.testing.assert_array_equal(gg.numpy(), sg.astype(np.int64))
+    np.testing.assert_array_equal(gs.numpy(), start.astype(np.int64))
+    np.testing.assert_array_equal(ge.numpy(), end.astype(np.int64))
+
+
+@pytest.mark.parametrize("case", ["ragged", "small_gauss", "long_lists"])
+def test_kept_pair_sets_equal(case):
+    """The kept (voxel, Gaussian) pairs themselves, not only their number:
+    the set the evaluator keeps equals the oracle's float32 keep rule."""
+    dims, n, lo, hi, seed = CASES[case]
+    p = rand_prims(np.random.default_rng(seed), n, dims, lo, hi)
+    ref = O.list_kept(p, dims, 3.0)
+    got = gve.gve_kept_pairs(dev(p), (dims[2], dims[1], dims[0])).numpy()
+    assert got.shape == ref.shape
+    np.testing.assert_array_equal(got, ref)

@@ -196,23 +196,22 @@ float or_exp_fixed(float x) { return exp_fixed(x); }
  * -log2(e)/2 Sigma^-1 = -log2(e)/2 R diag(s^-2) R^T in float32, one fixed
  * sequence of correctly rounded operations (the written order, no
  * contraction), the scales by exp_fixed. */
-static void pred_coeffs(const float* p32, pred_t* P)
+/* The float32 scales s = exp_fixed(log s) and rotation R of the normalised
+ * quaternion (Eq. 2), in the written order; 0 for an invalid record
+ * (non-finite values, zero quaternion, scales outside float range). */
+static int keep_frame(const float* p32, float s[3], float R[3][3])
 {
     int ok = 1;
     for (int i = 0; i < 12; ++i) ok = ok && isfinite(p32[i]);
-    for (int j = 0; j < 3; ++j) P->mu[j] = p32[j];
-    P->valid = 0;
-    if (!ok) return;
-    float s[3];
+    if (!ok) return 0;
     for (int j = 0; j < 3; ++j) s[j] = exp_fixed(p32[3 + j]);
     const float qw = p32[6], qx = p32[7], qy = p32[8], qz = p32[9];
     const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
     const float nq = sqrtf(n2);
-    if (!(nq > 0.0f) || !isfinite(nq)) return;
+    if (!(nq > 0.0f) || !isfinite(nq)) return 0;
     for (int j = 0; j < 3; ++j)
-        if (!(s[j] > 0.0f) || !isfinite(s[j])) return;
+        if (!(s[j] > 0.0f) || !isfinite(s[j])) return 0;
     const float w = qw / nq, x = qx / nq, y = qy / nq, z = qz / nq;
-    float R[3][3];
     R[0][0] = 1.0f - 2.0f * (y * y + z * z);
     R[0][1] = 2.0f * (x * y - w * z);
     R[0][2] = 2.0f * (x * z + w * y);
@@ -222,6 +221,15 @@ static void pred_coeffs(const float* p32, pred_t* P)
     R[2][0] = 2.0f * (x * z - w * y);
     R[2][1] = 2.0f * (y * z + w * x);
     R[2][2] = 1.0f - 2.0f * (x * x + y * y);
+    return 1;
+}
+
+static void pred_coeffs(const float* p32, pred_t* P)
+{
+    for (int j = 0; j < 3; ++j) P->mu[j] = p32[j];
+    P->valid = 0;
+    float s[3], R[3][3];
+    if (!keep_frame(p32, s, R)) return;
     float inv[3];
     for (int j = 0; j < 3; ++j) inv[j] = 1.0f / (s[j] * s[j]);
     const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
@@ -751,9 +759,14 @@ double or_refine(double* prm, int64_t n, const float* field, const int dims[3], 
 
 /* ------------------------------------------------------------------------ */
 /* Brick binning: which bricks of B^3 voxels may hold a kept pair of         */
-/* Gaussian i.  A conservative rule, decided bit-identically on both sides:  */
-/* FP64 box of Mahalanobis radius kb = k (1.0001 + 1e-5 cond) plus 0.01      */
-/* voxel, then a float32 whitened-distance lower bound per brick.            */
+/* Gaussian i.  A conservative rule, decided bit-identically on both sides,  */
+/* in float32 from the keep test's own scales and rotation (keep_frame):     */
+/* a box of Mahalanobis radius kb = k (1.0001 + 1e-5 cond) plus 0.01 voxel,  */
+/* then a whitened-distance lower bound per brick.  The relative margins    */
+/* (1e-4 + 1e-5 cond) exceed the float32 rounding of the box, of the        */
+/* rotation's departure from orthonormality and of the keep chain (a few    */
+/* ulps times cond); the 0.01 voxel exceeds the rounding of mu -/+ r and of */
+/* brick-centre offsets below 2^14.                                          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int blo[3], bhi[3];
@@ -766,37 +779,34 @@ typedef struct {
 static void bin_spec(const float* p32, const int dims[3], float k, int B, binspec_t* S)
 {
     memset(S, 0, sizeof(*S));
-    double p[12];
-    for (int i = 0; i < 12; ++i) p[i] = (double)p32[i];
-    act_t A;
-    activate(p, &A);
-    if (!A.valid) return;
-    double smin = A.s[0], smax = A.s[0];
-    for (int j = 1; j < 3; ++j) { if (A.s[j] < smin) smin = A.s[j]; if (A.s[j] > smax) smax = A.s[j]; }
-    double ratio = smax / smin;
-    double cond = ratio * ratio;
-    double kb = (double)k * (1.0001 + 1e-5 * cond);
+    float s[3], R[3][3];
+    if (!keep_frame(p32, s, R)) return;
+    float smin = s[0], smax = s[0];
+    for (int j = 1; j < 3; ++j) { if (s[j] < smin) smin = s[j]; if (s[j] > smax) smax = s[j]; }
+    float ratio = smax / smin;
+    float cond = ratio * ratio;
+    float kb = k * (1.0001f + 1e-5f * cond);
     if (!isfinite(kb)) return;
     for (int j = 0; j < 3; ++j) {
-        double var = ((A.R[j][0] * A.R[j][0]) * (A.s[0] * A.s[0]) + (A.R[j][1] * A.R[j][1]) * (A.s[1] * A.s[1]))
-                   + (A.R[j][2] * A.R[j][2]) * (A.s[2] * A.s[2]);
-        double r = kb * sqrt(var) + 0.01;
-        double l = ceil(A.mu[j] - r), h = floor(A.mu[j] + r);
+        float var = ((R[j][0] * R[j][0]) * (s[0] * s[0]) + (R[j][1] * R[j][1]) * (s[1] * s[1]))
+                  + (R[j][2] * R[j][2]) * (s[2] * s[2]);
+        float r = kb * sqrtf(var) + 0.01f;
+        float l = ceilf(p32[j] - r), h = floorf(p32[j] + r);
         if (!(l <= h) || !isfinite(l) || !isfinite(h)) return;
-        if (l < 0.0) l = 0.0;
-        if (h > (double)(dims[j] - 1)) h = (double)(dims[j] - 1);
+        if (l < 0.0f) l = 0.0f;
+        if (h > (float)(dims[j] - 1)) h = (float)(dims[j] - 1);
         if (l > h) return;
         S->blo[j] = (int)l / B;
         S->bhi[j] = (int)h / B;
     }
     for (int j = 0; j < 3; ++j)
-        for (int i = 0; i < 3; ++i) S->L[j][i] = (float)(A.R[i][j] / A.s[j]);
+        for (int i = 0; i < 3; ++i) S->L[j][i] = R[i][j] / s[j];
     float hB = (float)(0.5 * (double)(B - 1)) + 0.01f;
     for (int j = 0; j < 3; ++j) {
         float sabs = (fabsf(S->L[j][0]) + fabsf(S->L[j][1])) + fabsf(S->L[j][2]);
         S->e[j] = hB * sabs;
     }
-    S->K2 = (float)(kb * kb * 1.0001 + 1e-4);
+    S->K2 = (kb * kb) * 1.0001f + 1e-4f;
     S->nonempty = 1;
 }
 

@@ -1380,3 +1380,34 @@ def test_list_kept_matches_count_and_keep_rule():
     for v, i in L[:: max(1, L.shape[0] // 200)]:
         x, y, z = v % dims[0], (v // dims[0]) % dims[1], v // (dims[0] * dims[1])
         assert O.pred_t(p[i], int(x), int(y), int(z)) > T
+
+
+@pytest.mark.parametrize("B", [4, 8, 16])
+def test_binning_covers_kept_pairs_at_large_coordinates_and_anisotropy(B):
+    """The float32 cover stays conservative where float32 rounding is
+    largest: centres near x = 2^14 - 1 (the evaluation limit, where one ulp is
+    2^-10 voxel) and near the low border, anisotropy up to 12:1 in random
+    orientations.  Every kept pair's brick must be listed for its Gaussian."""
+    rng = np.random.default_rng(400 + B)
+    dims = (16384, 24, 20)
+    n = 60
+    p = np.zeros((n, 12), np.float64)
+    p[:, 0] = np.where(np.arange(n) % 2 == 0, rng.uniform(16360, 16383.5, n), rng.uniform(-1.0, 20.0, n))
+    p[:, 1] = rng.uniform(-1.0, 24.0, n)
+    p[:, 2] = rng.uniform(-1.0, 20.0, n)
+    sc = rng.uniform(0.3, 1.0, (n, 3))
+    sc[:, 0] *= rng.uniform(1.0, 12.0, n)
+    p[:, 3:6] = np.log(sc)
+    p[:, 6:10] = rng.normal(size=(n, 4))
+    p[:, 10] = 0.5
+    p32 = p.astype(np.float32)
+    kept = O.list_kept(p32, dims, 3.0)
+    assert kept.shape[0] > 1000
+    _, keys, gids = O.bin_pairs(p32, dims, 3.0, B)
+    listed = set(zip(keys.tolist(), gids.tolist()))
+    nbx, nby = (dims[0] + B - 1) // B, (dims[1] + B - 1) // B
+    v, i = kept[:, 0], kept[:, 1]
+    x, y, z = v % dims[0], (v // dims[0]) % dims[1], v // (dims[0] * dims[1])
+    bk = (z // B * nby + y // B) * nbx + x // B
+    missing = [(int(a), int(b)) for a, b in zip(bk, i) if (int(a), int(b)) not in listed]
+    assert not missing, missing[:5]

@@ -624,7 +624,12 @@ PEAK_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2}
 def gve_peak_bench(kind: str, iters: int, device=None):
     """(lane-operations per second, kernel ms) of one throughput
     microbenchmark: 'ffma', 'ffma2' (two operations per packed FMA) or 'ex2'."""
-    dev = torch.device("cuda", torch.cuda.current_device() if device is None else int(device))
+    if device is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    elif isinstance(device, torch.device):
+        dev = torch.device("cuda", device.index if device.index is not None else torch.cuda.current_device())
+    else:
+        dev = torch.device("cuda", int(device))
     ops = ctypes.c_double(0.0)
     ms = ctypes.c_float(0.0)
     with torch.cuda.device(dev):

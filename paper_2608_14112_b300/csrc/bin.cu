@@ -11,9 +11,9 @@
 //   ranges  per-brick [start, end) by adjacent difference.
 //
 // Bit-exactness: the keep-test coefficients and the brick cover are computed
-// with explicitly rounded FP64 operations (__dmul_rn & co., no contraction)
-// and explicitly rounded float32 operations, in the same order as the
-// oracle's definition, so both sides list exactly the same pairs.
+// with explicitly rounded float32 operations (__fmul_rn & co., no
+// contraction) in the same order as the oracle's definition, so both sides
+// list exactly the same pairs.
 #include <climits>
 
 #include "gve_int.cuh"
@@ -59,60 +59,40 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
         o[0] = r0; o[1] = r1; o[2] = r2;
         return;
     }
-    // the conservative brick cover from FP64 scales and rotation (the CPU
-    // reference of the binner uses the same FP64 activation)
-    bool ok = true;
-    for (int j = 0; j < 12; ++j) ok = ok && isfinite(pf[j]);
-    double s[3] = {0.0, 0.0, 0.0}, R[3][3];
-    if (ok) {
-        for (int j = 0; j < 3; ++j) s[j] = exp((double)pf[3 + j]);
-        const double qw = pf[6], qx = pf[7], qy = pf[8], qz = pf[9];
-        const double nq = __dsqrt_rn(da(da(da(dm(qw, qw), dm(qx, qx)), dm(qy, qy)), dm(qz, qz)));
-        ok = nq > 0.0 && isfinite(nq);
-        for (int j = 0; j < 3; ++j) ok = ok && s[j] > 0.0 && isfinite(s[j]);
-        if (ok) {
-            const double w = dd(qw, nq), x = dd(qx, nq), y = dd(qy, nq), z = dd(qz, nq);
-            R[0][0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
-            R[0][1] = dm(2.0, ds(dm(x, y), dm(w, z)));
-            R[0][2] = dm(2.0, da(dm(x, z), dm(w, y)));
-            R[1][0] = dm(2.0, da(dm(x, y), dm(w, z)));
-            R[1][1] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
-            R[1][2] = dm(2.0, ds(dm(y, z), dm(w, x)));
-            R[2][0] = dm(2.0, ds(dm(x, z), dm(w, y)));
-            R[2][1] = dm(2.0, da(dm(y, z), dm(w, x)));
-            R[2][2] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
-        }
-    }
-    if (ok) {
-        double smin = s[0], smax = s[0];
-        for (int j = 1; j < 3; ++j) { smin = fmin(smin, s[j]); smax = fmax(smax, s[j]); }
-        double ratio = dd(smax, smin);
-        double cond = dm(ratio, ratio);
-        double kb = dm((double)k, da(1.0001, dm(1e-5, cond)));
+    // the conservative brick cover, in float32 from the keep test's own
+    // scales and rotation (the CPU reference runs the same operations)
+    if (kc.ok) {
+        const float* sv = kc.s;
+        const float smin = fminf(sv[0], fminf(sv[1], sv[2])), smax = fmaxf(sv[0], fmaxf(sv[1], sv[2]));
+        const float ratio = __fdiv_rn(smax, smin);
+        const float cond = __fmul_rn(ratio, ratio);
+        const float kb = __fmul_rn(k, __fadd_rn(1.0001f, __fmul_rn(1e-5f, cond)));
         bool box_ok = isfinite(kb);
         for (int j = 0; j < 3 && box_ok; ++j) {
-            double var = da(da(dm(dm(R[j][0], R[j][0]), dm(s[0], s[0])), dm(dm(R[j][1], R[j][1]), dm(s[1], s[1]))),
-                            dm(dm(R[j][2], R[j][2]), dm(s[2], s[2])));
-            double r = da(dm(kb, __dsqrt_rn(var)), 0.01);
-            double mu = (double)pf[j];
-            double l = ceil(ds(mu, r)), h = floor(da(mu, r));
-            int nj = j == 0 ? g.nx : (j == 1 ? g.ny : g.nz);
+            const float var = __fadd_rn(
+                __fadd_rn(__fmul_rn(__fmul_rn(kc.R[j][0], kc.R[j][0]), __fmul_rn(sv[0], sv[0])),
+                          __fmul_rn(__fmul_rn(kc.R[j][1], kc.R[j][1]), __fmul_rn(sv[1], sv[1]))),
+                __fmul_rn(__fmul_rn(kc.R[j][2], kc.R[j][2]), __fmul_rn(sv[2], sv[2])));
+            const float r = __fadd_rn(__fmul_rn(kb, __fsqrt_rn(var)), 0.01f);
+            float l = ceilf(__fsub_rn(pf[j], r)), h = floorf(__fadd_rn(pf[j], r));
+            const int nj = j == 0 ? g.nx : (j == 1 ? g.ny : g.nz);
             if (!(l <= h) || !isfinite(l) || !isfinite(h)) { box_ok = false; break; }
-            if (l < 0.0) l = 0.0;
-            if (h > (double)(nj - 1)) h = (double)(nj - 1);
+            if (l < 0.0f) l = 0.0f;
+            if (h > (float)(nj - 1)) h = (float)(nj - 1);
             if (l > h) { box_ok = false; break; }
             b.blo[j] = (int)l / g.B;
             b.bhi[j] = (int)h / g.B;
         }
         if (box_ok) {
             for (int j = 0; j < 3; ++j)
-                for (int i2 = 0; i2 < 3; ++i2) b.L[j * 3 + i2] = (float)dd(R[i2][j], s[j]);
-            float hB = __fadd_rn((float)(0.5 * (double)(g.B - 1)), 0.01f);
+                for (int i2 = 0; i2 < 3; ++i2) b.L[j * 3 + i2] = __fdiv_rn(kc.R[i2][j], sv[j]);
+            const float hB = __fadd_rn((float)(0.5 * (double)(g.B - 1)), 0.01f);
             for (int j = 0; j < 3; ++j) {
-                float sabs = __fadd_rn(__fadd_rn(fabsf(b.L[j * 3 + 0]), fabsf(b.L[j * 3 + 1])), fabsf(b.L[j * 3 + 2]));
+                const float sabs =
+                    __fadd_rn(__fadd_rn(fabsf(b.L[j * 3 + 0]), fabsf(b.L[j * 3 + 1])), fabsf(b.L[j * 3 + 2]));
                 b.e[j] = __fmul_rn(hB, sabs);
             }
-            b.K2 = (float)da(dm(dm(kb, kb), 1.0001), 1e-4);
+            b.K2 = __fadd_rn(__fmul_rn(__fmul_rn(kb, kb), 1.0001f), 1e-4f);
             b.nonempty = 1;
         } else {
             for (int j = 0; j < 3; ++j) { b.blo[j] = 0; b.bhi[j] = -1; }

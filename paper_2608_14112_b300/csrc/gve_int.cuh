@@ -224,6 +224,8 @@ __device__ __forceinline__ float exp_fixed(float x)
 // quaternion or scale).
 struct KeepCoef {
     float4 r0, r1, r2;
+    float s[3];        // float32 scales exp_fixed(log s)
+    float R[3][3];     // rotation of the normalised quaternion
     bool ok;
 };
 
@@ -244,7 +246,8 @@ __device__ __forceinline__ void keep_coefficients(const float (&pf)[12], KeepCoe
     for (int j = 0; j < 3; ++j)
         if (!(s[j] > 0.0f) || !isfinite(s[j])) return;
     const float w = __fdiv_rn(qw, nq), x = __fdiv_rn(qx, nq), y = __fdiv_rn(qy, nq), z = __fdiv_rn(qz, nq);
-    float R[3][3];
+    float(&R)[3][3] = o.R;
+    for (int j = 0; j < 3; ++j) o.s[j] = s[j];
     R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(__fmul_rn(y, y), __fmul_rn(z, z))));
     R[0][1] = __fmul_rn(2.0f, __fsub_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
     R[0][2] = __fmul_rn(2.0f, __fadd_rn(__fmul_rn(x, z), __fmul_rn(w, y)));

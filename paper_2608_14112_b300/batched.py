@@ -1,8 +1,10 @@
 """Batched encode: many volumes (or timesteps) of uneven shapes encoded
 together -- analytic allocation of each volume's budget, one autotuning pass
 of the evaluator's launch shape, then refinement of all volumes with one
-CUDA graph launch per iteration (``gve_refine_batch``).  Each volume is
-encoded exactly as it would be alone (Sec. III-E of arxiv 2608.14112)."""
+CUDA graph launch per iteration (``gve_refine_batch``: per-volume binning,
+then one persistent kernel over the bricks of every volume for evaluation
+and update).  Each volume is encoded exactly as it would be alone
+(Sec. III-E of arxiv 2608.14112)."""
 from __future__ import annotations
 
 import time

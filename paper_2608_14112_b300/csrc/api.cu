@@ -58,6 +58,10 @@ gve_status ensure(gve_ctx* c, Buf& b, size_t bytes, cudaStream_t s)
         b.bytes = 0;
     }
     size_t want = bytes + bytes / 8;
+    // fault-injection hook (host side): GVE_FAULT=alloc makes every scratch
+    // allocation fail as an exhausted device would
+    if (const char* f = getenv("GVE_FAULT"))
+        if (strcmp(f, "alloc") == 0) return fail(c, GVE_E_NOMEM, "device scratch allocation failed (injected)");
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -333,6 +337,7 @@ void gve_ctx_destroy(gve_ctx* c)
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->bstate.p) cudaFree(c->bstate.p);
+    if (c->btab.p) cudaFree(c->btab.p);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;

@@ -36,6 +36,7 @@
 // unrolled loop), shifted to dx once per task, in packed f32x2 arithmetic.  Task sums meet in shared memory (float atomics); one
 // thread per Gaussian then issues three 16-byte vector atomics into its
 // global accumulator.  Nothing per pair or per voxel goes to HBM.
+#include "chain.cuh"
 #include "gve_int.cuh"
 
 namespace gve {
@@ -74,8 +75,11 @@ __device__ __forceinline__ void stage_chunk(const BrickArgs& a, uint32_t s0, int
     }
 }
 
+// The fused evaluation of one brick (all threads of the CTA take part; the
+// shared arrays are the CTA's).  Launched one CTA per brick by k_brick, and
+// in a loop over the bricks of many volumes by the batched kernel.
 template <int MODE, int B, int CH>
-__global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k_brick(const BrickArgs a)
+__device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned brick)
 {
     using S = BrickShape<B>;
     constexpr int NT = S::THREADS, NW = S::NW, HALF = S::HALF, SY = S::SY, SZ = S::SZ;
@@ -93,7 +97,6 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const BinGeom& g = a.g;
-    const long long brick = blockIdx.x;
     const int bx = (int)(brick % g.nbx);
     const int by = (int)((brick / g.nbx) % g.nby);
     const int bz = (int)(brick / ((long long)g.nbx * g.nby));
@@ -413,6 +416,12 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
     }
 }
 
+template <int MODE, int B, int CH>
+__global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k_brick(const BrickArgs a)
+{
+    brick_body<MODE, B, CH>(a, blockIdx.x);
+}
+
 template <int B, int CH>
 static void launch_brick_bc(int mode, const BrickArgs& a, cudaStream_t s)
 {
@@ -437,6 +446,165 @@ void launch_brick(int mode, const BrickArgs& a, cudaStream_t s)
     } else {
         if (c32) launch_brick_bc<8, 32>(mode, a, s); else launch_brick_bc<8, 64>(mode, a, s);
     }
+}
+
+// ------------------------------------------------------------------------
+// batched persistent iteration
+// ------------------------------------------------------------------------
+// Grid barrier of a cooperative launch with a bounded wait: thread 0 of each
+// CTA arrives on a counter; the last arrival resets it and advances the
+// generation, the others sleep until the generation moves or `limit` sleeps
+// pass, in which case the error flag is set.  Returns false (for the whole
+// CTA) when the wait ran out.
+__device__ __forceinline__ bool grid_barrier(BatchState* bs, unsigned expect, long long limit)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &bs->bar_gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&bs->bar_count, 1u) + 1u == expect) {
+            atomicExch(&bs->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&bs->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > limit) {
+                    ok = 0;
+                    atomicExch(&bs->err, 1);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// the chain rule out of line: its register needs stay out of the brick body's
+__device__ __noinline__ void chain_one_call(const long long i, const BatchIterArgs& p)
+{
+    chain_one(i, p.acc, p.acc, p.prims, p.grad, p.m, p.v, p.ad, p.do_adam, nullptr);
+}
+
+template <int B, int CH>
+__global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k_batch_iter(const BatchIterArgs p)
+{
+    constexpr int NT = BrickShape<B>::THREADS;
+    static_assert(sizeof(BrickArgs) % 4 == 0, "argument copy by words");
+    __shared__ BrickArgs s_a;
+    __shared__ unsigned long long s_gb;
+    __shared__ double s_red[2][NT / 32 > 0 ? NT / 32 : 1];
+    BatchState* bs = p.bs;
+    // an earlier wait ran out, or a volume's pairs overflowed: nothing runs
+    if (*(volatile int*)&bs->err || p.vargs[0].st->overflow) return;
+
+    // phase 1: the bricks of every volume from one work counter
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_gb = atomicAdd(&bs->next, 1ull);
+        __syncthreads();
+        const unsigned long long gb = s_gb;
+        if (gb >= (unsigned long long)p.nbricks) break;
+        int lo = 0, hi = p.nvol - 1;   // the volume holding global brick gb
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.boff[mid] <= (long long)gb) lo = mid; else hi = mid - 1;
+        }
+        if (lo != cur) {
+            const int* src = reinterpret_cast<const int*>(p.vargs + lo);
+            int* dst = reinterpret_cast<int*>(&s_a);
+            for (int w = threadIdx.x; w < (int)(sizeof(BrickArgs) / 4); w += NT) dst[w] = src[w];
+            cur = lo;
+            __syncthreads();
+        }
+        brick_body<kModeLoss, B, CH>(s_a, (unsigned)(gb - (unsigned long long)p.boff[lo]));
+        __syncthreads();
+    }
+    if (!grid_barrier(bs, p.expect, p.spin_limit)) return;
+
+    // phase 2a: each volume's SSE, summed in a fixed order by one CTA
+    for (int v = blockIdx.x; v < p.nvol; v += gridDim.x) {
+        const double2* part = p.vargs[v].part;
+        const long long nb = p.boff[v + 1] - p.boff[v];
+        double x = 0.0, y = 0.0;
+        for (long long i = threadIdx.x; i < nb; i += NT) {
+            const double2 q = part[i];
+            x += q.x;
+            y += q.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = x; s_red[1][threadIdx.x >> 5] = y; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < NT / 32; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
+            p.sse[2 * v] = a;
+            p.sse[2 * v + 1] = b;
+            if (p.trace) p.trace[(size_t)bs->it * p.nvol + v] = a * p.inv_m[v];
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) bs->next = 0;   // every CTA is past phase 1
+    // phase 2b: chain rule and Adam (or the gradient) of every Gaussian
+    const long long stride = (long long)gridDim.x * NT;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < p.ntot; i += stride) chain_one_call(i, p);
+}
+
+template <int B, int CH>
+static int batch_grid_bc()
+{
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iter<B, CH>, BrickShape<B>::THREADS, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * num_sms();
+}
+
+int batch_iter_grid(int B, int CH)
+{
+    const bool c32 = CH == 32;
+    if (B == 4) return c32 ? batch_grid_bc<4, 32>() : batch_grid_bc<4, 64>();
+    if (B == 16) return c32 ? batch_grid_bc<16, 32>() : batch_grid_bc<16, 64>();
+    return c32 ? batch_grid_bc<8, 32>() : batch_grid_bc<8, 64>();
+}
+
+template <int B, int CH>
+static cudaError_t launch_batch_bc(const BatchIterArgs& p, unsigned grid, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BrickShape<B>::THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_iter<B, CH>, p);
+}
+
+cudaError_t launch_batch_iter(int B, int CH, const BatchIterArgs& p, unsigned grid, cudaStream_t s)
+{
+    const bool c32 = CH == 32;
+    if (B == 4) return c32 ? launch_batch_bc<4, 32>(p, grid, s) : launch_batch_bc<4, 64>(p, grid, s);
+    if (B == 16) return c32 ? launch_batch_bc<16, 32>(p, grid, s) : launch_batch_bc<16, 64>(p, grid, s);
+    return c32 ? launch_batch_bc<8, 32>(p, grid, s) : launch_batch_bc<8, 64>(p, grid, s);
 }
 
 // ------------------------------------------------------------------------

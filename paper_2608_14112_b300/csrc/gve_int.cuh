@@ -93,7 +93,9 @@ struct gve_ctx {
     std::vector<cudaEvent_t> vjoin;
     cudaStream_t gstream = nullptr;
     cudaEvent_t fork = nullptr;
-    gve::Buf bstate;                 // batch device state: step counter, {bc1, bc2}
+    gve::Buf bstate;                 // batch device state (BatchState)
+    gve::Buf btab;                   // batch tables: per-volume evaluator arguments, brick offsets,
+                                     // 1 / voxels, SSE
     // stratified-sample refinement: class lists, per-block counts and
     // offsets, samples, cell table, sorted sample order, per-sample sums and
     // upstream gradients, loss
@@ -331,6 +333,7 @@ struct BrickArgs {
     unsigned long long pairs_cap;      // entries pairs can hold
 };
 void launch_brick(int mode, const BrickArgs& a, cudaStream_t s);
+
 // deterministic reduction of per-brick partials; writes st->sse and, if
 // trace != nullptr, trace[i] = sse_masked * inv_m with i = iter, or
 // i = (*iter_dev) * trace_stride + trace_col when iter_dev is set.
@@ -351,6 +354,48 @@ struct AdamArgs {
 void launch_chain(const float* acc_in, float* acc_zero, float* prims, long long n, float* grad,
                   float* m, float* v, const AdamArgs* adam, const DevState* st, cudaStream_t s,
                   const float* extra = nullptr);
+
+// ---- the batched persistent iteration (field.cu) ---------------------------
+// Device state of one batched refinement call.
+struct BatchState {
+    int it;                    // iteration index within the call
+    int first;                 // first iteration that overflowed, -1 if none
+    float bc[2];               // Adam bias corrections of the current step
+    unsigned long long next;   // bricks handed out by the work counter
+    unsigned bar_count;        // grid barrier: CTAs arrived
+    unsigned bar_gen;          // grid barrier: generation
+    int err;                   // 1: a bounded wait ran out (GVE_E_TIMEOUT)
+    int pad;
+};
+
+struct BatchIterArgs {
+    const BrickArgs* vargs;    // [nvol] evaluator arguments of each volume (device)
+    const long long* boff;     // [nvol + 1] first global brick of each volume (device)
+    const double* inv_m;       // [nvol] 1 / voxels (device)
+    int nvol;
+    long long nbricks;         // bricks of all volumes
+    long long ntot;            // Gaussians of all volumes (records concatenated)
+    BatchState* bs;
+    float* acc;                // [ntot][12] sums of the backward, cleared after use
+    float* prims;              // [ntot][12]
+    float* m;                  // Adam moments [ntot][12] each, or gradient scratch
+    float* v;
+    float* grad;               // gradient output [ntot][12] when do_adam == 0
+    int do_adam;
+    AdamArgs ad;
+    double* trace;             // [iters][nvol] masked mean squared errors, or nullptr
+    double* sse;               // [nvol][2] {masked, unmasked} SSE of this iteration (device)
+    unsigned expect;           // CTAs the grid barrier waits for
+    long long spin_limit;      // sleeps of ~128 ns before a wait gives up
+};
+// The resident grid of the persistent kernel for brick edge B and chunk CH
+// (0 when it cannot be launched cooperatively).
+int batch_iter_grid(int B, int CH);
+// One batched iteration as one cooperative launch: every volume's bricks
+// (fused forward + backward, loss mode) from a shared work counter, a bounded
+// grid barrier, then each volume's loss and the chain rule + Adam (or the
+// gradient) of every Gaussian.
+cudaError_t launch_batch_iter(int B, int CH, const BatchIterArgs& p, unsigned grid, cudaStream_t s);
 
 // ---- allocator (alloc.cu) ------------------------------------------------
 gve_status allocate(gve_ctx* c, const float* field, gve_dims d, int64_t budget,

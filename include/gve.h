@@ -294,6 +294,27 @@ GVE_API gve_status gve_proposal_backward(gve_ctx* ctx, const float* model_dev, c
                                          int64_t n, gve_dims dims, int32_t accumulate, float* dP_dev,
                                          void* stream);
 
+/* Input standardisation of the network from its training features X
+ * [rows][16] (rows >= 1): the column means and sample spreads in FP64 (two
+ * passes, a fixed summation order) go into the model's mean and inverse
+ * spread, a feature whose spread is at most 1e-3 (1 + |mean|) getting
+ * inverse spread 0 (it carries nothing to learn from). */
+GVE_API gve_status gve_mlp_standardise(gve_ctx* ctx, float* model_dev, const float* X_dev, int64_t rows,
+                                       void* stream);
+/* Training targets of the proposal from an allocation and its refinement:
+ * T[i] = refined minus allocated (a, log s0, log s1, log s2) of record i
+ * (prims0_dev, prims1_dev [n][12]; T_dev [n][4], 16-byte aligned). */
+GVE_API gve_status gve_proposal_targets(gve_ctx* ctx, const float* prims0_dev, const float* prims1_dev, int64_t n,
+                                        float* T_dev, void* stream);
+/* Divides each column of a target matrix T_dev [rows][4] (in place,
+ * 16-byte aligned) by its sample spread over the rows (FP64, at least
+ * 1e-6), the spreads written to scale_dev (device float[4]). */
+GVE_API gve_status gve_mlp_scale_targets(gve_ctx* ctx, float* T_dev, int64_t rows, float* scale_dev, void* stream);
+/* Multiplies output k of the network's last layer (W4 row k and b4[k]) by
+ * scale_dev[k] and refreshes the BF16 copies: a network trained on targets
+ * divided by those spreads then predicts the targets themselves. */
+GVE_API gve_status gve_mlp_fold_output_scale(gve_ctx* ctx, float* model_dev, const float* scale_dev, void* stream);
+
 /* Pre-encoding structure statistics (Sec. V-F, Table VI) of a device field
  * (float32, [nz][ny][nx], device memory, not modified).  Host output
  * out[5] = {occupancy (V > 0.02), share of the occupied voxels' float32

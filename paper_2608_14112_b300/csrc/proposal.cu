@@ -558,3 +558,176 @@ extern "C" gve_status gve_proposal_backward(gve_ctx* c, const float* model, cons
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "proposal backward");
     return GVE_OK;
 }
+
+// ---- training-set statistics and targets ------------------------------------
+// Column mean and spread of a row-major [rows][C] float32 matrix in FP64, in
+// a fixed order (so the same data give the same bits): blocks sum contiguous
+// row ranges, one block adds the block sums; the spread is the square root
+// of the centred sum of squares over rows - 1 (a second pass), as for the
+// sample standard deviation.
+namespace gve {
+namespace {
+
+constexpr int kMomBlocks = 256;
+
+template <int C>
+__global__ void __launch_bounds__(256) k_col_sums(const float* __restrict__ X, long long rows,
+                                                  const double* __restrict__ mean, double* __restrict__ part)
+{
+    __shared__ double sm[C][8];
+    const long long chunk = (rows + gridDim.x - 1) / gridDim.x;
+    const long long r0 = (long long)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+    double acc[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) acc[k] = 0.0;
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double x = (double)X[r * C + k];
+            const double d = mean ? x - mean[k] : x;
+            acc[k] += mean ? d * d : d;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < C) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sm[threadIdx.x][w];
+        part[blockIdx.x * C + threadIdx.x] = v;
+    }
+}
+
+// out[k] = sum of the block partials of column k, divided by `div`
+template <int C>
+__global__ void k_col_final(const double* __restrict__ part, int nb, double div, double* __restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= C) return;
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) v += part[b * C + k];
+    out[k] = v / div;
+}
+
+// moments[0..C) = column means, moments[C..2C) = column spreads
+template <int C>
+void col_moments(const float* X, long long rows, double* moments, double* part, cudaStream_t s)
+{
+    k_col_sums<C><<<kMomBlocks, 256, 0, s>>>(X, rows, nullptr, part);
+    k_col_final<C><<<1, 32, 0, s>>>(part, kMomBlocks, (double)rows, moments);
+    k_col_sums<C><<<kMomBlocks, 256, 0, s>>>(X, rows, moments, part);
+    k_col_final<C><<<1, 32, 0, s>>>(part, kMomBlocks, rows > 1 ? (double)(rows - 1) : 1.0, moments + C);
+}
+
+// the network's input standardisation from the feature moments: a feature
+// whose spread is at most 1e-3 (1 + |mean|) gets weight 0
+__global__ void k_set_norm(const double* __restrict__ mom, float* __restrict__ model)
+{
+    const int k = threadIdx.x;
+    if (k >= kIn) return;
+    const double mean = mom[k], sd = sqrt(mom[kIn + k]);
+    const bool live = sd > 1e-3 * (1.0 + fabs(mean));
+    model[kOffNorm + k] = (float)mean;
+    model[kOffNorm + kIn + k] = live ? (float)(1.0 / fmax(sd, 1e-30)) : 0.f;
+}
+
+// refined minus allocated (a, log s0, log s1, log s2)
+__global__ void k_targets(const float* __restrict__ p0, const float* __restrict__ p1, long long n, float* __restrict__ T)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* a = p0 + 12 * i;
+    const float* b = p1 + 12 * i;
+    reinterpret_cast<float4*>(T)[i] = make_float4(b[10] - a[10], b[3] - a[3], b[4] - a[4], b[5] - a[5]);
+}
+
+// scale[k] = max(spread_k, 1e-6) (float32); T[:, k] /= scale[k]
+__global__ void k_target_scale(const double* __restrict__ mom, float* __restrict__ scale)
+{
+    const int k = threadIdx.x;
+    if (k < kOut) scale[k] = (float)fmax(sqrt(mom[kOut + k]), 1e-6);
+}
+
+__global__ void k_div_cols(float* __restrict__ T, long long n, const float* __restrict__ scale)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 t = reinterpret_cast<float4*>(T)[i];
+    t.x /= scale[0]; t.y /= scale[1]; t.z /= scale[2]; t.w /= scale[3];
+    reinterpret_cast<float4*>(T)[i] = t;
+}
+
+// last layer rows k scaled by scale[k]: the network then predicts the
+// unscaled targets
+__global__ void k_fold_scale(float* __restrict__ model, const float* __restrict__ scale)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kOut * kH) model[kOffW4 + i] *= scale[i / kH];
+    else if (i < kOut * kH + kOut) model[kOffB4 + (i - kOut * kH)] *= scale[i - kOut * kH];
+}
+
+}  // namespace
+}  // namespace gve
+
+extern "C" gve_status gve_mlp_standardise(gve_ctx* c, float* model, const float* X, int64_t rows, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!model || !X || rows < 1) return fail(c, GVE_E_INVALID, "bad standardisation arguments");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    gve_status st = ensure(c, c->a_cnt, sizeof(double) * (kMomBlocks * kIn + 2 * kIn), s);
+    if (st != GVE_OK) return st;
+    double* part = (double*)c->a_cnt.p;
+    double* mom = part + kMomBlocks * kIn;
+    col_moments<kIn>(X, rows, mom, part, s);
+    k_set_norm<<<1, 32, 0, s>>>(mom, model);
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "mlp standardise");
+    return GVE_OK;
+}
+
+extern "C" gve_status gve_proposal_targets(gve_ctx* c, const float* prims0, const float* prims1, int64_t n,
+                                           float* T, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!prims0 || !prims1 || !T || n < 1) return fail(c, GVE_E_INVALID, "bad target arguments");
+    if (reinterpret_cast<uintptr_t>(T) & 15u) return fail(c, GVE_E_INVALID, "targets not 16-byte aligned");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    k_targets<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(prims0, prims1, n, T);
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "proposal targets");
+    return GVE_OK;
+}
+
+extern "C" gve_status gve_mlp_scale_targets(gve_ctx* c, float* T, int64_t rows, float* scale, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!T || !scale || rows < 1) return fail(c, GVE_E_INVALID, "bad target arguments");
+    if (reinterpret_cast<uintptr_t>(T) & 15u) return fail(c, GVE_E_INVALID, "targets not 16-byte aligned");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    gve_status st = ensure(c, c->a_cnt, sizeof(double) * (kMomBlocks * kIn + 2 * kIn), s);
+    if (st != GVE_OK) return st;
+    double* part = (double*)c->a_cnt.p;
+    double* mom = part + kMomBlocks * kIn;
+    col_moments<kOut>(T, rows, mom, part, s);
+    k_target_scale<<<1, 32, 0, s>>>(mom, scale);
+    k_div_cols<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(T, rows, scale);
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "scale targets");
+    return GVE_OK;
+}
+
+extern "C" gve_status gve_mlp_fold_output_scale(gve_ctx* c, float* model, const float* scale, void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (!model || !scale) return fail(c, GVE_E_INVALID, "null argument");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_fold_scale<<<(kOut * kH + kOut + 255) / 256, 256, 0, s>>>(model, scale);
+    k_mlp_quantise<<<(kP + 255) / 256, 256, 0, s>>>(model);
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "mlp fold");
+    return GVE_OK;
+}

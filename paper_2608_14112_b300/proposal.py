@@ -38,8 +38,13 @@ def _lib():
         L.gve_mlp_quantise.argtypes = [Pp, Pp, Pp]
         L.gve_proposal_apply.argtypes = [Pp, Pp, Pp, Pp, i64, gve.Dims, Pp]
         L.gve_proposal_backward.argtypes = [Pp, Pp, Pp, Pp, Pp, i64, gve.Dims, i32, Pp, Pp]
+        L.gve_mlp_standardise.argtypes = [Pp, Pp, Pp, i64, Pp]
+        L.gve_proposal_targets.argtypes = [Pp, Pp, Pp, i64, Pp, Pp]
+        L.gve_mlp_scale_targets.argtypes = [Pp, Pp, i64, Pp, Pp]
+        L.gve_mlp_fold_output_scale.argtypes = [Pp, Pp, Pp, Pp]
         for fn in ("gve_proposal_features", "gve_mlp_forward", "gve_mlp_grad", "gve_mlp_adam", "gve_mlp_quantise",
-                   "gve_proposal_apply", "gve_proposal_backward"):
+                   "gve_proposal_apply", "gve_proposal_backward", "gve_mlp_standardise", "gve_proposal_targets",
+                   "gve_mlp_scale_targets", "gve_mlp_fold_output_scale"):
             getattr(L, fn).restype = ctypes.c_int
         L._proposal_typed = True
     return L
@@ -96,16 +101,14 @@ class Proposal:
         gve._check(_lib().gve_mlp_quantise(c, _p(self.model), gve._stream(self.device)), c)
 
     def set_normalisation(self, X: torch.Tensor):
-        """Input standardisation from training features.  A feature whose
-        spread is negligible against its magnitude carries nothing to learn
-        from and gets weight 0, so that it cannot swing the network on data
-        where it does vary."""
-        mean = X.double().mean(0)
-        std = X.double().std(0)
-        live = std > 1e-3 * (1.0 + mean.abs())
-        istd = torch.where(live, 1.0 / std.clamp_min(1e-30), torch.zeros_like(std))
-        self.model[3 * P: 3 * P + 16] = mean.float()
-        self.model[3 * P + 16: 3 * P + 32] = istd.float()
+        """Input standardisation from training features (gve_mlp_standardise:
+        column means and spreads on the device; a feature whose spread is
+        negligible against its magnitude carries nothing to learn from and
+        gets weight 0, so that it cannot swing the network on data where it
+        does vary)."""
+        X = X.contiguous()
+        c = self._ctx()
+        gve._check(_lib().gve_mlp_standardise(c, _p(self.model), _p(X), X.shape[0], gve._stream(self.device)), c)
 
     def forward(self, X: torch.Tensor) -> torch.Tensor:
         Y = torch.empty((X.shape[0], 4), dtype=torch.float32, device=self.device)
@@ -129,13 +132,13 @@ class Proposal:
                                        float(eps), self.step, gve._stream(self.device)), c)
 
     def train(self, X: torch.Tensor, T: torch.Tensor, epochs: int = 20, batch: int = 4096, lr: float = 1e-3,
-              seed: int = 0) -> TrainLog:
-        """Minibatch Adam on the mean squared error of the corrections, each
-        output standardised by its spread over the training set; the scale is
-        folded back into the last layer afterwards."""
+              seed: int = 0, tscale: torch.Tensor | None = None) -> TrainLog:
+        """Minibatch Adam on the mean squared error of the corrections.  The
+        targets come from ``make_pairs`` divided by their spreads ``tscale``
+        (device float32 [4]); the scale is folded back into the last layer
+        afterwards (gve_mlp_fold_output_scale), so the trained network
+        predicts the corrections themselves."""
         self.set_normalisation(X)
-        tscale = T.double().std(0).clamp_min(1e-6).float()
-        T = (T / tscale).contiguous()
         self._quantise()
         g = torch.Generator(device=self.device)
         g.manual_seed(seed)
@@ -152,11 +155,10 @@ class Proposal:
                 total += loss
                 nb += 1
             losses.append(float(total.item()) / nb)
-        # undo the target standardisation in W4 and b4
-        W4 = self.model[:P][9408:9664].view(4, 64)
-        W4.mul_(tscale[:, None])
-        self.model[9664:9668].mul_(tscale)
-        self._quantise()
+        if tscale is not None:
+            c = self._ctx()
+            gve._check(_lib().gve_mlp_fold_output_scale(c, _p(self.model), _p(tscale), gve._stream(self.device)),
+                       c)
         return TrainLog(losses, epochs, R)
 
     def apply(self, feats: torch.Tensor, prims: torch.Tensor, shape):
@@ -217,15 +219,21 @@ class Proposal:
 
 
 def targets(prims0: torch.Tensor, prims1: torch.Tensor) -> torch.Tensor:
-    """Training targets: refined minus allocated (a, log s0, log s1, log s2)."""
-    d = prims1 - prims0
-    return torch.stack([d[:, 10], d[:, 3], d[:, 4], d[:, 5]], 1).contiguous()
+    """Training targets (gve_proposal_targets): refined minus allocated (a,
+    log s0, log s1, log s2)."""
+    n = prims0.shape[0]
+    T = torch.empty((n, 4), dtype=torch.float32, device=prims0.device)
+    c = gve.context(prims0.device.index)
+    gve._check(_lib().gve_proposal_targets(c, _p(prims0.contiguous()), _p(prims1.contiguous()), n, _p(T),
+                                           gve._stream(prims0.device)), c)
+    return T
 
 
 def make_pairs(fields, budget: int, iters: int, seed: int = 0, lr: float = 1e-2, chunk: int = 32):
     """Allocation -> refined pairs from the encoder itself: features of each
-    field's analytic allocation and the corrections refinement applied.
-    Fields are refined in batches with gve_refine_batch."""
+    field's analytic allocation and the corrections refinement applied
+    (unscaled; ``scale_targets`` divides them by their spreads).  Fields are
+    refined in batches with gve_refine_batch."""
     X, T = [], []
     for s in range(0, len(fields), chunk):
         group = fields[s:s + chunk]
@@ -241,6 +249,16 @@ def make_pairs(fields, budget: int, iters: int, seed: int = 0, lr: float = 1e-2,
         X.append(torch.cat(feats, 0))
         T.append(targets(P0, P1))
     return torch.cat(X, 0).contiguous(), torch.cat(T, 0).contiguous()
+
+
+def scale_targets(T: torch.Tensor):
+    """(a copy of T with each column divided by its spread, the spreads
+    (device float32 [4])), computed by gve_mlp_scale_targets."""
+    Ts = T.clone().contiguous()
+    sc = torch.empty(4, dtype=torch.float32, device=T.device)
+    c = gve.context(T.device.index)
+    gve._check(_lib().gve_mlp_scale_targets(c, _p(Ts), Ts.shape[0], _p(sc), gve._stream(T.device)), c)
+    return Ts, sc
 
 
 def allocations(fields, budget: int, seed: int = 0):

@@ -176,3 +176,55 @@ def test_trained_proposal_beats_plain_allocation():
         gain = 10 * torch.log10(t_plain / t_prop).cpu().numpy()
         assert gain[0] > 0.1, gain
         assert gain[5] > 0.0, gain
+
+
+def test_standardise_matches_column_moments():
+    """gve_mlp_standardise: column means and sample spreads (ddof 1) of the
+    training features, inverse spread 0 for a feature whose spread is at
+    most 1e-3 (1 + |mean|)."""
+    rng = np.random.default_rng(17)
+    X = rng.normal(size=(5003, 16)) * rng.uniform(0.1, 3.0, 16) + rng.normal(0, 2, 16)
+    X[:, 12] = 0.0                       # constant: dead
+    X[:, 13] = 5.0 + 1e-5 * rng.normal(size=5003)   # negligible spread: dead
+    X = X.astype(np.float32)
+    m = proposal.Proposal("cuda", seed=0)
+    m.set_normalisation(torch.from_numpy(X).cuda())
+    host = m.model.cpu().numpy()
+    mean, istd = host[3 * M.P:3 * M.P + 16], host[3 * M.P + 16:3 * M.P + 32]
+    X64 = X.astype(np.float64)
+    mu, sd = X64.mean(0), X64.std(0, ddof=1)
+    live = sd > 1e-3 * (1 + np.abs(mu))
+    assert live.tolist().count(False) == 2 and not live[12] and not live[13]
+    np.testing.assert_allclose(mean, mu.astype(np.float32), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(istd[live], (1.0 / sd[live]).astype(np.float32), rtol=1e-6)
+    assert (istd[~live] == 0).all()
+
+
+def test_targets_scale_and_fold():
+    """Targets refined - allocated (exact float32 differences), their
+    division by the column spreads (numpy float32 division of the same
+    spreads), and the fold of the spreads into the last layer (exact float32
+    products, BF16 copies refreshed)."""
+    rng = np.random.default_rng(18)
+    n = 3001
+    p0 = rng.normal(size=(n, 12)).astype(np.float32)
+    p1 = (p0 + rng.normal(0, [0.1] * 3 + [0.05, 0.2, 0.01] + [0.1] * 4 + [0.3, 0.0], (n, 12))).astype(np.float32)
+    T = proposal.targets(torch.from_numpy(p0).cuda(), torch.from_numpy(p1).cuda()).cpu().numpy()
+    want = np.stack([p1[:, 10] - p0[:, 10], p1[:, 3] - p0[:, 3], p1[:, 4] - p0[:, 4], p1[:, 5] - p0[:, 5]], 1)
+    np.testing.assert_array_equal(T, want)
+    Ts, sc = proposal.scale_targets(torch.from_numpy(T).cuda())
+    sc = sc.cpu().numpy()
+    sd = np.maximum(T.astype(np.float64).std(0, ddof=1), 1e-6).astype(np.float32)
+    np.testing.assert_allclose(sc, sd, rtol=1e-6)
+    np.testing.assert_array_equal(Ts.cpu().numpy(), (T / sc).astype(np.float32))
+    m = _model(seed=3)
+    before = m.model[:M.P].cpu().numpy().copy()
+    scale = torch.tensor([2.0, 0.5, 3.0, 0.25], device="cuda")
+    gve._check(proposal._lib().gve_mlp_fold_output_scale(m._ctx(), proposal._p(m.model), proposal._p(scale),
+                                                         gve._stream(m.device)), m._ctx())
+    after = m.model.cpu().numpy()
+    s = np.array([2.0, 0.5, 3.0, 0.25], np.float32)
+    np.testing.assert_array_equal(after[9408:9664].reshape(4, 64), before[9408:9664].reshape(4, 64) * s[:, None])
+    np.testing.assert_array_equal(after[9664:9668], before[9664:9668] * s)
+    np.testing.assert_array_equal(after[:9408], before[:9408])
+    np.testing.assert_array_equal(M.bf16_params(after), M.bf16_round(after[:M.P]))

@@ -49,6 +49,13 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr int kAccStride = 13;  // padded per-Gaussian stride of the shared sums
 
 // CTA geometry for brick edge B: one lane per row of B voxels along x (B^2
@@ -64,14 +71,36 @@ struct BrickShape {
     static constexpr int MINB = B == 16 ? 3 : (B == 8 ? 14 : 16);
 };
 
-template <int NT>
+// Stages the chunk's records: each thread takes whole Gaussians and issues
+// all of its list and record loads before any store, so a chunk costs two
+// dependent trips to L2 whatever the list length.
+template <int NT, int CH>
 __device__ __forceinline__ void stage_chunk(const BrickArgs& a, uint32_t s0, int c0, int cnt, float4* s_rec,
                                             uint32_t* s_msk, int tid)
 {
-    for (int j = tid; j < cnt * 3; j += NT) {
-        const uint32_t v = a.gids[s0 + c0 + j / 3];
-        s_rec[j] = a.rec[3 * (size_t)(v & kGidMask) + (j % 3)];
-        if (j % 3 == 0) s_msk[j / 3] = v >> kGidBits;
+    constexpr int PER = (CH + NT - 1) / NT;
+    uint32_t v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int j = tid + k * NT;
+        v[k] = j < cnt ? a.gids[s0 + c0 + j] : 0u;
+    }
+    float4 r[PER][3];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int j = tid + k * NT;
+        if (j < cnt) {
+            const float4* p = a.rec + 3 * (size_t)(v[k] & kGidMask);
+            r[k][0] = p[0]; r[k][1] = p[1]; r[k][2] = p[2];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int j = tid + k * NT;
+        if (j < cnt) {
+            s_rec[3 * j] = r[k][0]; s_rec[3 * j + 1] = r[k][1]; s_rec[3 * j + 2] = r[k][2];
+            s_msk[j] = v[k] >> kGidBits;
+        }
     }
 }
 
@@ -127,7 +156,7 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
         const int c0 = ch * CH;
         const int cnt = min(CH, L - c0);
         if (ch > 0) __syncthreads();
-        stage_chunk<NT>(a, s0, c0, cnt, s_rec, s_msk, tid);
+        stage_chunk<NT, CH>(a, s0, c0, cnt, s_rec, s_msk, tid);
         __syncthreads();
         // the warp's live Gaussians of this chunk, two at a time (list order kept)
         for (int base = 0; base < cnt; base += 32) {
@@ -227,17 +256,27 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
 
     const float rho0 = a.rho0;
     const size_t vrow = ((size_t)gz * g.ny + gy) * g.nx + gx0;
-    float up[B], vt[B];
-#pragma unroll
-    for (int q = 0; q < HALF; ++q) {
-        vt[2 * q] = a.normalized ? num[q].x / fmaxf(den[q].x, rho0) : num[q].x;
-        vt[2 * q + 1] = a.normalized ? num[q].y / fmaxf(den[q].y, rho0) : num[q].y;
-    }
+    float up[B], vt[B], inv[B];
     if (MODE == kModeEval) {
+        // the field handed to the caller: Eq. 3 with a correctly rounded division
+#pragma unroll
+        for (int q = 0; q < HALF; ++q) {
+            vt[2 * q] = a.normalized ? num[q].x / fmaxf(den[q].x, rho0) : num[q].x;
+            vt[2 * q + 1] = a.normalized ? num[q].y / fmaxf(den[q].y, rho0) : num[q].y;
+        }
 #pragma unroll
         for (int x = 0; x < B; ++x)
             if (x < nxin) a.field_out[vrow + x] = vt[x];
         return;
+    }
+    // loss and backward: one reciprocal of max(den, rho0) per voxel serves
+    // Vtilde = num / den' and gn = up / den' (rcp.approx: within 1 ulp)
+#pragma unroll
+    for (int q = 0; q < HALF; ++q) {
+        inv[2 * q] = a.normalized ? rcp_approx(fmaxf(den[q].x, rho0)) : 1.f;
+        inv[2 * q + 1] = a.normalized ? rcp_approx(fmaxf(den[q].y, rho0)) : 1.f;
+        vt[2 * q] = num[q].x * inv[2 * q];
+        vt[2 * q + 1] = num[q].y * inv[2 * q + 1];
     }
     if (MODE == kModeLoss) {
         float ef = 0.f, el = 0.f;
@@ -260,17 +299,19 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
 #pragma unroll
         for (int x = 0; x < B; ++x) up[x] = x < nxin ? a.upstream[vrow + x] : 0.f;
     }
-    if (has_row) {
+    // the upstream terms of the backward, only when the gradient is wanted
+    // (a forward-only loss evaluation has no sums to fill)
+    if (has_row && a.acc != nullptr && L > 0) {
 #pragma unroll
         for (int q = 0; q < HALF; ++q) {
             float gn0, gd0, gn1, gd1;
+            gn0 = up[2 * q] * inv[2 * q];
+            gn1 = up[2 * q + 1] * inv[2 * q + 1];
             if (a.normalized) {
-                gn0 = up[2 * q] / fmaxf(den[q].x, rho0);
-                gn1 = up[2 * q + 1] / fmaxf(den[q].y, rho0);
                 gd0 = den[q].x >= rho0 ? -vt[2 * q] * gn0 : 0.f;
                 gd1 = den[q].y >= rho0 ? -vt[2 * q + 1] * gn1 : 0.f;
             } else {
-                gn0 = up[2 * q]; gn1 = up[2 * q + 1]; gd0 = 0.f; gd1 = 0.f;
+                gd0 = 0.f; gd1 = 0.f;
             }
             s_g[row * HALF + q] = make_float4(gn0, gn1, gd0, gd1);
         }
@@ -290,7 +331,7 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
         const int cnt = min(CH, L - c0);
         if (ch != nchunks - 1) {
             __syncthreads();
-            stage_chunk<NT>(a, s0, c0, cnt, s_rec, s_msk, tid);
+            stage_chunk<NT, CH>(a, s0, c0, cnt, s_rec, s_msk, tid);
             __syncthreads();
         }
         // candidates c = sub-brick * CH + j: tasks come out sub-brick-major,

@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--sampled-n", type=int, default=1024, help="grid edge of the sampled workload (1024 or 512)")
     ap.add_argument("--prop-iters", type=int, default=200, help="refinement iterations per proposal evaluation")
     ap.add_argument("--pair-iters", type=int, default=500, help="refinement iterations behind the proposal's pairs")
+    ap.add_argument("--cal-iters", type=int, default=150,
+                    help="refinement iterations that judge the pairs proposal's step size")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
     ap.add_argument("--ttp-iters", type=int, default=2000, help="full schedule of the time-to-PSNR run (0 = skip)")
@@ -397,8 +399,11 @@ def run_proposal(args):
     same way.  Training set: 64 seeded 256^3 GRF fields with 25,000
     Gaussians each.  (a) the allocation -> refined pairs trainer: features of
     each analytic allocation against the change that --pair-iters refinement
-    iterations made to a and log s (targets scaled by their spreads); (b) the
-    end-to-end trainer through the encoder's loss.  Held out: 4 seeded 512^3
+    iterations made to a and log s (targets scaled by their spreads), then one
+    step size for its corrections chosen by the PSNR that --cal-iters
+    refinement iterations reach on 8 training fields (zero, the plain
+    allocation, among the candidates); (b) the end-to-end trainer through the
+    encoder's loss.  Held out: 4 seeded 512^3
     fields with 200,000 Gaussians, refined --prop-iters iterations from plain,
     (a)-corrected and (b)-corrected allocations.  Time-to-PSNR: wall time from
     the start of the allocation (features and MLP included) to the first
@@ -425,6 +430,7 @@ def run_proposal(args):
     Ts, tscale = proposal.scale_targets(T)
     m_pairs = proposal.Proposal(dev, seed=0)
     log_pairs = m_pairs.train(X, Ts, epochs=20, lr=1e-3, tscale=tscale)
+    cal = m_pairs.calibrate(tr[:8], 25_000, iters=args.cal_iters, seed=args.seed)
     torch.cuda.synchronize()
     train_pairs_s = time.perf_counter() - t0
     del tr, allocs, X, T, Ts
@@ -486,9 +492,11 @@ def run_proposal(args):
            "config": {"workload": "proposal_train_64x256^3_N25000_eval_4x512^3_N200000", "trunc_k": 3.0,
                       "value_is": "the allocation -> refined pairs trainer",
                       "pairs_trainer": f"targets from {args.pair_iters} refinement iterations, scaled by their "
-                                       "spreads, 20 epochs, batch 4096, lr 1e-3",
+                                       "spreads, 20 epochs, batch 4096, lr 1e-3; step size judged by "
+                                       f"{args.cal_iters} refinement iterations on 8 training fields",
                       "e2e_trainer": "through the encoder loss, 30 epochs, 4 fields per Adam step, lr 3e-3"},
            "judge": judge,
+           "calibration": {"gamma": m_pairs.gamma, "mean_psnr_by_gamma": {str(k): v for k, v in cal.items()}},
            "psnr": {k: {str(m): float(mean[k][m]) for m in marks} for k in kinds},
            "alloc_ms": ams, "train_s": {"pairs": train_pairs_s, "e2e": train_e2e_s},
            "train_loss_first_last": {"pairs": [log_pairs.losses[0], log_pairs.losses[-1]],

@@ -537,7 +537,7 @@ GVE_API gve_status gve_peak_bench(int32_t kind, int64_t iters, double* ops_per_s
  * fixed device footprint after start-up, no allocator locks on the call
  * path); the paper has no counterpart.  Same arguments and result as
  * gve_evaluate, without a context.  All scratch lives in one fixed
- * file-scope device array of the library (about 10 MB, held by every GPU
+ * file-scope device array of the library (about 7 MB, held by every GPU
  * that loads the library until the process exits).
  *   prims_dev      [n][12] float32, n <= GVE_NOALLOC_MAX_PRIMS.
  *   dims           at most GVE_NOALLOC_MAX_BRICKS bricks of 8^3, axes up to
@@ -548,7 +548,9 @@ GVE_API gve_status gve_peak_bench(int32_t kind, int64_t iters, double* ops_per_s
  * array and the launches are the current device's); GVE_E_INVALID otherwise.
  * Returns GVE_E_INVALID for sizes beyond the limits (before any launch), and
  * GVE_E_CAPACITY when the (brick, Gaussian) pair count, found on the device,
- * exceeds GVE_NOALLOC_MAX_PAIRS (the output is then not written).  The call
+ * exceeds GVE_NOALLOC_MAX_PAIRS, or the binning's (tile, Gaussian) pairs
+ * (tiles of 4^3 bricks) exceed 16 x GVE_NOALLOC_MAX_PRIMS (the output is then
+ * not written).  The call
  * synchronises `stream` to read that count.  The first call on a device
  * resolves the array's address with that device current; make it before any
  * stream capture (a cudaDeviceReset invalidates the resolved address).  All

@@ -30,8 +30,6 @@
 
 namespace gve {
 
-void launch_exscan_u32(const uint32_t* in, long long n, unsigned long long* out, void* scanp, cudaStream_t s);
-
 namespace {
 
 // ---------------- Philox4x32-10 (Salmon et al., SC'11) ----------------

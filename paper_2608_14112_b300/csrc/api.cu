@@ -87,6 +87,8 @@ __global__ void k_reset_state(DevState* st)
 {
     st->total = 0;
     st->max_total = 0;
+    st->total1 = 0;
+    st->max_total1 = 0;
     st->overflow = 0;
     st->first_overflow_iter = INT_MAX;
     st->err = 0;
@@ -153,7 +155,7 @@ gve_status read_state(Call& k, DevState* out)
     return GVE_OK;
 }
 
-// per-Gaussian and per-brick scratch
+// per-Gaussian, per-tile and per-brick scratch
 gve_status size_static(Call& k)
 {
     gve_ctx* c = k.c;
@@ -161,47 +163,65 @@ gve_status size_static(Call& k)
     GVE_TRY(ensure(c, c->rec, sizeof(float4) * 3 * n, k.s));
     GVE_TRY(ensure(c, c->binrec, sizeof(BinRec) * n, k.s));
     GVE_TRY(ensure(c, c->counts, sizeof(uint32_t) * n, k.s));
-    GVE_TRY(ensure(c, c->bmask, sizeof(uint32_t) * kMaskChunks * n, k.s));
     GVE_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * (n + 1), k.s));
     GVE_TRY(ensure(c, c->acc, sizeof(float) * 12 * n, k.s));
     GVE_TRY(ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, k.s));
+    GVE_TRY(ensure(c, c->trange, sizeof(uint32_t) * 2 * k.g.ntiles, k.s));
+    GVE_TRY(ensure(c, c->bcount, sizeof(uint32_t) * k.g.nbricks, k.s));
+    GVE_TRY(ensure(c, c->boff, sizeof(unsigned long long) * (k.g.nbricks + 1), k.s));
     GVE_TRY(ensure(c, c->ranges, sizeof(uint32_t) * 2 * k.g.nbricks, k.s));
     GVE_TRY(ensure(c, c->part, sizeof(double2) * (k.g.nbricks + 1024), k.s));
     return GVE_OK;
 }
 
-gve_status grow_pairs(Call& k, unsigned long long need)
+namespace {
+unsigned long long grown(unsigned long long need)
+{
+    unsigned long long cap = need + need / 4 + 65536;
+    return cap > 0xFFFFFFFFull ? 0xFFFFFFFFull : cap;
+}
+}  // namespace
+
+gve_status grow_pairs(Call& k, unsigned long long need1, unsigned long long need2)
 {
     gve_ctx* c = k.c;
-    if (need <= c->cap && c->keys[0].p) return GVE_OK;
-    unsigned long long cap = need + need / 4 + 65536;
-    if (cap > 0xFFFFFFFFull) cap = 0xFFFFFFFFull;
-    if (need > cap) return fail(c, GVE_E_CAPACITY, "more than 2^32 brick pairs");
-    for (int b = 0; b < 2; ++b) {
-        GVE_TRY(ensure(c, c->keys[b], sizeof(uint32_t) * cap, k.s));
-        GVE_TRY(ensure(c, c->vals[b], sizeof(uint32_t) * cap, k.s));
+    if (need1 > c->cap1 || !c->keys[0].p) {
+        const unsigned long long cap = grown(need1);
+        if (need1 > cap) return fail(c, GVE_E_CAPACITY, "more than 2^32 tile pairs");
+        for (int b = 0; b < 2; ++b) {
+            GVE_TRY(ensure(c, c->keys[b], sizeof(uint32_t) * cap, k.s));
+            GVE_TRY(ensure(c, c->vals[b], sizeof(uint32_t) * cap, k.s));
+        }
+        GVE_TRY(ensure(c, c->tmask, sizeof(unsigned long long) * cap, k.s));
+        GVE_TRY(ensure(c, c->hist, sizeof(uint32_t) * 256 * ((cap + kSortTile - 1) / kSortTile + 1), k.s));
+        c->cap1 = cap;
     }
-    GVE_TRY(ensure(c, c->hist, sizeof(uint32_t) * 256 * ((cap + kSortTile - 1) / kSortTile + 1), k.s));
-    c->cap = cap;
+    if (need2 > c->cap || !c->pairs.p) {
+        const unsigned long long cap = grown(need2);
+        if (need2 > cap) return fail(c, GVE_E_CAPACITY, "more than 2^32 brick pairs");
+        GVE_TRY(ensure(c, c->pairs, sizeof(uint32_t) * cap, k.s));
+        c->cap = cap;
+    }
     return GVE_OK;
 }
 
-// prep + count + scan, synchronise and size the pair buffers
+// sizing: the binning runs until both pair buffers hold its totals (three
+// runs at most: tile pairs, then brick pairs, are found too large)
 gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
 {
     gve_ctx* c = k.c;
     GVE_TRY(size_static(k));
-    reset_state(k);
-    launch_prep(prims, k.n, k.g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, k.s);
-    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, (uint32_t*)c->bmask.p,
-                 k.s);
-    launch_offsets((uint32_t*)c->counts.p, k.n, (unsigned long long*)c->offsets.p, c->scanp.p, dstate(c),
-                   ~0ull, 0, k.s);
-    c->launches += k.n > 0 ? 6 : 4;
-    GVE_CUDA(cudaGetLastError(), "launch (sizing)");
-    DevState h;
-    GVE_TRY(read_state(k, &h));
-    GVE_TRY(grow_pairs(k, h.total));
+    GVE_TRY(grow_pairs(k, 0, 0));
+    for (int run = 0; run < 3; ++run) {
+        reset_state(k);
+        GVE_TRY(bin_all(k, prims, o, 0));
+        DevState h;
+        GVE_TRY(read_state(k, &h));
+        if (!h.overflow) break;
+        const bool tiles = h.total1 > c->cap1;
+        GVE_TRY(grow_pairs(k, h.total1, tiles ? 0 : h.total));
+        if (!tiles) break;  // the brick total was complete: both sizes known
+    }
     // test hook: a logical pair capacity below what the binning needs, to
     // exercise the overflow detection and replay of refinement
     if (const char* tc = getenv("GVE_TEST_PAIR_CAP")) {
@@ -212,24 +232,39 @@ gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
     return GVE_OK;
 }
 
-// full binning: prep, count, offsets, emit, sort, ranges
-gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter)
+BinBufs bin_bufs(Call& k, uint32_t* gcount)
 {
     gve_ctx* c = k.c;
-    launch_prep(prims, k.n, k.g, o->trunc_k, (float4*)c->rec.p, (BinRec*)c->binrec.p, k.s);
-    launch_count((BinRec*)c->binrec.p, (float4*)c->rec.p, k.n, k.g, (uint32_t*)c->counts.p, (uint32_t*)c->bmask.p,
-                 k.s);
-    launch_offsets((uint32_t*)c->counts.p, k.n, (unsigned long long*)c->offsets.p, c->scanp.p, dstate(c), c->cap,
-                   iter, k.s);
-    launch_emit((BinRec*)c->binrec.p, (float4*)c->rec.p, (unsigned long long*)c->offsets.p, k.n, k.g,
-                (const uint32_t*)c->bmask.p, (uint32_t*)c->keys[0].p, (uint32_t*)c->vals[0].p, dstate(c), k.s);
-    uint32_t* kk[2] = {(uint32_t*)c->keys[0].p, (uint32_t*)c->keys[1].p};
-    uint32_t* vv[2] = {(uint32_t*)c->vals[0].p, (uint32_t*)c->vals[1].p};
-    k.sorted = launch_sort(kk, vv, dstate(c), c->cap, k.g.key_bits, (uint32_t*)c->hist.p, c->scanp.p, k.s);
-    uint32_t* start = (uint32_t*)c->ranges.p;
-    GVE_CUDA(cudaMemsetAsync(start, 0, sizeof(uint32_t) * 2 * k.g.nbricks, k.s), "memset ranges");
-    launch_ranges(kk[k.sorted], dstate(c), c->cap, start, start + k.g.nbricks, k.s);
-    c->launches += (k.n > 0 ? 3 : 0) + 4 + 5 * ((k.g.key_bits + 7) / 8) + 1;
+    BinBufs b{};
+    b.rec = (float4*)c->rec.p;
+    b.br = (BinRec*)c->binrec.p;
+    b.tcount = (uint32_t*)c->counts.p;
+    b.toff = (unsigned long long*)c->offsets.p;
+    b.scanp = c->scanp.p;
+    for (int i = 0; i < 2; ++i) {
+        b.tkeys[i] = (uint32_t*)c->keys[i].p;
+        b.tvals[i] = (uint32_t*)c->vals[i].p;
+    }
+    b.hist = (uint32_t*)c->hist.p;
+    b.tmask = (unsigned long long*)c->tmask.p;
+    b.cap1 = c->cap1;
+    b.trange = (uint32_t*)c->trange.p;
+    b.bcount = (uint32_t*)c->bcount.p;
+    b.boff = (unsigned long long*)c->boff.p;
+    b.ranges = (uint32_t*)c->ranges.p;
+    b.pairs = (uint32_t*)c->pairs.p;
+    b.cap = c->cap;
+    b.gcount = gcount;
+    b.st = dstate(c);
+    return b;
+}
+
+// full binning: prep, tile pairs and their sort, brick counts, ranges and
+// the brick pairs
+gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter, uint32_t* gcount)
+{
+    gve_ctx* c = k.c;
+    c->launches += launch_binning(bin_bufs(k, gcount), prims, k.n, k.g, o->trunc_k, iter, k.s);
     GVE_CUDA(cudaGetLastError(), "launch (binning)");
     return GVE_OK;
 }
@@ -241,7 +276,7 @@ BrickArgs brick_args(Call& k, const gve_eval_opts* o)
     a.g = k.g;
     a.start = (const uint32_t*)c->ranges.p;
     a.end = a.start + k.g.nbricks;
-    a.gids = (const uint32_t*)c->vals[k.sorted].p;
+    a.gids = (const uint32_t*)c->pairs.p;
     a.rec = (const float4*)c->rec.p;
     a.part = (double2*)c->part.p;
     a.st = dstate(c);
@@ -261,7 +296,6 @@ gve_status begin(gve_ctx* c, Call& k, int64_t n, gve_dims d, const gve_eval_opts
     k.s = (cudaStream_t)stream;
     k.n = n;
     k.g = make_geom(d, o->brick);
-    k.sorted = 0;
     c->launches = 0;
     GVE_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     GVE_TRY(ensure(c, c->state, sizeof(DevState), k.s));
@@ -319,8 +353,8 @@ void gve_ctx_destroy(gve_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->bmask, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
-                   &c->vals[0], &c->vals[1], &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
+    Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
+                   &c->vals[0], &c->vals[1], &c->tmask, &c->trange, &c->bcount, &c->boff, &c->pairs, &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
                    &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace,
                    &c->s_hi, &c->s_mid, &c->s_cnt, &c->s_off, &c->s_pts, &c->s_cell, &c->s_order, &c->s_nd,
                    &c->s_gg, &c->s_loss, &c->s_inv, &c->s_ex, &c->s_terms, &c->s_ccnt, &c->s_cand, &c->r_rec, &c->r_cnt, &c->r_off, &c->r_keys[0], &c->r_keys[1],
@@ -417,17 +451,16 @@ gve_status gve_bin(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const 
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
     GVE_TRY(size_pairs(k, prims, o));
-    GVE_TRY(bin_all(k, prims, o, 0));
+    GVE_TRY(bin_all(k, prims, o, 0, n > 0 ? counts : nullptr));
     DevState h;
     GVE_TRY(read_state(k, &h));
     *n_pairs = (int64_t)h.total;
     if (h.overflow) return fail(c, GVE_E_INTERNAL, "pair buffer sized by the sizing pass overflowed");
     if ((int64_t)h.total > cap) return fail(c, GVE_E_CAPACITY, "output capacity below the pair count");
-    if (n > 0) GVE_CUDA(cudaMemcpyAsync(counts, c->counts.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, k.s), "copy");
     if (h.total > 0) {
         if (!keys || !gids) return fail(c, GVE_E_INVALID, "null pair outputs");
-        GVE_CUDA(cudaMemcpyAsync(keys, c->keys[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
-        GVE_CUDA(cudaMemcpyAsync(gids, c->vals[k.sorted].p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
+        launch_fill_keys((const uint32_t*)c->ranges.p, k.g.nbricks, keys, k.s);
+        GVE_CUDA(cudaMemcpyAsync(gids, c->pairs.p, sizeof(uint32_t) * h.total, cudaMemcpyDeviceToDevice, k.s), "copy");
         k_strip_mask<<<4 * num_sms(), 256, 0, k.s>>>(gids, masks, h.total);
     }
     GVE_CUDA(cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint32_t) * 2 * k.g.nbricks, cudaMemcpyDeviceToDevice, k.s), "copy");
@@ -548,7 +581,7 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
         GVE_TRY(read_state(k, &h));
         if (h.overflow) {
             if (++retries > 8) return fail(c, GVE_E_CAPACITY, "pair count kept growing past capacity");
-            GVE_TRY(grow_pairs(k, h.max_total));
+            GVE_TRY(grow_pairs(k, h.max_total1, h.max_total));
             GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * nn, k.s), "memset acc");
             reset_state(k);
             it = h.first_overflow_iter;
@@ -587,7 +620,7 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
     if (h.overflow) {
         // the final evaluation alone overflowed: grow and redo it (untimed)
         fwd_timed = false;
-        GVE_TRY(grow_pairs(k, h.max_total));
+        GVE_TRY(grow_pairs(k, h.max_total1, h.max_total));
         reset_state(k);
         GVE_TRY(bin_all(k, prims, o, sc->iters));
         BrickArgs a = brick_args(k, o);

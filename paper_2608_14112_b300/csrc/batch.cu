@@ -185,8 +185,6 @@ gve_status setup_vols(gve_ctx* c, int nvol, const gve_volume* vols, float* prims
         vo.inv_m = 1.0 / ((double)vols[v].dims.nx * vols[v].dims.ny * vols[v].dims.nz);
         st = size_pairs(vo.k, vo.prims, o);
         if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
-        // the sorted pairs land in the buffer the radix passes end in
-        vo.k.sorted = ((vo.k.g.key_bits + 7) / 8) & 1;
         off += vols[v].n;
     }
     *ntot = off;
@@ -396,7 +394,9 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
             for (int v = 0; v < nvol; ++v) {
                 DevState h;
                 st = read_state(V[v].k, &h);
-                if (st == GVE_OK) st = grow_pairs(V[v].k, h.max_total > h.total ? h.max_total : h.total);
+                if (st == GVE_OK)
+                    st = grow_pairs(V[v].k, h.max_total1 > h.total1 ? h.max_total1 : h.total1,
+                                    h.max_total > h.total ? h.max_total : h.total);
                 if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
                 reset_state(V[v].k);
                 if (cudaStreamSynchronize(V[v].k.s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "sync");

@@ -1,14 +1,25 @@
 // bin.cu -- per-iteration preparation and the brick binner.
 //
 //   prep    one thread per Gaussian: activation of the Eq. 2 parameters,
-//           float32 keep-test coefficients, and the conservative brick cover.
-//   count   one warp per Gaussian: bricks of its box that pass the cover test.
-//   offsets exclusive scan of the counts (total checked against capacity).
-//   emit    one warp per Gaussian: (brick key, gid) pairs, Gaussian-major,
-//           bricks ascending (ballot + popc keeps the order).
+//           float32 keep-test coefficients, the conservative brick cover and
+//           the number of tiles (kTile^3 bricks) its brick box touches.
+//   stage 1 the (tile, Gaussian) pairs, Gaussian-major (exclusive scan of the
+//           tile counts, one warp per 32 Gaussians over their flattened tile
+//           boxes), stably sorted by tile key: every tile lists its Gaussians
+//           in ascending order.
+//   stage 2 one CTA per tile: the brick cover test on the bricks of each
+//           listed Gaussian's box inside the tile (a 64-bit pass mask per
+//           listed Gaussian, per-brick counts); the counts' exclusive scan
+//           over all bricks in key order gives each brick its [start, end);
+//           a second pass ranks every listed Gaussian within every brick it
+//           passes (earlier listed Gaussians that pass it) and writes the
+//           pair -- Gaussian index and sub-brick cover -- at start + rank.
+//   The result is the (brick, Gaussian) list sorted by brick key and, within
+//   a brick, by Gaussian index: what a stable sort of all brick pairs gives,
+//   without sorting them.
 //   sort    stable LSD radix sort, 8-bit digits, reduce-then-scan with a
-//           per-warp match_any ranking in the scatter.
-//   ranges  per-brick [start, end) by adjacent difference.
+//           per-warp match_any ranking in the scatter (stage 1, and the ray
+//           marcher's cell pairs).
 //
 // Bit-exactness: the keep-test coefficients and the brick cover are computed
 // with explicitly rounded float32 operations (__fmul_rn & co., no
@@ -29,6 +40,11 @@ BinGeom make_geom(gve_dims d, int B)
     int bits = 1;
     while ((1ll << bits) < g.nbricks) ++bits;
     g.key_bits = bits;
+    g.ntx = (g.nbx + kTile - 1) / kTile; g.nty = (g.nby + kTile - 1) / kTile; g.ntz = (g.nbz + kTile - 1) / kTile;
+    g.ntiles = (long long)g.ntx * g.nty * g.ntz;
+    bits = 1;
+    while ((1ll << bits) < g.ntiles) ++bits;
+    g.tkey_bits = bits;
     return g;
 }
 
@@ -38,7 +54,8 @@ BinGeom make_geom(gve_dims d, int B)
 // BIN = false: the keep coefficients only (the sampled path has no bricks)
 template <bool BIN>
 __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, long long n, BinGeom g,
-                                              float k, float4* __restrict__ rec, BinRec* __restrict__ br)
+                                              float k, float4* __restrict__ rec, BinRec* __restrict__ br,
+                                              uint32_t* __restrict__ tcount)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -100,21 +117,22 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
     }
     float4* o = rec + 3 * i;
     o[0] = r0; o[1] = r1; o[2] = r2;
-    if (BIN) br[i] = b;
+    if (BIN) {
+        br[i] = b;
+        uint32_t nt = 0;
+        if (b.nonempty)
+            nt = (uint32_t)(b.bhi[0] / kTile - b.blo[0] / kTile + 1) * (uint32_t)(b.bhi[1] / kTile - b.blo[1] / kTile + 1) *
+                 (uint32_t)(b.bhi[2] / kTile - b.blo[2] / kTile + 1);
+        tcount[i] = nt;
+    }
 }
 
-void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec, BinRec* br,
-                 cudaStream_t s)
-{
-    if (n <= 0) return;
-    k_prep<true><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, br);
-}
 
 void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cudaStream_t s)
 {
     if (n <= 0) return;
     BinGeom g{};
-    k_prep<false><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, nullptr);
+    k_prep<false><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, nullptr, nullptr);
 }
 
 // float32 cover test of one brick (same operation order as the oracle)
@@ -148,12 +166,12 @@ struct AxisGram {
     float g01, g02, g11, g12, g22;
 };
 
-__device__ __forceinline__ AxisGram axis_gram(const BinRec& b)
+__device__ __forceinline__ AxisGram axis_gram(const float* L)
 {
     AxisGram G{0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float l0 = b.L[j * 3 + 0], l1 = b.L[j * 3 + 1], l2 = b.L[j * 3 + 2];
+        const float l0 = L[j * 3 + 0], l1 = L[j * 3 + 1], l2 = L[j * 3 + 2];
         G.g01 = fmaf(l0, l1, G.g01);
         G.g02 = fmaf(l0, l2, G.g02);
         G.g11 = fmaf(l1, l1, G.g11);
@@ -176,7 +194,7 @@ __device__ __forceinline__ AxisGram axis_gram(const BinRec& b)
 // axis-aligned whitened bound of the brick test adds almost nothing here.)
 // Sub-bricks outside the grid get no bit.  Conservative: it never drops a
 // pair the keep test keeps.
-__device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, const AxisGram& G, float mux, float muy,
+__device__ __forceinline__ uint32_t subbrick_mask(const float* L, float K2, const AxisGram& G, float mux, float muy,
                                                   float muz, int B, int bx, int by, int bz, int ny, int nz)
 {
     const float hb = 0.5f * (float)(B - 1);
@@ -187,14 +205,14 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, const AxisGra
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, yy = 0.f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float yc = fmaf(b.L[j * 3 + 2], dcz, fmaf(b.L[j * 3 + 1], dcy, b.L[j * 3 + 0] * dcx));
-        c0 = fmaf(yc, b.L[j * 3 + 0], c0);
-        c1 = fmaf(yc, b.L[j * 3 + 1], c1);
-        c2 = fmaf(yc, b.L[j * 3 + 2], c2);
+        const float yc = fmaf(L[j * 3 + 2], dcz, fmaf(L[j * 3 + 1], dcy, L[j * 3 + 0] * dcx));
+        c0 = fmaf(yc, L[j * 3 + 0], c0);
+        c1 = fmaf(yc, L[j * 3 + 1], c1);
+        c2 = fmaf(yc, L[j * 3 + 2], c2);
         yy = fmaf(yc, yc, yy);
     }
     const float oyv = 0.25f * (float)B, ozv = 0.125f * (float)B;
-    const float K2m = b.K2 * 1.001f;
+    const float K2m = K2 * 1.001f;
     uint32_t m = 0;
 #pragma unroll
     for (int yh = 0; yh < 2; ++yh) {
@@ -217,159 +235,6 @@ __device__ __forceinline__ uint32_t subbrick_mask(const BinRec& b, const AxisGra
         }
     }
     return m;
-}
-
-// ------------------------------------------------------------------------
-// count / emit (one warp per Gaussian)
-// ------------------------------------------------------------------------
-// Bricks of a Gaussian's box in z-major order; the box has fewer than 2^31
-// bricks, so 32-bit index arithmetic suffices.  The pass/fail ballots of the
-// first kMaskChunks x 32 bricks are kept for the emission pass.
-// Division by the box extents: for boxes of fewer than 2^24 bricks a float
-// reciprocal gives the quotient to within one (relative error below 2^-23 on
-// quotients below 2^23; divisor 1 is exact), and one exact integer step
-// corrects it; larger boxes use integer division.
-struct BoxIdx {
-    uint32_t ex, exy;
-    float iex, iexy;
-    bool fast;
-};
-
-__device__ __forceinline__ BoxIdx box_idx(uint32_t ex, uint32_t exy, uint32_t tot)
-{
-    BoxIdx d;
-    d.ex = ex;
-    d.exy = exy;
-    d.iex = 1.f / (float)ex;
-    d.iexy = 1.f / (float)exy;
-    d.fast = tot < (1u << 24);
-    return d;
-}
-
-__device__ __forceinline__ uint32_t udiv_small(uint32_t t, uint32_t d, float id)
-{
-    int q = (int)__fmul_rn((float)t, id);
-    const int r = (int)t - q * (int)d;
-    if (r < 0) --q;
-    else if (r >= (int)d) ++q;
-    return (uint32_t)q;
-}
-
-__device__ __forceinline__ void box_brick(const BinRec& b, uint32_t t, const BoxIdx& d, int& bx, int& by, int& bz)
-{
-    uint32_t zq, yq;
-    if (d.fast) {
-        zq = udiv_small(t, d.exy, d.iexy);
-        yq = udiv_small(t - zq * d.exy, d.ex, d.iex);
-    } else {
-        zq = t / d.exy;
-        yq = (t - zq * d.exy) / d.ex;
-    }
-    const uint32_t r = t - zq * d.exy;
-    bx = b.blo[0] + (int)(r - yq * d.ex);
-    by = b.blo[1] + (int)yq;
-    bz = b.blo[2] + (int)zq;
-}
-
-__global__ void __launch_bounds__(256) k_count(const BinRec* __restrict__ br, const float4* __restrict__ rec,
-                                               long long n, BinGeom g, uint32_t* __restrict__ counts,
-                                               uint32_t* __restrict__ bmask)
-{
-    const int lane = threadIdx.x & 31;
-    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = wid; i < n; i += nw) {
-        const BinRec b = br[i];
-        uint32_t cnt = 0;
-        if (b.nonempty) {
-            const float4 r0 = rec[3 * i];
-            const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
-            const uint32_t exy = ex * ey, tot = exy * ez;
-        const BoxIdx D = box_idx(ex, exy, tot);
-            for (uint32_t t0 = 0, c = 0; t0 < tot; t0 += 32, ++c) {
-                const uint32_t t = t0 + lane;
-                bool pass = false;
-                if (t < tot) {
-                    int bx, by, bz;
-                    box_brick(b, t, D, bx, by, bz);
-                    pass = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                cnt += __popc(bal);
-                if (c < kMaskChunks && lane == 0) bmask[kMaskChunks * i + c] = bal;
-            }
-        }
-        if (lane == 0) counts[i] = cnt;
-    }
-}
-
-// One warp per Gaussian.  The listed bricks of its box are queued in box
-// order in shared memory and processed 32 at a time, so that every lane
-// computes a sub-brick cover (the costly part) instead of only the lanes
-// whose brick passed; pair i of the Gaussian goes to offsets[g] + i.
-__global__ void __launch_bounds__(256) k_emit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
-                                              const unsigned long long* __restrict__ offsets, long long n,
-                                              BinGeom g, const uint32_t* __restrict__ bmask,
-                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                              const DevState* __restrict__ st)
-{
-    if (st->overflow) return;
-    __shared__ uint32_t s_q[8][64];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t* q = s_q[w];
-    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = wid; i < n; i += nw) {
-        const BinRec b = br[i];
-        if (!b.nonempty) continue;
-        const float4 r0 = rec[3 * i];
-        const AxisGram G = axis_gram(b);
-        unsigned long long base = offsets[i];
-        const uint32_t ex = b.bhi[0] - b.blo[0] + 1, ey = b.bhi[1] - b.blo[1] + 1, ez = b.bhi[2] - b.blo[2] + 1;
-        const uint32_t exy = ex * ey, tot = exy * ez;
-        const BoxIdx D = box_idx(ex, exy, tot);
-        // write the first m queued bricks (m <= 32) as pairs base .. base + m - 1
-        auto flush = [&](uint32_t m) {
-            if ((uint32_t)lane < m) {
-                int bx, by, bz;
-                box_brick(b, q[lane], D, bx, by, bz);
-                const uint32_t key = (uint32_t)(((long long)bz * g.nby + by) * g.nbx + bx);
-                const uint32_t mask = subbrick_mask(b, G, r0.x, r0.y, r0.z, g.B, bx, by, bz, g.ny, g.nz);
-                keys[base + lane] = key;
-                vals[base + lane] = (uint32_t)i | (mask << kGidBits);
-            }
-            base += m;
-        };
-        uint32_t qn = 0;
-        for (uint32_t t0 = 0, c = 0; t0 < tot; t0 += 32, ++c) {
-            const uint32_t t = t0 + lane;
-            unsigned bal;
-            if (c < kMaskChunks) {
-                bal = bmask[kMaskChunks * i + c];
-            } else {
-                bool p = false;
-                if (t < tot) {
-                    int bx, by, bz;
-                    box_brick(b, t, D, bx, by, bz);
-                    p = brick_test(b, r0.x, r0.y, r0.z, g.B, bx, by, bz);
-                }
-                bal = __ballot_sync(0xffffffffu, p);
-            }
-            if ((bal >> lane) & 1u) q[qn + __popc(bal & lt)] = t;
-            qn += __popc(bal);
-            __syncwarp();
-            if (qn >= 32) {
-                flush(32);
-                __syncwarp();
-                if ((uint32_t)lane < qn - 32) q[lane] = q[32 + lane];
-                qn -= 32;
-                __syncwarp();
-            }
-        }
-        flush(qn);
-        __syncwarp();
-    }
 }
 
 // ------------------------------------------------------------------------
@@ -421,9 +286,9 @@ __device__ __forceinline__ T block_incl_scan(T v, T* smem /* 32 */, T* total)
 
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const TI* __restrict__ in, LenSpec L,
-                                                              TO* __restrict__ part, const DevState* st)
+                                                              TO* __restrict__ part, const int* stop)
 {
-    if (st && st->overflow) return;
+    if (stop && *stop) return;
     __shared__ TO sm[32];
     unsigned long long len = L.get();
     unsigned long long chunk = (len + gridDim.x - 1) / gridDim.x;
@@ -438,9 +303,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const TI* __restri
 
 template <typename TO>
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(TO* __restrict__ part, int nb, TO* total_out,
-                                                           const DevState* st)
+                                                           const int* stop)
 {
-    if (st && st->overflow) return;
+    if (stop && *stop) return;
     __shared__ TO sm[32];
     TO v = threadIdx.x < nb ? part[threadIdx.x] : TO(0);
     TO tot;
@@ -451,9 +316,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(TO* __restrict__ part
 
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const TI* in, TO* out, LenSpec L,
-                                                            const TO* __restrict__ part, const DevState* st)
+                                                            const TO* __restrict__ part, const int* stop)
 {
-    if (st && st->overflow) return;
+    if (stop && *stop) return;
     __shared__ TO sm[32];
     unsigned long long len = L.get();
     unsigned long long chunk = (len + gridDim.x - 1) / gridDim.x;
@@ -470,11 +335,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const TI* in, TO* ou
     }
 }
 
-__global__ void k_check_cap(DevState* st, const unsigned long long* total, unsigned long long cap, int iter)
+// pair total of a binning stage (0: brick pairs -> total, 1: tile pairs ->
+// total1) against its capacity; the first iteration to exceed it is kept
+__global__ void k_check_cap(DevState* st, const unsigned long long* total, unsigned long long cap, int iter, int stage)
 {
-    unsigned long long t = *total;
-    st->total = t;
-    if (t > st->max_total) st->max_total = t;
+    const unsigned long long t = *total;
+    unsigned long long& tot = stage ? st->total1 : st->total;
+    unsigned long long& mx = stage ? st->max_total1 : st->max_total;
+    tot = t;
+    if (t > mx) mx = t;
     if (t > cap && !st->overflow) {
         st->overflow = 1;
         st->first_overflow_iter = iter;
@@ -482,14 +351,14 @@ __global__ void k_check_cap(DevState* st, const unsigned long long* total, unsig
 }
 
 void launch_offsets(const uint32_t* counts, long long n, unsigned long long* offsets, void* scanp, DevState* st,
-                    unsigned long long cap, int iter, cudaStream_t s)
+                    unsigned long long cap, int iter, cudaStream_t s, int stage)
 {
     LenSpec L{nullptr, 0, (unsigned long long)n};
     auto* part = reinterpret_cast<unsigned long long*>(scanp);
     k_scan_reduce<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(counts, L, part, nullptr);
     k_scan_top<unsigned long long><<<1, kScanThreads, 0, s>>>(part, kScanBlocks, offsets + n, nullptr);
     k_scan_down<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(counts, offsets, L, part, nullptr);
-    k_check_cap<<<1, 1, 0, s>>>(st, offsets + n, cap, iter);
+    k_check_cap<<<1, 1, 0, s>>>(st, offsets + n, cap, iter, stage);
 }
 
 void launch_exscan_u32(const uint32_t* in, long long n, unsigned long long* out, void* scanp, cudaStream_t s)
@@ -501,46 +370,23 @@ void launch_exscan_u32(const uint32_t* in, long long n, unsigned long long* out,
     k_scan_down<uint32_t, unsigned long long><<<kScanBlocks, kScanThreads, 0, s>>>(in, out, L, part, nullptr);
 }
 
-static int emit_blocks(long long n)
-{
-    long long warps = n;
-    long long blocks = (warps * 32 + 255) / 256;
-    if (blocks > 64LL * num_sms()) blocks = 64LL * num_sms();
-    if (blocks < 1) blocks = 1;
-    return (int)blocks;
-}
-
-void launch_count(const BinRec* br, const float4* rec, long long n, const BinGeom& g, uint32_t* counts,
-                  uint32_t* bmask, cudaStream_t s)
-{
-    if (n <= 0) return;
-    k_count<<<emit_blocks(n), 256, 0, s>>>(br, rec, n, g, counts, bmask);
-}
-
-void launch_emit(const BinRec* br, const float4* rec, const unsigned long long* offsets, long long n,
-                 const BinGeom& g, const uint32_t* bmask, uint32_t* keys, uint32_t* vals, const DevState* st,
-                 cudaStream_t s)
-{
-    if (n <= 0) return;
-    k_emit<<<emit_blocks(n), 256, 0, s>>>(br, rec, offsets, n, g, bmask, keys, vals, st);
-}
-
 // ------------------------------------------------------------------------
 // stable LSD radix sort
 // ------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long sort_len(const DevState* st, unsigned long long cap)
+__device__ __forceinline__ unsigned long long sort_len(const unsigned long long* n_dev, unsigned long long cap)
 {
-    unsigned long long t = st->total;
+    const unsigned long long t = *n_dev;
     return t < cap ? t : cap;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys, const DevState* st,
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys, const unsigned long long* n_dev,
+                                                          const int* stop,
                                                           unsigned long long cap, int shift,
                                                           uint32_t* __restrict__ hist)
 {
-    if (st->overflow) return;
+    if (*stop) return;
     __shared__ uint32_t h[256];
-    unsigned long long n = sort_len(st, cap);
+    unsigned long long n = sort_len(n_dev, cap);
     unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         h[threadIdx.x] = 0;
@@ -585,10 +431,11 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
 __global__ void __launch_bounds__(kSortThreads, 3) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                             const DevState* st, unsigned long long cap, int shift,
+                                                             const unsigned long long* n_dev, const int* stop,
+                                                             unsigned long long cap, int shift,
                                                              const uint32_t* __restrict__ hist)
 {
-    if (st->overflow) return;
+    if (*stop) return;
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t wcnt[W][256];     // per-warp digit counts, then per-warp local offsets
     __shared__ uint32_t dstart[256];      // tile-local start of each digit
@@ -597,7 +444,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rs_scatter(const uint32_t* 
     __shared__ uint32_t wsum[W];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long n = sort_len(st, cap);
+    unsigned long long n = sort_len(n_dev, cap);
     unsigned long long ntiles = (n + kSortTile - 1) / kSortTile;
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
@@ -679,8 +526,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rs_scatter(const uint32_t* 
     }
 }
 
-int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsigned long long cap, int key_bits,
-                uint32_t* hist, void* scanp, cudaStream_t s)
+int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const unsigned long long* n_dev, const int* stop,
+                unsigned long long cap, int key_bits, uint32_t* hist, void* scanp, cudaStream_t s)
 {
     static_assert(kSortThreads == 256, "one thread per digit in the scatter");
     int passes = (key_bits + 7) / 8;
@@ -692,12 +539,12 @@ int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsign
     auto* part = reinterpret_cast<uint32_t*>(scanp);
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        k_rs_hist<<<grid, kSortThreads, 0, s>>>(keys[cur], st, cap, shift, hist);
-        LenSpec L{&st->total, cap, 0};
-        k_scan_reduce<uint32_t, uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(hist, L, part, st);
-        k_scan_top<uint32_t><<<1, kScanThreads, 0, s>>>(part, kScanBlocks, nullptr, st);
-        k_scan_down<uint32_t, uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(hist, hist, L, part, st);
-        k_rs_scatter<<<grid, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], st, cap,
+        k_rs_hist<<<grid, kSortThreads, 0, s>>>(keys[cur], n_dev, stop, cap, shift, hist);
+        LenSpec L{n_dev, cap, 0};
+        k_scan_reduce<uint32_t, uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(hist, L, part, stop);
+        k_scan_top<uint32_t><<<1, kScanThreads, 0, s>>>(part, kScanBlocks, nullptr, stop);
+        k_scan_down<uint32_t, uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(hist, hist, L, part, stop);
+        k_rs_scatter<<<grid, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_dev, stop, cap,
                                                    shift, hist);
         cur ^= 1;
     }
@@ -710,12 +557,13 @@ int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsign
 // Per-brick [start, end) of the sorted keys: each thread takes four
 // consecutive keys (one vector load; the key buffer is 256-byte aligned) and
 // compares them with their neighbours.
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ sk, const DevState* st,
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ sk, const unsigned long long* n_dev,
+                                                const int* stop,
                                                 unsigned long long cap, uint32_t* __restrict__ start,
                                                 uint32_t* __restrict__ end)
 {
-    if (st->overflow) return;
-    const unsigned long long n = sort_len(st, cap);
+    if (*stop) return;
+    const unsigned long long n = sort_len(n_dev, cap);
     const unsigned long long ng = (n + 3) / 4;
     for (unsigned long long gi = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; gi < ng;
          gi += (unsigned long long)gridDim.x * blockDim.x) {
@@ -740,10 +588,387 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ sk,
     }
 }
 
-void launch_ranges(const uint32_t* skeys, const DevState* st, unsigned long long cap, uint32_t* start,
-                   uint32_t* end, cudaStream_t s)
+void launch_ranges(const uint32_t* skeys, const unsigned long long* n_dev, const int* stop, unsigned long long cap,
+                   uint32_t* start, uint32_t* end, cudaStream_t s)
 {
-    k_ranges<<<16 * num_sms(), 256, 0, s>>>(skeys, st, cap, start, end);
+    k_ranges<<<16 * num_sms(), 256, 0, s>>>(skeys, n_dev, stop, cap, start, end);
+}
+
+
+// ------------------------------------------------------------------------
+// two-level binning: stage 1 (tiles) and stage 2 (bricks)
+// ------------------------------------------------------------------------
+// Owner of flattened item `it` among a warp's 32 entries: the first j whose
+// inclusive item count exceeds it (incl is non-decreasing, it < incl[31]).
+__device__ __forceinline__ int flat_owner(const uint32_t* incl, uint32_t it)
+{
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (incl[j + step - 1] <= it) j += step;
+    return j;
+}
+
+// Stage 1 emission: warp = 32 consecutive Gaussians; their tile boxes are
+// flattened (box-major, z-major inside a box) and handed out 32 items at a
+// time, so small and large boxes keep every lane busy.  The group's pairs
+// start at the scanned offset of its first Gaussian.
+__global__ void __launch_bounds__(256) k_temit(const BinRec* __restrict__ br, const uint32_t* __restrict__ tcount,
+                                               const unsigned long long* __restrict__ toff, long long n, BinGeom g,
+                                               uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
+                                               const DevState* __restrict__ st)
+{
+    if (st->overflow) return;
+    __shared__ uint32_t s_incl[8][32];
+    __shared__ int4 s_box[8][32];      // first tile (x, y, z) and x extent of each box
+    __shared__ uint32_t s_exy[8][32];  // x extent * y extent
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long ngroups = (n + 31) >> 5;
+    for (long long grp = (long long)blockIdx.x * 8 + w; grp < ngroups; grp += (long long)gridDim.x * 8) {
+        const long long i = (grp << 5) + lane;
+        uint32_t cnt = 0, exy = 1;
+        int4 box = make_int4(0, 0, 0, 1);
+        if (i < n) {
+            cnt = tcount[i];
+            if (cnt) {
+                const BinRec& b = br[i];
+                const int x0 = b.blo[0] / kTile, y0 = b.blo[1] / kTile, z0 = b.blo[2] / kTile;
+                const int ex = b.bhi[0] / kTile - x0 + 1, ey = b.bhi[1] / kTile - y0 + 1;
+                box = make_int4(x0, y0, z0, ex);
+                exy = (uint32_t)ex * (uint32_t)ey;
+            }
+        }
+        const uint32_t incl = warp_incl_scan(cnt);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        s_incl[w][lane] = incl;
+        s_box[w][lane] = box;
+        s_exy[w][lane] = exy;
+        __syncwarp();
+        const unsigned long long base = total ? toff[grp << 5] : 0ull;
+        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+            const uint32_t it = t0 + lane;
+            if (it < total) {
+                const int j = flat_owner(s_incl[w], it);
+                const uint32_t t = it - (j ? s_incl[w][j - 1] : 0u);
+                const int4 bx = s_box[w][j];
+                const uint32_t e2 = s_exy[w][j];
+                const uint32_t tz = t / e2, r = t - tz * e2;
+                const uint32_t ty = r / (uint32_t)bx.w, tx = r - ty * (uint32_t)bx.w;
+                tkeys[base + it] =
+                    (uint32_t)(((long long)(bx.z + (int)tz) * g.nty + (bx.y + (int)ty)) * g.ntx + (bx.x + (int)tx));
+                tvals[base + it] = (uint32_t)((grp << 5) + j);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void tile_origin(const BinGeom& g, long long tile, int& ox, int& oy, int& oz)
+{
+    ox = (int)(tile % g.ntx) * kTile;
+    oy = (int)((tile / g.ntx) % g.nty) * kTile;
+    oz = (int)(tile / ((long long)g.ntx * g.nty)) * kTile;
+}
+
+// Stage 2, first pass (one 256-thread CTA per tile): the cover test on the
+// bricks of each listed Gaussian's box inside the tile, flattened per warp
+// like stage 1.  Writes the 64-bit pass mask of every listed Gaussian (bit =
+// (z * 4 + y) * 4 + x of the brick inside the tile), the pair count of each
+// brick of the tile, and, when gcount is set, adds each Gaussian's passes to
+// gcount (introspection).
+__global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, const float4* __restrict__ rec,
+                                                const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
+                                                BinGeom g, unsigned long long* __restrict__ tmask,
+                                                uint32_t* __restrict__ bcount, uint32_t* __restrict__ gcount,
+                                                const DevState* __restrict__ st)
+{
+    if (st->overflow) return;
+    __shared__ BinRec s_br[256];
+    __shared__ float4 s_mu[256];
+    __shared__ uint32_t s_m[256][2];
+    __shared__ uint32_t s_cnt[64];
+    __shared__ uint32_t s_incl[8][32];
+    __shared__ int4 s_box[8][32];      // first brick (x, y, z) inside the tile and x extent
+    __shared__ uint32_t s_exy[8][32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long tile = blockIdx.x;
+    int ox, oy, oz;
+    tile_origin(g, tile, ox, oy, oz);
+    if (tid < 64) s_cnt[tid] = 0u;
+    __syncthreads();
+    const uint32_t ts = trange[tile], te = trange[g.ntiles + tile];
+    for (uint32_t r0 = ts; r0 < te; r0 += 256) {
+        const uint32_t e = r0 + tid;
+        uint32_t cnt = 0, exy = 1, gid = 0;
+        int4 box = make_int4(0, 0, 0, 1);
+        s_m[tid][0] = 0u;
+        s_m[tid][1] = 0u;
+        if (e < te) {
+            gid = tgid[e];
+            const BinRec b = br[gid];
+            s_br[tid] = b;
+            s_mu[tid] = rec[3 * (size_t)gid];
+            const int lx = max(b.blo[0], ox) - ox, hx = min(b.bhi[0], ox + kTile - 1) - ox;
+            const int ly = max(b.blo[1], oy) - oy, hy = min(b.bhi[1], oy + kTile - 1) - oy;
+            const int lz = max(b.blo[2], oz) - oz, hz = min(b.bhi[2], oz + kTile - 1) - oz;
+            if (lx <= hx && ly <= hy && lz <= hz) {
+                const int ex = hx - lx + 1, ey = hy - ly + 1;
+                box = make_int4(lx, ly, lz, ex);
+                exy = (uint32_t)(ex * ey);
+                cnt = exy * (uint32_t)(hz - lz + 1);
+            }
+        }
+        const uint32_t incl = warp_incl_scan(cnt);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        s_incl[w][lane] = incl;
+        s_box[w][lane] = box;
+        s_exy[w][lane] = exy;
+        __syncwarp();
+        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+            const uint32_t it = t0 + lane;
+            if (it < total) {
+                const int j = flat_owner(s_incl[w], it);
+                const uint32_t t = it - (j ? s_incl[w][j - 1] : 0u);
+                const int4 bx = s_box[w][j];
+                const uint32_t e2 = s_exy[w][j];
+                const uint32_t cz = t / e2, r = t - cz * e2;
+                const uint32_t cy = r / (uint32_t)bx.w, cx = r - cy * (uint32_t)bx.w;
+                const int lx = bx.x + (int)cx, ly = bx.y + (int)cy, lz = bx.z + (int)cz;
+                const int slot = (w << 5) + j;
+                const float4 mu = s_mu[slot];
+                if (brick_test(s_br[slot], mu.x, mu.y, mu.z, g.B, ox + lx, oy + ly, oz + lz)) {
+                    const int lb = (lz * kTile + ly) * kTile + lx;
+                    atomicOr(&s_m[slot][lb >> 5], 1u << (lb & 31));
+                    atomicAdd(&s_cnt[lb], 1u);
+                }
+            }
+        }
+        __syncwarp();
+        if (e < te) {
+            const uint32_t m0 = s_m[tid][0], m1 = s_m[tid][1];
+            tmask[e] = ((unsigned long long)m1 << 32) | m0;
+            if (gcount) atomicAdd(&gcount[gid], (uint32_t)(__popc(m0) + __popc(m1)));
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (tid < 64) {
+        const int bx = ox + (tid & 3), by = oy + ((tid >> 2) & 3), bz = oz + (tid >> 4);
+        if (bx < g.nbx && by < g.nby && bz < g.nbz) bcount[((long long)bz * g.nby + by) * g.nbx + bx] = s_cnt[tid];
+    }
+}
+
+// Stage 2 ranges from the scanned brick counts: [start, end) per brick, 0,0
+// for an empty brick; the total is checked against the pair capacity.
+__global__ void __launch_bounds__(256) k_brick_ranges(const uint32_t* __restrict__ bcount,
+                                                      const unsigned long long* __restrict__ boff, long long nbricks,
+                                                      uint32_t* __restrict__ start, uint32_t* __restrict__ end,
+                                                      DevState* st, unsigned long long cap, int iter)
+{
+    if (st->overflow) return;  // an earlier stage overflowed: the counts are stale
+    const unsigned long long total = boff[nbricks];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->total = total;
+        if (total > st->max_total) st->max_total = total;
+        if (total > cap) {
+            st->overflow = 1;
+            st->first_overflow_iter = iter;
+        }
+    }
+    if (total > cap) return;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nbricks;
+         b += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = bcount[b];
+        const uint32_t s0 = c ? (uint32_t)boff[b] : 0u;
+        start[b] = s0;
+        end[b] = c ? s0 + c : 0u;
+    }
+}
+
+// what the second pass needs of a listed Gaussian (19 words: an odd stride,
+// so consecutive slots fall in distinct banks)
+struct SubRec {
+    float L[9];
+    float K2;
+    float mx, my, mz;
+    AxisGram G;
+    uint32_t gid;
+};
+
+// Stage 2, second pass (one 256-thread CTA per tile): rounds of 256 listed
+// Gaussians (warp w holds list entries 32 w .. 32 w + 31 of the round).  Per
+// brick of the tile, each warp counts its entries that pass it (ballots);
+// the per-warp counts are scanned in warp order on top of the previous
+// rounds' counts, so an entry's rank in a brick is the number of earlier
+// list entries passing that brick.  Passing (entry, brick) pairs are queued
+// brick-major in shared memory and written 32 at a time, each lane computing
+// one pair's sub-brick cover.
+__global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
+                                               const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
+                                               const unsigned long long* __restrict__ tmask,
+                                               const unsigned long long* __restrict__ boff, BinGeom g,
+                                               uint32_t* __restrict__ pairs, const DevState* __restrict__ st)
+{
+    if (st->overflow) return;
+    const long long tile = blockIdx.x;
+    const uint32_t ts = trange[tile], te = trange[g.ntiles + tile];
+    if (ts >= te) return;
+    __shared__ SubRec s_r[256];
+    __shared__ uint32_t s_start[64], s_run[64];
+    __shared__ uint32_t s_wc[8][64];
+    __shared__ uint32_t s_qpos[8][64];
+    __shared__ uint16_t s_qjb[8][64];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int ox, oy, oz;
+    tile_origin(g, tile, ox, oy, oz);
+    if (tid < 64) {
+        const int bx = ox + (tid & 3), by = oy + ((tid >> 2) & 3), bz = oz + (tid >> 4);
+        s_run[tid] = 0u;
+        s_start[tid] = (bx < g.nbx && by < g.nby && bz < g.nbz)
+                           ? (uint32_t)boff[((long long)bz * g.nby + by) * g.nbx + bx]
+                           : 0u;
+    }
+    // write the first m queued pairs (m <= 32)
+    auto flush = [&](uint32_t m) {
+        if ((uint32_t)lane < m) {
+            const uint32_t jb = s_qjb[w][lane];
+            const SubRec& q = s_r[(w << 5) + (jb >> 6)];
+            const int lb = (int)(jb & 63u);
+            const uint32_t mask = subbrick_mask(q.L, q.K2, q.G, q.mx, q.my, q.mz, g.B, ox + (lb & 3),
+                                                oy + ((lb >> 2) & 3), oz + (lb >> 4), g.ny, g.nz);
+            pairs[s_qpos[w][lane]] = q.gid | (mask << kGidBits);
+        }
+    };
+    for (uint32_t r0 = ts; r0 < te; r0 += 256) {
+        const uint32_t e = r0 + tid;
+        uint32_t m0 = 0u, m1 = 0u;
+        if (e < te) {
+            const unsigned long long m = tmask[e];
+            m0 = (uint32_t)m;
+            m1 = (uint32_t)(m >> 32);
+            if (m) {
+                const uint32_t gid = tgid[e];
+                const BinRec b = br[gid];
+                const float4 mu = rec[3 * (size_t)gid];
+                SubRec& q = s_r[tid];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) q.L[j] = b.L[j];
+                q.K2 = b.K2;
+                q.mx = mu.x;
+                q.my = mu.y;
+                q.mz = mu.z;
+                q.G = axis_gram(b.L);
+                q.gid = gid;
+            }
+        }
+        s_wc[w][lane] = 0u;
+        s_wc[w][lane + 32] = 0u;
+        __syncwarp();
+        const uint32_t o0 = __reduce_or_sync(0xffffffffu, m0), o1 = __reduce_or_sync(0xffffffffu, m1);
+        for (uint32_t mm = o0; mm; mm &= mm - 1) {
+            const int b = __ffs(mm) - 1;
+            const unsigned bal = __ballot_sync(0xffffffffu, (m0 >> b) & 1u);
+            if (lane == 0) s_wc[w][b] = __popc(bal);
+        }
+        for (uint32_t mm = o1; mm; mm &= mm - 1) {
+            const int b = __ffs(mm) - 1;
+            const unsigned bal = __ballot_sync(0xffffffffu, (m1 >> b) & 1u);
+            if (lane == 0) s_wc[w][32 + b] = __popc(bal);
+        }
+        __syncthreads();
+        if (tid < 64) {
+            uint32_t run = s_run[tid];
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) {
+                const uint32_t c = s_wc[ww][tid];
+                s_wc[ww][tid] = run;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        uint32_t qn = 0;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const uint32_t mine = half ? m1 : m0;
+            for (uint32_t mm = half ? o1 : o0; mm; mm &= mm - 1) {
+                const int bb = __ffs(mm) - 1, b = bb + 32 * half;
+                const bool has = (mine >> bb) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, has);
+                if (has) {
+                    const uint32_t rk = __popc(bal & lt);
+                    s_qpos[w][qn + rk] = s_start[b] + s_wc[w][b] + rk;
+                    s_qjb[w][qn + rk] = (uint16_t)((lane << 6) | b);
+                }
+                qn += __popc(bal);
+                __syncwarp();
+                if (qn >= 32) {
+                    flush(32);
+                    __syncwarp();
+                    if ((uint32_t)lane < qn - 32) {
+                        s_qpos[w][lane] = s_qpos[w][lane + 32];
+                        s_qjb[w][lane] = s_qjb[w][lane + 32];
+                    }
+                    qn -= 32;
+                    __syncwarp();
+                }
+            }
+        }
+        flush(qn);
+        __syncthreads();
+    }
+}
+
+// fills keys[start, end) with the brick key of every non-empty brick
+// (introspection: the sorted key column of the pair list)
+__global__ void k_fill_keys(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end, long long nbricks,
+                            uint32_t* __restrict__ keys)
+{
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nbricks;
+         b += (long long)gridDim.x * blockDim.x)
+        for (uint32_t p = start[b]; p < end[b]; ++p) keys[p] = (uint32_t)b;
+}
+
+void launch_fill_keys(const uint32_t* ranges, long long nbricks, uint32_t* keys, cudaStream_t s)
+{
+    k_fill_keys<<<4 * num_sms(), 256, 0, s>>>(ranges, ranges + nbricks, nbricks, keys);
+}
+
+int launch_binning(const BinBufs& b, const float* prims, long long n, const BinGeom& g, float k, int iter,
+                   cudaStream_t s)
+{
+    DevState* st = b.st;
+    int launches = 0;
+    if (n > 0) {
+        k_prep<true><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, b.rec, b.br, b.tcount);
+        ++launches;
+    }
+    launch_offsets(b.tcount, n, b.toff, b.scanp, st, b.cap1, iter, s, 1);
+    launches += 4;
+    if (n > 0) {
+        long long blocks = ((n + 31) / 32 + 7) / 8;
+        if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
+        k_temit<<<(unsigned)blocks, 256, 0, s>>>(b.br, b.tcount, b.toff, n, g, b.tkeys[0], b.tvals[0], st);
+        ++launches;
+    }
+    uint32_t* kk[2] = {b.tkeys[0], b.tkeys[1]};
+    uint32_t* vv[2] = {b.tvals[0], b.tvals[1]};
+    const int cur = launch_sort(kk, vv, &st->total1, &st->overflow, b.cap1, g.tkey_bits, b.hist, b.scanp, s);
+    launches += 5 * ((g.tkey_bits + 7) / 8);
+    cudaMemsetAsync(b.trange, 0, sizeof(uint32_t) * 2 * (size_t)g.ntiles, s);
+    launch_ranges(kk[cur], &st->total1, &st->overflow, b.cap1, b.trange, b.trange + g.ntiles, s);
+    ++launches;
+    if (b.gcount && n > 0) cudaMemsetAsync(b.gcount, 0, sizeof(uint32_t) * (size_t)n, s);
+    k_bcount<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, g, b.tmask, b.bcount, b.gcount, st);
+    launch_exscan_u32(b.bcount, g.nbricks, b.boff, b.scanp, s);
+    long long rb = (g.nbricks + 255) / 256;
+    if (rb > 8LL * num_sms()) rb = 8LL * num_sms();
+    k_brick_ranges<<<(unsigned)rb, 256, 0, s>>>(b.bcount, b.boff, g.nbricks, b.ranges, b.ranges + g.nbricks, st,
+                                                b.cap, iter);
+    k_bemit<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.boff, g, b.pairs, st);
+    launches += 6;
+    return launches;
 }
 
 }  // namespace gve

@@ -10,9 +10,12 @@
 //   bin record      20 words per Gaussian: whitening L (row-major 3x3),
 //                   brick half-extent bound e[3], threshold K2, brick box
 //                   lo[3] / hi[3], non-empty flag.
-//   pair list       keys (brick index, z-major) and values (Gaussian index in
-//                   the low 24 bits, 8-bit sub-brick mask above), uint32,
-//                   double-buffered for the radix sort.
+//   tile pairs      (tile key, Gaussian index) uint32 pairs, double-buffered
+//                   for the radix sort, and a 64-bit brick pass mask per
+//                   sorted pair (tile = kTile^3 bricks).
+//   brick pairs     uint32 per pair, sorted by brick key then Gaussian index:
+//                   Gaussian index in the low 24 bits, 8-bit sub-brick mask
+//                   above.
 //   ranges          uint32 start[nbricks], end[nbricks].
 //   accumulators    float[12] per Gaussian: A = sum G gn, H = sum h, S1' (3),
 //                   S2' (6: xx yy zz xy xz yz), 0 -- the per-Gaussian sums of
@@ -36,6 +39,8 @@ constexpr double kNegHalfLog2e = -0.72134752044448170367996234050095;
 // sorted pair values: Gaussian index in the low 24 bits, sub-brick mask above
 constexpr int kGidBits = 24;
 constexpr uint32_t kGidMask = (1u << kGidBits) - 1u;
+// bricks per tile edge of the two-level binning (64 bricks: one 64-bit mask)
+constexpr int kTile = 4;
 
 struct __align__(16) BinRec {
     float L[9];
@@ -49,8 +54,10 @@ static_assert(sizeof(BinRec) == 80, "bin record is 20 words");
 
 // Device-side state of one call: pair totals and the sticky overflow flag.
 struct DevState {
-    unsigned long long total;        // pairs of the current binning
+    unsigned long long total;        // brick pairs of the current binning
     unsigned long long max_total;    // largest total seen since reset
+    unsigned long long total1;       // tile pairs of the current binning
+    unsigned long long max_total1;   // largest total1 seen since reset
     int overflow;                    // sticky: an iteration needed more than cap pairs
     int first_overflow_iter;         // first iteration that overflowed
     int err;                         // internal consistency error
@@ -71,9 +78,13 @@ struct Buf {
 struct gve_ctx {
     int device = 0;
     std::string err;
-    gve::Buf rec, binrec, counts, bmask, offsets, acc, adam;
-    gve::Buf keys[2], vals[2];
-    uint64_t cap = 0;                // pair capacity of keys/vals
+    gve::Buf rec, binrec, counts, offsets, acc, adam;
+    gve::Buf keys[2], vals[2];       // tile pairs (radix double buffer)
+    gve::Buf tmask, trange;          // brick pass mask per sorted tile pair; per-tile ranges
+    uint64_t cap1 = 0;               // tile-pair capacity
+    gve::Buf bcount, boff;           // per-brick pair counts and their exclusive scan
+    gve::Buf pairs;                  // brick pairs in brick order
+    uint64_t cap = 0;                // brick-pair capacity
     gve::Buf hist, scanp;
     gve::Buf ranges, part;
     gve::Buf state;
@@ -284,30 +295,58 @@ struct BinGeom {
     int nx, ny, nz, B, nbx, nby, nbz;
     long long nbricks;
     int key_bits;
+    int ntx, nty, ntz;         // tiles of kTile^3 bricks
+    long long ntiles;
+    int tkey_bits;
 };
 BinGeom make_geom(gve_dims d, int B);
 
-void launch_prep(const float* prims, long long n, const BinGeom& g, float k, float4* rec,
-                 BinRec* br, cudaStream_t s);
-// the keep coefficients alone (same values as launch_prep's rec)
+// the keep coefficients alone (same values as the binning's rec)
 void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cudaStream_t s);
-// per Gaussian: number of listed bricks, and the pass ballots of the first
-// kMaskChunks x 32 bricks of its box (reused by the emission pass)
-constexpr int kMaskChunks = 4;
-void launch_count(const BinRec* br, const float4* rec, long long n, const BinGeom& g, uint32_t* counts,
-                  uint32_t* bmask, cudaStream_t s);
-// exclusive scan of counts into offsets[0..n], total into st->total / max_total,
-// sets st->overflow when total > cap (iteration index `iter`).
+// exclusive scan of counts into offsets[0..n]; the total goes to st->total
+// (stage 0) or st->total1 (stage 1) and their maxima, and sets st->overflow
+// when total > cap (iteration index `iter`).
 void launch_offsets(const uint32_t* counts, long long n, unsigned long long* offsets, void* scanp,
-                    DevState* st, unsigned long long cap, int iter, cudaStream_t s);
-void launch_emit(const BinRec* br, const float4* rec, const unsigned long long* offsets, long long n,
-                 const BinGeom& g, const uint32_t* bmask, uint32_t* keys, uint32_t* vals, const DevState* st,
-                 cudaStream_t s);
-// Stable LSD radix sort of (keys, vals) by key; result ends in keys[out], vals[out].
-int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const DevState* st, unsigned long long cap,
-                int key_bits, uint32_t* hist, void* scanp, cudaStream_t s);
-void launch_ranges(const uint32_t* skeys, const DevState* st, unsigned long long cap,
+                    DevState* st, unsigned long long cap, int iter, cudaStream_t s, int stage = 0);
+// exclusive scan of n uint32 into out[0..n] (out[n] = total)
+void launch_exscan_u32(const uint32_t* in, long long n, unsigned long long* out, void* scanp, cudaStream_t s);
+// Stable LSD radix sort of (keys, vals) by key; the element count is read
+// on the device (min(*n_dev, cap)); nothing runs while *stop is set.  The
+// result ends in keys[out], vals[out].
+int launch_sort(uint32_t* keys[2], uint32_t* vals[2], const unsigned long long* n_dev, const int* stop,
+                unsigned long long cap, int key_bits, uint32_t* hist, void* scanp, cudaStream_t s);
+void launch_ranges(const uint32_t* skeys, const unsigned long long* n_dev, const int* stop, unsigned long long cap,
                    uint32_t* start, uint32_t* end, cudaStream_t s);
+
+// Scratch of one brick binning (see bin.cu): per Gaussian, per tile pair,
+// per tile, per brick and per brick pair.
+struct BinBufs {
+    float4* rec;                  // [n][3] keep coefficients
+    BinRec* br;                   // [n]
+    uint32_t* tcount;             // [n] tiles of each Gaussian's brick box
+    unsigned long long* toff;     // [n + 1] their exclusive scan
+    void* scanp;                  // [kScanBlocks] scan partials
+    uint32_t* tkeys[2];           // [cap1] tile keys (radix double buffer)
+    uint32_t* tvals[2];           // [cap1] Gaussian indices
+    uint32_t* hist;               // radix histograms for cap1 elements
+    unsigned long long* tmask;    // [cap1] brick pass mask per sorted tile pair
+    unsigned long long cap1;
+    uint32_t* trange;             // [2][ntiles]
+    uint32_t* bcount;             // [nbricks]
+    unsigned long long* boff;     // [nbricks + 1]
+    uint32_t* ranges;             // [2][nbricks] start, end (0, 0 = empty)
+    uint32_t* pairs;              // [cap] brick pairs in brick order
+    unsigned long long cap;
+    uint32_t* gcount;             // [n] brick pairs per Gaussian, or nullptr
+    DevState* st;
+};
+// Issues the whole binning on s without host synchronisation and returns
+// the kernels launched.  Tile pairs above cap1 or brick pairs above cap set
+// st->overflow (st->first_overflow_iter = iter) and skip the rest.
+int launch_binning(const BinBufs& b, const float* prims, long long n, const BinGeom& g, float k, int iter,
+                   cudaStream_t s);
+// keys[p] = brick of pair p, from the ranges (introspection)
+void launch_fill_keys(const uint32_t* ranges, long long nbricks, uint32_t* keys, cudaStream_t s);
 
 // ---- launchers (field.cu) ------------------------------------------------
 enum BrickMode { kModeEval = 0, kModeLoss = 1, kModeBwd = 2, kModeCount = 3 };
@@ -447,18 +486,19 @@ struct Call {
     cudaStream_t s;
     BinGeom g;
     long long n;
-    int sorted;  // which buffer holds the sorted pairs
 };
 DevState* dstate(gve_ctx* c);
 gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o);
 gve_status begin(gve_ctx* c, Call& k, int64_t n, gve_dims d, const gve_eval_opts* o, void* stream);
 gve_status reset_state(Call& k);
 gve_status read_state(Call& k, DevState* out);
-gve_status grow_pairs(Call& k, unsigned long long need);
+// grows the tile-pair (need1) and brick-pair (need2) buffers
+gve_status grow_pairs(Call& k, unsigned long long need1, unsigned long long need2);
 // per-Gaussian/per-brick scratch + sizing pass (synchronises k.s)
 gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o);
-// prep, count, offsets, emit, sort, ranges (stream-ordered, no host sync)
-gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter);
+// the whole binning (stream-ordered, no host sync); gcount (nullable):
+// brick pairs per Gaussian
+gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter, uint32_t* gcount = nullptr);
 BrickArgs brick_args(Call& k, const gve_eval_opts* o);
 
 }  // namespace gve

@@ -5,16 +5,17 @@
 // footprint after start-up, or a caller that has to run without taking the
 // allocator's locks.  gve_evaluate_noalloc serves them: it takes the same
 // inputs and output as gve_evaluate, needs no context, and keeps all of its
-// scratch (prepared records, brick pairs, sort buffers, ranges, device state)
-// in one fixed file-scope device array.  That array is part of the library
+// scratch (prepared records, tile and brick pairs, sort buffers, ranges,
+// device state) in one fixed file-scope device array.  That array is part of the library
 // image: every GPU that loads the library holds it (kScratchBytes) until the
 // process exits, whether or not the entry point is used.
 //
 // Limits (checked before any launch; larger requests get GVE_E_INVALID):
 //   primitives        <= GVE_NOALLOC_MAX_PRIMS   (8,192)
 //   bricks of 8^3     <= GVE_NOALLOC_MAX_BRICKS  (32,768, e.g. a 256^3 grid)
-//   (brick, Gaussian) pairs <= GVE_NOALLOC_MAX_PAIRS (524,288): data dependent,
-//   found on the device; a larger count returns GVE_E_CAPACITY and leaves the
+//   (brick, Gaussian) pairs <= GVE_NOALLOC_MAX_PAIRS (524,288) and (tile,
+//   Gaussian) pairs <= 131,072 (tiles of 4^3 bricks): data dependent, found
+//   on the device; a larger count returns GVE_E_CAPACITY and leaves the
 //   output unwritten.
 //
 // Set-up: the first call on a device (with that device current) resolves the
@@ -29,8 +30,8 @@
 // device.
 //
 // Sharing: every call uses the same array and finds the previous call's
-// contents there; the parts that must start at zero (the device state and the
-// per-brick ranges) are cleared by each call.  Calls whose work overlaps on
+// contents there; the part that must start at zero (the device state) is
+// cleared by each call, and the binning rewrites everything else it reads.  Calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on the array
 // and must be serialised by the caller.
 #include <atomic>
@@ -50,21 +51,29 @@ constexpr long long kNaPairs = GVE_NOALLOC_MAX_PAIRS;
 
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// tile pairs (stage 1 of the binning): up to 16 per primitive on average;
+// more return GVE_E_CAPACITY like the brick pairs
+constexpr long long kNaTilePairs = 16 * kNaPrims;
+
 // carve-up of the scratch array (byte offsets)
 constexpr size_t kOffState = 0;
 constexpr size_t kOffRec = align256(kOffState + sizeof(DevState));
 constexpr size_t kOffBin = align256(kOffRec + sizeof(float4) * 3 * kNaPrims);
-constexpr size_t kOffCounts = align256(kOffBin + sizeof(BinRec) * kNaPrims);
-constexpr size_t kOffBmask = align256(kOffCounts + sizeof(uint32_t) * kNaPrims);
-constexpr size_t kOffOffsets = align256(kOffBmask + sizeof(uint32_t) * kMaskChunks * kNaPrims);
-constexpr size_t kOffScan = align256(kOffOffsets + sizeof(unsigned long long) * (kNaPrims + 1));
-constexpr size_t kOffKeys0 = align256(kOffScan + sizeof(unsigned long long) * kScanBlocks);
-constexpr size_t kOffKeys1 = align256(kOffKeys0 + sizeof(uint32_t) * kNaPairs);
-constexpr size_t kOffVals0 = align256(kOffKeys1 + sizeof(uint32_t) * kNaPairs);
-constexpr size_t kOffVals1 = align256(kOffVals0 + sizeof(uint32_t) * kNaPairs);
-constexpr size_t kOffHist = align256(kOffVals1 + sizeof(uint32_t) * kNaPairs);
-constexpr size_t kOffRanges = align256(kOffHist + sizeof(uint32_t) * 256 * (kNaPairs / kSortTile + 1));
-constexpr size_t kScratchBytes = align256(kOffRanges + sizeof(uint32_t) * 2 * kNaBricks);
+constexpr size_t kOffTcount = align256(kOffBin + sizeof(BinRec) * kNaPrims);
+constexpr size_t kOffToff = align256(kOffTcount + sizeof(uint32_t) * kNaPrims);
+constexpr size_t kOffScan = align256(kOffToff + sizeof(unsigned long long) * (kNaPrims + 1));
+constexpr size_t kOffTkeys0 = align256(kOffScan + sizeof(unsigned long long) * kScanBlocks);
+constexpr size_t kOffTkeys1 = align256(kOffTkeys0 + sizeof(uint32_t) * kNaTilePairs);
+constexpr size_t kOffTvals0 = align256(kOffTkeys1 + sizeof(uint32_t) * kNaTilePairs);
+constexpr size_t kOffTvals1 = align256(kOffTvals0 + sizeof(uint32_t) * kNaTilePairs);
+constexpr size_t kOffHist = align256(kOffTvals1 + sizeof(uint32_t) * kNaTilePairs);
+constexpr size_t kOffTmask = align256(kOffHist + sizeof(uint32_t) * 256 * (kNaTilePairs / kSortTile + 1));
+constexpr size_t kOffTrange = align256(kOffTmask + sizeof(unsigned long long) * kNaTilePairs);
+constexpr size_t kOffBcount = align256(kOffTrange + sizeof(uint32_t) * 2 * kNaBricks);  // tiles <= bricks
+constexpr size_t kOffBoff = align256(kOffBcount + sizeof(uint32_t) * kNaBricks);
+constexpr size_t kOffRanges = align256(kOffBoff + sizeof(unsigned long long) * (kNaBricks + 1));
+constexpr size_t kOffPairs = align256(kOffRanges + sizeof(uint32_t) * 2 * kNaBricks);
+constexpr size_t kScratchBytes = align256(kOffPairs + sizeof(uint32_t) * kNaPairs);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -133,33 +142,38 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
     if (st != GVE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     DevState* dst = reinterpret_cast<DevState*>(base + kOffState);
-    float4* rec = reinterpret_cast<float4*>(base + kOffRec);
-    BinRec* br = reinterpret_cast<BinRec*>(base + kOffBin);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(base + kOffCounts);
-    uint32_t* bmask = reinterpret_cast<uint32_t*>(base + kOffBmask);
-    unsigned long long* offsets = reinterpret_cast<unsigned long long*>(base + kOffOffsets);
-    void* scanp = base + kOffScan;
-    uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(base + kOffKeys0), reinterpret_cast<uint32_t*>(base + kOffKeys1)};
-    uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(base + kOffVals0), reinterpret_cast<uint32_t*>(base + kOffVals1)};
-    uint32_t* hist = reinterpret_cast<uint32_t*>(base + kOffHist);
-    uint32_t* ranges = reinterpret_cast<uint32_t*>(base + kOffRanges);
+    BinBufs b{};
+    b.rec = reinterpret_cast<float4*>(base + kOffRec);
+    b.br = reinterpret_cast<BinRec*>(base + kOffBin);
+    b.tcount = reinterpret_cast<uint32_t*>(base + kOffTcount);
+    b.toff = reinterpret_cast<unsigned long long*>(base + kOffToff);
+    b.scanp = base + kOffScan;
+    b.tkeys[0] = reinterpret_cast<uint32_t*>(base + kOffTkeys0);
+    b.tkeys[1] = reinterpret_cast<uint32_t*>(base + kOffTkeys1);
+    b.tvals[0] = reinterpret_cast<uint32_t*>(base + kOffTvals0);
+    b.tvals[1] = reinterpret_cast<uint32_t*>(base + kOffTvals1);
+    b.hist = reinterpret_cast<uint32_t*>(base + kOffHist);
+    b.tmask = reinterpret_cast<unsigned long long*>(base + kOffTmask);
+    b.cap1 = (unsigned long long)kNaTilePairs;
+    b.trange = reinterpret_cast<uint32_t*>(base + kOffTrange);
+    b.bcount = reinterpret_cast<uint32_t*>(base + kOffBcount);
+    b.boff = reinterpret_cast<unsigned long long*>(base + kOffBoff);
+    b.ranges = reinterpret_cast<uint32_t*>(base + kOffRanges);
+    b.pairs = reinterpret_cast<uint32_t*>(base + kOffPairs);
+    b.cap = (unsigned long long)kNaPairs;
+    b.gcount = nullptr;
+    b.st = dst;
 
-    // the device state and the ranges must start at zero on every call
+    // the device state must start at zero on every call (the ranges are
+    // rewritten by every binning)
     if (cudaMemsetAsync(dst, 0, sizeof(DevState), s) != cudaSuccess) return GVE_E_CUDA;
-    const unsigned long long cap = (unsigned long long)kNaPairs;
-    launch_prep(prims, n, g, o->trunc_k, rec, br, s);
-    launch_count(br, rec, n, g, counts, bmask, s);
-    launch_offsets(counts, n, offsets, scanp, dst, cap, 0, s);
-    launch_emit(br, rec, offsets, n, g, bmask, keys[0], vals[0], dst, s);
-    const int out = launch_sort(keys, vals, dst, cap, g.key_bits, hist, scanp, s);
-    if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * g.nbricks, s) != cudaSuccess) return GVE_E_CUDA;
-    launch_ranges(keys[out], dst, cap, ranges, ranges + g.nbricks, s);
+    launch_binning(b, prims, n, g, o->trunc_k, 0, s);
     BrickArgs a{};
     a.g = g;
-    a.start = ranges;
-    a.end = ranges + g.nbricks;
-    a.gids = vals[out];
-    a.rec = rec;
+    a.start = b.ranges;
+    a.end = b.ranges + g.nbricks;
+    a.gids = b.pairs;
+    a.rec = b.rec;
     a.st = dst;
     a.T = (float)((double)o->trunc_k * (double)o->trunc_k * kNegHalfLog2e);
     a.rho0 = o->rho0;

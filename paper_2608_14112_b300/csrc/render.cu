@@ -470,8 +470,8 @@ gve_status gve_render_prepare(gve_ctx* c, const float* prims, int64_t n, gve_dim
     if (total > 0) {
         k_render_emit<<<nb, 256, 0, s>>>(prims, rec, n, o->trunc_k, g, off, kk[0], vv[0]);
         const int kb = key_bits_for(ncells);
-        const int sorted = launch_sort(kk, vv, st, cap, kb, (uint32_t*)c->r_hist.p, c->r_scanp.p, s);
-        launch_ranges(kk[sorted], st, cap, start, start + ncells, s);
+        const int sorted = launch_sort(kk, vv, &st->total, &st->overflow, cap, kb, (uint32_t*)c->r_hist.p, c->r_scanp.p, s);
+        launch_ranges(kk[sorted], &st->total, &st->overflow, cap, start, start + ncells, s);
         const unsigned gb = (unsigned)std::min<unsigned long long>((total + 255) / 256, 16ull * num_sms());
         k_render_gather<<<gb, 256, 0, s>>>(rec, vv[sorted], total, (float4*)c->r_crec.p);
         c->launches += 1 + 5 * ((kb + 7) / 8) + 1 + 1;

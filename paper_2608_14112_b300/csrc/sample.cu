@@ -582,7 +582,7 @@ gve_status full_grid_sse(gve_ctx* c, const float* prims, int64_t n, const float*
             *sse = h.sse[1];
             return GVE_OK;
         }
-        SMP_TRY(grow_pairs(k, h.max_total));
+        SMP_TRY(grow_pairs(k, h.max_total1, h.max_total));
         reset_state(k);
     }
     return fail(c, GVE_E_CAPACITY, "final evaluation overflowed");

@@ -9,7 +9,10 @@ encoder itself: features of an analytic allocation (Sec. III-E of arxiv
 2608.14112) against the change that full refinement made to a and log s.
 The last layer starts at zero, so an untrained model leaves the allocation
 unchanged -- plain allocation is the fallback, and refinement judges the
-result.
+result: after the regression, one step size for all corrections is chosen
+among a few candidates (zero, the plain allocation, included) by the PSNR
+that refinement reaches from the corrected allocations of training fields
+(``Proposal.calibrate``).
 """
 from __future__ import annotations
 
@@ -66,6 +69,10 @@ def features(field: torch.Tensor, prims: torch.Tensor, n_detail: int, gbar: floa
     return out
 
 
+# candidate step sizes of Proposal.calibrate (0 = plain allocation)
+CAL_GAMMAS = (0.0, 0.125, 0.25, 0.375, 0.5, 0.75, 1.0)
+
+
 @dataclass
 class TrainLog:
     losses: list
@@ -91,6 +98,7 @@ class Proposal:
         model[3 * P + 16: 3 * P + 32] = 1.0          # inverse standard deviation
         self.model = torch.from_numpy(model).to(self.device)
         self.step = 0
+        self.gamma = 1.0
         self._quantise()
 
     def _ctx(self):
@@ -160,6 +168,45 @@ class Proposal:
             gve._check(_lib().gve_mlp_fold_output_scale(c, _p(self.model), _p(tscale), gve._stream(self.device)),
                        c)
         return TrainLog(losses, epochs, R)
+
+    def scale_outputs(self, factors) -> None:
+        """Multiplies the network's four outputs by ``factors`` (folded into
+        the last layer by gve_mlp_fold_output_scale, BF16 copies refreshed)."""
+        sc = torch.as_tensor(factors, dtype=torch.float32, device=self.device).reshape(4).contiguous()
+        c = self._ctx()
+        gve._check(_lib().gve_mlp_fold_output_scale(c, _p(self.model), _p(sc), gve._stream(self.device)), c)
+
+    def calibrate(self, fields, budget: int, iters: int = 150, gammas=CAL_GAMMAS, seed: int = 0, lr: float = 1e-2,
+                  opts: gve.EvalOptions | None = None) -> dict:
+        """Step size of the corrections, judged by refinement itself.  For
+        each gamma the corrections gamma * (predicted change) are applied to
+        the analytic allocations of ``fields`` (seeds seed + i), all fields
+        are refined ``iters`` iterations together (gve_refine_batch), and the
+        gamma with the highest mean final PSNR is folded into the last layer;
+        gamma 0 is the plain allocation, so the result is never worse than
+        plain on these fields.  Returns {gamma: mean PSNR (dB)}."""
+        allocs, feats = [], []
+        for i, f in enumerate(fields):
+            Pv, info = gve.gve_allocate(f, budget, seed=seed + i)
+            allocs.append(Pv)
+            feats.append(features(f, Pv, info["n_detail"], info["gbar"]))
+        base = self.model.clone()
+        scores = {}
+        for gam in gammas:
+            Pc = [p.clone() for p in allocs]
+            if gam != 0.0:
+                self.model = base.clone()
+                self.scale_outputs([gam] * 4)
+                for f, x, p in zip(fields, feats, Pc):
+                    self.apply(x, p, f.shape)
+            psnr, _ = gve.gve_refine_batch(torch.cat(Pc, 0).contiguous(), fields, [budget] * len(fields), iters,
+                                           lr=lr, opts=opts)
+            scores[float(gam)] = float(np.mean(psnr))
+        best = max(scores, key=lambda g: (scores[g], -g))
+        self.model = base
+        self.scale_outputs([best] * 4)
+        self.gamma = best
+        return scores
 
     def apply(self, feats: torch.Tensor, prims: torch.Tensor, shape):
         """Correct the allocated records in place."""

@@ -2,9 +2,10 @@
 (4.3 GB) with 1,400,000 Gaussians, the size at which every throughput number
 is measured.
 
-Only this size exercises the 21-bit brick keys (three radix passes over about
-1.4e8 pairs in thousands of sort tiles), 2.1 M bricks, Gaussian lists of 1.4 M
-records and the allocator's selections over 10^9 voxels.  The FP64 oracle
+Only this size exercises the 21-bit brick keys (2.1 M bricks in 32,768 tiles
+of 4^3 bricks, about 1.4e8 brick pairs written from per-brick counts, over
+10^7 tile pairs sorted in thousands of radix-sort tiles), Gaussian lists of
+1.4 M records and the allocator's selections over 10^9 voxels.  The FP64 oracle
 cannot refine at this size, so it checks what it can compute exactly:
 
 * allocation (Sec. III-E, S1a-S1e): the split, distinct and eligible seeds,
@@ -140,7 +141,7 @@ def test_headline_field_and_gradients_after_refinement(headline):
     P = prims.clone()
     st = gve.gve_refine(P, V, iters=5, lr=1e-2)
     assert st["retries"] >= 0 and np.isfinite(st["psnr_final"])
-    assert st["brick_pairs"] > 50_000_000       # thousands of sort tiles, 21-bit keys: three radix passes
+    assert st["brick_pairs"] > 50_000_000       # 21-bit brick keys, tile lists over thousands of sort tiles
     moved = (P - prims).abs().max().item()
     assert moved > 1e-3
     _check_field_and_gradients(V, Vh, P, "refined")

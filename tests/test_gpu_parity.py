@@ -269,8 +269,9 @@ def test_brick_variants_bin_eval_grad(case, brick, chunk):
     assert rel_l2(gg2.cpu().numpy(), g) <= GRAD_TOL
 
 
-# sparse grids with more than 2^16 bricks: 17-18 key bits, so three radix
-# passes run, over many sort tiles (> 4,096 pairs each)
+# sparse grids with more than 2^16 bricks (17-18 bit brick keys): thousands
+# of tiles of 4^3 bricks, and tile lists spread over many radix-sort tiles
+# (more than 4,096 tile pairs)
 SCALE_CASES = {
     # name: (dims (nx, ny, nz), brick, n, s_lo, s_hi, seed)
     "b4_18bit": ((1040, 520, 16), 4, 6000, 0.6, 2.5, 31),
@@ -279,7 +280,7 @@ SCALE_CASES = {
 
 
 @pytest.mark.parametrize("case", list(SCALE_CASES))
-def test_binning_bit_exact_three_radix_passes(case):
+def test_binning_bit_exact_large_sparse_grids(case):
     dims, brick, n, lo, hi, seed = SCALE_CASES[case]
     nb = np.prod([(d + brick - 1) // brick for d in dims])
     assert nb > 2 ** 16

@@ -178,6 +178,26 @@ def test_trained_proposal_beats_plain_allocation():
         assert gain[5] > 0.0, gain
 
 
+def test_pairs_proposal_step_is_judged_by_refinement():
+    """The allocation -> refined pairs trainer and its refinement-judged step:
+    the chosen step's mean PSNR after refinement is the best of the
+    candidates, zero (the plain allocation) among them, and the folded
+    network predicts that multiple of its unscaled corrections."""
+    tr = [inputs.grf(96, seed=s, device="cuda") for s in range(300, 308)]
+    b = 96 ** 3 // 671
+    X, T = proposal.make_pairs(tr, b, iters=50, seed=0)
+    Ts, sc = proposal.scale_targets(T)
+    m = proposal.Proposal("cuda", seed=0)
+    m.train(X, Ts, epochs=10, lr=1e-3, tscale=sc)
+    y0 = m.forward(X[:512])
+    assert y0.abs().max().item() > 0
+    scores = m.calibrate(tr[:4], b, iters=30)
+    assert set(scores) == {float(g) for g in proposal.CAL_GAMMAS}
+    assert scores[m.gamma] == max(scores.values()) and scores[m.gamma] >= scores[0.0]
+    y1 = m.forward(X[:512])
+    torch.testing.assert_close(y1, m.gamma * y0, rtol=1e-2, atol=1e-5)
+
+
 def test_standardise_matches_column_moments():
     """gve_mlp_standardise: column means and sample spreads (ddof 1) of the
     training features, inverse spread 0 for a feature whose spread is at

@@ -167,6 +167,7 @@ gve_status size_static(Call& k)
     GVE_TRY(ensure(c, c->acc, sizeof(float) * 12 * n, k.s));
     GVE_TRY(ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, k.s));
     GVE_TRY(ensure(c, c->trange, sizeof(uint32_t) * 2 * k.g.ntiles, k.s));
+    GVE_TRY(ensure(c, c->cbase, sizeof(uint32_t) * 64 * cbase_chunks(c->cap1, k.g.ntiles), k.s));
     GVE_TRY(ensure(c, c->bcount, sizeof(uint32_t) * k.g.nbricks, k.s));
     GVE_TRY(ensure(c, c->boff, sizeof(unsigned long long) * (k.g.nbricks + 1), k.s));
     GVE_TRY(ensure(c, c->ranges, sizeof(uint32_t) * 2 * k.g.nbricks, k.s));
@@ -175,9 +176,12 @@ gve_status size_static(Call& k)
 }
 
 namespace {
-unsigned long long grown(unsigned long long need)
+// capacity for `need` pairs plus headroom for Gaussians that grow during
+// refinement: 1/4 for brick pairs, 1/1 for the ten times fewer tile pairs
+// (whose count follows the boxes' volume more steeply)
+unsigned long long grown(unsigned long long need, bool tiles)
 {
-    unsigned long long cap = need + need / 4 + 65536;
+    unsigned long long cap = need + (tiles ? need : need / 4) + 65536;
     return cap > 0xFFFFFFFFull ? 0xFFFFFFFFull : cap;
 }
 }  // namespace
@@ -186,18 +190,19 @@ gve_status grow_pairs(Call& k, unsigned long long need1, unsigned long long need
 {
     gve_ctx* c = k.c;
     if (need1 > c->cap1 || !c->keys[0].p) {
-        const unsigned long long cap = grown(need1);
+        const unsigned long long cap = grown(need1, true);
         if (need1 > cap) return fail(c, GVE_E_CAPACITY, "more than 2^32 tile pairs");
         for (int b = 0; b < 2; ++b) {
             GVE_TRY(ensure(c, c->keys[b], sizeof(uint32_t) * cap, k.s));
             GVE_TRY(ensure(c, c->vals[b], sizeof(uint32_t) * cap, k.s));
         }
         GVE_TRY(ensure(c, c->tmask, sizeof(unsigned long long) * cap, k.s));
+        GVE_TRY(ensure(c, c->cbase, sizeof(uint32_t) * 64 * cbase_chunks(cap, k.g.ntiles), k.s));
         GVE_TRY(ensure(c, c->hist, sizeof(uint32_t) * 256 * ((cap + kSortTile - 1) / kSortTile + 1), k.s));
         c->cap1 = cap;
     }
     if (need2 > c->cap || !c->pairs.p) {
-        const unsigned long long cap = grown(need2);
+        const unsigned long long cap = grown(need2, false);
         if (need2 > cap) return fail(c, GVE_E_CAPACITY, "more than 2^32 brick pairs");
         GVE_TRY(ensure(c, c->pairs, sizeof(uint32_t) * cap, k.s));
         c->cap = cap;
@@ -247,6 +252,7 @@ BinBufs bin_bufs(Call& k, uint32_t* gcount)
     }
     b.hist = (uint32_t*)c->hist.p;
     b.tmask = (unsigned long long*)c->tmask.p;
+    b.cbase = (uint32_t*)c->cbase.p;
     b.cap1 = c->cap1;
     b.trange = (uint32_t*)c->trange.p;
     b.bcount = (uint32_t*)c->bcount.p;
@@ -354,7 +360,7 @@ void gve_ctx_destroy(gve_ctx* c)
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
-                   &c->vals[0], &c->vals[1], &c->tmask, &c->trange, &c->bcount, &c->boff, &c->pairs, &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
+                   &c->vals[0], &c->vals[1], &c->tmask, &c->trange, &c->cbase, &c->bcount, &c->boff, &c->pairs, &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
                    &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace,
                    &c->s_hi, &c->s_mid, &c->s_cnt, &c->s_off, &c->s_pts, &c->s_cell, &c->s_order, &c->s_nd,
                    &c->s_gg, &c->s_loss, &c->s_inv, &c->s_ex, &c->s_terms, &c->s_ccnt, &c->s_cand, &c->r_rec, &c->r_cnt, &c->r_off, &c->r_keys[0], &c->r_keys[1],

@@ -391,12 +391,14 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
             }
             if (exec) cudaGraphExecDestroy(exec);
             exec = nullptr;
+            // every volume grows to half again what it has needed so far, so
+            // that volumes close to their capacity do not each force a replay
             for (int v = 0; v < nvol; ++v) {
                 DevState h;
                 st = read_state(V[v].k, &h);
-                if (st == GVE_OK)
-                    st = grow_pairs(V[v].k, h.max_total1 > h.total1 ? h.max_total1 : h.total1,
-                                    h.max_total > h.total ? h.max_total : h.total);
+                const unsigned long long n1 = h.max_total1 > h.total1 ? h.max_total1 : h.total1;
+                const unsigned long long n2 = h.max_total > h.total ? h.max_total : h.total;
+                if (st == GVE_OK) st = grow_pairs(V[v].k, n1 + n1 / 2, n2 + n2 / 2);
                 if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
                 reset_state(V[v].k);
                 if (cudaStreamSynchronize(V[v].k.s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "sync");

@@ -670,37 +670,71 @@ __device__ __forceinline__ void tile_origin(const BinGeom& g, long long tile, in
     oz = (int)(tile / ((long long)g.ntx * g.nty)) * kTile;
 }
 
-// Stage 2, first pass (one 256-thread CTA per tile): the cover test on the
-// bricks of each listed Gaussian's box inside the tile, flattened per warp
-// like stage 1.  Writes the 64-bit pass mask of every listed Gaussian (bit =
-// (z * 4 + y) * 4 + x of the brick inside the tile), the pair count of each
-// brick of the tile, and, when gcount is set, adds each Gaussian's passes to
-// gcount (introspection).
+// 32 x 32 bit transpose across a warp: lane i holds row x (bit j = column
+// j); afterwards lane j holds column j (bit i = bit j of lane i's row), i.e.
+// the ballot of bit j.  Five rounds of exchanging the off-diagonal blocks.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sh = 16 >> k;
+        const uint32_t m = masks[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y >> sh) & m)) : ((x & m) | ((y & m) << sh));
+    }
+    return x;
+}
+
+// floor(t / d) for t < 64 and 1 <= d <= 64 as (t * ceil(2^16 / d)) >> 16:
+// the rounding of the reciprocal adds less than t / 2^16 < 1/1024 < 1/d to
+// t / d, whose fraction is at most (d - 1) / d, so the floor is exact.
+__device__ __forceinline__ uint32_t small_div(uint32_t t, uint32_t magic) { return (t * magic) >> 16; }
+__device__ __forceinline__ uint32_t small_magic(uint32_t d) { return (65536u + d - 1u) / d; }
+
+// chunk index of chunk c (32 list entries) of the tile whose list starts at
+// ts: (ts >> 5) + tile + c -- distinct over all tiles, below
+// cap1 / 32 + ntiles + 1
+__device__ __forceinline__ unsigned long long chunk_id(uint32_t ts, long long tile, uint32_t c)
+{
+    return (unsigned long long)(ts >> 5) + (unsigned long long)tile + c;
+}
+
+// Stage 2, first pass (one 256-thread CTA per tile; rounds of 256 list
+// entries, warp w holding chunk 8 r + w = entries 32 w .. 32 w + 31 of round
+// r).  The cover test runs on the bricks of each listed Gaussian's box
+// inside the tile, flattened per warp as in stage 1.  Writes the 64-bit pass
+// mask of every entry (bit = (z * 4 + y) * 4 + x of the brick inside the
+// tile), per chunk and brick the passes of all earlier entries of the tile
+// (the chunk's base), the pair count of each brick of the tile, and, when
+// gcount is set, adds each Gaussian's passes to gcount (introspection).
 __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                                 const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
                                                 BinGeom g, unsigned long long* __restrict__ tmask,
-                                                uint32_t* __restrict__ bcount, uint32_t* __restrict__ gcount,
-                                                const DevState* __restrict__ st)
+                                                uint32_t* __restrict__ cbase, uint32_t* __restrict__ bcount,
+                                                uint32_t* __restrict__ gcount, const DevState* __restrict__ st)
 {
     if (st->overflow) return;
     __shared__ BinRec s_br[256];
     __shared__ float4 s_mu[256];
     __shared__ uint32_t s_m[256][2];
-    __shared__ uint32_t s_cnt[64];
+    __shared__ uint32_t s_wc[8][64];   // per-warp passes of each brick, then the chunk's base
+    __shared__ uint32_t s_run[64];     // passes of each brick by the tile's earlier rounds
     __shared__ uint32_t s_incl[8][32];
-    __shared__ int4 s_box[8][32];      // first brick (x, y, z) inside the tile and x extent
-    __shared__ uint32_t s_exy[8][32];
+    __shared__ int4 s_box[8][32];      // first brick (x, y, z) inside the tile, x extent
+    __shared__ uint2 s_div[8][32];     // reciprocal of x*y extent; reciprocal of x extent << 8 | x*y extent
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long tile = blockIdx.x;
     int ox, oy, oz;
     tile_origin(g, tile, ox, oy, oz);
-    if (tid < 64) s_cnt[tid] = 0u;
-    __syncthreads();
+    if (tid < 64) s_run[tid] = 0u;
     const uint32_t ts = trange[tile], te = trange[g.ntiles + tile];
     for (uint32_t r0 = ts; r0 < te; r0 += 256) {
         const uint32_t e = r0 + tid;
-        uint32_t cnt = 0, exy = 1, gid = 0;
+        uint32_t cnt = 0, gid = 0;
         int4 box = make_int4(0, 0, 0, 1);
+        uint2 dv = make_uint2(65536u, (65536u << 8) | 1u);
         s_m[tid][0] = 0u;
         s_m[tid][1] = 0u;
         if (e < te) {
@@ -712,9 +746,9 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
             const int ly = max(b.blo[1], oy) - oy, hy = min(b.bhi[1], oy + kTile - 1) - oy;
             const int lz = max(b.blo[2], oz) - oz, hz = min(b.bhi[2], oz + kTile - 1) - oz;
             if (lx <= hx && ly <= hy && lz <= hz) {
-                const int ex = hx - lx + 1, ey = hy - ly + 1;
-                box = make_int4(lx, ly, lz, ex);
-                exy = (uint32_t)(ex * ey);
+                const uint32_t ex = (uint32_t)(hx - lx + 1), exy = ex * (uint32_t)(hy - ly + 1);
+                box = make_int4(lx, ly, lz, (int)ex);
+                dv = make_uint2(small_magic(exy), (small_magic(ex) << 8) | exy);
                 cnt = exy * (uint32_t)(hz - lz + 1);
             }
         }
@@ -722,7 +756,7 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         s_incl[w][lane] = incl;
         s_box[w][lane] = box;
-        s_exy[w][lane] = exy;
+        s_div[w][lane] = dv;
         __syncwarp();
         for (uint32_t t0 = 0; t0 < total; t0 += 32) {
             const uint32_t it = t0 + lane;
@@ -730,31 +764,50 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
                 const int j = flat_owner(s_incl[w], it);
                 const uint32_t t = it - (j ? s_incl[w][j - 1] : 0u);
                 const int4 bx = s_box[w][j];
-                const uint32_t e2 = s_exy[w][j];
-                const uint32_t cz = t / e2, r = t - cz * e2;
-                const uint32_t cy = r / (uint32_t)bx.w, cx = r - cy * (uint32_t)bx.w;
+                const uint2 d = s_div[w][j];
+                const uint32_t cz = small_div(t, d.x), r = t - cz * (d.y & 255u);
+                const uint32_t cy = small_div(r, d.y >> 8), cx = r - cy * (uint32_t)bx.w;
                 const int lx = bx.x + (int)cx, ly = bx.y + (int)cy, lz = bx.z + (int)cz;
                 const int slot = (w << 5) + j;
                 const float4 mu = s_mu[slot];
                 if (brick_test(s_br[slot], mu.x, mu.y, mu.z, g.B, ox + lx, oy + ly, oz + lz)) {
                     const int lb = (lz * kTile + ly) * kTile + lx;
                     atomicOr(&s_m[slot][lb >> 5], 1u << (lb & 31));
-                    atomicAdd(&s_cnt[lb], 1u);
                 }
             }
         }
         __syncwarp();
+        const uint32_t m0 = s_m[tid][0], m1 = s_m[tid][1];
         if (e < te) {
-            const uint32_t m0 = s_m[tid][0], m1 = s_m[tid][1];
             tmask[e] = ((unsigned long long)m1 << 32) | m0;
             if (gcount) atomicAdd(&gcount[gid], (uint32_t)(__popc(m0) + __popc(m1)));
         }
-        __syncwarp();
+        // lane j: passes of bricks j and 32 + j by this warp's entries
+        s_wc[w][lane] = __popc(warp_transpose32(m0));
+        s_wc[w][32 + lane] = __popc(warp_transpose32(m1));
+        __syncthreads();
+        if (tid < 64) {
+            uint32_t run = s_run[tid];
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) {
+                const uint32_t c = s_wc[ww][tid];
+                s_wc[ww][tid] = run;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        const uint32_t c0 = r0 - ts + (uint32_t)(w << 5);   // first entry of the chunk, within the tile
+        if (ts + c0 < te) {
+            uint32_t* cb = cbase + 64ull * chunk_id(ts, tile, c0 >> 5);
+            cb[lane] = s_wc[w][lane];
+            cb[32 + lane] = s_wc[w][32 + lane];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (tid < 64) {
         const int bx = ox + (tid & 3), by = oy + ((tid >> 2) & 3), bz = oz + (tid >> 4);
-        if (bx < g.nbx && by < g.nby && bz < g.nbz) bcount[((long long)bz * g.nby + by) * g.nbx + bx] = s_cnt[tid];
+        if (bx < g.nbx && by < g.nby && bz < g.nbz) bcount[((long long)bz * g.nby + by) * g.nbx + bx] = s_run[tid];
     }
 }
 
@@ -795,17 +848,19 @@ struct SubRec {
     uint32_t gid;
 };
 
-// Stage 2, second pass (one 256-thread CTA per tile): rounds of 256 listed
-// Gaussians (warp w holds list entries 32 w .. 32 w + 31 of the round).  Per
-// brick of the tile, each warp counts its entries that pass it (ballots);
-// the per-warp counts are scanned in warp order on top of the previous
-// rounds' counts, so an entry's rank in a brick is the number of earlier
-// list entries passing that brick.  Passing (entry, brick) pairs are queued
-// brick-major in shared memory and written 32 at a time, each lane computing
-// one pair's sub-brick cover.
+// Stage 2, second pass (one 256-thread CTA per tile; warps take the tile's
+// chunks of 32 list entries independently, no block barrier after the
+// start).  Per chunk: the 64 per-brick ballots of the entries' masks come
+// from one bit transpose; the chunk's (entry, brick) pairs are laid out
+// brick-major in shared memory (slot = passes of lower bricks in the chunk
+// + passes of earlier entries in the brick), half of the bricks at a time;
+// then every lane takes one pair, computes its sub-brick cover and writes it
+// at brick start + chunk base + rank, so a brick's pairs of one chunk land
+// on consecutive addresses.
 __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                                const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
                                                const unsigned long long* __restrict__ tmask,
+                                               const uint32_t* __restrict__ cbase,
                                                const unsigned long long* __restrict__ boff, BinGeom g,
                                                uint32_t* __restrict__ pairs, const DevState* __restrict__ st)
 {
@@ -814,34 +869,25 @@ __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, co
     const uint32_t ts = trange[tile], te = trange[g.ntiles + tile];
     if (ts >= te) return;
     __shared__ SubRec s_r[256];
-    __shared__ uint32_t s_start[64], s_run[64];
-    __shared__ uint32_t s_wc[8][64];
-    __shared__ uint32_t s_qpos[8][64];
-    __shared__ uint16_t s_qjb[8][64];
+    __shared__ uint32_t s_start[64];
+    __shared__ uint32_t s_col[8][64];    // per brick: ballot of the chunk's entries passing it
+    __shared__ uint32_t s_pos[8][64];    // per brick: global position of the chunk's first pair in it
+    __shared__ uint32_t s_pre[8][64];    // per brick: pairs of lower bricks of the same half in the chunk
+    __shared__ uint16_t s_list[8][1024]; // (entry << 6 | brick), brick-major
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int ox, oy, oz;
     tile_origin(g, tile, ox, oy, oz);
     if (tid < 64) {
         const int bx = ox + (tid & 3), by = oy + ((tid >> 2) & 3), bz = oz + (tid >> 4);
-        s_run[tid] = 0u;
         s_start[tid] = (bx < g.nbx && by < g.nby && bz < g.nbz)
                            ? (uint32_t)boff[((long long)bz * g.nby + by) * g.nbx + bx]
                            : 0u;
     }
-    // write the first m queued pairs (m <= 32)
-    auto flush = [&](uint32_t m) {
-        if ((uint32_t)lane < m) {
-            const uint32_t jb = s_qjb[w][lane];
-            const SubRec& q = s_r[(w << 5) + (jb >> 6)];
-            const int lb = (int)(jb & 63u);
-            const uint32_t mask = subbrick_mask(q.L, q.K2, q.G, q.mx, q.my, q.mz, g.B, ox + (lb & 3),
-                                                oy + ((lb >> 2) & 3), oz + (lb >> 4), g.ny, g.nz);
-            pairs[s_qpos[w][lane]] = q.gid | (mask << kGidBits);
-        }
-    };
-    for (uint32_t r0 = ts; r0 < te; r0 += 256) {
-        const uint32_t e = r0 + tid;
+    __syncthreads();
+    const uint32_t nchunks = (te - ts + 31) >> 5;
+    for (uint32_t c = (uint32_t)w; c < nchunks; c += 8) {
+        const uint32_t e = ts + (c << 5) + lane;
         uint32_t m0 = 0u, m1 = 0u;
         if (e < te) {
             const unsigned long long m = tmask[e];
@@ -862,61 +908,42 @@ __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, co
                 q.gid = gid;
             }
         }
-        s_wc[w][lane] = 0u;
-        s_wc[w][lane + 32] = 0u;
+        const uint32_t* cb = cbase + 64ull * chunk_id(ts, tile, c);
+        const uint32_t col0 = warp_transpose32(m0), col1 = warp_transpose32(m1);
+        const uint32_t n0 = __popc(col0), n1 = __popc(col1);
+        const uint32_t p0 = warp_incl_scan(n0) - n0, p1 = warp_incl_scan(n1) - n1;
+        const uint32_t tot0 = __shfl_sync(0xffffffffu, p0 + n0, 31), tot1 = __shfl_sync(0xffffffffu, p1 + n1, 31);
+        s_col[w][lane] = col0;
+        s_col[w][32 + lane] = col1;
+        s_pre[w][lane] = p0;
+        s_pre[w][32 + lane] = p1;
+        s_pos[w][lane] = s_start[lane] + cb[lane];
+        s_pos[w][32 + lane] = s_start[32 + lane] + cb[32 + lane];
         __syncwarp();
-        const uint32_t o0 = __reduce_or_sync(0xffffffffu, m0), o1 = __reduce_or_sync(0xffffffffu, m1);
-        for (uint32_t mm = o0; mm; mm &= mm - 1) {
-            const int b = __ffs(mm) - 1;
-            const unsigned bal = __ballot_sync(0xffffffffu, (m0 >> b) & 1u);
-            if (lane == 0) s_wc[w][b] = __popc(bal);
-        }
-        for (uint32_t mm = o1; mm; mm &= mm - 1) {
-            const int b = __ffs(mm) - 1;
-            const unsigned bal = __ballot_sync(0xffffffffu, (m1 >> b) & 1u);
-            if (lane == 0) s_wc[w][32 + b] = __popc(bal);
-        }
-        __syncthreads();
-        if (tid < 64) {
-            uint32_t run = s_run[tid];
-#pragma unroll
-            for (int ww = 0; ww < 8; ++ww) {
-                const uint32_t c = s_wc[ww][tid];
-                s_wc[ww][tid] = run;
-                run += c;
-            }
-            s_run[tid] = run;
-        }
-        __syncthreads();
-        uint32_t qn = 0;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-            const uint32_t mine = half ? m1 : m0;
-            for (uint32_t mm = half ? o1 : o0; mm; mm &= mm - 1) {
-                const int bb = __ffs(mm) - 1, b = bb + 32 * half;
-                const bool has = (mine >> bb) & 1u;
-                const unsigned bal = __ballot_sync(0xffffffffu, has);
-                if (has) {
-                    const uint32_t rk = __popc(bal & lt);
-                    s_qpos[w][qn + rk] = s_start[b] + s_wc[w][b] + rk;
-                    s_qjb[w][qn + rk] = (uint16_t)((lane << 6) | b);
-                }
-                qn += __popc(bal);
-                __syncwarp();
-                if (qn >= 32) {
-                    flush(32);
-                    __syncwarp();
-                    if ((uint32_t)lane < qn - 32) {
-                        s_qpos[w][lane] = s_qpos[w][lane + 32];
-                        s_qjb[w][lane] = s_qjb[w][lane + 32];
-                    }
-                    qn -= 32;
-                    __syncwarp();
+            const uint32_t tot = half ? tot1 : tot0;
+            if (tot == 0) continue;
+            for (uint32_t mm = half ? m1 : m0; mm; mm &= mm - 1) {
+                const int b = (__ffs(mm) - 1) + 32 * half;
+                s_list[w][s_pre[w][b] + __popc(s_col[w][b] & lt)] = (uint16_t)((lane << 6) | b);
+            }
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < tot; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                if (k < tot) {
+                    const uint32_t jb = s_list[w][k];
+                    const uint32_t j = jb >> 6;
+                    const int lb = (int)(jb & 63u);
+                    const SubRec& q = s_r[(w << 5) + j];
+                    const uint32_t mask = subbrick_mask(q.L, q.K2, q.G, q.mx, q.my, q.mz, g.B, ox + (lb & 3),
+                                                        oy + ((lb >> 2) & 3), oz + (lb >> 4), g.ny, g.nz);
+                    const uint32_t rank = __popc(s_col[w][lb] & ((1u << j) - 1u));
+                    pairs[s_pos[w][lb] + rank] = q.gid | (mask << kGidBits);
                 }
             }
+            __syncwarp();
         }
-        flush(qn);
-        __syncthreads();
     }
 }
 
@@ -960,13 +987,15 @@ int launch_binning(const BinBufs& b, const float* prims, long long n, const BinG
     launch_ranges(kk[cur], &st->total1, &st->overflow, b.cap1, b.trange, b.trange + g.ntiles, s);
     ++launches;
     if (b.gcount && n > 0) cudaMemsetAsync(b.gcount, 0, sizeof(uint32_t) * (size_t)n, s);
-    k_bcount<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, g, b.tmask, b.bcount, b.gcount, st);
+    k_bcount<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, g, b.tmask, b.cbase, b.bcount,
+                                                 b.gcount, st);
     launch_exscan_u32(b.bcount, g.nbricks, b.boff, b.scanp, s);
     long long rb = (g.nbricks + 255) / 256;
     if (rb > 8LL * num_sms()) rb = 8LL * num_sms();
     k_brick_ranges<<<(unsigned)rb, 256, 0, s>>>(b.bcount, b.boff, g.nbricks, b.ranges, b.ranges + g.nbricks, st,
                                                 b.cap, iter);
-    k_bemit<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.boff, g, b.pairs, st);
+    k_bemit<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, g, b.pairs,
+                                                st);
     launches += 6;
     return launches;
 }

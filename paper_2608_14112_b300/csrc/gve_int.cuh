@@ -81,6 +81,7 @@ struct gve_ctx {
     gve::Buf rec, binrec, counts, offsets, acc, adam;
     gve::Buf keys[2], vals[2];       // tile pairs (radix double buffer)
     gve::Buf tmask, trange;          // brick pass mask per sorted tile pair; per-tile ranges
+    gve::Buf cbase;                  // per chunk of 32 tile-list entries: earlier passes per brick
     uint64_t cap1 = 0;               // tile-pair capacity
     gve::Buf bcount, boff;           // per-brick pair counts and their exclusive scan
     gve::Buf pairs;                  // brick pairs in brick order
@@ -330,6 +331,8 @@ struct BinBufs {
     uint32_t* tvals[2];           // [cap1] Gaussian indices
     uint32_t* hist;               // radix histograms for cap1 elements
     unsigned long long* tmask;    // [cap1] brick pass mask per sorted tile pair
+    uint32_t* cbase;              // [cbase_chunks(cap1, ntiles)][64] per chunk of 32 tile-list
+                                  // entries: passes of each brick by the tile's earlier entries
     unsigned long long cap1;
     uint32_t* trange;             // [2][ntiles]
     uint32_t* bcount;             // [nbricks]
@@ -340,6 +343,11 @@ struct BinBufs {
     uint32_t* gcount;             // [n] brick pairs per Gaussian, or nullptr
     DevState* st;
 };
+// chunks of 32 tile-list entries that cap1 tile pairs over ntiles tiles can form
+inline unsigned long long cbase_chunks(unsigned long long cap1, long long ntiles)
+{
+    return cap1 / 32 + (unsigned long long)ntiles + 2;
+}
 // Issues the whole binning on s without host synchronisation and returns
 // the kernels launched.  Tile pairs above cap1 or brick pairs above cap set
 // st->overflow (st->first_overflow_iter = iter) and skip the rest.

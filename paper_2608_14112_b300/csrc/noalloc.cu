@@ -54,6 +54,9 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // tile pairs (stage 1 of the binning): up to 16 per primitive on average;
 // more return GVE_E_CAPACITY like the brick pairs
 constexpr long long kNaTilePairs = 16 * kNaPrims;
+// tiles of a grid of at most kNaBricks bricks with axes of at most 2^11
+// bricks (the largest count, 2,410, is a 1 x 17 x 1,927-brick grid)
+constexpr long long kNaTiles = 2410;
 
 // carve-up of the scratch array (byte offsets)
 constexpr size_t kOffState = 0;
@@ -68,8 +71,9 @@ constexpr size_t kOffTvals0 = align256(kOffTkeys1 + sizeof(uint32_t) * kNaTilePa
 constexpr size_t kOffTvals1 = align256(kOffTvals0 + sizeof(uint32_t) * kNaTilePairs);
 constexpr size_t kOffHist = align256(kOffTvals1 + sizeof(uint32_t) * kNaTilePairs);
 constexpr size_t kOffTmask = align256(kOffHist + sizeof(uint32_t) * 256 * (kNaTilePairs / kSortTile + 1));
-constexpr size_t kOffTrange = align256(kOffTmask + sizeof(unsigned long long) * kNaTilePairs);
-constexpr size_t kOffBcount = align256(kOffTrange + sizeof(uint32_t) * 2 * kNaBricks);  // tiles <= bricks
+constexpr size_t kOffCbase = align256(kOffTmask + sizeof(unsigned long long) * kNaTilePairs);
+constexpr size_t kOffTrange = align256(kOffCbase + sizeof(uint32_t) * 64 * (kNaTilePairs / 32 + kNaTiles + 2));
+constexpr size_t kOffBcount = align256(kOffTrange + sizeof(uint32_t) * 2 * kNaTiles);
 constexpr size_t kOffBoff = align256(kOffBcount + sizeof(uint32_t) * kNaBricks);
 constexpr size_t kOffRanges = align256(kOffBoff + sizeof(unsigned long long) * (kNaBricks + 1));
 constexpr size_t kOffPairs = align256(kOffRanges + sizeof(uint32_t) * 2 * kNaBricks);
@@ -129,7 +133,7 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
         return GVE_E_INVALID;
     if (o->normalized && !(o->rho0 > 0.f)) return GVE_E_INVALID;
     const BinGeom g = make_geom(d, 8);
-    if (g.nbricks > kNaBricks) return GVE_E_INVALID;
+    if (g.nbricks > kNaBricks || g.ntiles > kNaTiles) return GVE_E_INVALID;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -154,6 +158,7 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
     b.tvals[1] = reinterpret_cast<uint32_t*>(base + kOffTvals1);
     b.hist = reinterpret_cast<uint32_t*>(base + kOffHist);
     b.tmask = reinterpret_cast<unsigned long long*>(base + kOffTmask);
+    b.cbase = reinterpret_cast<uint32_t*>(base + kOffCbase);
     b.cap1 = (unsigned long long)kNaTilePairs;
     b.trange = reinterpret_cast<uint32_t*>(base + kOffTrange);
     b.bcount = reinterpret_cast<uint32_t*>(base + kOffBcount);

@@ -166,12 +166,13 @@ gve_status size_static(Call& k)
     GVE_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * (n + 1), k.s));
     GVE_TRY(ensure(c, c->acc, sizeof(float) * 12 * n, k.s));
     GVE_TRY(ensure(c, c->scanp, sizeof(unsigned long long) * kScanBlocks, k.s));
-    GVE_TRY(ensure(c, c->trange, sizeof(uint32_t) * 2 * k.g.ntiles, k.s));
-    GVE_TRY(ensure(c, c->cbase, sizeof(uint32_t) * 64 * cbase_chunks(c->cap1, k.g.ntiles), k.s));
-    GVE_TRY(ensure(c, c->bcount, sizeof(uint32_t) * k.g.nbricks, k.s));
-    GVE_TRY(ensure(c, c->boff, sizeof(unsigned long long) * (k.g.nbricks + 1), k.s));
-    GVE_TRY(ensure(c, c->ranges, sizeof(uint32_t) * 2 * k.g.nbricks, k.s));
-    GVE_TRY(ensure(c, c->part, sizeof(double2) * (k.g.nbricks + 1024), k.s));
+    const long long nt = k.vt.toff[k.vt.nvol], nb = k.vt.boff[k.vt.nvol];
+    GVE_TRY(ensure(c, c->trange, sizeof(uint32_t) * 2 * nt, k.s));
+    GVE_TRY(ensure(c, c->cbase, sizeof(uint32_t) * 64 * cbase_chunks(c->cap1, nt), k.s));
+    GVE_TRY(ensure(c, c->bcount, sizeof(uint32_t) * nb, k.s));
+    GVE_TRY(ensure(c, c->boff, sizeof(unsigned long long) * (nb + 1), k.s));
+    GVE_TRY(ensure(c, c->ranges, sizeof(uint32_t) * 2 * nb, k.s));
+    GVE_TRY(ensure(c, c->part, sizeof(double2) * (nb + 1024), k.s));
     return GVE_OK;
 }
 
@@ -197,7 +198,7 @@ gve_status grow_pairs(Call& k, unsigned long long need1, unsigned long long need
             GVE_TRY(ensure(c, c->vals[b], sizeof(uint32_t) * cap, k.s));
         }
         GVE_TRY(ensure(c, c->tmask, sizeof(unsigned long long) * cap, k.s));
-        GVE_TRY(ensure(c, c->cbase, sizeof(uint32_t) * 64 * cbase_chunks(cap, k.g.ntiles), k.s));
+        GVE_TRY(ensure(c, c->cbase, sizeof(uint32_t) * 64 * cbase_chunks(cap, k.vt.toff[k.vt.nvol]), k.s));
         GVE_TRY(ensure(c, c->hist, sizeof(uint32_t) * 256 * ((cap + kSortTile - 1) / kSortTile + 1), k.s));
         c->cap1 = cap;
     }
@@ -270,7 +271,7 @@ BinBufs bin_bufs(Call& k, uint32_t* gcount)
 gve_status bin_all(Call& k, const float* prims, const gve_eval_opts* o, int iter, uint32_t* gcount)
 {
     gve_ctx* c = k.c;
-    c->launches += launch_binning(bin_bufs(k, gcount), prims, k.n, k.g, o->trunc_k, iter, k.s);
+    c->launches += launch_binning(bin_bufs(k, gcount), prims, k.n, k.vt, o->trunc_k, iter, k.s);
     GVE_CUDA(cudaGetLastError(), "launch (binning)");
     return GVE_OK;
 }
@@ -302,6 +303,7 @@ gve_status begin(gve_ctx* c, Call& k, int64_t n, gve_dims d, const gve_eval_opts
     k.s = (cudaStream_t)stream;
     k.n = n;
     k.g = make_geom(d, o->brick);
+    k.vt = single_volume(k.g, n);
     c->launches = 0;
     GVE_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     GVE_TRY(ensure(c, c->state, sizeof(DevState), k.s));
@@ -360,7 +362,7 @@ void gve_ctx_destroy(gve_ctx* c)
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     Buf* bufs[] = {&c->rec, &c->binrec, &c->counts, &c->offsets, &c->acc, &c->adam, &c->keys[0], &c->keys[1],
-                   &c->vals[0], &c->vals[1], &c->tmask, &c->trange, &c->cbase, &c->bcount, &c->boff, &c->pairs, &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
+                   &c->vals[0], &c->vals[1], &c->tmask, &c->trange, &c->cbase, &c->bcount, &c->csum, &c->boff, &c->pairs, &c->hist, &c->scanp, &c->ranges, &c->part, &c->state,
                    &c->a_g, &c->a_keys, &c->a_sel, &c->a_tmp, &c->a_cnt, &c->trace,
                    &c->s_hi, &c->s_mid, &c->s_cnt, &c->s_off, &c->s_pts, &c->s_cell, &c->s_order, &c->s_nd,
                    &c->s_gg, &c->s_loss, &c->s_inv, &c->s_ex, &c->s_terms, &c->s_ccnt, &c->s_cand, &c->r_rec, &c->r_cnt, &c->r_off, &c->r_keys[0], &c->r_keys[1],
@@ -371,9 +373,6 @@ void gve_ctx_destroy(gve_ctx* c)
     if (c->sev_ready)
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 64; ++b) cudaEventDestroy(c->sev[a][b]);
-    for (gve_ctx* s : c->sub) gve_ctx_destroy(s);
-    for (cudaStream_t vs : c->vstream) cudaStreamDestroy(vs);
-    for (cudaEvent_t ev : c->vjoin) cudaEventDestroy(ev);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->bstate.p) cudaFree(c->bstate.p);

@@ -1,28 +1,31 @@
 // batch.cu -- many volumes of uneven sizes refined together, and the
 // autotuner of the evaluator's launch shape.
 //
-// gve_refine_batch: each volume keeps its own binning (cell-free brick
-// pairs, sort, ranges) in its own sub-context and stream; the evaluation and
-// the update of all volumes are one persistent cooperative kernel
-// (k_batch_iter in field.cu): its CTAs take global brick ids from one work
-// counter, find each brick's volume in a table of brick offsets and run the
-// fused forward + backward of that volume's brick; after a bounded grid-wide
-// barrier the same launch reduces each volume's loss in a fixed order and
-// applies the chain rule and Adam to every Gaussian of every volume.  One
-// iteration -- bias corrections, the per-volume binning branches, the
-// batch-wide capacity check, the persistent kernel, the step counter -- is
+// gve_refine_batch: the volumes' records are one concatenated set; one
+// binning covers all of them (bin.cu with a table of the volumes: each
+// Gaussian is binned into the tiles and bricks of its own volume, tiles and
+// bricks numbered volume after volume), so every stage runs once over the
+// whole batch.  The evaluation and the update of all volumes are one
+// persistent cooperative kernel (k_batch_iter in field.cu): its CTAs take
+// global brick ids from one work counter, find each brick's volume in the
+// table of brick offsets and run the fused forward + backward of that
+// volume's brick; after a bounded grid-wide barrier the same launch reduces
+// each volume's loss in a fixed order and applies the chain rule and Adam to
+// every Gaussian of every volume.  One iteration -- bias corrections, the
+// binning, the capacity check, the persistent kernel, the step counter -- is
 // captured once as a CUDA graph and replayed; the Adam step and the trace
-// index come from device-side state.  All volumes advance in lockstep: if any
-// volume's pair count exceeds its capacity, every volume skips that iteration
-// and the host, after growing the scratch, replays from it.  A grid-barrier
-// wait that runs out (about a second; it only can when the grid is not
-// co-resident) sets a device flag: every later launch of the call does
-// nothing and the call returns GVE_E_TIMEOUT.
+// index come from device-side state.  If the pairs exceed their capacity the
+// iteration is skipped on the device and the host, after growing the
+// scratch, replays from it.  A grid-barrier wait that runs out (about a
+// second; it only can when the grid is not co-resident) sets a device flag:
+// every later launch of the call does nothing and the call returns
+// GVE_E_TIMEOUT.
 //
 // gve_autotune: times one loss-and-gradient pass (no parameter update) of the
 // batch -- binning plus the persistent kernel -- for every brick edge in
 // {4, 8, 16} and every Gaussians-per-block in {32, 64}, and returns the
 // fastest.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -36,12 +39,6 @@ namespace {
 
 constexpr int kMaxVol = 32;
 
-
-struct StatePtrs {
-    DevState* p[kMaxVol];
-    int n;
-};
-
 __global__ void k_batch_reset(BatchState* b, int it0)
 {
     b->it = it0;
@@ -50,6 +47,7 @@ __global__ void k_batch_reset(BatchState* b, int it0)
     b->bar_count = 0;
     b->bar_gen = 0;
     b->err = 0;
+    b->done = 0;
 }
 
 // bounded waits: about one second of ~128 ns sleeps; the fault-injection
@@ -71,35 +69,14 @@ __global__ void k_batch_bc(BatchState* b, int step0, float b1, float b2)
     b->bc[1] = (float)(1.0 - pow((double)b2, step));
 }
 
-__global__ void k_batch_overflow(StatePtrs sp, BatchState* b)
+__global__ void k_batch_overflow(const DevState* st, BatchState* b)
 {
-    int any = 0;
-    for (int v = 0; v < sp.n; ++v) any |= sp.p[v]->overflow;
-    if (!any) return;
-    if (b->first < 0) b->first = b->it;
-    for (int v = 0; v < sp.n; ++v) sp.p[v]->overflow = 1;
+    if (st->overflow && b->first < 0) b->first = b->it;
 }
 
 __global__ void k_batch_inc(BatchState* b) { b->it += 1; }
 
-gve_status make_sub(gve_ctx* c, gve_ctx** out)
-{
-    gve_ctx* s = new gve_ctx();
-    s->device = c->device;
-    if (cudaMallocHost(&s->hstate, sizeof(DevState)) != cudaSuccess) {
-        delete s;
-        return fail(c, GVE_E_NOMEM, "pinned host state");
-    }
-    if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess) {
-        cudaFreeHost(s->hstate);
-        delete s;
-        return cuda_fail(c, cudaGetLastError(), "event create");
-    }
-    *out = s;
-    return GVE_OK;
-}
-
-gve_status ensure_batch(gve_ctx* c, int nvol)
+gve_status ensure_batch(gve_ctx* c)
 {
     if (!c->gstream) {
         if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess)
@@ -107,123 +84,129 @@ gve_status ensure_batch(gve_ctx* c, int nvol)
         if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
             return cuda_fail(c, cudaGetLastError(), "event create");
     }
-    while ((int)c->sub.size() < nvol) {
-        gve_ctx* s = nullptr;
-        gve_status st = make_sub(c, &s);
-        if (st != GVE_OK) return st;
-        c->sub.push_back(s);
-        cudaStream_t vs = nullptr;
-        cudaEvent_t ev = nullptr;
-        if (cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
-            return cuda_fail(c, cudaGetLastError(), "stream create");
-        c->vstream.push_back(vs);
-        c->vjoin.push_back(ev);
-    }
     gve_status st = ensure(c, c->bstate, sizeof(BatchState), c->gstream);
     if (st != GVE_OK) return st;
-    return ensure(c, c->btab, sizeof(BrickArgs) * kMaxVol + sizeof(long long) * (kMaxVol + 1) +
-                                  sizeof(double) * kMaxVol * 3, c->gstream);
+    return ensure(c, c->btab, sizeof(double) * kMaxVol * 2, c->gstream);
 }
 
 struct Vol {
-    Call k;
+    BinGeom g;
     const float* field;
-    float* prims;
     long long goff;   // first Gaussian of the volume in the concatenated records
     double inv_m;
 };
-
-// device tables of one batch: evaluator arguments, brick offsets, 1 / voxels, SSE
-struct Tables {
-    BrickArgs* vargs;
-    long long* boff;
-    double* inv_m;
-    double* sse;
-};
-
-Tables tables(gve_ctx* c)
-{
-    Tables t;
-    char* b = (char*)c->btab.p;
-    t.vargs = reinterpret_cast<BrickArgs*>(b);
-    t.boff = reinterpret_cast<long long*>(b + sizeof(BrickArgs) * kMaxVol);
-    t.inv_m = reinterpret_cast<double*>(b + sizeof(BrickArgs) * kMaxVol + sizeof(long long) * (kMaxVol + 1));
-    t.sse = t.inv_m + kMaxVol;
-    return t;
-}
 
 gve_status check_batch(gve_ctx* c, int nvol, const gve_volume* vols, const float* prims, const gve_eval_opts* o)
 {
     if (!c) return GVE_E_INVALID;
     if (nvol < 1 || nvol > kMaxVol || !vols) return fail(c, GVE_E_INVALID, "volume count must be 1..32");
     if (!prims || (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "bad primitive pointer");
+    long long total = 0;
     for (int v = 0; v < nvol; ++v) {
         if (!vols[v].field_dev) return fail(c, GVE_E_INVALID, "null field in batch");
         gve_status st = check_common(c, prims, vols[v].n, vols[v].dims, o);
         if (st != GVE_OK) return st;
+        total += vols[v].n;
     }
+    if (total > (long long)kGidMask + 1) return fail(c, GVE_E_INVALID, "more than 2^24 primitives in the batch");
     return GVE_OK;
 }
 
-// Build the per-volume calls (sub-contexts, streams) and size their scratch.
+// One batch: its volumes and the call whose binning covers all of them.
+struct Batch {
+    int nvol;
+    Vol V[kMaxVol];
+    Call k;            // the whole batch: n = all Gaussians, vt = the volumes
+    long long ntot;
+};
+
+// Build the batch's volume table on the context's batch stream and size the
+// binning scratch for it.
 gve_status setup_vols(gve_ctx* c, int nvol, const gve_volume* vols, float* prims, const gve_eval_opts* o,
-                      Vol* V, long long* ntot, cudaStream_t caller)
+                      Batch* b, cudaStream_t caller)
 {
-    gve_status st = ensure_batch(c, nvol);
+    gve_status st = ensure_batch(c);
     if (st != GVE_OK) return st;
-    if (cudaEventRecord(c->fork, caller) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
+    if (cudaEventRecord(c->fork, caller) != cudaSuccess || cudaStreamWaitEvent(c->gstream, c->fork, 0) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "event");
+    b->nvol = nvol;
+    Call& k = b->k;
+    k.c = c;
+    k.s = c->gstream;
+    VolTab& vt = k.vt;
+    vt = VolTab{};
+    vt.nvol = nvol;
     long long off = 0;
     for (int v = 0; v < nvol; ++v) {
-        if (cudaStreamWaitEvent(c->vstream[v], c->fork, 0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "wait");
-        Vol& vo = V[v];
-        st = begin(c->sub[v], vo.k, vols[v].n, vols[v].dims, o, c->vstream[v]);
-        if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
+        Vol& vo = b->V[v];
+        vo.g = make_geom(vols[v].dims, o->brick);
         vo.field = vols[v].field_dev;
-        vo.prims = prims + 12 * off;
         vo.goff = off;
         vo.inv_m = 1.0 / ((double)vols[v].dims.nx * vols[v].dims.ny * vols[v].dims.nz);
-        st = size_pairs(vo.k, vo.prims, o);
-        if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
+        vt.g[v] = vo.g;
+        vt.goff[v] = off;
+        vt.toff[v + 1] = vt.toff[v] + vo.g.ntiles;
+        vt.boff[v + 1] = vt.boff[v] + vo.g.nbricks;
         off += vols[v].n;
     }
-    *ntot = off;
+    vt.goff[nvol] = off;
+    if (vt.toff[nvol] > (long long)INT_MAX || vt.boff[nvol] > (long long)INT_MAX)
+        return fail(c, GVE_E_INVALID, "the batch has too many bricks");
+    b->ntot = off;
+    k.n = off;
+    k.g = vt.g[0];
+    c->launches = 0;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    st = ensure(c, c->state, sizeof(DevState), k.s);
+    if (st != GVE_OK) return st;
+    st = size_pairs(k, prims, o);
+    if (st != GVE_OK) return st;
     return ensure(c, c->acc, sizeof(float) * 12 * (off > 0 ? off : 1), c->gstream);
 }
 
-// The persistent kernel's arguments; uploads the volume tables (their
-// pointers change only when the scratch grows).
-gve_status batch_args(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* o, const gve_schedule* sc, long long ntot,
-                      float* prims, float* m, float* v, float* grad, double* trace, BatchIterArgs* out)
+// evaluator arguments of volume v over the batch's binning: its geometry,
+// its bricks' ranges and SSE partials; Gaussian indices are global
+BrickArgs vol_args(const Batch& b, int v, const gve_eval_opts* o, float mask_thresh)
 {
-    Tables t = tables(c);
-    BrickArgs va[kMaxVol];
-    long long boff[kMaxVol + 1];
-    double inv_m[kMaxVol];
-    boff[0] = 0;
-    for (int i = 0; i < nvol; ++i) {
-        va[i] = brick_args(V[i].k, o);
-        va[i].field = V[i].field;
-        va[i].mask_thresh = sc ? sc->mask_thresh : -1.f;
-        va[i].acc = (float*)c->acc.p + 12 * V[i].goff;
-        boff[i + 1] = boff[i] + V[i].k.g.nbricks;
-        inv_m[i] = V[i].inv_m;
-    }
-    cudaStream_t g = c->gstream;
-    if (cudaMemcpyAsync(t.vargs, va, sizeof(BrickArgs) * nvol, cudaMemcpyHostToDevice, g) != cudaSuccess ||
-        cudaMemcpyAsync(t.boff, boff, sizeof(long long) * (nvol + 1), cudaMemcpyHostToDevice, g) != cudaSuccess ||
-        cudaMemcpyAsync(t.inv_m, inv_m, sizeof(double) * nvol, cudaMemcpyHostToDevice, g) != cudaSuccess ||
-        cudaStreamSynchronize(g) != cudaSuccess)
-        return cuda_fail(c, cudaGetLastError(), "batch tables");
+    Call k = b.k;
+    gve_ctx* c = k.c;
+    BrickArgs a = brick_args(k, o);
+    const long long nb = k.vt.boff[k.vt.nvol], b0 = k.vt.boff[v];
+    a.g = b.V[v].g;
+    a.start = (const uint32_t*)c->ranges.p + b0;
+    a.end = (const uint32_t*)c->ranges.p + nb + b0;
+    a.part = (double2*)c->part.p + b0;
+    a.inv_m = (float)b.V[v].inv_m;
+    a.field = b.V[v].field;
+    a.mask_thresh = mask_thresh;
+    a.acc = (float*)c->acc.p;
+    return a;
+}
+
+// The persistent kernel's arguments, the volume tables included (rebuilt
+// when the scratch grows).
+gve_status batch_args(gve_ctx* c, const Batch& b, const gve_eval_opts* o, const gve_schedule* sc, float* prims,
+                      float* m, float* v, float* grad, double* trace, BatchIterArgs* out)
+{
+    const int nvol = b.nvol;
+    static_assert(kMaxVol <= kMaxBatchVol, "volume table size");
     const int grid = batch_iter_grid(o->brick, o->gaussians_per_block == 32 ? 32 : 64);
     if (grid <= 0) return fail(c, GVE_E_CUDA, "the device cannot launch the persistent kernel cooperatively");
     BatchIterArgs p{};
-    p.vargs = t.vargs;
-    p.boff = t.boff;
-    p.inv_m = t.inv_m;
+    for (int i = 0; i < nvol; ++i) {
+        p.va[i] = vol_args(b, i, o, sc ? sc->mask_thresh : -1.f);
+        p.inv_m[i] = b.V[i].inv_m;
+    }
+    for (int i = 0; i <= nvol; ++i) p.boff[i] = b.k.vt.boff[i];
+    p.coff[0] = 0;
+    for (int i = 0; i < nvol; ++i) p.coff[i + 1] = p.coff[i] + (b.V[i].g.nbricks + kSseChunk - 1) / kSseChunk;
+    p.nchunks = p.coff[nvol];
+    gve_status st = ensure(c, c->csum, sizeof(double2) * (p.nchunks > 0 ? p.nchunks : 1), c->gstream);
+    if (st != GVE_OK) return st;
+    p.csum = (double2*)c->csum.p;
     p.nvol = nvol;
-    p.nbricks = boff[nvol];
-    p.ntot = ntot;
+    p.nbricks = p.boff[nvol];
+    p.ntot = b.ntot;
     p.bs = (BatchState*)c->bstate.p;
     p.acc = (float*)c->acc.p;
     p.prims = prims;
@@ -236,7 +219,7 @@ gve_status batch_args(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* o, cons
         p.ad.bc_dev = p.bs->bc;
     }
     p.trace = trace;
-    p.sse = t.sse;
+    p.sse = (double*)c->btab.p;
     const bool inject = fault("timeout");
     p.expect = (unsigned)grid + (inject ? 1u : 0u);
     p.spin_limit = inject ? kSpinLimitTest : kSpinLimit;
@@ -244,26 +227,17 @@ gve_status batch_args(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* o, cons
     return GVE_OK;
 }
 
-// One iteration of the batch on c->gstream: bias corrections, every
-// volume's binning on its own stream, the capacity check, the persistent
-// kernel, the step counter.
-gve_status issue_iteration(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* o, const gve_schedule* sc,
+// One iteration of the batch on c->gstream: bias corrections, the binning of
+// all volumes, the capacity check, the persistent kernel, the step counter.
+gve_status issue_iteration(gve_ctx* c, Batch& b, const gve_eval_opts* o, const gve_schedule* sc, float* prims,
                            const BatchIterArgs& p, unsigned grid)
 {
     BatchState* bs = (BatchState*)c->bstate.p;
-    StatePtrs sp{};
-    sp.n = nvol;
-    for (int v = 0; v < nvol; ++v) sp.p[v] = dstate(c->sub[v]);
     cudaStream_t g = c->gstream;
     if (sc) k_batch_bc<<<1, 1, 0, g>>>(bs, sc->step0, sc->beta1, sc->beta2);
-    cudaEventRecord(c->fork, g);
-    for (int v = 0; v < nvol; ++v) {
-        cudaStreamWaitEvent(c->vstream[v], c->fork, 0);
-        bin_all(V[v].k, V[v].prims, o, 0);
-        cudaEventRecord(c->vjoin[v], c->vstream[v]);
-        cudaStreamWaitEvent(g, c->vjoin[v], 0);
-    }
-    k_batch_overflow<<<1, 1, 0, g>>>(sp, bs);
+    gve_status st = bin_all(b.k, prims, o, 0);
+    if (st != GVE_OK) return st;
+    k_batch_overflow<<<1, 1, 0, g>>>(dstate(c), bs);
     cudaError_t e = launch_batch_iter(o->brick, o->gaussians_per_block == 32 ? 32 : 64, p, grid, g);
     if (e != cudaSuccess) return cuda_fail(c, e, "persistent batch kernel");
     k_batch_inc<<<1, 1, 0, g>>>(bs);
@@ -272,7 +246,7 @@ gve_status issue_iteration(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* o,
 
 // The iteration as a CUDA graph (nullptr in *exec when the capture is not
 // possible: the iteration is then issued directly every time).
-gve_status capture_iteration(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* o, const gve_schedule* sc,
+gve_status capture_iteration(gve_ctx* c, Batch& b, const gve_eval_opts* o, const gve_schedule* sc, float* prims,
                              const BatchIterArgs& p, unsigned grid, cudaGraphExec_t* exec)
 {
     *exec = nullptr;
@@ -280,7 +254,7 @@ gve_status capture_iteration(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* 
     cudaStream_t g = c->gstream;
     if (cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "begin capture");
-    gve_status st = issue_iteration(c, nvol, V, o, sc, p, grid);
+    gve_status st = issue_iteration(c, b, o, sc, prims, p, grid);
     cudaError_t e = cudaStreamEndCapture(g, &graph);
     if (st != GVE_OK || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -297,14 +271,14 @@ gve_status capture_iteration(gve_ctx* c, int nvol, Vol* V, const gve_eval_opts* 
     return GVE_OK;
 }
 
-gve_status run_iteration(gve_ctx* c, cudaGraphExec_t exec, int nvol, Vol* V, const gve_eval_opts* o,
-                         const gve_schedule* sc, const BatchIterArgs& p, unsigned grid)
+gve_status run_iteration(gve_ctx* c, cudaGraphExec_t exec, Batch& b, const gve_eval_opts* o, const gve_schedule* sc,
+                         float* prims, const BatchIterArgs& p, unsigned grid)
 {
     if (exec) {
         if (cudaGraphLaunch(exec, c->gstream) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "graph launch");
         return GVE_OK;
     }
-    return issue_iteration(c, nvol, V, o, sc, p, grid);
+    return issue_iteration(c, b, o, sc, prims, p, grid);
 }
 
 }  // namespace
@@ -328,10 +302,10 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
     if (adam_state && (reinterpret_cast<uintptr_t>(adam_state) & 15u)) return fail(c, GVE_E_INVALID, "adam alignment");
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t caller = (cudaStream_t)stream;
-    Vol V[kMaxVol];
-    long long ntot = 0;
-    st = setup_vols(c, nvol, vols, prims, o, V, &ntot, caller);
+    Batch b;
+    st = setup_vols(c, nvol, vols, prims, o, &b, caller);
     if (st != GVE_OK) return st;
+    const long long ntot = b.ntot;
     float* m = adam_state;
     if (!m) {
         st = ensure(c, c->adam, sizeof(float) * 24 * (ntot > 0 ? ntot : 1), c->gstream);
@@ -341,10 +315,6 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
             return cuda_fail(c, cudaGetLastError(), "memset adam");
     }
     float* vmom = m + 12 * ntot;
-    for (int v = 0; v < nvol; ++v) {
-        cudaEventRecord(c->vjoin[v], V[v].k.s);
-        cudaStreamWaitEvent(c->gstream, c->vjoin[v], 0);
-    }
     if (cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (ntot > 0 ? ntot : 1), c->gstream) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "memset acc");
     double* tr = trace;
@@ -355,12 +325,14 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
     }
     BatchState* bs = (BatchState*)c->bstate.p;
     BatchIterArgs p{};
-    st = batch_args(c, nvol, V, o, sc, ntot, prims, m, vmom, nullptr, tr, &p);
+    st = batch_args(c, b, o, sc, prims, m, vmom, nullptr, tr, &p);
     if (st != GVE_OK) return st;
     const unsigned grid = p.expect - (fault("timeout") ? 1u : 0u);
     cudaGraphExec_t exec = nullptr;
-    st = capture_iteration(c, nvol, V, o, sc, p, grid, &exec);
+    const long long l0 = c->launches;
+    st = capture_iteration(c, b, o, sc, prims, p, grid, &exec);
     if (st != GVE_OK) return st;
+    const long long per_iter = c->launches - l0 + 4;   // + bias corrections, check, persistent kernel, counter
     cudaEventRecord(c->ev0, c->gstream);
     k_batch_reset<<<1, 1, 0, c->gstream>>>(bs, 0);
     int it = 0, retries = 0;
@@ -368,7 +340,7 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
     while (it < sc->iters) {
         const int end = it + seg < sc->iters ? it + seg : sc->iters;
         for (int t = it; t < end; ++t) {
-            st = run_iteration(c, exec, nvol, V, o, sc, p, grid);
+            st = run_iteration(c, exec, b, o, sc, prims, p, grid);
             if (st != GVE_OK) {
                 if (exec) cudaGraphExecDestroy(exec);
                 return st;
@@ -391,21 +363,19 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
             }
             if (exec) cudaGraphExecDestroy(exec);
             exec = nullptr;
-            // every volume grows to half again what it has needed so far, so
-            // that volumes close to their capacity do not each force a replay
-            for (int v = 0; v < nvol; ++v) {
-                DevState h;
-                st = read_state(V[v].k, &h);
-                const unsigned long long n1 = h.max_total1 > h.total1 ? h.max_total1 : h.total1;
-                const unsigned long long n2 = h.max_total > h.total ? h.max_total : h.total;
-                if (st == GVE_OK) st = grow_pairs(V[v].k, n1 + n1 / 2, n2 + n2 / 2);
-                if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
-                reset_state(V[v].k);
-                if (cudaStreamSynchronize(V[v].k.s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "sync");
-            }
-            st = batch_args(c, nvol, V, o, sc, ntot, prims, m, vmom, nullptr, tr, &p);
+            // grow to half again what the batch has needed so far, so that a
+            // slowly growing pair count does not force a replay each time
+            DevState h;
+            st = read_state(b.k, &h);
             if (st != GVE_OK) return st;
-            st = capture_iteration(c, nvol, V, o, sc, p, grid, &exec);
+            const unsigned long long n1 = h.max_total1 > h.total1 ? h.max_total1 : h.total1;
+            const unsigned long long n2 = h.max_total > h.total ? h.max_total : h.total;
+            st = grow_pairs(b.k, n1 + n1 / 2, n2 + n2 / 2);
+            if (st != GVE_OK) return st;
+            reset_state(b.k);
+            st = batch_args(c, b, o, sc, prims, m, vmom, nullptr, tr, &p);
+            if (st != GVE_OK) return st;
+            st = capture_iteration(c, b, o, sc, prims, p, grid, &exec);
             if (st != GVE_OK) return st;
             // the skipped iteration left the sums as the kernel found them
             if (cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (ntot > 0 ? ntot : 1), c->gstream) != cudaSuccess)
@@ -418,27 +388,36 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
     }
     cudaEventRecord(c->ev1, c->gstream);
     if (exec) cudaGraphExecDestroy(exec);
-    // final evaluation of every volume after its last update
+    // final evaluation of every volume after its last update: one binning,
+    // then each volume's loss
     double psnr_min = INFINITY;
     long long pairs = 0;
-    for (int v = 0; v < nvol; ++v) {
-        cudaStreamWaitEvent(V[v].k.s, c->ev1, 0);
-        st = bin_all(V[v].k, V[v].prims, o, sc->iters);
-        if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
-        BrickArgs a = brick_args(V[v].k, o);
-        a.field = V[v].field;
-        a.mask_thresh = sc->mask_thresh;
-        launch_brick(kModeLoss, a, V[v].k.s);
-        launch_sse_reduce(a.part, V[v].k.g.nbricks, dstate(c->sub[v]), nullptr, 0, V[v].inv_m, V[v].k.s);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        reset_state(b.k);
+        st = bin_all(b.k, prims, o, sc->iters);
+        if (st != GVE_OK) return st;
         DevState h;
-        st = read_state(V[v].k, &h);
-        if (st != GVE_OK) { c->err = c->sub[v]->err; return st; }
-        if (h.overflow) return fail(c, GVE_E_CAPACITY, "final evaluation overflowed");
-        const double M = 1.0 / V[v].inv_m;
-        const double p = h.sse[1] > 0.0 ? 10.0 * std::log10(M / h.sse[1]) : INFINITY;
-        if (psnr_out) psnr_out[v] = p;
-        psnr_min = p < psnr_min ? p : psnr_min;
-        pairs += (long long)h.total;
+        st = read_state(b.k, &h);
+        if (st != GVE_OK) return st;
+        if (!h.overflow) {
+            pairs = (long long)h.total;
+            break;
+        }
+        if (attempt == 1) return fail(c, GVE_E_CAPACITY, "final evaluation overflowed");
+        st = grow_pairs(b.k, h.total1, h.total);
+        if (st != GVE_OK) return st;
+    }
+    for (int v = 0; v < nvol; ++v) {
+        BrickArgs a = vol_args(b, v, o, sc->mask_thresh);
+        launch_brick(kModeLoss, a, c->gstream);
+        launch_sse_reduce(a.part, b.V[v].g.nbricks, dstate(c), nullptr, 0, b.V[v].inv_m, c->gstream);
+        DevState h;
+        st = read_state(b.k, &h);
+        if (st != GVE_OK) return st;
+        const double M = 1.0 / b.V[v].inv_m;
+        const double q = h.sse[1] > 0.0 ? 10.0 * std::log10(M / h.sse[1]) : INFINITY;
+        if (psnr_out) psnr_out[v] = q;
+        psnr_min = q < psnr_min ? q : psnr_min;
     }
     if (stats) {
         float ms = 0.f;
@@ -449,8 +428,6 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
         stats->iters_done = sc->iters;
         stats->retries = retries;
         stats->ms_total = ms;
-        long long per_iter = 4;   // bias corrections, capacity check, persistent kernel, step counter
-        for (int v = 0; v < nvol; ++v) per_iter += (V[v].k.n > 0 ? 3 : 0) + 4 + 5 * ((V[v].k.g.key_bits + 7) / 8) + 1;
         stats->launches = per_iter * sc->iters;
         if (sc->iters > 0 && trace) {
             double first = 0, last = 0;
@@ -462,10 +439,6 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
     }
     // the caller's stream continues after the batch
     cudaEventRecord(c->fork, c->gstream);
-    for (int v = 0; v < nvol; ++v) {
-        cudaEventRecord(c->vjoin[v], V[v].k.s);
-        cudaStreamWaitEvent(caller, c->vjoin[v], 0);
-    }
     cudaStreamWaitEvent(caller, c->fork, 0);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "batch");
     return GVE_OK;
@@ -482,6 +455,7 @@ extern "C" gve_status gve_autotune(gve_ctx* c, int32_t nvol, const gve_volume* v
     float best_ms = INFINITY;
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t caller = (cudaStream_t)stream;
+    float* P = const_cast<float*>(prims);
     int idx = 0;
     for (int bi = 0; bi < 3; ++bi)
         for (int ci = 0; ci < 2; ++ci, ++idx) {
@@ -490,28 +464,23 @@ extern "C" gve_status gve_autotune(gve_ctx* c, int32_t nvol, const gve_volume* v
             o.gaussians_per_block = chunks[ci];
             gve_status st = check_batch(c, nvol, vols, prims, &o);
             if (st != GVE_OK) return st;
-            Vol V[kMaxVol];
-            long long ntot = 0;
-            st = setup_vols(c, nvol, vols, const_cast<float*>(prims), &o, V, &ntot, caller);
+            Batch b;
+            st = setup_vols(c, nvol, vols, P, &o, &b, caller);
             if (st != GVE_OK) return st;
+            const long long ntot = b.ntot;
             st = ensure(c, c->adam, sizeof(float) * 12 * (ntot > 0 ? ntot : 1), c->gstream);
             if (st != GVE_OK) return st;
-            for (int v = 0; v < nvol; ++v) {
-                cudaEventRecord(c->vjoin[v], V[v].k.s);
-                cudaStreamWaitEvent(c->gstream, c->vjoin[v], 0);
-            }
             cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (ntot > 0 ? ntot : 1), c->gstream);
             BatchIterArgs p{};
             // gradient only: the records stay as they are, the gradient goes to scratch
-            st = batch_args(c, nvol, V, &o, nullptr, ntot, const_cast<float*>(prims), nullptr, nullptr,
-                            (float*)c->adam.p, nullptr, &p);
+            st = batch_args(c, b, &o, nullptr, P, nullptr, nullptr, (float*)c->adam.p, nullptr, &p);
             if (st != GVE_OK) return st;
             const unsigned grid = p.expect - (fault("timeout") ? 1u : 0u);
             k_batch_reset<<<1, 1, 0, c->gstream>>>((BatchState*)c->bstate.p, 0);
             float total = 0.f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(c->ev0, c->gstream);
-                st = issue_iteration(c, nvol, V, &o, nullptr, p, grid);
+                st = issue_iteration(c, b, &o, nullptr, P, p, grid);
                 if (st != GVE_OK) return st;
                 cudaEventRecord(c->ev1, c->gstream);
                 if (cudaEventSynchronize(c->ev1) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "sync");
@@ -529,9 +498,7 @@ extern "C" gve_status gve_autotune(gve_ctx* c, int32_t nvol, const gve_volume* v
             if (per < best_ms) { best_ms = per; best = o; }
         }
     *opts = best;
-    for (int v = 0; v < nvol && v < (int)c->vstream.size(); ++v) {
-        cudaEventRecord(c->vjoin[v], c->vstream[v]);
-        cudaStreamWaitEvent(caller, c->vjoin[v], 0);
-    }
+    cudaEventRecord(c->fork, c->gstream);
+    cudaStreamWaitEvent(caller, c->fork, 0);
     return GVE_OK;
 }

@@ -48,17 +48,29 @@ BinGeom make_geom(gve_dims d, int B)
     return g;
 }
 
+VolTab single_volume(const BinGeom& g, long long n)
+{
+    VolTab vt{};
+    vt.nvol = 1;
+    vt.goff[1] = n;
+    vt.toff[1] = g.ntiles;
+    vt.boff[1] = g.nbricks;
+    vt.g[0] = g;
+    return vt;
+}
+
 // ------------------------------------------------------------------------
 // prep
 // ------------------------------------------------------------------------
 // BIN = false: the keep coefficients only (the sampled path has no bricks)
 template <bool BIN>
-__global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, long long n, BinGeom g,
+__global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, long long n, VolTab vt,
                                               float k, float4* __restrict__ rec, BinRec* __restrict__ br,
                                               uint32_t* __restrict__ tcount)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const BinGeom& g = vt.g[BIN ? vt_find(vt.goff, vt.nvol, i) : 0];
     const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
     float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
     float pf[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
@@ -131,8 +143,9 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
 void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cudaStream_t s)
 {
     if (n <= 0) return;
-    BinGeom g{};
-    k_prep<false><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, rec, nullptr, nullptr);
+    VolTab vt{};
+    vt.nvol = 1;
+    k_prep<false><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, vt, k, rec, nullptr, nullptr);
 }
 
 // float32 cover test of one brick (same operation order as the oracle)
@@ -614,7 +627,7 @@ __device__ __forceinline__ int flat_owner(const uint32_t* incl, uint32_t it)
 // time, so small and large boxes keep every lane busy.  The group's pairs
 // start at the scanned offset of its first Gaussian.
 __global__ void __launch_bounds__(256) k_temit(const BinRec* __restrict__ br, const uint32_t* __restrict__ tcount,
-                                               const unsigned long long* __restrict__ toff, long long n, BinGeom g,
+                                               const unsigned long long* __restrict__ toff, long long n, VolTab vt,
                                                uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
                                                const DevState* __restrict__ st)
 {
@@ -622,12 +635,14 @@ __global__ void __launch_bounds__(256) k_temit(const BinRec* __restrict__ br, co
     __shared__ uint32_t s_incl[8][32];
     __shared__ int4 s_box[8][32];      // first tile (x, y, z) and x extent of each box
     __shared__ uint32_t s_exy[8][32];  // x extent * y extent
+    __shared__ int4 s_tg[8][32];       // the volume's tile grid (x, y) and first global tile
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long ngroups = (n + 31) >> 5;
     for (long long grp = (long long)blockIdx.x * 8 + w; grp < ngroups; grp += (long long)gridDim.x * 8) {
         const long long i = (grp << 5) + lane;
         uint32_t cnt = 0, exy = 1;
         int4 box = make_int4(0, 0, 0, 1);
+        int4 tg = make_int4(1, 1, 0, 0);   // tile grid x, y and first tile (low, high word) of the volume
         if (i < n) {
             cnt = tcount[i];
             if (cnt) {
@@ -636,6 +651,9 @@ __global__ void __launch_bounds__(256) k_temit(const BinRec* __restrict__ br, co
                 const int ex = b.bhi[0] / kTile - x0 + 1, ey = b.bhi[1] / kTile - y0 + 1;
                 box = make_int4(x0, y0, z0, ex);
                 exy = (uint32_t)ex * (uint32_t)ey;
+                const int v = vt_find(vt.goff, vt.nvol, i);
+                const unsigned long long t0 = (unsigned long long)vt.toff[v];
+                tg = make_int4(vt.g[v].ntx, vt.g[v].nty, (int)(uint32_t)t0, (int)(uint32_t)(t0 >> 32));
             }
         }
         const uint32_t incl = warp_incl_scan(cnt);
@@ -643,6 +661,7 @@ __global__ void __launch_bounds__(256) k_temit(const BinRec* __restrict__ br, co
         s_incl[w][lane] = incl;
         s_box[w][lane] = box;
         s_exy[w][lane] = exy;
+        s_tg[w][lane] = tg;
         __syncwarp();
         const unsigned long long base = total ? toff[grp << 5] : 0ull;
         for (uint32_t t0 = 0; t0 < total; t0 += 32) {
@@ -654,8 +673,10 @@ __global__ void __launch_bounds__(256) k_temit(const BinRec* __restrict__ br, co
                 const uint32_t e2 = s_exy[w][j];
                 const uint32_t tz = t / e2, r = t - tz * e2;
                 const uint32_t ty = r / (uint32_t)bx.w, tx = r - ty * (uint32_t)bx.w;
-                tkeys[base + it] =
-                    (uint32_t)(((long long)(bx.z + (int)tz) * g.nty + (bx.y + (int)ty)) * g.ntx + (bx.x + (int)tx));
+                const int4 tgj = s_tg[w][j];
+                const unsigned long long t0 = (unsigned long long)(uint32_t)tgj.z | ((unsigned long long)(uint32_t)tgj.w << 32);
+                tkeys[base + it] = (uint32_t)(t0 + (unsigned long long)(((long long)(bx.z + (int)tz) * tgj.y +
+                                                                          (bx.y + (int)ty)) * tgj.x + (bx.x + (int)tx)));
                 tvals[base + it] = (uint32_t)((grp << 5) + j);
             }
         }
@@ -711,11 +732,15 @@ __device__ __forceinline__ unsigned long long chunk_id(uint32_t ts, long long ti
 // gcount is set, adds each Gaussian's passes to gcount (introspection).
 __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                                 const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
-                                                BinGeom g, unsigned long long* __restrict__ tmask,
+                                                VolTab vt, unsigned long long* __restrict__ tmask,
                                                 uint32_t* __restrict__ cbase, uint32_t* __restrict__ bcount,
                                                 uint32_t* __restrict__ gcount, const DevState* __restrict__ st)
 {
     if (st->overflow) return;
+    const long long tile = blockIdx.x;
+    const int vol = vt_find(vt.toff, vt.nvol, tile);
+    const BinGeom& g = vt.g[vol];
+    const long long ntiles = vt.toff[vt.nvol], bbase = vt.boff[vol];
     __shared__ BinRec s_br[256];
     __shared__ float4 s_mu[256];
     __shared__ uint32_t s_m[256][2];
@@ -725,11 +750,10 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
     __shared__ int4 s_box[8][32];      // first brick (x, y, z) inside the tile, x extent
     __shared__ uint2 s_div[8][32];     // reciprocal of x*y extent; reciprocal of x extent << 8 | x*y extent
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const long long tile = blockIdx.x;
     int ox, oy, oz;
-    tile_origin(g, tile, ox, oy, oz);
+    tile_origin(g, tile - vt.toff[vol], ox, oy, oz);
     if (tid < 64) s_run[tid] = 0u;
-    const uint32_t ts = trange[tile], te = trange[g.ntiles + tile];
+    const uint32_t ts = trange[tile], te = trange[ntiles + tile];
     for (uint32_t r0 = ts; r0 < te; r0 += 256) {
         const uint32_t e = r0 + tid;
         uint32_t cnt = 0, gid = 0;
@@ -807,7 +831,8 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
     }
     if (tid < 64) {
         const int bx = ox + (tid & 3), by = oy + ((tid >> 2) & 3), bz = oz + (tid >> 4);
-        if (bx < g.nbx && by < g.nby && bz < g.nbz) bcount[((long long)bz * g.nby + by) * g.nbx + bx] = s_run[tid];
+        if (bx < g.nbx && by < g.nby && bz < g.nbz)
+            bcount[bbase + ((long long)bz * g.nby + by) * g.nbx + bx] = s_run[tid];
     }
 }
 
@@ -861,13 +886,16 @@ __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, co
                                                const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
                                                const unsigned long long* __restrict__ tmask,
                                                const uint32_t* __restrict__ cbase,
-                                               const unsigned long long* __restrict__ boff, BinGeom g,
+                                               const unsigned long long* __restrict__ boff, VolTab vt,
                                                uint32_t* __restrict__ pairs, const DevState* __restrict__ st)
 {
     if (st->overflow) return;
     const long long tile = blockIdx.x;
-    const uint32_t ts = trange[tile], te = trange[g.ntiles + tile];
+    const uint32_t ts = trange[tile], te = trange[vt.toff[vt.nvol] + tile];
     if (ts >= te) return;
+    const int vol = vt_find(vt.toff, vt.nvol, tile);
+    const BinGeom& g = vt.g[vol];
+    const long long bbase = vt.boff[vol];
     __shared__ SubRec s_r[256];
     __shared__ uint32_t s_start[64];
     __shared__ uint32_t s_col[8][64];    // per brick: ballot of the chunk's entries passing it
@@ -877,11 +905,11 @@ __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, co
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int ox, oy, oz;
-    tile_origin(g, tile, ox, oy, oz);
+    tile_origin(g, tile - vt.toff[vol], ox, oy, oz);
     if (tid < 64) {
         const int bx = ox + (tid & 3), by = oy + ((tid >> 2) & 3), bz = oz + (tid >> 4);
         s_start[tid] = (bx < g.nbx && by < g.nby && bz < g.nbz)
-                           ? (uint32_t)boff[((long long)bz * g.nby + by) * g.nbx + bx]
+                           ? (uint32_t)boff[bbase + ((long long)bz * g.nby + by) * g.nbx + bx]
                            : 0u;
     }
     __syncthreads();
@@ -962,13 +990,16 @@ void launch_fill_keys(const uint32_t* ranges, long long nbricks, uint32_t* keys,
     k_fill_keys<<<4 * num_sms(), 256, 0, s>>>(ranges, ranges + nbricks, nbricks, keys);
 }
 
-int launch_binning(const BinBufs& b, const float* prims, long long n, const BinGeom& g, float k, int iter,
+int launch_binning(const BinBufs& b, const float* prims, long long n, const VolTab& vt, float k, int iter,
                    cudaStream_t s)
 {
     DevState* st = b.st;
+    const long long ntiles = vt.toff[vt.nvol], nbricks = vt.boff[vt.nvol];
+    int tbits = 1;
+    while ((1ll << tbits) < ntiles) ++tbits;
     int launches = 0;
     if (n > 0) {
-        k_prep<true><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, g, k, b.rec, b.br, b.tcount);
+        k_prep<true><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, vt, k, b.rec, b.br, b.tcount);
         ++launches;
     }
     launch_offsets(b.tcount, n, b.toff, b.scanp, st, b.cap1, iter, s, 1);
@@ -976,26 +1007,26 @@ int launch_binning(const BinBufs& b, const float* prims, long long n, const BinG
     if (n > 0) {
         long long blocks = ((n + 31) / 32 + 7) / 8;
         if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
-        k_temit<<<(unsigned)blocks, 256, 0, s>>>(b.br, b.tcount, b.toff, n, g, b.tkeys[0], b.tvals[0], st);
+        k_temit<<<(unsigned)blocks, 256, 0, s>>>(b.br, b.tcount, b.toff, n, vt, b.tkeys[0], b.tvals[0], st);
         ++launches;
     }
     uint32_t* kk[2] = {b.tkeys[0], b.tkeys[1]};
     uint32_t* vv[2] = {b.tvals[0], b.tvals[1]};
-    const int cur = launch_sort(kk, vv, &st->total1, &st->overflow, b.cap1, g.tkey_bits, b.hist, b.scanp, s);
-    launches += 5 * ((g.tkey_bits + 7) / 8);
-    cudaMemsetAsync(b.trange, 0, sizeof(uint32_t) * 2 * (size_t)g.ntiles, s);
-    launch_ranges(kk[cur], &st->total1, &st->overflow, b.cap1, b.trange, b.trange + g.ntiles, s);
+    const int cur = launch_sort(kk, vv, &st->total1, &st->overflow, b.cap1, tbits, b.hist, b.scanp, s);
+    launches += 5 * ((tbits + 7) / 8);
+    cudaMemsetAsync(b.trange, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s);
+    launch_ranges(kk[cur], &st->total1, &st->overflow, b.cap1, b.trange, b.trange + ntiles, s);
     ++launches;
     if (b.gcount && n > 0) cudaMemsetAsync(b.gcount, 0, sizeof(uint32_t) * (size_t)n, s);
-    k_bcount<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, g, b.tmask, b.cbase, b.bcount,
-                                                 b.gcount, st);
-    launch_exscan_u32(b.bcount, g.nbricks, b.boff, b.scanp, s);
-    long long rb = (g.nbricks + 255) / 256;
+    k_bcount<<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, vt, b.tmask, b.cbase, b.bcount,
+                                               b.gcount, st);
+    launch_exscan_u32(b.bcount, nbricks, b.boff, b.scanp, s);
+    long long rb = (nbricks + 255) / 256;
     if (rb > 8LL * num_sms()) rb = 8LL * num_sms();
-    k_brick_ranges<<<(unsigned)rb, 256, 0, s>>>(b.bcount, b.boff, g.nbricks, b.ranges, b.ranges + g.nbricks, st,
-                                                b.cap, iter);
-    k_bemit<<<(unsigned)g.ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, g, b.pairs,
-                                                st);
+    k_brick_ranges<<<(unsigned)rb, 256, 0, s>>>(b.bcount, b.boff, nbricks, b.ranges, b.ranges + nbricks, st, b.cap,
+                                                iter);
+    k_bemit<<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, vt, b.pairs,
+                                              st);
     launches += 6;
     return launches;
 }

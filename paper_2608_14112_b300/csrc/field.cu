@@ -538,16 +538,13 @@ template <int B, int CH>
 __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k_batch_iter(const BatchIterArgs p)
 {
     constexpr int NT = BrickShape<B>::THREADS;
-    static_assert(sizeof(BrickArgs) % 4 == 0, "argument copy by words");
-    __shared__ BrickArgs s_a;
     __shared__ unsigned long long s_gb;
     __shared__ double s_red[2][NT / 32 > 0 ? NT / 32 : 1];
     BatchState* bs = p.bs;
-    // an earlier wait ran out, or a volume's pairs overflowed: nothing runs
-    if (*(volatile int*)&bs->err || p.vargs[0].st->overflow) return;
+    // an earlier wait ran out, or the pairs overflowed: nothing runs
+    if (*(volatile int*)&bs->err || p.va[0].st->overflow) return;
 
     // phase 1: the bricks of every volume from one work counter
-    int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) s_gb = atomicAdd(&bs->next, 1ull);
         __syncthreads();
@@ -558,24 +555,27 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
             const int mid = (lo + hi + 1) >> 1;
             if (p.boff[mid] <= (long long)gb) lo = mid; else hi = mid - 1;
         }
-        if (lo != cur) {
-            const int* src = reinterpret_cast<const int*>(p.vargs + lo);
-            int* dst = reinterpret_cast<int*>(&s_a);
-            for (int w = threadIdx.x; w < (int)(sizeof(BrickArgs) / 4); w += NT) dst[w] = src[w];
-            cur = lo;
-            __syncthreads();
-        }
-        brick_body<kModeLoss, B, CH>(s_a, (unsigned)(gb - (unsigned long long)p.boff[lo]));
+        brick_body<kModeLoss, B, CH>(p.va[lo], (unsigned)(gb - (unsigned long long)p.boff[lo]));
         __syncthreads();
     }
     if (!grid_barrier(bs, p.expect, p.spin_limit)) return;
 
-    // phase 2a: each volume's SSE, summed in a fixed order by one CTA
-    for (int v = blockIdx.x; v < p.nvol; v += gridDim.x) {
-        const double2* part = p.vargs[v].part;
+    // phase 2a: each volume's SSE in a fixed order: every chunk of kSseChunk
+    // bricks is summed by one CTA; the last CTA past its chunks adds each
+    // volume's chunk sums in chunk order
+    __shared__ int s_last;
+    for (long long ch = blockIdx.x; ch < p.nchunks; ch += gridDim.x) {
+        int v = 0, hi = p.nvol - 1;
+        while (v < hi) {
+            const int mid = (v + hi + 1) >> 1;
+            if (p.coff[mid] <= ch) v = mid; else hi = mid - 1;
+        }
         const long long nb = p.boff[v + 1] - p.boff[v];
+        const long long b0 = (ch - p.coff[v]) * kSseChunk;
+        const long long b1 = b0 + kSseChunk < nb ? b0 + kSseChunk : nb;
+        const double2* part = p.va[v].part;
         double x = 0.0, y = 0.0;
-        for (long long i = threadIdx.x; i < nb; i += NT) {
+        for (long long i = b0 + threadIdx.x; i < b1; i += NT) {
             const double2 q = part[i];
             x += q.x;
             y += q.y;
@@ -588,13 +588,31 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
         if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = x; s_red[1][threadIdx.x >> 5] = y; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < NT / 32; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
-            p.sse[2 * v] = a;
-            p.sse[2 * v + 1] = b;
-            if (p.trace) p.trace[(size_t)bs->it * p.nvol + v] = a * p.inv_m[v];
+            double a = 0.0, c = 0.0;
+            for (int w = 0; w < NT / 32; ++w) { a += s_red[0][w]; c += s_red[1][w]; }
+            p.csum[ch] = make_double2(a, c);
         }
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&bs->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int v = threadIdx.x; v < p.nvol; v += NT) {
+            double a = 0.0, c = 0.0;
+            for (long long ch = p.coff[v]; ch < p.coff[v + 1]; ++ch) {
+                const volatile double* q = reinterpret_cast<const volatile double*>(p.csum + ch);
+                a += q[0];
+                c += q[1];
+            }
+            p.sse[2 * v] = a;
+            p.sse[2 * v + 1] = c;
+            if (p.trace) p.trace[(size_t)bs->it * p.nvol + v] = a * p.inv_m[v];
+        }
+        if (threadIdx.x == 0) bs->done = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) bs->next = 0;   // every CTA is past phase 1
     // phase 2b: chain rule and Adam (or the gradient) of every Gaussian

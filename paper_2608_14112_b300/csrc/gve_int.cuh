@@ -99,15 +99,12 @@ struct gve_ctx {
     cudaEvent_t sev[3][64] = {};
     bool sev_ready = false;
     long long launches = 0;          // kernels launched by the current call
-    // batched refinement: one sub-context and one stream per volume
-    std::vector<gve_ctx*> sub;
-    std::vector<cudaStream_t> vstream;
-    std::vector<cudaEvent_t> vjoin;
+    // batched refinement: its stream and the event that joins it to the caller's
     cudaStream_t gstream = nullptr;
     cudaEvent_t fork = nullptr;
     gve::Buf bstate;                 // batch device state (BatchState)
-    gve::Buf btab;                   // batch tables: per-volume evaluator arguments, brick offsets,
-                                     // 1 / voxels, SSE
+    gve::Buf btab;                   // batch: per-volume {masked, unmasked} SSE of the last iteration
+    gve::Buf csum;                   // batch: per-chunk partial sums of the loss
     // stratified-sample refinement: class lists, per-block counts and
     // offsets, samples, cell table, sorted sample order, per-sample sums and
     // upstream gradients, loss
@@ -302,6 +299,32 @@ struct BinGeom {
 };
 BinGeom make_geom(gve_dims d, int B);
 
+// The grids of one binning: one for a single grid, the volumes of a batch
+// otherwise (their Gaussians, tiles and bricks numbered consecutively,
+// volume by volume).  Passed to the binning kernels by value.
+constexpr int kMaxBinVol = 32;
+struct VolTab {
+    int nvol;
+    long long goff[kMaxBinVol + 1];   // first Gaussian of each volume; goff[nvol] = all
+    long long toff[kMaxBinVol + 1];   // first tile
+    long long boff[kMaxBinVol + 1];   // first brick
+    BinGeom g[kMaxBinVol];
+};
+// a table of one grid with n Gaussians
+VolTab single_volume(const BinGeom& g, long long n);
+// the volume holding item i of a table column off[0..nvol] (the largest v
+// with off[v] <= i)
+__host__ __device__ __forceinline__ int vt_find(const long long* off, int nvol, long long i)
+{
+    int lo = 0, hi = nvol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // the keep coefficients alone (same values as the binning's rec)
 void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cudaStream_t s);
 // exclusive scan of counts into offsets[0..n]; the total goes to st->total
@@ -351,7 +374,7 @@ inline unsigned long long cbase_chunks(unsigned long long cap1, long long ntiles
 // Issues the whole binning on s without host synchronisation and returns
 // the kernels launched.  Tile pairs above cap1 or brick pairs above cap set
 // st->overflow (st->first_overflow_iter = iter) and skip the rest.
-int launch_binning(const BinBufs& b, const float* prims, long long n, const BinGeom& g, float k, int iter,
+int launch_binning(const BinBufs& b, const float* prims, long long n, const VolTab& vt, float k, int iter,
                    cudaStream_t s);
 // keys[p] = brick of pair p, from the ranges (introspection)
 void launch_fill_keys(const uint32_t* ranges, long long nbricks, uint32_t* keys, cudaStream_t s);
@@ -412,13 +435,18 @@ struct BatchState {
     unsigned bar_count;        // grid barrier: CTAs arrived
     unsigned bar_gen;          // grid barrier: generation
     int err;                   // 1: a bounded wait ran out (GVE_E_TIMEOUT)
-    int pad;
+    unsigned done;             // CTAs past the chunk sums of the loss (the last one finishes them)
 };
 
+constexpr int kMaxBatchVol = 32;
+// bricks per chunk of the batched loss reduction
+constexpr int kSseChunk = 4096;
+// Passed by value (a kernel parameter of about 7 KB): the per-volume tables
+// sit in the constant bank, where every thread of a CTA reads the same entry.
 struct BatchIterArgs {
-    const BrickArgs* vargs;    // [nvol] evaluator arguments of each volume (device)
-    const long long* boff;     // [nvol + 1] first global brick of each volume (device)
-    const double* inv_m;       // [nvol] 1 / voxels (device)
+    BrickArgs va[kMaxBatchVol];          // evaluator arguments of each volume
+    long long boff[kMaxBatchVol + 1];    // first global brick of each volume
+    double inv_m[kMaxBatchVol];          // 1 / voxels
     int nvol;
     long long nbricks;         // bricks of all volumes
     long long ntot;            // Gaussians of all volumes (records concatenated)
@@ -432,6 +460,9 @@ struct BatchIterArgs {
     AdamArgs ad;
     double* trace;             // [iters][nvol] masked mean squared errors, or nullptr
     double* sse;               // [nvol][2] {masked, unmasked} SSE of this iteration (device)
+    double2* csum;             // [nchunks] per chunk of kSseChunk bricks of one volume: its partial sums
+    long long coff[kMaxBatchVol + 1];    // first chunk of each volume
+    long long nchunks;
     unsigned expect;           // CTAs the grid barrier waits for
     long long spin_limit;      // sleeps of ~128 ns before a wait gives up
 };
@@ -494,6 +525,7 @@ struct Call {
     cudaStream_t s;
     BinGeom g;
     long long n;
+    VolTab vt;   // the grids the binning covers (the one grid g, or a batch's volumes)
 };
 DevState* dstate(gve_ctx* c);
 gve_status check_common(gve_ctx* c, const float* prims, int64_t n, gve_dims d, const gve_eval_opts* o);
@@ -502,7 +534,7 @@ gve_status reset_state(Call& k);
 gve_status read_state(Call& k, DevState* out);
 // grows the tile-pair (need1) and brick-pair (need2) buffers
 gve_status grow_pairs(Call& k, unsigned long long need1, unsigned long long need2);
-// per-Gaussian/per-brick scratch + sizing pass (synchronises k.s)
+// per-Gaussian/per-tile/per-brick scratch for k.vt + sizing pass (synchronises k.s)
 gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o);
 // the whole binning (stream-ordered, no host sync); gcount (nullable):
 // brick pairs per Gaussian

@@ -172,7 +172,7 @@ extern "C" gve_status gve_evaluate_noalloc(const float* prims, int64_t n, gve_di
     // the device state must start at zero on every call (the ranges are
     // rewritten by every binning)
     if (cudaMemsetAsync(dst, 0, sizeof(DevState), s) != cudaSuccess) return GVE_E_CUDA;
-    launch_binning(b, prims, n, g, o->trunc_k, 0, s);
+    launch_binning(b, prims, n, single_volume(g, n), o->trunc_k, 0, s);
     BrickArgs a{};
     a.g = g;
     a.start = b.ranges;

@@ -203,7 +203,11 @@ def time_to_psnr(V, w, opts, seed, alloc_ms, full=2000, reduced=300):
     PSNR - 0.1 dB; its time is the allocation plus the iterations needed to
     first reach it, at this run's own ms per iteration (CUDA events).  The
     reduced schedule is the same run's first `reduced` iterations (constant
-    learning rate: a shorter schedule is a prefix of the longer one)."""
+    learning rate: a shorter schedule is a prefix of the longer one).  Late in
+    the run the PSNR moves by a few tenths of a dB from one iteration to the
+    next (constant-step Adam), so the final value is one sample of that
+    motion; the same measure is also given against the median PSNR of the
+    last 50 iterations ("smoothed")."""
     import numpy as np
     import torch
     from paper_2608_14112_b300 import gve
@@ -229,13 +233,19 @@ def time_to_psnr(V, w, opts, seed, alloc_ms, full=2000, reduced=300):
     final = float(st["psnr_final"])
     target = final - 0.1
     t_star = int(np.nonzero(after >= target)[0][0]) + 1
+    tail = float(np.median(after[-50:]))
+    t_smooth = int(np.nonzero(after >= tail - 0.1)[0][0]) + 1
     red = float(after[reduced - 1])
     return {"schedule_full": full, "schedule_reduced": reduced, "psnr_full_db": final,
             "psnr_reduced_db": red, "reduced_gap_db": final - red, "target_db": target,
             "iters_to_target": t_star, "ms_per_iter": ms_iter, "alloc_ms": alloc_ms,
             "full_s": (alloc_ms + full * ms_iter) / 1e3, "reduced_s": (alloc_ms + reduced * ms_iter) / 1e3,
             "time_to_target_s": (alloc_ms + t_star * ms_iter) / 1e3,
-            "reduced_reaches_target": bool(red >= target), "launches": int(st["launches"]),
+            "reduced_reaches_target": bool(red >= target),
+            "smoothed": {"final_median_last50_db": tail, "target_db": tail - 0.1, "iters_to_target": t_smooth,
+                         "time_to_target_s": (alloc_ms + t_smooth * ms_iter) / 1e3,
+                         "last50_min_max_db": [float(after[-50:].min()), float(after[-50:].max())]},
+            "launches": int(st["launches"]),
             "kept_pairs_start_end": [int(kept_start), int(kept_end)], "clocks": clk,
             "psnr_at": {str(t): float(after[t - 1]) for t in (1, 10, 50, 100, 300, 500, 1000, 1500, 2000) if t <= full}}
 
@@ -349,7 +359,9 @@ def run_reference(args):
 def run_batched(args):
     """16 uneven GRF volumes (8 cubes 96^3..384^3, 8 slabs), budgets = voxels
     / 64 rounded half-up to 1,024: batched encode (one graph launch per
-    iteration) against the same volumes encoded one after another."""
+    iteration) against the same volumes encoded one after another; the
+    speedup is given for the whole encode (allocations included, the same
+    sequential allocations on both sides) and for the refinement alone."""
     import numpy as np
     import torch
     from paper_2608_14112_b300 import batched
@@ -374,9 +386,14 @@ def run_batched(args):
     # the same volumes one after another through gve_refine
     t0 = time.perf_counter()
     psnr_seq = []
+    t_seq_refine = 0.0
     for f, n in zip(fields, budgets):
         P, _ = gve.gve_allocate(f, n, seed=args.seed)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         st = gve.gve_refine(P, f, iters=iters, opts=warm.options)
+        torch.cuda.synchronize()
+        t_seq_refine += time.perf_counter() - t1
         psnr_seq.append(st["psnr_final"])
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
@@ -388,6 +405,8 @@ def run_batched(args):
            "config": {"workload": "batched_16_grf", "voxels": nvox, "gaussians": int(sum(budgets)),
                       "brick": res.options.brick, "gaussians_per_block": res.options.gaussians_per_block},
            "batched_wall_s": t_batch, "sequential_wall_s": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+           "refine_s": {"batched": res.refine_s, "sequential": t_seq_refine},
+           "speedup_vs_sequential_refine": t_seq_refine / res.refine_s,
            "psnr_batched": res.psnr, "psnr_sequential": psnr_seq,
            "max_psnr_gap_db": float(np.max(np.abs(np.array(res.psnr) - np.array(psnr_seq)))),
            "alloc_s": res.alloc_s, "autotune_ms": {f"{k[0]}x{k[1]}": v for k, v in res.tune_ms.items()}}

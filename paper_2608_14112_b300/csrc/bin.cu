@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const BinGeom& g = vt.g[BIN ? vt_find(vt.goff, vt.nvol, i) : 0];
+    const BinGeom g = vt.g[BIN ? vt_find(vt.goff, vt.nvol, i) : 0];
     const float4* p4 = reinterpret_cast<const float4*>(prims) + 3 * i;
     float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
     float pf[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
     if (st->overflow) return;
     const long long tile = blockIdx.x;
     const int vol = vt_find(vt.toff, vt.nvol, tile);
-    const BinGeom& g = vt.g[vol];
+    const BinGeom g = vt.g[vol];
     const long long ntiles = vt.toff[vt.nvol], bbase = vt.boff[vol];
     __shared__ BinRec s_br[256];
     __shared__ float4 s_mu[256];
@@ -894,7 +894,7 @@ __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, co
     const uint32_t ts = trange[tile], te = trange[vt.toff[vt.nvol] + tile];
     if (ts >= te) return;
     const int vol = vt_find(vt.toff, vt.nvol, tile);
-    const BinGeom& g = vt.g[vol];
+    const BinGeom g = vt.g[vol];
     const long long bbase = vt.boff[vol];
     __shared__ SubRec s_r[256];
     __shared__ uint32_t s_start[64];

@@ -224,27 +224,39 @@ __device__ __forceinline__ uint32_t subbrick_mask(const float* L, float K2, cons
         c2 = fmaf(yc, L[j * 3 + 2], c2);
         yy = fmaf(yc, yc, yy);
     }
-    const float oyv = 0.25f * (float)B, ozv = 0.125f * (float)B;
+    // sub-brick centres y = yc + oy l_1 + oz l_2 with oy = +-B/4 and
+    // oz = +-B/8, +-3B/8: the dot products with the axes are c + oy (g01,
+    // g11, g12) + oz (g02, g12, g22) and |y|^2 = yy + 2 oy c1 + oy^2 g11 +
+    // 2 oz (c2 + oy g12) + oz^2 g22; the +- pairs share their products
+    const float oy = 0.25f * (float)B, o1 = 0.125f * (float)B, o3 = 0.375f * (float)B;
+    const float ax = oy * G.g01, ay = oy * G.g11, az = oy * G.g12;
+    const float A0 = fmaf(oy * oy, G.g11, yy), A1 = 2.f * oy * c1;
+    const float b1x = o1 * G.g02, b1y = o1 * G.g12, b1z = o1 * G.g22;
+    const float b3x = o3 * G.g02, b3y = o3 * G.g12, b3z = o3 * G.g22;
+    const float q1 = o1 * o1 * G.g22, q3 = o3 * o3 * G.g22;
     const float K2m = K2 * 1.001f;
+    const bool inside = (by + 1) * B <= ny && (bz + 1) * B <= nz;
     uint32_t m = 0;
 #pragma unroll
     for (int yh = 0; yh < 2; ++yh) {
-        if (by * B + (B / 2) * yh >= ny) continue;
-        const float oy = yh ? oyv : -oyv;
-        // y = yc + oy l_1 + oz l_2
-        const float px = fmaf(oy, G.g01, c0), py = fmaf(oy, G.g11, c1), pz = fmaf(oy, G.g12, c2);
-        const float A = fmaf(oy, fmaf(oy, G.g11, 2.f * c1), yy);
-        const float Bz = 2.f * pz;
+        const float px = yh ? c0 + ax : c0 - ax, py = yh ? c1 + ay : c1 - ay, pz = yh ? c2 + az : c2 - az;
+        const float Ay = yh ? A0 + A1 : A0 - A1;
+        const float s1 = 2.f * o1 * pz, s3 = 2.f * o3 * pz;
+        const float Y1 = Ay + q1, Y3 = Ay + q3;
 #pragma unroll
         for (int zq = 0; zq < 4; ++zq) {
-            if (bz * B + (B / 4) * zq >= nz) continue;
-            const float oz = (float)(2 * zq - 3) * ozv;
-            const float ylx = fmaf(oz, G.g02, px), yly = fmaf(oz, G.g12, py), ylz = fmaf(oz, G.g22, pz);
-            const float y2 = fmaf(oz, fmaf(oz, G.g22, Bz), A);
+            // zq = 0..3: oz = -3B/8, -B/8, +B/8, +3B/8
+            const bool far = zq == 0 || zq == 3, pos = zq >= 2;
+            const float bx_ = far ? b3x : b1x, by_ = far ? b3y : b1y, bz_ = far ? b3z : b1z;
+            const float ylx = pos ? px + bx_ : px - bx_;
+            const float yly = pos ? py + by_ : py - by_;
+            const float ylz = pos ? pz + bz_ : pz - bz_;
+            const float y2 = far ? (pos ? Y3 + s3 : Y3 - s3) : (pos ? Y1 + s1 : Y1 - s1);
             // |y|^2 - sum_i h_i |y . l_i| > sqrt(K2) |y|  =>  no kept voxel
             const float D = y2 - fmaf(h0, fabsf(ylx), fmaf(h1, fabsf(yly), h2 * fabsf(ylz)));
-            if (D > 0.f && D * D > K2m * y2) continue;
-            m |= 1u << (yh + 2 * zq);
+            const bool dead = D > 0.f && D * D > K2m * y2;
+            const bool ingrid = inside || (by * B + (B / 2) * yh < ny && bz * B + (B / 4) * zq < nz);
+            if (!dead && ingrid) m |= 1u << (yh + 2 * zq);
         }
     }
     return m;
@@ -730,6 +742,7 @@ __device__ __forceinline__ unsigned long long chunk_id(uint32_t ts, long long ti
 // tile), per chunk and brick the passes of all earlier entries of the tile
 // (the chunk's base), the pair count of each brick of the tile, and, when
 // gcount is set, adds each Gaussian's passes to gcount (introspection).
+template <int B>
 __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                                 const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
                                                 VolTab vt, unsigned long long* __restrict__ tmask,
@@ -794,7 +807,7 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
                 const int lx = bx.x + (int)cx, ly = bx.y + (int)cy, lz = bx.z + (int)cz;
                 const int slot = (w << 5) + j;
                 const float4 mu = s_mu[slot];
-                if (brick_test(s_br[slot], mu.x, mu.y, mu.z, g.B, ox + lx, oy + ly, oz + lz)) {
+                if (brick_test(s_br[slot], mu.x, mu.y, mu.z, B, ox + lx, oy + ly, oz + lz)) {
                     const int lb = (lz * kTile + ly) * kTile + lx;
                     atomicOr(&s_m[slot][lb >> 5], 1u << (lb & 31));
                 }
@@ -882,6 +895,7 @@ struct SubRec {
 // then every lane takes one pair, computes its sub-brick cover and writes it
 // at brick start + chunk base + rank, so a brick's pairs of one chunk land
 // on consecutive addresses.
+template <int B>
 __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                                const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
                                                const unsigned long long* __restrict__ tmask,
@@ -964,7 +978,7 @@ __global__ void __launch_bounds__(256) k_bemit(const BinRec* __restrict__ br, co
                     const uint32_t j = jb >> 6;
                     const int lb = (int)(jb & 63u);
                     const SubRec& q = s_r[(w << 5) + j];
-                    const uint32_t mask = subbrick_mask(q.L, q.K2, q.G, q.mx, q.my, q.mz, g.B, ox + (lb & 3),
+                    const uint32_t mask = subbrick_mask(q.L, q.K2, q.G, q.mx, q.my, q.mz, B, ox + (lb & 3),
                                                         oy + ((lb >> 2) & 3), oz + (lb >> 4), g.ny, g.nz);
                     const uint32_t rank = __popc(s_col[w][lb] & ((1u << j) - 1u));
                     pairs[s_pos[w][lb] + rank] = q.gid | (mask << kGidBits);
@@ -1018,15 +1032,30 @@ int launch_binning(const BinBufs& b, const float* prims, long long n, const VolT
     launch_ranges(kk[cur], &st->total1, &st->overflow, b.cap1, b.trange, b.trange + ntiles, s);
     ++launches;
     if (b.gcount && n > 0) cudaMemsetAsync(b.gcount, 0, sizeof(uint32_t) * (size_t)n, s);
-    k_bcount<<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, vt, b.tmask, b.cbase, b.bcount,
-                                               b.gcount, st);
+    const int B = vt.g[0].B;   // one brick edge for every volume
+    if (B == 4)
+        k_bcount<4><<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, vt, b.tmask, b.cbase, b.bcount,
+                                                      b.gcount, st);
+    else if (B == 16)
+        k_bcount<16><<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, vt, b.tmask, b.cbase,
+                                                       b.bcount, b.gcount, st);
+    else
+        k_bcount<8><<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, vt, b.tmask, b.cbase, b.bcount,
+                                                      b.gcount, st);
     launch_exscan_u32(b.bcount, nbricks, b.boff, b.scanp, s);
     long long rb = (nbricks + 255) / 256;
     if (rb > 8LL * num_sms()) rb = 8LL * num_sms();
     k_brick_ranges<<<(unsigned)rb, 256, 0, s>>>(b.bcount, b.boff, nbricks, b.ranges, b.ranges + nbricks, st, b.cap,
                                                 iter);
-    k_bemit<<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, vt, b.pairs,
-                                              st);
+    if (B == 4)
+        k_bemit<4><<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, vt,
+                                                     b.pairs, st);
+    else if (B == 16)
+        k_bemit<16><<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, vt,
+                                                      b.pairs, st);
+    else
+        k_bemit<8><<<(unsigned)ntiles, 256, 0, s>>>(b.br, b.rec, vv[cur], b.trange, b.tmask, b.cbase, b.boff, vt,
+                                                     b.pairs, st);
     launches += 6;
     return launches;
 }

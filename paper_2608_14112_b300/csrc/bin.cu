@@ -737,13 +737,14 @@ __device__ __forceinline__ unsigned long long chunk_id(uint32_t ts, long long ti
 // Stage 2, first pass (one 256-thread CTA per tile; rounds of 256 list
 // entries, warp w holding chunk 8 r + w = entries 32 w .. 32 w + 31 of round
 // r).  The cover test runs on the bricks of each listed Gaussian's box
-// inside the tile, flattened per warp as in stage 1.  Writes the 64-bit pass
+// inside the tile: the box's rows of bricks along x (up to four) are
+// flattened per warp as in stage 1, and each lane tests one row.  Writes the 64-bit pass
 // mask of every entry (bit = (z * 4 + y) * 4 + x of the brick inside the
 // tile), per chunk and brick the passes of all earlier entries of the tile
 // (the chunk's base), the pair count of each brick of the tile, and, when
 // gcount is set, adds each Gaussian's passes to gcount (introspection).
 template <int B>
-__global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, 6) k_bcount(const BinRec* __restrict__ br, const float4* __restrict__ rec,
                                                 const uint32_t* __restrict__ tgid, const uint32_t* __restrict__ trange,
                                                 VolTab vt, unsigned long long* __restrict__ tmask,
                                                 uint32_t* __restrict__ cbase, uint32_t* __restrict__ bcount,
@@ -761,7 +762,7 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
     __shared__ uint32_t s_run[64];     // passes of each brick by the tile's earlier rounds
     __shared__ uint32_t s_incl[8][32];
     __shared__ int4 s_box[8][32];      // first brick (x, y, z) inside the tile, x extent
-    __shared__ uint2 s_div[8][32];     // reciprocal of x*y extent; reciprocal of x extent << 8 | x*y extent
+    __shared__ uint2 s_div[8][32];     // reciprocal of the y extent, y extent
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int ox, oy, oz;
     tile_origin(g, tile - vt.toff[vol], ox, oy, oz);
@@ -771,7 +772,7 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
         const uint32_t e = r0 + tid;
         uint32_t cnt = 0, gid = 0;
         int4 box = make_int4(0, 0, 0, 1);
-        uint2 dv = make_uint2(65536u, (65536u << 8) | 1u);
+        uint2 dv = make_uint2(65536u, 1u);
         s_m[tid][0] = 0u;
         s_m[tid][1] = 0u;
         if (e < te) {
@@ -783,10 +784,10 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
             const int ly = max(b.blo[1], oy) - oy, hy = min(b.bhi[1], oy + kTile - 1) - oy;
             const int lz = max(b.blo[2], oz) - oz, hz = min(b.bhi[2], oz + kTile - 1) - oz;
             if (lx <= hx && ly <= hy && lz <= hz) {
-                const uint32_t ex = (uint32_t)(hx - lx + 1), exy = ex * (uint32_t)(hy - ly + 1);
-                box = make_int4(lx, ly, lz, (int)ex);
-                dv = make_uint2(small_magic(exy), (small_magic(ex) << 8) | exy);
-                cnt = exy * (uint32_t)(hz - lz + 1);
+                const uint32_t ey = (uint32_t)(hy - ly + 1);
+                box = make_int4(lx, ly, lz, hx - lx + 1);
+                dv = make_uint2(small_magic(ey), ey);
+                cnt = ey * (uint32_t)(hz - lz + 1);   // rows of bricks along x
             }
         }
         const uint32_t incl = warp_incl_scan(cnt);
@@ -802,15 +803,17 @@ __global__ void __launch_bounds__(256) k_bcount(const BinRec* __restrict__ br, c
                 const uint32_t t = it - (j ? s_incl[w][j - 1] : 0u);
                 const int4 bx = s_box[w][j];
                 const uint2 d = s_div[w][j];
-                const uint32_t cz = small_div(t, d.x), r = t - cz * (d.y & 255u);
-                const uint32_t cy = small_div(r, d.y >> 8), cx = r - cy * (uint32_t)bx.w;
-                const int lx = bx.x + (int)cx, ly = bx.y + (int)cy, lz = bx.z + (int)cz;
+                const uint32_t cz = small_div(t, d.x), cy = t - cz * d.y;
+                const int ly = bx.y + (int)cy, lz = bx.z + (int)cz;
                 const int slot = (w << 5) + j;
                 const float4 mu = s_mu[slot];
-                if (brick_test(s_br[slot], mu.x, mu.y, mu.z, B, ox + lx, oy + ly, oz + lz)) {
-                    const int lb = (lz * kTile + ly) * kTile + lx;
-                    atomicOr(&s_m[slot][lb >> 5], 1u << (lb & 31));
-                }
+                // the row's bricks share one word of the mask (4 | 32)
+                const int lb0 = (lz * kTile + ly) * kTile + bx.x;
+                uint32_t bits = 0;
+                for (int cx = 0; cx < bx.w; ++cx)
+                    if (brick_test(s_br[slot], mu.x, mu.y, mu.z, B, ox + bx.x + cx, oy + ly, oz + lz))
+                        bits |= 1u << cx;
+                if (bits) atomicOr(&s_m[slot][lb0 >> 5], bits << (lb0 & 31));
             }
         }
         __syncwarp();

@@ -214,6 +214,21 @@ typedef struct {
     int64_t n;                /* primitives of this volume */
 } gve_volume;
 
+/* Allocation of a batch (the batched form, Sec. III-E per volume): volume
+ * v's vols[v].n Gaussians are allocated, exactly as gve_allocate with opts
+ * would allocate them on that volume alone, into rows [off_v, off_v + n_v)
+ * of prims_dev (volumes in order, concatenated; off_v = sum of the earlier
+ * n).  The volumes run concurrently: up to 8 host threads, each with its own
+ * internal context (scratch of about 12 bytes per voxel of the largest
+ * volume it takes) and stream, largest volumes first; the caller's stream
+ * waits for all of them.  infos (host, optional) [nvol] receives each
+ * volume's summary.  Returns the first failing volume's status in volume
+ * order (gve_last_error names the volume), e.g. GVE_E_BUDGET when its field
+ * cannot support its budget; 1 <= nvol <= 32. */
+GVE_API gve_status gve_allocate_batch(gve_ctx* ctx, int32_t nvol, const gve_volume* vols,
+                                      const gve_alloc_opts* opts, float* prims_dev, gve_alloc_info* infos,
+                                      void* stream);
+
 /* Batched refinement of many volumes of uneven shapes (the batched encode
  * form; each volume is refined exactly as gve_refine would, Sec. III-E).
  * The records of all volumes are concatenated in prims_dev ([sum n][12],

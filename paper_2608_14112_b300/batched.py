@@ -1,10 +1,11 @@
 """Batched encode: many volumes (or timesteps) of uneven shapes encoded
-together -- analytic allocation of each volume's budget, one autotuning pass
-of the evaluator's launch shape, then refinement of all volumes with one
-CUDA graph launch per iteration (``gve_refine_batch``: per-volume binning,
-then one persistent kernel over the bricks of every volume for evaluation
-and update).  Each volume is encoded exactly as it would be alone
-(Sec. III-E of arxiv 2608.14112)."""
+together -- analytic allocation of each volume's budget (all volumes
+concurrently, ``gve_allocate_batch``), one autotuning pass of the
+evaluator's launch shape, then refinement of all volumes with one CUDA graph
+launch per iteration (``gve_refine_batch``: one binning of all volumes, then
+one persistent kernel over the bricks of every volume for evaluation and
+update).  Each volume is encoded exactly as it would be alone (Sec. III-E of
+arxiv 2608.14112)."""
 from __future__ import annotations
 
 import time
@@ -31,19 +32,15 @@ def encode_batch(fields, budgets, iters: int, lr: float = 1e-2, seed: int = 0, a
     """Allocate ``budgets[v]`` Gaussians in each ``fields[v]`` (CUDA float32,
     shape (nz, ny, nx)) and refine all volumes for ``iters`` iterations."""
     dev = fields[0].device
-    total = int(sum(budgets))
-    prims = torch.empty((total, 12), dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    off = 0
-    views = []
-    for f, n in zip(fields, budgets):
-        view = prims[off:off + n]
-        gve.gve_allocate(f, int(n), seed=seed, out=view)
-        views.append(view)
-        off += n
+    prims, _ = gve.gve_allocate_batch(fields, budgets, seed=seed)
     torch.cuda.synchronize(dev)
     alloc_s = time.perf_counter() - t0
+    views, off = [], 0
+    for n in budgets:
+        views.append(prims[off:off + n])
+        off += n
     o = opts or gve.EvalOptions()
     table = {}
     if autotune:

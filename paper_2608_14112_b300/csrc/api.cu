@@ -373,6 +373,9 @@ void gve_ctx_destroy(gve_ctx* c)
     if (c->sev_ready)
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 64; ++b) cudaEventDestroy(c->sev[a][b]);
+    for (gve_ctx* w : c->asub) gve_ctx_destroy(w);
+    for (cudaStream_t as : c->astream) cudaStreamDestroy(as);
+    for (cudaEvent_t ev : c->ajoin) cudaEventDestroy(ev);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->bstate.p) cudaFree(c->bstate.p);

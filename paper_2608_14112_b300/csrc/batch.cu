@@ -25,11 +25,16 @@
 // batch -- binning plus the persistent kernel -- for every brick edge in
 // {4, 8, 16} and every Gaussians-per-block in {32, 64}, and returns the
 // fastest.
+#include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "gve_int.cuh"
 
@@ -441,6 +446,88 @@ extern "C" gve_status gve_refine_batch(gve_ctx* c, int32_t nvol, const gve_volum
     cudaEventRecord(c->fork, c->gstream);
     cudaStreamWaitEvent(caller, c->fork, 0);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "batch");
+    return GVE_OK;
+}
+
+// Concurrent allocation of a batch's volumes: up to kAllocWorkers host
+// threads, each with its own context (scratch) and stream, take volumes
+// largest first from a shared counter; volume v's records go to rows
+// [off_v, off_v + n_v) of prims.  Each volume's result is exactly that of
+// gve_allocate on it alone.
+constexpr int kAllocWorkers = 8;
+
+extern "C" gve_status gve_allocate_batch(gve_ctx* c, int32_t nvol, const gve_volume* vols,
+                                         const gve_alloc_opts* o, float* prims, gve_alloc_info* infos,
+                                         void* stream)
+{
+    if (!c) return GVE_E_INVALID;
+    if (nvol < 1 || nvol > kMaxVol || !vols || !o) return fail(c, GVE_E_INVALID, "volume count must be 1..32");
+    if (!prims || (reinterpret_cast<uintptr_t>(prims) & 15u)) return fail(c, GVE_E_INVALID, "bad primitive pointer");
+    long long off[kMaxVol + 1];
+    off[0] = 0;
+    for (int v = 0; v < nvol; ++v) {
+        if (!vols[v].field_dev || vols[v].n < 0) return fail(c, GVE_E_INVALID, "bad volume in batch");
+        off[v + 1] = off[v] + vols[v].n;
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    const int nw = std::min(nvol, kAllocWorkers);
+    while ((int)c->asub.size() < nw) {
+        gve_ctx* w = nullptr;
+        gve_status st = gve_ctx_create(&w, c->device);
+        if (st != GVE_OK) return fail(c, st, "allocation worker context");
+        cudaStream_t as = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&as, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            gve_ctx_destroy(w);
+            return cuda_fail(c, cudaGetLastError(), "allocation worker stream");
+        }
+        c->asub.push_back(w);
+        c->astream.push_back(as);
+        c->ajoin.push_back(ev);
+    }
+    gve_status st = ensure_batch(c);
+    if (st != GVE_OK) return st;
+    cudaStream_t caller = (cudaStream_t)stream;
+    if (cudaEventRecord(c->fork, caller) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event");
+    for (int w = 0; w < nw; ++w)
+        if (cudaStreamWaitEvent(c->astream[w], c->fork, 0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "wait");
+    // largest volumes first
+    int order[kMaxVol];
+    for (int v = 0; v < nvol; ++v) order[v] = v;
+    auto voxels = [&](int v) { return (long long)vols[v].dims.nx * vols[v].dims.ny * vols[v].dims.nz; };
+    std::stable_sort(order, order + nvol, [&](int a, int b) { return voxels(a) > voxels(b); });
+    std::vector<gve_status> status(nvol, GVE_OK);
+    std::vector<std::string> msg(nvol);
+    std::atomic<int> next{0};
+    auto work = [&](int w) {
+        cudaSetDevice(c->device);
+        for (int k = next.fetch_add(1); k < nvol; k = next.fetch_add(1)) {
+            const int v = order[k];
+            gve_alloc_info info{};
+            const gve_status s = gve_allocate(c->asub[w], vols[v].field_dev, vols[v].dims, vols[v].n, o,
+                                              prims + 12 * off[v], nullptr, &info, c->astream[w]);
+            status[v] = s;
+            if (s != GVE_OK) msg[v] = c->asub[w]->err;
+            if (infos) infos[v] = info;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(work, w);
+    work(0);
+    for (std::thread& t : pool) t.join();
+    for (int w = 0; w < nw; ++w) {
+        cudaEventRecord(c->ajoin[w], c->astream[w]);
+        cudaStreamWaitEvent(caller, c->ajoin[w], 0);
+    }
+    for (int v = 0; v < nvol; ++v)
+        if (status[v] != GVE_OK) {
+            char buf[64];
+            snprintf(buf, sizeof(buf), "volume %d: ", v);
+            c->err = std::string(buf) + msg[v];
+            return status[v];
+        }
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "allocate batch");
     return GVE_OK;
 }
 

@@ -99,6 +99,11 @@ struct gve_ctx {
     cudaEvent_t sev[3][64] = {};
     bool sev_ready = false;
     long long launches = 0;          // kernels launched by the current call
+    // batched allocation: one worker context, stream and join event per
+    // concurrent allocation
+    std::vector<gve_ctx*> asub;
+    std::vector<cudaStream_t> astream;
+    std::vector<cudaEvent_t> ajoin;
     // batched refinement: its stream and the event that joins it to the caller's
     cudaStream_t gstream = nullptr;
     cudaEvent_t fork = nullptr;

@@ -133,6 +133,9 @@ def lib():
             L.gve_refine_batch.argtypes = [P, i32, ctypes.POINTER(Volume), P, ctypes.POINTER(Schedule), P, P, P,
                                            ctypes.POINTER(Stats), P]
             L.gve_autotune.argtypes = [P, i32, ctypes.POINTER(Volume), P, ctypes.POINTER(EvalOpts), P, P]
+            L.gve_allocate_batch.argtypes = [P, i32, ctypes.POINTER(Volume), ctypes.POINTER(AllocOpts), P,
+                                             ctypes.POINTER(AllocInfo), P]
+            L.gve_allocate_batch.restype = st
             for f in ("gve_allocate", "gve_evaluate", "gve_loss_grad", "gve_backward", "gve_refine", "gve_bin",
                       "gve_count_pairs", "gve_evaluate_noalloc", "gve_refine_batch", "gve_autotune", "gve_kept_pairs",
                       "gve_normalize", "gve_peak_bench"):
@@ -537,6 +540,28 @@ def gve_allocate(field: torch.Tensor, budget: int, detail_frac: float = 0.55, oc
         raise BudgetError(lib().gve_last_error(c).decode(), int(fm.value))
     _check(s, c)
     return out, {name: getattr(info, name) for name, _ in AllocInfo._fields_}
+
+
+def gve_allocate_batch(fields, budgets, detail_frac: float = 0.55, occ_thresh: float = 0.02, w0: float = 0.1,
+                       seed: int = 0, out: torch.Tensor | None = None):
+    """Allocation of every volume of a batch, run concurrently
+    (gve_allocate_batch): volume v's ``budgets[v]`` records land in rows
+    [sum(budgets[:v]), sum(budgets[:v + 1])) of one (sum(budgets), 12)
+    tensor, each exactly as gve_allocate would write them.  Returns (prims,
+    list of info dicts); raises GveError naming the first failing volume."""
+    dev = fields[0].device
+    total = int(sum(int(n) for n in budgets))
+    if out is None:
+        out = torch.empty((total, 12), dtype=torch.float32, device=dev)
+    _prims(out)
+    if out.shape[0] != total:
+        raise ValueError("out must hold sum(budgets) records")
+    vols = _volumes(fields, budgets)
+    o = AllocOpts(float(detail_frac), float(w0), float(occ_thresh), 0, int(seed) & (2 ** 64 - 1))
+    infos = (AllocInfo * len(fields))()
+    c = context(dev.index)
+    _check(lib().gve_allocate_batch(c, len(fields), vols, ctypes.byref(o), _ptr(out), infos, _stream(dev)), c)
+    return out, [{name: getattr(inf, name) for name, _ in AllocInfo._fields_} for inf in infos]
 
 
 def gve_bin(prims: torch.Tensor, shape, opts: EvalOptions | None = None, cap: int | None = None,

@@ -1,6 +1,11 @@
-"""Batched refinement (per-volume binning, then one persistent cooperative
-kernel for the evaluation and update of all volumes, one CUDA graph launch
-per iteration) and the launch-shape autotuner.
+"""Batched allocation (all volumes concurrently), batched refinement (one
+binning of all volumes, then one persistent cooperative kernel for the
+evaluation and update of all volumes, one CUDA graph launch per iteration)
+and the launch-shape autotuner.
+
+The batched allocation must write, volume by volume, exactly the records
+gve_allocate writes for that volume alone (bit for bit), and report a volume
+whose field cannot support its budget by name.
 
 A batch of uneven volumes must give, volume by volume, what the FP64 oracle's
 refinement gives (final PSNR within 0.05 dB, losses within 2e-3 relative, the
@@ -182,3 +187,28 @@ def test_alloc_fault_returns_nomem_and_context_recovers():
         assert torch.allclose(out, ref, rtol=1e-6, atol=1e-7)
     finally:
         L.gve_ctx_destroy(ctx)
+
+
+def test_allocate_batch_matches_single_volume_allocation():
+    """Twelve uneven volumes (more than the eight allocation workers): every
+    volume's records and summary equal gve_allocate's on it alone."""
+    shapes = SHAPES * 3
+    fields = [torch.from_numpy(inputs.grf(shp, seed=60 + i)).cuda() for i, shp in enumerate(shapes)]
+    budgets = [max(64, (s[0] * s[1] * s[2]) // 40) for s in shapes]
+    P, infos = gve.gve_allocate_batch(fields, budgets, seed=3)
+    torch.cuda.synchronize()
+    off = 0
+    for f, n, info in zip(fields, budgets, infos):
+        ref, rinfo = gve.gve_allocate(f, n, seed=3)
+        assert torch.equal(P[off:off + n], ref)
+        assert info == rinfo
+        off += n
+
+
+def test_allocate_batch_reports_the_infeasible_volume():
+    fields = [torch.from_numpy(inputs.grf(shp, seed=70 + i)).cuda() for i, shp in enumerate(SHAPES)]
+    budgets = [64, 64, 10 ** 6, 64]          # volume 2 holds fewer voxels than its budget
+    with pytest.raises(gve.GveError) as e:
+        gve.gve_allocate_batch(fields, budgets, seed=0)
+    assert e.value.status == gve.GVE_E_BUDGET and "volume 2" in str(e.value)
+

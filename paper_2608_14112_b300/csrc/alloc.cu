@@ -1138,7 +1138,6 @@ __device__ __forceinline__ float chunk_grad(const StatGrid& g, const Row& r, int
 }
 
 constexpr int kBatch1 = 4;
-constexpr int kBatch2 = 8;
 
 // sweep 1 also writes each voxel's gradient bits (kStatEmpty where the
 // voxel is not occupied), so that sweep 2 reads 4 bytes per voxel instead of

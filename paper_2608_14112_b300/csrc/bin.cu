@@ -148,26 +148,35 @@ void launch_prep_rec(const float* prims, long long n, float k, float4* rec, cuda
     k_prep<false><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(prims, n, vt, k, rec, nullptr, nullptr);
 }
 
-// float32 cover test of one brick (same operation order as the oracle)
-__device__ __forceinline__ bool brick_test(const BinRec& b, float mux, float muy, float muz, int B, int bx,
-                                           int by, int bz)
+
+// The float32 cover test of two neighbouring bricks (bx, bx + 1) at once.
+// Per brick, with c its centre (brick origin + (B - 1) / 2) and in the
+// oracle's operation order: y_j = L_j2 dz + (L_j1 dy + L_j0 dx) with d =
+// c - mu, a_j = max(|y_j| - e_j, 0), pass iff a_0^2 + (a_1^2 + a_2^2) <= K2,
+// every operation correctly rounded (packed f32x2 multiplies and FMAs are
+// two IEEE operations lane by lane).  Bit 0: brick bx passes; bit 1: bx + 1.
+template <int B>
+__device__ __forceinline__ uint32_t brick_test2(const BinRec& b, float mux, float muy, float muz, int bx, int by,
+                                                int bz)
 {
-    float half = (float)(0.5 * (double)(B - 1));
-    float cx = __fadd_rn((float)(bx * B), half);
-    float cy = __fadd_rn((float)(by * B), half);
-    float cz = __fadd_rn((float)(bz * B), half);
-    float dcx = __fsub_rn(cx, mux), dcy = __fsub_rn(cy, muy), dcz = __fsub_rn(cz, muz);
-    float acc[3];
+    const float half = (float)(0.5 * (double)(B - 1));
+    const float2 cx = make_float2(__fadd_rn((float)(bx * B), half), __fadd_rn((float)((bx + 1) * B), half));
+    const float cy = __fadd_rn((float)(by * B), half), cz = __fadd_rn((float)(bz * B), half);
+    const float2 dcx = __fadd2_rn(cx, make_float2(-mux, -mux));   // cx - mu_x
+    const float dcy = __fsub_rn(cy, muy), dcz = __fsub_rn(cz, muz);
+    float2 acc[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        float t0 = __fmul_rn(b.L[j * 3 + 0], dcx);
-        float y = __fmaf_rn(b.L[j * 3 + 2], dcz, __fmaf_rn(b.L[j * 3 + 1], dcy, t0));
-        float a = __fsub_rn(fabsf(y), b.e[j]);
-        acc[j] = a > 0.0f ? a : 0.0f;
+        const float l0 = b.L[j * 3 + 0], l1 = b.L[j * 3 + 1], l2 = b.L[j * 3 + 2];
+        const float2 t0 = __fmul2_rn(make_float2(l0, l0), dcx);
+        const float2 y = __ffma2_rn(make_float2(l2, l2), make_float2(dcz, dcz),
+                                    __ffma2_rn(make_float2(l1, l1), make_float2(dcy, dcy), t0));
+        const float ax = __fsub_rn(fabsf(y.x), b.e[j]), ay = __fsub_rn(fabsf(y.y), b.e[j]);
+        acc[j] = make_float2(ax > 0.0f ? ax : 0.0f, ay > 0.0f ? ay : 0.0f);
     }
-    float a22 = __fmul_rn(acc[2], acc[2]);
-    float sq = __fmaf_rn(acc[0], acc[0], __fmaf_rn(acc[1], acc[1], a22));
-    return sq <= b.K2;
+    const float2 a22 = __fmul2_rn(acc[2], acc[2]);
+    const float2 sq = __ffma2_rn(acc[0], acc[0], __ffma2_rn(acc[1], acc[1], a22));
+    return (sq.x <= b.K2 ? 1u : 0u) | (sq.y <= b.K2 ? 2u : 0u);
 }
 
 // Gram matrix of the whitened voxel axes l_i (l_i[j] = L[j][i]), shared by
@@ -738,7 +747,8 @@ __device__ __forceinline__ unsigned long long chunk_id(uint32_t ts, long long ti
 // entries, warp w holding chunk 8 r + w = entries 32 w .. 32 w + 31 of round
 // r).  The cover test runs on the bricks of each listed Gaussian's box
 // inside the tile: the box's rows of bricks along x (up to four) are
-// flattened per warp as in stage 1, and each lane tests one row.  Writes the 64-bit pass
+// flattened per warp as in stage 1, and each lane tests one row, two bricks
+// at a time.  Writes the 64-bit pass
 // mask of every entry (bit = (z * 4 + y) * 4 + x of the brick inside the
 // tile), per chunk and brick the passes of all earlier entries of the tile
 // (the chunk's base), the pair count of each brick of the tile, and, when
@@ -810,9 +820,10 @@ __global__ void __launch_bounds__(256, 6) k_bcount(const BinRec* __restrict__ br
                 // the row's bricks share one word of the mask (4 | 32)
                 const int lb0 = (lz * kTile + ly) * kTile + bx.x;
                 uint32_t bits = 0;
-                for (int cx = 0; cx < bx.w; ++cx)
-                    if (brick_test(s_br[slot], mu.x, mu.y, mu.z, B, ox + bx.x + cx, oy + ly, oz + lz))
-                        bits |= 1u << cx;
+                for (int cx = 0; cx < bx.w; cx += 2) {
+                    const uint32_t two = brick_test2<B>(s_br[slot], mu.x, mu.y, mu.z, ox + bx.x + cx, oy + ly, oz + lz);
+                    bits |= (cx + 1 < bx.w ? two : (two & 1u)) << cx;
+                }
                 if (bits) atomicOr(&s_m[slot][lb0 >> 5], bits << (lb0 & 31));
             }
         }

@@ -69,6 +69,9 @@ def parse():
                     help="refinement iterations that judge the pairs proposal's step size")
     ap.add_argument("--proposal-headline", action="store_true",
                     help="proposal workload: also judge both trainers on the 1024^3 headline field")
+    ap.add_argument("--proposal-fields", choices=["grf", "fbm_crops"], default="grf",
+                    help="proposal workload: training and held-out fields (GRF, or crops of 1024^3 fbm + fronts "
+                         "fields of other seeds: the headline field's family)")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
     ap.add_argument("--ttp-iters", type=int, default=2000, help="full schedule of the time-to-PSNR run (0 = skip)")
@@ -484,8 +487,9 @@ def proposal_headline_judge(models, args):
 
 def run_proposal(args):
     """Learned proposal against plain allocation, both trainers judged the
-    same way.  Training set: 64 seeded 256^3 GRF fields with 25,000
-    Gaussians each.  (a) the allocation -> refined pairs trainer: features of
+    same way.  Training set: 64 seeded 256^3 GRF fields (or, with
+    --proposal-fields fbm_crops, 256^3 crops of fbm + fronts fields) with
+    25,000 Gaussians each.  (a) the allocation -> refined pairs trainer: features of
     each analytic allocation against the change that --pair-iters refinement
     iterations made to a and log s (targets scaled by their spreads), then one
     step size for its corrections chosen by the PSNR that --cal-iters
@@ -505,7 +509,21 @@ def run_proposal(args):
     gbuild.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    tr = [inputs.grf(256, seed=s, device=dev) for s in range(1000, 1064)]
+    if args.proposal_fields == "fbm_crops":
+        # 256^3 crops at seeded corners and 512^3 centre crops of 1024^3 fbm + fronts
+        # fields: the headline field's statistics at the same grid scale
+        crng = np.random.default_rng(7)
+        tr = [inputs.fbm_fronts(1024, seed=s, device=dev,
+                                region=(tuple(int(v) for v in crng.integers(0, 769, 3)), (256, 256, 256)))
+              for s in range(1000, 1064)]
+
+        def held_out(seed):
+            return inputs.fbm_fronts(1024, seed=seed, device=dev, region=((256, 256, 256), (512, 512, 512)))
+    else:
+        tr = [inputs.grf(256, seed=s, device=dev) for s in range(1000, 1064)]
+
+        def held_out(seed):
+            return inputs.grf(512, seed=seed, device=dev)
     allocs = proposal.allocations(tr, 25_000, seed=args.seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -530,7 +548,7 @@ def run_proposal(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
     for seed in (2000, 2001, 2002, 2003):
-        V = inputs.grf(512, seed=seed, device=dev)
+        V = held_out(seed)
         for kind, model in kinds.items():
             torch.cuda.synchronize()
             e0.record(stream)
@@ -579,6 +597,8 @@ def run_proposal(args):
            "ms_per_step": msi, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16 weights, f32", "data": "synthetic",
            "config": {"workload": "proposal_train_64x256^3_N25000_eval_4x512^3_N200000", "trunc_k": 3.0,
+                      "fields": ("GRF k^-5/3" if args.proposal_fields == "grf" else
+                                 "crops of 1024^3 fbm + fronts fields (256^3 training, 512^3 centre held out)"),
                       "value_is": "the allocation -> refined pairs trainer",
                       "pairs_trainer": f"targets from {args.pair_iters} refinement iterations, scaled by their "
                                        "spreads, 20 epochs, batch 4096, lr 1e-3; step size judged by "

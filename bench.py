@@ -67,9 +67,9 @@ def parse():
     ap.add_argument("--pair-iters", type=int, default=500, help="refinement iterations behind the proposal's pairs")
     ap.add_argument("--cal-iters", type=int, default=150,
                     help="refinement iterations that judge the pairs proposal's step size")
-    ap.add_argument("--proposal-headline", action="store_true",
-                    help="proposal workload: also judge both trainers on the 1024^3 headline field")
-    ap.add_argument("--proposal-fields", choices=["grf", "fbm_crops"], default="grf",
+    ap.add_argument("--no-proposal-headline", dest="proposal_headline", action="store_false",
+                    help="proposal workload: skip the judge of both trainers on the 1024^3 headline field")
+    ap.add_argument("--proposal-fields", choices=["grf", "fbm_crops"], default="fbm_crops",
                     help="proposal workload: training and held-out fields (GRF, or crops of 1024^3 fbm + fronts "
                          "fields of other seeds: the headline field's family)")
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
@@ -487,16 +487,17 @@ def proposal_headline_judge(models, args):
 
 def run_proposal(args):
     """Learned proposal against plain allocation, both trainers judged the
-    same way.  Training set: 64 seeded 256^3 GRF fields (or, with
-    --proposal-fields fbm_crops, 256^3 crops of fbm + fronts fields) with
-    25,000 Gaussians each.  (a) the allocation -> refined pairs trainer: features of
+    same way.  Training set: 64 seeded 256^3 crops of 1024^3 fbm + fronts
+    fields (the headline field's family; --proposal-fields grf: GRF fields)
+    with 25,000 Gaussians each.  (a) the allocation -> refined pairs trainer: features of
     each analytic allocation against the change that --pair-iters refinement
     iterations made to a and log s (targets scaled by their spreads), then one
     step size for its corrections chosen by the PSNR that --cal-iters
     refinement iterations reach on 8 training fields (zero, the plain
     allocation, among the candidates); (b) the end-to-end trainer through the
-    encoder's loss.  Held out: 4 seeded 512^3
-    fields with 200,000 Gaussians, refined --prop-iters iterations from plain,
+    encoder's loss.  Held out: 4 seeded 512^3 fields of the same family (centre
+    crops of fbm + fronts fields of other seeds) with 200,000 Gaussians,
+    refined --prop-iters iterations from plain,
     (a)-corrected and (b)-corrected allocations.  Time-to-PSNR: wall time from
     the start of the allocation (features and MLP included) to the first
     iteration at the plain schedule's final PSNR - 0.1 dB, at the measured

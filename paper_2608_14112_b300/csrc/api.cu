@@ -285,7 +285,7 @@ BrickArgs brick_args(Call& k, const gve_eval_opts* o)
     a.end = a.start + k.g.nbricks;
     a.gids = (const uint32_t*)c->pairs.p;
     a.rec = (const float4*)c->rec.p;
-    a.part = (double2*)c->part.p;
+    a.part = (float2*)c->part.p;
     a.st = dstate(c);
     double k2 = (double)o->trunc_k * (double)o->trunc_k;
     a.T = (float)(k2 * kNegHalfLog2e);

@@ -180,7 +180,7 @@ BrickArgs vol_args(const Batch& b, int v, const gve_eval_opts* o, float mask_thr
     a.g = b.V[v].g;
     a.start = (const uint32_t*)c->ranges.p + b0;
     a.end = (const uint32_t*)c->ranges.p + nb + b0;
-    a.part = (double2*)c->part.p + b0;
+    a.part = (float2*)c->part.p + b0;
     a.inv_m = (float)b.V[v].inv_m;
     a.field = b.V[v].field;
     a.mask_thresh = mask_thresh;

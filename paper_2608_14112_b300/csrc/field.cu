@@ -49,6 +49,19 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+// asynchronous global -> shared copies (each thread waits for its own)
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -123,6 +136,7 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
     __shared__ int s_scan[NW];
     __shared__ float s_red[2][NW];
     __shared__ unsigned long long s_cnt[3][NW];
+    __shared__ __align__(16) float s_v[(MODE == kModeLoss || MODE == kModeBwd) ? S::ROWS * B : 4];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const BinGeom& g = a.g;
@@ -141,6 +155,20 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
     const bool rowin = has_row && gy < g.ny && gz < g.nz;
     const int nxin = rowin ? min(B, g.nx - gx0) : 0;  // in-grid voxels of the row
     const float fy = (float)gy, fz = (float)gz;
+    if (MODE == kModeLoss || MODE == kModeBwd) {
+        // the row's target (loss) or upstream (backward) values travel to
+        // shared memory while the forward phase runs
+        if (nxin > 0) {
+            const float* src = (MODE == kModeLoss ? a.field : a.upstream) + (((size_t)gz * g.ny + gy) * g.nx + gx0);
+            float* dst = s_v + row * B;
+            if (nxin == B && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+#pragma unroll
+                for (int x = 0; x < B; x += 4) cp_async16(dst + x, src + x);
+            } else {
+                for (int x = 0; x < nxin; ++x) cp_async4(dst + x, src + x);
+            }
+        }
+    }
     // sub-brick bits (bit = y half + 2 * z quarter) covering this warp's rows
     uint32_t wmask = 0;
     {
@@ -278,11 +306,13 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
         vt[2 * q] = num[q].x * inv[2 * q];
         vt[2 * q + 1] = num[q].y * inv[2 * q + 1];
     }
+    cp_async_wait_all();
+    const float* sv = s_v + (MODE == kModeLoss || MODE == kModeBwd ? row * B : 0);
     if (MODE == kModeLoss) {
         float ef = 0.f, el = 0.f;
 #pragma unroll
         for (int x = 0; x < B; ++x) {
-            const float V = x < nxin ? a.field[vrow + x] : 0.f;
+            const float V = x < nxin ? sv[x] : 0.f;
             const float r = x < nxin ? vt[x] - V : 0.f;
             const float rl = (a.mask_thresh < 0.f || V > a.mask_thresh) ? r : 0.f;
             ef = fmaf(r, r, ef);
@@ -297,7 +327,7 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
         if (lane == 0) { s_red[0][warp] = el; s_red[1][warp] = ef; }
     } else {  // kModeBwd
 #pragma unroll
-        for (int x = 0; x < B; ++x) up[x] = x < nxin ? a.upstream[vrow + x] : 0.f;
+        for (int x = 0; x < B; ++x) up[x] = x < nxin ? sv[x] : 0.f;
     }
     // the upstream terms of the backward, only when the gradient is wanted
     // (a forward-only loss evaluation has no sums to fill)
@@ -318,9 +348,9 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
     }
     __syncthreads();
     if (MODE == kModeLoss && tid == 0) {
-        double el = 0.0, ef = 0.0;
-        for (int w = 0; w < NW; ++w) { el += (double)s_red[0][w]; ef += (double)s_red[1][w]; }
-        a.part[brick] = make_double2(el, ef);
+        float el = 0.f, ef = 0.f;
+        for (int w = 0; w < NW; ++w) { el += s_red[0][w]; ef += s_red[1][w]; }
+        a.part[brick] = make_float2(el, ef);
     }
     if (a.acc == nullptr || L == 0) return;
 
@@ -573,12 +603,12 @@ __global__ void __launch_bounds__(BrickShape<B>::THREADS, BrickShape<B>::MINB) k
         const long long nb = p.boff[v + 1] - p.boff[v];
         const long long b0 = (ch - p.coff[v]) * kSseChunk;
         const long long b1 = b0 + kSseChunk < nb ? b0 + kSseChunk : nb;
-        const double2* part = p.va[v].part;
+        const float2* part = p.va[v].part;
         double x = 0.0, y = 0.0;
         for (long long i = b0 + threadIdx.x; i < b1; i += NT) {
-            const double2 q = part[i];
-            x += q.x;
-            y += q.y;
+            const float2 q = part[i];
+            x += (double)q.x;
+            y += (double)q.y;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -671,7 +701,7 @@ cudaError_t launch_batch_iter(int B, int CH, const BatchIterArgs& p, unsigned gr
 // ------------------------------------------------------------------------
 constexpr int kRedBlocks = 592;
 
-__global__ void __launch_bounds__(256) k_sse_partial(const double2* __restrict__ part, long long nb,
+__global__ void __launch_bounds__(256) k_sse_partial(const float2* __restrict__ part, long long nb,
                                                      double2* __restrict__ out, const DevState* st)
 {
     if (st->overflow) return;
@@ -680,9 +710,9 @@ __global__ void __launch_bounds__(256) k_sse_partial(const double2* __restrict__
     long long b0 = (long long)blockIdx.x * chunk, b1 = min(nb, b0 + chunk);
     double x = 0.0, y = 0.0;
     for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        double2 p = part[i];
-        x += p.x;
-        y += p.y;
+        const float2 p = part[i];
+        x += (double)p.x;
+        y += (double)p.y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -722,11 +752,13 @@ __global__ void __launch_bounds__(1024) k_sse_final(const double2* __restrict__ 
     }
 }
 
-void launch_sse_reduce(const double2* part, long long nbricks, DevState* st, double* trace, int iter,
+void launch_sse_reduce(const float2* part, long long nbricks, DevState* st, double* trace, int iter,
                        double inv_m, cudaStream_t s, const int* iter_dev, int trace_stride, int trace_col)
 {
-    // the second half of the partial buffer is scratch for the block sums
-    double2* tmp = const_cast<double2*>(part) + nbricks;
+    // the partial buffer past the bricks' sums (16-byte aligned) is scratch
+    // for the block sums
+    const uintptr_t end = reinterpret_cast<uintptr_t>(part + nbricks);
+    double2* tmp = reinterpret_cast<double2*>((end + 15) & ~static_cast<uintptr_t>(15));
     k_sse_partial<<<kRedBlocks, 256, 0, s>>>(part, nbricks, tmp, st);
     k_sse_final<<<1, 1024, 0, s>>>(tmp, kRedBlocks, st, trace, iter, inv_m, iter_dev, trace_stride, trace_col);
 }

@@ -396,7 +396,7 @@ struct BrickArgs {
     const float* upstream;     // dL/dVtilde (backward mode)
     float* field_out;          // Vtilde (eval mode) or nullptr
     float* acc;                // [n][12] accumulators (loss/bwd)
-    double2* part;             // per-brick {masked, unmasked} SSE
+    float2* part;              // per-brick {masked, unmasked} SSE (float32 within a brick)
     DevState* st;
     float T;                   // float32 keep threshold
     float rho0;
@@ -412,7 +412,7 @@ void launch_brick(int mode, const BrickArgs& a, cudaStream_t s);
 // deterministic reduction of per-brick partials; writes st->sse and, if
 // trace != nullptr, trace[i] = sse_masked * inv_m with i = iter, or
 // i = (*iter_dev) * trace_stride + trace_col when iter_dev is set.
-void launch_sse_reduce(const double2* part, long long nbricks, DevState* st, double* trace, int iter,
+void launch_sse_reduce(const float2* part, long long nbricks, DevState* st, double* trace, int iter,
                        double inv_m, cudaStream_t s, const int* iter_dev = nullptr, int trace_stride = 1,
                        int trace_col = 0);
 

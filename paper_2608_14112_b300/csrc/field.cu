@@ -130,7 +130,11 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
     if (a.st->overflow) return;
     __shared__ float4 s_rec[CH * 3];
     __shared__ uint32_t s_msk[CH];
-    __shared__ float4 s_g[S::ROWS * HALF];  // per row: HALF x (gn[x], gn[x+1], gd[x], gd[x+1])
+    // per row: HALF x (gn[x], gn[x+1], gd[x], gd[x+1]), stored sub-brick by
+    // sub-brick in blocks of GBLK float4 (one of padding), so that lanes
+    // reading the same position in different sub-bricks hit different banks
+    constexpr int GBLK = SY * SZ * HALF + 1;
+    __shared__ float4 s_g[8 * GBLK];
     __shared__ float s_acc[CH * kAccStride];
     __shared__ uint16_t s_task[CH * 8];
     __shared__ int s_scan[NW];
@@ -343,7 +347,8 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
             } else {
                 gd0 = 0.f; gd1 = 0.f;
             }
-            s_g[row * HALF + q] = make_float4(gn0, gn1, gd0, gd1);
+            s_g[(ly / SY + 2 * (lz / SZ)) * GBLK + (ly % SY + SY * (lz % SZ)) * HALF + q] =
+                make_float4(gn0, gn1, gd0, gd1);
         }
     }
     __syncthreads();
@@ -427,7 +432,7 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
                     const float bb = __fmaf_rn(r1.z, dy, e_);
                     const float cc = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
                     const float2 b2 = f2(bb), c2 = f2(cc);
-                    const float4* gp = s_g + ((zb + zs) * B + yb + yr) * HALF;
+                    const float4* gp = s_g + sbt * GBLK + (yr + SY * zs) * HALF;
                     float2 R0 = make_float2(0.f, 0.f), R1 = R0;
 #pragma unroll
                     for (int q = 0; q < HALF; ++q) {

@@ -238,6 +238,27 @@ gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
     return GVE_OK;
 }
 
+// one binning of prims (tagged iteration 0) into pair buffers large enough
+// for it: a context whose buffers already hold it bins once; otherwise the
+// buffers grow and the binning runs again (four runs at most).  On return the
+// device state holds that binning's totals and zero counters.
+gve_status bin_sized(Call& k, const float* prims, const gve_eval_opts* o)
+{
+    gve_ctx* c = k.c;
+    GVE_TRY(size_static(k));
+    GVE_TRY(grow_pairs(k, 0, 0));
+    for (int run = 0; run < 4; ++run) {
+        reset_state(k);
+        GVE_TRY(bin_all(k, prims, o, 0));
+        DevState h;
+        GVE_TRY(read_state(k, &h));
+        if (!h.overflow) return GVE_OK;
+        const bool tiles = h.total1 > c->cap1;
+        GVE_TRY(grow_pairs(k, h.total1, tiles ? 0 : h.total));
+    }
+    return fail(c, GVE_E_CAPACITY, "pair count kept growing past capacity");
+}
+
 BinBufs bin_bufs(Call& k, uint32_t* gcount)
 {
     gve_ctx* c = k.c;
@@ -392,8 +413,7 @@ gve_status gve_evaluate(gve_ctx* c, const float* prims, int64_t n, gve_dims d, c
     if (!field_out) return fail(c, GVE_E_INVALID, "null output field");
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    GVE_TRY(size_pairs(k, prims, o));
-    GVE_TRY(bin_all(k, prims, o, 0));
+    GVE_TRY(bin_sized(k, prims, o));
     BrickArgs a = brick_args(k, o);
     a.field_out = field_out;
     launch_brick(kModeEval, a, k.s);
@@ -410,9 +430,8 @@ gve_status gve_loss_grad(gve_ctx* c, const float* prims, int64_t n, const float*
     if (grad && (reinterpret_cast<uintptr_t>(grad) & 15u)) return fail(c, GVE_E_INVALID, "gradient not 16-byte aligned");
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    GVE_TRY(size_pairs(k, prims, o));
+    GVE_TRY(bin_sized(k, prims, o));
     GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (n > 0 ? n : 1), k.s), "memset acc");
-    GVE_TRY(bin_all(k, prims, o, 0));
     BrickArgs a = brick_args(k, o);
     a.field = field;
     a.mask_thresh = mask_thresh;
@@ -437,9 +456,8 @@ gve_status gve_backward(gve_ctx* c, const float* prims, int64_t n, gve_dims d, c
     if (grad && (reinterpret_cast<uintptr_t>(grad) & 15u)) return fail(c, GVE_E_INVALID, "gradient not 16-byte aligned");
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    GVE_TRY(size_pairs(k, prims, o));
+    GVE_TRY(bin_sized(k, prims, o));
     GVE_CUDA(cudaMemsetAsync(c->acc.p, 0, sizeof(float) * 12 * (n > 0 ? n : 1), k.s), "memset acc");
-    GVE_TRY(bin_all(k, prims, o, 0));
     BrickArgs a = brick_args(k, o);
     a.upstream = grad_field;
     a.acc = (float*)c->acc.p;
@@ -483,8 +501,7 @@ gve_status gve_count_pairs(gve_ctx* c, const float* prims, int64_t n, gve_dims d
     if (!kept || !cand) return fail(c, GVE_E_INVALID, "null output");
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    GVE_TRY(size_pairs(k, prims, o));
-    GVE_TRY(bin_all(k, prims, o, 0));
+    GVE_TRY(bin_sized(k, prims, o));
     BrickArgs a = brick_args(k, o);
     launch_brick(kModeCount, a, k.s);
     GVE_CUDA(cudaGetLastError(), "launch (count)");
@@ -503,8 +520,7 @@ gve_status gve_kept_pairs(gve_ctx* c, const float* prims, int64_t n, gve_dims d,
     if ((int64_t)d.nx * d.ny * d.nz > ((int64_t)1 << 40)) return fail(c, GVE_E_INVALID, "grid above 2^40 voxels");
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    GVE_TRY(size_pairs(k, prims, o));
-    GVE_TRY(bin_all(k, prims, o, 0));
+    GVE_TRY(bin_sized(k, prims, o));
     BrickArgs a = brick_args(k, o);
     a.pairs = reinterpret_cast<unsigned long long*>(pairs);
     a.pairs_cap = (unsigned long long)cap;
@@ -532,7 +548,15 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
     const gve_eval_opts* o = &sc->eval;
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    GVE_TRY(size_pairs(k, prims, o));
+    if (c->keys[0].p && c->pairs.p && !getenv("GVE_TEST_PAIR_CAP")) {
+        // pair buffers from an earlier call: the first iteration's binning
+        // sizes them (an overflow grows them and replays from there)
+        GVE_TRY(size_static(k));
+        GVE_TRY(grow_pairs(k, 0, 0));
+        reset_state(k);
+    } else {
+        GVE_TRY(size_pairs(k, prims, o));
+    }
     long long nn = n > 0 ? n : 1;
     float* m = adam_state;
     if (!m) {

@@ -57,9 +57,11 @@ def test_peak_microbenchmarks_run_and_stay_physical():
                                              "--format=csv,noheader,nounits"]).decode().split()[0])
     except Exception:
         mhz = 2100.0
-    ffma, ms = gve.gve_peak_bench("ffma", 2000)
-    assert ms > 0 and 0 < ffma <= 1.02 * sms * 128 * mhz * 1e6
-    ffma2, _ = gve.gve_peak_bench("ffma2", 2000)
+    # best of three runs each: the first launches may still see the clock ramping up
+    runs = {kind: [gve.gve_peak_bench(kind, it) for _ in range(3)]
+            for kind, it in (("ffma", 2000), ("ffma2", 2000), ("ex2", 500))}
+    assert all(ms > 0 for r in runs.values() for _, ms in r)
+    ffma, ffma2, ex2 = (max(v for v, _ in runs[k]) for k in ("ffma", "ffma2", "ex2"))
+    assert 0 < ffma <= 1.02 * sms * 128 * mhz * 1e6
     assert ffma2 > 0.5 * ffma
-    ex2, _ = gve.gve_peak_bench("ex2", 500)
     assert 0 < ex2 < ffma

@@ -213,6 +213,16 @@ gve_status grow_pairs(Call& k, unsigned long long need1, unsigned long long need
 
 // sizing: the binning runs until both pair buffers hold its totals (three
 // runs at most: tile pairs, then brick pairs, are found too large)
+// test hook: a logical pair capacity below what the binning needs, to
+// exercise the overflow detection and replay of refinement
+void test_pair_cap(gve_ctx* c)
+{
+    if (const char* tc = getenv("GVE_TEST_PAIR_CAP")) {
+        const unsigned long long t = strtoull(tc, nullptr, 10);
+        if (t > 0 && t < c->cap) c->cap = t;
+    }
+}
+
 gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
 {
     gve_ctx* c = k.c;
@@ -228,12 +238,7 @@ gve_status size_pairs(Call& k, const float* prims, const gve_eval_opts* o)
         GVE_TRY(grow_pairs(k, h.total1, tiles ? 0 : h.total));
         if (!tiles) break;  // the brick total was complete: both sizes known
     }
-    // test hook: a logical pair capacity below what the binning needs, to
-    // exercise the overflow detection and replay of refinement
-    if (const char* tc = getenv("GVE_TEST_PAIR_CAP")) {
-        const unsigned long long t = strtoull(tc, nullptr, 10);
-        if (t > 0 && t < c->cap) c->cap = t;
-    }
+    test_pair_cap(c);
     reset_state(k);
     return GVE_OK;
 }
@@ -548,11 +553,12 @@ gve_status gve_refine(gve_ctx* c, float* prims, int64_t n, const float* field, g
     const gve_eval_opts* o = &sc->eval;
     Call k;
     GVE_TRY(begin(c, k, n, d, o, stream));
-    if (c->keys[0].p && c->pairs.p && !getenv("GVE_TEST_PAIR_CAP")) {
+    if (c->keys[0].p && c->pairs.p) {
         // pair buffers from an earlier call: the first iteration's binning
         // sizes them (an overflow grows them and replays from there)
         GVE_TRY(size_static(k));
         GVE_TRY(grow_pairs(k, 0, 0));
+        test_pair_cap(c);
         reset_state(k);
     } else {
         GVE_TRY(size_pairs(k, prims, o));

@@ -108,7 +108,36 @@ __global__ void __launch_bounds__(256) k_grad_occ(const float* __restrict__ V, i
     }
 }
 
-// keys: detail (mode 0), coverage (mode 1), gbar (mode 2, 32-bit)
+// detail key of voxel v (Efraimidis-Spirakis with weight g > 0): -ln(u) / g
+// in FP64, u = (2m + 1) 2^-53 from the voxel's Philox draw; its bits order as
+// the key (positive doubles)
+__device__ __forceinline__ unsigned long long detail_key(unsigned long long v, float gv, unsigned long long seed)
+{
+    uint32_t r[4];
+    draw(v, 0u, seed, r);
+    unsigned long long m = (((unsigned long long)r[0] << 32) | r[1]) >> 12;
+    double u = (double)(2 * m + 1) * 0x1p-53;
+    double kd = -log(u) / (double)gv;
+    return (unsigned long long)__double_as_longlong(kd);
+}
+
+// float32 companion of detail_key, within a relative 2^-21 of it (the bound
+// used is 2^-16): -ln(u) as -logf(u) for u <= 1/2, and as -log1pf(-(1 - u))
+// above, with 1 - u formed exactly from the integer 2^53 - (2m + 1); both
+// arguments are one rounding from exact, and -ln is well conditioned on
+// either side (relative condition number below 1.45)
+__device__ __forceinline__ uint32_t detail_key32(unsigned long long v, float gv, unsigned long long seed)
+{
+    uint32_t r[4];
+    draw(v, 0u, seed, r);
+    const unsigned long long m = (((unsigned long long)r[0] << 32) | r[1]) >> 12;
+    const unsigned long long a = 2 * m + 1;
+    const float L = a <= (1ull << 52) ? -logf((float)a * 0x1p-53f)
+                                       : -log1pf(-((float)((1ull << 53) - a) * 0x1p-53f));
+    return __float_as_uint(L / gv);
+}
+
+// keys: detail (mode 0, FP64; mode 3, float32), coverage (mode 1), gbar (mode 2, 32-bit)
 __global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const float* __restrict__ g, long long M,
                                               float thr, unsigned long long seed, int mode,
                                               unsigned long long* __restrict__ k64, uint32_t* __restrict__ k32)
@@ -117,6 +146,11 @@ __global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const
         const bool occ = V[v] > thr;
         if (mode == 2) {
             k32[v] = occ ? __float_as_uint(g[v]) : 0xFFFFFFFFu;
+            continue;
+        }
+        if (mode == 3) {
+            const float gv = g[v];
+            k32[v] = occ && gv > 0.0f ? detail_key32((unsigned long long)v, gv, seed) : 0xFFFFFFFFu;
             continue;
         }
         unsigned long long key = ~0ull;
@@ -128,17 +162,28 @@ __global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const
             }
         } else {
             const float gv = g[v];
-            if (occ && gv > 0.0f) {
-                uint32_t r[4];
-                draw((unsigned long long)v, 0u, seed, r);
-                unsigned long long m = (((unsigned long long)r[0] << 32) | r[1]) >> 12;
-                double u = (double)(2 * m + 1) * 0x1p-53;
-                double kd = -log(u) / (double)gv;
-                key = (unsigned long long)__double_as_longlong(kd);
-            }
+            if (occ && gv > 0.0f) key = detail_key((unsigned long long)v, gv, seed);
         }
         k64[v] = key;
     }
+}
+
+// exact detail keys of the candidate voxels
+__global__ void __launch_bounds__(256) k_detail_keys(const float* __restrict__ g, const long long* __restrict__ cand,
+                                                     long long C, unsigned long long seed,
+                                                     unsigned long long* __restrict__ key)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const long long v = cand[i];
+    key[i] = detail_key((unsigned long long)v, g[v], seed);
+}
+
+__global__ void __launch_bounds__(256) k_gather_vox(const long long* __restrict__ cand, const long long* __restrict__ pos,
+                                                    long long n, long long* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cand[pos[i]];
 }
 
 template <typename K>
@@ -535,6 +580,70 @@ gve_status draw_set(gve_ctx* c, const unsigned long long* keys, long long M, lon
     return GVE_OK;
 }
 
+// the detail draw: the same seeds as draw_set over every voxel's FP64 key,
+// with FP64 only where it can decide.  The float32 keys (mode 3) are within
+// a relative e = 2^-16 of the FP64 ones, so if t is the Nd-th smallest float
+// key, at least Nd FP64 keys are <= t / (1 - e), and every voxel whose FP64
+// key is at most the Nd-th smallest one has a float key <= t (1 + e) / (1 - e).
+// Those candidates (in voxel order) get their FP64 keys, and draw_set over
+// them picks the same voxels, ties included, in the same order.  Falls back
+// to FP64 keys everywhere when the candidates would not fit beside the
+// float keys (or t is not finite).
+gve_status draw_detail(gve_ctx* c, const float* V, const float* g, long long M, float thr, unsigned long long seed,
+                       long long Nd, long long* out, cudaStream_t s)
+{
+    if (Nd <= 0) return GVE_OK;
+    unsigned long long* k64 = (unsigned long long*)c->a_keys.p;
+    uint32_t* kf = (uint32_t*)c->a_keys.p;
+    bool fast = getenv("GVE_TEST_DRAW_FULL") == nullptr;
+    long long C = 0;
+    uint32_t bb = 0;
+    const long long nblk = (M + kCompactChunk - 1) / kCompactChunk;
+    gve_status st = ensure(c, c->a_cnt, sizeof(uint32_t) * nblk + sizeof(unsigned long long) * (nblk + 1) + 64, s);
+    if (st != GVE_OK) return st;
+    uint32_t* bcnt = (uint32_t*)c->a_cnt.p;
+    unsigned long long* boff = (unsigned long long*)((char*)c->a_cnt.p + ((sizeof(uint32_t) * nblk + 15) / 16) * 16);
+    if (fast) {
+        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, seed, 3, nullptr, kf);
+        uint32_t tb = 0;
+        if ((st = radix_select<uint32_t>(c, kf, M, (unsigned long long)(Nd - 1), &tb, s)) != GVE_OK) return st;
+        float t;
+        memcpy(&t, &tb, sizeof(t));
+        fast = std::isfinite(t);
+        if (fast) {
+            const double e = 0x1p-16;
+            const double bd = (double)t * (1.0 + e) / (1.0 - e);
+            float bf = (float)bd;
+            if ((double)bf < bd) bf = std::nextafter(bf, INFINITY);
+            memcpy(&bb, &bf, sizeof(bb));
+            k_compact_count<uint32_t><<<(unsigned)nblk, 256, 0, s>>>(kf, M, bb, M, 0, bcnt);
+            launch_exscan_u32(bcnt, nblk, boff, c->scanp.p, s);
+            unsigned long long hcnt = 0;
+            cudaError_t e2 = cudaMemcpyAsync(&hcnt, boff + nblk, sizeof(hcnt), cudaMemcpyDeviceToHost, s);
+            if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "detail candidates");
+            C = (long long)hcnt;
+            // candidates, their FP64 keys and the picked positions beside the float keys
+            fast = C >= Nd && 16 * C + 8 * Nd + 64 <= 4 * M;
+        }
+    }
+    if (!fast) {
+        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, seed, 0, k64, nullptr);
+        return draw_set(c, k64, M, Nd, out, s);
+    }
+    const size_t base = ((size_t)4 * M + 15) / 16 * 16;
+    long long* cand = (long long*)((char*)c->a_keys.p + base);
+    unsigned long long* kc = (unsigned long long*)(cand + C);
+    long long* pos = (long long*)(kc + C);
+    k_compact_write<uint32_t><<<(unsigned)nblk, 256, 0, s>>>(kf, M, bb, M, 0, boff, C, cand);
+    k_detail_keys<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(g, cand, C, seed, kc);
+    if ((st = draw_set(c, kc, C, Nd, pos, s)) != GVE_OK) return st;
+    k_gather_vox<<<(unsigned)((Nd + 255) / 256), 256, 0, s>>>(cand, pos, Nd, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "detail draw");
+    return GVE_OK;
+}
+
 gve_status group_spacing(gve_ctx* c, const long long* vox, long long ng, gve_dims d, long long n_occ, long long N,
                          double* h, cudaStream_t s)
 {
@@ -619,8 +728,7 @@ gve_status allocate(gve_ctx* c, const float* V, gve_dims d, int64_t N, const gve
     unsigned long long* k64 = (unsigned long long*)c->a_keys.p;
     long long* vd = (long long*)c->a_sel.p;
     long long* vc = vd + Nd;
-    k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, o->seed, 0, k64, nullptr);
-    if ((st = draw_set(c, k64, M, Nd, vd, s)) != GVE_OK) return st;
+    if ((st = draw_detail(c, V, g, M, thr, o->seed, Nd, vd, s)) != GVE_OK) return st;
     k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, o->seed, 1, k64, nullptr);
     if ((st = draw_set(c, k64, M, Nc, vc, s)) != GVE_OK) return st;
     // group spacing

@@ -7,6 +7,7 @@ bricks with ragged tails, Gaussian lists longer than one shared-memory chunk,
 empty and degenerate inputs.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -239,6 +240,31 @@ def test_allocate_matches_oracle(small_workload):
     assert (dots > 1 - 1e-5).mean() > 0.999
     np.testing.assert_allclose(P[:, 10:12], prm[:, 10:12], rtol=1e-5, atol=1e-6)
     assert info["n_detail"] == 2253 and info["n_coverage"] == 4096 - 2253
+
+
+@pytest.mark.parametrize("kind", ["grf", "fbm"])
+def test_detail_draw_matches_fp64_keys_everywhere(kind):
+    """The detail draw computes FP64 keys only for the voxels whose float32
+    keys come near the selection threshold; the allocation equals the one
+    drawn from FP64 keys at every voxel bit for bit, at a moderate budget and
+    at the largest budget the field supports (the threshold among the
+    largest keys)."""
+    dev_ = torch.device("cuda", 0)
+    V = inputs.grf(96, seed=21, device=dev_) if kind == "grf" else inputs.fbm_fronts(96, seed=22, device=dev_)
+    try:
+        gve.gve_allocate(V, 10 ** 9, seed=5)
+        raise AssertionError("a budget of 10^9 on 96^3 voxels must be infeasible")
+    except gve.BudgetError as e:
+        fmax = e.feasible_max
+    for budget in (20_000, fmax):
+        P, info = gve.gve_allocate(V, budget, seed=5)
+        os.environ["GVE_TEST_DRAW_FULL"] = "1"
+        try:
+            Q, info_q = gve.gve_allocate(V, budget, seed=5)
+        finally:
+            del os.environ["GVE_TEST_DRAW_FULL"]
+        assert torch.equal(P, Q), budget
+        assert info == info_q
 
 
 def test_allocate_grf_and_budget_error():

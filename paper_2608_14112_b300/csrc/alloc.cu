@@ -137,7 +137,7 @@ __device__ __forceinline__ uint32_t detail_key32(unsigned long long v, float gv,
     return __float_as_uint(L / gv);
 }
 
-// keys: detail (mode 0, FP64; mode 3, float32), coverage (mode 1), gbar (mode 2, 32-bit)
+// keys: detail (mode 0, FP64; mode 3, float32), coverage (mode 1; mode 4, its top 32 bits), gbar (mode 2, 32-bit)
 __global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const float* __restrict__ g, long long M,
                                               float thr, unsigned long long seed, int mode,
                                               unsigned long long* __restrict__ k64, uint32_t* __restrict__ k32)
@@ -151,6 +151,12 @@ __global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const
         if (mode == 3) {
             const float gv = g[v];
             k32[v] = occ && gv > 0.0f ? detail_key32((unsigned long long)v, gv, seed) : 0xFFFFFFFFu;
+            continue;
+        }
+        if (mode == 4) {  // the coverage key's top 32 bits
+            uint32_t r[4];
+            if (occ) draw((unsigned long long)v, 1u, seed, r);
+            k32[v] = occ ? r[0] : 0xFFFFFFFFu;
             continue;
         }
         unsigned long long key = ~0ull;
@@ -168,15 +174,26 @@ __global__ void __launch_bounds__(256) k_keys(const float* __restrict__ V, const
     }
 }
 
-// exact detail keys of the candidate voxels
-__global__ void __launch_bounds__(256) k_detail_keys(const float* __restrict__ g, const long long* __restrict__ cand,
-                                                     long long C, unsigned long long seed,
-                                                     unsigned long long* __restrict__ key)
+// the full 64-bit keys (mode 0: detail, mode 1: coverage) of the candidate voxels
+__global__ void __launch_bounds__(256) k_cand_keys(const float* __restrict__ V, const float* __restrict__ g, float thr,
+                                                   const long long* __restrict__ cand, long long C,
+                                                   unsigned long long seed, int mode,
+                                                   unsigned long long* __restrict__ key)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C) return;
     const long long v = cand[i];
-    key[i] = detail_key((unsigned long long)v, g[v], seed);
+    const bool occ = V[v] > thr;
+    unsigned long long k = ~0ull;
+    if (mode == 0) {
+        const float gv = g[v];
+        if (occ && gv > 0.0f) k = detail_key((unsigned long long)v, gv, seed);
+    } else if (occ) {
+        uint32_t r[4];
+        draw((unsigned long long)v, 1u, seed, r);
+        k = ((unsigned long long)r[0] << 32) | r[1];
+    }
+    key[i] = k;
 }
 
 __global__ void __launch_bounds__(256) k_gather_vox(const long long* __restrict__ cand, const long long* __restrict__ pos,
@@ -580,21 +597,25 @@ gve_status draw_set(gve_ctx* c, const unsigned long long* keys, long long M, lon
     return GVE_OK;
 }
 
-// the detail draw: the same seeds as draw_set over every voxel's FP64 key,
-// with FP64 only where it can decide.  The float32 keys (mode 3) are within
-// a relative e = 2^-16 of the FP64 ones, so if t is the Nd-th smallest float
-// key, at least Nd FP64 keys are <= t / (1 - e), and every voxel whose FP64
-// key is at most the Nd-th smallest one has a float key <= t (1 + e) / (1 - e).
-// Those candidates (in voxel order) get their FP64 keys, and draw_set over
-// them picks the same voxels, ties included, in the same order.  Falls back
-// to FP64 keys everywhere when the candidates would not fit beside the
-// float keys (or t is not finite).
-gve_status draw_detail(gve_ctx* c, const float* V, const float* g, long long M, float thr, unsigned long long seed,
-                       long long Nd, long long* out, cudaStream_t s)
+// One draw (mode 0: detail, FP64 keys; mode 1: coverage, 64-bit integer
+// keys) in two levels: the same seeds as draw_set over every voxel's key,
+// with the full key computed only where it can decide.  A 32-bit surrogate
+// of each key is selected first: for the coverage keys their top 32 bits (a
+// monotone map, so the n-th smallest surrogate t is the surrogate of the
+// n-th smallest key, and every voxel whose key is at most that key has a
+// surrogate <= t); for the detail keys a float32 key within a relative
+// e = 2^-16 of the FP64 one (at least n FP64 keys are <= t / (1 - e), and
+// every voxel whose FP64 key is at most the n-th smallest has a float key
+// <= t (1 + e) / (1 - e)).  The candidates under that bound (in voxel order)
+// get their full keys, and draw_set over them picks the same voxels, ties
+// included, in the same order.  Falls back to full keys everywhere when the
+// candidates would not fit beside the surrogates (or t is not finite).
+gve_status draw_two_level(gve_ctx* c, const float* V, const float* g, long long M, float thr, unsigned long long seed,
+                          int mode, long long n, long long* out, cudaStream_t s)
 {
-    if (Nd <= 0) return GVE_OK;
+    if (n <= 0) return GVE_OK;
     unsigned long long* k64 = (unsigned long long*)c->a_keys.p;
-    uint32_t* kf = (uint32_t*)c->a_keys.p;
+    uint32_t* k32 = (uint32_t*)c->a_keys.p;
     bool fast = getenv("GVE_TEST_DRAW_FULL") == nullptr;
     long long C = 0;
     uint32_t bb = 0;
@@ -604,43 +625,47 @@ gve_status draw_detail(gve_ctx* c, const float* V, const float* g, long long M, 
     uint32_t* bcnt = (uint32_t*)c->a_cnt.p;
     unsigned long long* boff = (unsigned long long*)((char*)c->a_cnt.p + ((sizeof(uint32_t) * nblk + 15) / 16) * 16);
     if (fast) {
-        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, seed, 3, nullptr, kf);
+        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, seed, mode == 0 ? 3 : 4, nullptr, k32);
         uint32_t tb = 0;
-        if ((st = radix_select<uint32_t>(c, kf, M, (unsigned long long)(Nd - 1), &tb, s)) != GVE_OK) return st;
-        float t;
-        memcpy(&t, &tb, sizeof(t));
-        fast = std::isfinite(t);
-        if (fast) {
+        if ((st = radix_select<uint32_t>(c, k32, M, (unsigned long long)(n - 1), &tb, s)) != GVE_OK) return st;
+        if (mode == 0) {
+            float t;
+            memcpy(&t, &tb, sizeof(t));
+            fast = std::isfinite(t);
             const double e = 0x1p-16;
             const double bd = (double)t * (1.0 + e) / (1.0 - e);
             float bf = (float)bd;
             if ((double)bf < bd) bf = std::nextafter(bf, INFINITY);
             memcpy(&bb, &bf, sizeof(bb));
-            k_compact_count<uint32_t><<<(unsigned)nblk, 256, 0, s>>>(kf, M, bb, M, 0, bcnt);
+        } else {
+            bb = tb;
+        }
+        if (fast) {
+            k_compact_count<uint32_t><<<(unsigned)nblk, 256, 0, s>>>(k32, M, bb, M, 0, bcnt);
             launch_exscan_u32(bcnt, nblk, boff, c->scanp.p, s);
             unsigned long long hcnt = 0;
             cudaError_t e2 = cudaMemcpyAsync(&hcnt, boff + nblk, sizeof(hcnt), cudaMemcpyDeviceToHost, s);
             if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-            if (e2 != cudaSuccess) return cuda_fail(c, e2, "detail candidates");
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "draw candidates");
             C = (long long)hcnt;
-            // candidates, their FP64 keys and the picked positions beside the float keys
-            fast = C >= Nd && 16 * C + 8 * Nd + 64 <= 4 * M;
+            // candidates, their full keys and the picked positions beside the surrogates
+            fast = C >= n && 16 * C + 8 * n + 64 <= 4 * M;
         }
     }
     if (!fast) {
-        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, seed, 0, k64, nullptr);
-        return draw_set(c, k64, M, Nd, out, s);
+        k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, seed, mode, k64, nullptr);
+        return draw_set(c, k64, M, n, out, s);
     }
     const size_t base = ((size_t)4 * M + 15) / 16 * 16;
     long long* cand = (long long*)((char*)c->a_keys.p + base);
     unsigned long long* kc = (unsigned long long*)(cand + C);
     long long* pos = (long long*)(kc + C);
-    k_compact_write<uint32_t><<<(unsigned)nblk, 256, 0, s>>>(kf, M, bb, M, 0, boff, C, cand);
-    k_detail_keys<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(g, cand, C, seed, kc);
-    if ((st = draw_set(c, kc, C, Nd, pos, s)) != GVE_OK) return st;
-    k_gather_vox<<<(unsigned)((Nd + 255) / 256), 256, 0, s>>>(cand, pos, Nd, out);
+    k_compact_write<uint32_t><<<(unsigned)nblk, 256, 0, s>>>(k32, M, bb, M, 0, boff, C, cand);
+    k_cand_keys<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(V, g, thr, cand, C, seed, mode, kc);
+    if ((st = draw_set(c, kc, C, n, pos, s)) != GVE_OK) return st;
+    k_gather_vox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, pos, n, out);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, "detail draw");
+    if (e != cudaSuccess) return cuda_fail(c, e, "two-level draw");
     return GVE_OK;
 }
 
@@ -725,12 +750,10 @@ gve_status allocate(gve_ctx* c, const float* V, gve_dims d, int64_t N, const gve
     memcpy(&gbar_f, &gbits, sizeof(float));
     const double gbar = (double)gbar_f;
     // draws
-    unsigned long long* k64 = (unsigned long long*)c->a_keys.p;
     long long* vd = (long long*)c->a_sel.p;
     long long* vc = vd + Nd;
-    if ((st = draw_detail(c, V, g, M, thr, o->seed, Nd, vd, s)) != GVE_OK) return st;
-    k_keys<<<grid_for(M), 256, 0, s>>>(V, g, M, thr, o->seed, 1, k64, nullptr);
-    if ((st = draw_set(c, k64, M, Nc, vc, s)) != GVE_OK) return st;
+    if ((st = draw_two_level(c, V, g, M, thr, o->seed, 0, Nd, vd, s)) != GVE_OK) return st;
+    if ((st = draw_two_level(c, V, g, M, thr, o->seed, 1, Nc, vc, s)) != GVE_OK) return st;
     // group spacing
     double hd = 0, hcv = 0;
     if ((st = group_spacing(c, vd, Nd, d, n_occ, N, &hd, s)) != GVE_OK) return st;

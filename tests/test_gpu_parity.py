@@ -242,25 +242,26 @@ def test_allocate_matches_oracle(small_workload):
     assert info["n_detail"] == 2253 and info["n_coverage"] == 4096 - 2253
 
 
-@pytest.mark.parametrize("kind", ["grf", "fbm"])
-def test_detail_draw_matches_fp64_keys_everywhere(kind):
-    """The detail draw computes FP64 keys only for the voxels whose float32
-    keys come near the selection threshold; the allocation equals the one
-    drawn from FP64 keys at every voxel bit for bit, at a moderate budget and
-    at the largest budget the field supports (the threshold among the
-    largest keys)."""
+@pytest.mark.parametrize("kind,occ", [("grf", 0.02), ("fbm", 0.02), ("fbm", 0.5)])
+def test_two_level_draws_match_full_keys(kind, occ):
+    """Both draws select on 32-bit surrogates of their keys first and compute
+    the full keys (FP64 for the detail draw) only for the voxels near the
+    threshold; the allocation equals the one drawn from full keys at every
+    voxel bit for bit, at a moderate budget and at the largest budget the
+    field supports (thresholds among the largest keys), with most voxels
+    occupied or about half of them."""
     dev_ = torch.device("cuda", 0)
     V = inputs.grf(96, seed=21, device=dev_) if kind == "grf" else inputs.fbm_fronts(96, seed=22, device=dev_)
     try:
-        gve.gve_allocate(V, 10 ** 9, seed=5)
+        gve.gve_allocate(V, 10 ** 9, seed=5, occ_thresh=occ)
         raise AssertionError("a budget of 10^9 on 96^3 voxels must be infeasible")
     except gve.BudgetError as e:
         fmax = e.feasible_max
     for budget in (20_000, fmax):
-        P, info = gve.gve_allocate(V, budget, seed=5)
+        P, info = gve.gve_allocate(V, budget, seed=5, occ_thresh=occ)
         os.environ["GVE_TEST_DRAW_FULL"] = "1"
         try:
-            Q, info_q = gve.gve_allocate(V, budget, seed=5)
+            Q, info_q = gve.gve_allocate(V, budget, seed=5, occ_thresh=occ)
         finally:
             del os.environ["GVE_TEST_DRAW_FULL"]
         assert torch.equal(P, Q), budget

@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="pick brick edge / Gaussians per block first")
     ap.add_argument("--e2e-iters", type=int, default=300)
     ap.add_argument("--ttp-iters", type=int, default=2000, help="full schedule of the time-to-PSNR run (0 = skip)")
+    ap.add_argument("--no-proposal-ttp", dest="proposal_ttp", action="store_false",
+                    help="headline: skip training the pairs proposal and its time-to-PSNR against plain")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample", type=int, default=192, help="edge of the CPU sample sub-volume")
     ap.add_argument("--sample-iters", type=int, default=3)
@@ -419,6 +421,102 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def proposal_fields(kind, dev):
+    """The proposals' training fields and the held-out field generator:
+    64 seeded 256^3 crops (corners from numpy's generator with seed 7) of
+    1024^3 fbm + fronts fields of seeds 1000-1063, the headline field's
+    family, and 512^3 centre crops of other seeds; or (kind "grf") 256^3 and
+    512^3 Gaussian random fields of those seeds."""
+    import numpy as np
+    from paper_2608_14112_b300 import inputs
+    if kind == "fbm_crops":
+        crng = np.random.default_rng(7)
+        tr = [inputs.fbm_fronts(1024, seed=s, device=dev,
+                                region=(tuple(int(v) for v in crng.integers(0, 769, 3)), (256, 256, 256)))
+              for s in range(1000, 1064)]
+
+        def held_out(seed):
+            return inputs.fbm_fronts(1024, seed=seed, device=dev, region=((256, 256, 256), (512, 512, 512)))
+    else:
+        tr = [inputs.grf(256, seed=s, device=dev) for s in range(1000, 1064)]
+
+        def held_out(seed):
+            return inputs.grf(512, seed=seed, device=dev)
+    return tr, held_out
+
+
+def train_pairs_proposal(tr, args, dev):
+    """The allocation -> refined pairs trainer: features of each training
+    field's analytic allocation (25,000 Gaussians) against the change that
+    --pair-iters refinement iterations made to a and log s (targets scaled by
+    their spreads), 20 epochs, then the step size of its corrections judged
+    by --cal-iters refinement iterations on 8 training fields."""
+    from paper_2608_14112_b300 import proposal
+    X, T = proposal.make_pairs(tr, 25_000, iters=args.pair_iters, seed=args.seed)
+    Ts, tscale = proposal.scale_targets(T)
+    m = proposal.Proposal(dev, seed=0)
+    log = m.train(X, Ts, epochs=20, lr=1e-3, tscale=tscale)
+    cal = m.calibrate(tr[:8], 25_000, iters=args.cal_iters, seed=args.seed)
+    return m, log, cal
+
+
+def headline_proposal_ttp(V, w, ttp, args):
+    """The learned proposal (allocation -> refined pairs, trained on the
+    headline field's family) against plain allocation on the headline field
+    itself, against the targets of the plain time-to-PSNR run: the proposal
+    start (allocation, features and network, CUDA events) refines in
+    segments of 100 iterations until it reaches both targets or the full
+    schedule ends; time = start + iterations to the target at its own ms per
+    iteration, the same measure as the plain run's."""
+    import numpy as np
+    import torch
+    from paper_2608_14112_b300 import gve, proposal
+    dev = V.device
+    t0 = time.perf_counter()
+    tr, _ = proposal_fields("fbm_crops", dev)
+    model, log, cal = train_pairs_proposal(tr, args, dev)
+    del tr
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    targets = {"final": ttp["target_db"], "median_last50": ttp["smoothed"]["target_db"]}
+    plain_s = {"final": ttp["time_to_target_s"], "median_last50": ttp["smoothed"]["time_to_target_s"]}
+    full = ttp["schedule_full"]
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    P, info = gve.gve_allocate(V, w["budget"], seed=args.seed)
+    F = proposal.features(V, P, info["n_detail"], info["gbar"])
+    model.apply(F, P, V.shape)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    start_ms = e0.elapsed_time(e1)
+    state = torch.zeros((2, P.shape[0], 12), dtype=torch.float32, device=dev)
+    curve, ms_total, done = [], 0.0, 0
+    while done < full:
+        seg = min(100, full - done)
+        tr_ = torch.zeros(seg, dtype=torch.float64, device=dev)
+        st = gve.gve_refine(P, V, iters=seg, lr=w["lr"], adam_state=state, step0=done, trace=tr_)
+        curve.extend((-10.0 * np.log10(tr_.cpu().numpy()[1:])).tolist())
+        curve.append(st["psnr_final"])
+        ms_total += st["ms_total"]
+        done += seg
+        if max(curve) >= max(targets.values()):
+            break
+    c = np.array(curve)
+    msi = ms_total / done
+    its = {k: (int(np.nonzero(c >= t)[0][0]) + 1 if (c >= t).any() else None) for k, t in targets.items()}
+    times = {k: (None if it is None else (start_ms + it * msi) / 1e3) for k, it in its.items()}
+    return {"trainer": "allocation -> refined pairs (64 crops of 256^3 from 1024^3 fbm + fronts fields of "
+                       f"other seeds, 25,000 Gaussians each, targets from {args.pair_iters} iterations, step "
+                       f"judged by {args.cal_iters} iterations on 8 of them)",
+            "train_s": train_s, "train_loss_first_last": [log.losses[0], log.losses[-1]], "gamma": model.gamma,
+            "targets_db": targets, "start_ms": start_ms, "ms_per_iter": msi, "iters_run": done,
+            "iters_to_target": its, "time_to_target_s": times, "plain_time_to_target_s": plain_s,
+            "psnr_at": {str(t): float(c[t - 1]) for t in (1, 10, 100, 300) if t <= len(c)},
+            "speedup_vs_plain": {k: (None if times[k] is None else plain_s[k] / times[k]) for k in targets}}
+
+
 def proposal_headline_judge(models, args):
     """Both proposals against plain allocation on the headline field (fbm +
     fronts 1024^3, 1.4 M Gaussians, the headline learning rate): plain runs
@@ -510,21 +608,7 @@ def run_proposal(args):
     gbuild.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    if args.proposal_fields == "fbm_crops":
-        # 256^3 crops at seeded corners and 512^3 centre crops of 1024^3 fbm + fronts
-        # fields: the headline field's statistics at the same grid scale
-        crng = np.random.default_rng(7)
-        tr = [inputs.fbm_fronts(1024, seed=s, device=dev,
-                                region=(tuple(int(v) for v in crng.integers(0, 769, 3)), (256, 256, 256)))
-              for s in range(1000, 1064)]
-
-        def held_out(seed):
-            return inputs.fbm_fronts(1024, seed=seed, device=dev, region=((256, 256, 256), (512, 512, 512)))
-    else:
-        tr = [inputs.grf(256, seed=s, device=dev) for s in range(1000, 1064)]
-
-        def held_out(seed):
-            return inputs.grf(512, seed=seed, device=dev)
+    tr, held_out = proposal_fields(args.proposal_fields, dev)
     allocs = proposal.allocations(tr, 25_000, seed=args.seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -533,14 +617,10 @@ def run_proposal(args):
     torch.cuda.synchronize()
     train_e2e_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    X, T = proposal.make_pairs(tr, 25_000, iters=args.pair_iters, seed=args.seed)
-    Ts, tscale = proposal.scale_targets(T)
-    m_pairs = proposal.Proposal(dev, seed=0)
-    log_pairs = m_pairs.train(X, Ts, epochs=20, lr=1e-3, tscale=tscale)
-    cal = m_pairs.calibrate(tr[:8], 25_000, iters=args.cal_iters, seed=args.seed)
+    m_pairs, log_pairs, cal = train_pairs_proposal(tr, args, dev)
     torch.cuda.synchronize()
     train_pairs_s = time.perf_counter() - t0
-    del tr, allocs, X, T, Ts
+    del tr, allocs
     iters = args.prop_iters
     marks = [m for m in (0, 1, 5, 10, 20, 50, 100, 150, 199, 299, 499) if m < iters]
     kinds = {"plain": None, "pairs": m_pairs, "e2e": m_e2e}
@@ -1089,6 +1169,8 @@ def run_ours(args):
     if args.ttp_iters > 0 and rank == 0:
         ttp = time_to_psnr(V, w, opts, args.seed, alloc_ms, full=args.ttp_iters,
                            reduced=min(300, args.ttp_iters))
+        if args.proposal_ttp and args.workload == "headline":
+            ttp["proposal"] = headline_proposal_ttp(V, w, ttp, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -161,7 +161,11 @@ GVE_API const char* gve_last_error(const gve_ctx* ctx);
  *   info         host, optional summary.
  * Synchronises `stream` (the feasibility check reads two counts).
  * Returns GVE_E_BUDGET without writing prims_dev when the field cannot
- * support the budget. */
+ * support the budget.  The draws select on 32-bit surrogates of their keys
+ * and compute the full keys (FP64 for the detail draw) only near the
+ * threshold; the seeds are those of a draw over every voxel's full key
+ * (the environment variable GVE_TEST_DRAW_FULL, for tests, forces that
+ * draw). */
 GVE_API gve_status gve_allocate(gve_ctx* ctx, const float* field_dev, gve_dims dims, int64_t budget,
                         const gve_alloc_opts* opts, float* prims_dev, int64_t* feasible_max,
                         gve_alloc_info* info, void* stream);

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) k_prep(const float* __restrict__ prims, l
         if (box_ok) {
             for (int j = 0; j < 3; ++j)
                 for (int i2 = 0; i2 < 3; ++i2) b.L[j * 3 + i2] = __fdiv_rn(kc.R[i2][j], sv[j]);
-            const float hB = __fadd_rn((float)(0.5 * (double)(g.B - 1)), 0.01f);
+            const float hB = __fadd_rn(0.5f * (float)(g.B - 1), 0.01f);
             for (int j = 0; j < 3; ++j) {
                 const float sabs =
                     __fadd_rn(__fadd_rn(fabsf(b.L[j * 3 + 0]), fabsf(b.L[j * 3 + 1])), fabsf(b.L[j * 3 + 2]));
@@ -159,7 +159,7 @@ template <int B>
 __device__ __forceinline__ uint32_t brick_test2(const BinRec& b, float mux, float muy, float muz, int bx, int by,
                                                 int bz)
 {
-    const float half = (float)(0.5 * (double)(B - 1));
+    const float half = 0.5f * (float)(B - 1);
     const float2 cx = make_float2(__fadd_rn((float)(bx * B), half), __fadd_rn((float)((bx + 1) * B), half));
     const float cy = __fadd_rn((float)(by * B), half), cz = __fadd_rn((float)(bz * B), half);
     const float2 dcx = __fadd2_rn(cx, make_float2(-mux, -mux));   // cx - mu_x

@@ -902,17 +902,19 @@ def run_structure(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": kern, "stage_ms": kms,
                 "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"}
-    Vh = V.cpu().pin_memory()
-    Vd = torch.empty_like(V)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        Vd.copy_(Vh, non_blocking=True)
-        gve.gve_structure_stats(Vd)
-    torch.cuda.synchronize()
-    enc = (time.perf_counter() - t0) / args.e2e_steps
-    e2e = {"value": M / enc / 1e9, "unit": "Gvoxel/s", "h2d_bytes_per_step": int(M * 4),
-           "d2h_bytes_per_step": 5 * 8, "includes": "H2D field from pinned memory, both sweeps, results to host"}
+    e2e = None
+    if args.e2e_steps > 0:
+        Vh = V.cpu().pin_memory()
+        Vd = torch.empty_like(V)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            Vd.copy_(Vh, non_blocking=True)
+            gve.gve_structure_stats(Vd)
+        torch.cuda.synchronize()
+        enc = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": M / enc / 1e9, "unit": "Gvoxel/s", "h2d_bytes_per_step": int(M * 4),
+               "d2h_bytes_per_step": 5 * 8, "includes": "H2D field from pinned memory, both sweeps, results to host"}
     cpu = None
     if not args.no_cpu_baseline:
         sec, desc = structure_cpu_sample(args)

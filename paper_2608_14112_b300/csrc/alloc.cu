@@ -1412,6 +1412,32 @@ __global__ void __launch_bounds__(kSweep1vThreads, 3) k_stat_sweep1v(StatGrid g,
             float pg = 0.0f, p[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             unsigned nocc = 0;
             uint32_t gb[4];
+            // the y and z gradient terms and the differences to the y, z
+            // and lag-16 neighbours of voxels (0, 1) and (2, 3) in packed
+            // f32x2 operations (lane-wise the scalar operations)
+            float2 py[2], pz[2];
+            float2 pp[5] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                            make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const float2 cc = h2 ? make_float2(c.z, c.w) : make_float2(c.x, c.y);
+                const float2 yp2 = h2 ? make_float2(yp.z, yp.w) : make_float2(yp.x, yp.y);
+                const float2 ym2 = h2 ? make_float2(ym.z, ym.w) : make_float2(ym.x, ym.y);
+                const float2 zp2 = h2 ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y);
+                const float2 zm2 = h2 ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y);
+                const float2 gy2 = __fmul2_rn(make_float2(fy, fy), __fadd2_rn(yp2, make_float2(-ym2.x, -ym2.y)));
+                const float2 gz2 = __fmul2_rn(make_float2(fz, fz), __fadd2_rn(zp2, make_float2(-zm2.x, -zm2.y)));
+                py[h2] = __fmul2_rn(gy2, gy2);
+                pz[h2] = __fmul2_rn(gz2, gz2);
+                const float2 nb[5] = {yp2, zp2, h2 ? make_float2(x16.z, x16.w) : make_float2(x16.x, x16.y),
+                                      h2 ? make_float2(y16.z, y16.w) : make_float2(y16.x, y16.y),
+                                      h2 ? make_float2(z16.z, z16.w) : make_float2(z16.x, z16.y)};
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const float2 d2 = __fadd2_rn(nb[k], make_float2(-cc.x, -cc.y));
+                    pp[k] = __ffma2_rn(d2, d2, pp[k]);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float cj = f4c(c, j);
@@ -1419,9 +1445,9 @@ __global__ void __launch_bounds__(kSweep1vThreads, 3) k_stat_sweep1v(StatGrid g,
                 const float xp = j < 3 ? f4c(c, j + 1) : xp3;
                 const float fx = (j == 0 && x == 0) || (j == 3 && x + 4 >= g.nx) ? 1.0f : 0.5f;
                 const float gx = fx * (xp - xm);
-                const float gy = fy * (f4c(yp, j) - f4c(ym, j));
-                const float gz = fz * (f4c(zp, j) - f4c(zm, j));
-                const float sx = gx * gx, s2 = gy * gy, s3 = gz * gz;
+                const float sx = gx * gx;
+                const float s2 = (j & 1) ? py[j >> 1].y : py[j >> 1].x;
+                const float s3 = (j & 1) ? pz[j >> 1].y : pz[j >> 1].x;
                 float sq = sx + s2;
                 sq = sq + s3;
                 const float gm = sqrtf(sq);
@@ -1430,19 +1456,11 @@ __global__ void __launch_bounds__(kSweep1vThreads, 3) k_stat_sweep1v(StatGrid g,
                 nocc += occupied;
                 gb[j] = occupied ? __float_as_uint(gm) : kStatEmpty;
                 if (occupied) atomicAdd(&h[stat_bin(gm)], 1u);
-                float d = xp - cj;
+                const float d = xp - cj;
                 p[0] = fmaf(d, d, p[0]);
-                d = f4c(yp, j) - cj;
-                p[1] = fmaf(d, d, p[1]);
-                d = f4c(zp, j) - cj;
-                p[2] = fmaf(d, d, p[2]);
-                d = f4c(x16, j) - cj;
-                p[3] = fmaf(d, d, p[3]);
-                d = f4c(y16, j) - cj;
-                p[4] = fmaf(d, d, p[4]);
-                d = f4c(z16, j) - cj;
-                p[5] = fmaf(d, d, p[5]);
             }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) p[k + 1] = pp[k].x + pp[k].y;
             G4[(base >> 2) + xi] = make_uint4(gb[0], gb[1], gb[2], gb[3]);
             occ += nocc;
             acc[0].add(pg);

@@ -247,9 +247,9 @@ def test_two_level_draws_match_full_keys(kind, occ):
     """Both draws select on 32-bit surrogates of their keys first and compute
     the full keys (FP64 for the detail draw) only for the voxels near the
     threshold; the allocation equals the one drawn from full keys at every
-    voxel bit for bit, at a moderate budget and at the largest budget the
-    field supports (thresholds among the largest keys), with most voxels
-    occupied or about half of them."""
+    voxel bit for bit, from small budgets to the largest one the field
+    supports (thresholds among the largest keys), with most voxels occupied
+    or about half of them."""
     dev_ = torch.device("cuda", 0)
     V = inputs.grf(96, seed=21, device=dev_) if kind == "grf" else inputs.fbm_fronts(96, seed=22, device=dev_)
     try:
@@ -257,7 +257,9 @@ def test_two_level_draws_match_full_keys(kind, occ):
         raise AssertionError("a budget of 10^9 on 96^3 voxels must be infeasible")
     except gve.BudgetError as e:
         fmax = e.feasible_max
-    for budget in (20_000, fmax):
+    # 20,000: a few candidates; a quarter of the voxels: about as many
+    # candidates as fit beside the surrogates; fmax: the full-key fallback
+    for budget in (20_000, V.numel() // 4, fmax):
         P, info = gve.gve_allocate(V, budget, seed=5, occ_thresh=occ)
         os.environ["GVE_TEST_DRAW_FULL"] = "1"
         try:

@@ -68,11 +68,11 @@ def _single(fields, counts, prims, iters, opts=None):
     return torch.cat(outs, 0), psnr, torch.stack(traces, 1)
 
 
-@pytest.mark.parametrize("brick", [8, 4])
-def test_batch_matches_per_volume_refine(batch, brick):
+@pytest.mark.parametrize("brick,gpb", [(8, 0), (4, 0), (16, 0), (8, 32)])
+def test_batch_matches_per_volume_refine(batch, brick, gpb):
     fields, counts, prims = batch
     iters = 6
-    opts = gve.EvalOptions(brick=brick)
+    opts = gve.EvalOptions(brick=brick, gaussians_per_block=gpb)
     ref, ref_psnr, ref_trace = _single(fields, counts, prims, iters, opts)
     P = prims.clone()
     trace = torch.zeros(iters * len(fields), dtype=torch.float64, device="cuda")

@@ -20,10 +20,13 @@
 // FMA, lane-wise identical to the scalar chain), the pair is kept iff t > T,
 // and G = 2^t on the SFU (ex2.approx).  num += w a G, den += w G;
 // Vtilde = num / max(den, rho0) (Eq. 3), residual and per-brick SSE
-// (float32 within the CTA, FP64 across CTAs: B300's FP64 rate is a small
-// fraction of its FP32 rate).  The upstream gradient gives per voxel
-// gn = dL/dnum = up / max(den, rho0) and gd = dL/dden = -Vtilde gn (when
-// den >= rho0), kept in shared memory.
+// (float32 within the CTA, FP64 across CTAs, in the reduction kernel:
+// B300's FP64 rate is a small fraction of its FP32 rate).  The row's target
+// values (or, in the backward mode, its upstream gradient) are copied to
+// shared memory with cp.async when the brick starts, so that their HBM
+// latency passes during the forward work.  The upstream gradient gives per
+// voxel gn = dL/dnum = up / max(den, rho0) and gd = dL/dden = -Vtilde gn
+// (when den >= rho0), kept in shared memory sub-brick by sub-brick.
 //
 // Phase 2 (backward): the (Gaussian, live sub-brick) tasks are compacted
 // (sub-brick-major) and spread over all threads; a task recomputes G by the
@@ -33,9 +36,10 @@
 // (dL/da = w A, dL/dw = H, and the chain rule scales S1, S2 by -w/2), with
 // the y- and z-dependence factored per row and per slice and the
 // x-moments taken against the brick-local offset X (constants of the
-// unrolled loop), shifted to dx once per task, in packed f32x2 arithmetic.  Task sums meet in shared memory (float atomics); one
-// thread per Gaussian then issues three 16-byte vector atomics into its
-// global accumulator.  Nothing per pair or per voxel goes to HBM.
+// unrolled loop), shifted to dx once per task, in packed f32x2
+// arithmetic.  Task sums meet in shared memory (float atomics); one thread
+// per Gaussian then issues three 16-byte vector atomics into its global
+// accumulator.  Nothing per pair or per voxel goes to HBM.
 #include "chain.cuh"
 #include "gve_int.cuh"
 

@@ -93,3 +93,23 @@ def test_recorded_traffic_follows_its_kernel_source(tmp_path, monkeypatch):
     src.write_text(src.read_text().replace("p[0] = 1;", "p[0] = 2;"))
     assert bench.recorded_traffic("t", 4000) is None                        # this kernel changed
     assert bench.recorded_traffic("missing", 4000) is None
+
+
+def test_batched_volumes_shard_across_ranks():
+    """The batched workload's volumes go to ranks with no exchange: each
+    volume to exactly one rank, deterministically, the largest first to the
+    least-loaded rank (so no rank holds more than the lightest rank plus the
+    largest volume)."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2608_14112_b300 import inputs
+    sizes = [int(np.prod(s)) for s in inputs.BATCHED_SHAPES]
+    assert bench.shard_volumes(sizes, 1, 0) == list(range(len(sizes)))
+    for ws in (2, 3, 4, 8):
+        shards = [bench.shard_volumes(sizes, ws, r) for r in range(ws)]
+        assert sorted(i for s in shards for i in s) == list(range(len(sizes)))
+        assert shards == [bench.shard_volumes(sizes, ws, r) for r in range(ws)]
+        loads = [sum(sizes[i] for i in s) for s in shards]
+        assert max(loads) - min(loads) <= max(sizes)

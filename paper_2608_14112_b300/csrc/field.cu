@@ -121,6 +121,91 @@ __device__ __forceinline__ void stage_chunk(const BrickArgs& a, uint32_t s0, int
     }
 }
 
+// One backward task: the sums of Gaussian j (staged record) over slices
+// zs0 .. zs0 + NZ - 1 of sub-brick sbt, added to its shared sums.  Whole
+// tasks take all SZ slices; the tail of a round may be split into halves.
+template <int B, int NZ>
+__device__ __forceinline__ void task_sums(const float4* s_rec, const float4* s_g, float* s_acc, int j, int sbt,
+                                          int zs0, int by, int bz, float fxb, float T)
+{
+    using S = BrickShape<B>;
+    constexpr int HALF = S::HALF, SY = S::SY, SZ = S::SZ;
+    constexpr int GBLK = SY * SZ * HALF + 1;
+    const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
+    const float2 nmu = f2(-r0.x);
+    float2 dx[HALF];
+#pragma unroll
+    for (int q = 0; q < HALF; ++q)
+        dx[q] = __fadd2_rn(make_float2(fxb + (float)(2 * q), fxb + (float)(2 * q + 1)), nmu);
+    const int yb = SY * (sbt & 1), zb = SZ * (sbt >> 1);
+    const float2 qxx = f2(r0.w), amp = f2(r2.w);
+    // h = G (a gn + gd); x-moments against the brick-local X = x - x0,
+    // shifted to dx = X + (x0 - mu_x) once per task below.  Per-voxel
+    // sums are packed; the per-row and per-slice sums are scalar, so
+    // they run beside the packed pipe instead of on it.
+    float2 A = make_float2(0.f, 0.f), R2 = A;
+    float S0 = 0.f, S1x = 0.f, S1y = 0.f, S1z = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
+#pragma unroll
+    for (int i = 0; i < NZ; ++i) {
+        const int zs = zs0 + i;
+        const float dz = __fsub_rn((float)(bz * B + zb + zs), r0.z);
+        const float e_ = __fmul_rn(r1.w, dz), f_ = __fmul_rn(r2.x, dz);
+        const float dzh = __fmul_rn(dz, __fmul_rn(r1.y, dz));
+        float T0 = 0.f, T1 = 0.f, Ty = 0.f;
+#pragma unroll
+        for (int yr = 0; yr < SY; ++yr) {
+            const float dy = __fsub_rn((float)(by * B + yb + yr), r0.y);
+            const float bb = __fmaf_rn(r1.z, dy, e_);
+            const float cc = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
+            const float2 b2 = f2(bb), c2 = f2(cc);
+            const float4* gp = s_g + sbt * GBLK + (yr + SY * zs) * HALF;
+            float2 R0 = make_float2(0.f, 0.f), R1 = R0;
+#pragma unroll
+            for (int q = 0; q < HALF; ++q) {
+                const float4 gv = gp[q];
+                const float2 t = __ffma2_rn(dx[q], __ffma2_rn(qxx, dx[q], b2), c2);
+                float2 G;
+                G.x = t.x > T ? ex2_approx(t.x) : 0.f;
+                G.y = t.y > T ? ex2_approx(t.y) : 0.f;
+                const float2 gn = make_float2(gv.x, gv.y);
+                const float2 h = __fmul2_rn(G, __ffma2_rn(amp, gn, make_float2(gv.z, gv.w)));
+                A = __ffma2_rn(G, gn, A);
+                R0 = __fadd2_rn(R0, h);
+                const float X0 = (float)(2 * q), X1 = (float)(2 * q + 1);
+                R1 = __ffma2_rn(h, make_float2(X0, X1), R1);
+                R2 = __ffma2_rn(h, make_float2(X0 * X0, X1 * X1), R2);
+            }
+            const float r0s = R0.x + R0.y, r1s = R1.x + R1.y;
+            const float dyr0 = dy * r0s;
+            S1y = fmaf(dy, r0s, S1y);
+            Sxy = fmaf(dy, r1s, Sxy);
+            Syy = fmaf(dy, dyr0, Syy);
+            T0 += r0s;
+            T1 += r1s;
+            Ty += dyr0;
+        }
+        S0 += T0;
+        S1x += T1;
+        S1z = fmaf(dz, T0, S1z);
+        Sxz = fmaf(dz, T1, Sxz);
+        Syz = fmaf(dz, Ty, Syz);
+        Szz = fmaf(dz * dz, T0, Szz);
+    }
+    const float del = __fsub_rn(fxb, r0.x);
+    float* sa = s_acc + j * kAccStride;
+    atomicAdd(sa + 0, A.x + A.y);
+    atomicAdd(sa + 1, S0);
+    atomicAdd(sa + 2, fmaf(del, S0, S1x));
+    atomicAdd(sa + 3, S1y);
+    atomicAdd(sa + 4, S1z);
+    atomicAdd(sa + 5, fmaf(del, fmaf(del, S0, 2.f * S1x), R2.x + R2.y));
+    atomicAdd(sa + 6, Syy);
+    atomicAdd(sa + 7, Szz);
+    atomicAdd(sa + 8, fmaf(del, S1y, Sxy));
+    atomicAdd(sa + 9, fmaf(del, S1z, Sxz));
+    atomicAdd(sa + 10, Syz);
+}
+
 // The fused evaluation of one brick (all threads of the CTA take part; the
 // shared arrays are the CTA's).  Launched one CTA per brick by k_brick, and
 // in a loop over the bricks of many volumes by the batched kernel.
@@ -407,81 +492,18 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
         }
         __syncthreads();
 
-        for (int tk = tid; tk < ntask; tk += NT) {
+        // whole tasks in rounds of NT; a last round of at most 16 tasks is
+        // taken by one warp as twice as many half tasks (SZ / 2 slices each)
+        const int full = ntask - ntask % NT, rem = ntask - full;
+        const bool split = SZ >= 2 && rem > 0 && 2 * rem <= 32;
+        for (int tk = tid; tk < (split ? full : ntask); tk += NT) {
             const int task = s_task[tk];
-            const int j = task & 255, sbt = task >> 8;
-            const float4 r0 = s_rec[3 * j], r1 = s_rec[3 * j + 1], r2 = s_rec[3 * j + 2];
-            const float2 nmu = f2(-r0.x);
-            float2 dx[HALF];
-#pragma unroll
-            for (int q = 0; q < HALF; ++q)
-                dx[q] = __fadd2_rn(make_float2(fxb + (float)(2 * q), fxb + (float)(2 * q + 1)), nmu);
-            const int yb = SY * (sbt & 1), zb = SZ * (sbt >> 1);
-            const float2 qxx = f2(r0.w), amp = f2(r2.w);
-            // h = G (a gn + gd); x-moments against the brick-local X = x - x0,
-            // shifted to dx = X + (x0 - mu_x) once per task below.  Per-voxel
-            // sums are packed; the per-row and per-slice sums are scalar, so
-            // they run beside the packed pipe instead of on it.
-            float2 A = make_float2(0.f, 0.f), R2 = A;
-            float S0 = 0.f, S1x = 0.f, S1y = 0.f, S1z = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
-#pragma unroll
-            for (int zs = 0; zs < SZ; ++zs) {
-                const float dz = __fsub_rn((float)(bz * B + zb + zs), r0.z);
-                const float e_ = __fmul_rn(r1.w, dz), f_ = __fmul_rn(r2.x, dz);
-                const float dzh = __fmul_rn(dz, __fmul_rn(r1.y, dz));
-                float T0 = 0.f, T1 = 0.f, Ty = 0.f;
-#pragma unroll
-                for (int yr = 0; yr < SY; ++yr) {
-                    const float dy = __fsub_rn((float)(by * B + yb + yr), r0.y);
-                    const float bb = __fmaf_rn(r1.z, dy, e_);
-                    const float cc = __fmaf_rn(dy, __fmaf_rn(r1.x, dy, f_), dzh);
-                    const float2 b2 = f2(bb), c2 = f2(cc);
-                    const float4* gp = s_g + sbt * GBLK + (yr + SY * zs) * HALF;
-                    float2 R0 = make_float2(0.f, 0.f), R1 = R0;
-#pragma unroll
-                    for (int q = 0; q < HALF; ++q) {
-                        const float4 gv = gp[q];
-                        const float2 t = __ffma2_rn(dx[q], __ffma2_rn(qxx, dx[q], b2), c2);
-                        float2 G;
-                        G.x = t.x > T ? ex2_approx(t.x) : 0.f;
-                        G.y = t.y > T ? ex2_approx(t.y) : 0.f;
-                        const float2 gn = make_float2(gv.x, gv.y);
-                        const float2 h = __fmul2_rn(G, __ffma2_rn(amp, gn, make_float2(gv.z, gv.w)));
-                        A = __ffma2_rn(G, gn, A);
-                        R0 = __fadd2_rn(R0, h);
-                        const float X0 = (float)(2 * q), X1 = (float)(2 * q + 1);
-                        R1 = __ffma2_rn(h, make_float2(X0, X1), R1);
-                        R2 = __ffma2_rn(h, make_float2(X0 * X0, X1 * X1), R2);
-                    }
-                    const float r0s = R0.x + R0.y, r1s = R1.x + R1.y;
-                    const float dyr0 = dy * r0s;
-                    S1y = fmaf(dy, r0s, S1y);
-                    Sxy = fmaf(dy, r1s, Sxy);
-                    Syy = fmaf(dy, dyr0, Syy);
-                    T0 += r0s;
-                    T1 += r1s;
-                    Ty += dyr0;
-                }
-                S0 += T0;
-                S1x += T1;
-                S1z = fmaf(dz, T0, S1z);
-                Sxz = fmaf(dz, T1, Sxz);
-                Syz = fmaf(dz, Ty, Syz);
-                Szz = fmaf(dz * dz, T0, Szz);
-            }
-            const float del = __fsub_rn(fxb, r0.x);
-            float* sa = s_acc + j * kAccStride;
-            atomicAdd(sa + 0, A.x + A.y);
-            atomicAdd(sa + 1, S0);
-            atomicAdd(sa + 2, fmaf(del, S0, S1x));
-            atomicAdd(sa + 3, S1y);
-            atomicAdd(sa + 4, S1z);
-            atomicAdd(sa + 5, fmaf(del, fmaf(del, S0, 2.f * S1x), R2.x + R2.y));
-            atomicAdd(sa + 6, Syy);
-            atomicAdd(sa + 7, Szz);
-            atomicAdd(sa + 8, fmaf(del, S1y, Sxy));
-            atomicAdd(sa + 9, fmaf(del, S1z, Sxz));
-            atomicAdd(sa + 10, Syz);
+            task_sums<B, SZ>(s_rec, s_g, s_acc, task & 255, task >> 8, 0, by, bz, fxb, T);
+        }
+        if (SZ >= 2 && split && tid < 2 * rem) {
+            const int task = s_task[full + tid % rem];
+            task_sums<B, (SZ >= 2 ? SZ / 2 : 1)>(s_rec, s_g, s_acc, task & 255, task >> 8, (tid / rem) * (SZ / 2), by,
+                                                  bz, fxb, T);
         }
         __syncthreads();
         for (int j = tid; j < cnt; j += NT) {

@@ -496,14 +496,20 @@ __device__ __forceinline__ void brick_body(const BrickArgs& a, const unsigned br
         // taken by one warp as twice as many half tasks (SZ / 2 slices each)
         const int full = ntask - ntask % NT, rem = ntask - full;
         const bool split = SZ >= 2 && rem > 0 && 2 * rem <= 32;
-        for (int tk = tid; tk < (split ? full : ntask); tk += NT) {
+        const bool split2x = SZ >= 2 && NT >= 64 && rem > 16 && rem <= 32;
+        for (int tk = tid; tk < (split || split2x ? full : ntask); tk += NT) {
             const int task = s_task[tk];
             task_sums<B, SZ>(s_rec, s_g, s_acc, task & 255, task >> 8, 0, by, bz, fxb, T);
         }
-        if (SZ >= 2 && split && tid < 2 * rem) {
-            const int task = s_task[full + tid % rem];
-            task_sums<B, (SZ >= 2 ? SZ / 2 : 1)>(s_rec, s_g, s_acc, task & 255, task >> 8, (tid / rem) * (SZ / 2), by,
-                                                  bz, fxb, T);
+        // a last round of 17 to 32 tasks: each of two warps takes one half of
+        // every task
+        const bool split2 = SZ >= 2 && NT >= 64 && rem > 16 && rem <= 32;
+        const bool half = (split && tid < 2 * rem) || (split2 && tid < 64 && (tid & 31) < rem);
+        if (SZ >= 2 && half) {
+            const int k = split ? tid % rem : (tid & 31), h = split ? tid / rem : (tid >> 5);
+            const int task = s_task[full + k];
+            task_sums<B, (SZ >= 2 ? SZ / 2 : 1)>(s_rec, s_g, s_acc, task & 255, task >> 8, h * (SZ / 2), by, bz, fxb,
+                                                  T);
         }
         __syncthreads();
         for (int j = tid; j < cnt; j += NT) {
